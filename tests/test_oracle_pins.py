@@ -1,0 +1,466 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these re-types an oracle formula: each compares the oracle with a
+published known answer, a closed form, an invariant of the definition, a
+hand-written example or a different construction of the same quantity.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2504_06067_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ------------------------------------------------------------------ Philox --
+def test_philox_known_answers(orc):
+    """Published Philox4x32-10 known-answer vectors (Salmon et al., SC'11)."""
+    for row in _read_golden("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in row]
+        out = orc.philox4x32_10(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_priorities_are_distinct_streams(orc):
+    # ref and member priorities come from different counters: same index,
+    # different stream word -> (almost surely) different words.
+    a = [orc.ref_priority(0, 3, j) for j in range(64)]
+    b = [orc.member_priority(0, 3, j) for j in range(64)]
+    assert a != b and len(set(a)) == 64
+
+
+# ------------------------------------------------------------- Das-Dennis --
+@pytest.mark.parametrize("m,p,w", [(3, 12, 91), (5, 20, 10626), (10, 3, 220), (10, 2, 55),
+                                   (2, 7, 8), (4, 1, 4)])
+def test_das_dennis_count_closed_form(orc, m, p, w):
+    """w = C(p+m-1, m-1) (the lattice of compositions of p into m parts)."""
+    assert orc.das_dennis_count(m, p) == w == math.comb(p + m - 1, m - 1)
+    Z = orc.refdirs(m, p)
+    assert Z.shape == (w, m)
+    # every row on the unit simplex, entries multiples of 1/p, rows distinct
+    assert np.allclose(Z.sum(1), 1.0, atol=1e-12)
+    k = Z * p
+    assert np.allclose(k, np.round(k), atol=1e-9)
+    assert len({tuple(np.round(r).astype(int)) for r in k}) == w
+
+
+def test_das_dennis_golden_m3_p2(orc):
+    Z = orc.refdirs(3, 2)
+    G = np.array([[float(x) for x in r] for r in _read_golden("das_dennis_m3_p2.txt")])
+    assert np.array_equal(Z, G)
+
+
+def test_das_dennis_two_layer(orc):
+    """Two layers: 220 outer (p1=3) + 55 inner (p2=2) = 275 for m = 10;
+    the inner layer is shrunk toward the centroid and still sums to 1."""
+    Z = orc.refdirs(10, 3, 2, 0.5)
+    assert Z.shape == (275, 10)
+    assert np.allclose(Z.sum(1), 1.0, atol=1e-12)
+    inner = Z[220:]
+    assert inner.min() >= 0.05 - 1e-15  # (1 - tau)/m = 0.05
+    # the vertices e_q are in the outer layer
+    for q in range(10):
+        e = np.zeros(10)
+        e[q] = 1.0
+        assert np.any(np.all(Z[:220] == e, axis=1))
+
+
+# --------------------------------------------------------------- dominance --
+def test_dominance_examples(orc):
+    assert orc.dominates([1, 2], [2, 3])
+    assert orc.dominates([1, 2], [1, 3])
+    assert not orc.dominates([1, 2], [1, 2])          # equal: no dominance
+    assert not orc.dominates([1, 3], [2, 2])          # incomparable
+    assert not orc.dominates([2, 2], [1, 3])
+    assert not orc.dominates([-0.0, 1.0], [0.0, 1.0])  # -0 == +0
+    assert not orc.dominates([0.0, 1.0], [-0.0, 1.0])
+    assert orc.dominates([-1.0, 0.0], [-0.0, 0.0])
+
+
+def test_dominance_is_product_order_on_grid(orc):
+    """On the integer grid {0,1,2}^m, a dominates b iff b - a is a nonzero
+    vector of N^m (closed form of the Pareto order), checked exhaustively."""
+    for m in (2, 3):
+        pts = list(itertools.product(range(3), repeat=m))
+        for a in pts:
+            for b in pts:
+                diff = [y - x for x, y in zip(a, b)]
+                expect = all(t >= 0 for t in diff) and any(t > 0 for t in diff)
+                assert orc.dominates(a, b) == expect
+
+
+def test_dominance_strict_partial_order(orc):
+    F = wl.objectives("grid", 40, 3, seed=1)
+    D = np.array([[orc.dominates(F[i], F[j]) for j in range(40)] for i in range(40)])
+    assert not D.diagonal().any()                 # irreflexive
+    assert not (D & D.T).any()                    # antisymmetric
+    D2 = (D.astype(int) @ D.astype(int)) > 0
+    assert not (D2 & ~D).any()                    # transitive
+
+
+# ---------------------------------------------------------------- sorting --
+def _front_invariants(orc, F, rank, N, full):
+    n2 = F.shape[0]
+    l = rank.max()
+    fronts = [np.flatnonzero(rank == k) for k in range(l + 1)]
+    assert sum(len(f) for f in fronts) == (n2 if full else int((rank >= 0).sum()))
+    for k, f in enumerate(fronts):
+        assert len(f) > 0
+        for i in f:              # mutually non-dominated
+            for j in f:
+                assert not orc.dominates(F[i], F[j])
+        if k > 0:                # dominated by some member of the previous front
+            for j in f:
+                assert any(orc.dominates(F[i], F[j]) for i in fronts[k - 1])
+        # no member of a later (or dropped) set dominates a member of front k
+        later = np.flatnonzero((rank > k) | (rank < 0))
+        for j in f:
+            for i in later:
+                assert not orc.dominates(F[i], F[j])
+    if not full:
+        cum = np.cumsum([len(f) for f in fronts])
+        assert cum[-1] >= N and (l == 0 or cum[-2] < N)
+
+
+@pytest.mark.parametrize("kind", wl.KINDS)
+def test_nds_invariants(orc, kind):
+    N = 30
+    F = wl.objectives(kind, 2 * N, 3, seed=2)
+    for full in (False, True):
+        rank, l = orc.nds(F, N, full_sort=full)
+        assert l == rank.max()
+        _front_invariants(orc, F, rank, N, full)
+
+
+def test_nds_grid_closed_form(orc):
+    """On the full grid {0..a}^m the front index of x is sum(x) (anti-diagonals)."""
+    for m, a in ((2, 5), (3, 3)):
+        pts = np.array(list(itertools.product(range(a + 1), repeat=m)), dtype=np.float32)
+        n2 = len(pts) - len(pts) % 2
+        pts = pts[:n2]
+        rank, _ = orc.nds(pts, n2 // 2, full_sort=True)
+        assert np.array_equal(rank, pts.sum(1).astype(int))
+
+
+def test_nds_chain_and_equal(orc):
+    F = wl.objectives("chain", 20, 4)
+    rank, l = orc.nds(F, 10, full_sort=True)
+    assert sorted(rank.tolist()) == list(range(20))
+    rank, l = orc.nds(F, 10)
+    assert l == 9 and (rank >= 0).sum() == 10
+    F = wl.objectives("equal", 20, 4)
+    rank, l = orc.nds(F, 10)
+    assert l == 0 and (rank == 0).all()
+
+
+# ---------------------------------------------------------- normalization --
+def test_normalize_axis_extremes_closed_form(orc):
+    """Extremes on the axes: z* = 0 and the hyperplane through A_q e_q has
+    intercepts exactly A_q."""
+    A = np.array([2.0, 3.0, 5.0, 0.5], dtype=np.float32)
+    m = 4
+    rng = np.random.default_rng(0)
+    inner = rng.random((12, m)).astype(np.float32) * 0.1 + 0.05
+    ext = np.diag(A)
+    F = np.vstack([inner[:6], ext, inner[6:]]).astype(np.float32)
+    n2 = F.shape[0]
+    F = np.vstack([F, F[:(n2 % 2)]])  # even
+    F[:, :] = np.where(F == 0.0, 0.0, F)
+    # make the ideal exactly 0: zeros in every column come from the axis points
+    rank = np.zeros(F.shape[0], dtype=np.int32)
+    zstar, a, extremes, fb = orc.normalize(F, rank, 0)
+    assert np.array_equal(zstar, np.zeros(m))
+    assert not fb
+    assert np.allclose(a, A.astype(np.float64), rtol=1e-12)
+    for q in range(m):
+        assert np.array_equal(F[extremes[q]], ext[q])
+
+
+def test_normalize_extremes_on_hyperplane(orc):
+    """When the solve succeeds, every extreme point lies on the normalised
+    hyperplane: sum_r (f_er - z*_r) / a_r = 1."""
+    for seed in range(5):
+        F = wl.objectives("late", 200, 5, seed=seed)
+        rank, l = orc.nds(F, 100)
+        zstar, a, ext, fb = orc.normalize(F, rank, l)
+        if fb:
+            continue
+        for q in range(5):
+            s = np.sum((F[ext[q]].astype(np.float64) - zstar) / a)
+            assert abs(s - 1.0) < 1e-9
+        # ideal point is the column minimum over S u F_l
+        T = (rank >= 0) & (rank <= l)
+        assert np.array_equal(zstar, F[T].min(0).astype(np.float64))
+
+
+def test_normalize_singular_fallback(orc):
+    """All members identical in every column but one: the extreme matrix is
+    singular; intercepts fall back to the maximum translated objective, and to
+    1 where that maximum is 0."""
+    m = 3
+    F = np.zeros((8, m), dtype=np.float32)
+    F[:, 0] = np.arange(8, dtype=np.float32)
+    F[:, 1] = 2.0
+    F[:, 2] = 7.0 - np.arange(8, dtype=np.float32)
+    rank = np.zeros(8, dtype=np.int32)
+    zstar, a, ext, fb = orc.normalize(F, rank, 0)
+    assert fb
+    assert np.array_equal(a, np.array([7.0, 1.0, 7.0]))
+
+
+# ------------------------------------------------------------ association --
+def test_associate_point_on_direction(orc):
+    """A point on direction j (after normalisation) has d = 0 and pi = j."""
+    Z = orc.refdirs(3, 4)
+    m = 3
+    zstar = np.zeros(m)
+    a = np.ones(m)
+    # choose interior directions (no ties with others along the ray)
+    js = [4, 7, 11]
+    F = np.array([Z[j] * s for j, s in zip(js, (0.5, 1.0, 3.0))] + [Z[0]], dtype=np.float32)
+    rank = np.zeros(4, dtype=np.int32)
+    pi, dist = orc.associate(F, rank, 0, zstar, a, Z)
+    assert pi[:3].tolist() == js
+    assert np.all(dist[:3] < 1e-7)
+
+
+def test_associate_matches_vector_rejection(orc):
+    """Eq. 2 with cos^2 equals the length of the rejection of f' from the
+    direction (a different construction of the perpendicular distance)."""
+    m = 4
+    Z = orc.refdirs(m, 5)
+    F = wl.objectives("late", 300, m, seed=3)
+    rank, l = orc.nds(F, 150)
+    zstar, a, _, _ = orc.normalize(F, rank, l)
+    pi, dist = orc.associate(F, rank, l, zstar, a, Z)
+    T = np.flatnonzero((rank >= 0) & (rank <= l))
+    Zh = Z / np.linalg.norm(Z, axis=1, keepdims=True)
+    for i in T:
+        fp = (F[i].astype(np.float64) - zstar) / a
+        proj = fp @ Zh.T
+        rej = np.linalg.norm(fp[None, :] - proj[:, None] * Zh, axis=1)
+        j = int(np.argmin(rej))
+        srt = np.sort(rej)
+        if srt[1] - srt[0] > 1e-9:
+            assert pi[i] == j
+        assert abs(dist[i] - rej[pi[i]]) < 1e-9 * max(1.0, np.linalg.norm(fp))
+    assert np.all(pi[rank < 0] == -1)
+
+
+def test_associate_2d_angle(orc):
+    """m = 2: perpendicular distance = |f'| |sin(theta_f - theta_z)|."""
+    Z = orc.refdirs(2, 9)
+    F = wl.objectives("uniform", 60, 2, seed=4)
+    rank = np.zeros(60, dtype=np.int32)
+    zstar = F.min(0).astype(np.float64)
+    a = (F.max(0).astype(np.float64) - zstar)
+    pi, dist = orc.associate(F, rank, 0, zstar, a, Z)
+    for i in range(60):
+        fp = (F[i].astype(np.float64) - zstar) / a
+        r = np.hypot(*fp)
+        th = math.atan2(fp[1], fp[0])
+        d = [r * abs(math.sin(th - math.atan2(z[1], z[0]))) for z in Z]
+        assert abs(dist[i] - min(d)) < 1e-12 * max(1.0, r)
+
+
+# ------------------------------------------------------------------ niching --
+def _niche_case(orc, kind, N, m, p, seed):
+    F = wl.objectives(kind, 2 * N, m, seed=seed)
+    Z = orc.refdirs(m, p)
+    rank, l = orc.nds(F, N)
+    nS = int(((rank >= 0) & (rank < l)).sum())
+    nFl = int((rank == l).sum())
+    K = N - nS
+    zstar, a, _, _ = orc.normalize(F, rank, l)
+    pi, dist = orc.associate(F, rank, l, zstar, a, Z)
+    return F, Z, rank, l, K, nFl, pi, dist
+
+
+@pytest.mark.parametrize("kind", ["early", "late", "uniform", "simplex", "dups", "grid"])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_niche_alg1_equals_alg2(orc, kind, seed):
+    """The Alg. 1 while-loop and the Alg. 2 cached batched loop (with the
+    last batch truncated in shuffled-reference order) pick identical sets."""
+    for N, m, p in ((40, 3, 6), (64, 5, 3), (30, 4, 4)):
+        F, Z, rank, l, K, nFl, pi, dist = _niche_case(orc, kind, N, m, p, seed)
+        if K == nFl:
+            continue
+        for gen in (0, 5):
+            a = orc.niche(rank, l, K, pi, dist, Z.shape[0], seed, gen, 0)
+            b = orc.niche(rank, l, K, pi, dist, Z.shape[0], seed, gen, 1)
+            assert a.sum() == K
+            assert np.array_equal(a, b)
+
+
+def test_niche_water_filling_and_nearest(orc):
+    """Properties of the loop: (1) final niche levels are filled evenly --
+    every reference with members left over ends with a count no lower than
+    the last count taken from any reference; (2) a reference with no member
+    in S that receives a pick receives its nearest member first."""
+    for seed in range(6):
+        F, Z, rank, l, K, nFl, pi, dist = _niche_case(orc, "early", 60, 3, 8, seed)
+        if K == nFl:
+            continue
+        w = Z.shape[0]
+        picked = orc.niche(rank, l, K, pi, dist, w, seed, 1, 0)
+        rho = np.bincount(pi[(rank >= 0) & (rank < l)], minlength=w)
+        rhop = np.bincount(pi[rank == l], minlength=w)
+        took = np.bincount(pi[picked], minlength=w)
+        final = rho + took
+        top_taken = max(final[j] - 1 for j in range(w) if took[j] > 0)
+        left = [final[j] for j in range(w) if rhop[j] > took[j]]
+        assert all(v >= top_taken for v in left)
+        for j in range(w):
+            if rho[j] == 0 and took[j] > 0:
+                mem = np.flatnonzero((rank == l) & (pi == j))
+                nearest = mem[np.argmin(dist[mem])]
+                assert picked[nearest]
+
+
+def test_niche_single_ref_nearest(orc):
+    """Hand example: one reference, no member in S, two F_l members, K = 1:
+    the nearest one is taken whatever the priorities."""
+    rank = np.array([0, 0], dtype=np.int32)
+    pi = np.array([0, 0], dtype=np.int32)
+    for dist in ([0.3, 0.1], [0.1, 0.3]):
+        d = np.array(dist)
+        for variant in (0, 1):
+            picked = orc.niche(rank, 0, 1, pi, d, 1, 0, 0, variant)
+            assert picked.tolist() == [d[0] < d[1], d[1] < d[0]]
+
+
+# ------------------------------------------------------------------ select --
+@pytest.mark.parametrize("kind", wl.KINDS)
+def test_select_invariants(orc, kind):
+    N, m = 48, 4
+    F = wl.objectives(kind, 2 * N, m, seed=7)
+    Z = orc.refdirs(m, 5)
+    r = orc.select(F, N, Z, seed=3, gen=2)
+    sel = r["selected"]
+    assert len(sel) == N and np.all(np.diff(sel) > 0)
+    rank, l = r["rank"], r["l"]
+    S = np.flatnonzero((rank >= 0) & (rank < l))
+    assert set(S) <= set(sel)
+    assert set(sel) <= set(np.flatnonzero((rank >= 0) & (rank <= l)))
+    r1 = orc.select(F, N, Z, seed=3, gen=2, variant=1)
+    assert np.array_equal(r1["selected"], sel)
+
+
+# --------------------------------------------------------------- variation --
+def test_sbx_conserves_parent_mean(orc):
+    """SBX children average to the parents' average (c1 + c2 = x1 + x2) when
+    no clipping and no mutation happen; with eta -> inf children = parents."""
+    N, d = 64, 10
+    X = (wl.population(N, d, seed=1) * 0.2 + 0.4).astype(np.float32)
+    rank = np.zeros(N, dtype=np.int32)
+    C = orc.vary(X, rank, seed=5, gen=0, eta_c=20.0, p_m=0.0)
+    # ranks equal -> tournament keeps the first drawn index; recover parents
+    for q in range(N // 2):
+        c1, c2 = C[2 * q].astype(np.float64), C[2 * q + 1].astype(np.float64)
+        # each variable: either copied or crossed; in both cases sums match
+        s = c1 + c2
+        # parents are rows of X: find a pair whose sums match
+        found = False
+        for a_ in range(N):
+            for b_ in range(N):
+                if np.allclose(X[a_].astype(np.float64) + X[b_], s, atol=2e-7):
+                    found = True
+                    break
+            if found:
+                break
+        assert found
+    C2 = orc.vary(X, rank, seed=5, gen=0, eta_c=1e9, p_m=0.0)
+    assert np.all(np.isin(C2.round(5), X.round(5)))
+
+
+def test_variation_bounds_and_identity(orc):
+    N, d = 50, 13
+    X = wl.population(N, d, seed=2)
+    rank = wl.parent_ranks(N, 3)
+    C = orc.vary(X, rank, seed=1, gen=4)
+    assert C.min() >= 0.0 and C.max() <= 1.0
+    # p_c = 0 and p_m = 0: children are copies of tournament winners
+    C0 = orc.vary(X, rank, seed=1, gen=4, p_c=0.0, p_m=0.0)
+    rows = {tuple(r) for r in X}
+    assert all(tuple(r) in rows for r in C0)
+    # the tournament prefers the lower front: the winners' mean rank is lower
+    idx = [next(i for i in range(N) if np.array_equal(X[i], r)) for r in C0]
+    assert rank[idx].mean() < rank.mean()
+
+
+def test_mutation_changes_about_pm_fraction(orc):
+    N, d = 400, 50
+    X = wl.population(N, d, seed=3)
+    rank = np.zeros(N, dtype=np.int32)
+    C0 = orc.vary(X, rank, seed=2, gen=0, p_m=0.0)
+    C1 = orc.vary(X, rank, seed=2, gen=0, p_m=0.1)
+    frac = np.mean(C0 != C1)
+    assert 0.08 < frac < 0.12
+
+
+# --------------------------------------------------------------- objective --
+def test_objective_front_sums_to_one(orc):
+    """g = 0 (x_v = 0.5 for v >= m-1): sum_j f_j = 1 (the closed-form front)."""
+    m, d = 5, 20
+    W = wl.objective_weights(m, 0)
+    X = wl.population(100, d, seed=4)
+    X[:, m - 1:] = 0.5
+    F = orc.evaluate(X, W)
+    assert np.allclose(F.astype(np.float64).sum(1), 1.0, atol=1e-6)
+    # W = 0: every objective equals (1 + g) / m
+    X2 = wl.population(10, d, seed=5)
+    F2 = orc.evaluate(X2, np.zeros_like(W))
+    g = ((X2[:, m - 1:].astype(np.float64) - 0.5) ** 2).sum(1)
+    assert np.allclose(F2, ((1 + g) / m)[:, None], rtol=1e-6)
+
+
+def test_init_uniform(orc):
+    X = orc.init_population(200, 30, seed=9)
+    assert X.min() >= 0 and X.max() < 1
+    assert abs(X.mean() - 0.5) < 0.01
+    assert not np.array_equal(X, orc.init_population(200, 30, seed=10))
+
+
+# --------------------------------------------------------------------- IGD --
+def test_igd_closed_forms(orc):
+    R = np.array([[0.0, 1.0], [1.0, 0.0]])
+    assert orc.igd(R.astype(np.float32), R) == 0.0
+    P = np.array([[0.0, 0.0]], dtype=np.float32)
+    assert abs(orc.igd(P, R) - 1.0) < 1e-15
+    P = np.array([[0.0, 1.0], [3.0, 4.0]], dtype=np.float32)
+    assert abs(orc.igd(P, R) - (0.0 + math.sqrt(2.0)) / 2) < 1e-15
+
+
+# -------------------------------------------------------------- full runs --
+def test_small_run_approaches_closed_form_front(orc):
+    """m = 3, N = 92, p = 12, d = 12: after 100 generations the rank-0 set
+    sits near the closed-form front (sum f = 1) and its IGD to a sample of
+    the true front is small."""
+    cfg = wl.SMALL
+    W = wl.objective_weights(cfg.m, cfg.seed)
+    Z = orc.refdirs(cfg.m, cfg.p1)
+    X, F, rank = orc.run(cfg.N, cfg.d, W, Z, cfg.seed, 100)
+    P = F[rank == 0].astype(np.float64)
+    assert np.mean(np.abs(P.sum(1) - 1.0)) < 0.05
+    y = wl.front_sample(cfg.m, 2000)
+    Xf = np.full((len(y), cfg.d), 0.5, dtype=np.float32)
+    Xf[:, :cfg.m - 1] = y
+    R = orc.evaluate(Xf, W).astype(np.float64)
+    igd_end = orc.igd(F[rank == 0], R)
+    X0 = orc.init_population(cfg.N, cfg.d, cfg.seed)
+    igd_start = orc.igd(orc.evaluate(X0, W), R)
+    assert igd_end < 0.1 * igd_start
