@@ -1,0 +1,188 @@
+/*
+ * nsga3.h -- C ABI of the GB300 NSGA-III environmental-selection engine.
+ *
+ * The method is the per-generation NSGA-III step of arXiv 2504.06067:
+ * variation of the parents (Alg. 1 line 1), merge R_t = P_t u Q_t (line 2),
+ * non-dominated sorting into F_s, F_l, F_drop (line 3), normalization and
+ * association with reference points (line 5; Alg. 2 lines 1-4, Eq. 2),
+ * niche counts (line 6; Alg. 2 lines 5-7) and niche selection of the last
+ * front (lines 7-19; Alg. 2 lines 8-26).  All objectives are minimised
+ * (Eq. 1).
+ *
+ * Conventions for every call:
+ *   - Objective matrices are FP32, row-major, one row per individual.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous and stream-ordered unless stated.
+ *   - Pointers documented as "any" may point to device memory or to host
+ *     memory (pinned or pageable); the library copies with cudaMemcpyDefault.
+ *     Pointers documented as "device" must be device memory.  The caller
+ *     owns every pointer it passes; the context owns all its workspace.
+ *   - A return value other than NSGA3_OK means the call enqueued nothing
+ *     (argument errors) or that a CUDA call failed; nsga3_last_error()
+ *     describes it.  Errors detected on the device (non-finite objectives,
+ *     timeouts, internal invariant failures) are sticky in the context and
+ *     returned by nsga3_sync().  Nothing aborts the process.
+ *   - One context must not be used from two host threads at once.
+ */
+#ifndef NSGA3_H
+#define NSGA3_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nsga3_ctx nsga3_ctx;
+
+typedef enum {
+    NSGA3_OK = 0,
+    NSGA3_EINVAL = 1,     /* bad argument */
+    NSGA3_ENOMEM = 2,     /* device allocation failed */
+    NSGA3_ECUDA = 3,      /* a CUDA runtime call failed */
+    NSGA3_ENONFINITE = 4, /* NaN or Inf in the objectives given to nsga3_select */
+    NSGA3_ETIMEOUT = 5,   /* a bounded device wait expired */
+    NSGA3_ESTATE = 6,     /* call not valid in this context state */
+    NSGA3_EINTERNAL = 7   /* a device-side invariant failed */
+} nsga3_status;
+
+/* Options of a context.  Initialise with nsga3_default_opts(). */
+typedef struct {
+    uint64_t seed;          /* Philox key (seed lo, seed hi) */
+    int p2;                 /* inner-layer Das-Dennis divisions, 0 = single layer */
+    double tau;             /* inner-layer shrink factor (z_in = (1-tau)/m + tau z) */
+    float eta_c;            /* SBX distribution index (default 20) */
+    float eta_m;            /* polynomial-mutation distribution index (default 20) */
+    float p_c;              /* crossover probability per pair (default 1) */
+    float p_m;              /* mutation probability per variable; < 0 -> 1/d (default) */
+    int full_sort;          /* 1: rank every front (F_drop gets its real front index) */
+    int debug_recheck_all;  /* 1: association rechecks every reference in FP64 */
+    const float* W;         /* host, m x (m-1) row-major weights of the softmax-simplex
+                               objective f = (1+g) softmax(W x[:m-1]); NULL: the context
+                               only serves nsga3_select / nsga3_set_population */
+} nsga3_opts;
+
+/* Fills *o with the defaults above (seed 0, single layer, tau 0.5). */
+void nsga3_default_opts(nsga3_opts* o);
+
+/*
+ * Creates a context for populations of N individuals (merged 2N), m
+ * objectives (2 <= m <= 10), d variables (d >= m - 1 when W is given) and
+ * Das-Dennis divisions ref_divisions >= 1 (Sec. II-C: w points uniform on
+ * the unit simplex; opts->p2 > 0 adds an inner layer).  N must be even,
+ * 2 <= N and 2N <= 2^21.  Allocates all device workspace (about
+ * (2N)^2 / 8 bytes for the dominance matrix) on the current device and
+ * builds the reference directions.  *out receives the context.
+ * Errors: EINVAL (sizes), ENOMEM, ECUDA.
+ */
+nsga3_status nsga3_create(int m, int d, int N, int ref_divisions, const nsga3_opts* opts,
+                          nsga3_ctx** out);
+
+/* Frees the context and its device memory (synchronises its work). */
+void nsga3_destroy(nsga3_ctx* ctx);
+
+/* Human-readable description of the last error of ctx (or of the last failed
+ * nsga3_create on this thread when ctx is NULL).  Never NULL. */
+const char* nsga3_last_error(const nsga3_ctx* ctx);
+
+/* Number w of reference directions. */
+int nsga3_num_refs(const nsga3_ctx* ctx);
+
+/* Copies the w x m FP64 reference directions (Das-Dennis, lexicographic order
+ * of the compositions, outer layer first) to Z (any).  Synchronous. */
+nsga3_status nsga3_get_refs(nsga3_ctx* ctx, double* Z);
+
+/*
+ * Environmental selection of N out of the merged 2N individuals (Alg. 1
+ * lines 3-19, Alg. 2).
+ *   objs      any, 2N x m FP32 objectives (minimised); read before return
+ *             on the stream.
+ *   ranks     any, 2N int32 out: 0-based front index for fronts F_1..F_l,
+ *             -1 for F_drop (with opts.full_sort every front is ranked).
+ *   selected  any, N int32 out: indices of P_{t+1} in ascending order.
+ * Random choices of the niche selection use this context's generation
+ * counter (nsga3_set_counter); nsga3_select does not advance it.
+ * Non-finite objectives set NSGA3_ENONFINITE, reported by nsga3_sync().
+ */
+nsga3_status nsga3_select(nsga3_ctx* ctx, const float* objs, int32_t* ranks, int32_t* selected,
+                          void* stream);
+
+/* Initial population: x ~ U[0,1]^d from Philox(i*d+v, 0, 6, 0), evaluated;
+ * parent ranks 0; generation counter 0.  Needs opts.W. */
+nsga3_status nsga3_init(nsga3_ctx* ctx, void* stream);
+
+/* Variation + objective only (Alg. 1 line 1): children of the current
+ * parents into rows N..2N-1 of the merged population (see
+ * nsga3_get_children).  Does not advance the counter.  Needs opts.W. */
+nsga3_status nsga3_vary(nsga3_ctx* ctx, void* stream);
+
+/* One generation (Alg. 1): variation, merge, selection, next population;
+ * advances the counter by one.  One CUDA-graph launch. Needs opts.W. */
+nsga3_status nsga3_step(nsga3_ctx* ctx, void* stream);
+
+/* `generations` calls of nsga3_step. */
+nsga3_status nsga3_run(nsga3_ctx* ctx, int generations, void* stream);
+
+/* Runs one generation of every context in ctxs[0..n) as one CUDA-graph
+ * launch per generation (the runs' kernels overlap on the device), for
+ * `generations` generations.  Every context needs opts.W and must live on
+ * the current device.  The graph is built on the first call for a given
+ * list and reused while the list is unchanged. */
+nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* stream);
+
+/* Copies the N parents out: X (any, N x d), F (any, N x m), rank (any, N).
+ * Any pointer may be NULL to skip it. */
+nsga3_status nsga3_get_population(nsga3_ctx* ctx, float* X, float* F, int32_t* rank, void* stream);
+
+/* Replaces the N parents: X (any, N x d), F (any, N x m), rank (any, N).
+ * Any pointer may be NULL to keep the current values. */
+nsga3_status nsga3_set_population(nsga3_ctx* ctx, const float* X, const float* F,
+                                  const int32_t* rank, void* stream);
+
+/* Copies the N children of the last nsga3_vary / nsga3_step variation:
+ * X (any, N x d), F (any, N x m); either may be NULL. */
+nsga3_status nsga3_get_children(nsga3_ctx* ctx, float* X, float* F, void* stream);
+
+/* Sets / reads the Philox generation counter (counter word 1). */
+nsga3_status nsga3_set_counter(nsga3_ctx* ctx, uint64_t gen, void* stream);
+nsga3_status nsga3_get_counter(nsga3_ctx* ctx, uint64_t* gen, void* stream); /* synchronous */
+
+/* Waits for `stream`, then returns and clears the context's sticky device
+ * status (NSGA3_OK, NSGA3_ENONFINITE, NSGA3_ETIMEOUT or NSGA3_EINTERNAL). */
+nsga3_status nsga3_sync(nsga3_ctx* ctx, void* stream);
+
+/*
+ * Diagnostics of the last selection (synchronous): info[0..11] =
+ *   l, |S|, K, |F_l|, niching needed, normalization fallback,
+ *   peel passes, |S u F_l|, level L*, refs taken at L*, list overflows,
+ *   debug recheck misses.
+ */
+nsga3_status nsga3_get_selection_info(nsga3_ctx* ctx, int32_t* info);
+
+/* Normalization of the last niching selection (synchronous): ideal point
+ * zstar[m], intercepts a[m] (FP64), extreme-point indices ext[m]; any may be
+ * NULL. */
+nsga3_status nsga3_get_normalization(nsga3_ctx* ctx, double* zstar, double* a, int32_t* ext);
+
+/* Association of the last niching selection (synchronous): pi (any, 2N
+ * int32, -1 outside S u F_l) and dist (any, 2N FP64). */
+nsga3_status nsga3_get_association(nsga3_ctx* ctx, int32_t* pi, double* dist);
+
+/*
+ * Device times (ms) of the phases of the last replayed generation or
+ * selection, measured by CUDA events recorded inside the graph:
+ *   ms[0] variation+objective, ms[1] dominance matrix, ms[2] front peel,
+ *   ms[3] normalization + association + niching, ms[4] compaction + gather,
+ *   ms[5] whole graph.  Synchronous; n is the capacity of ms (up to 6).
+ */
+nsga3_status nsga3_phase_times(nsga3_ctx* ctx, float* ms, int n);
+
+/* Kernel launches made by the last replayed generation or selection
+ * (fixed launches plus one per peel pass).  Synchronous. */
+nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NSGA3_H */

@@ -192,8 +192,8 @@ int orc_dominates(const float *a, const float *b, int m)
 /* Realised by dominator counting: a member enters the next front when     */
 /* its count of not-yet-ranked dominators reaches 0.  Sorting stops after  */
 /* the first front l with |F_1|+...+|F_l| >= N (Alg. 1: F_s, F_l, F_drop); */
-/* full_sort ranks every member.  rank = 0-based front index, -1 = F_drop. */
-/* Returns l, or -1 on error.                                              */
+/* full_sort goes on ranking every member (l is still that first front).   */
+/* rank = 0-based front index, -1 = F_drop.  Returns l, or -1 on error.    */
 /* ---------------------------------------------------------------------- */
 int orc_nds(const float *F, int n2, int m, int N, int full_sort, int32_t *rank)
 {
@@ -212,7 +212,7 @@ int orc_nds(const float *F, int n2, int m, int N, int full_sort, int32_t *rank)
     while (nf > 0) {
         for (int t = 0; t < nf; ++t) rank[front[t]] = k;
         cum += nf;
-        l = k;
+        if (l < 0 && cum >= N) l = k;
         if (!full_sort && cum >= N) break;
         int nn = 0;
         for (int t = 0; t < nf; ++t) {
@@ -268,6 +268,9 @@ int orc_normalize(const float *F, const int32_t *rank, int n2, int m, int l,
         }
     }
     if (!any) return ORC_EINVAL;
+    /* -0.0 and +0.0 are the same minimum; keep +0.0 so that f - z* is defined
+       by the value alone */
+    for (int q = 0; q < m; ++q) zstar[q] = zstar[q] + 0.0;
 
     /* ASF extreme points */
     for (int q = 0; q < m; ++q) {

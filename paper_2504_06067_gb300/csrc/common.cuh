@@ -1,0 +1,184 @@
+// common.cuh -- device-side types and helpers shared by the NSGA-III kernels.
+//
+// Layout of one run in HBM (n2 = 2N merged population, ld = n2 rounded up
+// to a multiple of 256, NW = ld / 32 bit-mask words):
+//   X     n2 x d  FP32 row-major   parents rows [0,N), children rows [N,2N)
+//   F     ld x m  FP32 row-major   rows >= n2 are NaN padding (never dominate)
+//   Dom   NW x ld u32              bit (i mod 32) of Dom[i/32][j] = "i dominates j"
+//   rank2 ld int32                 front index of the merged population, -1 = F_drop
+//   pi/dist ld                     association (reference index, FP64 distance)
+//   Zd    w x m   FP64             Das-Dennis directions; Zh w x M4 FP32 unit copy
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#define NSGA3_MAX_M 10
+#define NSGA3_TILE 256          // column tile of the dominance build; ld % 256 == 0
+#define NSGA3_PEEL_COLS 128     // columns per peel chunk (4 per lane, 32 lanes)
+
+// device status codes (same values as the C ABI's nsga3_status)
+#define DEV_OK 0
+#define DEV_ENONFINITE 4
+#define DEV_ETIMEOUT 5
+#define DEV_EINTERNAL 7
+
+// Random-number streams (third counter word of Philox).
+enum : uint32_t {
+    RNG_TOURNAMENT = 1,
+    RNG_SBX = 2,
+    RNG_PM = 3,
+    RNG_REFPRIO = 4,
+    RNG_MEMPRIO = 5,
+    RNG_INIT = 6
+};
+
+// Control block of one run, resident in device memory.  Written by the
+// selection kernels, read back by the host only for diagnostics.
+struct Ctrl {
+    uint32_t gen;            // Philox generation counter (word 1 of the counter)
+    int32_t status;          // DEV_* of the last failure, 0 if none
+    int32_t k;               // front being built by the current peel pass
+    int32_t cum;             // members ranked so far
+    int32_t l;               // selecting front (first with cum >= N)
+    int32_t nS;              // |S| = members of fronts < l
+    int32_t K;               // N - |S|
+    int32_t nFl;             // |F_l|
+    int32_t need_niche;      // K < |F_l|
+    int32_t fallback;        // normalization used the nadir fallback
+    int32_t passes;          // peel passes (kernel launches) in the last selection
+    uint32_t front_size;     // size of the front being built
+    uint32_t chunks_done;    // completion ticket of the peel pass
+    int32_t nT;              // |S u F_l| (association set)
+    int32_t Lstar;           // niche level threshold L*
+    int32_t rlev;            // refs taken at level L*
+    int32_t nsel;            // selected count written by the compaction
+    int32_t overflow;        // association candidate-list overflows (slow path taken)
+    int32_t recheck_miss;    // debug: association misses found by the full FP64 recheck
+    int32_t nlarge;          // references whose partial take needs the block-wide select
+    uint32_t zmin[NSGA3_MAX_M];  // ideal point as order-preserving uint of FP32
+    double zstar[NSGA3_MAX_M];   // ideal point (FP64, +0.0 for zero)
+    double a[NSGA3_MAX_M];       // intercepts
+    int32_t ext[NSGA3_MAX_M];    // extreme-point indices
+};
+
+// Device pointers and sizes of one run, passed by value to every kernel.
+struct RunView {
+    int m, d, N, n2, ld, NW, w, M4;   // M4 = m rounded up to a multiple of 4
+    int full_sort;
+    int debug_recheck_all;
+    uint64_t seed;
+    float eta_c, eta_m, p_c, p_m;
+    Ctrl* ctrl;
+    float* X;          // n2 x d
+    float* F;          // ld x m
+    int32_t* rank;     // parents' ranks (N), used by the tournament
+    float* Xtmp;       // N x d gather target
+    float* Ftmp;       // N x m
+    int32_t* ranktmp;  // N
+    uint32_t* Dom;     // NW x ld
+    int32_t* cnt;      // ld   remaining dominator counts
+    int32_t* rank2;    // ld   merged ranks
+    uint32_t* rem;     // NW   not-yet-ranked mask
+    uint32_t* front;   // 2 x NW  ping-pong front masks
+    uint32_t* chunk_done;  // ld / NSGA3_PEEL_COLS tickets
+    uint32_t* selmask;     // NW picked members of F_l
+    int32_t* Tlist;        // n2 members of S u F_l
+    double* fprime;        // n2 x m  normalised objectives (indexed by T slot)
+    double* fnorm;         // n2      |f'|
+    float* uhat;           // n2 x M4 FP32 unit vectors
+    int32_t* pi;           // ld
+    double* dist;          // ld
+    double* ext_part;      // parts x m  per-block ASF minima
+    int32_t* ext_idx;      // parts x m
+    double* nad_part;      // parts x m  per-block maxima of f - z*
+    int ext_parts;
+    int32_t* rho;          // w
+    int32_t* rhop;         // w
+    int32_t* take;         // w
+    int32_t* ref_off;      // w + 1
+    int32_t* cursor;       // w
+    int32_t* bucket;       // n2
+    int4* large;           // w   (ref, members still to take, excluded member, -)
+    int32_t* sel;          // N   selected indices, ascending
+    const double* Zd;      // w x m
+    const double* nz;      // w
+    const float* Zh;       // w x M4
+    const float* Wobj;     // m x (m-1)
+};
+
+// ------------------------------------------------------------ Philox ------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit products by the published multipliers; the key advances by
+// the published Weyl increments between rounds.
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint64_t seed)
+{
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t lo0 = 0xD2511F53u * c0;
+        uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+        uint32_t lo1 = 0xCD9E8D57u * c2;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+// uniform FP32 in [0,1): top 24 bits of the word times 2^-24 (exact)
+__device__ __forceinline__ float u01(uint32_t w) { return (float)(w >> 8) * 5.9604644775390625e-08f; }
+// integer in [0,n): (w * n) >> 32
+__device__ __forceinline__ uint32_t bounded(uint32_t w, uint32_t n)
+{
+    return (uint32_t)(((uint64_t)w * (uint64_t)n) >> 32);
+}
+
+// ------------------------------------------------- ordered float bits -----
+__device__ __forceinline__ uint32_t f2ord(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// -------------------------------------------------------- warp helpers ----
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void set_status(Ctrl* c, int s)
+{
+    atomicCAS(&c->status, 0, s);
+}
+
+__device__ __forceinline__ int read_status(const Ctrl* c)
+{
+    return *(volatile const int32_t*)&c->status;
+}
+
+// lexicographic (value, index) minimum for doubles
+__device__ __forceinline__ bool lex_less(double a, int ia, double b, int ib)
+{
+    return a < b || (a == b && ia < ib);
+}

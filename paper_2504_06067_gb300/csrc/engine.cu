@@ -1,0 +1,714 @@
+// engine.cu -- NSGA-III run context, device workspace, CUDA-graph capture of
+// a selection / a generation, and the C ABI declared in include/nsga3.h.
+//
+// A generation is captured once per context as a CUDA graph:
+//   vary+eval -> reset -> dominance -> WHILE(peel pass) -> post-peel
+//   -> IF(niching needed){ ideal, extremes, solve, prep, scan, level,
+//                           bucket, pick } -> compaction -> gather -> gen++
+// The WHILE node replays the peel kernel until its last CTA clears the
+// condition (one pass per front), and the IF node skips the niching when
+// |S| + |F_l| == N, so a replay never returns to the host.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "nsga3.h"
+
+cudaError_t niche_init_attributes();
+
+namespace {
+
+thread_local std::string g_create_error;
+
+enum { EV_START, EV_VARY, EV_DOM, EV_PEEL, EV_NICHE, EV_END, EV_COUNT };
+
+__global__ void k_set_gen(Ctrl* c, uint32_t gen) { c->gen = gen; }
+
+}  // namespace
+
+struct nsga3_ctx {
+    int device = 0, num_sms = 0;
+    int m = 0, d = 0, N = 0, n2 = 0, ld = 0, NW = 0, w = 0, M4 = 0, p1 = 0, p2 = 0;
+    double tau = 0.5;
+    nsga3_opts opts{};
+    bool has_W = false;
+    RunView v{};    // generation view (population buffers)
+    RunView vs{};   // selection view (own objective buffer)
+    std::vector<void*> allocs;
+    cudaGraphExec_t gx_select = nullptr, gx_step = nullptr;
+    cudaStream_t cap = nullptr, cap2 = nullptr;
+    cudaEvent_t ev[EV_COUNT] = {};
+    int nsplit = 1;
+    int last_kind = 0;  // 1 = select, 2 = step
+    std::string err;
+    // batched graph cache
+    std::vector<nsga3_ctx*> batch_key;
+    cudaGraphExec_t gx_batch = nullptr;
+};
+
+namespace {
+
+nsga3_status fail(nsga3_ctx* c, nsga3_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_create_error = buf;
+    return s;
+}
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(ctx, NSGA3_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                     \
+    } while (0)
+
+long long binom(int n, int k)
+{
+    if (k < 0 || k > n) return 0;
+    long long r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+template <typename T>
+nsga3_status alloc(nsga3_ctx* ctx, T** p, size_t count)
+{
+    void* q = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, NSGA3_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return NSGA3_OK;
+}
+
+#define AL(ptr, count)                                       \
+    do {                                                     \
+        nsga3_status s_ = alloc(ctx, &(ptr), (size_t)(count)); \
+        if (s_ != NSGA3_OK) return s_;                       \
+    } while (0)
+
+// Adds a conditional node after the capture's current dependencies and
+// returns its body graph; later captured work depends on the node.
+nsga3_status add_conditional(nsga3_ctx* ctx, cudaStream_t s, cudaGraphConditionalNodeType type,
+                             unsigned dflt, cudaGraphConditionalHandle* h, cudaGraph_t* body)
+{
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
+    if (st != cudaStreamCaptureStatusActive) return fail(ctx, NSGA3_ECUDA, "stream is not capturing");
+    CK(cudaGraphConditionalHandleCreate(h, g, dflt, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = *h;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+    *body = p.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return NSGA3_OK;
+}
+
+nsga3_status record_event(nsga3_ctx* ctx, cudaStream_t s, int which, bool events)
+{
+    if (!events) return NSGA3_OK;
+    CK(cudaEventRecordWithFlags(ctx->ev[which], s, cudaEventRecordExternal));
+    return NSGA3_OK;
+}
+
+// Records the selection pipeline of view `v` into the capture running on `s`
+// (`s2` is a spare stream used to capture conditional bodies).
+nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, cudaStream_t s2,
+                              bool check_finite, bool events)
+{
+    CK(launch_sel_reset(v, s));
+    if (check_finite) CK(launch_check_finite(v, s));
+    CK(launch_dominance(v, s));
+    nsga3_status st = record_event(ctx, s, EV_DOM, events);
+    if (st) return st;
+    cudaGraphConditionalHandle h_peel, h_niche;
+    cudaGraph_t body;
+    st = add_conditional(ctx, s, cudaGraphCondTypeWhile, 1u, &h_peel, &body);
+    if (st) return st;
+    CK(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    {
+        cudaError_t e = launch_peel(v, ctx->nsplit, h_peel, s2);
+        cudaGraph_t tmp;
+        cudaError_t e2 = cudaStreamEndCapture(s2, &tmp);
+        CK(e);
+        CK(e2);
+    }
+    st = record_event(ctx, s, EV_PEEL, events);
+    if (st) return st;
+    // the IF handle is created first so that post-peel can set it
+    {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+        CK(cudaGraphConditionalHandleCreate(&h_niche, g, 0u, cudaGraphCondAssignDefault));
+    }
+    CK(launch_post_peel(v, h_niche, s));
+    {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+        cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+        p.conditional.handle = h_niche;
+        p.conditional.type = cudaGraphCondTypeIf;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+        body = p.conditional.phGraph_out[0];
+        CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    }
+    CK(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    {
+        cudaError_t e = cudaSuccess;
+        if (e == cudaSuccess) e = launch_norm_ideal(v, s2);
+        if (e == cudaSuccess) e = launch_norm_extreme(v, s2);
+        if (e == cudaSuccess) e = launch_norm_solve(v, s2);
+        if (e == cudaSuccess) e = launch_assoc_prep(v, s2);
+        if (e == cudaSuccess) e = launch_assoc_scan(v, s2);
+        if (e == cudaSuccess) e = launch_level(v, s2);
+        if (e == cudaSuccess) e = launch_bucket(v, s2);
+        if (e == cudaSuccess) e = launch_pick(v, s2);
+        cudaGraph_t tmp;
+        cudaError_t e2 = cudaStreamEndCapture(s2, &tmp);
+        CK(e);
+        CK(e2);
+    }
+    st = record_event(ctx, s, EV_NICHE, events);
+    if (st) return st;
+    CK(launch_compact(v, s));
+    return NSGA3_OK;
+}
+
+nsga3_status record_generation(nsga3_ctx* ctx, cudaStream_t s, cudaStream_t s2, bool events)
+{
+    nsga3_status st = record_event(ctx, s, EV_START, events);
+    if (st) return st;
+    CK(launch_vary_eval(ctx->v, s));
+    st = record_event(ctx, s, EV_VARY, events);
+    if (st) return st;
+    st = record_selection(ctx, ctx->v, s, s2, false, events);
+    if (st) return st;
+    CK(launch_gather(ctx->v, s));
+    CK(launch_bump_gen(ctx->v, s));
+    return record_event(ctx, s, EV_END, events);
+}
+
+nsga3_status build_graphs(nsga3_ctx* ctx)
+{
+    cudaGraph_t g = nullptr;
+    // selection graph
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeRelaxed));
+    nsga3_status st = record_event(ctx, ctx->cap, EV_START, true);
+    if (!st) st = record_event(ctx, ctx->cap, EV_VARY, true);
+    if (!st) st = record_selection(ctx, ctx->vs, ctx->cap, ctx->cap2, true, true);
+    if (!st) st = record_event(ctx, ctx->cap, EV_END, true);
+    {
+        cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
+        if (st) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        CK(e);
+    }
+    CK(cudaGraphInstantiate(&ctx->gx_select, g, 0));
+    cudaGraphDestroy(g);
+    g = nullptr;
+    if (!ctx->has_W) return NSGA3_OK;
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeRelaxed));
+    st = record_generation(ctx, ctx->cap, ctx->cap2, true);
+    {
+        cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
+        if (st) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        CK(e);
+    }
+    CK(cudaGraphInstantiate(&ctx->gx_step, g, 0));
+    cudaGraphDestroy(g);
+    return NSGA3_OK;
+}
+
+nsga3_status setup(nsga3_ctx* ctx)
+{
+    const int m = ctx->m, d = ctx->d, N = ctx->N, n2 = ctx->n2, ld = ctx->ld, NW = ctx->NW;
+    const int w = ctx->w, M4 = ctx->M4;
+    RunView& v = ctx->v;
+    v.m = m;
+    v.d = d;
+    v.N = N;
+    v.n2 = n2;
+    v.ld = ld;
+    v.NW = NW;
+    v.w = w;
+    v.M4 = M4;
+    v.full_sort = ctx->opts.full_sort ? 1 : 0;
+    v.debug_recheck_all = ctx->opts.debug_recheck_all ? 1 : 0;
+    v.seed = ctx->opts.seed;
+    v.eta_c = ctx->opts.eta_c;
+    v.eta_m = ctx->opts.eta_m;
+    v.p_c = ctx->opts.p_c;
+    v.p_m = ctx->opts.p_m < 0.0f ? 1.0f / (float)d : ctx->opts.p_m;
+    v.ext_parts = (n2 + 255) / 256;
+    if (v.ext_parts > 256) v.ext_parts = 256;
+
+    AL(v.ctrl, 1);
+    AL(v.X, (size_t)n2 * d);
+    AL(v.F, (size_t)ld * m);
+    AL(v.rank, N);
+    AL(v.Xtmp, (size_t)N * d);
+    AL(v.Ftmp, (size_t)N * m);
+    AL(v.ranktmp, N);
+    AL(v.Dom, (size_t)NW * ld);
+    AL(v.cnt, ld);
+    AL(v.rank2, ld);
+    AL(v.rem, NW);
+    AL(v.front, 2 * NW);
+    AL(v.chunk_done, ld / NSGA3_PEEL_COLS);
+    AL(v.selmask, NW);
+    AL(v.Tlist, n2);
+    AL(v.fprime, (size_t)n2 * m);
+    AL(v.fnorm, n2);
+    AL(v.uhat, (size_t)n2 * M4);
+    AL(v.pi, ld);
+    AL(v.dist, ld);
+    AL(v.ext_part, (size_t)v.ext_parts * m);
+    AL(v.ext_idx, (size_t)v.ext_parts * m);
+    AL(v.nad_part, (size_t)v.ext_parts * m);
+    AL(v.rho, w);
+    AL(v.rhop, w);
+    AL(v.take, w);
+    AL(v.ref_off, w + 1);
+    AL(v.cursor, w);
+    AL(v.bucket, n2);
+    AL(v.large, w);
+    AL(v.sel, N);
+    double* Zd;
+    double* nz;
+    float* Zh;
+    float* Wd;
+    AL(Zd, (size_t)w * m);
+    AL(nz, w);
+    AL(Zh, (size_t)w * M4);
+    AL(Wd, (size_t)m * (m - 1));
+    v.Zd = Zd;
+    v.nz = nz;
+    v.Zh = Zh;
+    v.Wobj = Wd;
+    ctx->vs = v;
+    AL(ctx->vs.F, (size_t)ld * m);
+
+    CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&ctx->cap2, cudaStreamNonBlocking));
+    for (int e = 0; e < EV_COUNT; ++e) CK(cudaEventCreate(&ctx->ev[e]));
+    cudaStream_t s = ctx->cap;
+    CK(cudaMemsetAsync(v.ctrl, 0, sizeof(Ctrl), s));
+    CK(cudaMemsetAsync(v.Dom, 0, (size_t)NW * ld * sizeof(uint32_t), s));
+    CK(cudaMemsetAsync(v.rank, 0, (size_t)N * sizeof(int32_t), s));
+    CK(cudaMemsetAsync(v.X, 0, (size_t)n2 * d * sizeof(float), s));
+    CK(cudaMemsetAsync(v.F, 0, (size_t)ld * m * sizeof(float), s));
+    CK(cudaMemsetAsync(ctx->vs.F, 0, (size_t)ld * m * sizeof(float), s));
+    CK(cudaMemsetAsync(v.pi, 0xff, (size_t)ld * sizeof(int32_t), s));
+    CK(cudaMemsetAsync(v.dist, 0, (size_t)ld * sizeof(double), s));
+    CK(launch_nan_pad(v, s));
+    CK(launch_nan_pad(ctx->vs, s));
+    CK(launch_refdirs(v, ctx->p1, ctx->p2, ctx->tau, Zd, nz, Zh, s));
+    if (ctx->has_W)
+        CK(cudaMemcpyAsync(Wd, ctx->opts.W, (size_t)m * (m - 1) * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->nsplit = peel_nsplit(v, ctx->num_sms);
+    return build_graphs(ctx);
+}
+
+std::mutex g_attr_mutex;
+bool g_attr_done = false;
+
+nsga3_status init_attributes(nsga3_ctx* ctx)
+{
+    std::lock_guard<std::mutex> lk(g_attr_mutex);
+    if (g_attr_done) return NSGA3_OK;
+    CK(niche_init_attributes());
+    g_attr_done = true;
+    return NSGA3_OK;
+}
+
+nsga3_status device_status(nsga3_ctx* ctx, bool clear)
+{
+    int32_t st = 0;
+    CK(cudaMemcpy(&st, &ctx->v.ctrl->status, sizeof st, cudaMemcpyDeviceToHost));
+    if (clear && st) CK(cudaMemset(&ctx->v.ctrl->status, 0, sizeof st));
+    return (nsga3_status)st;
+}
+
+}  // namespace
+
+// =============================================================== C ABI ====
+extern "C" {
+
+void nsga3_default_opts(nsga3_opts* o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->seed = 0;
+    o->p2 = 0;
+    o->tau = 0.5;
+    o->eta_c = 20.0f;
+    o->eta_m = 20.0f;
+    o->p_c = 1.0f;
+    o->p_m = -1.0f;
+    o->full_sort = 0;
+    o->debug_recheck_all = 0;
+    o->W = nullptr;
+}
+
+nsga3_status nsga3_create(int m, int d, int N, int ref_divisions, const nsga3_opts* opts,
+                          nsga3_ctx** out)
+{
+    nsga3_ctx* ctx = nullptr;
+    if (!out) return fail(nullptr, NSGA3_EINVAL, "out is NULL");
+    *out = nullptr;
+    nsga3_opts o;
+    nsga3_default_opts(&o);
+    if (opts) o = *opts;
+    if (m < 2 || m > NSGA3_MAX_M) return fail(nullptr, NSGA3_EINVAL, "m=%d outside [2, %d]", m, NSGA3_MAX_M);
+    if (N < 2 || (N & 1)) return fail(nullptr, NSGA3_EINVAL, "N=%d must be even and >= 2", N);
+    if (N > (1 << 20)) return fail(nullptr, NSGA3_EINVAL, "N=%d above 2^20", N);
+    if (d < 1) return fail(nullptr, NSGA3_EINVAL, "d=%d < 1", d);
+    if (o.W && d < m - 1) return fail(nullptr, NSGA3_EINVAL, "d=%d < m-1 with an objective", d);
+    if ((long long)N * d >= (1LL << 32)) return fail(nullptr, NSGA3_EINVAL, "N*d must be < 2^32");
+    if (ref_divisions < 1 || o.p2 < 0) return fail(nullptr, NSGA3_EINVAL, "bad reference divisions");
+    if (!(o.tau >= 0.0 && o.tau <= 1.0)) return fail(nullptr, NSGA3_EINVAL, "tau outside [0,1]");
+    long long w = binom(ref_divisions + m - 1, m - 1) + (o.p2 > 0 ? binom(o.p2 + m - 1, m - 1) : 0);
+    if (w < 1 || w > (1LL << 24)) return fail(nullptr, NSGA3_EINVAL, "reference set size %lld", w);
+    ctx = new nsga3_ctx();
+    ctx->m = m;
+    ctx->d = d;
+    ctx->N = N;
+    ctx->n2 = 2 * N;
+    ctx->ld = (ctx->n2 + NSGA3_TILE - 1) / NSGA3_TILE * NSGA3_TILE;
+    ctx->NW = ctx->ld / 32;
+    ctx->w = (int)w;
+    ctx->M4 = (m + 3) & ~3;
+    ctx->p1 = ref_divisions;
+    ctx->p2 = o.p2;
+    ctx->tau = o.tau;
+    ctx->opts = o;
+    ctx->has_W = o.W != nullptr;  // W is read during create only
+    nsga3_status st = NSGA3_OK;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        st = fail(ctx, NSGA3_ECUDA, "no CUDA device");
+    }
+    if (!st) st = init_attributes(ctx);
+    if (!st) st = setup(ctx);
+    ctx->opts.W = nullptr;
+    if (st) {
+        g_create_error = ctx->err;
+        nsga3_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return NSGA3_OK;
+}
+
+void nsga3_destroy(nsga3_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    if (ctx->gx_batch) cudaGraphExecDestroy(ctx->gx_batch);
+    if (ctx->gx_select) cudaGraphExecDestroy(ctx->gx_select);
+    if (ctx->gx_step) cudaGraphExecDestroy(ctx->gx_step);
+    for (int e = 0; e < EV_COUNT; ++e)
+        if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->cap2) cudaStreamDestroy(ctx->cap2);
+    for (void* p : ctx->allocs) cudaFree(p);
+    cudaGetLastError();
+    delete ctx;
+}
+
+const char* nsga3_last_error(const nsga3_ctx* ctx)
+{
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+int nsga3_num_refs(const nsga3_ctx* ctx) { return ctx ? ctx->w : 0; }
+
+nsga3_status nsga3_get_refs(nsga3_ctx* ctx, double* Z)
+{
+    if (!ctx || !Z) return fail(ctx, NSGA3_EINVAL, "null argument");
+    CK(cudaMemcpy(Z, ctx->v.Zd, (size_t)ctx->w * ctx->m * sizeof(double), cudaMemcpyDefault));
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_select(nsga3_ctx* ctx, const float* objs, int32_t* ranks, int32_t* selected,
+                          void* stream)
+{
+    if (!ctx || !objs || !ranks || !selected) return fail(ctx, NSGA3_EINVAL, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(ctx->vs.F, objs, (size_t)ctx->n2 * ctx->m * sizeof(float), cudaMemcpyDefault, s));
+    CK(cudaGraphLaunch(ctx->gx_select, s));
+    CK(cudaMemcpyAsync(ranks, ctx->vs.rank2, (size_t)ctx->n2 * sizeof(int32_t), cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(selected, ctx->vs.sel, (size_t)ctx->N * sizeof(int32_t), cudaMemcpyDefault, s));
+    ctx->last_kind = 1;
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_init(nsga3_ctx* ctx, void* stream)
+{
+    if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
+    if (!ctx->has_W) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W was NULL)");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(launch_init(ctx->v, s));
+    k_set_gen<<<1, 1, 0, s>>>(ctx->v.ctrl, 0u);
+    CK(cudaGetLastError());
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_vary(nsga3_ctx* ctx, void* stream)
+{
+    if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
+    if (!ctx->has_W) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W was NULL)");
+    CK(launch_vary_eval(ctx->v, (cudaStream_t)stream));
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_step(nsga3_ctx* ctx, void* stream)
+{
+    if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
+    if (!ctx->gx_step) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W was NULL)");
+    CK(cudaGraphLaunch(ctx->gx_step, (cudaStream_t)stream));
+    ctx->last_kind = 2;
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_run(nsga3_ctx* ctx, int generations, void* stream)
+{
+    if (!ctx || generations < 0) return fail(ctx, NSGA3_EINVAL, "bad arguments");
+    for (int g = 0; g < generations; ++g) {
+        nsga3_status st = nsga3_step(ctx, stream);
+        if (st) return st;
+    }
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* stream)
+{
+    nsga3_ctx* ctx = (n > 0 && ctxs) ? ctxs[0] : nullptr;
+    if (!ctx || generations < 0) return fail(ctx, NSGA3_EINVAL, "bad arguments");
+    for (int r = 0; r < n; ++r)
+        if (!ctxs[r] || !ctxs[r]->has_W) return fail(ctx, NSGA3_EINVAL, "run %d has no objective", r);
+    std::vector<nsga3_ctx*> key(ctxs, ctxs + n);
+    if (!ctx->gx_batch || ctx->batch_key != key) {
+        if (ctx->gx_batch) {
+            cudaGraphExecDestroy(ctx->gx_batch);
+            ctx->gx_batch = nullptr;
+        }
+        // one branch per run: fork from the capture stream with events
+        std::vector<cudaStream_t> br(n), br2(n);
+        std::vector<cudaEvent_t> evs(n + 1);
+        nsga3_status st = NSGA3_OK;
+        for (int r = 0; r < n && !st; ++r) {
+            if (cudaStreamCreateWithFlags(&br[r], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&br2[r], cudaStreamNonBlocking) != cudaSuccess)
+                st = fail(ctx, NSGA3_ECUDA, "stream creation failed");
+        }
+        for (int r = 0; r <= n && !st; ++r)
+            if (cudaEventCreateWithFlags(&evs[r], cudaEventDisableTiming) != cudaSuccess)
+                st = fail(ctx, NSGA3_ECUDA, "event creation failed");
+        cudaGraph_t g = nullptr;
+        if (!st) {
+            cudaStream_t s0 = ctx->cap;
+            if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+                st = fail(ctx, NSGA3_ECUDA, "capture begin failed");
+            if (!st && cudaEventRecord(evs[n], s0) != cudaSuccess) st = fail(ctx, NSGA3_ECUDA, "fork failed");
+            for (int r = 0; r < n && !st; ++r) {
+                if (cudaStreamWaitEvent(br[r], evs[n], 0) != cudaSuccess) {
+                    st = fail(ctx, NSGA3_ECUDA, "fork wait failed");
+                    break;
+                }
+                st = record_generation(ctxs[r], br[r], br2[r], false);
+                if (st) {
+                    ctx->err = ctxs[r]->err;
+                    break;
+                }
+                if (cudaEventRecord(evs[r], br[r]) != cudaSuccess ||
+                    cudaStreamWaitEvent(s0, evs[r], 0) != cudaSuccess)
+                    st = fail(ctx, NSGA3_ECUDA, "join failed");
+            }
+            cudaError_t e = cudaStreamEndCapture(s0, &g);
+            if (!st && e != cudaSuccess) st = fail(ctx, NSGA3_ECUDA, "capture failed: %s", cudaGetErrorString(e));
+            if (!st && cudaGraphInstantiate(&ctx->gx_batch, g, 0) != cudaSuccess)
+                st = fail(ctx, NSGA3_ECUDA, "batched graph instantiation failed");
+            if (g) cudaGraphDestroy(g);
+        }
+        for (int r = 0; r < n; ++r) {
+            if (br[r]) cudaStreamDestroy(br[r]);
+            if (br2[r]) cudaStreamDestroy(br2[r]);
+        }
+        for (int r = 0; r <= n; ++r)
+            if (evs[r]) cudaEventDestroy(evs[r]);
+        cudaGetLastError();
+        if (st) return st;
+        ctx->batch_key = key;
+    }
+    for (int g = 0; g < generations; ++g) CK(cudaGraphLaunch(ctx->gx_batch, (cudaStream_t)stream));
+    for (int r = 0; r < n; ++r) ctxs[r]->last_kind = 3;
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_get_population(nsga3_ctx* ctx, float* X, float* F, int32_t* rank, void* stream)
+{
+    if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (X) CK(cudaMemcpyAsync(X, ctx->v.X, (size_t)ctx->N * ctx->d * sizeof(float), cudaMemcpyDefault, s));
+    if (F) CK(cudaMemcpyAsync(F, ctx->v.F, (size_t)ctx->N * ctx->m * sizeof(float), cudaMemcpyDefault, s));
+    if (rank) CK(cudaMemcpyAsync(rank, ctx->v.rank, (size_t)ctx->N * sizeof(int32_t), cudaMemcpyDefault, s));
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_set_population(nsga3_ctx* ctx, const float* X, const float* F, const int32_t* rank,
+                                  void* stream)
+{
+    if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (X) CK(cudaMemcpyAsync(ctx->v.X, X, (size_t)ctx->N * ctx->d * sizeof(float), cudaMemcpyDefault, s));
+    if (F) CK(cudaMemcpyAsync(ctx->v.F, F, (size_t)ctx->N * ctx->m * sizeof(float), cudaMemcpyDefault, s));
+    if (rank) CK(cudaMemcpyAsync(ctx->v.rank, rank, (size_t)ctx->N * sizeof(int32_t), cudaMemcpyDefault, s));
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_get_children(nsga3_ctx* ctx, float* X, float* F, void* stream)
+{
+    if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = ctx->N;
+    if (X) CK(cudaMemcpyAsync(X, ctx->v.X + N * ctx->d, N * ctx->d * sizeof(float), cudaMemcpyDefault, s));
+    if (F) CK(cudaMemcpyAsync(F, ctx->v.F + N * ctx->m, N * ctx->m * sizeof(float), cudaMemcpyDefault, s));
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_set_counter(nsga3_ctx* ctx, uint64_t gen, void* stream)
+{
+    if (!ctx || gen > 0xffffffffull) return fail(ctx, NSGA3_EINVAL, "bad arguments");
+    k_set_gen<<<1, 1, 0, (cudaStream_t)stream>>>(ctx->v.ctrl, (uint32_t)gen);
+    CK(cudaGetLastError());
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_get_counter(nsga3_ctx* ctx, uint64_t* gen, void* stream)
+{
+    if (!ctx || !gen) return fail(ctx, NSGA3_EINVAL, "null argument");
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    uint32_t g = 0;
+    CK(cudaMemcpy(&g, &ctx->v.ctrl->gen, sizeof g, cudaMemcpyDeviceToHost));
+    *gen = g;
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_sync(nsga3_ctx* ctx, void* stream)
+{
+    if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return device_status(ctx, true);
+}
+
+nsga3_status nsga3_get_selection_info(nsga3_ctx* ctx, int32_t* info)
+{
+    if (!ctx || !info) return fail(ctx, NSGA3_EINVAL, "null argument");
+    Ctrl c;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(&c, ctx->v.ctrl, sizeof c, cudaMemcpyDeviceToHost));
+    info[0] = c.l;
+    info[1] = c.nS;
+    info[2] = c.K;
+    info[3] = c.nFl;
+    info[4] = c.need_niche;
+    info[5] = c.fallback;
+    info[6] = c.passes;
+    info[7] = c.nT;
+    info[8] = c.Lstar;
+    info[9] = c.rlev;
+    info[10] = c.overflow;
+    info[11] = c.recheck_miss;
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_get_normalization(nsga3_ctx* ctx, double* zstar, double* a, int32_t* ext)
+{
+    if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
+    Ctrl c;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(&c, ctx->v.ctrl, sizeof c, cudaMemcpyDeviceToHost));
+    for (int q = 0; q < ctx->m; ++q) {
+        if (zstar) zstar[q] = c.zstar[q];
+        if (a) a[q] = c.a[q];
+        if (ext) ext[q] = c.ext[q];
+    }
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_get_association(nsga3_ctx* ctx, int32_t* pi, double* dist)
+{
+    if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
+    CK(cudaDeviceSynchronize());
+    if (pi) CK(cudaMemcpy(pi, ctx->v.pi, (size_t)ctx->n2 * sizeof(int32_t), cudaMemcpyDefault));
+    if (dist) CK(cudaMemcpy(dist, ctx->v.dist, (size_t)ctx->n2 * sizeof(double), cudaMemcpyDefault));
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_phase_times(nsga3_ctx* ctx, float* ms, int n)
+{
+    if (!ctx || !ms || n < 1) return fail(ctx, NSGA3_EINVAL, "bad arguments");
+    CK(cudaEventSynchronize(ctx->ev[EV_END]));
+    const int pairs[6][2] = {{EV_START, EV_VARY}, {EV_VARY, EV_DOM},   {EV_DOM, EV_PEEL},
+                             {EV_PEEL, EV_NICHE}, {EV_NICHE, EV_END}, {EV_START, EV_END}};
+    for (int t = 0; t < n && t < 6; ++t) {
+        float x = 0.0f;
+        CK(cudaEventElapsedTime(&x, ctx->ev[pairs[t][0]], ctx->ev[pairs[t][1]]));
+        ms[t] = x;
+    }
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches)
+{
+    if (!ctx || !launches) return fail(ctx, NSGA3_EINVAL, "null argument");
+    Ctrl c;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(&c, ctx->v.ctrl, sizeof c, cudaMemcpyDeviceToHost));
+    // reset, dominance, post-peel, compaction (+ finite check for a selection;
+    // + variation, gather, counter for a generation), one per peel pass, and
+    // 9 niching launches when the IF branch ran
+    int fixed = (ctx->last_kind == 1) ? 5 : 7;
+    *launches = fixed + c.passes + (c.need_niche ? 9 : 0);
+    return NSGA3_OK;
+}
+
+}  // extern "C"

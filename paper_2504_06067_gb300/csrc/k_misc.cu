@@ -1,0 +1,201 @@
+// k_misc.cu -- per-selection reset, boundary check of the objectives,
+// compaction of the selected indices and the next-population gather
+// (Alg. 2 last line: P_{t+1} = rows with rank < l after selection).
+#include "kernels.cuh"
+
+namespace {
+
+__global__ void k_sel_reset(RunView v, int nchunks)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    for (int j = tid; j < v.ld; j += stride) {
+        v.cnt[j] = 0;
+        v.rank2[j] = -1;
+    }
+    for (int wd = tid; wd < v.NW; wd += stride) {
+        const int lo = wd * 32;
+        uint32_t m = 0u;
+        if (lo + 32 <= v.n2)
+            m = 0xffffffffu;
+        else if (lo < v.n2)
+            m = (1u << (v.n2 - lo)) - 1u;
+        v.rem[wd] = m;
+        v.selmask[wd] = 0u;
+    }
+    for (int t = tid; t < nchunks; t += stride) v.chunk_done[t] = 0u;
+    for (int j = tid; j < v.w; j += stride) {
+        v.rho[j] = 0;
+        v.rhop[j] = 0;
+    }
+    if (tid == 0) {
+        Ctrl* c = v.ctrl;
+        c->k = 0;
+        c->cum = 0;
+        c->l = -1;
+        c->nS = 0;
+        c->K = 0;
+        c->nFl = 0;
+        c->need_niche = 0;
+        c->fallback = 0;
+        c->passes = 0;
+        c->front_size = 0u;
+        c->chunks_done = 0u;
+        c->nT = 0;
+        c->Lstar = -1;
+        c->rlev = 0;
+        c->nsel = 0;
+        c->nlarge = 0;
+        c->overflow = 0;
+        c->recheck_miss = 0;
+        for (int q = 0; q < NSGA3_MAX_M; ++q) c->zmin[q] = 0xffffffffu;
+    }
+}
+
+__global__ void k_check_finite(RunView v)
+{
+    const long long n = (long long)v.n2 * v.m;
+    bool bad = false;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+        bad |= !isfinite(v.F[e]);
+    if (__any_sync(0xffffffffu, bad) && lane_id() == 0) set_status(v.ctrl, DEV_ENONFINITE);
+}
+
+// selected = S u (picked members of F_l), or S u F_l when no niching is
+// needed; written in ascending index order by one CTA (popc scan over words)
+__global__ void __launch_bounds__(1024) k_compact(RunView v)
+{
+    uint32_t* words = v.front;  // front masks are dead after the peel: NW words of scratch
+    __shared__ int scratch[40];
+    Ctrl* c = v.ctrl;
+    if (read_status(c)) return;
+    const int l = c->l, need = c->need_niche;
+    const int lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int wd = warp; wd < v.NW; wd += nwarps) {
+        const int j = wd * 32 + lane;
+        const int r = j < v.n2 ? v.rank2[j] : -1;
+        const bool take = r >= 0 && (r < l || (r == l && (!need || ((v.selmask[wd] >> lane) & 1u))));
+        const uint32_t word = __ballot_sync(0xffffffffu, take);
+        if (lane == 0) words[wd] = word;
+    }
+    __syncthreads();
+    const int per = (v.NW + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int lo = min(v.NW, (int)threadIdx.x * per), hi = min(v.NW, lo + per);
+    int s = 0;
+    for (int wd = lo; wd < hi; ++wd) s += __popc(words[wd]);
+    // block exclusive scan of s
+    int inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) scratch[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int x = lane < nwarps ? scratch[lane] : 0, xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += y;
+        }
+        scratch[lane] = xi - x;
+        if (lane == 31) scratch[32] = xi;
+    }
+    __syncthreads();
+    int run = scratch[warp] + inc - s;
+    for (int wd = lo; wd < hi; ++wd) {
+        uint32_t word = words[wd];
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            if (run < v.N) v.sel[run] = wd * 32 + b;
+            ++run;
+        }
+    }
+    if (threadIdx.x == 0) {
+        c->nsel = scratch[32];
+        if (scratch[32] != v.N) set_status(c, DEV_EINTERNAL);
+    }
+}
+
+// next population rows (warp per row)
+__global__ void k_gather(RunView v)
+{
+    if (read_status(v.ctrl)) return;
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = lane_id();
+    if (p >= v.N) return;
+    const int i = v.sel[p];
+    const float* src = v.X + (size_t)i * v.d;
+    float* dst = v.Xtmp + (size_t)p * v.d;
+    for (int e = lane; e < v.d; e += 32) dst[e] = src[e];
+    if (lane < v.m) v.Ftmp[(size_t)p * v.m + lane] = v.F[(size_t)i * v.m + lane];
+    if (lane == 0) v.ranktmp[p] = v.rank2[i];
+}
+
+__global__ void k_bump_gen(RunView v)
+{
+    if (read_status(v.ctrl) == 0) v.ctrl->gen += 1u;
+}
+
+__global__ void k_nan_pad(RunView v)
+{
+    const long long lo = (long long)v.n2 * v.m, hi = (long long)v.ld * v.m;
+    for (long long e = lo + blockIdx.x * (long long)blockDim.x + threadIdx.x; e < hi;
+         e += (long long)gridDim.x * blockDim.x)
+        v.F[e] = __int_as_float(0x7fc00000);
+}
+
+}  // namespace
+
+cudaError_t launch_sel_reset(const RunView& v, cudaStream_t s)
+{
+    int n = v.ld > v.w ? v.ld : v.w;
+    int blocks = (n + 255) / 256;
+    if (blocks > 2048) blocks = 2048;
+    k_sel_reset<<<blocks, 256, 0, s>>>(v, v.ld / NSGA3_PEEL_COLS);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const RunView& v, cudaStream_t s)
+{
+    long long n = (long long)v.n2 * v.m;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    k_check_finite<<<(unsigned)blocks, 256, 0, s>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const RunView& v, cudaStream_t s)
+{
+    k_compact<<<1, 1024, 0, s>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const RunView& v, cudaStream_t s)
+{
+    long long threads = (long long)v.N * 32;
+    k_gather<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(v.X, v.Xtmp, (size_t)v.N * v.d * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(v.F, v.Ftmp, (size_t)v.N * v.m * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(v.rank, v.ranktmp, (size_t)v.N * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+}
+
+cudaError_t launch_bump_gen(const RunView& v, cudaStream_t s)
+{
+    k_bump_gen<<<1, 1, 0, s>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nan_pad(const RunView& v, cudaStream_t s)
+{
+    k_nan_pad<<<64, 256, 0, s>>>(v);
+    return cudaGetLastError();
+}
+

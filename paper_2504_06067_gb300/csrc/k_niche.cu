@@ -1,0 +1,438 @@
+// k_niche.cu -- niche selection of K = N - |S| members of F_l (Alg. 1 lines
+// 7-19; Alg. 2 lines 7-26).
+//
+// The paper's loop takes, round after round, one member from every
+// reference of minimum niche count (the cache tensor Q and cursor s of
+// Alg. 2 serve whole rounds at once) and truncates the last round in
+// shuffled-reference order.  Rounds are exhausted level by level, so the
+// outcome has a closed form that needs no loop:
+//   each reference j orders its F_l members: the nearest first (min d, then
+//   lowest index) when rho_j = 0, then by ascending Philox member priority
+//   (then index); the member at position t has level rho_j + t;
+//   L* = min { L : sum_j min(rho'_j, max(0, L + 1 - rho_j)) >= K };
+//   every member of level < L* is taken, and of the references holding a
+//   level-L* member, the r = K - count(L* - 1) of smallest (ref priority, j)
+//   take that member.
+// Random choices use fixed Philox priorities of this generation: reference
+// j -> word 0 of Philox(j, gen, 4, 0), member i -> word 0 of
+// Philox(i, gen, 5, 0); ties go to the lower index.
+#include "kernels.cuh"
+
+namespace {
+
+constexpr int LB = 1024;    // threads of the single-CTA kernels
+constexpr int LCAP = 4096;  // niche levels resolved by the shared histogram
+constexpr int EXACT = 1024; // candidates ranked pairwise in the last select phase
+
+__device__ __forceinline__ uint32_t ref_prio(uint64_t seed, uint32_t gen, int j)
+{
+    return philox((uint32_t)j, gen, RNG_REFPRIO, 0u, seed).x;
+}
+__device__ __forceinline__ uint32_t mem_prio(uint64_t seed, uint32_t gen, int i)
+{
+    return philox((uint32_t)i, gen, RNG_MEMPRIO, 0u, seed).x;
+}
+
+// ------------------------------------------------ block-wide helpers -------
+__device__ int block_sum(int x, int* scratch)
+{
+    x = warp_sum(x);
+    if (lane_id() == 0) scratch[threadIdx.x >> 5] = x;
+    __syncthreads();
+    int t = 0;
+    if (threadIdx.x < 32) {
+        t = (threadIdx.x < (blockDim.x >> 5)) ? scratch[threadIdx.x] : 0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) scratch[32] = t;
+    }
+    __syncthreads();
+    t = scratch[32];
+    __syncthreads();
+    return t;
+}
+
+// exclusive scan of one value per thread; returns the prefix, *total the sum
+__device__ int block_excl_scan(int x, int* scratch, int* total)
+{
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    int inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) scratch[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int v = (lane < (int)(blockDim.x >> 5)) ? scratch[lane] : 0;
+        int vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, vi, o);
+            if (lane >= o) vi += y;
+        }
+        scratch[lane] = vi - v;
+        if (lane == 31) scratch[32] = vi;
+    }
+    __syncthreads();
+    const int res = scratch[warp] + inc - x;
+    *total = scratch[32];
+    __syncthreads();
+    return res;
+}
+
+// Exclusive scan of a[0..n) into out[0..n] (out[n] = total) by one block:
+// each thread scans a contiguous run.
+__device__ void block_scan_array(const int32_t* a, int32_t* out, int n, int* scratch)
+{
+    const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+    int s = 0;
+    for (int e = lo; e < hi; ++e) s += a[e];
+    int total;
+    int run = block_excl_scan(s, scratch, &total);
+    for (int e = lo; e < hi; ++e) {
+        out[e] = run;
+        run += a[e];
+    }
+    if (threadIdx.x == 0) out[n] = total;
+}
+
+struct SelShared {
+    int hist[256];
+    int scratch[40];
+    unsigned long long keys[EXACT];
+    int idxs[EXACT];
+    int nex;
+    int bsel;
+    int before;
+};
+
+// Calls mark(idx) for the `need` smallest keys among {idx in [0,n) : pred}.
+// Keys are unique 64-bit values.  8-bit radix passes narrow the candidates
+// to one digit bucket until at most EXACT remain, which are then ranked
+// pairwise.  Every thread of the block must call it.
+template <class Key, class Pred, class Mark>
+__device__ void block_select_smallest(int n, int need, Key key, Pred pred, Mark mark, SelShared& sh)
+{
+    unsigned long long prefix = 0ull, pmask = 0ull;
+    int shift = 56;
+    while (need > 0) {
+        int cnt = 0;
+        for (int e = threadIdx.x; e < n; e += blockDim.x)
+            if (pred(e) && (key(e) & pmask) == prefix) ++cnt;
+        cnt = block_sum(cnt, sh.scratch);
+        if (cnt <= need) {  // every remaining candidate is taken
+            for (int e = threadIdx.x; e < n; e += blockDim.x)
+                if (pred(e) && (key(e) & pmask) == prefix) mark(e);
+            return;
+        }
+        if (cnt <= EXACT || shift < 0) {
+            if (threadIdx.x == 0) sh.nex = 0;
+            __syncthreads();
+            for (int e = threadIdx.x; e < n; e += blockDim.x) {
+                if (pred(e)) {
+                    unsigned long long k = key(e);
+                    if ((k & pmask) == prefix) {
+                        int p = atomicAdd(&sh.nex, 1);
+                        if (p < EXACT) {
+                            sh.keys[p] = k;
+                            sh.idxs[p] = e;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            const int ne = min(sh.nex, EXACT);
+            for (int a = threadIdx.x; a < ne; a += blockDim.x) {
+                const unsigned long long ka = sh.keys[a];
+                int rk = 0;
+                for (int b = 0; b < ne; ++b) rk += sh.keys[b] < ka;
+                if (rk < need) mark(sh.idxs[a]);
+            }
+            __syncthreads();
+            return;
+        }
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) sh.hist[t] = 0;
+        __syncthreads();
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            if (pred(e)) {
+                unsigned long long k = key(e);
+                if ((k & pmask) == prefix) atomicAdd(&sh.hist[(int)((k >> shift) & 255ull)], 1);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0, b = 0;
+            for (; b < 256; ++b) {
+                if (run + sh.hist[b] >= need) break;
+                run += sh.hist[b];
+            }
+            sh.bsel = b;
+            sh.before = run;
+        }
+        __syncthreads();
+        const int b = sh.bsel, before = sh.before;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            if (pred(e)) {
+                unsigned long long k = key(e);
+                if ((k & pmask) == prefix && (int)((k >> shift) & 255ull) < b) mark(e);
+            }
+        }
+        __syncthreads();
+        need -= before;
+        prefix |= (unsigned long long)b << shift;
+        pmask |= 255ull << shift;
+        shift -= 8;
+    }
+}
+
+// ------------------------------------------------------------ k_level ------
+struct LevelShared {
+    int lev[LCAP + 1];
+    int scratch[40];
+    int Lstar;
+    int maxhi;
+    SelShared sel;
+};
+
+__global__ void __launch_bounds__(LB) k_level(RunView v)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    LevelShared& sh = *reinterpret_cast<LevelShared*>(smraw);
+    Ctrl* c = v.ctrl;
+    if (read_status(c)) return;
+    const int w = v.w, K = c->K;
+    const uint32_t gen = c->gen;
+    for (int t = threadIdx.x; t <= LCAP; t += LB) sh.lev[t] = 0;
+    if (threadIdx.x == 0) {
+        sh.Lstar = LCAP;
+        sh.maxhi = 0;
+    }
+    __syncthreads();
+    int mymax = 0;
+    for (int j = threadIdx.x; j < w; j += LB) {
+        const int rp = v.rhop[j];
+        if (rp > 0) {
+            const int lo = v.rho[j], hi = lo + rp;
+            if (lo < LCAP) atomicAdd(&sh.lev[lo], 1);
+            if (hi < LCAP) atomicAdd(&sh.lev[hi], -1);
+            mymax = max(mymax, hi);
+        }
+    }
+    atomicMax(&sh.maxhi, mymax);
+    __syncthreads();
+    // n(L) = prefix sum of the difference array; count(L) = prefix sum of n(L)
+    {
+        constexpr int PER = LCAP / LB;
+        int loc[PER];
+        int s = 0;
+        for (int t = 0; t < PER; ++t) {
+            s += sh.lev[threadIdx.x * PER + t];
+            loc[t] = s;
+        }
+        int total;
+        int off = block_excl_scan(s, sh.scratch, &total);
+        for (int t = 0; t < PER; ++t) loc[t] += off;  // n(L)
+        int s2 = 0;
+        for (int t = 0; t < PER; ++t) {
+            s2 += loc[t];
+            loc[t] = s2;
+        }
+        int off2 = block_excl_scan(s2, sh.scratch, &total);
+        for (int t = 0; t < PER; ++t) {
+            const int L = threadIdx.x * PER + t;
+            sh.lev[L] = loc[t] + off2;  // count(L)
+        }
+        __syncthreads();
+        for (int t = 0; t < PER; ++t) {
+            const int L = threadIdx.x * PER + t;
+            if (sh.lev[L] >= K) atomicMin(&sh.Lstar, L);
+        }
+        __syncthreads();
+    }
+    int Lstar = sh.Lstar;
+    int before;
+    if (Lstar < LCAP) {
+        before = Lstar > 0 ? sh.lev[Lstar - 1] : 0;
+    } else {
+        // deep levels: binary search with block-reduced counts
+        auto count_le = [&](int L) {
+            int s = 0;
+            for (int j = threadIdx.x; j < w; j += LB) {
+                const int rp = v.rhop[j];
+                if (rp > 0) s += min(rp, max(0, L + 1 - v.rho[j]));
+            }
+            return block_sum(s, sh.scratch);
+        };
+        int lo = LCAP, hi = max(LCAP, sh.maxhi - 1);
+        while (lo < hi) {
+            const int mid = lo + (hi - lo) / 2;
+            if (count_le(mid) >= K)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        Lstar = lo;
+        before = count_le(Lstar - 1);
+    }
+    const int r = K - before;
+    for (int j = threadIdx.x; j < w; j += LB) {
+        const int rp = v.rhop[j];
+        v.take[j] = rp > 0 ? min(rp, max(0, Lstar - v.rho[j])) : 0;
+    }
+    __syncthreads();
+    auto pred = [&](int j) {
+        const int rp = v.rhop[j];
+        const int lo = v.rho[j];
+        return rp > 0 && lo <= Lstar && Lstar < lo + rp;
+    };
+    auto key = [&](int j) {
+        return ((unsigned long long)ref_prio(v.seed, gen, j) << 32) | (unsigned)j;
+    };
+    auto mark = [&](int j) { v.take[j] += 1; };
+    block_select_smallest(w, r, key, pred, mark, sh.sel);
+    __syncthreads();
+    block_scan_array(v.rhop, v.ref_off, w, sh.scratch);
+    for (int j = threadIdx.x; j < w; j += LB) v.cursor[j] = 0;
+    if (threadIdx.x == 0) {
+        c->Lstar = Lstar;
+        c->rlev = r;
+        c->nlarge = 0;
+    }
+}
+
+// ----------------------------------------------------------- k_bucket ------
+__global__ void k_bucket(RunView v)
+{
+    Ctrl* c = v.ctrl;
+    if (read_status(c)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= v.n2 || v.rank2[i] != c->l) return;
+    const int j = v.pi[i];
+    const int p = atomicAdd(&v.cursor[j], 1);
+    v.bucket[v.ref_off[j] + p] = i;
+}
+
+__device__ __forceinline__ void mark_member(const RunView& v, int i)
+{
+    atomicOr(&v.selmask[i >> 5], 1u << (i & 31));
+}
+
+// ------------------------------------------------------------- k_pick ------
+// one warp per reference
+__global__ void __launch_bounds__(256) k_pick(RunView v)
+{
+    Ctrl* c = v.ctrl;
+    if (read_status(c)) return;
+    const int lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t gen = c->gen;
+    for (int j = gw; j < v.w; j += nw) {
+        const int take = v.take[j];
+        if (take == 0) continue;
+        const int cnt = v.rhop[j], off = v.ref_off[j];
+        if (take >= cnt) {
+            for (int e = lane; e < cnt; e += 32) mark_member(v, v.bucket[off + e]);
+            continue;
+        }
+        int need = take, excl = -1;
+        if (v.rho[j] == 0) {
+            double bd = CUDART_INF;
+            int bi = 0x7fffffff;
+            for (int e = lane; e < cnt; e += 32) {
+                const int i = v.bucket[off + e];
+                if (lex_less(v.dist[i], i, bd, bi)) {
+                    bd = v.dist[i];
+                    bi = i;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                double od = __shfl_xor_sync(0xffffffffu, bd, o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (lex_less(od, oi, bd, bi)) {
+                    bd = od;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) mark_member(v, bi);
+            excl = bi;
+            need -= 1;
+        }
+        if (need == 0) continue;
+        if (cnt <= 32) {
+            unsigned long long k = ~0ull;
+            int i = -1;
+            if (lane < cnt) {
+                i = v.bucket[off + lane];
+                if (i != excl) k = ((unsigned long long)mem_prio(v.seed, gen, i) << 32) | (unsigned)i;
+            }
+            int rk = 0;
+            for (int b = 0; b < cnt; ++b) {
+                unsigned long long kb = __shfl_sync(0xffffffffu, k, b);
+                rk += kb < k;
+            }
+            if (lane < cnt && i != excl && rk < need) mark_member(v, i);
+        } else if (lane == 0) {
+            const int p = atomicAdd(&c->nlarge, 1);
+            v.large[p] = make_int4(j, need, excl, 0);
+        }
+    }
+}
+
+// large buckets with a partial take: one CTA per bucket
+__global__ void __launch_bounds__(LB) k_pick_large(RunView v)
+{
+    __shared__ SelShared sh;
+    Ctrl* c = v.ctrl;
+    if (read_status(c)) return;
+    const int nl = c->nlarge;
+    const uint32_t gen = c->gen;
+    for (int t = blockIdx.x; t < nl; t += gridDim.x) {
+        const int4 L = v.large[t];
+        const int j = L.x, need = L.y, excl = L.z;
+        const int cnt = v.rhop[j], off = v.ref_off[j];
+        const int32_t* mem = v.bucket + off;
+        auto pred = [&](int e) { return mem[e] != excl; };
+        auto key = [&](int e) {
+            const int i = mem[e];
+            return ((unsigned long long)mem_prio(v.seed, gen, i) << 32) | (unsigned)i;
+        };
+        auto mark = [&](int e) { mark_member(v, mem[e]); };
+        block_select_smallest(cnt, need, key, pred, mark, sh);
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_level(const RunView& v, cudaStream_t s)
+{
+    k_level<<<1, LB, sizeof(LevelShared), s>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket(const RunView& v, cudaStream_t s)
+{
+    k_bucket<<<(v.n2 + 255) / 256, 256, 0, s>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pick(const RunView& v, cudaStream_t s)
+{
+    int blocks = (v.w + 7) / 8;
+    if (blocks > 4096) blocks = 4096;
+    k_pick<<<blocks, 256, 0, s>>>(v);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_pick_large<<<64, LB, 0, s>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t niche_init_attributes()
+{
+    return cudaFuncSetAttribute(k_level, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(LevelShared));
+}

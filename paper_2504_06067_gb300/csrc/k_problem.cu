@@ -1,0 +1,200 @@
+// k_problem.cu -- reference directions, initial population and the fused
+// variation + objective kernel around the selection.
+//
+// Reference directions (Sec. II-C): Das-Dennis lattice {k/p : sum k = p} in
+// lexicographic order of k, optional inner layer (1 - tau)/m + tau z; one
+// thread unranks one composition.  FP64 with _rn intrinsics.
+//
+// Variation (Alg. 1 line 1; Sec. III-A), one warp per offspring pair q:
+//   tournament: Philox(q, gen, 1, 0) -> a1, b1, a2, b2 in [0, N); the lower
+//   front wins, ties keep the first drawn; Philox(q, gen, 1, 1) word 0 < p_c
+//   lets the pair cross.  SBX per variable v (Philox(q*d+v, gen, 2, 0)):
+//   word 1 < 0.5 crosses v with spread beta from word 0, word 2 < 0.5 swaps
+//   the children; clip to [0,1].  Polynomial mutation of child c, variable v
+//   (Philox(c*d+v, gen, 3, 0)): word 0 < p_m mutates with u = word 1.
+//   Children go to rows N + 2q and N + 2q + 1.  FP32 arithmetic.
+// Objective (the softmax-simplex family): k = m - 1,
+//   g = sum_{v >= k} (x_v - 0.5)^2, f_j = (1 + g) softmax(W x[0:k])_j,
+//   evaluated in FP64 and rounded to FP32.
+#include "kernels.cuh"
+
+namespace {
+
+__device__ long long binom_ll(int n, int k)
+{
+    if (k < 0 || k > n) return 0;
+    long long r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+__global__ void k_refdirs(int m, int p1, int p2, double tau, int w1, int w, double* Zd, double* nz,
+                          float* Zh, int M4)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= w) return;
+    const bool inner = t >= w1;
+    const int p = inner ? p2 : p1;
+    long long idx = inner ? t - w1 : t;
+    int k[NSGA3_MAX_M];
+    int left = p;
+    for (int q = 0; q < m - 1; ++q) {
+        int val = 0;
+        for (; val <= left; ++val) {
+            const long long n = binom_ll(left - val + (m - q - 2), m - q - 2);
+            if (idx < n) break;
+            idx -= n;
+        }
+        k[q] = val;
+        left -= val;
+    }
+    k[m - 1] = left;
+    double z[NSGA3_MAX_M];
+    double s = 0.0;
+    for (int q = 0; q < m; ++q) {
+        double zq = __ddiv_rn((double)k[q], (double)p);
+        if (inner) {
+            const double a = __ddiv_rn(__dsub_rn(1.0, tau), (double)m);
+            const double b = __dmul_rn(tau, zq);
+            zq = __dadd_rn(a, b);
+        }
+        z[q] = zq;
+        Zd[(size_t)t * m + q] = zq;
+        s = __dadd_rn(s, __dmul_rn(zq, zq));
+    }
+    const double n = __dsqrt_rn(s);
+    nz[t] = n;
+    for (int q = 0; q < M4; ++q) Zh[(size_t)t * M4 + q] = q < m ? __double2float_rn(__ddiv_rn(z[q], n)) : 0.0f;
+}
+
+// objective of one row whose variables sit across the warp (x_v in lane v % 32,
+// iteration v / 32); xs[] holds the lane's values, k = m - 1 < 32.
+__device__ void warp_eval_row(const float* xrow, int d, int m, const float* W, float* frow)
+{
+    const int lane = lane_id();
+    const int k = m - 1;
+    double g = 0.0;
+    for (int v = k + lane; v < d; v += 32) {
+        const double t = __dsub_rn((double)xrow[v], 0.5);
+        g = __dadd_rn(g, __dmul_rn(t, t));
+    }
+    g = warp_sum(g);
+    double e = 0.0;
+    if (lane < m) {
+        double a = 0.0;
+        for (int v = 0; v < k; ++v) a = __dadd_rn(a, __dmul_rn((double)W[lane * k + v], (double)xrow[v]));
+        e = exp(a);
+    }
+    double den = warp_sum(lane < m ? e : 0.0);
+    if (lane < m) frow[lane] = __double2float_rn(__dmul_rn(__dadd_rn(1.0, g), __ddiv_rn(e, den)));
+}
+
+__global__ void k_init(RunView v)
+{
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= v.N) return;
+    const int lane = lane_id();
+    float* xrow = v.X + (size_t)i * v.d;
+    for (int e = lane; e < v.d; e += 32) {
+        U4 r = philox((uint32_t)i * (uint32_t)v.d + (uint32_t)e, 0u, RNG_INIT, 0u, v.seed);
+        xrow[e] = u01(r.x);
+    }
+    __syncwarp();
+    warp_eval_row(xrow, v.d, v.m, v.Wobj, v.F + (size_t)i * v.m);
+    if (lane == 0) v.rank[i] = 0;
+}
+
+__device__ __forceinline__ float pm_mutate(float y, float u, float eta_m)
+{
+    const float mp = 1.0f / (eta_m + 1.0f);
+    float dq;
+    if (u < 0.5f) {
+        const float xy = 1.0f - y;
+        const float val = 2.0f * u + (1.0f - 2.0f * u) * powf(xy, eta_m + 1.0f);
+        dq = powf(val, mp) - 1.0f;
+    } else {
+        const float xy = 1.0f - (1.0f - y);
+        const float val = 2.0f * (1.0f - u) + 2.0f * (u - 0.5f) * powf(xy, eta_m + 1.0f);
+        dq = 1.0f - powf(val, mp);
+    }
+    y = y + dq;
+    return fminf(fmaxf(y, 0.0f), 1.0f);
+}
+
+__global__ void k_vary_eval(RunView v)
+{
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= v.N / 2) return;
+    if (read_status(v.ctrl)) return;
+    const int lane = lane_id();
+    const uint32_t gen = v.ctrl->gen;
+    const int N = v.N, d = v.d;
+    const U4 t = philox((uint32_t)q, gen, RNG_TOURNAMENT, 0u, v.seed);
+    const U4 cx = philox((uint32_t)q, gen, RNG_TOURNAMENT, 1u, v.seed);
+    const uint32_t a1 = bounded(t.x, N), b1 = bounded(t.y, N);
+    const uint32_t a2 = bounded(t.z, N), b2 = bounded(t.w, N);
+    const uint32_t p1 = v.rank[b1] < v.rank[a1] ? b1 : a1;
+    const uint32_t p2 = v.rank[b2] < v.rank[a2] ? b2 : a2;
+    const bool cross = u01(cx.x) < v.p_c;
+    const float e = 1.0f / (v.eta_c + 1.0f);
+    const int c0 = 2 * q, c1i = 2 * q + 1;
+    float* x0 = v.X + (size_t)(N + c0) * d;
+    float* x1 = v.X + (size_t)(N + c1i) * d;
+    for (int var = lane; var < d; var += 32) {
+        const float y1 = v.X[(size_t)p1 * d + var], y2 = v.X[(size_t)p2 * d + var];
+        float c1 = y1, c2 = y2;
+        const U4 sb = philox((uint32_t)q * (uint32_t)d + (uint32_t)var, gen, RNG_SBX, 0u, v.seed);
+        if (cross && u01(sb.y) < 0.5f) {
+            const float u = u01(sb.x);
+            const float beta = (u <= 0.5f) ? powf(2.0f * u, e) : powf(1.0f / (2.0f * (1.0f - u)), e);
+            c1 = 0.5f * ((1.0f + beta) * y1 + (1.0f - beta) * y2);
+            c2 = 0.5f * ((1.0f - beta) * y1 + (1.0f + beta) * y2);
+            if (u01(sb.z) < 0.5f) {
+                const float tmp = c1;
+                c1 = c2;
+                c2 = tmp;
+            }
+            c1 = fminf(fmaxf(c1, 0.0f), 1.0f);
+            c2 = fminf(fmaxf(c2, 0.0f), 1.0f);
+        }
+        const U4 m0 = philox((uint32_t)c0 * (uint32_t)d + (uint32_t)var, gen, RNG_PM, 0u, v.seed);
+        if (u01(m0.x) < v.p_m) c1 = pm_mutate(c1, u01(m0.y), v.eta_m);
+        const U4 m1 = philox((uint32_t)c1i * (uint32_t)d + (uint32_t)var, gen, RNG_PM, 0u, v.seed);
+        if (u01(m1.x) < v.p_m) c2 = pm_mutate(c2, u01(m1.y), v.eta_m);
+        x0[var] = c1;
+        x1[var] = c2;
+    }
+    __syncwarp();
+    warp_eval_row(x0, d, v.m, v.Wobj, v.F + (size_t)(N + c0) * v.m);
+    warp_eval_row(x1, d, v.m, v.Wobj, v.F + (size_t)(N + c1i) * v.m);
+}
+
+}  // namespace
+
+cudaError_t launch_refdirs(const RunView& v, int p1, int p2, double tau, double* Zd, double* nz,
+                           float* Zh, cudaStream_t s)
+{
+    long long w1 = 1;
+    {
+        // C(p1 + m - 1, m - 1)
+        long long r = 1;
+        for (int i = 1; i <= v.m - 1; ++i) r = r * (p1 + i) / i;
+        w1 = r;
+    }
+    k_refdirs<<<(v.w + 127) / 128, 128, 0, s>>>(v.m, p1, p2, tau, (int)w1, v.w, Zd, nz, Zh, v.M4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const RunView& v, cudaStream_t s)
+{
+    long long threads = (long long)v.N * 32;
+    k_init<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vary_eval(const RunView& v, cudaStream_t s)
+{
+    long long threads = (long long)(v.N / 2) * 32;
+    k_vary_eval<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
+    return cudaGetLastError();
+}

@@ -1,0 +1,37 @@
+// kernels.cuh -- launch wrappers for the NSGA-III kernels (host side).
+// Every wrapper enqueues on `s` and returns the launch error; grids are
+// derived from the run's fixed sizes, so the same launches can be captured
+// into a CUDA graph once and replayed every generation.
+#pragma once
+#include "common.cuh"
+
+// setup (Sec. II-C reference points; init population)
+cudaError_t launch_refdirs(const RunView& v, int p1, int p2, double tau, double* Zd, double* nz,
+                           float* Zh, cudaStream_t s);
+cudaError_t launch_init(const RunView& v, cudaStream_t s);
+cudaError_t launch_nan_pad(const RunView& v, cudaStream_t s);
+
+// variation + objective (Alg. 1 "Crossover+Mutation", Sec. III-A)
+cudaError_t launch_vary_eval(const RunView& v, cudaStream_t s);
+
+// selection (Alg. 1 sort / Alg. 2)
+cudaError_t launch_sel_reset(const RunView& v, cudaStream_t s);
+cudaError_t launch_check_finite(const RunView& v, cudaStream_t s);
+cudaError_t launch_dominance(const RunView& v, cudaStream_t s);
+int peel_nsplit(const RunView& v, int num_sms);
+cudaError_t launch_peel(const RunView& v, int nsplit, cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_post_peel(const RunView& v, cudaGraphConditionalHandle h_niche, cudaStream_t s);
+cudaError_t launch_norm_ideal(const RunView& v, cudaStream_t s);
+cudaError_t launch_norm_extreme(const RunView& v, cudaStream_t s);
+cudaError_t launch_norm_solve(const RunView& v, cudaStream_t s);
+cudaError_t launch_assoc_prep(const RunView& v, cudaStream_t s);
+cudaError_t launch_assoc_scan(const RunView& v, cudaStream_t s);
+cudaError_t launch_level(const RunView& v, cudaStream_t s);
+cudaError_t launch_bucket(const RunView& v, cudaStream_t s);
+cudaError_t launch_pick(const RunView& v, cudaStream_t s);
+cudaError_t launch_compact(const RunView& v, cudaStream_t s);
+cudaError_t launch_gather(const RunView& v, cudaStream_t s);
+cudaError_t launch_bump_gen(const RunView& v, cudaStream_t s);
+
+// one-time attribute setup (dynamic shared memory opt-in)
+cudaError_t kernels_init_attributes();

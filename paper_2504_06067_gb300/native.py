@@ -1,0 +1,111 @@
+"""ctypes binding of libnsga3.so with the entry-point names of include/nsga3.h.
+
+Argument marshalling only: every computation runs in the CUDA library.
+Pointers are passed as integers (``tensor.data_ptr()`` for torch tensors,
+``array.ctypes.data`` for numpy arrays); streams as ``cudaStream_t`` values
+(``torch.cuda.current_stream().cuda_stream``).  Importing this module raises
+if the library has not been built, and there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnsga3.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libnsga3.so is not built (run __graft_entry__.build() or "
+                      "python -m paper_2504_06067_gb300.build); there is no CPU fallback")
+
+_lib = C.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, EINTERNAL = range(8)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE",
+                5: "ETIMEOUT", 6: "ESTATE", 7: "EINTERNAL"}
+
+
+class nsga3_opts(C.Structure):
+    _fields_ = [
+        ("seed", C.c_uint64),
+        ("p2", C.c_int),
+        ("tau", C.c_double),
+        ("eta_c", C.c_float),
+        ("eta_m", C.c_float),
+        ("p_c", C.c_float),
+        ("p_m", C.c_float),
+        ("full_sort", C.c_int),
+        ("debug_recheck_all", C.c_int),
+        ("W", C.c_void_p),
+    ]
+
+
+_P = C.c_void_p
+_CTX = C.c_void_p
+_I = C.c_int
+_SIGS = {
+    "nsga3_default_opts": (None, [C.POINTER(nsga3_opts)]),
+    "nsga3_create": (_I, [_I, _I, _I, _I, C.POINTER(nsga3_opts), C.POINTER(_CTX)]),
+    "nsga3_destroy": (None, [_CTX]),
+    "nsga3_last_error": (C.c_char_p, [_CTX]),
+    "nsga3_num_refs": (_I, [_CTX]),
+    "nsga3_get_refs": (_I, [_CTX, _P]),
+    "nsga3_select": (_I, [_CTX, _P, _P, _P, _P]),
+    "nsga3_init": (_I, [_CTX, _P]),
+    "nsga3_vary": (_I, [_CTX, _P]),
+    "nsga3_step": (_I, [_CTX, _P]),
+    "nsga3_run": (_I, [_CTX, _I, _P]),
+    "nsga3_run_batch": (_I, [C.POINTER(_CTX), _I, _I, _P]),
+    "nsga3_get_population": (_I, [_CTX, _P, _P, _P, _P]),
+    "nsga3_set_population": (_I, [_CTX, _P, _P, _P, _P]),
+    "nsga3_get_children": (_I, [_CTX, _P, _P, _P]),
+    "nsga3_set_counter": (_I, [_CTX, C.c_uint64, _P]),
+    "nsga3_get_counter": (_I, [_CTX, C.POINTER(C.c_uint64), _P]),
+    "nsga3_sync": (_I, [_CTX, _P]),
+    "nsga3_get_selection_info": (_I, [_CTX, _P]),
+    "nsga3_get_normalization": (_I, [_CTX, _P, _P, _P]),
+    "nsga3_get_association": (_I, [_CTX, _P, _P]),
+    "nsga3_phase_times": (_I, [_CTX, _P, _I]),
+    "nsga3_last_launches": (_I, [_CTX, _P]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+    globals()[_name] = _f
+
+
+class NSGA3Error(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def check(status, ctx=None):
+    """Raise NSGA3Error for a non-OK status (message from nsga3_last_error)."""
+    if status != OK:
+        msg = nsga3_last_error(ctx)
+        raise NSGA3Error(status, msg.decode() if msg else "")
+    return status
+
+
+def default_opts(**kw) -> nsga3_opts:
+    o = nsga3_opts()
+    nsga3_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def create(m, d, N, ref_divisions, opts=None):
+    """nsga3_create; returns the context handle (an int)."""
+    if opts is None:
+        opts = default_opts()
+    h = _CTX()
+    check(nsga3_create(m, d, N, ref_divisions, C.byref(opts), C.byref(h)))
+    return h.value
+
+
+def run_batch(ctxs, generations, stream=0):
+    arr = (_CTX * len(ctxs))(*ctxs)
+    return nsga3_run_batch(arr, len(ctxs), generations, stream)

@@ -1,0 +1,162 @@
+"""GPU parity of the generation around the selection: initial population,
+variation + objective (tolerance), the next population (bit-exact given the
+GPU's own children), determinism, resume, and the IGD of full runs."""
+import numpy as np
+import pytest
+
+from paper_2504_06067_gb300 import workloads as wl
+
+from gpu_util import Run
+
+pytestmark = pytest.mark.gpu
+
+# Children are FP32 in [0, 1]; the GPU evaluates SBX / PM with FP32 powf and
+# the oracle in FP64, so they agree to 1e-6 of the variable range.  The
+# objective is evaluated in FP64 on both sides and rounded to FP32.
+X_TOL = 1e-6
+F_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def n():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    from paper_2504_06067_gb300 import native
+    return native
+
+
+CFGS = [wl.SMALL, wl.RunConfig("m5_N1000_d100", m=5, d=100, N=1000, p1=7),
+        wl.RunConfig("m10_N600_d60", m=10, d=60, N=600, p1=3, p2=2)]
+
+
+@pytest.mark.parametrize("cfg", CFGS, ids=lambda c: c.name)
+def test_init_matches_oracle(n, orc, cfg):
+    W = wl.objective_weights(cfg.m, 0)
+    with Run(n, cfg.m, cfg.d, cfg.N, cfg.p1, p2=cfg.p2, seed=cfg.seed, W=W) as r:
+        r.check(n.nsga3_init(r.ctx, None))
+        X, F, rank = r.population()
+        Xo = orc.init_population(cfg.N, cfg.d, cfg.seed)
+        assert np.array_equal(X, Xo)
+        Fo = orc.evaluate(Xo, W)
+        np.testing.assert_allclose(F, Fo, rtol=F_RTOL, atol=0)
+        assert (rank == 0).all() and r.counter() == 0
+
+
+@pytest.mark.parametrize("cfg", CFGS, ids=lambda c: c.name)
+@pytest.mark.parametrize("gen", [0, 17])
+def test_variation_matches_oracle(n, orc, cfg, gen):
+    W = wl.objective_weights(cfg.m, 1)
+    X = wl.population(cfg.N, cfg.d, seed=gen)
+    F = orc.evaluate(X, W)
+    rank = wl.parent_ranks(cfg.N, 4, seed=gen)
+    with Run(n, cfg.m, cfg.d, cfg.N, cfg.p1, p2=cfg.p2, seed=3, W=W) as r:
+        r.set_population(X, F, rank)
+        r.check(n.nsga3_set_counter(r.ctx, gen, None))
+        r.check(n.nsga3_vary(r.ctx, None))
+        Xc, Fc = r.children()
+    Xo = orc.vary(X, rank, seed=3, gen=gen)
+    assert np.max(np.abs(Xc.astype(np.float64) - Xo)) <= X_TOL
+    # objective of the GPU's own children, evaluated by the oracle
+    np.testing.assert_allclose(Fc, orc.evaluate(Xc, W), rtol=F_RTOL, atol=0)
+
+
+@pytest.mark.parametrize("cfg", CFGS, ids=lambda c: c.name)
+def test_step_selects_like_oracle(n, orc, cfg):
+    """After one generation the next population equals the oracle's
+    selection over (parents u the GPU's children), bit for bit."""
+    W = wl.objective_weights(cfg.m, 2)
+    Z = orc.refdirs(cfg.m, cfg.p1, cfg.p2, cfg.tau)
+    with Run(n, cfg.m, cfg.d, cfg.N, cfg.p1, p2=cfg.p2, seed=9, W=W) as r:
+        r.check(n.nsga3_init(r.ctx, None))
+        for g in range(4):
+            X, F, rank = r.population()
+            r.check(n.nsga3_step(r.ctx, None))
+            assert r.sync() == 0
+            Xc, Fc = r.children()
+            Xn, Fn, rn = r.population()
+            RX = np.vstack([X, Xc])
+            RF = np.vstack([F, Fc])
+            ref = orc.select(RF, cfg.N, Z, seed=9, gen=g)
+            sel = ref["selected"]
+            assert np.array_equal(Xn, RX[sel]) and np.array_equal(Fn, RF[sel])
+            assert np.array_equal(rn, ref["rank"][sel])
+        assert r.counter() == 4
+
+
+def test_runs_are_deterministic_and_resume(n, orc):
+    cfg = CFGS[1]
+    W = wl.objective_weights(cfg.m, 0)
+    with Run(n, cfg.m, cfg.d, cfg.N, cfg.p1, seed=4, W=W) as a, \
+            Run(n, cfg.m, cfg.d, cfg.N, cfg.p1, seed=4, W=W) as b:
+        a.check(n.nsga3_init(a.ctx, None))
+        a.check(n.nsga3_run(a.ctx, 20, None))
+        pa = a.population()
+        # 10 generations, checkpoint through the host, resume in a new context
+        b.check(n.nsga3_init(b.ctx, None))
+        b.check(n.nsga3_run(b.ctx, 10, None))
+        X, F, rank = b.population()
+        gen = b.counter()
+    with Run(n, cfg.m, cfg.d, cfg.N, cfg.p1, seed=4, W=W) as c:
+        c.set_population(X, F, rank)
+        c.check(n.nsga3_set_counter(c.ctx, gen, None))
+        c.check(n.nsga3_run(c.ctx, 10, None))
+        pc = c.population()
+    for u, v in zip(pa, pc):
+        assert np.array_equal(u, v)
+
+
+def _igd(orc, F, rank, W, m):
+    y = wl.front_sample(m, 10000)
+    Xf = np.full((len(y), m - 1), 0.0, dtype=np.float32)
+    Xf[:, :] = y
+    R = orc.evaluate(np.hstack([Xf, np.full((len(y), 1), 0.5, np.float32)]), W).astype(np.float64)
+    return orc.igd(F[rank == 0], R)
+
+
+def test_igd_matches_oracle_median(n, orc):
+    """m = 3, N = 92, p = 12, d = 12, 100 generations, seeds 0..4: the median
+    IGD of the GPU runs is within 2% of the oracle runs' median."""
+    cfg = wl.SMALL
+    W = wl.objective_weights(cfg.m, 0)
+    Z = orc.refdirs(cfg.m, cfg.p1)
+    gi, oi = [], []
+    for seed in range(5):
+        with Run(n, cfg.m, cfg.d, cfg.N, cfg.p1, seed=seed, W=W) as r:
+            r.check(n.nsga3_init(r.ctx, None))
+            r.check(n.nsga3_run(r.ctx, cfg.generations, None))
+            assert r.sync() == 0
+            X, F, rank = r.population()
+        gi.append(_igd(orc, F, rank, W, cfg.m))
+        Xo, Fo, ro = orc.run(cfg.N, cfg.d, W, Z, seed, cfg.generations)
+        oi.append(_igd(orc, Fo, ro, W, cfg.m))
+    g, o = float(np.median(gi)), float(np.median(oi))
+    assert abs(g - o) <= 0.02 * o, (gi, oi)
+
+
+def test_batched_runs_equal_single_runs(n, orc):
+    """Several uneven runs advanced by one batched graph per generation give
+    the same populations as each run stepped alone."""
+    cfgs = wl.batched_configs(n_runs=6, generations=5)
+    cfgs = [c for c in cfgs if c.N <= 4000][:4]
+    runs = []
+    try:
+        for c in cfgs:
+            W = wl.objective_weights(c.m, c.seed)
+            r = Run(n, c.m, c.d, c.N, c.p1, seed=c.seed, W=W)
+            r.check(n.nsga3_init(r.ctx, None))
+            runs.append((c, W, r))
+        n.check(n.run_batch([r.ctx for _, _, r in runs], 5, None))
+        for c, W, r in runs:
+            assert r.sync() == 0
+            got = r.population()
+            with Run(n, c.m, c.d, c.N, c.p1, seed=c.seed, W=W) as alone:
+                alone.check(n.nsga3_init(alone.ctx, None))
+                alone.check(n.nsga3_run(alone.ctx, 5, None))
+                exp = alone.population()
+            for u, v in zip(got, exp):
+                assert np.array_equal(u, v)
+    finally:
+        for _, _, r in runs:
+            r.close()

@@ -1,0 +1,134 @@
+"""GPU parity of the environmental selection against the FP64 oracle.
+
+The bar is bit-exact: ranks, selected indices, the normalization (ideal
+point, intercepts, extremes) and the association (pi, d) must equal the
+oracle's on identical FP32 objectives.
+"""
+import numpy as np
+import pytest
+
+from paper_2504_06067_gb300 import workloads as wl
+
+from gpu_util import Run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def n():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    from paper_2504_06067_gb300 import native
+    return native
+
+
+def _compare(orc, run, F, Z, seed, gen, check_assoc=True):
+    st, rank, sel = run.select(F, gen=gen)
+    assert st == 0, "device status %d" % st
+    ref = orc.select(F, run.N, Z, seed=seed, gen=gen)
+    info = run.info()
+    assert info["l"] == ref["l"] and info["nS"] == ref["nS"] and info["nFl"] == ref["nFl"]
+    assert np.array_equal(rank, ref["rank"])
+    if ref["niche"] and check_assoc:
+        z, a, e = run.normalization()
+        zs, aa, ee, fb = orc.normalize(F, ref["rank"], ref["l"])
+        assert np.array_equal(z, zs) and np.array_equal(a, aa) and np.array_equal(e, ee)
+        assert bool(info["fallback"]) == fb
+        pi, dist = run.association()
+        T = (ref["rank"] >= 0) & (ref["rank"] <= ref["l"])
+        assert np.array_equal(pi[T], ref["pi"][T])
+        assert np.array_equal(dist[T], ref["dist"][T])
+    assert np.array_equal(sel, ref["selected"])
+    return info, ref
+
+
+def test_refdirs_bit_exact(n, orc):
+    for m, p1, p2 in ((3, 12, 0), (5, 20, 0), (10, 3, 2), (2, 7, 0), (8, 5, 3)):
+        with Run(n, m, m + 2, 64, p1, p2=p2) as r:
+            Z = r.refs()
+            assert np.array_equal(Z, orc.refdirs(m, p1, p2, 0.5))
+
+
+@pytest.mark.parametrize("kind", wl.KINDS)
+@pytest.mark.parametrize("shape", [(3, 92, 12, 0), (5, 300, 6, 0), (10, 500, 3, 2), (2, 70, 9, 0)])
+def test_select_parity(n, orc, kind, shape):
+    m, N, p1, p2 = shape
+    Z = orc.refdirs(m, p1, p2, 0.5)
+    with Run(n, m, m + 1, N, p1, p2=p2, seed=11) as r:
+        for s in range(2):
+            F = wl.objectives(kind, 2 * N, m, seed=s)
+            _compare(orc, r, F, Z, seed=11, gen=s + 1)
+
+
+def test_select_parity_ragged_sizes(n, orc):
+    """Sizes that are not multiples of the 32/128/256 tiles (ragged tails)."""
+    for m, N in ((3, 2), (4, 6), (3, 130), (6, 258), (7, 514)):
+        p = wl.largest_p(m, N)
+        Z = orc.refdirs(m, p)
+        with Run(n, m, m + 1, N, p, seed=5) as r:
+            for kind in ("early", "late", "dups"):
+                F = wl.objectives(kind, 2 * N, m, seed=N)
+                _compare(orc, r, F, Z, seed=5, gen=7)
+
+
+def test_select_parity_scale_shape(n, orc):
+    """m = 5, p = 20 (10,626 directions), N = 10,628: the plain-at-scale shape."""
+    cfg = wl.SCALE
+    Z = orc.refdirs(cfg.m, cfg.p1)
+    with Run(n, cfg.m, cfg.d, cfg.N, cfg.p1, seed=0) as r:
+        for kind in ("late", "early"):
+            F = wl.objectives(kind, 2 * cfg.N, cfg.m, seed=3)
+            info, ref = _compare(orc, r, F, Z, seed=0, gen=4)
+            assert info["overflow"] == 0
+
+
+def test_full_sort_ranks_everyone(n, orc):
+    m, N = 4, 200
+    Z = orc.refdirs(m, 5)
+    with Run(n, m, m + 1, N, 5, full_sort=1) as r:
+        for kind in ("early", "chain", "grid"):
+            F = wl.objectives(kind, 2 * N, m, seed=2)
+            st, rank, sel = r.select(F, gen=1)
+            assert st == 0
+            ref = orc.select(F, N, Z, seed=0, gen=1, full_sort=True)
+            assert np.array_equal(rank, ref["rank"]) and (rank >= 0).all()
+            assert np.array_equal(sel, ref["selected"])
+
+
+def test_debug_recheck_finds_no_miss(n, orc):
+    m, N = 5, 2000
+    p = 9
+    Z = orc.refdirs(m, p)
+    with Run(n, m, m + 1, N, p, debug_recheck_all=1) as r:
+        for kind in ("late", "simplex", "uniform"):
+            F = wl.objectives(kind, 2 * N, m, seed=9)
+            info, _ = _compare(orc, r, F, Z, seed=0, gen=2)
+            if info["niche"]:
+                assert info["recheck_miss"] == 0
+
+
+def test_nonfinite_objectives_rejected(n, orc):
+    m, N = 3, 64
+    with Run(n, m, m + 1, N, 6) as r:
+        F = wl.objectives("late", 2 * N, m)
+        for bad in (np.nan, np.inf, -np.inf):
+            G = F.copy()
+            G[17, 1] = bad
+            st, _, _ = r.select(G)
+            assert st == n.ENONFINITE
+        # the context recovers: the status is cleared by the sync
+        st, rank, sel = r.select(F, gen=0)
+        assert st == 0
+        ref = orc.select(F, N, orc.refdirs(m, 6), seed=0, gen=0)
+        assert np.array_equal(sel, ref["selected"])
+
+
+def test_bad_arguments(n):
+    import ctypes as C
+    h = C.c_void_p()
+    o = n.default_opts()
+    for args in ((1, 3, 10, 4), (11, 3, 10, 4), (3, 3, 9, 4), (3, 3, 10, 0), (3, 3, 0, 4)):
+        assert n.nsga3_create(*args, C.byref(o), C.byref(h)) == n.EINVAL
+        assert h.value is None
