@@ -1,0 +1,427 @@
+#!/usr/bin/env python3
+"""NSGA-III generation throughput on GB300.
+
+One step = one generation of a plain NSGA-III run: variation + objective,
+then the environmental selection over the merged 2N x m objectives
+(dominance matrix, front peel, normalization, association, niching) and the
+gather of the next population, as one CUDA-graph launch of the C-ABI
+library.  Default workload: m = 5, p = 20 (10,626 Das-Dennis directions),
+N = 10,628, d = 100, the 500-generation run timed from generation 0 after
+warm-up generations on the same context (re-initialised).
+
+Metric: selected solutions per second (N x generations / device time), plus
+generations per second.  The L2 cache is flushed (256 MB write) before every
+timed step; each step is timed by CUDA events on the launching stream.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): each rank advances an independent replica (seed + rank),
+"scaling": "weak"; rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2504_06067_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "selected sols/s & gens/s (% HBM roofline); batched/served runs/s, p50/p99 vs plain"
+WORKLOADS = {"small": wl.SMALL, "scale": wl.SCALE, "large": wl.LARGE}
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+NUM_SMS = 152
+LANES_PER_SM = 128
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=500)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="scale")
+    p.add_argument("--cpu-budget", type=float, default=20.0,
+                   help="seconds of oracle work for the cpu_baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args(argv)
+
+
+# ------------------------------------------------------------ distributed --
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max(dist, x, device="cpu"):
+    """Max of a float over ranks (identity without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks ----
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except (OSError, ValueError):
+        return dict(PEAKS_FALLBACK), "fallback"
+
+
+def ncu_traffic(kernel, workload):
+    """Per-launch DRAM bytes of `kernel` on `workload` from the committed ncu
+    summary, or None when absent or taken on a different kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) != 4 or line.startswith("#"):
+            continue
+        k, wk, traffic, sha = parts
+        if k != kernel or wk != workload:
+            continue
+        src = os.path.join(ROOT, "paper_2504_06067_gb300", "csrc", sha.split(":")[0])
+        want = sha.split(":")[1]
+        try:
+            got = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        except OSError:
+            return None
+        return float(traffic) if got == want else None
+    return None
+
+
+# ------------------------------------------------------------- our impl ----
+def run_ours(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    from paper_2504_06067_gb300 import native as n
+
+    cfg = WORKLOADS[args.workload]
+    seed = cfg.seed + rank
+    W = wl.objective_weights(cfg.m, cfg.seed)
+    opts = n.default_opts(seed=seed, p2=cfg.p2, tau=cfg.tau, W=W.ctypes.data)
+    ctx = n.create(cfg.m, cfg.d, cfg.N, cfg.p1, opts)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    info = (C.c_int32 * 13)()
+    phases = (C.c_float * 7)()
+    launches = C.c_int32()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def ok(st):
+        return n.check(st, ctx)
+
+    # warm-up generations, then restart the run from generation 0
+    ok(n.nsga3_init(ctx, sh))
+    for _ in range(args.warmup):
+        ok(n.nsga3_step(ctx, sh))
+    ok(n.nsga3_sync(ctx, sh))
+    ok(n.nsga3_init(ctx, sh))
+    ok(n.nsga3_sync(ctx, sh))
+
+    K = args.steps
+    ph_tot = [0.0] * 7
+    peel_rows = 0
+    passes = 0
+    niche_steps = 0
+    assoc_pairs = 0
+    n_launch = 0
+    step_ms = []
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ok(n.nsga3_step(ctx, sh))
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        ok(n.nsga3_phase_times(ctx, phases, 7))
+        ok(n.nsga3_get_selection_info(ctx, info))
+        ok(n.nsga3_last_launches(ctx, C.byref(launches)))
+        for t in range(7):
+            ph_tot[t] += phases[t]
+        passes += info[6]
+        peel_rows += info[12]
+        n_launch += launches.value
+        if info[4]:
+            niche_steps += 1
+            assoc_pairs += info[7] * n.nsga3_num_refs(ctx)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clocks = sampler.stop()
+    st = n.nsga3_sync(ctx, sh)
+    if st != n.OK:
+        raise RuntimeError("device status %d after the timed run" % st)
+    total_s = sum(step_ms) / 1e3
+    total_s_max = reduce_max(dist, total_s, "cuda")
+
+    # end to end through the C ABI with pinned host buffers: upload the
+    # parents, one generation, read the next population back
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.empty((cfg.N, cfg.d), dtype=torch.float32).pin_memory()
+        Fh = torch.empty((cfg.N, cfg.m), dtype=torch.float32).pin_memory()
+        Rh = torch.empty(cfg.N, dtype=torch.int32).pin_memory()
+        ok(n.nsga3_init(ctx, sh))
+        ok(n.nsga3_get_population(ctx, Xh.data_ptr(), Fh.data_ptr(), Rh.data_ptr(), sh))
+        ok(n.nsga3_sync(ctx, sh))
+        e2e_ms = []
+        Ke = min(K, 200)
+        for k in range(Ke):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ok(n.nsga3_set_population(ctx, Xh.data_ptr(), Fh.data_ptr(), Rh.data_ptr(), sh))
+            ok(n.nsga3_step(ctx, sh))
+            ok(n.nsga3_get_population(ctx, Xh.data_ptr(), Fh.data_ptr(), Rh.data_ptr(), sh))
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+        ok(n.nsga3_sync(ctx, sh))
+        e_s = reduce_max(dist, sum(e2e_ms) / 1e3, "cuda")
+        per_step = cfg.N * (cfg.d + cfg.m + 1) * 4
+        e2e = {"value": world * cfg.N * Ke / e_s, "unit": "sols/s", "h2d_bytes_per_step": per_step,
+               "d2h_bytes_per_step": per_step, "steps": Ke,
+               "gens_per_s": Ke / e_s}
+    n.nsga3_destroy(ctx)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+
+    peaks, peak_kind = measured_peaks()
+    names = ["variation", "reset", "dominance", "peel", "niching", "gather", "total"]
+    avg = {nm: ph_tot[i] / K for i, nm in enumerate(names)}
+    # dominant kernel by time: the dominance build (ALU) or the peel (HBM)
+    n2 = 2 * cfg.N
+    pairs = n2 * (n2 - 1) / 2
+    clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    if avg["dominance"] >= avg["peel"]:
+        ops = pairs * 2 * cfg.m  # FP32 compares: all(f_i <= f_j) and all(f_j <= f_i)
+        achieved = ops / (avg["dominance"] / 1e3) / 1e12
+        peak = NUM_SMS * LANES_PER_SM * clk / 1e12
+        roof = {"kernel": "k_dominance", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Tcompare/s", "frac": achieved / peak,
+                "peak_source": "152 SMs x 128 lanes x %.0f MHz (max SM clock, %s)" % (clk / 1e6, peak_kind),
+                "algorithmic": "n2(n2-1)/2 pairs x 2m compares per launch",
+                "traffic": ncu_traffic("k_dominance", cfg.name)}
+    else:
+        bytes_read = peel_rows / K * n2 * 4.0
+        per_launch_s = avg["peel"] / 1e3
+        achieved = bytes_read / per_launch_s / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"kernel": "k_peel (all passes of one selection)", "bound": "hbm", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": "hbm_gbs (%s)" % peak_kind,
+                "algorithmic": "dominator word-rows in the pass lists x 2N x 4 B",
+                "traffic": ncu_traffic("k_peel", cfg.name)}
+    value = world * cfg.N * K / total_s_max
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "sols/s",
+        "gens_per_s": world * K / total_s_max,
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": total_s_max * 1e3 / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded softmax-simplex objective, W ~ N(0,1); stands in for DTLZ)",
+        "config": {"workload": cfg.name, "m": cfg.m, "N": cfg.N, "d": cfg.d, "refs": cfg.w,
+                   "generations": "timed %d from generation 0" % K,
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "phase_ms": {k: round(v, 5) for k, v in avg.items()},
+        "peel_passes_per_step": passes / K,
+        "niching_steps": niche_steps,
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": n_launch,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return line
+
+
+# ----------------------------------------------------------------- oracle ----
+def oracle_generations(cfg, budget_s, max_steps=None, warmup=0):
+    """Times oracle generations of `cfg` from a seeded initial population until
+    the budget is spent (at least one).  Returns (seconds per generation, n)."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    W = wl.objective_weights(cfg.m, cfg.seed)
+    Z = oracle.refdirs(cfg.m, cfg.p1, cfg.p2, cfg.tau)
+    X = oracle.init_population(cfg.N, cfg.d, cfg.seed)
+    F = oracle.evaluate(X, W)
+    rank = np.zeros(cfg.N, np.int32)
+    g = 0
+    for _ in range(warmup):
+        X, F, rank = oracle.generation(X, F, rank, W, Z, cfg.seed, g)
+        g += 1
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        X, F, rank = oracle.generation(X, F, rank, W, Z, cfg.seed, g)
+        times.append(time.perf_counter() - t0)
+        g += 1
+        if max_steps is not None and len(times) >= max_steps:
+            break
+        if time.perf_counter() - t_start >= budget_s:
+            break
+    return sum(times) / len(times), len(times)
+
+
+def cpu_baseline(cfg, budget_s):
+    spg, n = oracle_generations(cfg, budget_s)
+    return {"value": cfg.N / spg, "unit": "sols/s", "cores": 1, "kind": "oracle",
+            "sample": "%d generation(s) of %s from generation 0 (FP64 C oracle, single thread, "
+                      "%d host cores on the box)" % (n, cfg.name, os.cpu_count() or 0)}
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm, on this workload's metric."""
+    if rank != 0:
+        return None
+    cfg = WORKLOADS[args.workload]
+    budget = 150.0
+    spg, nsteps = oracle_generations(cfg, budget, max_steps=args.steps, warmup=min(args.warmup, 1))
+    value = cfg.N / spg
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "sols/s",
+        "gens_per_s": 1.0 / spg,
+        "n_gpus": world,
+        "steps": nsteps,
+        "warmup": min(args.warmup, 1),
+        "ms_per_step": spg * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded softmax-simplex objective)",
+        "config": {"workload": cfg.name, "m": cfg.m, "N": cfg.N, "d": cfg.d, "refs": cfg.w,
+                   "generations": "%d timed of the requested %d (150 s budget)" % (nsteps, args.steps)},
+        "cpu_baseline": {"value": value, "unit": "sols/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d generation(s) of %s from generation 1" % (nsteps, cfg.name)},
+        "e2e": {"value": value, "unit": "sols/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -152,10 +152,11 @@ nsga3_status nsga3_get_counter(nsga3_ctx* ctx, uint64_t* gen, void* stream); /* 
 nsga3_status nsga3_sync(nsga3_ctx* ctx, void* stream);
 
 /*
- * Diagnostics of the last selection (synchronous): info[0..11] =
+ * Diagnostics of the last selection (synchronous): info[0..12] =
  *   l, |S|, K, |F_l|, niching needed, normalization fallback,
  *   peel passes, |S u F_l|, level L*, refs taken at L*, list overflows,
- *   debug recheck misses.
+ *   debug recheck misses, dominator word-rows read by the peel (each row
+ *   is 2N 32-bit words).  info must hold 13 entries.
  */
 nsga3_status nsga3_get_selection_info(nsga3_ctx* ctx, int32_t* info);
 
@@ -171,9 +172,10 @@ nsga3_status nsga3_get_association(nsga3_ctx* ctx, int32_t* pi, double* dist);
 /*
  * Device times (ms) of the phases of the last replayed generation or
  * selection, measured by CUDA events recorded inside the graph:
- *   ms[0] variation+objective, ms[1] dominance matrix, ms[2] front peel,
- *   ms[3] normalization + association + niching, ms[4] compaction + gather,
- *   ms[5] whole graph.  Synchronous; n is the capacity of ms (up to 6).
+ *   ms[0] variation+objective, ms[1] per-selection reset (+ finite check),
+ *   ms[2] dominance matrix kernel, ms[3] front peel (all passes),
+ *   ms[4] normalization + association + niching, ms[5] compaction + gather,
+ *   ms[6] whole graph.  Synchronous; n is the capacity of ms (up to 7).
  */
 nsga3_status nsga3_phase_times(nsga3_ctx* ctx, float* ms, int n);
 

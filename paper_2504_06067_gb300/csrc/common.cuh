@@ -56,6 +56,11 @@ struct Ctrl {
     int32_t overflow;        // association candidate-list overflows (slow path taken)
     int32_t recheck_miss;    // debug: association misses found by the full FP64 recheck
     int32_t nlarge;          // references whose partial take needs the block-wide select
+    uint32_t peel_rows;      // dominator word-rows in the peel's row lists, all passes
+    uint32_t front_words;    // nonzero mask words of the front being built
+    int32_t peel_more;       // eager mode: 1 if another peel pass is needed
+    int32_t ncand;           // association candidates written by the scan
+    int32_t nslow;           // points sent to the full FP64 association scan
     uint32_t zmin[NSGA3_MAX_M];  // ideal point as order-preserving uint of FP32
     double zstar[NSGA3_MAX_M];   // ideal point (FP64, +0.0 for zero)
     double a[NSGA3_MAX_M];       // intercepts
@@ -96,6 +101,7 @@ struct RunView {
     int32_t* rho;          // w
     int32_t* rhop;         // w
     int32_t* take;         // w
+    uint32_t* refprio;     // w   Philox reference priorities of this generation
     int32_t* ref_off;      // w + 1
     int32_t* cursor;       // w
     int32_t* bucket;       // n2
@@ -105,6 +111,17 @@ struct RunView {
     const double* nz;      // w
     const float* Zh;       // w x M4
     const float* Wobj;     // m x (m-1)
+    // association scan: references reordered into compact blocks of 32
+    int nblk;              // ceil(w / 32)
+    const float* blk_c;    // nblk x M4  unit cone centres (FP32)
+    const float2* blk_r;   // nblk       (cos r, sin r) of the inflated cone radius
+    const float* blk_z;    // w x M4     zhat in block order
+    const int32_t* blk_j;  // w          original reference index in block order
+    int2* arun;            // n2         candidate run (start, count) per T slot; start -1 = slow
+    int2* cand;            // cand_cap   (T slot, reference)
+    double* cdist;         // cand_cap   FP64 distance of each candidate
+    int cand_cap;
+    int32_t* slow;         // n2         T slots for the full FP64 scan
 };
 
 // ------------------------------------------------------------ Philox ------

@@ -9,9 +9,13 @@
 // condition (one pass per front), and the IF node skips the niching when
 // |S| + |F_l| == N, so a replay never returns to the host.
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <cmath>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -23,8 +27,9 @@ cudaError_t niche_init_attributes();
 namespace {
 
 thread_local std::string g_create_error;
+std::mutex g_attr_mutex;
 
-enum { EV_START, EV_VARY, EV_DOM, EV_PEEL, EV_NICHE, EV_END, EV_COUNT };
+enum { EV_START, EV_VARY, EV_RESET, EV_DOM, EV_PEEL, EV_NICHE, EV_END, EV_COUNT };
 
 __global__ void k_set_gen(Ctrl* c, uint32_t gen) { c->gen = gen; }
 
@@ -44,6 +49,7 @@ struct nsga3_ctx {
     cudaEvent_t ev[EV_COUNT] = {};
     int nsplit = 1;
     int last_kind = 0;  // 1 = select, 2 = step
+    bool eager = false; // NSGA3_EAGER=1: no graphs, host-driven peel loop (profiling)
     std::string err;
     // batched graph cache
     std::vector<nsga3_ctx*> batch_key;
@@ -130,7 +136,10 @@ nsga3_status add_conditional(nsga3_ctx* ctx, cudaStream_t s, cudaGraphConditiona
 nsga3_status record_event(nsga3_ctx* ctx, cudaStream_t s, int which, bool events)
 {
     if (!events) return NSGA3_OK;
-    CK(cudaEventRecordWithFlags(ctx->ev[which], s, cudaEventRecordExternal));
+    if (ctx->eager)
+        CK(cudaEventRecord(ctx->ev[which], s));
+    else
+        CK(cudaEventRecordWithFlags(ctx->ev[which], s, cudaEventRecordExternal));
     return NSGA3_OK;
 }
 
@@ -141,8 +150,10 @@ nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, 
 {
     CK(launch_sel_reset(v, s));
     if (check_finite) CK(launch_check_finite(v, s));
+    nsga3_status st = record_event(ctx, s, EV_RESET, events);
+    if (st) return st;
     CK(launch_dominance(v, s));
-    nsga3_status st = record_event(ctx, s, EV_DOM, events);
+    st = record_event(ctx, s, EV_DOM, events);
     if (st) return st;
     cudaGraphConditionalHandle h_peel, h_niche;
     cudaGraph_t body;
@@ -150,7 +161,7 @@ nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, 
     if (st) return st;
     CK(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     {
-        cudaError_t e = launch_peel(v, ctx->nsplit, h_peel, s2);
+        cudaError_t e = launch_peel(v, ctx->nsplit, h_peel, 1, s2);
         cudaGraph_t tmp;
         cudaError_t e2 = cudaStreamEndCapture(s2, &tmp);
         CK(e);
@@ -188,7 +199,7 @@ nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, 
         if (e == cudaSuccess) e = launch_norm_extreme(v, s2);
         if (e == cudaSuccess) e = launch_norm_solve(v, s2);
         if (e == cudaSuccess) e = launch_assoc_prep(v, s2);
-        if (e == cudaSuccess) e = launch_assoc_scan(v, s2);
+        if (e == cudaSuccess) e = launch_assoc_scan(v, ctx->num_sms, s2);
         if (e == cudaSuccess) e = launch_level(v, s2);
         if (e == cudaSuccess) e = launch_bucket(v, s2);
         if (e == cudaSuccess) e = launch_pick(v, s2);
@@ -217,8 +228,63 @@ nsga3_status record_generation(nsga3_ctx* ctx, cudaStream_t s, cudaStream_t s2, 
     return record_event(ctx, s, EV_END, events);
 }
 
+// Eager execution of the same kernels without graphs: the peel loop and
+// the niching branch are decided on the host from the control block.  Used
+// for profiling tools that cannot see inside conditional graphs.
+nsga3_status eager_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, bool check_finite)
+{
+    CK(launch_sel_reset(v, s));
+    if (check_finite) CK(launch_check_finite(v, s));
+    nsga3_status st = record_event(ctx, s, EV_RESET, true);
+    if (st) return st;
+    CK(launch_dominance(v, s));
+    st = record_event(ctx, s, EV_DOM, true);
+    if (st) return st;
+    int32_t more = 1;
+    for (int pass = 0; more && pass <= ctx->n2; ++pass) {
+        CK(launch_peel(v, ctx->nsplit, 0, 0, s));
+        CK(cudaMemcpyAsync(&more, &v.ctrl->peel_more, sizeof more, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    st = record_event(ctx, s, EV_PEEL, true);
+    if (st) return st;
+    int32_t hdr[2] = {0, 0};  // status, need_niche
+    CK(cudaMemcpyAsync(&hdr[0], &v.ctrl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hdr[1], &v.ctrl->need_niche, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hdr[0] == 0 && hdr[1]) {
+        CK(launch_norm_ideal(v, s));
+        CK(launch_norm_extreme(v, s));
+        CK(launch_norm_solve(v, s));
+        CK(launch_assoc_prep(v, s));
+        CK(launch_assoc_scan(v, ctx->num_sms, s));
+        CK(launch_level(v, s));
+        CK(launch_bucket(v, s));
+        CK(launch_pick(v, s));
+    }
+    st = record_event(ctx, s, EV_NICHE, true);
+    if (st) return st;
+    CK(launch_compact(v, s));
+    return NSGA3_OK;
+}
+
+nsga3_status eager_generation(nsga3_ctx* ctx, cudaStream_t s)
+{
+    nsga3_status st = record_event(ctx, s, EV_START, true);
+    if (st) return st;
+    CK(launch_vary_eval(ctx->v, s));
+    st = record_event(ctx, s, EV_VARY, true);
+    if (st) return st;
+    st = eager_selection(ctx, ctx->v, s, false);
+    if (st) return st;
+    CK(launch_gather(ctx->v, s));
+    CK(launch_bump_gen(ctx->v, s));
+    return record_event(ctx, s, EV_END, true);
+}
+
 nsga3_status build_graphs(nsga3_ctx* ctx)
 {
+    if (ctx->eager) return NSGA3_OK;
     cudaGraph_t g = nullptr;
     // selection graph
     CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeRelaxed));
@@ -251,6 +317,87 @@ nsga3_status build_graphs(nsga3_ctx* ctx)
     CK(cudaGraphInstantiate(&ctx->gx_step, g, 0));
     cudaGraphDestroy(g);
     return NSGA3_OK;
+}
+
+// Orders the w reference directions into blocks of 32 by recursive median
+// splits of their unit vectors along the widest coordinate (every block but
+// the last holds exactly 32), and records each block's unit centre and
+// angular radius, inflated by 1e-6 rad to cover the FP32 rounding of the
+// centre.  Only the association scan's pruning uses this order; results are
+// reported with the original indices.
+void build_ref_blocks(int m, int w, int M4, const std::vector<double>& Z, std::vector<float>& cent,
+                      std::vector<float2>& crsr, std::vector<float>& zp, std::vector<int32_t>& jidx)
+{
+    std::vector<double> U((size_t)w * m);
+    for (int j = 0; j < w; ++j) {
+        double s = 0.0;
+        for (int q = 0; q < m; ++q) s += Z[(size_t)j * m + q] * Z[(size_t)j * m + q];
+        const double n = std::sqrt(s);
+        for (int q = 0; q < m; ++q) U[(size_t)j * m + q] = Z[(size_t)j * m + q] / n;
+    }
+    std::vector<int32_t> perm(w);
+    std::iota(perm.begin(), perm.end(), 0);
+    struct Range {
+        int lo, hi;
+    };
+    std::vector<Range> stack{{0, w}};
+    while (!stack.empty()) {
+        Range r = stack.back();
+        stack.pop_back();
+        if (r.hi - r.lo <= 32) continue;
+        int dim = 0;
+        double widest = -1.0;
+        for (int q = 0; q < m; ++q) {
+            double lo = 1e300, hi = -1e300;
+            for (int t = r.lo; t < r.hi; ++t) {
+                const double x = U[(size_t)perm[t] * m + q];
+                lo = std::min(lo, x);
+                hi = std::max(hi, x);
+            }
+            if (hi - lo > widest) {
+                widest = hi - lo;
+                dim = q;
+            }
+        }
+        const int nbk = (r.hi - r.lo + 31) / 32;
+        const int mid = r.lo + 32 * (nbk / 2);
+        std::nth_element(perm.begin() + r.lo, perm.begin() + mid, perm.begin() + r.hi,
+                         [&](int a, int b) {
+                             const double xa = U[(size_t)a * m + dim], xb = U[(size_t)b * m + dim];
+                             return xa < xb || (xa == xb && a < b);
+                         });
+        stack.push_back({r.lo, mid});
+        stack.push_back({mid, r.hi});
+    }
+    const int nb = (w + 31) / 32;
+    cent.assign((size_t)nb * M4, 0.0f);
+    crsr.assign(nb, make_float2(1.0f, 0.0f));
+    zp.assign((size_t)w * M4, 0.0f);
+    jidx.assign(w, 0);
+    for (int b = 0; b < nb; ++b) {
+        const int lo = 32 * b, hi = std::min(w, lo + 32);
+        double cvec[NSGA3_MAX_M] = {0};
+        for (int t = lo; t < hi; ++t)
+            for (int q = 0; q < m; ++q) cvec[q] += U[(size_t)perm[t] * m + q];
+        double cn = 0.0;
+        for (int q = 0; q < m; ++q) cn += cvec[q] * cvec[q];
+        cn = std::sqrt(cn);
+        for (int q = 0; q < m; ++q) cvec[q] /= cn;
+        double cmin = 1.0;
+        for (int t = lo; t < hi; ++t) {
+            double dt = 0.0;
+            for (int q = 0; q < m; ++q) dt += U[(size_t)perm[t] * m + q] * cvec[q];
+            cmin = std::min(cmin, dt);
+        }
+        double r = std::acos(std::max(-1.0, std::min(1.0, cmin))) + 1e-6;
+        if (r > M_PI) r = M_PI;
+        crsr[b] = make_float2((float)std::cos(r), (float)std::sin(r));
+        for (int q = 0; q < m; ++q) cent[(size_t)b * M4 + q] = (float)cvec[q];
+        for (int t = lo; t < hi; ++t) {
+            jidx[t] = perm[t];
+            for (int q = 0; q < m; ++q) zp[(size_t)t * M4 + q] = (float)U[(size_t)perm[t] * m + q];
+        }
+    }
 }
 
 nsga3_status setup(nsga3_ctx* ctx)
@@ -302,11 +449,30 @@ nsga3_status setup(nsga3_ctx* ctx)
     AL(v.rho, w);
     AL(v.rhop, w);
     AL(v.take, w);
+    AL(v.refprio, w);
     AL(v.ref_off, w + 1);
     AL(v.cursor, w);
     AL(v.bucket, n2);
     AL(v.large, w);
     AL(v.sel, N);
+    v.nblk = (w + 31) / 32;
+    v.cand_cap = 4 * n2 + 64;
+    AL(v.arun, n2);
+    AL(v.cand, v.cand_cap);
+    AL(v.cdist, v.cand_cap);
+    AL(v.slow, n2);
+    float* bc;
+    float2* br;
+    float* bz;
+    int32_t* bj;
+    AL(bc, (size_t)v.nblk * M4);
+    AL(br, v.nblk);
+    AL(bz, (size_t)w * M4);
+    AL(bj, w);
+    v.blk_c = bc;
+    v.blk_r = br;
+    v.blk_z = bz;
+    v.blk_j = bj;
     double* Zd;
     double* nz;
     float* Zh;
@@ -340,11 +506,41 @@ nsga3_status setup(nsga3_ctx* ctx)
     if (ctx->has_W)
         CK(cudaMemcpyAsync(Wd, ctx->opts.W, (size_t)m * (m - 1) * sizeof(float), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
+    {
+        std::vector<double> Zh((size_t)w * m);
+        CK(cudaMemcpy(Zh.data(), Zd, Zh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        std::vector<float> hc, hz;
+        std::vector<float2> hr;
+        std::vector<int32_t> hj;
+        build_ref_blocks(m, w, M4, Zh, hc, hr, hz, hj);
+        CK(cudaMemcpy(bc, hc.data(), hc.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(br, hr.data(), hr.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(bz, hz.data(), hz.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(bj, hj.data(), hj.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        ctx->vs.blk_c = bc;
+        ctx->vs.blk_r = br;
+        ctx->vs.blk_z = bz;
+        ctx->vs.blk_j = bj;
+        ctx->vs.nblk = v.nblk;
+        ctx->vs.arun = v.arun;
+        ctx->vs.cand = v.cand;
+        ctx->vs.cdist = v.cdist;
+        ctx->vs.cand_cap = v.cand_cap;
+        ctx->vs.slow = v.slow;
+    }
+    cudaError_t ae;
+    {
+        std::lock_guard<std::mutex> lk(g_attr_mutex);
+        ae = assoc_prepare(v);
+    }
+    if (ae != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, NSGA3_EINVAL, "%d reference directions exceed the association scan's tables", w);
+    }
     ctx->nsplit = peel_nsplit(v, ctx->num_sms);
     return build_graphs(ctx);
 }
 
-std::mutex g_attr_mutex;
 bool g_attr_done = false;
 
 nsga3_status init_attributes(nsga3_ctx* ctx)
@@ -418,6 +614,10 @@ nsga3_status nsga3_create(int m, int d, int N, int ref_divisions, const nsga3_op
     ctx->tau = o.tau;
     ctx->opts = o;
     ctx->has_W = o.W != nullptr;  // W is read during create only
+    {
+        const char* e = getenv("NSGA3_EAGER");
+        ctx->eager = e && e[0] == '1';
+    }
     nsga3_status st = NSGA3_OK;
     if (cudaGetDevice(&ctx->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
@@ -473,7 +673,15 @@ nsga3_status nsga3_select(nsga3_ctx* ctx, const float* objs, int32_t* ranks, int
     if (!ctx || !objs || !ranks || !selected) return fail(ctx, NSGA3_EINVAL, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(ctx->vs.F, objs, (size_t)ctx->n2 * ctx->m * sizeof(float), cudaMemcpyDefault, s));
-    CK(cudaGraphLaunch(ctx->gx_select, s));
+    if (ctx->eager) {
+        nsga3_status st = record_event(ctx, s, EV_START, true);
+        if (!st) st = record_event(ctx, s, EV_VARY, true);
+        if (!st) st = eager_selection(ctx, ctx->vs, s, true);
+        if (!st) st = record_event(ctx, s, EV_END, true);
+        if (st) return st;
+    } else {
+        CK(cudaGraphLaunch(ctx->gx_select, s));
+    }
     CK(cudaMemcpyAsync(ranks, ctx->vs.rank2, (size_t)ctx->n2 * sizeof(int32_t), cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(selected, ctx->vs.sel, (size_t)ctx->N * sizeof(int32_t), cudaMemcpyDefault, s));
     ctx->last_kind = 1;
@@ -502,8 +710,13 @@ nsga3_status nsga3_vary(nsga3_ctx* ctx, void* stream)
 nsga3_status nsga3_step(nsga3_ctx* ctx, void* stream)
 {
     if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
-    if (!ctx->gx_step) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W was NULL)");
-    CK(cudaGraphLaunch(ctx->gx_step, (cudaStream_t)stream));
+    if (!ctx->has_W) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W was NULL)");
+    if (ctx->eager) {
+        nsga3_status st = eager_generation(ctx, (cudaStream_t)stream);
+        if (st) return st;
+    } else {
+        CK(cudaGraphLaunch(ctx->gx_step, (cudaStream_t)stream));
+    }
     ctx->last_kind = 2;
     return NSGA3_OK;
 }
@@ -524,6 +737,14 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
     if (!ctx || generations < 0) return fail(ctx, NSGA3_EINVAL, "bad arguments");
     for (int r = 0; r < n; ++r)
         if (!ctxs[r] || !ctxs[r]->has_W) return fail(ctx, NSGA3_EINVAL, "run %d has no objective", r);
+    if (ctx->eager) {
+        for (int g = 0; g < generations; ++g)
+            for (int r = 0; r < n; ++r) {
+                nsga3_status st = nsga3_step(ctxs[r], stream);
+                if (st) return st;
+            }
+        return NSGA3_OK;
+    }
     std::vector<nsga3_ctx*> key(ctxs, ctxs + n);
     if (!ctx->gx_batch || ctx->batch_key != key) {
         if (ctx->gx_batch) {
@@ -553,14 +774,16 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
                     st = fail(ctx, NSGA3_ECUDA, "fork wait failed");
                     break;
                 }
-                st = record_generation(ctxs[r], br[r], br2[r], false);
-                if (st) {
+                nsga3_status rs = record_generation(ctxs[r], br[r], br2[r], false);
+                if (rs) {
+                    st = rs;
                     ctx->err = ctxs[r]->err;
-                    break;
                 }
+                // join the branch even after a failure so the capture ends cleanly
                 if (cudaEventRecord(evs[r], br[r]) != cudaSuccess ||
-                    cudaStreamWaitEvent(s0, evs[r], 0) != cudaSuccess)
-                    st = fail(ctx, NSGA3_ECUDA, "join failed");
+                    cudaStreamWaitEvent(s0, evs[r], 0) != cudaSuccess) {
+                    if (!st) st = fail(ctx, NSGA3_ECUDA, "join failed");
+                }
             }
             cudaError_t e = cudaStreamEndCapture(s0, &g);
             if (!st && e != cudaSuccess) st = fail(ctx, NSGA3_ECUDA, "capture failed: %s", cudaGetErrorString(e));
@@ -657,6 +880,7 @@ nsga3_status nsga3_get_selection_info(nsga3_ctx* ctx, int32_t* info)
     info[9] = c.rlev;
     info[10] = c.overflow;
     info[11] = c.recheck_miss;
+    info[12] = (int32_t)c.peel_rows;
     return NSGA3_OK;
 }
 
@@ -687,9 +911,10 @@ nsga3_status nsga3_phase_times(nsga3_ctx* ctx, float* ms, int n)
 {
     if (!ctx || !ms || n < 1) return fail(ctx, NSGA3_EINVAL, "bad arguments");
     CK(cudaEventSynchronize(ctx->ev[EV_END]));
-    const int pairs[6][2] = {{EV_START, EV_VARY}, {EV_VARY, EV_DOM},   {EV_DOM, EV_PEEL},
-                             {EV_PEEL, EV_NICHE}, {EV_NICHE, EV_END}, {EV_START, EV_END}};
-    for (int t = 0; t < n && t < 6; ++t) {
+    const int pairs[7][2] = {{EV_START, EV_VARY}, {EV_VARY, EV_RESET}, {EV_RESET, EV_DOM},
+                             {EV_DOM, EV_PEEL},   {EV_PEEL, EV_NICHE}, {EV_NICHE, EV_END},
+                             {EV_START, EV_END}};
+    for (int t = 0; t < n && t < 7; ++t) {
         float x = 0.0f;
         CK(cudaEventElapsedTime(&x, ctx->ev[pairs[t][0]], ctx->ev[pairs[t][1]]));
         ms[t] = x;
@@ -705,9 +930,9 @@ nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches)
     CK(cudaMemcpy(&c, ctx->v.ctrl, sizeof c, cudaMemcpyDeviceToHost));
     // reset, dominance, post-peel, compaction (+ finite check for a selection;
     // + variation, gather, counter for a generation), one per peel pass, and
-    // 9 niching launches when the IF branch ran
+    // 12 niching launches when the IF branch ran
     int fixed = (ctx->last_kind == 1) ? 5 : 7;
-    *launches = fixed + c.passes + (c.need_niche ? 9 : 0);
+    *launches = fixed + c.passes + (c.need_niche ? 12 : 0);
     return NSGA3_OK;
 }
 

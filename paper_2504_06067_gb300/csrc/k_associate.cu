@@ -3,28 +3,43 @@
 // D_ij = |f'| sqrt(1 - cos^2), pi_i = argmin_j D_ij, d_i = min_j D_ij) and
 // the niche counts rho (over S) and rho' (over F_l) of Alg. 2 lines 5-6.
 //
-// Exactness: the FP64 distance of the oracle is reproduced operation for
-// operation (_rn intrinsics, left-to-right sums) but only for candidate
-// references.  Candidates come from an FP32 scan of cosines
-// qhat_j = u . zhat_j with unit vectors u = f'/|f'|, zhat_j = z_j/|z_j|
-// (components >= 0).  Each qhat_j is within Delta = (m+4) 2^-24 of the
-// exact cosine (FP32 rounding of u and zhat plus m FMA roundings over
-// non-negative terms of sum <= 1).  A reference whose qhat is more than
-// 2 Delta + 1e-12 below the best qhat therefore has an exact cosine at least
-// 1e-12 below the best reference's; since the vertices e_q are references,
-// the best cosine is >= 1/sqrt(m), so its exact 1 - c^2 is larger by
-// > 1e-12/sqrt(m) -- far above the FP64 evaluation error (~1e-15) -- and its
-// FP64 distance is strictly larger: it can neither win nor tie.  The FP64
-// argmin over the candidates (ties -> lowest j) thus equals the argmin over
-// all j.  A point whose per-lane candidate list overflows is rescanned in
-// FP64 over all references by its whole CTA.
+// Exactness.  The FP64 distance is evaluated operation for operation like a
+// plain CPU evaluation (_rn intrinsics, left-to-right sums), but only for
+// candidate references.  Candidates come from FP32 cosines
+// qhat_j = u . zhat_j of the unit vectors u = f'/|f'| and zhat_j = z_j/|z_j|
+// (all components >= 0).  qhat_j is within Delta = (m+4) 2^-24 of the exact
+// cosine (FP32 rounding of u and zhat, m FMA roundings over non-negative
+// terms summing to <= 1).  A reference whose qhat is more than
+// band = 2 Delta + 1e-12 below the best qhat has an exact cosine > 1e-12
+// below the best reference's; as the vertices e_q are references the best
+// cosine is >= 1/sqrt(m), so its exact 1 - c^2 is larger by > 1e-12/sqrt(m),
+// far above the FP64 evaluation error (~1e-15): its FP64 distance is
+// strictly larger, so it can neither win nor tie.  The FP64 argmin over the
+// candidates (ties -> lowest j) equals the argmin over all references.
+//
+// Pruning.  References are reordered (host, at context creation) into
+// spatially compact blocks of 32 by recursive median splits; block b has a
+// unit centre c_b and angular radius r_b.  For a point at angle theta from
+// c_b every reference of the block has cosine <= cos(max(0, theta - r_b))
+// = cos(theta) cos(r_b) + sin(theta) sin(r_b) when theta > r_b (sin(theta)
+// computed from the rejection vector u - cos(theta) c_b, which has no
+// cancellation).  With its FP32 error below EPS, a block whose bound + EPS
+// is below best - band cannot hold a candidate and is skipped.  A warp owns
+// one point: it bounds every block, scans the best-bounded block first, then
+// the blocks that survive the bound.
+//
+// FP64 work (GB300 runs FP64 at 1/64 of the FP32 rate) is kept converged:
+// the scan only writes (point, reference) candidate runs; a separate kernel
+// evaluates one candidate per thread, and a third takes each point's argmin.
+// A point whose candidate list overflows is rescanned in FP64 over all
+// references by a whole CTA (k_assoc_slow), as is every point in debug mode.
 #include "kernels.cuh"
 
 namespace {
 
-constexpr int AB = 256;      // threads per CTA (8 warps)
-constexpr int RT = 256;      // references per shared-memory tile
-constexpr int NCAND = 4;     // candidate slots per lane
+constexpr int AB = 256;   // threads per CTA (8 warps, one point per warp)
+constexpr int LC = 64;    // candidate slots per warp
+constexpr float EPS = 1e-5f;
 
 __device__ __forceinline__ double perp_dist(const double* fp, double nf, const double* Zj, double nzj,
                                             int m)
@@ -57,148 +72,258 @@ __global__ void __launch_bounds__(AB) k_assoc_prep(RunView v)
     }
     const double nf = __dsqrt_rn(ss);
     v.fnorm[s] = nf;
+    const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
     for (int q = 0; q < v.M4; ++q)
-        v.uhat[(size_t)s * v.M4 + q] = (q < m && nf > 0.0) ? __double2float_rn(__ddiv_rn(fp[q], nf)) : 0.0f;
+        v.uhat[(size_t)s * v.M4 + q] = q < m ? __double2float_rn(fp[q] * inv) : 0.0f;
 }
 
 template <int M>
 __global__ void __launch_bounds__(AB) k_assoc_scan(RunView v)
 {
     constexpr int M4 = (M + 3) & ~3;
-    __shared__ __align__(16) float zt[RT * M4];
-    __shared__ float s_best[8][32];
-    __shared__ double s_d[8][32];
-    __shared__ int s_j[8][32];
-    __shared__ int s_ovf[32];
-    __shared__ double s_fd[32];
-    __shared__ int s_fj[32];
+    extern __shared__ __align__(16) float sm[];
     Ctrl* c = v.ctrl;
     if (read_status(c)) return;
     const int nT = c->nT;
+    const int nb = v.nblk;
     const int lane = lane_id(), warp = threadIdx.x >> 5;
-    const int s0 = blockIdx.x * 32;
-    if (s0 >= nT) return;
-    const int slot = s0 + lane;
-    const bool live = slot < nT;
+    float* cent = sm;                                                     // nb x M4
+    float2* crsr = reinterpret_cast<float2*>(cent + (size_t)nb * M4);      // nb
+    float* wall = reinterpret_cast<float*>(crsr + nb);                     // 8 x nb bounds
+    float* wbnd = wall + (size_t)warp * nb;
+    int* lj = reinterpret_cast<int*>(wall + (size_t)8 * nb) + warp * 2 * LC;
+    float* lq = reinterpret_cast<float*>(lj + LC);
+    for (int e = threadIdx.x; e < nb * M4; e += AB) cent[e] = v.blk_c[e];
+    for (int e = threadIdx.x; e < nb; e += AB) crsr[e] = v.blk_r[e];
+    __syncthreads();
     const float band = 2.0f * (float)(M + 4) * 5.9604644775390625e-08f + 1e-12f;
-
-    float u[M4];
-#pragma unroll
-    for (int q = 0; q < M4; ++q) u[q] = live ? v.uhat[(size_t)slot * M4 + q] : 0.0f;
-
-    float best = -2.0f;
-    int cj[NCAND];
-    float cq[NCAND];
-#pragma unroll
-    for (int t = 0; t < NCAND; ++t) {
-        cj[t] = -1;
-        cq[t] = -2.0f;
-    }
-    int ovf = 0;
     const int w = v.w;
-    for (int tb = 0; tb < w; tb += RT) {
-        const int nt = min(RT, w - tb);
-        __syncthreads();
-        const float4* src = reinterpret_cast<const float4*>(v.Zh + (size_t)tb * M4);
-        float4* dst = reinterpret_cast<float4*>(zt);
-        for (int e = threadIdx.x; e < nt * M4 / 4; e += AB) dst[e] = src[e];
-        __syncthreads();
-        for (int r = warp; r < nt; r += 8) {
-            const float4* z4 = reinterpret_cast<const float4*>(zt + r * M4);
-            float qh = 0.0f;
+
+    for (int pt = blockIdx.x * 8 + warp; pt < nT; pt += gridDim.x * 8) {
+        float u[M];
 #pragma unroll
-            for (int q4 = 0; q4 < M4 / 4; ++q4) {
-                float4 z = z4[q4];
-                qh = fmaf(u[4 * q4 + 0], z.x, qh);
-                qh = fmaf(u[4 * q4 + 1], z.y, qh);
-                qh = fmaf(u[4 * q4 + 2], z.z, qh);
-                qh = fmaf(u[4 * q4 + 3], z.w, qh);
+        for (int q = 0; q < M; ++q) u[q] = v.uhat[(size_t)pt * M4 + q];
+        if (v.fnorm[pt] == 0.0) {  // every distance is 0: handled by the finalisation
+            if (lane == 0) v.arun[pt] = make_int2(0, 0);
+            continue;
+        }
+        // phase 1: cone bound of every block
+        float bmax = -4.0f;
+        int bb = 0x7fffffff;
+        for (int b = lane; b < nb; b += 32) {
+            const float* cb = cent + b * M4;
+            float ct = 0.0f;
+#pragma unroll
+            for (int q = 0; q < M; ++q) ct = fmaf(u[q], cb[q], ct);
+            float s2 = 0.0f;
+#pragma unroll
+            for (int q = 0; q < M; ++q) {
+                const float r = fmaf(-ct, cb[q], u[q]);
+                s2 = fmaf(r, r, s2);
             }
-            if (qh >= best - band) {
-                const int j = tb + r;
-                if (qh > best + band) {
-#pragma unroll
-                    for (int t = 0; t < NCAND; ++t) cj[t] = -1;
-                }
-                if (qh > best) best = qh;
-                // place into a free or stale slot
-                bool placed = false;
-#pragma unroll
-                for (int t = 0; t < NCAND; ++t) {
-                    if (!placed && (cj[t] < 0 || cq[t] < best - band)) {
-                        cj[t] = j;
-                        cq[t] = qh;
-                        placed = true;
-                    }
-                }
-                if (!placed) ovf = 1;
+            const float2 cs = crsr[b];
+            const float bound = (ct >= cs.x) ? 1.0f : fmaf(ct, cs.x, sqrtf(s2) * cs.y);
+            wbnd[b] = bound;
+            if (bound > bmax) {
+                bmax = bound;
+                bb = b;
             }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, bmax, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bb, o);
+            if (ob > bmax || (ob == bmax && oi < bb)) {
+                bmax = ob;
+                bb = oi;
+            }
+        }
+        __syncwarp();
+        // phase 2: scan the best-bounded block, then every block the bound cannot exclude
+        float best = -4.0f;
+        int nl = 0;
+        bool ovf = false;
+        auto scan_block = [&](int b) {
+            const int pos = b * 32 + lane;
+            float qh = -4.0f;
+            int j = -1;
+            if (pos < w) {
+                const float4* z4 = reinterpret_cast<const float4*>(v.blk_z + (size_t)pos * M4);
+                float zz[M4];
+#pragma unroll
+                for (int q4 = 0; q4 < M4 / 4; ++q4) {
+                    const float4 z = __ldg(z4 + q4);
+                    zz[4 * q4 + 0] = z.x;
+                    zz[4 * q4 + 1] = z.y;
+                    zz[4 * q4 + 2] = z.z;
+                    zz[4 * q4 + 3] = z.w;
+                }
+                qh = 0.0f;
+#pragma unroll
+                for (int q = 0; q < M; ++q) qh = fmaf(u[q], zz[q], qh);
+                j = v.blk_j[pos];
+            }
+            float wm = qh;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+            best = fmaxf(best, wm);
+            const bool keep = j >= 0 && qh >= best - band;
+            unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (nl + __popc(bal) > LC) {  // drop entries that fell out of the band
+                __syncwarp();
+                int kept = 0;
+                for (int e0 = 0; e0 < nl; e0 += 32) {
+                    const int e = e0 + lane;
+                    const bool k2 = e < nl && lq[e] >= best - band;
+                    const unsigned b2 = __ballot_sync(0xffffffffu, k2);
+                    int jj = 0;
+                    float qq = 0.0f;
+                    if (k2) {
+                        jj = lj[e];
+                        qq = lq[e];
+                    }
+                    __syncwarp();
+                    if (k2) {
+                        const int p = kept + __popc(b2 & ((1u << lane) - 1u));
+                        lj[p] = jj;
+                        lq[p] = qq;
+                    }
+                    kept += __popc(b2);
+                    __syncwarp();
+                }
+                nl = kept;
+                if (nl + __popc(bal) > LC) {
+                    ovf = true;
+                    bal = 0u;
+                }
+            }
+            if (keep && bal) {
+                const int p = nl + __popc(bal & ((1u << lane) - 1u));
+                lj[p] = j;
+                lq[p] = qh;
+            }
+            nl += __popc(bal);
+            __syncwarp();
+        };
+        scan_block(bb);
+        for (int base = 0; base < nb; base += 32) {
+            const int b = base + lane;
+            const bool f = b < nb && b != bb && wbnd[b] + EPS >= best - band;
+            unsigned msk = __ballot_sync(0xffffffffu, f);
+            while (msk) {
+                const int b2 = base + __ffs(msk) - 1;
+                msk &= msk - 1;
+                if (wbnd[b2] + EPS >= best - band) scan_block(b2);
+            }
+        }
+        // final candidates: q >= best - band
+        int cnt = 0;
+        for (int e0 = 0; e0 < nl; e0 += 32) {
+            const int e = e0 + lane;
+            cnt += __popc(__ballot_sync(0xffffffffu, e < nl && lq[e] >= best - band));
+        }
+        int start = 0;
+        if (lane == 0 && !ovf) start = atomicAdd(&c->ncand, cnt);
+        start = __shfl_sync(0xffffffffu, start, 0);
+        if (ovf || start + cnt > v.cand_cap) {
+            if (lane == 0) {
+                v.arun[pt] = make_int2(-1, 0);
+                v.slow[atomicAdd(&c->nslow, 1)] = pt;
+            }
+            __syncwarp();
+            continue;
+        }
+        int off = 0;
+        for (int e0 = 0; e0 < nl; e0 += 32) {
+            const int e = e0 + lane;
+            const bool k2 = e < nl && lq[e] >= best - band;
+            const unsigned b2 = __ballot_sync(0xffffffffu, k2);
+            if (k2) v.cand[start + off + __popc(b2 & ((1u << lane) - 1u))] = make_int2(pt, lj[e]);
+            off += __popc(b2);
+        }
+        if (lane == 0) v.arun[pt] = make_int2(start, cnt);
+        __syncwarp();
     }
-    // merge the 8 warps' maxima per point
-    s_best[warp][lane] = best;
-    if (warp == 0) s_ovf[lane] = 0;
-    __syncthreads();
-    if (ovf) atomicOr(&s_ovf[lane], 1);
-    float B = s_best[0][lane];
+}
+
+// one FP64 distance per candidate (converged)
+template <int M>
+__global__ void __launch_bounds__(AB) k_assoc_recheck(RunView v)
+{
+    Ctrl* c = v.ctrl;
+    if (read_status(c)) return;
+    const int n = min(c->ncand, v.cand_cap);
+    for (int e = blockIdx.x * AB + threadIdx.x; e < n; e += gridDim.x * AB) {
+        const int2 pj = v.cand[e];
+        double fp[M];
 #pragma unroll
-    for (int t = 1; t < 8; ++t) B = fmaxf(B, s_best[t][lane]);
-    // FP64 recheck of this lane's surviving candidates
-    double fp[M];
-    double nf = 0.0;
-    if (live) {
-#pragma unroll
-        for (int q = 0; q < M; ++q) fp[q] = v.fprime[(size_t)slot * M + q];
-        nf = v.fnorm[slot];
+        for (int q = 0; q < M; ++q) fp[q] = v.fprime[(size_t)pj.x * M + q];
+        v.cdist[e] = perp_dist(fp, v.fnorm[pj.x], v.Zd + (size_t)pj.y * M, v.nz[pj.y], M);
     }
-    double bd = CUDART_INF;
-    int bj = 0x7fffffff;
-#pragma unroll
-    for (int t = 0; t < NCAND; ++t) {
-        if (live && cj[t] >= 0 && cq[t] >= B - band) {
-            const int j = cj[t];
-            double d = perp_dist(fp, nf, v.Zd + (size_t)j * M, v.nz[j], M);
+}
+
+__device__ __forceinline__ void write_assoc(const RunView& v, Ctrl* c, int i, int j, double d)
+{
+    v.pi[i] = j;
+    v.dist[i] = d;
+    if (v.rank2[i] < c->l)
+        atomicAdd(&v.rho[j], 1);
+    else
+        atomicAdd(&v.rhop[j], 1);
+}
+
+// per point: lexicographic (d, j) minimum of its candidates
+__global__ void __launch_bounds__(AB) k_assoc_final(RunView v)
+{
+    Ctrl* c = v.ctrl;
+    if (read_status(c)) return;
+    const int pt = blockIdx.x * AB + threadIdx.x;
+    if (pt >= c->nT) return;
+    const int2 run = v.arun[pt];
+    if (run.x < 0) return;  // slow path
+    double bd = 0.0;
+    int bj = 0;
+    if (v.fnorm[pt] != 0.0) {
+        bd = CUDART_INF;
+        bj = 0x7fffffff;
+        for (int e = run.x; e < run.x + run.y; ++e) {
+            const double d = v.cdist[e];
+            const int j = v.cand[e].y;
             if (lex_less(d, j, bd, bj)) {
                 bd = d;
                 bj = j;
             }
         }
     }
-    s_d[warp][lane] = bd;
-    s_j[warp][lane] = bj;
-    __syncthreads();
-    if (warp == 0) {
-        double fd = s_d[0][lane];
-        int fj = s_j[0][lane];
-        for (int t = 1; t < 8; ++t)
-            if (lex_less(s_d[t][lane], s_j[t][lane], fd, fj)) {
-                fd = s_d[t][lane];
-                fj = s_j[t][lane];
-            }
-        if (live && nf == 0.0) {  // |f'| = 0: every distance is 0, the first reference wins
-            fd = 0.0;
-            fj = 0;
-        }
-        s_fd[lane] = fd;
-        s_fj[lane] = fj;
+    if (v.debug_recheck_all) {
+        v.dist[v.Tlist[pt]] = bd;  // compared by k_assoc_slow
+        v.pi[v.Tlist[pt]] = bj;
+        v.slow[atomicAdd(&c->nslow, 1)] = pt;
+        return;
     }
-    __syncthreads();
-    // overflowed lists (and every point in debug mode): full FP64 scan by the whole CTA
-    const unsigned need =
-        __ballot_sync(0xffffffffu, live && nf != 0.0 && (s_ovf[lane] || v.debug_recheck_all));
-    unsigned todo = need;
-    while (todo) {
-        const int p = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int sp = s0 + p;
-        double fpp[M];
+    write_assoc(v, c, v.Tlist[pt], bj, bd);
+}
+
+// full FP64 scan of one point per CTA (overflowed lists, debug mode)
+template <int M>
+__global__ void __launch_bounds__(AB) k_assoc_slow(RunView v)
+{
+    __shared__ double sd[AB / 32];
+    __shared__ int sj[AB / 32];
+    Ctrl* c = v.ctrl;
+    if (read_status(c)) return;
+    const int ns = c->nslow;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    for (int t = blockIdx.x; t < ns; t += gridDim.x) {
+        const int pt = v.slow[t];
+        double fp[M];
 #pragma unroll
-        for (int q = 0; q < M; ++q) fpp[q] = v.fprime[(size_t)sp * M + q];
-        const double nfp = v.fnorm[sp];
+        for (int q = 0; q < M; ++q) fp[q] = v.fprime[(size_t)pt * M + q];
+        const double nf = v.fnorm[pt];
         double d0 = CUDART_INF;
         int j0 = 0x7fffffff;
-        for (int j = threadIdx.x; j < w; j += AB) {
-            double d = perp_dist(fpp, nfp, v.Zd + (size_t)j * M, v.nz[j], M);
+        for (int j = threadIdx.x; j < v.w; j += AB) {
+            const double d = perp_dist(fp, nf, v.Zd + (size_t)j * M, v.nz[j], M);
             if (lex_less(d, j, d0, j0)) {
                 d0 = d;
                 j0 = j;
@@ -206,53 +331,63 @@ __global__ void __launch_bounds__(AB) k_assoc_scan(RunView v)
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            double od = __shfl_xor_sync(0xffffffffu, d0, o);
-            int oj = __shfl_xor_sync(0xffffffffu, j0, o);
+            const double od = __shfl_xor_sync(0xffffffffu, d0, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, j0, o);
             if (lex_less(od, oj, d0, j0)) {
                 d0 = od;
                 j0 = oj;
             }
         }
         if (lane == 0) {
-            s_d[warp][p] = d0;
-            s_j[warp][p] = j0;
+            sd[warp] = d0;
+            sj[warp] = j0;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double fd = s_d[0][p];
-            int fj = s_j[0][p];
-            for (int t = 1; t < 8; ++t)
-                if (lex_less(s_d[t][p], s_j[t][p], fd, fj)) {
-                    fd = s_d[t][p];
-                    fj = s_j[t][p];
+            for (int q = 1; q < AB / 32; ++q)
+                if (lex_less(sd[q], sj[q], d0, j0)) {
+                    d0 = sd[q];
+                    j0 = sj[q];
                 }
-            if (s_ovf[p]) {
+            const int i = v.Tlist[pt];
+            if (v.arun[pt].x < 0) {
                 atomicAdd(&c->overflow, 1);
-            } else if (fd != s_fd[p] || fj != s_fj[p]) {
-                atomicAdd(&c->recheck_miss, 1);  // debug mode: the filter lost the argmin
+            } else if (v.debug_recheck_all && (v.pi[i] != j0 || v.dist[i] != d0)) {
+                atomicAdd(&c->recheck_miss, 1);
             }
-            s_fd[p] = fd;
-            s_fj[p] = fj;
+            write_assoc(v, c, i, j0, d0);
         }
         __syncthreads();
     }
-    if (warp == 0 && live) {
-        const int i = v.Tlist[slot];
-        const int fj = s_fj[lane];
-        v.pi[i] = fj;
-        v.dist[i] = s_fd[lane];
-        if (v.rank2[i] < c->l)
-            atomicAdd(&v.rho[fj], 1);
-        else
-            atomicAdd(&v.rhop[fj], 1);
-    }
+}
+
+size_t scan_smem(const RunView& v) { return (size_t)v.nblk * (v.M4 + 2 + 8) * 4 + 8 * 2 * LC * 4; }
+
+template <int M>
+cudaError_t launch_m(const RunView& v, cudaStream_t s, int num_sms)
+{
+    const size_t sm = scan_smem(v);
+    int blocks = (v.n2 + 7) / 8;
+    if (blocks > num_sms * 4) blocks = num_sms * 4;
+    k_assoc_scan<M><<<blocks, AB, sm, s>>>(v);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int rb = (v.cand_cap + AB - 1) / AB;
+    if (rb > num_sms * 8) rb = num_sms * 8;
+    k_assoc_recheck<M><<<rb, AB, 0, s>>>(v);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_assoc_final<<<(v.n2 + AB - 1) / AB, AB, 0, s>>>(v);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_assoc_slow<M><<<num_sms, AB, 0, s>>>(v);
+    return cudaGetLastError();
 }
 
 template <int M>
-cudaError_t launch_scan_m(const RunView& v, cudaStream_t s)
+cudaError_t attr_m(size_t sm)
 {
-    k_assoc_scan<M><<<(v.n2 + 31) / 32, AB, 0, s>>>(v);
-    return cudaGetLastError();
+    return cudaFuncSetAttribute(k_assoc_scan<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
 
 }  // namespace
@@ -263,18 +398,44 @@ cudaError_t launch_assoc_prep(const RunView& v, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_assoc_scan(const RunView& v, cudaStream_t s)
+cudaError_t launch_assoc_scan(const RunView& v, int num_sms, cudaStream_t s)
 {
     switch (v.m) {
-    case 2: return launch_scan_m<2>(v, s);
-    case 3: return launch_scan_m<3>(v, s);
-    case 4: return launch_scan_m<4>(v, s);
-    case 5: return launch_scan_m<5>(v, s);
-    case 6: return launch_scan_m<6>(v, s);
-    case 7: return launch_scan_m<7>(v, s);
-    case 8: return launch_scan_m<8>(v, s);
-    case 9: return launch_scan_m<9>(v, s);
-    case 10: return launch_scan_m<10>(v, s);
+    case 2: return launch_m<2>(v, s, num_sms);
+    case 3: return launch_m<3>(v, s, num_sms);
+    case 4: return launch_m<4>(v, s, num_sms);
+    case 5: return launch_m<5>(v, s, num_sms);
+    case 6: return launch_m<6>(v, s, num_sms);
+    case 7: return launch_m<7>(v, s, num_sms);
+    case 8: return launch_m<8>(v, s, num_sms);
+    case 9: return launch_m<9>(v, s, num_sms);
+    case 10: return launch_m<10>(v, s, num_sms);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Shared-memory opt-in of the scan for this run's block count; fails when the
+// block tables do not fit (about 5,000 blocks of 32 references).  The opt-in
+// is a property of the kernel, shared by every context of the process, so it
+// only ever grows (serialised by the caller).
+cudaError_t assoc_prepare(const RunView& v)
+{
+    static size_t granted[NSGA3_MAX_M + 1] = {0};
+    const size_t sm = scan_smem(v);
+    if (sm > 220 * 1024) return cudaErrorInvalidValue;
+    if (v.m < 2 || v.m > NSGA3_MAX_M) return cudaErrorInvalidValue;
+    if (sm <= granted[v.m]) return cudaSuccess;
+    granted[v.m] = sm;
+    switch (v.m) {
+    case 2: return attr_m<2>(sm);
+    case 3: return attr_m<3>(sm);
+    case 4: return attr_m<4>(sm);
+    case 5: return attr_m<5>(sm);
+    case 6: return attr_m<6>(sm);
+    case 7: return attr_m<7>(sm);
+    case 8: return attr_m<8>(sm);
+    case 9: return attr_m<9>(sm);
+    case 10: return attr_m<10>(sm);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -24,9 +24,11 @@ __global__ void k_sel_reset(RunView v, int nchunks)
         v.selmask[wd] = 0u;
     }
     for (int t = tid; t < nchunks; t += stride) v.chunk_done[t] = 0u;
+    const uint32_t gen = v.ctrl->gen;
     for (int j = tid; j < v.w; j += stride) {
         v.rho[j] = 0;
         v.rhop[j] = 0;
+        v.refprio[j] = philox((uint32_t)j, gen, RNG_REFPRIO, 0u, v.seed).x;
     }
     if (tid == 0) {
         Ctrl* c = v.ctrl;
@@ -46,6 +48,10 @@ __global__ void k_sel_reset(RunView v, int nchunks)
         c->rlev = 0;
         c->nsel = 0;
         c->nlarge = 0;
+        c->peel_rows = (uint32_t)v.NW;  // pass 0 reads every row
+        c->ncand = 0;
+        c->nslow = 0;
+        c->front_words = 0u;
         c->overflow = 0;
         c->recheck_miss = 0;
         for (int q = 0; q < NSGA3_MAX_M; ++q) c->zmin[q] = 0xffffffffu;

@@ -24,10 +24,6 @@ constexpr int LB = 1024;    // threads of the single-CTA kernels
 constexpr int LCAP = 4096;  // niche levels resolved by the shared histogram
 constexpr int EXACT = 1024; // candidates ranked pairwise in the last select phase
 
-__device__ __forceinline__ uint32_t ref_prio(uint64_t seed, uint32_t gen, int j)
-{
-    return philox((uint32_t)j, gen, RNG_REFPRIO, 0u, seed).x;
-}
 __device__ __forceinline__ uint32_t mem_prio(uint64_t seed, uint32_t gen, int i)
 {
     return philox((uint32_t)i, gen, RNG_MEMPRIO, 0u, seed).x;
@@ -203,7 +199,6 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
     Ctrl* c = v.ctrl;
     if (read_status(c)) return;
     const int w = v.w, K = c->K;
-    const uint32_t gen = c->gen;
     for (int t = threadIdx.x; t <= LCAP; t += LB) sh.lev[t] = 0;
     if (threadIdx.x == 0) {
         sh.Lstar = LCAP;
@@ -287,9 +282,7 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
         const int lo = v.rho[j];
         return rp > 0 && lo <= Lstar && Lstar < lo + rp;
     };
-    auto key = [&](int j) {
-        return ((unsigned long long)ref_prio(v.seed, gen, j) << 32) | (unsigned)j;
-    };
+    auto key = [&](int j) { return ((unsigned long long)v.refprio[j] << 32) | (unsigned)j; };
     auto mark = [&](int j) { v.take[j] += 1; };
     block_select_smallest(w, r, key, pred, mark, sh.sel);
     __syncthreads();
@@ -383,7 +376,7 @@ __global__ void __launch_bounds__(256) k_pick(RunView v)
 }
 
 // large buckets with a partial take: one CTA per bucket
-__global__ void __launch_bounds__(LB) k_pick_large(RunView v)
+__global__ void __launch_bounds__(512) k_pick_large(RunView v)
 {
     __shared__ SelShared sh;
     Ctrl* c = v.ctrl;
@@ -427,7 +420,7 @@ cudaError_t launch_pick(const RunView& v, cudaStream_t s)
     k_pick<<<blocks, 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_pick_large<<<64, LB, 0, s>>>(v);
+    k_pick_large<<<16, 512, 0, s>>>(v);
     return cudaGetLastError();
 }
 

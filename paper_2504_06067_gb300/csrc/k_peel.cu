@@ -18,7 +18,8 @@ namespace {
 
 constexpr int LISTCAP = 2048;
 
-__global__ void __launch_bounds__(256) k_peel(RunView v, int nsplit, cudaGraphConditionalHandle h)
+__global__ void __launch_bounds__(256) k_peel(RunView v, int nsplit, cudaGraphConditionalHandle h,
+                                              int in_graph)
 {
     __shared__ int red[8][NSGA3_PEEL_COLS];
     __shared__ uint2 list[LISTCAP];
@@ -27,7 +28,12 @@ __global__ void __launch_bounds__(256) k_peel(RunView v, int nsplit, cudaGraphCo
     Ctrl* c = v.ctrl;
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     if (read_status(c)) {
-        if (blockIdx.x == 0 && tid == 0) cudaGraphSetConditional(h, 0);
+        if (blockIdx.x == 0 && tid == 0) {
+            if (in_graph)
+                cudaGraphSetConditional(h, 0);
+            else
+                c->peel_more = 0;
+        }
         return;
     }
     const int k = *(volatile int32_t*)&c->k;
@@ -132,7 +138,10 @@ __global__ void __launch_bounds__(256) k_peel(RunView v, int nsplit, cudaGraphCo
             const int wd = j0 / 32 + warp;
             v.front[(k & 1) * v.NW + wd] = word;
             v.rem[wd] &= ~word;
-            if (word) atomicAdd(&c->front_size, (unsigned)__popc(word));
+            if (word) {
+                atomicAdd(&c->front_size, (unsigned)__popc(word));
+                atomicAdd(&c->front_words, 1u);
+            }
         }
     }
     if (tid == 0) v.chunk_done[chunk] = 0;
@@ -157,11 +166,15 @@ __global__ void __launch_bounds__(256) k_peel(RunView v, int nsplit, cudaGraphCo
     }
     if (fs == 0 && cum < v.n2) set_status(c, DEV_EINTERNAL);
     const bool more = fs > 0 && cum < v.n2 && (v.full_sort || c->l < 0);
+    const unsigned fw = atomicAdd(&c->front_words, 0u);
+    if (more) c->peel_rows += fw;  // rows the next pass reads
+    c->front_words = 0u;
     c->front_size = 0;
     c->chunks_done = 0;
     c->k = k + 1;
+    c->peel_more = more ? 1 : 0;
     __threadfence();
-    cudaGraphSetConditional(h, more ? 1u : 0u);
+    if (in_graph) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 __global__ void k_post_peel(RunView v, cudaGraphConditionalHandle h_niche)
@@ -184,10 +197,11 @@ int peel_nsplit(const RunView& v, int num_sms)
     return ns;
 }
 
-cudaError_t launch_peel(const RunView& v, int nsplit, cudaGraphConditionalHandle h, cudaStream_t s)
+cudaError_t launch_peel(const RunView& v, int nsplit, cudaGraphConditionalHandle h, int in_graph,
+                        cudaStream_t s)
 {
     const int nchunks = v.ld / NSGA3_PEEL_COLS;
-    k_peel<<<nchunks * nsplit, 256, 0, s>>>(v, nsplit, h);
+    k_peel<<<nchunks * nsplit, 256, 0, s>>>(v, nsplit, h, in_graph);
     return cudaGetLastError();
 }
 

@@ -48,10 +48,10 @@ class Run:
         return st, rank, sel
 
     def info(self):
-        a = np.zeros(12, np.int32)
+        a = np.zeros(13, np.int32)
         self.check(self.n.nsga3_get_selection_info(self.ctx, a.ctypes.data))
         keys = ["l", "nS", "K", "nFl", "niche", "fallback", "passes", "nT", "Lstar", "rlev",
-                "overflow", "recheck_miss"]
+                "overflow", "recheck_miss", "peel_rows"]
         return dict(zip(keys, (int(x) for x in a)))
 
     def normalization(self):
