@@ -4,7 +4,9 @@
 // to a multiple of 256, NW = ld / 32 bit-mask words):
 //   X     n2 x d  FP32 row-major   parents rows [0,N), children rows [N,2N)
 //   F     ld x m  FP32 row-major   rows >= n2 are NaN padding (never dominate)
-//   Dom   NW x ld u32              bit (i mod 32) of Dom[i/32][j] = "i dominates j"
+//   Fp    ld x m  FP32             F in bucket order of f_0 (perm: position -> index)
+//   Dom   NW x ld u32              bit (i mod 32) of Dom[i/32][j] = "i dominates j",
+//                                  i, j positions in bucket order
 //   rank2 ld int32                 front index of the merged population, -1 = F_drop
 //   pi/dist ld                     association (reference index, FP64 distance)
 //   Zd    w x m   FP64             Das-Dennis directions; Zh w x M4 FP32 unit copy
@@ -16,6 +18,7 @@
 #define NSGA3_MAX_M 10
 #define NSGA3_TILE 256          // column tile of the dominance build; ld % 256 == 0
 #define NSGA3_PEEL_COLS 128     // columns per peel chunk (4 per lane, 32 lanes)
+#define SORT_NB 4096            // f_0 buckets of the bucket order
 
 // device status codes (same values as the C ABI's nsga3_status)
 #define DEV_OK 0
@@ -61,6 +64,10 @@ struct Ctrl {
     int32_t peel_more;       // eager mode: 1 if another peel pass is needed
     int32_t ncand;           // association candidates written by the scan
     int32_t nslow;           // points sent to the full FP64 association scan
+    uint32_t ext_done;       // completion ticket of the extreme-point blocks
+    uint32_t sort_done;      // completion ticket of the bucket histogram
+    uint32_t f0lo, f0hi;     // range of f_0 as order-preserving uint
+    uint32_t cmp_done;       // completion ticket of the compaction blocks
     uint32_t zmin[NSGA3_MAX_M];  // ideal point as order-preserving uint of FP32
     double zstar[NSGA3_MAX_M];   // ideal point (FP64, +0.0 for zero)
     double a[NSGA3_MAX_M];       // intercepts
@@ -83,10 +90,15 @@ struct RunView {
     int32_t* ranktmp;  // N
     uint32_t* Dom;     // NW x ld
     int32_t* cnt;      // ld   remaining dominator counts
-    int32_t* rank2;    // ld   merged ranks
+    int32_t* rank2;    // ld   merged ranks (original order)
+    int32_t* srank;    // ld   merged ranks in bucket order (peel)
+    int32_t* perm;     // ld   bucket order position -> original index
+    uint32_t* skey;    // ld   bucket of each position (0xffffffff for padding)
+    float* Fp;         // ld x m objectives in bucket order, -0.0 as +0.0, NaN padding
+    int32_t* bcnt;     // SORT_NB bucket counts, then offsets / cursors
     uint32_t* rem;     // NW   not-yet-ranked mask
     uint32_t* front;   // 2 x NW  ping-pong front masks
-    uint32_t* chunk_done;  // ld / NSGA3_PEEL_COLS tickets
+    uint32_t* chunk_lim;   // ld / NSGA3_PEEL_COLS dominator row blocks a column chunk reads
     uint32_t* selmask;     // NW picked members of F_l
     int32_t* Tlist;        // n2 members of S u F_l
     double* fprime;        // n2 x m  normalised objectives (indexed by T slot)

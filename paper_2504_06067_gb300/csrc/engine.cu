@@ -150,6 +150,7 @@ nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, 
 {
     CK(launch_sel_reset(v, s));
     if (check_finite) CK(launch_check_finite(v, s));
+    CK(launch_sort(v, ctx->num_sms, s));
     nsga3_status st = record_event(ctx, s, EV_RESET, events);
     if (st) return st;
     CK(launch_dominance(v, s));
@@ -176,7 +177,7 @@ nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, 
         CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
         CK(cudaGraphConditionalHandleCreate(&h_niche, g, 0u, cudaGraphCondAssignDefault));
     }
-    CK(launch_post_peel(v, h_niche, s));
+    CK(launch_post_peel(v, h_niche, 1, s));
     {
         cudaStreamCaptureStatus cs;
         cudaGraph_t g = nullptr;
@@ -197,7 +198,6 @@ nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, 
         cudaError_t e = cudaSuccess;
         if (e == cudaSuccess) e = launch_norm_ideal(v, s2);
         if (e == cudaSuccess) e = launch_norm_extreme(v, s2);
-        if (e == cudaSuccess) e = launch_norm_solve(v, s2);
         if (e == cudaSuccess) e = launch_assoc_prep(v, s2);
         if (e == cudaSuccess) e = launch_assoc_scan(v, ctx->num_sms, s2);
         if (e == cudaSuccess) e = launch_level(v, s2);
@@ -235,6 +235,7 @@ nsga3_status eager_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, b
 {
     CK(launch_sel_reset(v, s));
     if (check_finite) CK(launch_check_finite(v, s));
+    CK(launch_sort(v, ctx->num_sms, s));
     nsga3_status st = record_event(ctx, s, EV_RESET, true);
     if (st) return st;
     CK(launch_dominance(v, s));
@@ -248,6 +249,7 @@ nsga3_status eager_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, b
     }
     st = record_event(ctx, s, EV_PEEL, true);
     if (st) return st;
+    CK(launch_post_peel(v, 0, 0, s));
     int32_t hdr[2] = {0, 0};  // status, need_niche
     CK(cudaMemcpyAsync(&hdr[0], &v.ctrl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&hdr[1], &v.ctrl->need_niche, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -255,7 +257,6 @@ nsga3_status eager_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, b
     if (hdr[0] == 0 && hdr[1]) {
         CK(launch_norm_ideal(v, s));
         CK(launch_norm_extreme(v, s));
-        CK(launch_norm_solve(v, s));
         CK(launch_assoc_prep(v, s));
         CK(launch_assoc_scan(v, ctx->num_sms, s));
         CK(launch_level(v, s));
@@ -420,8 +421,8 @@ nsga3_status setup(nsga3_ctx* ctx)
     v.eta_m = ctx->opts.eta_m;
     v.p_c = ctx->opts.p_c;
     v.p_m = ctx->opts.p_m < 0.0f ? 1.0f / (float)d : ctx->opts.p_m;
-    v.ext_parts = (n2 + 255) / 256;
-    if (v.ext_parts > 256) v.ext_parts = 256;
+    v.ext_parts = (n2 + 63) / 64;
+    if (v.ext_parts > 4 * ctx->num_sms) v.ext_parts = 4 * ctx->num_sms;
 
     AL(v.ctrl, 1);
     AL(v.X, (size_t)n2 * d);
@@ -433,9 +434,14 @@ nsga3_status setup(nsga3_ctx* ctx)
     AL(v.Dom, (size_t)NW * ld);
     AL(v.cnt, ld);
     AL(v.rank2, ld);
+    AL(v.srank, ld);
+    AL(v.perm, ld);
+    AL(v.skey, ld);
+    AL(v.Fp, (size_t)ld * m);
+    AL(v.bcnt, SORT_NB + 1);
     AL(v.rem, NW);
     AL(v.front, 2 * NW);
-    AL(v.chunk_done, ld / NSGA3_PEEL_COLS);
+    AL(v.chunk_lim, ld / NSGA3_PEEL_COLS);
     AL(v.selmask, NW);
     AL(v.Tlist, n2);
     AL(v.fprime, (size_t)n2 * m);
@@ -928,11 +934,11 @@ nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches)
     Ctrl c;
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(&c, ctx->v.ctrl, sizeof c, cudaMemcpyDeviceToHost));
-    // reset, dominance, post-peel, compaction (+ finite check for a selection;
-    // + variation, gather, counter for a generation), one per peel pass, and
-    // 12 niching launches when the IF branch ran
-    int fixed = (ctx->last_kind == 1) ? 5 : 7;
-    *launches = fixed + c.passes + (c.need_niche ? 12 : 0);
+    // reset, 3 sort, dominance, post-peel, compaction (+ finite check for a
+    // selection; + variation, objective, gather, counter for a generation),
+    // one per peel pass, and 11 niching launches when the IF branch ran
+    int fixed = (ctx->last_kind == 1) ? 8 : 11;
+    *launches = fixed + c.passes + (c.need_niche ? 11 : 0);
     return NSGA3_OK;
 }
 

@@ -129,14 +129,11 @@ __global__ void __launch_bounds__(AB) k_assoc_scan(RunView v)
                 bb = b;
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, bmax, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bb, o);
-            if (ob > bmax || (ob == bmax && oi < bb)) {
-                bmax = ob;
-                bb = oi;
-            }
+        // bounds are >= 0 (u, c_b, cos r >= 0): their bits order like unsigned ints
+        {
+            const unsigned mx = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(bmax, 0.0f)));
+            const unsigned cand = (__float_as_uint(fmaxf(bmax, 0.0f)) == mx) ? (unsigned)bb : 0xffffffffu;
+            bb = (int)__reduce_min_sync(0xffffffffu, cand);
         }
         __syncwarp();
         // phase 2: scan the best-bounded block, then every block the bound cannot exclude
@@ -163,9 +160,8 @@ __global__ void __launch_bounds__(AB) k_assoc_scan(RunView v)
                 for (int q = 0; q < M; ++q) qh = fmaf(u[q], zz[q], qh);
                 j = v.blk_j[pos];
             }
-            float wm = qh;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+            // cosines are >= 0, so the float bits order like unsigned ints
+            const float wm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(qh, 0.0f))));
             best = fmaxf(best, wm);
             const bool keep = j >= 0 && qh >= best - band;
             unsigned bal = __ballot_sync(0xffffffffu, keep);
@@ -368,7 +364,7 @@ cudaError_t launch_m(const RunView& v, cudaStream_t s, int num_sms)
 {
     const size_t sm = scan_smem(v);
     int blocks = (v.n2 + 7) / 8;
-    if (blocks > num_sms * 4) blocks = num_sms * 4;
+    if (blocks > num_sms * 8) blocks = num_sms * 8;
     k_assoc_scan<M><<<blocks, AB, sm, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

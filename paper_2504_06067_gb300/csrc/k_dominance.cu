@@ -9,15 +9,21 @@
 // the upper block triangle; warp w takes row block ib = 8 * ti + w (lane =
 // row i, its m objectives in registers) against each column block jb >= ib
 // of the tile, with the column points broadcast from shared memory.  Per
-// pair two predicate chains give A = all(f_i <= f_j), B = all(f_j <= f_i);
-// "i dom j" = A & !B, "j dom i" = B & !A (identical vectors: neither).
+// pair the m differences f_j - f_i and f_i - f_j run on the FMA pipe and
+// their sign bits are OR-ed (3-input LOP3): A = "no f_i > f_j" and
+// B = "no f_j > f_i"; "i dom j" = A & !B, "j dom i" = B & !A (identical
+// vectors: neither).  -0.0 is turned into +0.0 when the tile is staged.
+// Points are in bucket order of f_0 (k_sort.cu); when the row block's
+// largest f_0 is below the column block's smallest, only "i dom j" is
+// possible, strictness is implied by f_i0 < f_j0, and the test needs the
+// m - 1 differences of objectives 1..m-1 only.
 // "j dom i" bits gathered over j are already column words Dom[jb][i];
 // "i dom j" bits gathered over j are row words and are transposed in-warp
 // (32 x 32 bit transpose by five shuffle stages) into Dom[ib][j].
-// Padding rows/columns hold NaN: every compare with NaN is false, so they
-// neither dominate nor are dominated.
+// Padding rows/columns hold NaN: both differences of a pair with a padding
+// point are the same NaN, so neither direction gets a bit.
 //
-// Bound: issue of FP32 compares (2m per unordered pair) -- ALU, not HBM.
+// Bound: the ALU pipe (sign-bit logic) and instruction issue -- not HBM.
 #include "kernels.cuh"
 
 namespace {
@@ -42,9 +48,10 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x)
 
 __device__ __forceinline__ void decode_tile(long long t, int T, int& ti, int& tj)
 {
-    // tiles (ti <= tj) enumerated row by row: row ti starts at ti*T - ti*(ti-1)/2
-    double b = 2.0 * T + 1.0;
-    int r = (int)floor((b - sqrt(b * b - 8.0 * (double)t)) * 0.5);
+    // tiles (ti <= tj) enumerated row by row: row ti starts at ti*T - ti*(ti-1)/2;
+    // FP32 estimate of the row, corrected exactly by the integer loops below
+    float b = 2.0f * (float)T + 1.0f;
+    int r = (int)floorf((b - sqrtf(fmaxf(0.0f, b * b - 8.0f * (float)t))) * 0.5f);
     if (r < 0) r = 0;
     if (r > T - 1) r = T - 1;
     auto start = [&](long long x) { return x * T - x * (x - 1) / 2; };
@@ -61,14 +68,17 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
     __shared__ __align__(16) float srow[NSGA3_TILE * M4];
     __shared__ __align__(16) float scol[NSGA3_TILE * M4];
     if (read_status(v.ctrl)) return;
+    __shared__ int s_tile[2];
     const int T = v.ld / NSGA3_TILE;
-    int ti, tj;
-    decode_tile(blockIdx.x, T, ti, tj);
+    if (threadIdx.x == 0) decode_tile(blockIdx.x, T, s_tile[0], s_tile[1]);
+    __syncthreads();
+    const int ti = s_tile[0], tj = s_tile[1];
     const int r0 = ti * NSGA3_TILE, c0 = tj * NSGA3_TILE;
+    // Fp holds -0.0 as +0.0, so equal values subtract to +0.0
     for (int e = threadIdx.x; e < NSGA3_TILE * M; e += blockDim.x) {
         int p = e / M, q = e - p * M;
-        srow[p * M4 + q] = v.F[(size_t)r0 * M + e];
-        scol[p * M4 + q] = v.F[(size_t)c0 * M + e];
+        srow[p * M4 + q] = v.Fp[(size_t)r0 * M + e];
+        scol[p * M4 + q] = v.Fp[(size_t)c0 * M + e];
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -82,18 +92,53 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
         if (jb < ib) continue;  // lower block triangle: done by the transposed tile
         uint32_t dij = 0, dji = 0;
         const float* colp = scol + cb * 32 * M4;
+        // every row's f_0 below every column's f_0: only "row dom column" can
+        // hold, f_i0 < f_j0 makes it strict, and it needs objectives 1..m-1
+        float rmax = fi[0], cmin = colp[lane * M4];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+            cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+        }
+        if (jb != ib && rmax < cmin) {
+            uint32_t acc = 0u;
 #pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-            const float* fj = colp + k * M4;
-            bool A = true, B = true;
+            for (int k = 31; k >= 0; --k) {
+                const float* fj = colp + k * M4;
+                uint32_t oa = 0u;
+#pragma unroll
+                for (int q = 1; q < M; ++q) oa |= __float_as_uint(fj[q] - fi[q]);
+                acc = __funnelshift_l(oa, acc, 1);  // sign set: some f_iq > f_jq
+            }
+            uint32_t* D = v.Dom;
+            D[(size_t)jb * v.ld + ib * 32 + lane] = 0u;
+            D[(size_t)ib * v.ld + jb * 32 + lane] = warp_transpose32(~acc);
+            continue;
+        }
+        // columns k = 31 .. 0: the funnel shift leaves column k's bit at position k
+#pragma unroll 8
+        for (int k = 31; k >= 0; --k) {
+            const float4* fj4 = reinterpret_cast<const float4*>(colp + k * M4);
+            float fj[M4];
+#pragma unroll
+            for (int q4 = 0; q4 < M4 / 4; ++q4) {
+                const float4 t = fj4[q4];
+                fj[4 * q4 + 0] = t.x;
+                fj[4 * q4 + 1] = t.y;
+                fj[4 * q4 + 2] = t.z;
+                fj[4 * q4 + 3] = t.w;
+            }
+            // sign(f_j - f_i) per objective: 0 if f_i <= f_j, 1 if f_i > f_j
+            // (exact FP32 subtraction of finite values; NaN padding gives +NaN)
+            uint32_t oa = 0u, ob = 0u;
 #pragma unroll
             for (int q = 0; q < M; ++q) {
-                float x = fj[q];
-                A = A && (fi[q] <= x);
-                B = B && (x <= fi[q]);
+                oa |= __float_as_uint(fj[q] - fi[q]);
+                ob |= __float_as_uint(fi[q] - fj[q]);
             }
-            if (A && !B) dij |= 1u << k;
-            if (B && !A) dji |= 1u << k;
+            // i dom j: no f_i > f_j and some f_i < f_j; j dom i symmetric
+            dij = __funnelshift_l(ob & ~oa, dij, 1);
+            dji = __funnelshift_l(oa & ~ob, dji, 1);
         }
         uint32_t* D = v.Dom;
         // column i = ib*32 + lane, dominators j in block jb

@@ -5,14 +5,16 @@
 
 namespace {
 
-__global__ void k_sel_reset(RunView v, int nchunks)
+__global__ void k_sel_reset(RunView v)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     for (int j = tid; j < v.ld; j += stride) {
         v.cnt[j] = 0;
         v.rank2[j] = -1;
+        v.srank[j] = -1;
     }
+    for (int b = tid; b < SORT_NB; b += stride) v.bcnt[b] = 0;
     for (int wd = tid; wd < v.NW; wd += stride) {
         const int lo = wd * 32;
         uint32_t m = 0u;
@@ -23,7 +25,6 @@ __global__ void k_sel_reset(RunView v, int nchunks)
         v.rem[wd] = m;
         v.selmask[wd] = 0u;
     }
-    for (int t = tid; t < nchunks; t += stride) v.chunk_done[t] = 0u;
     const uint32_t gen = v.ctrl->gen;
     for (int j = tid; j < v.w; j += stride) {
         v.rho[j] = 0;
@@ -48,9 +49,14 @@ __global__ void k_sel_reset(RunView v, int nchunks)
         c->rlev = 0;
         c->nsel = 0;
         c->nlarge = 0;
-        c->peel_rows = (uint32_t)v.NW;  // pass 0 reads every row
+        c->peel_rows = 0u;
         c->ncand = 0;
         c->nslow = 0;
+        c->ext_done = 0u;
+        c->sort_done = 0u;
+        c->f0lo = 0xffffffffu;
+        c->f0hi = 0u;
+        c->cmp_done = 0u;
         c->front_words = 0u;
         c->overflow = 0;
         c->recheck_miss = 0;
@@ -69,28 +75,36 @@ __global__ void k_check_finite(RunView v)
 }
 
 // selected = S u (picked members of F_l), or S u F_l when no niching is
-// needed; written in ascending index order by one CTA (popc scan over words)
+// needed, in ascending index order.  Every warp builds one 32-member mask
+// word (ballot); the last CTA to finish scans the words' popcounts and
+// writes the indices.
 __global__ void __launch_bounds__(1024) k_compact(RunView v)
 {
     uint32_t* words = v.front;  // front masks are dead after the peel: NW words of scratch
     __shared__ int scratch[40];
+    __shared__ unsigned ticket;
     Ctrl* c = v.ctrl;
     if (read_status(c)) return;
     const int l = c->l, need = c->need_niche;
     const int lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int wd = warp; wd < v.NW; wd += nwarps) {
+    const int wd = blockIdx.x * nwarps + warp;
+    if (wd < v.NW) {
         const int j = wd * 32 + lane;
         const int r = j < v.n2 ? v.rank2[j] : -1;
         const bool take = r >= 0 && (r < l || (r == l && (!need || ((v.selmask[wd] >> lane) & 1u))));
         const uint32_t word = __ballot_sync(0xffffffffu, take);
         if (lane == 0) words[wd] = word;
     }
+    __threadfence();
     __syncthreads();
+    if (threadIdx.x == 0) ticket = atomicAdd(&c->cmp_done, 1u);
+    __syncthreads();
+    if (ticket != gridDim.x - 1) return;
+    __threadfence();
     const int per = (v.NW + (int)blockDim.x - 1) / (int)blockDim.x;
     const int lo = min(v.NW, (int)threadIdx.x * per), hi = min(v.NW, lo + per);
     int s = 0;
-    for (int wd = lo; wd < hi; ++wd) s += __popc(words[wd]);
-    // block exclusive scan of s
+    for (int t = lo; t < hi; ++t) s += __popc(__ldcg(&words[t]));
     int inc = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -111,16 +125,17 @@ __global__ void __launch_bounds__(1024) k_compact(RunView v)
     }
     __syncthreads();
     int run = scratch[warp] + inc - s;
-    for (int wd = lo; wd < hi; ++wd) {
-        uint32_t word = words[wd];
+    for (int t = lo; t < hi; ++t) {
+        uint32_t word = __ldcg(&words[t]);
         while (word) {
             const int b = __ffs(word) - 1;
             word &= word - 1;
-            if (run < v.N) v.sel[run] = wd * 32 + b;
+            if (run < v.N) v.sel[run] = t * 32 + b;
             ++run;
         }
     }
     if (threadIdx.x == 0) {
+        c->cmp_done = 0u;
         c->nsel = scratch[32];
         if (scratch[32] != v.N) set_status(c, DEV_EINTERNAL);
     }
@@ -150,8 +165,12 @@ __global__ void k_nan_pad(RunView v)
 {
     const long long lo = (long long)v.n2 * v.m, hi = (long long)v.ld * v.m;
     for (long long e = lo + blockIdx.x * (long long)blockDim.x + threadIdx.x; e < hi;
-         e += (long long)gridDim.x * blockDim.x)
+         e += (long long)gridDim.x * blockDim.x) {
         v.F[e] = __int_as_float(0x7fc00000);
+        v.Fp[e] = __int_as_float(0x7fc00000);
+    }
+    for (int p = v.n2 + blockIdx.x * blockDim.x + threadIdx.x; p < v.ld; p += gridDim.x * blockDim.x)
+        v.skey[p] = 0xffffffffu;
 }
 
 }  // namespace
@@ -161,7 +180,7 @@ cudaError_t launch_sel_reset(const RunView& v, cudaStream_t s)
     int n = v.ld > v.w ? v.ld : v.w;
     int blocks = (n + 255) / 256;
     if (blocks > 2048) blocks = 2048;
-    k_sel_reset<<<blocks, 256, 0, s>>>(v, v.ld / NSGA3_PEEL_COLS);
+    k_sel_reset<<<blocks, 256, 0, s>>>(v);
     return cudaGetLastError();
 }
 
@@ -176,7 +195,7 @@ cudaError_t launch_check_finite(const RunView& v, cudaStream_t s)
 
 cudaError_t launch_compact(const RunView& v, cudaStream_t s)
 {
-    k_compact<<<1, 1024, 0, s>>>(v);
+    k_compact<<<(v.NW + 31) / 32, 1024, 0, s>>>(v);
     return cudaGetLastError();
 }
 

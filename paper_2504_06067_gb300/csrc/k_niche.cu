@@ -23,6 +23,8 @@ namespace {
 constexpr int LB = 1024;    // threads of the single-CTA kernels
 constexpr int LCAP = 4096;  // niche levels resolved by the shared histogram
 constexpr int EXACT = 1024; // candidates ranked pairwise in the last select phase
+constexpr int CKCAP = 4096; // level-L* reference keys staged in shared memory
+constexpr int RRCAP = 12288; // references whose (rho, rho') are staged in shared memory
 
 __device__ __forceinline__ uint32_t mem_prio(uint64_t seed, uint32_t gen, int i)
 {
@@ -189,7 +191,10 @@ struct LevelShared {
     int scratch[40];
     int Lstar;
     int maxhi;
+    int nck;
     SelShared sel;
+    unsigned long long ck[CKCAP];
+    int2 rr[RRCAP];        // (rho_j, rho'_j)
 };
 
 __global__ void __launch_bounds__(LB) k_level(RunView v)
@@ -199,6 +204,11 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
     Ctrl* c = v.ctrl;
     if (read_status(c)) return;
     const int w = v.w, K = c->K;
+    const bool staged = w <= RRCAP;
+    if (staged)
+        for (int j = threadIdx.x; j < w; j += LB) sh.rr[j] = make_int2(v.rho[j], v.rhop[j]);
+    auto rho_of = [&](int j) { return staged ? sh.rr[j].x : v.rho[j]; };
+    auto rhop_of = [&](int j) { return staged ? sh.rr[j].y : v.rhop[j]; };
     for (int t = threadIdx.x; t <= LCAP; t += LB) sh.lev[t] = 0;
     if (threadIdx.x == 0) {
         sh.Lstar = LCAP;
@@ -207,9 +217,9 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
     __syncthreads();
     int mymax = 0;
     for (int j = threadIdx.x; j < w; j += LB) {
-        const int rp = v.rhop[j];
+        const int rp = rhop_of(j);
         if (rp > 0) {
-            const int lo = v.rho[j], hi = lo + rp;
+            const int lo = rho_of(j), hi = lo + rp;
             if (lo < LCAP) atomicAdd(&sh.lev[lo], 1);
             if (hi < LCAP) atomicAdd(&sh.lev[hi], -1);
             mymax = max(mymax, hi);
@@ -255,8 +265,8 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
         auto count_le = [&](int L) {
             int s = 0;
             for (int j = threadIdx.x; j < w; j += LB) {
-                const int rp = v.rhop[j];
-                if (rp > 0) s += min(rp, max(0, L + 1 - v.rho[j]));
+                const int rp = rhop_of(j);
+                if (rp > 0) s += min(rp, max(0, L + 1 - rho_of(j)));
             }
             return block_sum(s, sh.scratch);
         };
@@ -272,21 +282,52 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
         before = count_le(Lstar - 1);
     }
     const int r = K - before;
+    if (threadIdx.x == 0) sh.nck = 0;
+    __syncthreads();
     for (int j = threadIdx.x; j < w; j += LB) {
-        const int rp = v.rhop[j];
-        v.take[j] = rp > 0 ? min(rp, max(0, Lstar - v.rho[j])) : 0;
+        const int rp = rhop_of(j);
+        const int lo = rho_of(j);
+        v.take[j] = rp > 0 ? min(rp, max(0, Lstar - lo)) : 0;
+        if (rp > 0 && lo <= Lstar && Lstar < lo + rp) {
+            const int p = atomicAdd(&sh.nck, 1);
+            if (p < CKCAP) sh.ck[p] = ((unsigned long long)v.refprio[j] << 32) | (unsigned)j;
+        }
     }
     __syncthreads();
-    auto pred = [&](int j) {
-        const int rp = v.rhop[j];
-        const int lo = v.rho[j];
-        return rp > 0 && lo <= Lstar && Lstar < lo + rp;
-    };
-    auto key = [&](int j) { return ((unsigned long long)v.refprio[j] << 32) | (unsigned)j; };
-    auto mark = [&](int j) { v.take[j] += 1; };
-    block_select_smallest(w, r, key, pred, mark, sh.sel);
+    const int nC = sh.nck;
+    if (nC <= CKCAP) {
+        // the level-L* references are staged in shared memory
+        auto key = [&](int e) { return sh.ck[e]; };
+        auto pred = [&](int) { return true; };
+        auto mark = [&](int e) { v.take[(int)(sh.ck[e] & 0xffffffffull)] += 1; };
+        block_select_smallest(nC, r, key, pred, mark, sh.sel);
+    } else {
+        auto pred = [&](int j) {
+            const int rp = rhop_of(j);
+            const int lo = rho_of(j);
+            return rp > 0 && lo <= Lstar && Lstar < lo + rp;
+        };
+        auto key = [&](int j) { return ((unsigned long long)v.refprio[j] << 32) | (unsigned)j; };
+        auto mark = [&](int j) { v.take[j] += 1; };
+        block_select_smallest(w, r, key, pred, mark, sh.sel);
+    }
     __syncthreads();
-    block_scan_array(v.rhop, v.ref_off, w, sh.scratch);
+    if (staged) {
+        // exclusive scan of rho' over contiguous runs held in shared memory
+        const int per = (w + LB - 1) / LB;
+        const int lo = min(w, (int)threadIdx.x * per), hi = min(w, lo + per);
+        int sum = 0;
+        for (int j = lo; j < hi; ++j) sum += sh.rr[j].y;
+        int total;
+        int run = block_excl_scan(sum, sh.scratch, &total);
+        for (int j = lo; j < hi; ++j) {
+            v.ref_off[j] = run;
+            run += sh.rr[j].y;
+        }
+        if (threadIdx.x == 0) v.ref_off[w] = total;
+    } else {
+        block_scan_array(v.rhop, v.ref_off, w, sh.scratch);
+    }
     for (int j = threadIdx.x; j < w; j += LB) v.cursor[j] = 0;
     if (threadIdx.x == 0) {
         c->Lstar = Lstar;

@@ -15,7 +15,8 @@
 
 namespace {
 
-constexpr int NB = 256;
+constexpr int NB = 256;   // k_norm_ideal
+constexpr int EB = 64;    // k_norm_extreme: small blocks spread the FP64 latency over the SMs
 
 // members of T are appended to Tlist; ideal point by order-preserving atomicMin
 __global__ void __launch_bounds__(NB) k_norm_ideal(RunView v)
@@ -49,125 +50,34 @@ __device__ __forceinline__ double zstar_of(const Ctrl* c, int q)
     return __dadd_rn((double)ord2f(c->zmin[q]), 0.0);
 }
 
-// per-block (min ASF, lowest index) per axis and per-block max of f~
-__global__ void __launch_bounds__(NB) k_norm_extreme(RunView v)
+// Non-negative doubles order like their bit patterns; -0.0 is mapped to
+// +0.0 so that the two zeros compare equal, as IEEE comparisons do.
+__device__ __forceinline__ unsigned long long okey(double x)
 {
-    __shared__ double s_asf[NB / 32][NSGA3_MAX_M];
-    __shared__ int s_idx[NB / 32][NSGA3_MAX_M];
-    __shared__ double s_nad[NB / 32][NSGA3_MAX_M];
-    Ctrl* c = v.ctrl;
-    if (read_status(c)) return;
-    const int m = v.m, nT = c->nT;
-    const int lane = lane_id(), warp = threadIdx.x >> 5;
-    double zs[NSGA3_MAX_M];
-    for (int q = 0; q < m; ++q) zs[q] = zstar_of(c, q);
-    double best[NSGA3_MAX_M], nad[NSGA3_MAX_M];
-    int bidx[NSGA3_MAX_M];
-    for (int q = 0; q < m; ++q) {
-        best[q] = CUDART_INF;
-        bidx[q] = 0x7fffffff;
-        nad[q] = 0.0;
-    }
-    for (int s = blockIdx.x * NB + threadIdx.x; s < nT; s += gridDim.x * NB) {
-        const int i = v.Tlist[s];
-        double ft[NSGA3_MAX_M];
-        double mx1 = -CUDART_INF, mx2 = -CUDART_INF;
-        int r1 = -1;
-        for (int r = 0; r < m; ++r) {
-            ft[r] = __dsub_rn((double)v.F[(size_t)i * m + r], zs[r]);
-            if (ft[r] > mx1) {
-                mx2 = mx1;
-                mx1 = ft[r];
-                r1 = r;
-            } else if (ft[r] > mx2) {
-                mx2 = ft[r];
-            }
-            nad[r] = fmax(nad[r], ft[r]);
-        }
-        const double d1 = __ddiv_rn(mx1, 1e-6), d2 = __ddiv_rn(mx2, 1e-6);
-        for (int q = 0; q < m; ++q) {
-            double other = (q == r1) ? d2 : d1;
-            double asf = ft[q] > other ? ft[q] : other;
-            if (lex_less(asf, i, best[q], bidx[q])) {
-                best[q] = asf;
-                bidx[q] = i;
-            }
-        }
-    }
-    for (int q = 0; q < m; ++q) {
-        double b = best[q], n = nad[q];
-        int bi = bidx[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            double ob = __shfl_xor_sync(0xffffffffu, b, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            double on = __shfl_xor_sync(0xffffffffu, n, o);
-            if (lex_less(ob, oi, b, bi)) {
-                b = ob;
-                bi = oi;
-            }
-            n = fmax(n, on);
-        }
-        if (lane == 0) {
-            s_asf[warp][q] = b;
-            s_idx[warp][q] = bi;
-            s_nad[warp][q] = n;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < m) {
-        const int q = threadIdx.x;
-        double b = s_asf[0][q], n = s_nad[0][q];
-        int bi = s_idx[0][q];
-        for (int w = 1; w < NB / 32; ++w) {
-            if (lex_less(s_asf[w][q], s_idx[w][q], b, bi)) {
-                b = s_asf[w][q];
-                bi = s_idx[w][q];
-            }
-            n = fmax(n, s_nad[w][q]);
-        }
-        v.ext_part[blockIdx.x * m + q] = b;
-        v.ext_idx[blockIdx.x * m + q] = bi;
-        v.nad_part[blockIdx.x * m + q] = n;
-    }
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b << 1) == 0ull ? 0ull : b;  // integer test for +-0 (FP64 compares are slow)
 }
 
-// final reduction + Gaussian elimination (one thread does the m x m solve)
-__global__ void __launch_bounds__(32) k_norm_solve(RunView v)
+__device__ __forceinline__ bool key_less(unsigned long long a, int ia, unsigned long long b, int ib)
 {
-    Ctrl* c = v.ctrl;
-    if (read_status(c)) return;
+    return a < b || (a == b && ia < ib);
+}
+
+// Gaussian elimination with partial pivoting (first maximal |pivot|) on
+// E b = 1, a = 1 / b, nadir fallback; one thread, _rn intrinsics.
+__device__ void solve_intercepts(const RunView& v, Ctrl* c, const int* ext, const double* nad)
+{
     const int m = v.m;
-    __shared__ int s_ext[NSGA3_MAX_M];
-    __shared__ double s_nad[NSGA3_MAX_M];
-    if (threadIdx.x < m) {
-        const int q = threadIdx.x;
-        double b = CUDART_INF, n = 0.0;
-        int bi = 0x7fffffff;
-        for (int p = 0; p < v.ext_parts; ++p) {
-            double pb = v.ext_part[p * m + q];
-            int pi = v.ext_idx[p * m + q];
-            if (lex_less(pb, pi, b, bi)) {
-                b = pb;
-                bi = pi;
-            }
-            n = fmax(n, v.nad_part[p * m + q]);
-        }
-        s_ext[q] = bi;
-        s_nad[q] = n;
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
     double zs[NSGA3_MAX_M];
     for (int q = 0; q < m; ++q) {
         zs[q] = zstar_of(c, q);
         c->zstar[q] = zs[q];
-        c->ext[q] = s_ext[q];
+        c->ext[q] = ext[q];
     }
     double A[NSGA3_MAX_M][NSGA3_MAX_M], rhs[NSGA3_MAX_M], b[NSGA3_MAX_M];
     bool ok = true;
     for (int q = 0; q < m; ++q) {
-        const int e = s_ext[q];
+        const int e = ext[q];
         if (e < 0 || e >= v.n2) ok = false;
         for (int r = 0; r < m; ++r)
             A[q][r] = ok ? __dsub_rn((double)v.F[(size_t)e * m + r], zs[r]) : 0.0;
@@ -215,8 +125,141 @@ __global__ void __launch_bounds__(32) k_norm_solve(RunView v)
     }
     c->fallback = ok ? 0 : 1;
     for (int q = 0; q < m; ++q) {
-        if (!ok) a[q] = (s_nad[q] == 0.0) ? 1.0 : s_nad[q];
+        if (!ok) a[q] = (nad[q] == 0.0) ? 1.0 : nad[q];
         c->a[q] = a[q];
+    }
+}
+
+// Per-block (min ASF, lowest index) per axis and max of f~; the last block
+// to finish reduces the blocks' results and solves for the intercepts.
+__global__ void __launch_bounds__(EB) k_norm_extreme(RunView v)
+{
+    __shared__ unsigned long long s_key[EB / 32][NSGA3_MAX_M];
+    __shared__ int s_idx[EB / 32][NSGA3_MAX_M];
+    __shared__ unsigned long long s_nad[EB / 32][NSGA3_MAX_M];
+    __shared__ unsigned s_ticket;
+    __shared__ int f_ext[NSGA3_MAX_M];
+    __shared__ double f_nad[NSGA3_MAX_M];
+    Ctrl* c = v.ctrl;
+    if (read_status(c)) return;
+    const int m = v.m, nT = c->nT;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    double zs[NSGA3_MAX_M];
+    for (int q = 0; q < m; ++q) zs[q] = zstar_of(c, q);
+    unsigned long long best[NSGA3_MAX_M], nad[NSGA3_MAX_M];
+    int bidx[NSGA3_MAX_M];
+    for (int q = 0; q < m; ++q) {
+        best[q] = ~0ull;
+        bidx[q] = 0x7fffffff;
+        nad[q] = 0ull;
+    }
+    for (int s = blockIdx.x * EB + threadIdx.x; s < nT; s += gridDim.x * EB) {
+        const int i = v.Tlist[s];
+        double ft[NSGA3_MAX_M];
+        unsigned long long m1 = 0ull, m2 = 0ull;  // largest and second largest key (f~ >= 0)
+        int r1 = 0;
+        for (int r = 0; r < m; ++r) {
+            ft[r] = __dsub_rn((double)v.F[(size_t)i * m + r], zs[r]);
+            const unsigned long long kr = okey(ft[r]);
+            if (kr > m1) {
+                m2 = m1;
+                m1 = kr;
+                r1 = r;
+            } else if (kr > m2) {
+                m2 = kr;
+            }
+            nad[r] = max(nad[r], kr);
+        }
+        const double d1 = __ddiv_rn(__longlong_as_double((long long)m1), 1e-6);
+        const double d2 = __ddiv_rn(__longlong_as_double((long long)m2), 1e-6);
+        const unsigned long long k1 = okey(d1), k2 = okey(d2);
+        for (int q = 0; q < m; ++q) {
+            const unsigned long long other = (q == r1) ? k2 : k1;
+            const unsigned long long kq = okey(ft[q]);
+            const unsigned long long asf = kq > other ? kq : other;
+            if (key_less(asf, i, best[q], bidx[q])) {
+                best[q] = asf;
+                bidx[q] = i;
+            }
+        }
+    }
+    for (int q = 0; q < m; ++q) {
+        unsigned long long b = best[q], n = nad[q];
+        int bi = bidx[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            const unsigned long long on = __shfl_xor_sync(0xffffffffu, n, o);
+            if (key_less(ob, oi, b, bi)) {
+                b = ob;
+                bi = oi;
+            }
+            n = max(n, on);
+        }
+        if (lane == 0) {
+            s_key[warp][q] = b;
+            s_idx[warp][q] = bi;
+            s_nad[warp][q] = n;
+        }
+    }
+    __syncthreads();
+    unsigned long long* pk = reinterpret_cast<unsigned long long*>(v.ext_part);
+    unsigned long long* pn = reinterpret_cast<unsigned long long*>(v.nad_part);
+    if (threadIdx.x < m) {
+        const int q = threadIdx.x;
+        unsigned long long b = s_key[0][q], n = s_nad[0][q];
+        int bi = s_idx[0][q];
+        for (int w = 1; w < EB / 32; ++w) {
+            if (key_less(s_key[w][q], s_idx[w][q], b, bi)) {
+                b = s_key[w][q];
+                bi = s_idx[w][q];
+            }
+            n = max(n, s_nad[w][q]);
+        }
+        pk[blockIdx.x * m + q] = b;
+        v.ext_idx[blockIdx.x * m + q] = bi;
+        pn[blockIdx.x * m + q] = n;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_ticket = atomicAdd(&c->ext_done, 1u);
+    __syncthreads();
+    if (s_ticket != gridDim.x - 1) return;
+    // last block: reduce over the blocks (warp w reduces axes w, w + 8, ...)
+    __threadfence();
+    for (int q = warp; q < m; q += EB / 32) {
+        unsigned long long b = ~0ull, n = 0ull;
+        int bi = 0x7fffffff;
+        for (int p = lane; p < (int)gridDim.x; p += 32) {
+            const unsigned long long pb = __ldcg(&pk[p * m + q]);
+            const int pi = __ldcg(&v.ext_idx[p * m + q]);
+            if (key_less(pb, pi, b, bi)) {
+                b = pb;
+                bi = pi;
+            }
+            n = max(n, __ldcg(&pn[p * m + q]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            const unsigned long long on = __shfl_xor_sync(0xffffffffu, n, o);
+            if (key_less(ob, oi, b, bi)) {
+                b = ob;
+                bi = oi;
+            }
+            n = max(n, on);
+        }
+        if (lane == 0) {
+            f_ext[q] = bi;
+            f_nad[q] = __longlong_as_double((long long)n);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        c->ext_done = 0u;
+        solve_intercepts(v, c, f_ext, f_nad);
     }
 }
 
@@ -230,12 +273,6 @@ cudaError_t launch_norm_ideal(const RunView& v, cudaStream_t s)
 
 cudaError_t launch_norm_extreme(const RunView& v, cudaStream_t s)
 {
-    k_norm_extreme<<<v.ext_parts, NB, 0, s>>>(v);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_norm_solve(const RunView& v, cudaStream_t s)
-{
-    k_norm_solve<<<1, 32, 0, s>>>(v);
+    k_norm_extreme<<<v.ext_parts, EB, 0, s>>>(v);
     return cudaGetLastError();
 }

@@ -4,27 +4,32 @@
 //
 // One launch per front, replayed by a CUDA-graph WHILE node; the last CTA
 // of a pass sets the node's condition, so the host never synchronises.
+// Positions are in bucket order of f_0 (k_sort.cu); ranks are written back
+// to the original order by k_post_peel.
 //   pass 0:   cnt[j]  = popc over all dominator words of column j
 //   pass k>0: cnt[j] -= popc(Dom[w][j] & front_{k-1}[w]) over the nonzero
 //             words w of the previous front's mask
 //   front_k   = { j unranked : cnt[j] == 0 }, rank2[j] = k
-// A CTA owns 128 columns (uint4 per lane) and one of `nsplit` row ranges;
-// partial counts meet in global atomics, and the last CTA of each column
-// chunk (ticket) ranks its columns, so a front mask word has exactly one
-// writer per pass.  Bound: HBM / L2 bandwidth of the Dom reads.
+// A CTA of 32 warps owns 128 columns (uint4 per lane); its warps split the
+// dominator rows and meet in shared memory, so the CTA alone updates its
+// columns' counts, ranks them and writes their front-mask words.  The last
+// CTA of a pass (ticket) closes the front.  Bound: HBM / L2 bandwidth of the
+// Dom reads.
 #include "kernels.cuh"
 
 namespace {
 
+constexpr int PT = 1024;          // threads per CTA: 32 warps split the dominator rows
+constexpr int PW = PT / 32;
 constexpr int LISTCAP = 2048;
 
-__global__ void __launch_bounds__(256) k_peel(RunView v, int nsplit, cudaGraphConditionalHandle h,
-                                              int in_graph)
+__global__ void __launch_bounds__(PT) k_peel(RunView v, cudaGraphConditionalHandle h, int in_graph)
 {
-    __shared__ int red[8][NSGA3_PEEL_COLS];
+    __shared__ int red[PW][NSGA3_PEEL_COLS];
     __shared__ uint2 list[LISTCAP];
     __shared__ int nlist;
-    __shared__ unsigned ticket;
+    __shared__ uint32_t kmax;
+    __shared__ int slim;
     Ctrl* c = v.ctrl;
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     if (read_status(c)) {
@@ -38,32 +43,57 @@ __global__ void __launch_bounds__(256) k_peel(RunView v, int nsplit, cudaGraphCo
     }
     const int k = *(volatile int32_t*)&c->k;
     const int nchunks = v.ld / NSGA3_PEEL_COLS;
-    const int chunk = blockIdx.x / nsplit, split = blockIdx.x - chunk * nsplit;
+    const int chunk = blockIdx.x;
     const int j0 = chunk * NSGA3_PEEL_COLS;
-    const int w_lo = (int)((long long)split * v.NW / nsplit);
-    const int w_hi = (int)((long long)(split + 1) * v.NW / nsplit);
 
     uint32_t rw = (tid < NSGA3_PEEL_COLS / 32) ? v.rem[j0 / 32 + tid] : 0u;
     const int any_rem = __syncthreads_or(rw != 0u);
+    // Dominators of a column have f_0 <= its f_0: in bucket order, only row
+    // blocks whose first bucket key is <= the chunk's largest key can hold
+    // bits for this chunk (keys are non-decreasing along the order).
+    int lim;
+    if (k == 0) {
+        if (tid == 0) kmax = 0u;
+        __syncthreads();
+        if (tid < NSGA3_PEEL_COLS && j0 + tid < v.n2) atomicMax(&kmax, v.skey[j0 + tid]);
+        __syncthreads();
+        const uint32_t km = kmax;
+        int cntb = 0;
+        for (int I = tid; I < v.NW; I += PT) cntb += (v.skey[I * 32] <= km);
+        cntb = warp_sum(cntb);
+        if (tid == 0) slim = 0;
+        __syncthreads();
+        if (lane == 0 && cntb) atomicAdd(&slim, cntb);
+        __syncthreads();
+        lim = slim;
+        if (tid == 0) {
+            v.chunk_lim[chunk] = (uint32_t)lim;
+            if (any_rem) atomicAdd(&c->peel_rows, (unsigned)lim);
+        }
+    } else {
+        lim = (int)v.chunk_lim[chunk];
+    }
 
     uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     if (any_rem) {
         const uint4* base = reinterpret_cast<const uint4*>(v.Dom + j0) + lane;
         const size_t ld4 = (size_t)v.ld / 4;
         if (k == 0) {
-            int w = w_lo + warp;
-            for (; w + 24 < w_hi; w += 32) {
-                uint4 x0 = __ldg(base + (size_t)w * ld4);
-                uint4 x1 = __ldg(base + (size_t)(w + 8) * ld4);
-                uint4 x2 = __ldg(base + (size_t)(w + 16) * ld4);
-                uint4 x3 = __ldg(base + (size_t)(w + 24) * ld4);
-                a0 += __popc(x0.x) + __popc(x1.x) + __popc(x2.x) + __popc(x3.x);
-                a1 += __popc(x0.y) + __popc(x1.y) + __popc(x2.y) + __popc(x3.y);
-                a2 += __popc(x0.z) + __popc(x1.z) + __popc(x2.z) + __popc(x3.z);
-                a3 += __popc(x0.w) + __popc(x1.w) + __popc(x2.w) + __popc(x3.w);
+            int w = warp;
+            for (; w + 7 * PW < lim; w += 8 * PW) {
+                uint4 x[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) x[t] = __ldg(base + (size_t)(w + PW * t) * ld4);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    a0 += __popc(x[t].x);
+                    a1 += __popc(x[t].y);
+                    a2 += __popc(x[t].z);
+                    a3 += __popc(x[t].w);
+                }
             }
-            for (; w < w_hi; w += 8) {
-                uint4 x = __ldg(base + (size_t)w * ld4);
+            for (; w < lim; w += PW) {
+                const uint4 x = __ldg(base + (size_t)w * ld4);
                 a0 += __popc(x.x);
                 a1 += __popc(x.y);
                 a2 += __popc(x.z);
@@ -71,29 +101,37 @@ __global__ void __launch_bounds__(256) k_peel(RunView v, int nsplit, cudaGraphCo
             }
         } else {
             const uint32_t* prev = v.front + ((k - 1) & 1) * v.NW;
-            for (int wb = w_lo; wb < w_hi; wb += LISTCAP) {
-                const int whe = min(wb + LISTCAP, w_hi);
+            for (int wb = 0; wb < lim; wb += LISTCAP) {
+                const int whe = min(wb + LISTCAP, lim);
                 if (tid == 0) nlist = 0;
                 __syncthreads();
-                for (int w = wb + tid; w < whe; w += blockDim.x) {
-                    uint32_t msk = prev[w];
+                for (int w = wb + tid; w < whe; w += PT) {
+                    const uint32_t msk = prev[w];
                     if (msk) list[atomicAdd(&nlist, 1)] = make_uint2((unsigned)w, msk);
                 }
                 __syncthreads();
                 const int n = nlist;
+                if (tid == 0) atomicAdd(&c->peel_rows, (unsigned)n);
                 int e = warp;
-                for (; e + 8 < n; e += 16) {
-                    uint2 L0 = list[e], L1 = list[e + 8];
-                    uint4 x0 = __ldg(base + (size_t)L0.x * ld4);
-                    uint4 x1 = __ldg(base + (size_t)L1.x * ld4);
-                    a0 += __popc(x0.x & L0.y) + __popc(x1.x & L1.y);
-                    a1 += __popc(x0.y & L0.y) + __popc(x1.y & L1.y);
-                    a2 += __popc(x0.z & L0.y) + __popc(x1.z & L1.y);
-                    a3 += __popc(x0.w & L0.y) + __popc(x1.w & L1.y);
+                for (; e + 3 * PW < n; e += 4 * PW) {
+                    uint2 L[4];
+                    uint4 x[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        L[t] = list[e + PW * t];
+                        x[t] = __ldg(base + (size_t)L[t].x * ld4);
+                    }
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        a0 += __popc(x[t].x & L[t].y);
+                        a1 += __popc(x[t].y & L[t].y);
+                        a2 += __popc(x[t].z & L[t].y);
+                        a3 += __popc(x[t].w & L[t].y);
+                    }
                 }
-                for (; e < n; e += 8) {
-                    uint2 L = list[e];
-                    uint4 x = __ldg(base + (size_t)L.x * ld4);
+                for (; e < n; e += PW) {
+                    const uint2 L = list[e];
+                    const uint4 x = __ldg(base + (size_t)L.x * ld4);
                     a0 += __popc(x.x & L.y);
                     a1 += __popc(x.y & L.y);
                     a2 += __popc(x.z & L.y);
@@ -108,32 +146,22 @@ __global__ void __launch_bounds__(256) k_peel(RunView v, int nsplit, cudaGraphCo
     red[warp][lane * 4 + 2] = (int)a2;
     red[warp][lane * 4 + 3] = (int)a3;
     __syncthreads();
+    // this CTA owns its 128 columns: update the counts and rank the new front
     if (tid < NSGA3_PEEL_COLS) {
         int sum = 0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) sum += red[w][tid];
-        const int j = j0 + tid;
-        if (sum != 0 && j < v.n2 && v.rank2[j] < 0) atomicAdd(&v.cnt[j], k == 0 ? sum : -sum);
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) ticket = atomicAdd(&v.chunk_done[chunk], 1u);
-    __syncthreads();
-    if (ticket != (unsigned)(nsplit - 1)) return;
-
-    // last split of this column chunk: rank its columns
-    __threadfence();
-    if (tid < NSGA3_PEEL_COLS) {
+#pragma unroll 8
+        for (int w = 0; w < PW; ++w) sum += red[w][tid];
         const int j = j0 + tid;
         bool nf = false;
-        if (j < v.n2 && v.rank2[j] < 0) {
-            int cv = atomicAdd(&v.cnt[j], 0);
+        if (j < v.n2 && v.srank[j] < 0) {
+            const int cv = (k == 0) ? sum : v.cnt[j] - sum;
+            v.cnt[j] = cv;
             if (cv == 0) {
-                v.rank2[j] = k;
+                v.srank[j] = k;
                 nf = true;
             }
         }
-        uint32_t word = __ballot_sync(0xffffffffu, nf);
+        const uint32_t word = __ballot_sync(0xffffffffu, nf);
         if (lane == 0) {
             const int wd = j0 / 32 + warp;
             v.front[(k & 1) * v.NW + wd] = word;
@@ -144,11 +172,10 @@ __global__ void __launch_bounds__(256) k_peel(RunView v, int nsplit, cudaGraphCo
             }
         }
     }
-    if (tid == 0) v.chunk_done[chunk] = 0;
     __threadfence();
     __syncthreads();
     if (tid != 0) return;
-    unsigned g = atomicAdd(&c->chunks_done, 1u);
+    const unsigned g = atomicAdd(&c->chunks_done, 1u);
     if (g != (unsigned)(nchunks - 1)) return;
 
     // last chunk of the pass: close front k and decide whether to continue
@@ -166,8 +193,6 @@ __global__ void __launch_bounds__(256) k_peel(RunView v, int nsplit, cudaGraphCo
     }
     if (fs == 0 && cum < v.n2) set_status(c, DEV_EINTERNAL);
     const bool more = fs > 0 && cum < v.n2 && (v.full_sort || c->l < 0);
-    const unsigned fw = atomicAdd(&c->front_words, 0u);
-    if (more) c->peel_rows += fw;  // rows the next pass reads
     c->front_words = 0u;
     c->front_size = 0;
     c->chunks_done = 0;
@@ -177,36 +202,38 @@ __global__ void __launch_bounds__(256) k_peel(RunView v, int nsplit, cudaGraphCo
     if (in_graph) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
-__global__ void k_post_peel(RunView v, cudaGraphConditionalHandle h_niche)
+// ranks back to the original order; the first thread sets the niching branch
+__global__ void k_post_peel(RunView v, cudaGraphConditionalHandle h_niche, int in_graph)
 {
     Ctrl* c = v.ctrl;
-    const int go = (read_status(c) == 0 && c->l >= 0 && c->need_niche) ? 1 : 0;
-    cudaGraphSetConditional(h_niche, (unsigned)go);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < v.n2) v.rank2[v.perm[p]] = v.srank[p];
+    if (p == 0 && in_graph) {
+        const int go = (read_status(c) == 0 && c->l >= 0 && c->need_niche) ? 1 : 0;
+        cudaGraphSetConditional(h_niche, (unsigned)go);
+    }
 }
 
 }  // namespace
 
 int peel_nsplit(const RunView& v, int num_sms)
 {
-    const int nchunks = v.ld / NSGA3_PEEL_COLS;
-    int target = num_sms * 8;
-    int ns = (target + nchunks - 1) / nchunks;
-    if (ns < 1) ns = 1;
-    if (ns > 16) ns = 16;
-    if (ns > v.NW) ns = v.NW;
-    return ns;
+    (void)v;
+    (void)num_sms;
+    return 1;  // one CTA per column chunk
 }
 
 cudaError_t launch_peel(const RunView& v, int nsplit, cudaGraphConditionalHandle h, int in_graph,
                         cudaStream_t s)
 {
-    const int nchunks = v.ld / NSGA3_PEEL_COLS;
-    k_peel<<<nchunks * nsplit, 256, 0, s>>>(v, nsplit, h, in_graph);
+    (void)nsplit;
+    k_peel<<<v.ld / NSGA3_PEEL_COLS, PT, 0, s>>>(v, h, in_graph);
     return cudaGetLastError();
 }
 
-cudaError_t launch_post_peel(const RunView& v, cudaGraphConditionalHandle h_niche, cudaStream_t s)
+cudaError_t launch_post_peel(const RunView& v, cudaGraphConditionalHandle h_niche, int in_graph,
+                             cudaStream_t s)
 {
-    k_post_peel<<<1, 1, 0, s>>>(v, h_niche);
+    k_post_peel<<<(v.n2 + 255) / 256, 256, 0, s>>>(v, h_niche, in_graph);
     return cudaGetLastError();
 }

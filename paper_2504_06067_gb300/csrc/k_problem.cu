@@ -15,7 +15,7 @@
 //   Children go to rows N + 2q and N + 2q + 1.  FP32 arithmetic.
 // Objective (the softmax-simplex family): k = m - 1,
 //   g = sum_{v >= k} (x_v - 0.5)^2, f_j = (1 + g) softmax(W x[0:k])_j,
-//   evaluated in FP64 and rounded to FP32.
+//   g summed in FP32 with Kahan compensation, softmax in FP64, rounded to FP32.
 #include "kernels.cuh"
 
 namespace {
@@ -67,26 +67,45 @@ __global__ void k_refdirs(int m, int p1, int p2, double tau, int w1, int w, doub
     for (int q = 0; q < M4; ++q) Zh[(size_t)t * M4 + q] = q < m ? __double2float_rn(__ddiv_rn(z[q], n)) : 0.0f;
 }
 
-// objective of one row whose variables sit across the warp (x_v in lane v % 32,
-// iteration v / 32); xs[] holds the lane's values, k = m - 1 < 32.
-__device__ void warp_eval_row(const float* xrow, int d, int m, const float* W, float* frow)
+// Objective of rows [row0, row0 + n): a block covers OR = 32 rows with
+// OR * m threads.  g is summed in FP32 with Kahan compensation (relative
+// error ~1e-7; GB300's FP64 pipe runs at 1/64 of FP32).  Thread (row, j)
+// forms a_j = sum_v W_jv x_v in FP64 (left to right) and e_j = exp(a_j); the
+// row's denominator adds e_0..e_{m-1} in order, f_j = (1 + g) e_j / den in
+// FP64, rounded to FP32.
+constexpr int OR = 32;
+
+__global__ void k_objective(RunView v, int row0, int n)
 {
-    const int lane = lane_id();
-    const int k = m - 1;
-    double g = 0.0;
-    for (int v = k + lane; v < d; v += 32) {
-        const double t = __dsub_rn((double)xrow[v], 0.5);
-        g = __dadd_rn(g, __dmul_rn(t, t));
+    __shared__ double sg[OR];
+    __shared__ double se[OR * NSGA3_MAX_M];
+    const int m = v.m, d = v.d, k = m - 1;
+    const int base = blockIdx.x * OR;
+    const int rr = threadIdx.x / m, j = threadIdx.x - (threadIdx.x / m) * m;
+    const bool live = rr < OR && base + rr < n;
+    const float* x = v.X + (size_t)(row0 + base + rr) * d;
+    if (live && j == 0) {
+        float sum = 0.0f, comp = 0.0f;
+        for (int e = k; e < d; ++e) {
+            const float t = x[e] - 0.5f;
+            const float y = t * t - comp;
+            const float s2 = sum + y;
+            comp = (s2 - sum) - y;
+            sum = s2;
+        }
+        sg[rr] = (double)sum - (double)comp;
     }
-    g = warp_sum(g);
-    double e = 0.0;
-    if (lane < m) {
+    if (live) {
         double a = 0.0;
-        for (int v = 0; v < k; ++v) a = __dadd_rn(a, __dmul_rn((double)W[lane * k + v], (double)xrow[v]));
-        e = exp(a);
+        for (int e = 0; e < k; ++e) a = __dadd_rn(a, __dmul_rn((double)v.Wobj[j * k + e], (double)x[e]));
+        se[rr * m + j] = exp(a);
     }
-    double den = warp_sum(lane < m ? e : 0.0);
-    if (lane < m) frow[lane] = __double2float_rn(__dmul_rn(__dadd_rn(1.0, g), __ddiv_rn(e, den)));
+    __syncthreads();
+    if (!live) return;
+    double den = 0.0;
+    for (int t = 0; t < m; ++t) den = __dadd_rn(den, se[rr * m + t]);
+    const double f = __dmul_rn(__dadd_rn(1.0, sg[rr]), __ddiv_rn(se[rr * m + j], den));
+    v.F[(size_t)(row0 + base + rr) * m + j] = __double2float_rn(f);
 }
 
 __global__ void k_init(RunView v)
@@ -99,8 +118,6 @@ __global__ void k_init(RunView v)
         U4 r = philox((uint32_t)i * (uint32_t)v.d + (uint32_t)e, 0u, RNG_INIT, 0u, v.seed);
         xrow[e] = u01(r.x);
     }
-    __syncwarp();
-    warp_eval_row(xrow, v.d, v.m, v.Wobj, v.F + (size_t)i * v.m);
     if (lane == 0) v.rank[i] = 0;
 }
 
@@ -164,9 +181,6 @@ __global__ void k_vary_eval(RunView v)
         x0[var] = c1;
         x1[var] = c2;
     }
-    __syncwarp();
-    warp_eval_row(x0, d, v.m, v.Wobj, v.F + (size_t)(N + c0) * v.m);
-    warp_eval_row(x1, d, v.m, v.Wobj, v.F + (size_t)(N + c1i) * v.m);
 }
 
 }  // namespace
@@ -189,6 +203,9 @@ cudaError_t launch_init(const RunView& v, cudaStream_t s)
 {
     long long threads = (long long)v.N * 32;
     k_init<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_objective<<<(v.N + OR - 1) / OR, OR * v.m, 0, s>>>(v, 0, v.N);
     return cudaGetLastError();
 }
 
@@ -196,5 +213,8 @@ cudaError_t launch_vary_eval(const RunView& v, cudaStream_t s)
 {
     long long threads = (long long)(v.N / 2) * 32;
     k_vary_eval<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_objective<<<(v.N + OR - 1) / OR, OR * v.m, 0, s>>>(v, v.N, v.N);
     return cudaGetLastError();
 }
