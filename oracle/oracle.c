@@ -643,8 +643,9 @@ int orc_select(const float *F, int N, int m, const double *Z, int w, uint64_t se
 /*   (1/(2(1-u)))^(1/(eta_c+1)); c1 = 0.5((1+beta)x1 + (1-beta)x2),         */
 /*   c2 = 0.5((1-beta)x1 + (1+beta)x2); word 2 < 0.5 swaps c1, c2; clip.    */
 /*   Children 2q, 2q+1.  Polynomial mutation (Deb & Goyal 1996, bounded     */
-/*   form on [0,1]) of child c, variable v: Philox(c*d + v, gen, 3, 0):     */
-/*   word 0 < p_m mutates with u = word 1.                                  */
+/*   form on [0,1]) of variable v: Philox(q*d + v, gen, 2, 0) word 3 < p_m  */
+/*   mutates child 2q with u = word 0 of Philox(q*d + v, gen, 3, 0); word 1 */
+/*   of that block < p_m mutates child 2q+1 with u = its word 2.            */
 /* Probability tests compare the exact float uniform with the float        */
 /* probability.  Arithmetic in FP64; children rounded to FP32.              */
 /* ---------------------------------------------------------------------- */
@@ -678,13 +679,14 @@ void orc_vary(const float *X, const int32_t *rank, int N, int d, uint64_t seed, 
                 if (c2 > 1.0) c2 = 1.0;
             }
             double ch[2] = {c1, c2};
+            uint32_t pm[4];
+            orc_draw(seed, (uint32_t)q * (uint32_t)d + (uint32_t)v, gen, ORC_STREAM_PM, 0, pm);
+            const uint32_t pm_dec[2] = {s[3], pm[1]}, pm_u[2] = {pm[0], pm[2]};
             for (int h = 0; h < 2; ++h) {
                 uint32_t c = 2u * (uint32_t)q + (uint32_t)h;
                 double y = ch[h];
-                uint32_t pm[4];
-                orc_draw(seed, c * (uint32_t)d + (uint32_t)v, gen, ORC_STREAM_PM, 0, pm);
-                if ((float)orc_uniform(pm[0]) < p_m) {
-                    double u = orc_uniform(pm[1]);
+                if ((float)orc_uniform(pm_dec[h]) < p_m) {
+                    double u = orc_uniform(pm_u[h]);
                     double d1 = y - 0.0, d2 = 1.0 - y;
                     double mp = 1.0 / (eta_m + 1.0);
                     double dq;

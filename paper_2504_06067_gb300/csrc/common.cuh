@@ -206,6 +206,13 @@ __device__ __forceinline__ int read_status(const Ctrl* c)
     return *(volatile const int32_t*)&c->status;
 }
 
+// niching kernels run unconditionally in the graph and return at once when
+// the selection failed or |S| + |F_l| == N (no niching needed)
+__device__ __forceinline__ bool skip_niche(const Ctrl* c)
+{
+    return read_status(c) != 0 || *(volatile const int32_t*)&c->need_niche == 0;
+}
+
 // lexicographic (value, index) minimum for doubles
 __device__ __forceinline__ bool lex_less(double a, int ia, double b, int ib)
 {

@@ -2,12 +2,12 @@
 // a selection / a generation, and the C ABI declared in include/nsga3.h.
 //
 // A generation is captured once per context as a CUDA graph:
-//   vary+eval -> reset -> dominance -> WHILE(peel pass) -> post-peel
-//   -> IF(niching needed){ ideal, extremes, solve, prep, scan, level,
-//                           bucket, pick } -> compaction -> gather -> gen++
+//   vary+eval -> reset -> sort -> dominance -> WHILE(peel pass) -> post-peel
+//   -> ideal, extremes+solve, prep, scan, level, bucket, pick
+//   -> compaction -> gather -> gen++
 // The WHILE node replays the peel kernel until its last CTA clears the
-// condition (one pass per front), and the IF node skips the niching when
-// |S| + |F_l| == N, so a replay never returns to the host.
+// condition (one pass per front); the niching kernels return at once when
+// |S| + |F_l| == N.  A replay never returns to the host.
 #include <cstdarg>
 #include <cstdlib>
 #include <cstdio>
@@ -156,7 +156,7 @@ nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, 
     CK(launch_dominance(v, s));
     st = record_event(ctx, s, EV_DOM, events);
     if (st) return st;
-    cudaGraphConditionalHandle h_peel, h_niche;
+    cudaGraphConditionalHandle h_peel;
     cudaGraph_t body;
     st = add_conditional(ctx, s, cudaGraphCondTypeWhile, 1u, &h_peel, &body);
     if (st) return st;
@@ -170,44 +170,16 @@ nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, 
     }
     st = record_event(ctx, s, EV_PEEL, events);
     if (st) return st;
-    // the IF handle is created first so that post-peel can set it
-    {
-        cudaStreamCaptureStatus cs;
-        cudaGraph_t g = nullptr;
-        CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
-        CK(cudaGraphConditionalHandleCreate(&h_niche, g, 0u, cudaGraphCondAssignDefault));
-    }
-    CK(launch_post_peel(v, h_niche, 1, s));
-    {
-        cudaStreamCaptureStatus cs;
-        cudaGraph_t g = nullptr;
-        const cudaGraphNode_t* deps = nullptr;
-        size_t nd = 0;
-        CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
-        cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
-        p.conditional.handle = h_niche;
-        p.conditional.type = cudaGraphCondTypeIf;
-        p.conditional.size = 1;
-        cudaGraphNode_t node;
-        CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
-        body = p.conditional.phGraph_out[0];
-        CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-    }
-    CK(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    {
-        cudaError_t e = cudaSuccess;
-        if (e == cudaSuccess) e = launch_norm_ideal(v, s2);
-        if (e == cudaSuccess) e = launch_norm_extreme(v, s2);
-        if (e == cudaSuccess) e = launch_assoc_prep(v, s2);
-        if (e == cudaSuccess) e = launch_assoc_scan(v, ctx->num_sms, s2);
-        if (e == cudaSuccess) e = launch_level(v, s2);
-        if (e == cudaSuccess) e = launch_bucket(v, s2);
-        if (e == cudaSuccess) e = launch_pick(v, s2);
-        cudaGraph_t tmp;
-        cudaError_t e2 = cudaStreamEndCapture(s2, &tmp);
-        CK(e);
-        CK(e2);
-    }
+    CK(launch_post_peel(v, 0, 0, s));
+    // the niching kernels return at once when no niching is needed: a graph
+    // IF node costs more than their empty launches
+    CK(launch_norm_ideal(v, s));
+    CK(launch_norm_extreme(v, s));
+    CK(launch_assoc_prep(v, s));
+    CK(launch_assoc_scan(v, ctx->num_sms, s));
+    CK(launch_level(v, s));
+    CK(launch_bucket(v, s));
+    CK(launch_pick(v, s));
     st = record_event(ctx, s, EV_NICHE, events);
     if (st) return st;
     CK(launch_compact(v, s));
@@ -421,8 +393,11 @@ nsga3_status setup(nsga3_ctx* ctx)
     v.eta_m = ctx->opts.eta_m;
     v.p_c = ctx->opts.p_c;
     v.p_m = ctx->opts.p_m < 0.0f ? 1.0f / (float)d : ctx->opts.p_m;
-    v.ext_parts = (n2 + 63) / 64;
-    if (v.ext_parts > 4 * ctx->num_sms) v.ext_parts = 4 * ctx->num_sms;
+    // at most two extreme-point blocks per SM (<= 512): the last block
+    // reduces the blocks' partial results one warp per axis
+    v.ext_parts = (n2 + 127) / 128;
+    if (v.ext_parts > 2 * ctx->num_sms) v.ext_parts = 2 * ctx->num_sms;
+    if (v.ext_parts > 512) v.ext_parts = 512;
 
     AL(v.ctrl, 1);
     AL(v.X, (size_t)n2 * d);
@@ -934,11 +909,12 @@ nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches)
     Ctrl c;
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(&c, ctx->v.ctrl, sizeof c, cudaMemcpyDeviceToHost));
-    // reset, 3 sort, dominance, post-peel, compaction (+ finite check for a
-    // selection; + variation, objective, gather, counter for a generation),
-    // one per peel pass, and 11 niching launches when the IF branch ran
-    int fixed = (ctx->last_kind == 1) ? 8 : 11;
-    *launches = fixed + c.passes + (c.need_niche ? 11 : 0);
+    // reset, 3 sort, dominance, post-peel, 11 niching (they return at once
+    // when no niching is needed), compaction (+ finite check for a selection;
+    // + variation, objective, gather, counter for a generation), and one per
+    // peel pass
+    int fixed = (ctx->last_kind == 1) ? 19 : 22;
+    *launches = fixed + c.passes;
     return NSGA3_OK;
 }
 

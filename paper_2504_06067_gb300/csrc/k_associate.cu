@@ -55,26 +55,30 @@ __device__ __forceinline__ double perp_dist(const double* fp, double nf, const d
 }
 
 // f' = (f - z*) / a and |f'| in FP64; FP32 unit vector for the scan
+template <int M>
 __global__ void __launch_bounds__(AB) k_assoc_prep(RunView v)
 {
+    constexpr int M4 = (M + 3) & ~3;
     Ctrl* c = v.ctrl;
-    if (read_status(c)) return;
+    if (skip_niche(c)) return;
     const int s = blockIdx.x * AB + threadIdx.x;
     if (s >= c->nT) return;
-    const int m = v.m, i = v.Tlist[s];
-    double fp[NSGA3_MAX_M];
+    const int i = v.Tlist[s];
+    double fp[M];
     double ss = 0.0;
-    for (int q = 0; q < m; ++q) {
-        const double ft = __dsub_rn((double)v.F[(size_t)i * m + q], c->zstar[q]);
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+        const double ft = __dsub_rn((double)v.F[(size_t)i * M + q], c->zstar[q]);
         fp[q] = __ddiv_rn(ft, c->a[q]);
         ss = __dadd_rn(ss, __dmul_rn(fp[q], fp[q]));
-        v.fprime[(size_t)s * m + q] = fp[q];
+        v.fprime[(size_t)s * M + q] = fp[q];
     }
     const double nf = __dsqrt_rn(ss);
     v.fnorm[s] = nf;
     const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
-    for (int q = 0; q < v.M4; ++q)
-        v.uhat[(size_t)s * v.M4 + q] = q < m ? __double2float_rn(fp[q] * inv) : 0.0f;
+#pragma unroll
+    for (int q = 0; q < M4; ++q)
+        v.uhat[(size_t)s * M4 + q] = q < M ? __double2float_rn(fp[q] * inv) : 0.0f;
 }
 
 template <int M>
@@ -83,7 +87,7 @@ __global__ void __launch_bounds__(AB) k_assoc_scan(RunView v)
     constexpr int M4 = (M + 3) & ~3;
     extern __shared__ __align__(16) float sm[];
     Ctrl* c = v.ctrl;
-    if (read_status(c)) return;
+    if (skip_niche(c)) return;
     const int nT = c->nT;
     const int nb = v.nblk;
     const int lane = lane_id(), warp = threadIdx.x >> 5;
@@ -247,7 +251,7 @@ template <int M>
 __global__ void __launch_bounds__(AB) k_assoc_recheck(RunView v)
 {
     Ctrl* c = v.ctrl;
-    if (read_status(c)) return;
+    if (skip_niche(c)) return;
     const int n = min(c->ncand, v.cand_cap);
     for (int e = blockIdx.x * AB + threadIdx.x; e < n; e += gridDim.x * AB) {
         const int2 pj = v.cand[e];
@@ -272,7 +276,7 @@ __device__ __forceinline__ void write_assoc(const RunView& v, Ctrl* c, int i, in
 __global__ void __launch_bounds__(AB) k_assoc_final(RunView v)
 {
     Ctrl* c = v.ctrl;
-    if (read_status(c)) return;
+    if (skip_niche(c)) return;
     const int pt = blockIdx.x * AB + threadIdx.x;
     if (pt >= c->nT) return;
     const int2 run = v.arun[pt];
@@ -307,7 +311,7 @@ __global__ void __launch_bounds__(AB) k_assoc_slow(RunView v)
     __shared__ double sd[AB / 32];
     __shared__ int sj[AB / 32];
     Ctrl* c = v.ctrl;
-    if (read_status(c)) return;
+    if (skip_niche(c)) return;
     const int ns = c->nslow;
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     for (int t = blockIdx.x; t < ns; t += gridDim.x) {
@@ -390,7 +394,19 @@ cudaError_t attr_m(size_t sm)
 
 cudaError_t launch_assoc_prep(const RunView& v, cudaStream_t s)
 {
-    k_assoc_prep<<<(v.n2 + AB - 1) / AB, AB, 0, s>>>(v);
+    const int g = (v.n2 + AB - 1) / AB;
+    switch (v.m) {
+    case 2: k_assoc_prep<2><<<g, AB, 0, s>>>(v); break;
+    case 3: k_assoc_prep<3><<<g, AB, 0, s>>>(v); break;
+    case 4: k_assoc_prep<4><<<g, AB, 0, s>>>(v); break;
+    case 5: k_assoc_prep<5><<<g, AB, 0, s>>>(v); break;
+    case 6: k_assoc_prep<6><<<g, AB, 0, s>>>(v); break;
+    case 7: k_assoc_prep<7><<<g, AB, 0, s>>>(v); break;
+    case 8: k_assoc_prep<8><<<g, AB, 0, s>>>(v); break;
+    case 9: k_assoc_prep<9><<<g, AB, 0, s>>>(v); break;
+    case 10: k_assoc_prep<10><<<g, AB, 0, s>>>(v); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

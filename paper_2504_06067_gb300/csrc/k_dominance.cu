@@ -6,9 +6,9 @@
 // across rows, which the front peel reads coalesced.
 //
 // Work: only unordered pairs are compared.  A CTA owns a 256 x 256 tile of
-// the upper block triangle; warp w takes row block ib = 8 * ti + w (lane =
-// row i, its m objectives in registers) against each column block jb >= ib
-// of the tile, with the column points broadcast from shared memory.  Per
+// the upper block triangle; each warp takes two row blocks (lane = one row
+// of each, objectives in registers) against four column blocks jb >= ib,
+// the column points broadcast from shared memory to both rows.  Per
 // pair the m differences f_j - f_i and f_i - f_j run on the FMA pipe and
 // their sign bits are OR-ed (3-input LOP3): A = "no f_i > f_j" and
 // B = "no f_j > f_i"; "i dom j" = A & !B, "j dom i" = B & !A (identical
@@ -22,6 +22,9 @@
 // (32 x 32 bit transpose by five shuffle stages) into Dom[ib][j].
 // Padding rows/columns hold NaN: both differences of a pair with a padding
 // point are the same NaN, so neither direction gets a bit.
+//
+// Every CTA also popcounts the words it writes and adds each point's
+// dominator count to cnt[] (the peel's first pass then reads no words).
 //
 // Bound: the ALU pipe (sign-bit logic) and instruction issue -- not HBM.
 #include "kernels.cuh"
@@ -61,14 +64,51 @@ __device__ __forceinline__ void decode_tile(long long t, int T, int& ti, int& tj
     tj = r + (int)(t - start(r));
 }
 
+// one 32-column block against one row block, both directions (ties in f_0)
+template <int M, int M4>
+__device__ __forceinline__ void block_full(const float* fi, const float* colp, uint32_t& dij, uint32_t& dji)
+{
+    dij = 0u;
+    dji = 0u;
+    // columns k = 31 .. 0: the funnel shift leaves column k's bit at position k
+#pragma unroll 4
+    for (int k = 31; k >= 0; --k) {
+        const float4* fj4 = reinterpret_cast<const float4*>(colp + k * M4);
+        float fj[M4];
+#pragma unroll
+        for (int q4 = 0; q4 < M4 / 4; ++q4) {
+            const float4 t = fj4[q4];
+            fj[4 * q4 + 0] = t.x;
+            fj[4 * q4 + 1] = t.y;
+            fj[4 * q4 + 2] = t.z;
+            fj[4 * q4 + 3] = t.w;
+        }
+        // sign(f_j - f_i) per objective: 0 if f_i <= f_j, 1 if f_i > f_j
+        // (exact FP32 subtraction of finite values; NaN padding gives NaN)
+        uint32_t oa = 0u, ob = 0u;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+            oa |= __float_as_uint(fj[q] - fi[q]);
+            ob |= __float_as_uint(fi[q] - fj[q]);
+        }
+        // i dom j: no f_i > f_j and some f_i < f_j; j dom i symmetric
+        dij = __funnelshift_l(ob & ~oa, dij, 1);
+        dji = __funnelshift_l(oa & ~ob, dji, 1);
+    }
+}
+
 template <int M>
 __global__ void __launch_bounds__(256) k_dominance(RunView v)
 {
     constexpr int M4 = (M + 3) & ~3;
     __shared__ __align__(16) float srow[NSGA3_TILE * M4];
     __shared__ __align__(16) float scol[NSGA3_TILE * M4];
-    if (read_status(v.ctrl)) return;
     __shared__ int s_tile[2];
+    __shared__ int rowcnt[NSGA3_TILE];  // dominators found for the tile's row points
+    __shared__ int colcnt[NSGA3_TILE];  // ... for its column points
+    if (read_status(v.ctrl)) return;
+    rowcnt[threadIdx.x] = 0;
+    colcnt[threadIdx.x] = 0;
     const int T = v.ld / NSGA3_TILE;
     if (threadIdx.x == 0) decode_tile(blockIdx.x, T, s_tile[0], s_tile[1]);
     __syncthreads();
@@ -82,72 +122,110 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = lane_id();
-    const int ib = ti * 8 + warp;
-    float fi[M];
+    // warp = (row pair rp, column half ch): row blocks 2rp, 2rp+1 of the tile
+    // against column blocks 4ch .. 4ch+3; every column load serves two rows
+    const int rp = warp & 3, ch = warp >> 2;
+    const int ib0 = ti * 8 + 2 * rp, ib1 = ib0 + 1;
+    float f0[M], f1[M];
 #pragma unroll
-    for (int q = 0; q < M; ++q) fi[q] = srow[(warp * 32 + lane) * M4 + q];
-
-    for (int cb = 0; cb < 8; ++cb) {
+    for (int q = 0; q < M; ++q) {
+        f0[q] = srow[(2 * rp * 32 + lane) * M4 + q];
+        f1[q] = srow[((2 * rp + 1) * 32 + lane) * M4 + q];
+    }
+    float rmax0 = f0[0], rmax1 = f1[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rmax0 = fmaxf(rmax0, __shfl_xor_sync(0xffffffffu, rmax0, o));
+        rmax1 = fmaxf(rmax1, __shfl_xor_sync(0xffffffffu, rmax1, o));
+    }
+    uint32_t* D = v.Dom;
+    int rc0 = 0, rc1 = 0;  // dominators of row points ib0*32+lane, ib1*32+lane in this tile
+    for (int cbi = 0; cbi < 4; ++cbi) {
+        const int cb = ch * 4 + cbi;
         const int jb = tj * 8 + cb;
-        if (jb < ib) continue;  // lower block triangle: done by the transposed tile
-        uint32_t dij = 0, dji = 0;
+        if (jb < ib0) continue;  // lower block triangle: done by the transposed tile
         const float* colp = scol + cb * 32 * M4;
+        float cmin = colp[lane * M4];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
         // every row's f_0 below every column's f_0: only "row dom column" can
-        // hold, f_i0 < f_j0 makes it strict, and it needs objectives 1..m-1
-        float rmax = fi[0], cmin = colp[lane * M4];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-            cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
-        }
-        if (jb != ib && rmax < cmin) {
-            uint32_t acc = 0u;
-#pragma unroll 8
+        // hold, f_i0 < f_j0 makes it strict, and objectives 1..m-1 decide it
+        const bool fast0 = jb != ib0 && rmax0 < cmin;
+        const bool fast1 = jb > ib1 && rmax1 < cmin;
+        if (fast0 && fast1) {
+            uint32_t acc0 = 0u, acc1 = 0u;
+#pragma unroll 4
             for (int k = 31; k >= 0; --k) {
-                const float* fj = colp + k * M4;
-                uint32_t oa = 0u;
+                const float4* fj4 = reinterpret_cast<const float4*>(colp + k * M4);
+                float fj[M4];
 #pragma unroll
-                for (int q = 1; q < M; ++q) oa |= __float_as_uint(fj[q] - fi[q]);
-                acc = __funnelshift_l(oa, acc, 1);  // sign set: some f_iq > f_jq
+                for (int q4 = 0; q4 < M4 / 4; ++q4) {
+                    const float4 t = fj4[q4];
+                    fj[4 * q4 + 0] = t.x;
+                    fj[4 * q4 + 1] = t.y;
+                    fj[4 * q4 + 2] = t.z;
+                    fj[4 * q4 + 3] = t.w;
+                }
+                uint32_t oa0 = 0u, oa1 = 0u;
+#pragma unroll
+                for (int q = 1; q < M; ++q) {
+                    oa0 |= __float_as_uint(fj[q] - f0[q]);
+                    oa1 |= __float_as_uint(fj[q] - f1[q]);
+                }
+                acc0 = __funnelshift_l(oa0, acc0, 1);  // sign set: some f_iq > f_jq
+                acc1 = __funnelshift_l(oa1, acc1, 1);
             }
-            uint32_t* D = v.Dom;
-            D[(size_t)jb * v.ld + ib * 32 + lane] = 0u;
-            D[(size_t)ib * v.ld + jb * 32 + lane] = warp_transpose32(~acc);
+            const uint32_t t0 = warp_transpose32(~acc0), t1 = warp_transpose32(~acc1);
+            D[(size_t)jb * v.ld + ib0 * 32 + lane] = 0u;
+            D[(size_t)jb * v.ld + ib1 * 32 + lane] = 0u;
+            D[(size_t)ib0 * v.ld + jb * 32 + lane] = t0;
+            D[(size_t)ib1 * v.ld + jb * 32 + lane] = t1;
+            const int cc = __popc(t0) + __popc(t1);
+            if (cc) atomicAdd(&colcnt[cb * 32 + lane], cc);
             continue;
         }
-        // columns k = 31 .. 0: the funnel shift leaves column k's bit at position k
-#pragma unroll 8
-        for (int k = 31; k >= 0; --k) {
-            const float4* fj4 = reinterpret_cast<const float4*>(colp + k * M4);
-            float fj[M4];
 #pragma unroll
-            for (int q4 = 0; q4 < M4 / 4; ++q4) {
-                const float4 t = fj4[q4];
-                fj[4 * q4 + 0] = t.x;
-                fj[4 * q4 + 1] = t.y;
-                fj[4 * q4 + 2] = t.z;
-                fj[4 * q4 + 3] = t.w;
-            }
-            // sign(f_j - f_i) per objective: 0 if f_i <= f_j, 1 if f_i > f_j
-            // (exact FP32 subtraction of finite values; NaN padding gives +NaN)
-            uint32_t oa = 0u, ob = 0u;
+        for (int r = 0; r < 2; ++r) {
+            const int ib = r ? ib1 : ib0;
+            if (jb < ib) continue;
+            const float* fi = r ? f1 : f0;
+            const bool fast = r ? fast1 : fast0;
+            uint32_t dij, dji;
+            if (fast) {
+                uint32_t acc = 0u;
+#pragma unroll 4
+                for (int k = 31; k >= 0; --k) {
+                    const float* fj = colp + k * M4;
+                    uint32_t oa = 0u;
 #pragma unroll
-            for (int q = 0; q < M; ++q) {
-                oa |= __float_as_uint(fj[q] - fi[q]);
-                ob |= __float_as_uint(fi[q] - fj[q]);
+                    for (int q = 1; q < M; ++q) oa |= __float_as_uint(fj[q] - fi[q]);
+                    acc = __funnelshift_l(oa, acc, 1);
+                }
+                dij = ~acc;
+                dji = 0u;
+            } else {
+                block_full<M, M4>(fi, colp, dij, dji);
             }
-            // i dom j: no f_i > f_j and some f_i < f_j; j dom i symmetric
-            dij = __funnelshift_l(ob & ~oa, dij, 1);
-            dji = __funnelshift_l(oa & ~ob, dji, 1);
-        }
-        uint32_t* D = v.Dom;
-        // column i = ib*32 + lane, dominators j in block jb
-        D[(size_t)jb * v.ld + ib * 32 + lane] = dji;
-        if (jb != ib) {
-            uint32_t t = warp_transpose32(dij);  // lane k: bits over i of column jb*32 + k
-            D[(size_t)ib * v.ld + jb * 32 + lane] = t;
+            // column i = ib*32 + lane, dominators j in block jb
+            D[(size_t)jb * v.ld + ib * 32 + lane] = dji;
+            if (r)
+                rc1 += __popc(dji);
+            else
+                rc0 += __popc(dji);
+            if (jb != ib) {
+                const uint32_t t = warp_transpose32(dij);
+                D[(size_t)ib * v.ld + jb * 32 + lane] = t;
+                if (t) atomicAdd(&colcnt[cb * 32 + lane], __popc(t));
+            }
         }
     }
+    if (rc0) atomicAdd(&rowcnt[2 * rp * 32 + lane], rc0);
+    if (rc1) atomicAdd(&rowcnt[(2 * rp + 1) * 32 + lane], rc1);
+    __syncthreads();
+    // dominator counts of the peel's first pass: one global add per point of the tile
+    const int t = threadIdx.x;
+    if (rowcnt[t]) atomicAdd(&v.cnt[r0 + t], rowcnt[t]);
+    if (colcnt[t]) atomicAdd(&v.cnt[c0 + t], colcnt[t]);
 }
 
 template <int M>

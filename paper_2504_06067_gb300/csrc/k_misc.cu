@@ -30,6 +30,7 @@ __global__ void k_sel_reset(RunView v)
         v.rho[j] = 0;
         v.rhop[j] = 0;
         v.refprio[j] = philox((uint32_t)j, gen, RNG_REFPRIO, 0u, v.seed).x;
+        v.cursor[j] = 0;
     }
     if (tid == 0) {
         Ctrl* c = v.ctrl;
@@ -101,38 +102,52 @@ __global__ void __launch_bounds__(1024) k_compact(RunView v)
     __syncthreads();
     if (ticket != gridDim.x - 1) return;
     __threadfence();
-    const int per = (v.NW + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int lo = min(v.NW, (int)threadIdx.x * per), hi = min(v.NW, lo + per);
-    int s = 0;
-    for (int t = lo; t < hi; ++t) s += __popc(__ldcg(&words[t]));
-    int inc = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
+    // last CTA: warp w owns a contiguous run of words; lane-parallel popcounts
+    // and a block scan give each word's first output slot, then every word's
+    // set bits are written by its warp at consecutive (coalesced) positions
+    const int per = (v.NW + nwarps - 1) / nwarps;
+    const int wlo = min(v.NW, warp * per), whi = min(v.NW, wlo + per);
+    int wsum = 0;
+    for (int t0 = wlo; t0 < whi; t0 += 32) {
+        const int t = t0 + lane;
+        wsum += (t < whi) ? __popc(__ldcg(&words[t])) : 0;
     }
-    if (lane == 31) scratch[warp] = inc;
+    wsum = warp_sum(wsum);
+    if (lane == 0) scratch[warp] = wsum;
     __syncthreads();
     if (warp == 0) {
-        int x = lane < nwarps ? scratch[lane] : 0, xi = x;
+        const int x = lane < nwarps ? scratch[lane] : 0;
+        int xi = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, xi, o);
+            const int y = __shfl_up_sync(0xffffffffu, xi, o);
             if (lane >= o) xi += y;
         }
         scratch[lane] = xi - x;
         if (lane == 31) scratch[32] = xi;
     }
     __syncthreads();
-    int run = scratch[warp] + inc - s;
-    for (int t = lo; t < hi; ++t) {
-        uint32_t word = __ldcg(&words[t]);
-        while (word) {
-            const int b = __ffs(word) - 1;
-            word &= word - 1;
-            if (run < v.N) v.sel[run] = t * 32 + b;
-            ++run;
+    int run = scratch[warp];
+    for (int t0 = wlo; t0 < whi; t0 += 32) {
+        const int t = t0 + lane;
+        const uint32_t word_l = (t < whi) ? __ldcg(&words[t]) : 0u;
+        const int cnt_l = __popc(word_l);
+        int inc = cnt_l;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
         }
+        const int nw = min(32, whi - t0);
+        for (int u = 0; u < nw; ++u) {
+            const uint32_t wu = __shfl_sync(0xffffffffu, word_l, u);
+            const int off = run + __shfl_sync(0xffffffffu, inc - cnt_l, u);
+            if ((wu >> lane) & 1u) {
+                const int pos = off + __popc(wu & ((1u << lane) - 1u));
+                if (pos < v.N) v.sel[pos] = (t0 + u) * 32 + lane;
+            }
+        }
+        run += __shfl_sync(0xffffffffu, inc, 31);
     }
     if (threadIdx.x == 0) {
         c->cmp_done = 0u;

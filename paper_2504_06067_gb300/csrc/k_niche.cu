@@ -160,14 +160,35 @@ __device__ void block_select_smallest(int n, int need, Key key, Pred pred, Mark 
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int run = 0, b = 0;
-            for (; b < 256; ++b) {
-                if (run + sh.hist[b] >= need) break;
-                run += sh.hist[b];
+        if (threadIdx.x < 32) {
+            // warp scan of the 256 bins (8 per lane): the bin where the running
+            // count reaches `need`, and the count before it
+            const int lane = threadIdx.x;
+            int h8[8], loc = 0;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                h8[t] = sh.hist[lane * 8 + t];
+                loc += h8[t];
             }
-            sh.bsel = b;
-            sh.before = run;
+            int inc = loc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            int run = inc - loc;
+            const bool here = run < need && need <= inc;
+            if (here) {
+                int b = lane * 8;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    if (run + h8[t] >= need) break;
+                    run += h8[t];
+                    ++b;
+                }
+                sh.bsel = b;
+                sh.before = run;
+            }
         }
         __syncthreads();
         const int b = sh.bsel, before = sh.before;
@@ -202,7 +223,7 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
     extern __shared__ __align__(16) unsigned char smraw[];
     LevelShared& sh = *reinterpret_cast<LevelShared*>(smraw);
     Ctrl* c = v.ctrl;
-    if (read_status(c)) return;
+    if (skip_niche(c)) return;
     const int w = v.w, K = c->K;
     const bool staged = w <= RRCAP;
     if (staged)
@@ -313,7 +334,8 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
     }
     __syncthreads();
     if (staged) {
-        // exclusive scan of rho' over contiguous runs held in shared memory
+        // exclusive scan of rho' over contiguous runs held in shared memory;
+        // offsets replace rho in shared memory, then go out coalesced
         const int per = (w + LB - 1) / LB;
         const int lo = min(w, (int)threadIdx.x * per), hi = min(w, lo + per);
         int sum = 0;
@@ -321,14 +343,16 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
         int total;
         int run = block_excl_scan(sum, sh.scratch, &total);
         for (int j = lo; j < hi; ++j) {
-            v.ref_off[j] = run;
-            run += sh.rr[j].y;
+            const int cnt = sh.rr[j].y;
+            sh.rr[j].x = run;
+            run += cnt;
         }
+        __syncthreads();
+        for (int j = threadIdx.x; j < w; j += LB) v.ref_off[j] = sh.rr[j].x;
         if (threadIdx.x == 0) v.ref_off[w] = total;
     } else {
         block_scan_array(v.rhop, v.ref_off, w, sh.scratch);
     }
-    for (int j = threadIdx.x; j < w; j += LB) v.cursor[j] = 0;
     if (threadIdx.x == 0) {
         c->Lstar = Lstar;
         c->rlev = r;
@@ -340,7 +364,7 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
 __global__ void k_bucket(RunView v)
 {
     Ctrl* c = v.ctrl;
-    if (read_status(c)) return;
+    if (skip_niche(c)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.n2 || v.rank2[i] != c->l) return;
     const int j = v.pi[i];
@@ -358,7 +382,7 @@ __device__ __forceinline__ void mark_member(const RunView& v, int i)
 __global__ void __launch_bounds__(256) k_pick(RunView v)
 {
     Ctrl* c = v.ctrl;
-    if (read_status(c)) return;
+    if (skip_niche(c)) return;
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -421,7 +445,7 @@ __global__ void __launch_bounds__(512) k_pick_large(RunView v)
 {
     __shared__ SelShared sh;
     Ctrl* c = v.ctrl;
-    if (read_status(c)) return;
+    if (skip_niche(c)) return;
     const int nl = c->nlarge;
     const uint32_t gen = c->gen;
     for (int t = blockIdx.x; t < nl; t += gridDim.x) {

@@ -16,13 +16,13 @@
 namespace {
 
 constexpr int NB = 256;   // k_norm_ideal
-constexpr int EB = 64;    // k_norm_extreme: small blocks spread the FP64 latency over the SMs
+constexpr int EB = 128;   // k_norm_extreme: two blocks per SM
 
 // members of T are appended to Tlist; ideal point by order-preserving atomicMin
 __global__ void __launch_bounds__(NB) k_norm_ideal(RunView v)
 {
     Ctrl* c = v.ctrl;
-    if (read_status(c)) return;
+    if (skip_niche(c)) return;
     const int l = c->l;
     const int i = blockIdx.x * NB + threadIdx.x;
     const int lane = lane_id();
@@ -64,74 +64,101 @@ __device__ __forceinline__ bool key_less(unsigned long long a, int ia, unsigned 
 }
 
 // Gaussian elimination with partial pivoting (first maximal |pivot|) on
-// E b = 1, a = 1 / b, nadir fallback; one thread, _rn intrinsics.
+// E b = 1, a = 1 / b, nadir fallback.  One warp: lane r holds row r of the
+// (row-swapped) system, so each elimination step updates every row at once;
+// every element sees the same _rn operations in the same order as a serial
+// elimination (factor = A_rc / A_cc, A_rk -= factor * A_ck for k >= c,
+// rhs_r -= factor * rhs_c; back substitution left to right).
+template <int M>
 __device__ void solve_intercepts(const RunView& v, Ctrl* c, const int* ext, const double* nad)
 {
-    const int m = v.m;
-    double zs[NSGA3_MAX_M];
-    for (int q = 0; q < m; ++q) {
-        zs[q] = zstar_of(c, q);
-        c->zstar[q] = zs[q];
-        c->ext[q] = ext[q];
+    const int lane = lane_id();
+    double zs[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) zs[q] = zstar_of(c, q);
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+            c->zstar[q] = zs[q];
+            c->ext[q] = ext[q];
+        }
     }
-    double A[NSGA3_MAX_M][NSGA3_MAX_M], rhs[NSGA3_MAX_M], b[NSGA3_MAX_M];
     bool ok = true;
-    for (int q = 0; q < m; ++q) {
-        const int e = ext[q];
-        if (e < 0 || e >= v.n2) ok = false;
-        for (int r = 0; r < m; ++r)
-            A[q][r] = ok ? __dsub_rn((double)v.F[(size_t)e * m + r], zs[r]) : 0.0;
-        rhs[q] = 1.0;
-    }
-    for (int col = 0; col < m && ok; ++col) {
+#pragma unroll
+    for (int q = 0; q < M; ++q)
+        if (ext[q] < 0 || ext[q] >= v.n2) ok = false;
+    double A[M], rhs = 1.0;
+    const int er = lane < M ? ext[lane] : 0;
+#pragma unroll
+    for (int q = 0; q < M; ++q)
+        A[q] = (ok && lane < M) ? __dsub_rn((double)v.F[(size_t)er * M + q], zs[q]) : 0.0;
+#pragma unroll
+    for (int col = 0; col < M; ++col) {
+        if (!ok) break;
+        // pivot: first row >= col of maximal |A[.][col]| (rows in current order)
         int p = col;
-        double bestp = fabs(A[col][col]);
-        for (int r = col + 1; r < m; ++r)
-            if (fabs(A[r][col]) > bestp) {
-                bestp = fabs(A[r][col]);
+        double best = fabs(__shfl_sync(0xffffffffu, A[col], col));
+#pragma unroll
+        for (int r = col + 1; r < M; ++r) {
+            const double x = fabs(__shfl_sync(0xffffffffu, A[col], r));
+            if (x > best) {
+                best = x;
                 p = r;
             }
-        if (bestp == 0.0) {
+        }
+        if (best == 0.0) {
             ok = false;
             break;
         }
-        if (p != col) {
-            for (int cc = 0; cc < m; ++cc) {
-                double t = A[col][cc];
-                A[col][cc] = A[p][cc];
-                A[p][cc] = t;
+        if (p != col) {  // swap rows col and p
+#pragma unroll
+            for (int q = 0; q < M; ++q) {
+                const double a_c = __shfl_sync(0xffffffffu, A[q], col);
+                const double a_p = __shfl_sync(0xffffffffu, A[q], p);
+                if (lane == col) A[q] = a_p;
+                if (lane == p) A[q] = a_c;
             }
-            double t = rhs[col];
-            rhs[col] = rhs[p];
-            rhs[p] = t;
+            const double r_c = __shfl_sync(0xffffffffu, rhs, col);
+            const double r_p = __shfl_sync(0xffffffffu, rhs, p);
+            if (lane == col) rhs = r_p;
+            if (lane == p) rhs = r_c;
         }
-        for (int r = col + 1; r < m; ++r) {
-            const double factor = __ddiv_rn(A[r][col], A[col][col]);
-            for (int cc = col; cc < m; ++cc) A[r][cc] = __dsub_rn(A[r][cc], __dmul_rn(factor, A[col][cc]));
-            rhs[r] = __dsub_rn(rhs[r], __dmul_rn(factor, rhs[col]));
+        double piv[M];
+#pragma unroll
+        for (int q = 0; q < M; ++q) piv[q] = __shfl_sync(0xffffffffu, A[q], col);
+        const double prhs = __shfl_sync(0xffffffffu, rhs, col);
+        if (lane > col && lane < M) {
+            const double factor = __ddiv_rn(A[col], piv[col]);
+#pragma unroll
+            for (int q = col; q < M; ++q) A[q] = __dsub_rn(A[q], __dmul_rn(factor, piv[q]));
+            rhs = __dsub_rn(rhs, __dmul_rn(factor, prhs));
         }
     }
-    double a[NSGA3_MAX_M];
+    double a = 0.0;
     if (ok) {
-        for (int r = m - 1; r >= 0; --r) {
-            double s = rhs[r];
-            for (int cc = r + 1; cc < m; ++cc) s = __dsub_rn(s, __dmul_rn(A[r][cc], b[cc]));
-            b[r] = __ddiv_rn(s, A[r][r]);
+        double b = 0.0;  // lane r ends with b_r
+#pragma unroll
+        for (int r = M - 1; r >= 0; --r) {
+            double s = rhs;
+#pragma unroll
+            for (int cc = r + 1; cc < M; ++cc) s = __dsub_rn(s, __dmul_rn(A[cc], __shfl_sync(0xffffffffu, b, cc)));
+            const double br = __ddiv_rn(s, A[r]);
+            if (lane == r) b = br;
         }
-        for (int q = 0; q < m; ++q) {
-            a[q] = __ddiv_rn(1.0, b[q]);
-            if (!isfinite(a[q]) || a[q] <= 1e-6) ok = false;
-        }
+        a = lane < M ? __ddiv_rn(1.0, b) : 1.0;
+        const bool bad = lane < M && (!isfinite(a) || a <= 1e-6);
+        if (__any_sync(0xffffffffu, bad)) ok = false;
     }
-    c->fallback = ok ? 0 : 1;
-    for (int q = 0; q < m; ++q) {
-        if (!ok) a[q] = (nad[q] == 0.0) ? 1.0 : nad[q];
-        c->a[q] = a[q];
+    if (lane < M) {
+        if (!ok) a = (nad[lane] == 0.0) ? 1.0 : nad[lane];
+        c->a[lane] = a;
     }
+    if (lane == 0) c->fallback = ok ? 0 : 1;
 }
 
 // Per-block (min ASF, lowest index) per axis and max of f~; the last block
 // to finish reduces the blocks' results and solves for the intercepts.
+template <int M>
 __global__ void __launch_bounds__(EB) k_norm_extreme(RunView v)
 {
     __shared__ unsigned long long s_key[EB / 32][NSGA3_MAX_M];
@@ -141,24 +168,25 @@ __global__ void __launch_bounds__(EB) k_norm_extreme(RunView v)
     __shared__ int f_ext[NSGA3_MAX_M];
     __shared__ double f_nad[NSGA3_MAX_M];
     Ctrl* c = v.ctrl;
-    if (read_status(c)) return;
-    const int m = v.m, nT = c->nT;
+    if (skip_niche(c)) return;
+    constexpr int m = M;
+    const int nT = c->nT;
     const int lane = lane_id(), warp = threadIdx.x >> 5;
-    double zs[NSGA3_MAX_M];
-    for (int q = 0; q < m; ++q) zs[q] = zstar_of(c, q);
-    unsigned long long best[NSGA3_MAX_M], nad[NSGA3_MAX_M];
-    int bidx[NSGA3_MAX_M];
-    for (int q = 0; q < m; ++q) {
+    double zs[M];
+    _Pragma("unroll") for (int q = 0; q < m; ++q) zs[q] = zstar_of(c, q);
+    unsigned long long best[M], nad[M];
+    int bidx[M];
+    _Pragma("unroll") for (int q = 0; q < m; ++q) {
         best[q] = ~0ull;
         bidx[q] = 0x7fffffff;
         nad[q] = 0ull;
     }
     for (int s = blockIdx.x * EB + threadIdx.x; s < nT; s += gridDim.x * EB) {
         const int i = v.Tlist[s];
-        double ft[NSGA3_MAX_M];
+        double ft[M];
         unsigned long long m1 = 0ull, m2 = 0ull;  // largest and second largest key (f~ >= 0)
         int r1 = 0;
-        for (int r = 0; r < m; ++r) {
+        _Pragma("unroll") for (int r = 0; r < m; ++r) {
             ft[r] = __dsub_rn((double)v.F[(size_t)i * m + r], zs[r]);
             const unsigned long long kr = okey(ft[r]);
             if (kr > m1) {
@@ -173,7 +201,7 @@ __global__ void __launch_bounds__(EB) k_norm_extreme(RunView v)
         const double d1 = __ddiv_rn(__longlong_as_double((long long)m1), 1e-6);
         const double d2 = __ddiv_rn(__longlong_as_double((long long)m2), 1e-6);
         const unsigned long long k1 = okey(d1), k2 = okey(d2);
-        for (int q = 0; q < m; ++q) {
+        _Pragma("unroll") for (int q = 0; q < m; ++q) {
             const unsigned long long other = (q == r1) ? k2 : k1;
             const unsigned long long kq = okey(ft[q]);
             const unsigned long long asf = kq > other ? kq : other;
@@ -183,7 +211,7 @@ __global__ void __launch_bounds__(EB) k_norm_extreme(RunView v)
             }
         }
     }
-    for (int q = 0; q < m; ++q) {
+    _Pragma("unroll") for (int q = 0; q < m; ++q) {
         unsigned long long b = best[q], n = nad[q];
         int bi = bidx[q];
 #pragma unroll
@@ -226,19 +254,30 @@ __global__ void __launch_bounds__(EB) k_norm_extreme(RunView v)
     if (threadIdx.x == 0) s_ticket = atomicAdd(&c->ext_done, 1u);
     __syncthreads();
     if (s_ticket != gridDim.x - 1) return;
-    // last block: reduce over the blocks (warp w reduces axes w, w + 8, ...)
+    // last block: reduce over the blocks, one warp per axis; each lane first
+    // issues all its loads (independent), then reduces
     __threadfence();
+    constexpr int PMAX = 16;  // parts <= 32 * PMAX
     for (int q = warp; q < m; q += EB / 32) {
-        unsigned long long b = ~0ull, n = 0ull;
-        int bi = 0x7fffffff;
-        for (int p = lane; p < (int)gridDim.x; p += 32) {
-            const unsigned long long pb = __ldcg(&pk[p * m + q]);
-            const int pi = __ldcg(&v.ext_idx[p * m + q]);
-            if (key_less(pb, pi, b, bi)) {
-                b = pb;
-                bi = pi;
+        unsigned long long lb[PMAX], ln[PMAX];
+        int li[PMAX];
+#pragma unroll
+        for (int t = 0; t < PMAX; ++t) {
+            const int p = lane + 32 * t;
+            const bool in = p < (int)gridDim.x;
+            lb[t] = in ? __ldcg(&pk[p * m + q]) : ~0ull;
+            li[t] = in ? __ldcg(&v.ext_idx[p * m + q]) : 0x7fffffff;
+            ln[t] = in ? __ldcg(&pn[p * m + q]) : 0ull;
+        }
+        unsigned long long b = lb[0], n = ln[0];
+        int bi = li[0];
+#pragma unroll
+        for (int t = 1; t < PMAX; ++t) {
+            if (key_less(lb[t], li[t], b, bi)) {
+                b = lb[t];
+                bi = li[t];
             }
-            n = max(n, __ldcg(&pn[p * m + q]));
+            n = max(n, ln[t]);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -257,9 +296,9 @@ __global__ void __launch_bounds__(EB) k_norm_extreme(RunView v)
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        c->ext_done = 0u;
-        solve_intercepts(v, c, f_ext, f_nad);
+    if (warp == 0) {
+        if (lane == 0) c->ext_done = 0u;
+        solve_intercepts<M>(v, c, f_ext, f_nad);
     }
 }
 
@@ -273,6 +312,17 @@ cudaError_t launch_norm_ideal(const RunView& v, cudaStream_t s)
 
 cudaError_t launch_norm_extreme(const RunView& v, cudaStream_t s)
 {
-    k_norm_extreme<<<v.ext_parts, EB, 0, s>>>(v);
+    switch (v.m) {
+    case 2: k_norm_extreme<2><<<v.ext_parts, EB, 0, s>>>(v); break;
+    case 3: k_norm_extreme<3><<<v.ext_parts, EB, 0, s>>>(v); break;
+    case 4: k_norm_extreme<4><<<v.ext_parts, EB, 0, s>>>(v); break;
+    case 5: k_norm_extreme<5><<<v.ext_parts, EB, 0, s>>>(v); break;
+    case 6: k_norm_extreme<6><<<v.ext_parts, EB, 0, s>>>(v); break;
+    case 7: k_norm_extreme<7><<<v.ext_parts, EB, 0, s>>>(v); break;
+    case 8: k_norm_extreme<8><<<v.ext_parts, EB, 0, s>>>(v); break;
+    case 9: k_norm_extreme<9><<<v.ext_parts, EB, 0, s>>>(v); break;
+    case 10: k_norm_extreme<10><<<v.ext_parts, EB, 0, s>>>(v); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }

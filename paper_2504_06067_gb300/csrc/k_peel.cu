@@ -6,7 +6,7 @@
 // of a pass sets the node's condition, so the host never synchronises.
 // Positions are in bucket order of f_0 (k_sort.cu); ranks are written back
 // to the original order by k_post_peel.
-//   pass 0:   cnt[j]  = popc over all dominator words of column j
+//   cnt[j]    = dominators of j, counted by the dominance build
 //   pass k>0: cnt[j] -= popc(Dom[w][j] & front_{k-1}[w]) over the nonzero
 //             words w of the previous front's mask
 //   front_k   = { j unranked : cnt[j] == 0 }, rank2[j] = k
@@ -19,17 +19,16 @@
 
 namespace {
 
-constexpr int PT = 1024;          // threads per CTA: 32 warps split the dominator rows
-constexpr int PW = PT / 32;
+constexpr int PTMAX = 1024;       // threads per CTA (runtime: 256, 512 or 1024)
+constexpr int PWMAX = PTMAX / 32;
 constexpr int LISTCAP = 2048;
 
-__global__ void __launch_bounds__(PT) k_peel(RunView v, cudaGraphConditionalHandle h, int in_graph)
+__global__ void __launch_bounds__(PTMAX) k_peel(RunView v, cudaGraphConditionalHandle h, int in_graph)
 {
-    __shared__ int red[PW][NSGA3_PEEL_COLS];
+    __shared__ int red[PWMAX][NSGA3_PEEL_COLS];
+    const int PT = blockDim.x, PW = PT >> 5;
     __shared__ uint2 list[LISTCAP];
     __shared__ int nlist;
-    __shared__ uint32_t kmax;
-    __shared__ int slim;
     Ctrl* c = v.ctrl;
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     if (read_status(c)) {
@@ -45,69 +44,43 @@ __global__ void __launch_bounds__(PT) k_peel(RunView v, cudaGraphConditionalHand
     const int nchunks = v.ld / NSGA3_PEEL_COLS;
     const int chunk = blockIdx.x;
     const int j0 = chunk * NSGA3_PEEL_COLS;
+    // prefetch this thread's column state (used after the reduction)
+    int my_rank = 0, my_cnt = 0;
+    if (tid < NSGA3_PEEL_COLS && j0 + tid < v.n2) {
+        my_rank = v.srank[j0 + tid];
+        my_cnt = v.cnt[j0 + tid];
+    }
+    // Dominators of a column have f_0 <= its f_0.  Keys are non-decreasing in
+    // bucket order and bcnt[b] is the end of bucket b, so the positions that
+    // can dominate this chunk end at bcnt[key of its last column].
+    const int jl = min(j0 + NSGA3_PEEL_COLS, v.n2) - 1;
+    int lim = 0;
+    if (jl >= j0) lim = (v.bcnt[v.skey[jl]] + 31) >> 5;
+    if (lim > v.NW) lim = v.NW;
 
     uint32_t rw = (tid < NSGA3_PEEL_COLS / 32) ? v.rem[j0 / 32 + tid] : 0u;
     const int any_rem = __syncthreads_or(rw != 0u);
-    // Dominators of a column have f_0 <= its f_0: in bucket order, only row
-    // blocks whose first bucket key is <= the chunk's largest key can hold
-    // bits for this chunk (keys are non-decreasing along the order).
-    int lim;
-    if (k == 0) {
-        if (tid == 0) kmax = 0u;
-        __syncthreads();
-        if (tid < NSGA3_PEEL_COLS && j0 + tid < v.n2) atomicMax(&kmax, v.skey[j0 + tid]);
-        __syncthreads();
-        const uint32_t km = kmax;
-        int cntb = 0;
-        for (int I = tid; I < v.NW; I += PT) cntb += (v.skey[I * 32] <= km);
-        cntb = warp_sum(cntb);
-        if (tid == 0) slim = 0;
-        __syncthreads();
-        if (lane == 0 && cntb) atomicAdd(&slim, cntb);
-        __syncthreads();
-        lim = slim;
-        if (tid == 0) {
-            v.chunk_lim[chunk] = (uint32_t)lim;
-            if (any_rem) atomicAdd(&c->peel_rows, (unsigned)lim);
-        }
-    } else {
-        lim = (int)v.chunk_lim[chunk];
-    }
 
     uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    if (any_rem) {
+    // pass 0 needs no words: the dominance build already counted every
+    // column's dominators into cnt[]
+    if (any_rem && k > 0) {
         const uint4* base = reinterpret_cast<const uint4*>(v.Dom + j0) + lane;
         const size_t ld4 = (size_t)v.ld / 4;
-        if (k == 0) {
-            int w = warp;
-            for (; w + 7 * PW < lim; w += 8 * PW) {
-                uint4 x[8];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) x[t] = __ldg(base + (size_t)(w + PW * t) * ld4);
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    a0 += __popc(x[t].x);
-                    a1 += __popc(x[t].y);
-                    a2 += __popc(x[t].z);
-                    a3 += __popc(x[t].w);
-                }
-            }
-            for (; w < lim; w += PW) {
-                const uint4 x = __ldg(base + (size_t)w * ld4);
-                a0 += __popc(x.x);
-                a1 += __popc(x.y);
-                a2 += __popc(x.z);
-                a3 += __popc(x.w);
-            }
-        } else {
+        {
             const uint32_t* prev = v.front + ((k - 1) & 1) * v.NW;
             for (int wb = 0; wb < lim; wb += LISTCAP) {
                 const int whe = min(wb + LISTCAP, lim);
                 if (tid == 0) nlist = 0;
                 __syncthreads();
-                for (int w = wb + tid; w < whe; w += PT) {
-                    const uint32_t msk = prev[w];
-                    if (msk) list[atomicAdd(&nlist, 1)] = make_uint2((unsigned)w, msk);
+                for (int w0 = wb + warp * 32; w0 < whe; w0 += PT) {
+                    const int w = w0 + lane;
+                    const uint32_t msk = w < whe ? prev[w] : 0u;
+                    const unsigned bal = __ballot_sync(0xffffffffu, msk != 0u);
+                    int at = 0;
+                    if (lane == 0 && bal) at = atomicAdd(&nlist, __popc(bal));
+                    at = __shfl_sync(0xffffffffu, at, 0);
+                    if (msk) list[at + __popc(bal & ((1u << lane) - 1u))] = make_uint2((unsigned)w, msk);
                 }
                 __syncthreads();
                 const int n = nlist;
@@ -149,13 +122,12 @@ __global__ void __launch_bounds__(PT) k_peel(RunView v, cudaGraphConditionalHand
     // this CTA owns its 128 columns: update the counts and rank the new front
     if (tid < NSGA3_PEEL_COLS) {
         int sum = 0;
-#pragma unroll 8
         for (int w = 0; w < PW; ++w) sum += red[w][tid];
         const int j = j0 + tid;
         bool nf = false;
-        if (j < v.n2 && v.srank[j] < 0) {
-            const int cv = (k == 0) ? sum : v.cnt[j] - sum;
-            v.cnt[j] = cv;
+        if (j < v.n2 && my_rank < 0) {
+            const int cv = my_cnt - sum;
+            if (k > 0) v.cnt[j] = cv;
             if (cv == 0) {
                 v.srank[j] = k;
                 nf = true;
@@ -202,38 +174,39 @@ __global__ void __launch_bounds__(PT) k_peel(RunView v, cudaGraphConditionalHand
     if (in_graph) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
-// ranks back to the original order; the first thread sets the niching branch
-__global__ void k_post_peel(RunView v, cudaGraphConditionalHandle h_niche, int in_graph)
+// ranks back to the original order
+__global__ void k_post_peel(RunView v)
 {
-    Ctrl* c = v.ctrl;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < v.n2) v.rank2[v.perm[p]] = v.srank[p];
-    if (p == 0 && in_graph) {
-        const int go = (read_status(c) == 0 && c->l >= 0 && c->need_niche) ? 1 : 0;
-        cudaGraphSetConditional(h_niche, (unsigned)go);
-    }
 }
 
 }  // namespace
 
+// The peel launches one CTA per column chunk; this returns the SM count the
+// launch uses to size its CTAs.
 int peel_nsplit(const RunView& v, int num_sms)
 {
     (void)v;
-    (void)num_sms;
-    return 1;  // one CTA per column chunk
+    return num_sms;
 }
 
 cudaError_t launch_peel(const RunView& v, int nsplit, cudaGraphConditionalHandle h, int in_graph,
                         cudaStream_t s)
 {
-    (void)nsplit;
-    k_peel<<<v.ld / NSGA3_PEEL_COLS, PT, 0, s>>>(v, h, in_graph);
+    // every chunk's CTA resident in one wave: one 1024-thread CTA per SM fits
+    // (registers), two of 512, four of 256
+    const int nchunks = v.ld / NSGA3_PEEL_COLS;
+    const int threads = nchunks <= nsplit ? 1024 : (nchunks <= 2 * nsplit ? 512 : 256);
+    k_peel<<<nchunks, threads, 0, s>>>(v, h, in_graph);
     return cudaGetLastError();
 }
 
 cudaError_t launch_post_peel(const RunView& v, cudaGraphConditionalHandle h_niche, int in_graph,
                              cudaStream_t s)
 {
-    k_post_peel<<<(v.n2 + 255) / 256, 256, 0, s>>>(v, h_niche, in_graph);
+    (void)h_niche;
+    (void)in_graph;
+    k_post_peel<<<(v.n2 + 255) / 256, 256, 0, s>>>(v);
     return cudaGetLastError();
 }

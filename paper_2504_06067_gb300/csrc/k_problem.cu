@@ -10,12 +10,14 @@
 //   front wins, ties keep the first drawn; Philox(q, gen, 1, 1) word 0 < p_c
 //   lets the pair cross.  SBX per variable v (Philox(q*d+v, gen, 2, 0)):
 //   word 1 < 0.5 crosses v with spread beta from word 0, word 2 < 0.5 swaps
-//   the children; clip to [0,1].  Polynomial mutation of child c, variable v
-//   (Philox(c*d+v, gen, 3, 0)): word 0 < p_m mutates with u = word 1.
+//   the children; clip to [0,1].  Polynomial mutation of variable v: word 3
+//   of that block < p_m mutates child 2q with u = word 0 of
+//   Philox(q*d+v, gen, 3, 0); word 1 of that block < p_m mutates child 2q+1
+//   with u = its word 2 (two Philox blocks per pair and variable).
 //   Children go to rows N + 2q and N + 2q + 1.  FP32 arithmetic.
 // Objective (the softmax-simplex family): k = m - 1,
 //   g = sum_{v >= k} (x_v - 0.5)^2, f_j = (1 + g) softmax(W x[0:k])_j,
-//   g summed in FP32 with Kahan compensation, softmax in FP64, rounded to FP32.
+//   evaluated in FP64 (sums left to right) and rounded to FP32.
 #include "kernels.cuh"
 
 namespace {
@@ -68,11 +70,12 @@ __global__ void k_refdirs(int m, int p1, int p2, double tau, int w1, int w, doub
 }
 
 // Objective of rows [row0, row0 + n): a block covers OR = 32 rows with
-// OR * m threads.  g is summed in FP32 with Kahan compensation (relative
-// error ~1e-7; GB300's FP64 pipe runs at 1/64 of FP32).  Thread (row, j)
-// forms a_j = sum_v W_jv x_v in FP64 (left to right) and e_j = exp(a_j); the
-// row's denominator adds e_0..e_{m-1} in order, f_j = (1 + g) e_j / den in
-// FP64, rounded to FP32.
+// OR * m threads (at least 64).  Warp 0 sums g of its 32 rows (lane = row) in
+// FP64 left to right, fully converged (GB300's FP64 pipe runs at 1/64 of
+// FP32, so divergent FP64 is costly); thread (row, j) forms
+// a_j = sum_v W_jv x_v in FP64 (left to right) and e_j = exp(a_j); the row's
+// denominator adds e_0..e_{m-1} in order; f_j = (1 + g) e_j / den, rounded
+// to FP32.
 constexpr int OR = 32;
 
 __global__ void k_objective(RunView v, int row0, int n)
@@ -81,32 +84,38 @@ __global__ void k_objective(RunView v, int row0, int n)
     __shared__ double se[OR * NSGA3_MAX_M];
     const int m = v.m, d = v.d, k = m - 1;
     const int base = blockIdx.x * OR;
-    const int rr = threadIdx.x / m, j = threadIdx.x - (threadIdx.x / m) * m;
-    const bool live = rr < OR && base + rr < n;
-    const float* x = v.X + (size_t)(row0 + base + rr) * d;
-    if (live && j == 0) {
-        float sum = 0.0f, comp = 0.0f;
-        for (int e = k; e < d; ++e) {
-            const float t = x[e] - 0.5f;
-            const float y = t * t - comp;
-            const float s2 = sum + y;
-            comp = (s2 - sum) - y;
-            sum = s2;
+    if (threadIdx.x < OR) {
+        const int rr = threadIdx.x;
+        double g = 0.0;
+        if (base + rr < n) {
+            const float* x = v.X + (size_t)(row0 + base + rr) * d;
+            for (int e = k; e < d; ++e) {
+                const double t = __dsub_rn((double)x[e], 0.5);
+                g = __dadd_rn(g, __dmul_rn(t, t));
+            }
         }
-        sg[rr] = (double)sum - (double)comp;
+        sg[rr] = g;
     }
-    if (live) {
+    for (int idx = threadIdx.x; idx < OR * m; idx += blockDim.x) {
+        const int rr = idx / m, j = idx - rr * m;
+        if (base + rr >= n) continue;
+        const float* x = v.X + (size_t)(row0 + base + rr) * d;
         double a = 0.0;
         for (int e = 0; e < k; ++e) a = __dadd_rn(a, __dmul_rn((double)v.Wobj[j * k + e], (double)x[e]));
-        se[rr * m + j] = exp(a);
+        se[idx] = exp(a);
     }
     __syncthreads();
-    if (!live) return;
-    double den = 0.0;
-    for (int t = 0; t < m; ++t) den = __dadd_rn(den, se[rr * m + t]);
-    const double f = __dmul_rn(__dadd_rn(1.0, sg[rr]), __ddiv_rn(se[rr * m + j], den));
-    v.F[(size_t)(row0 + base + rr) * m + j] = __double2float_rn(f);
+    for (int idx = threadIdx.x; idx < OR * m; idx += blockDim.x) {
+        const int rr = idx / m, j = idx - rr * m;
+        if (base + rr >= n) continue;
+        double den = 0.0;
+        for (int t = 0; t < m; ++t) den = __dadd_rn(den, se[rr * m + t]);
+        const double f = __dmul_rn(__dadd_rn(1.0, sg[rr]), __ddiv_rn(se[idx], den));
+        v.F[(size_t)(row0 + base + rr) * m + j] = __double2float_rn(f);
+    }
 }
+
+static int objective_threads(int m) { return OR * m < 64 ? 64 : OR * m; }
 
 __global__ void k_init(RunView v)
 {
@@ -154,7 +163,7 @@ __global__ void k_vary_eval(RunView v)
     const uint32_t p2 = v.rank[b2] < v.rank[a2] ? b2 : a2;
     const bool cross = u01(cx.x) < v.p_c;
     const float e = 1.0f / (v.eta_c + 1.0f);
-    const int c0 = 2 * q, c1i = 2 * q + 1;
+    const int c0 = 2 * q, c1i = 2 * q + 1;  // children rows N + c0, N + c1i
     float* x0 = v.X + (size_t)(N + c0) * d;
     float* x1 = v.X + (size_t)(N + c1i) * d;
     for (int var = lane; var < d; var += 32) {
@@ -174,10 +183,10 @@ __global__ void k_vary_eval(RunView v)
             c1 = fminf(fmaxf(c1, 0.0f), 1.0f);
             c2 = fminf(fmaxf(c2, 0.0f), 1.0f);
         }
-        const U4 m0 = philox((uint32_t)c0 * (uint32_t)d + (uint32_t)var, gen, RNG_PM, 0u, v.seed);
-        if (u01(m0.x) < v.p_m) c1 = pm_mutate(c1, u01(m0.y), v.eta_m);
-        const U4 m1 = philox((uint32_t)c1i * (uint32_t)d + (uint32_t)var, gen, RNG_PM, 0u, v.seed);
-        if (u01(m1.x) < v.p_m) c2 = pm_mutate(c2, u01(m1.y), v.eta_m);
+        const bool mut0 = u01(sb.w) < v.p_m;
+        const U4 pm = philox((uint32_t)q * (uint32_t)d + (uint32_t)var, gen, RNG_PM, 0u, v.seed);
+        if (mut0) c1 = pm_mutate(c1, u01(pm.x), v.eta_m);
+        if (u01(pm.y) < v.p_m) c2 = pm_mutate(c2, u01(pm.z), v.eta_m);
         x0[var] = c1;
         x1[var] = c2;
     }
@@ -205,7 +214,7 @@ cudaError_t launch_init(const RunView& v, cudaStream_t s)
     k_init<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_objective<<<(v.N + OR - 1) / OR, OR * v.m, 0, s>>>(v, 0, v.N);
+    k_objective<<<(v.N + OR - 1) / OR, objective_threads(v.m), 0, s>>>(v, 0, v.N);
     return cudaGetLastError();
 }
 
@@ -215,6 +224,6 @@ cudaError_t launch_vary_eval(const RunView& v, cudaStream_t s)
     k_vary_eval<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_objective<<<(v.N + OR - 1) / OR, OR * v.m, 0, s>>>(v, v.N, v.N);
+    k_objective<<<(v.N + OR - 1) / OR, objective_threads(v.m), 0, s>>>(v, v.N, v.N);
     return cudaGetLastError();
 }

@@ -116,13 +116,17 @@ def _igd(orc, F, rank, W, m):
 
 
 def test_igd_matches_oracle_median(n, orc):
-    """m = 3, N = 92, p = 12, d = 12, 100 generations, seeds 0..4: the median
-    IGD of the GPU runs is within 2% of the oracle runs' median."""
+    """m = 3, N = 92, p = 12, d = 12, 100 generations: the median IGD of the
+    GPU runs is within 2% of the oracle runs' median.  GPU and oracle runs of
+    one seed separate after a few generations (FP32 vs FP64 variation
+    arithmetic), so the medians compare two samples of one distribution whose
+    seed-to-seed spread is ~1.6%; 16 seeds keep the medians' noise near 0.5%
+    (5 seeds would fail a correct implementation about one time in eight)."""
     cfg = wl.SMALL
     W = wl.objective_weights(cfg.m, 0)
     Z = orc.refdirs(cfg.m, cfg.p1)
     gi, oi = [], []
-    for seed in range(5):
+    for seed in range(16):
         with Run(n, cfg.m, cfg.d, cfg.N, cfg.p1, seed=seed, W=W) as r:
             r.check(n.nsga3_init(r.ctx, None))
             r.check(n.nsga3_run(r.ctx, cfg.generations, None))
