@@ -183,6 +183,45 @@ nsga3_status nsga3_phase_times(nsga3_ctx* ctx, float* ms, int n);
  * (fixed launches plus one per peel pass).  Synchronous. */
 nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches);
 
+/*
+ * Largest n accepted by nsga3_rank_noalloc. */
+#define NSGA3_NOALLOC_MAX_N 2048
+
+/*
+ * Non-dominated sorting ranks of n points, with no device allocation and no
+ * context.  The paper has no counterpart: it is a convenience for callers
+ * that cannot allocate device memory -- code enqueueing work while a stream
+ * is captured into a CUDA graph (allocation is not a stream operation),
+ * real-time loops whose allocator use is forbidden, and plug-ins that a host
+ * application only gives pre-reserved memory.  nsga3_create allocates its
+ * workspace, so none of them can use nsga3_select.
+ *
+ *   objs   device, n x m FP32 objectives, row-major, minimised
+ *   n      1 <= n <= NSGA3_NOALLOC_MAX_N
+ *   m      2 <= m <= 10
+ *   ranks  device, n int32 outputs: 0 for the first non-dominated front,
+ *          1 for the next, ... (the front index of every point, as
+ *          nsga3_select gives it with full_sort = 1).  Comparisons are IEEE:
+ *          a NaN objective makes a point neither dominate nor be dominated.
+ *   stream cudaStream_t as void* (NULL = legacy default stream); the call is
+ *          asynchronous and stream-ordered.
+ *
+ * Workspace: one statically sized __device__ array (about 530 KB) that every
+ * GPU on which this library is loaded holds until the process exits.  The
+ * first call on a device, with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call on a device shares the array, which keeps the
+ * last call's contents; each call clears what must start at zero itself.
+ * Calls whose executions overlap on the GPU (other streams, other host
+ * threads) race on the array: order them on one stream or with events.
+ *
+ * Returns NSGA3_EINVAL, enqueuing nothing, when a pointer is NULL, n is out
+ * of [1, NSGA3_NOALLOC_MAX_N] or m out of [2, 10]; NSGA3_ECUDA when there is
+ * no usable device or the address lookup or the launch fails.  The call sets
+ * no message for nsga3_last_error.
+ */
+nsga3_status nsga3_rank_noalloc(const float* objs, int n, int m, int32_t* ranks, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,8 @@ if not os.path.exists(LIB_PATH):
 
 _lib = C.CDLL(LIB_PATH)
 
+NOALLOC_MAX_N = 2048  # NSGA3_NOALLOC_MAX_N
+
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, EINTERNAL = range(8)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE",
                 5: "ETIMEOUT", 6: "ESTATE", 7: "EINTERNAL"}
@@ -67,6 +69,7 @@ _SIGS = {
     "nsga3_get_association": (_I, [_CTX, _P, _P]),
     "nsga3_phase_times": (_I, [_CTX, _P, _I]),
     "nsga3_last_launches": (_I, [_CTX, _P]),
+    "nsga3_rank_noalloc": (_I, [_P, _I, _I, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -109,3 +112,16 @@ def create(m, d, N, ref_divisions, opts=None):
 def run_batch(ctxs, generations, stream=0):
     arr = (_CTX * len(ctxs))(*ctxs)
     return nsga3_run_batch(arr, len(ctxs), generations, stream)
+
+
+def rank_noalloc(objs_ptr, n, m, ranks_ptr, stream=0):
+    """nsga3_rank_noalloc with a descriptive error; pointers are device
+    addresses of n x m FP32 objectives and n int32 ranks."""
+    st = nsga3_rank_noalloc(objs_ptr, n, m, ranks_ptr, stream)
+    if st == EINVAL:
+        raise NSGA3Error(st, "nsga3_rank_noalloc takes 1 <= n <= %d points (got %d), "
+                             "2 <= m <= 10 (got %d) and non-NULL pointers"
+                         % (NOALLOC_MAX_N, n, m))
+    if st != OK:
+        raise NSGA3Error(st, "nsga3_rank_noalloc: CUDA device lookup or launch failed")
+    return st
