@@ -45,10 +45,13 @@ LANES_PER_SM = 128
 def parse_args(argv=None):
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=500)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed generations (default: the workload's run length)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=sorted(WORKLOADS), default="scale")
+    p.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served"], default="scale")
+    p.add_argument("--runs", type=int, default=64, help="batched: independent runs")
+    p.add_argument("--requests", type=int, default=None, help="served: requests of the stream")
     p.add_argument("--cpu-budget", type=float, default=20.0,
                    help="seconds of oracle work for the cpu_baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -343,6 +346,141 @@ def run_ours(args, world, rank, local):
     return line
 
 
+# ---------------------------------------------------------------- batched ----
+def run_batched(args, world, rank, local):
+    """64 uneven independent runs (N log-uniform in [100, 20000], m in
+    {3, 5, 8}, d = m + 19): one batched CUDA graph per generation against the
+    plain path (each run alone, one graph launch per generation, runs one
+    after another).  A step is one generation of every run; both arms time
+    initialisation + `steps` generations of all runs, and the batched arm
+    also the read-back of every final population (e2e)."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    from paper_2504_06067_gb300 import native as n
+
+    gens = args.steps
+    cfgs = wl.batched_configs(n_runs=args.runs, seed=0, generations=gens)
+    Ws = [wl.objective_weights(c.m, c.seed) for c in cfgs]
+    ctxs = []
+    for c, W in zip(cfgs, Ws):
+        o = n.default_opts(seed=c.seed + 1000003 * rank, W=W.ctypes.data)
+        ctxs.append(n.create(c.m, c.d, c.N, c.p1, o))
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    hosts = [(torch.empty((c.N, c.d), dtype=torch.float32).pin_memory(),
+              torch.empty((c.N, c.m), dtype=torch.float32).pin_memory(),
+              torch.empty(c.N, dtype=torch.int32).pin_memory()) for c in cfgs]
+
+    def launches():
+        tot = C.c_int64()
+        s = 0
+        for x in ctxs:
+            n.check(n.nsga3_total_launches(x, C.byref(tot)), x)
+            s += tot.value
+        return s
+
+    def plain():
+        for x in ctxs:
+            n.check(n.nsga3_init(x, sh), x)
+            n.check(n.nsga3_run(x, gens, sh), x)
+
+    def batched():
+        for x in ctxs:
+            n.check(n.nsga3_init(x, sh), x)
+        n.check(n.run_batch(ctxs, gens, sh), ctxs[0])
+
+    def read_back():
+        for x, (X, F, R) in zip(ctxs, hosts):
+            n.check(n.nsga3_get_population(x, X.data_ptr(), F.data_ptr(), R.data_ptr(), sh), x)
+
+    # warm-up: build every graph (the batched one included)
+    for x in ctxs:
+        n.check(n.nsga3_init(x, sh), x)
+    n.check(n.run_batch(ctxs, max(args.warmup, 1), sh), ctxs[0])
+    for x in ctxs:
+        n.check(n.nsga3_run(x, max(args.warmup, 1), sh), x)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    res = {}
+    for arm, fn in (("plain", plain), ("batched", batched)):
+        barrier(dist)
+        torch.cuda.synchronize()
+        l0 = launches()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        w0 = time.perf_counter()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        read_back()
+        e2.record(stream)
+        e2.synchronize()
+        wall = time.perf_counter() - w0
+        res[arm] = {"s": reduce_max(dist, e0.elapsed_time(e1) / 1e3, "cuda"),
+                    "e2e_s": reduce_max(dist, e0.elapsed_time(e2) / 1e3, "cuda"),
+                    "wall_s": wall, "launches": launches() - l0,
+                    "pop": [tuple(t.clone() for t in h) for h in hosts]}
+        for x in ctxs:
+            st = n.nsga3_sync(x, sh)
+            if st != n.OK:
+                raise RuntimeError("device status %d in the %s arm" % (st, arm))
+    clocks = sampler.stop()
+    same = all(all(torch.equal(a, b) for a, b in zip(p, q))
+               for p, q in zip(res["plain"]["pop"], res["batched"]["pop"]))
+    for x in ctxs:
+        n.nsga3_destroy(x)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+    R = len(cfgs)
+    b, p = res["batched"], res["plain"]
+    dom_bytes = sum((2 * c.N) ** 2 / 8 for c in cfgs)
+    line = {
+        "metric": METRIC,
+        "value": world * R / b["s"],
+        "unit": "runs/s",
+        "n_gpus": world,
+        "steps": gens,
+        "warmup": max(args.warmup, 1),
+        "ms_per_step": b["s"] * 1e3 / gens,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded softmax-simplex objectives)",
+        "config": {"workload": "batched_%druns_%dgens" % (R, gens), "runs": R,
+                   "N": [c.N for c in cfgs], "m": [c.m for c in cfgs],
+                   "d": "m + 19", "seeds": "0..%d" % (R - 1),
+                   "l2": "not flushed: the runs' bit matrices alone hold %.2f GB, above the "
+                         "129 MB L2" % (dom_bytes / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "plain": {"value": world * R / p["s"], "unit": "runs/s", "ms": p["s"] * 1e3,
+                  "gpu_launches": p["launches"]},
+        "batched_vs_plain": p["s"] / b["s"],
+        "identical_populations": bool(same),
+        "gens_per_s": world * R * gens / b["s"],
+        "sols_per_s": world * sum(c.N for c in cfgs) * gens / b["s"],
+        "e2e": {"value": world * R / b["e2e_s"], "unit": "runs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": sum(c.N * (c.d + c.m + 1) * 4 for c in cfgs) / gens,
+                "note": "inputs are (m, d, N, seed, W) set at creation; the final populations "
+                        "are read back into pinned host memory inside the timed region"},
+        "gpu_launches": b["launches"],
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return line
+
+
+def run_served(args, world, rank, local):
+    raise SystemExit("served mode is not built yet")
+
+
 # ----------------------------------------------------------------- oracle ----
 def oracle_generations(cfg, budget_s, max_steps=None, warmup=0):
     """Times oracle generations of `cfg` from a seeded initial population until
@@ -417,8 +555,14 @@ def run_reference(args, world, rank):
 def main(argv=None):
     args = parse_args(argv)
     world, rank, local = dist_env()
+    if args.steps is None:
+        args.steps = {"batched": 300, "served": 0}.get(args.workload) or WORKLOADS[args.workload].generations
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batched":
+        run_batched(args, world, rank, local)
+    elif args.workload == "served":
+        run_served(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

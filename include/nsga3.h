@@ -183,6 +183,11 @@ nsga3_status nsga3_phase_times(nsga3_ctx* ctx, float* ms, int n);
  * (fixed launches plus one per peel pass).  Synchronous. */
 nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches);
 
+/* Kernel launches made on behalf of ctx since nsga3_create (the set-up
+ * kernels excluded): initialisation, variation, every replayed generation or
+ * selection and each of their peel passes.  Synchronous. */
+nsga3_status nsga3_total_launches(nsga3_ctx* ctx, int64_t* launches);
+
 /*
  * Largest n accepted by nsga3_rank_noalloc. */
 #define NSGA3_NOALLOC_MAX_N 2048

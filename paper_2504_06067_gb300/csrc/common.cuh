@@ -72,6 +72,7 @@ struct Ctrl {
     double zstar[NSGA3_MAX_M];   // ideal point (FP64, +0.0 for zero)
     double a[NSGA3_MAX_M];       // intercepts
     int32_t ext[NSGA3_MAX_M];    // extreme-point indices
+    unsigned long long passes_total;  // peel passes since the context was created
 };
 
 // Device pointers and sizes of one run, passed by value to every kernel.

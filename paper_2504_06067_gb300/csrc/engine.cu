@@ -49,6 +49,7 @@ struct nsga3_ctx {
     cudaEvent_t ev[EV_COUNT] = {};
     int nsplit = 1;
     int last_kind = 0;  // 1 = select, 2 = step
+    long long host_launches = 0;  // kernels launched by calls (peel passes counted on the device)
     bool eager = false; // NSGA3_EAGER=1: no graphs, host-driven peel loop (profiling)
     std::string err;
     // batched graph cache
@@ -663,6 +664,7 @@ nsga3_status nsga3_select(nsga3_ctx* ctx, const float* objs, int32_t* ranks, int
     } else {
         CK(cudaGraphLaunch(ctx->gx_select, s));
     }
+    ctx->host_launches += 19;
     CK(cudaMemcpyAsync(ranks, ctx->vs.rank2, (size_t)ctx->n2 * sizeof(int32_t), cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(selected, ctx->vs.sel, (size_t)ctx->N * sizeof(int32_t), cudaMemcpyDefault, s));
     ctx->last_kind = 1;
@@ -677,6 +679,7 @@ nsga3_status nsga3_init(nsga3_ctx* ctx, void* stream)
     CK(launch_init(ctx->v, s));
     k_set_gen<<<1, 1, 0, s>>>(ctx->v.ctrl, 0u);
     CK(cudaGetLastError());
+    ctx->host_launches += 3;
     return NSGA3_OK;
 }
 
@@ -685,6 +688,7 @@ nsga3_status nsga3_vary(nsga3_ctx* ctx, void* stream)
     if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
     if (!ctx->has_W) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W was NULL)");
     CK(launch_vary_eval(ctx->v, (cudaStream_t)stream));
+    ctx->host_launches += 2;
     return NSGA3_OK;
 }
 
@@ -698,6 +702,7 @@ nsga3_status nsga3_step(nsga3_ctx* ctx, void* stream)
     } else {
         CK(cudaGraphLaunch(ctx->gx_step, (cudaStream_t)stream));
     }
+    ctx->host_launches += 22;
     ctx->last_kind = 2;
     return NSGA3_OK;
 }
@@ -783,7 +788,10 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
         ctx->batch_key = key;
     }
     for (int g = 0; g < generations; ++g) CK(cudaGraphLaunch(ctx->gx_batch, (cudaStream_t)stream));
-    for (int r = 0; r < n; ++r) ctxs[r]->last_kind = 3;
+    for (int r = 0; r < n; ++r) {
+        ctxs[r]->last_kind = 3;
+        ctxs[r]->host_launches += 22LL * generations;
+    }
     return NSGA3_OK;
 }
 
@@ -915,6 +923,16 @@ nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches)
     // peel pass
     int fixed = (ctx->last_kind == 1) ? 19 : 22;
     *launches = fixed + c.passes;
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_total_launches(nsga3_ctx* ctx, int64_t* launches)
+{
+    if (!ctx || !launches) return fail(ctx, NSGA3_EINVAL, "null argument");
+    unsigned long long passes = 0;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(&passes, &ctx->v.ctrl->passes_total, sizeof passes, cudaMemcpyDeviceToHost));
+    *launches = ctx->host_launches + (long long)passes;
     return NSGA3_OK;
 }
 

@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(PTMAX) k_peel(RunView v, cudaGraphConditionalH
     const int cum = c->cum + fs;
     c->cum = cum;
     c->passes += 1;
+    c->passes_total += 1ull;
     if (c->l < 0 && cum >= v.N) {
         c->l = k;
         c->nFl = fs;

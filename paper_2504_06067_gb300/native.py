@@ -69,6 +69,7 @@ _SIGS = {
     "nsga3_get_association": (_I, [_CTX, _P, _P]),
     "nsga3_phase_times": (_I, [_CTX, _P, _I]),
     "nsga3_last_launches": (_I, [_CTX, _P]),
+    "nsga3_total_launches": (_I, [_CTX, _P]),
     "nsga3_rank_noalloc": (_I, [_P, _I, _I, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
