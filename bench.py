@@ -477,8 +477,129 @@ def run_batched(args, world, rank, local):
     return line
 
 
+def _serve(n, reqs, budget, max_active, gens_per_launch):
+    """Replays a request stream against one server: requests are submitted
+    at their arrival times (relative to the first), results fetched as they
+    complete.  Returns per-request infos and the server statistics."""
+    import threading
+    srv = n.Server(budget, max_active=max_active, gens_per_launch=gens_per_launch)
+    infos = {}
+    errors = []
+
+    def producer():
+        t0 = time.perf_counter()
+        for t, c in reqs:
+            dt = t - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            try:
+                srv.submit(c.m, c.d, c.N, c.p1, c.generations, wl.objective_weights(c.m, c.seed),
+                           seed=c.seed, p2=c.p2)
+            except Exception as e:  # noqa: BLE001 - reported below
+                errors.append(repr(e))
+
+    th = threading.Thread(target=producer)
+    th.start()
+    while len(infos) < len(reqs) and not errors:
+        rid = srv.wait(1000)
+        if rid < 0:
+            continue
+        st, info = srv.fetch(rid)
+        infos[rid] = info
+    th.join()
+    stats = srv.stats()
+    srv.close()
+    if errors:
+        raise RuntimeError(errors[0])
+    bad = [i for i in infos.values() if i.status != n.OK]
+    if bad:
+        raise RuntimeError("run failed: status %d %s" % (bad[0].status, bad[0].message.decode()))
+    return infos, stats
+
+
+def _latency_summary(infos, reqs):
+    import numpy as np
+    lat = np.array([i.t_done - i.t_submit for i in infos.values()])
+    t_first = min(i.t_submit for i in infos.values())
+    t_last = max(i.t_done for i in infos.values())
+    work = sum(c.N * c.generations for _, c in reqs)
+    return {"runs_per_s": len(infos) / (t_last - t_first), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "makespan_s": t_last - t_first,
+            "sols_per_s": work / (t_last - t_first), "requests": len(infos)}
+
+
 def run_served(args, world, rank, local):
-    raise SystemExit("served mode is not built yet")
+    """A Poisson stream of run requests (40 per second; N log-uniform in
+    [100, 50000], m in 3..10, 50..1000 generations, d = m + 29) served by the
+    continuous-batching server (64 slots, 8 generations per launch batch),
+    against the plain path (the same server with one slot: one run at a time,
+    in arrival order).  Latency = completion - arrival on the server clock;
+    runs/s = requests / (last completion - first arrival)."""
+    import torch
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    from paper_2504_06067_gb300 import native as n
+
+    n_req = args.requests or 400
+    reqs_all = wl.served_requests(n_req=n_req, rate_hz=40.0, seed=rank)
+    n_plain = min(n_req, 100)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(min(0.7 * free, 160e9))
+    # warm-up: one small run through each kind of server
+    warm = [(0.0, wl.RunConfig("w", m=3, d=32, N=100, p1=12, generations=5, seed=0))]
+    _serve(n, warm, budget // 8, 2, 8)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(dist)
+    plain_inf, plain_stats = _serve(n, reqs_all[:n_plain], budget, 1, 8)
+    served_small, _ = _serve(n, reqs_all[:n_plain], budget, 64, 8)
+    served_inf, served_stats = _serve(n, reqs_all, budget, 64, 8)
+    barrier(dist)
+    clocks = sampler.stop()
+    plain = _latency_summary(plain_inf, reqs_all[:n_plain])
+    same = _latency_summary(served_small, reqs_all[:n_plain])
+    full = _latency_summary(served_inf, reqs_all)
+    makespan = reduce_max(dist, full["makespan_s"], "cuda")
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+    line = {
+        "metric": METRIC,
+        "value": world * full["requests"] / makespan,
+        "unit": "runs/s",
+        "n_gpus": world,
+        "steps": full["requests"],
+        "warmup": 1,
+        "ms_per_step": makespan * 1e3 / full["requests"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded softmax-simplex objectives, Poisson arrivals)",
+        "config": {"workload": "served_%dreq_40hz" % n_req, "requests": n_req, "rate_hz": 40.0,
+                   "N": "log-uniform [100, 50000]", "m": "3..10", "generations": "50..1000",
+                   "d": "m + 29", "slots": 64, "gens_per_launch": 8, "budget_bytes": budget,
+                   "l2": "not flushed: concurrent runs' working sets exceed the 129 MB L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "served": full,
+        "served_first_%d" % n_plain: same,
+        "plain_first_%d" % n_plain: plain,
+        "served_vs_plain_runs_per_s": same["runs_per_s"] / plain["runs_per_s"],
+        "peak_active": served_stats["peak_active"],
+        "peak_bytes": served_stats["peak_bytes"],
+        "e2e": {"value": world * full["requests"] / makespan, "unit": "runs/s",
+                "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": sum(c.N * (c.d + c.m + 1) * 4 for _, c in reqs_all) / n_req,
+                "note": "the server API is host-to-host: requests in, final populations out in host "
+                        "memory; value and e2e are the same measurement"},
+        "gpu_launches": served_stats["launches"],
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return line
 
 
 # ----------------------------------------------------------------- oracle ----
@@ -556,7 +677,9 @@ def main(argv=None):
     args = parse_args(argv)
     world, rank, local = dist_env()
     if args.steps is None:
-        args.steps = {"batched": 300, "served": 0}.get(args.workload) or WORKLOADS[args.workload].generations
+        args.steps = {"batched": 300, "served": 0}.get(args.workload)
+        if args.steps is None:
+            args.steps = WORKLOADS[args.workload].generations
     if args.impl == "reference":
         run_reference(args, world, rank)
     elif args.workload == "batched":

@@ -81,6 +81,13 @@ nsga3_status nsga3_create(int m, int d, int N, int ref_divisions, const nsga3_op
 /* Frees the context and its device memory (synchronises its work). */
 void nsga3_destroy(nsga3_ctx* ctx);
 
+/* Device bytes nsga3_create allocates for these arguments (each buffer
+ * rounded up to 256 bytes); no allocation and no device work.  Without a
+ * device the per-SM buffers are sized for 256 SMs (an upper bound).
+ * Errors: EINVAL as nsga3_create. */
+nsga3_status nsga3_workspace_bytes(int m, int d, int N, int ref_divisions, const nsga3_opts* opts,
+                                   uint64_t* bytes);
+
 /* Human-readable description of the last error of ctx (or of the last failed
  * nsga3_create on this thread when ctx is NULL).  Never NULL. */
 const char* nsga3_last_error(const nsga3_ctx* ctx);
@@ -187,6 +194,78 @@ nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches);
  * kernels excluded): initialisation, variation, every replayed generation or
  * selection and each of their peel passes.  Synchronous. */
 nsga3_status nsga3_total_launches(nsga3_ctx* ctx, int64_t* launches);
+
+/* ------------------------------------------------------------------------
+ * Run server: continuous batching of independent runs on one GPU.
+ *
+ * Requests arrive at any time (any host thread).  A worker thread admits
+ * them in arrival order while a slot is free and the memory budget holds the
+ * run's workspace (nsga3_workspace_bytes), carving contexts out of one
+ * arena allocated at creation, so admission and release never call
+ * cudaMalloc or cudaFree.  Admitted runs advance concurrently, each on its
+ * own stream, `gens_per_launch` generations per launch batch; a finished
+ * run's population is copied to host memory and its slot and memory are
+ * reused at once.  A run's result depends only on its request (Philox
+ * counters), never on the other runs in flight.
+ * ------------------------------------------------------------------------ */
+typedef struct nsga3_server nsga3_server;
+
+typedef struct {
+    int m, d, N, ref_divisions;  /* as nsga3_create */
+    int generations;             /* >= 0 */
+    nsga3_opts opts;             /* opts.W (host, m x (m-1)) is required and is
+                                    copied by nsga3_server_submit */
+} nsga3_request;
+
+typedef struct {
+    int32_t status;              /* nsga3_status of the run */
+    int32_t m, d, N, generations;
+    uint64_t workspace_bytes;
+    double t_submit, t_admit, t_done;  /* seconds on the server clock; t_admit < 0 if never admitted */
+    char message[256];           /* error text when status != NSGA3_OK */
+} nsga3_run_info;
+
+typedef struct {
+    int64_t submitted, admitted, completed, active, pending, peak_active;
+    int64_t launches;            /* kernels launched for the completed runs */
+    uint64_t budget_bytes, bytes_in_use, peak_bytes;
+} nsga3_server_stats;
+
+/* Creates a server on the current device: one cudaMalloc of memory_budget
+ * bytes, max_active slot streams (1..1024) and the worker thread.
+ * max_active = 1 serves one run at a time (the plain path).
+ * Errors: EINVAL, ENOMEM (the budget cannot be allocated), ECUDA. */
+nsga3_status nsga3_server_create(uint64_t memory_budget, int max_active, int gens_per_launch,
+                                 nsga3_server** out);
+
+/* Queues a request; *id receives its id (0, 1, ... in submission order).
+ * Thread-safe, never blocks on the device.  Errors: EINVAL (arguments as
+ * nsga3_create, generations < 0, no opts.W), ESTATE (server shutting down).
+ * A request whose workspace exceeds the budget completes with ENOMEM. */
+nsga3_status nsga3_server_submit(nsga3_server* srv, const nsga3_request* req, int64_t* id);
+
+/* Waits up to timeout_ms (< 0: forever) for a completed run not yet
+ * returned by an earlier wait; *id = -1 on timeout. */
+nsga3_status nsga3_server_wait(nsga3_server* srv, int timeout_ms, int64_t* id);
+
+/* Copies a completed run's final population to host memory (X: N x d,
+ * F: N x m, rank: N; any may be NULL), fills *info (may be NULL) and
+ * releases the result.  Returns the run's status; EINVAL for an unknown or
+ * already fetched id. */
+nsga3_status nsga3_server_fetch(nsga3_server* srv, int64_t id, float* X, float* F, int32_t* rank,
+                                nsga3_run_info* info);
+
+nsga3_status nsga3_server_get_stats(nsga3_server* srv, nsga3_server_stats* stats);
+
+/* Seconds since the server was created (the clock of nsga3_run_info). */
+double nsga3_server_now(const nsga3_server* srv);
+
+/* Description of the last failed nsga3_server_submit. */
+const char* nsga3_server_last_error(const nsga3_server* srv);
+
+/* Stops the server: pending requests complete with ESTATE, active runs are
+ * stopped after their queued work; frees the arena and the streams. */
+void nsga3_server_destroy(nsga3_server* srv);
 
 /*
  * Largest n accepted by nsga3_rank_noalloc. */

@@ -21,6 +21,7 @@
 
 #include "kernels.cuh"
 #include "nsga3.h"
+#include "runtime.h"
 
 cudaError_t niche_init_attributes();
 
@@ -50,6 +51,9 @@ struct nsga3_ctx {
     int nsplit = 1;
     int last_kind = 0;  // 1 = select, 2 = step
     long long host_launches = 0;  // kernels launched by calls (peel passes counted on the device)
+    DeviceArena* arena = nullptr;  // workspace source (nullptr: cudaMalloc per buffer)
+    bool count_only = false;       // sizing pass: count bytes, allocate nothing
+    size_t counted = 0;
     bool eager = false; // NSGA3_EAGER=1: no graphs, host-driven peel loop (profiling)
     std::string err;
     // batched graph cache
@@ -95,10 +99,20 @@ nsga3_status alloc(nsga3_ctx* ctx, T** p, size_t count)
     void* q = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(&q, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ctx, NSGA3_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    if (ctx->count_only) {
+        ctx->counted += DeviceArena::round_up(bytes);
+        *p = nullptr;
+        return NSGA3_OK;
+    }
+    if (ctx->arena) {
+        q = ctx->arena->alloc(bytes);
+        if (!q) return fail(ctx, NSGA3_ENOMEM, "device arena has no free block of %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, NSGA3_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        }
     }
     ctx->allocs.push_back(q);
     *p = static_cast<T*>(q);
@@ -374,7 +388,9 @@ void build_ref_blocks(int m, int w, int M4, const std::vector<double>& Z, std::v
     }
 }
 
-nsga3_status setup(nsga3_ctx* ctx)
+// Allocates every device buffer of the context (or, in a sizing pass, only
+// counts their bytes).
+nsga3_status setup_alloc(nsga3_ctx* ctx)
 {
     const int m = ctx->m, d = ctx->d, N = ctx->N, n2 = ctx->n2, ld = ctx->ld, NW = ctx->NW;
     const int w = ctx->w, M4 = ctx->M4;
@@ -469,6 +485,24 @@ nsga3_status setup(nsga3_ctx* ctx)
     v.Wobj = Wd;
     ctx->vs = v;
     AL(ctx->vs.F, (size_t)ld * m);
+    return NSGA3_OK;
+}
+
+nsga3_status setup(nsga3_ctx* ctx)
+{
+    nsga3_status ast = setup_alloc(ctx);
+    if (ast) return ast;
+    const int m = ctx->m, d = ctx->d, N = ctx->N, n2 = ctx->n2, ld = ctx->ld, NW = ctx->NW;
+    const int w = ctx->w, M4 = ctx->M4;
+    RunView& v = ctx->v;
+    double* Zd = const_cast<double*>(v.Zd);
+    double* nz = const_cast<double*>(v.nz);
+    float* Zh = const_cast<float*>(v.Zh);
+    float* Wd = const_cast<float*>(v.Wobj);
+    float* bc = const_cast<float*>(v.blk_c);
+    float2* br = const_cast<float2*>(v.blk_r);
+    float* bz = const_cast<float*>(v.blk_z);
+    int32_t* bj = const_cast<int32_t*>(v.blk_j);
 
     CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&ctx->cap2, cudaStreamNonBlocking));
@@ -542,7 +576,128 @@ nsga3_status device_status(nsga3_ctx* ctx, bool clear)
     return (nsga3_status)st;
 }
 
+// Checks the arguments of a context and fills its sizes (no device work).
+nsga3_status ctx_fields(nsga3_ctx* ctx, int m, int d, int N, int ref_divisions, const nsga3_opts* opts)
+{
+    nsga3_opts o;
+    nsga3_default_opts(&o);
+    if (opts) o = *opts;
+    if (m < 2 || m > NSGA3_MAX_M) return fail(ctx, NSGA3_EINVAL, "m=%d outside [2, %d]", m, NSGA3_MAX_M);
+    if (N < 2 || (N & 1)) return fail(ctx, NSGA3_EINVAL, "N=%d must be even and >= 2", N);
+    if (N > (1 << 20)) return fail(ctx, NSGA3_EINVAL, "N=%d above 2^20", N);
+    if (d < 1) return fail(ctx, NSGA3_EINVAL, "d=%d < 1", d);
+    if (o.W && d < m - 1) return fail(ctx, NSGA3_EINVAL, "d=%d < m-1 with an objective", d);
+    if ((long long)N * d >= (1LL << 32)) return fail(ctx, NSGA3_EINVAL, "N*d must be < 2^32");
+    if (ref_divisions < 1 || o.p2 < 0) return fail(ctx, NSGA3_EINVAL, "bad reference divisions");
+    if (!(o.tau >= 0.0 && o.tau <= 1.0)) return fail(ctx, NSGA3_EINVAL, "tau outside [0,1]");
+    long long w = binom(ref_divisions + m - 1, m - 1) + (o.p2 > 0 ? binom(o.p2 + m - 1, m - 1) : 0);
+    if (w < 1 || w > (1LL << 24)) return fail(ctx, NSGA3_EINVAL, "reference set size %lld", w);
+    ctx->m = m;
+    ctx->d = d;
+    ctx->N = N;
+    ctx->n2 = 2 * N;
+    ctx->ld = (ctx->n2 + NSGA3_TILE - 1) / NSGA3_TILE * NSGA3_TILE;
+    ctx->NW = ctx->ld / 32;
+    ctx->w = (int)w;
+    ctx->M4 = (m + 3) & ~3;
+    ctx->p1 = ref_divisions;
+    ctx->p2 = o.p2;
+    ctx->tau = o.tau;
+    ctx->opts = o;
+    ctx->has_W = o.W != nullptr;  // W is read during create only
+    return NSGA3_OK;
+}
+
 }  // namespace
+
+nsga3_status ctx_create(int m, int d, int N, int ref_divisions, const nsga3_opts* opts, DeviceArena* arena,
+                        nsga3_ctx** out, std::string* err)
+{
+    if (!out) {
+        if (err) *err = "out is NULL";
+        return NSGA3_EINVAL;
+    }
+    *out = nullptr;
+    nsga3_ctx* ctx = new nsga3_ctx();
+    ctx->arena = arena;
+    nsga3_status st = ctx_fields(ctx, m, d, N, ref_divisions, opts);
+    if (!st) {
+        const char* e = getenv("NSGA3_EAGER");
+        ctx->eager = e && e[0] == '1';
+        if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(ctx, NSGA3_ECUDA, "no CUDA device");
+        }
+    }
+    if (!st) st = init_attributes(ctx);
+    if (!st) st = setup(ctx);
+    ctx->opts.W = nullptr;
+    if (st) {
+        if (err) *err = ctx->err;
+        ctx_destroy(ctx, arena == nullptr);
+        return st;
+    }
+    *out = ctx;
+    return NSGA3_OK;
+}
+
+nsga3_status ctx_workspace_bytes(int m, int d, int N, int ref_divisions, const nsga3_opts* opts, int num_sms,
+                                 size_t* bytes, std::string* err)
+{
+    nsga3_ctx c;
+    c.count_only = true;
+    nsga3_status st = ctx_fields(&c, m, d, N, ref_divisions, opts);
+    if (!st) {
+        c.num_sms = num_sms;
+        if (c.num_sms <= 0) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+                cudaGetLastError();
+                c.num_sms = 256;  // no device: an upper bound of the per-SM buffers
+            }
+        }
+        st = setup_alloc(&c);
+    }
+    if (st) {
+        if (err) *err = c.err;
+        return st;
+    }
+    *bytes = c.counted;
+    return NSGA3_OK;
+}
+
+void ctx_destroy(nsga3_ctx* ctx, bool sync_device)
+{
+    if (!ctx) return;
+    if (sync_device) cudaDeviceSynchronize();
+    if (ctx->gx_batch) cudaGraphExecDestroy(ctx->gx_batch);
+    if (ctx->gx_select) cudaGraphExecDestroy(ctx->gx_select);
+    if (ctx->gx_step) cudaGraphExecDestroy(ctx->gx_step);
+    for (int e = 0; e < EV_COUNT; ++e)
+        if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->cap2) cudaStreamDestroy(ctx->cap2);
+    for (void* p : ctx->allocs) {
+        if (ctx->arena)
+            ctx->arena->release(p);
+        else
+            cudaFree(p);
+    }
+    cudaGetLastError();
+    delete ctx;
+}
+
+nsga3_status ctx_launches(nsga3_ctx* ctx, void* stream, long long* launches)
+{
+    unsigned long long passes = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(&passes, &ctx->v.ctrl->passes_total, sizeof passes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *launches = ctx->host_launches + (long long)passes;
+    return NSGA3_OK;
+}
 
 // =============================================================== C ABI ====
 extern "C" {
@@ -566,72 +721,24 @@ void nsga3_default_opts(nsga3_opts* o)
 nsga3_status nsga3_create(int m, int d, int N, int ref_divisions, const nsga3_opts* opts,
                           nsga3_ctx** out)
 {
-    nsga3_ctx* ctx = nullptr;
-    if (!out) return fail(nullptr, NSGA3_EINVAL, "out is NULL");
-    *out = nullptr;
-    nsga3_opts o;
-    nsga3_default_opts(&o);
-    if (opts) o = *opts;
-    if (m < 2 || m > NSGA3_MAX_M) return fail(nullptr, NSGA3_EINVAL, "m=%d outside [2, %d]", m, NSGA3_MAX_M);
-    if (N < 2 || (N & 1)) return fail(nullptr, NSGA3_EINVAL, "N=%d must be even and >= 2", N);
-    if (N > (1 << 20)) return fail(nullptr, NSGA3_EINVAL, "N=%d above 2^20", N);
-    if (d < 1) return fail(nullptr, NSGA3_EINVAL, "d=%d < 1", d);
-    if (o.W && d < m - 1) return fail(nullptr, NSGA3_EINVAL, "d=%d < m-1 with an objective", d);
-    if ((long long)N * d >= (1LL << 32)) return fail(nullptr, NSGA3_EINVAL, "N*d must be < 2^32");
-    if (ref_divisions < 1 || o.p2 < 0) return fail(nullptr, NSGA3_EINVAL, "bad reference divisions");
-    if (!(o.tau >= 0.0 && o.tau <= 1.0)) return fail(nullptr, NSGA3_EINVAL, "tau outside [0,1]");
-    long long w = binom(ref_divisions + m - 1, m - 1) + (o.p2 > 0 ? binom(o.p2 + m - 1, m - 1) : 0);
-    if (w < 1 || w > (1LL << 24)) return fail(nullptr, NSGA3_EINVAL, "reference set size %lld", w);
-    ctx = new nsga3_ctx();
-    ctx->m = m;
-    ctx->d = d;
-    ctx->N = N;
-    ctx->n2 = 2 * N;
-    ctx->ld = (ctx->n2 + NSGA3_TILE - 1) / NSGA3_TILE * NSGA3_TILE;
-    ctx->NW = ctx->ld / 32;
-    ctx->w = (int)w;
-    ctx->M4 = (m + 3) & ~3;
-    ctx->p1 = ref_divisions;
-    ctx->p2 = o.p2;
-    ctx->tau = o.tau;
-    ctx->opts = o;
-    ctx->has_W = o.W != nullptr;  // W is read during create only
-    {
-        const char* e = getenv("NSGA3_EAGER");
-        ctx->eager = e && e[0] == '1';
-    }
-    nsga3_status st = NSGA3_OK;
-    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
-        cudaGetLastError();
-        st = fail(ctx, NSGA3_ECUDA, "no CUDA device");
-    }
-    if (!st) st = init_attributes(ctx);
-    if (!st) st = setup(ctx);
-    ctx->opts.W = nullptr;
-    if (st) {
-        g_create_error = ctx->err;
-        nsga3_destroy(ctx);
-        return st;
-    }
-    *out = ctx;
-    return NSGA3_OK;
+    std::string err;
+    nsga3_status st = ctx_create(m, d, N, ref_divisions, opts, nullptr, out, &err);
+    if (st) g_create_error = err;
+    return st;
 }
 
-void nsga3_destroy(nsga3_ctx* ctx)
+void nsga3_destroy(nsga3_ctx* ctx) { ctx_destroy(ctx, true); }
+
+nsga3_status nsga3_workspace_bytes(int m, int d, int N, int ref_divisions, const nsga3_opts* opts,
+                                   uint64_t* bytes)
 {
-    if (!ctx) return;
-    cudaDeviceSynchronize();
-    if (ctx->gx_batch) cudaGraphExecDestroy(ctx->gx_batch);
-    if (ctx->gx_select) cudaGraphExecDestroy(ctx->gx_select);
-    if (ctx->gx_step) cudaGraphExecDestroy(ctx->gx_step);
-    for (int e = 0; e < EV_COUNT; ++e)
-        if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);
-    if (ctx->cap) cudaStreamDestroy(ctx->cap);
-    if (ctx->cap2) cudaStreamDestroy(ctx->cap2);
-    for (void* p : ctx->allocs) cudaFree(p);
-    cudaGetLastError();
-    delete ctx;
+    if (!bytes) return fail(nullptr, NSGA3_EINVAL, "bytes is NULL");
+    std::string err;
+    size_t b = 0;
+    nsga3_status st = ctx_workspace_bytes(m, d, N, ref_divisions, opts, 0, &b, &err);
+    if (st) return fail(nullptr, st, "%s", err.c_str());
+    *bytes = b;
+    return NSGA3_OK;
 }
 
 const char* nsga3_last_error(const nsga3_ctx* ctx)

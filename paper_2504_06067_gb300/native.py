@@ -42,6 +42,25 @@ class nsga3_opts(C.Structure):
     ]
 
 
+class nsga3_request(C.Structure):
+    _fields_ = [("m", C.c_int), ("d", C.c_int), ("N", C.c_int), ("ref_divisions", C.c_int),
+                ("generations", C.c_int), ("opts", nsga3_opts)]
+
+
+class nsga3_run_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("m", C.c_int32), ("d", C.c_int32), ("N", C.c_int32),
+                ("generations", C.c_int32), ("workspace_bytes", C.c_uint64),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("message", C.c_char * 256)]
+
+
+class nsga3_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("active", C.c_int64), ("pending", C.c_int64), ("peak_active", C.c_int64),
+                ("launches", C.c_int64), ("budget_bytes", C.c_uint64), ("bytes_in_use", C.c_uint64),
+                ("peak_bytes", C.c_uint64)]
+
+
 _P = C.c_void_p
 _CTX = C.c_void_p
 _I = C.c_int
@@ -71,6 +90,15 @@ _SIGS = {
     "nsga3_last_launches": (_I, [_CTX, _P]),
     "nsga3_total_launches": (_I, [_CTX, _P]),
     "nsga3_rank_noalloc": (_I, [_P, _I, _I, _P, _P]),
+    "nsga3_workspace_bytes": (_I, [_I, _I, _I, _I, C.POINTER(nsga3_opts), C.POINTER(C.c_uint64)]),
+    "nsga3_server_create": (_I, [C.c_uint64, _I, _I, C.POINTER(_P)]),
+    "nsga3_server_submit": (_I, [_P, C.POINTER(nsga3_request), C.POINTER(C.c_int64)]),
+    "nsga3_server_wait": (_I, [_P, _I, C.POINTER(C.c_int64)]),
+    "nsga3_server_fetch": (_I, [_P, C.c_int64, _P, _P, _P, C.POINTER(nsga3_run_info)]),
+    "nsga3_server_get_stats": (_I, [_P, C.POINTER(nsga3_server_stats)]),
+    "nsga3_server_now": (C.c_double, [_P]),
+    "nsga3_server_last_error": (C.c_char_p, [_P]),
+    "nsga3_server_destroy": (None, [_P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -126,3 +154,65 @@ def rank_noalloc(objs_ptr, n, m, ranks_ptr, stream=0):
     if st != OK:
         raise NSGA3Error(st, "nsga3_rank_noalloc: CUDA device lookup or launch failed")
     return st
+
+
+def workspace_bytes(m, d, N, ref_divisions, opts=None):
+    """nsga3_workspace_bytes: device bytes nsga3_create would allocate."""
+    if opts is None:
+        opts = default_opts()
+    b = C.c_uint64()
+    check(nsga3_workspace_bytes(m, d, N, ref_divisions, C.byref(opts), C.byref(b)))
+    return b.value
+
+
+class Server:
+    """Thin owner of an nsga3_server handle (calls map one to one)."""
+
+    def __init__(self, memory_budget, max_active=64, gens_per_launch=8):
+        h = C.c_void_p()
+        st = nsga3_server_create(int(memory_budget), max_active, gens_per_launch, C.byref(h))
+        if st != OK:
+            raise NSGA3Error(st, "nsga3_server_create failed")
+        self.h = h.value
+        self._keep = {}
+
+    def submit(self, m, d, N, ref_divisions, generations, W, **opts):
+        import numpy as np
+        W = np.ascontiguousarray(W, dtype=np.float32)
+        o = default_opts(W=W.ctypes.data, **opts)
+        req = nsga3_request(m, d, N, ref_divisions, generations, o)
+        i = C.c_int64()
+        st = nsga3_server_submit(self.h, C.byref(req), C.byref(i))
+        if st != OK:
+            msg = nsga3_server_last_error(self.h)
+            raise NSGA3Error(st, msg.decode() if msg else "")
+        return i.value
+
+    def wait(self, timeout_ms=-1):
+        i = C.c_int64()
+        check(nsga3_server_wait(self.h, timeout_ms, C.byref(i)))
+        return i.value
+
+    def fetch(self, rid, X=0, F=0, rank=0):
+        info = nsga3_run_info()
+        st = nsga3_server_fetch(self.h, rid, X, F, rank, C.byref(info))
+        return st, info
+
+    def stats(self):
+        s = nsga3_server_stats()
+        check(nsga3_server_get_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def now(self):
+        return nsga3_server_now(self.h)
+
+    def close(self):
+        if self.h:
+            nsga3_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

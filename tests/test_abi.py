@@ -56,3 +56,32 @@ def test_create_without_gpu_fails_cleanly(lib):
     # argument errors are reported before any device work
     assert n.nsga3_create(1, 12, 92, 12, C.byref(o), C.byref(h)) == n.EINVAL
     assert n.nsga3_create(3, 12, 91, 12, C.byref(o), C.byref(h)) == n.EINVAL
+
+
+def test_workspace_bytes_without_gpu(lib):
+    """The sizing pass touches no device: the bit matrix dominates at scale,
+    the count grows with N and bad arguments are rejected like nsga3_create."""
+    from paper_2504_06067_gb300 import native as n
+    prev = 0
+    for N in (92, 1000, 10628, 100000):
+        b = n.workspace_bytes(5, 100, N, 4)
+        ld = -(-2 * N // 256) * 256
+        assert b >= ld * ld // 8 + 2 * N * 100 * 4
+        assert b > prev
+        prev = b
+    big = n.workspace_bytes(10, 200, 100000, 3, n.default_opts(p2=2))
+    assert 5.0e9 < big < 5.6e9
+    out = C.c_uint64()
+    o = n.default_opts()
+    assert n.nsga3_workspace_bytes(1, 12, 92, 12, C.byref(o), C.byref(out)) == n.EINVAL
+    assert n.nsga3_workspace_bytes(3, 12, 91, 12, C.byref(o), C.byref(out)) == n.EINVAL
+
+
+def test_server_create_without_gpu_fails_cleanly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2504_06067_gb300 import native as n
+    h = C.c_void_p()
+    assert n.nsga3_server_create(1 << 20, 4, 8, C.byref(h)) == n.ECUDA and h.value is None
+    assert n.nsga3_server_create(1 << 20, 0, 8, C.byref(h)) == n.EINVAL
