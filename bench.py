@@ -86,6 +86,13 @@ def reduce_max(dist, x, device="cpu"):
     return float(t.item())
 
 
+def job_rate(dist, world, units_per_rank, seconds, device="cpu"):
+    """Whole-job throughput: the units all ranks processed divided by the
+    slowest rank's time.  Returns (rate, max seconds)."""
+    t = reduce_max(dist, seconds, device)
+    return world * units_per_rank / t, t
+
+
 def barrier(dist):
     if dist is not None:
         dist.barrier()
@@ -247,7 +254,7 @@ def run_ours(args, world, rank, local):
     if st != n.OK:
         raise RuntimeError("device status %d after the timed run" % st)
     total_s = sum(step_ms) / 1e3
-    total_s_max = reduce_max(dist, total_s, "cuda")
+    value, total_s_max = job_rate(dist, world, cfg.N * K, total_s, "cuda")
 
     # end to end through the C ABI with pinned host buffers: upload the
     # parents, one generation, read the next population back
@@ -311,7 +318,6 @@ def run_ours(args, world, rank, local):
                 "peak_source": "hbm_gbs (%s)" % peak_kind,
                 "algorithmic": "dominator row segments read (128 columns x 4 B each), all passes",
                 "traffic": ncu_traffic("k_peel", cfg.name)}
-    value = world * cfg.N * K / total_s_max
     line = {
         "metric": METRIC,
         "value": value,

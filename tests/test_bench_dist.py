@@ -1,0 +1,52 @@
+"""bench.py's multi-rank bookkeeping on CPU: two gloo ranks, a barrier, the
+max-over-ranks time and the whole-job rate (N GPUs are replicas: units of
+every rank over the slowest rank's time)."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    w, r, _ = bench.dist_env()
+    dist = bench.dist_init(w, "gloo")
+    bench.barrier(dist)
+    rate, tmax = bench.job_rate(dist, w, 1000, 1.0 + r, "cpu")
+    q.put((r, w, rate, tmax))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    torch = pytest.importorskip("torch")
+    mp = torch.multiprocessing.get_context("spawn")
+    q = mp.Queue()
+    port = _free_port()
+    ps = [mp.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r, w, rate, tmax in res:
+        assert w == 2 and tmax == 2.0 and rate == 2 * 1000 / 2.0
+
+
+def test_single_process_needs_no_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.dist_init(1, "gloo") is None
+    assert bench.job_rate(None, 1, 50, 2.0) == (25.0, 2.0)
