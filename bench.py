@@ -370,6 +370,7 @@ def run_batched(args, world, rank, local):
     cfgs = wl.batched_configs(n_runs=args.runs, seed=0, generations=gens)
     Ws = [wl.objective_weights(c.m, c.seed) for c in cfgs]
     ctxs = []
+    progress("creating %d contexts" % len(cfgs))
     for c, W in zip(cfgs, Ws):
         o = n.default_opts(seed=c.seed + 1000003 * rank, W=W.ctypes.data)
         ctxs.append(n.create(c.m, c.d, c.N, c.p1, o))
@@ -402,6 +403,7 @@ def run_batched(args, world, rank, local):
             n.check(n.nsga3_get_population(x, X.data_ptr(), F.data_ptr(), R.data_ptr(), sh), x)
 
     # warm-up: build every graph (the batched one included)
+    progress("warm-up")
     for x in ctxs:
         n.check(n.nsga3_init(x, sh), x)
     n.check(n.run_batch(ctxs, max(args.warmup, 1), sh), ctxs[0])
@@ -413,6 +415,7 @@ def run_batched(args, world, rank, local):
     sampler.start()
     res = {}
     for arm, fn in (("plain", plain), ("batched", batched)):
+        progress("%s arm" % arm)
         barrier(dist)
         torch.cuda.synchronize()
         l0 = launches()
@@ -433,6 +436,16 @@ def run_batched(args, world, rank, local):
             st = n.nsga3_sync(x, sh)
             if st != n.OK:
                 raise RuntimeError("device status %d in the %s arm" % (st, arm))
+    # the same runs through the run server: every run on its own stream,
+    # no per-generation join between runs
+    torch.cuda.synchronize()
+    progress("server arm")
+    reqs = [(0.0, c) for c in cfgs]
+    budget = int(min(0.7 * torch.cuda.mem_get_info()[0], 160e9))
+    w0 = time.perf_counter()
+    sinf, _ = _serve(n, reqs, budget, len(cfgs), 8)
+    server_s = time.perf_counter() - w0
+    server_span = max(i.t_done for i in sinf.values()) - min(i.t_submit for i in sinf.values())
     clocks = sampler.stop()
     same = all(all(torch.equal(a, b) for a, b in zip(p, q))
                for p, q in zip(res["plain"]["pop"], res["batched"]["pop"]))
@@ -467,6 +480,9 @@ def run_batched(args, world, rank, local):
         "plain": {"value": world * R / p["s"], "unit": "runs/s", "ms": p["s"] * 1e3,
                   "gpu_launches": p["launches"]},
         "batched_vs_plain": p["s"] / b["s"],
+        "server_streams": {"value": world * R / server_span, "unit": "runs/s", "wall_s": server_s,
+                           "note": "the same runs submitted at once to the run server (one stream "
+                                   "per run, 8 generations per launch batch, no join per generation)"},
         "identical_populations": bool(same),
         "gens_per_s": world * R * gens / b["s"],
         "sols_per_s": world * sum(c.N for c in cfgs) * gens / b["s"],
@@ -679,7 +695,17 @@ def run_reference(args, world, rank):
     return line
 
 
+def progress(msg):
+    """One line of progress on stderr (stdout carries only the JSON line)."""
+    print("[bench %.1fs] %s" % (time.perf_counter() - T_START, msg), file=sys.stderr, flush=True)
+
+
+T_START = time.perf_counter()
+
+
 def main(argv=None):
+    import faulthandler
+    faulthandler.enable()
     args = parse_args(argv)
     world, rank, local = dist_env()
     if args.steps is None:
