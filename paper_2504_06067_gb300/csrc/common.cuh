@@ -114,7 +114,6 @@ struct RunView {
     int32_t* rho;          // w
     int32_t* rhop;         // w
     int32_t* take;         // w
-    uint32_t* refprio;     // w   Philox reference priorities of this generation
     int32_t* ref_off;      // w + 1
     int32_t* cursor;       // w
     int32_t* bucket;       // n2

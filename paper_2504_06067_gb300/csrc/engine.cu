@@ -447,7 +447,6 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     AL(v.rho, w);
     AL(v.rhop, w);
     AL(v.take, w);
-    AL(v.refprio, w);
     AL(v.ref_off, w + 1);
     AL(v.cursor, w);
     AL(v.bucket, n2);

@@ -25,11 +25,9 @@ __global__ void k_sel_reset(RunView v)
         v.rem[wd] = m;
         v.selmask[wd] = 0u;
     }
-    const uint32_t gen = v.ctrl->gen;
     for (int j = tid; j < v.w; j += stride) {
         v.rho[j] = 0;
         v.rhop[j] = 0;
-        v.refprio[j] = philox((uint32_t)j, gen, RNG_REFPRIO, 0u, v.seed).x;
         v.cursor[j] = 0;
     }
     if (tid == 0) {

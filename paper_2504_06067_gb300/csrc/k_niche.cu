@@ -31,6 +31,11 @@ __device__ __forceinline__ uint32_t mem_prio(uint64_t seed, uint32_t gen, int i)
     return philox((uint32_t)i, gen, RNG_MEMPRIO, 0u, seed).x;
 }
 
+__device__ __forceinline__ unsigned long long ref_key(uint64_t seed, uint32_t gen, int j)
+{
+    return ((unsigned long long)philox((uint32_t)j, gen, RNG_REFPRIO, 0u, seed).x << 32) | (unsigned)j;
+}
+
 // ------------------------------------------------ block-wide helpers -------
 __device__ int block_sum(int x, int* scratch)
 {
@@ -225,9 +230,24 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
     Ctrl* c = v.ctrl;
     if (skip_niche(c)) return;
     const int w = v.w, K = c->K;
+    const uint32_t gen = c->gen;
     const bool staged = w <= RRCAP;
-    if (staged)
-        for (int j = threadIdx.x; j < w; j += LB) sh.rr[j] = make_int2(v.rho[j], v.rhop[j]);
+    if (staged) {
+        // all loads of a thread in flight at once (one SM does this work)
+        constexpr int PT = RRCAP / LB;
+        int a[PT], b[PT];
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            const int j = threadIdx.x + t * LB;
+            a[t] = j < w ? v.rho[j] : 0;
+            b[t] = j < w ? v.rhop[j] : 0;
+        }
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            const int j = threadIdx.x + t * LB;
+            if (j < w) sh.rr[j] = make_int2(a[t], b[t]);
+        }
+    }
     auto rho_of = [&](int j) { return staged ? sh.rr[j].x : v.rho[j]; };
     auto rhop_of = [&](int j) { return staged ? sh.rr[j].y : v.rhop[j]; };
     for (int t = threadIdx.x; t <= LCAP; t += LB) sh.lev[t] = 0;
@@ -303,34 +323,117 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
         before = count_le(Lstar - 1);
     }
     const int r = K - before;
-    if (threadIdx.x == 0) sh.nck = 0;
-    __syncthreads();
-    for (int j = threadIdx.x; j < w; j += LB) {
-        const int rp = rhop_of(j);
-        const int lo = rho_of(j);
-        v.take[j] = rp > 0 ? min(rp, max(0, Lstar - lo)) : 0;
-        if (rp > 0 && lo <= Lstar && Lstar < lo + rp) {
-            const int p = atomicAdd(&sh.nck, 1);
-            if (p < CKCAP) sh.ck[p] = ((unsigned long long)v.refprio[j] << 32) | (unsigned)j;
+    if (staged) {
+        // The r smallest (priority, j) keys among the level-L* references:
+        // each thread keeps the keys of its references in registers; one
+        // 12-bit radix pass over the priorities' top bits finds the bin
+        // holding the r-th key (about nC / 4096 keys per bin), the keys below
+        // it are taken and the bin is ranked pairwise.
+        constexpr int PT = RRCAP / LB;
+        static_assert(LCAP == 4 * LB, "histogram bins per thread");
+        unsigned long long kk[PT];
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            const int j = threadIdx.x + t * LB;
+            kk[t] = ~0ull;
+            if (j < w) {
+                const int rp = sh.rr[j].y, lo = sh.rr[j].x;
+                v.take[j] = rp > 0 ? min(rp, max(0, Lstar - lo)) : 0;
+                if (rp > 0 && lo <= Lstar && Lstar < lo + rp) kk[t] = ref_key(v.seed, gen, j);
+            }
         }
-    }
-    __syncthreads();
-    const int nC = sh.nck;
-    if (nC <= CKCAP) {
-        // the level-L* references are staged in shared memory
-        auto key = [&](int e) { return sh.ck[e]; };
-        auto pred = [&](int) { return true; };
-        auto mark = [&](int e) { v.take[(int)(sh.ck[e] & 0xffffffffull)] += 1; };
-        block_select_smallest(nC, r, key, pred, mark, sh.sel);
+        __syncthreads();  // every thread has read `before` from the level table
+        int* hist = sh.lev;
+        for (int t = threadIdx.x; t < LCAP; t += LB) hist[t] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < PT; ++t)
+            if (kk[t] != ~0ull) atomicAdd(&hist[(int)(kk[t] >> 52)], 1);
+        __syncthreads();
+        {
+            int h4[4], loc = 0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                h4[t] = hist[threadIdx.x * 4 + t];
+                loc += h4[t];
+            }
+            int total;
+            int run = block_excl_scan(loc, sh.scratch, &total);
+            if (run < r && r <= run + loc) {
+                int b = threadIdx.x * 4;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    if (run + h4[t] >= r) break;
+                    run += h4[t];
+                    ++b;
+                }
+                sh.sel.bsel = b;
+                sh.sel.before = run;
+            }
+        }
+        if (threadIdx.x == 0) sh.sel.nex = 0;
+        __syncthreads();
+        const int b = sh.sel.bsel, need = r - sh.sel.before;
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            if (kk[t] == ~0ull) continue;
+            const int bin = (int)(kk[t] >> 52);
+            if (bin < b) {
+                v.take[threadIdx.x + t * LB] += 1;
+            } else if (bin == b) {
+                const int p = atomicAdd(&sh.sel.nex, 1);
+                if (p < EXACT) sh.sel.keys[p] = kk[t];
+            }
+        }
+        __syncthreads();
+        const int ne = sh.sel.nex;
+        if (ne <= EXACT) {
+            for (int a = threadIdx.x; a < ne; a += LB) {
+                const unsigned long long ka = sh.sel.keys[a];
+                int rk = 0;
+                for (int q = 0; q < ne; ++q) rk += sh.sel.keys[q] < ka;
+                if (rk < need) v.take[(int)(ka & 0xffffffffull)] += 1;
+            }
+        } else {
+            // more than EXACT keys share the bin (not expected for Philox
+            // priorities): select among them generically
+            auto pred = [&](int j) {
+                const int rp = sh.rr[j].y, lo = sh.rr[j].x;
+                return rp > 0 && lo <= Lstar && Lstar < lo + rp && (int)(ref_key(v.seed, gen, j) >> 52) == b;
+            };
+            auto key = [&](int j) { return ref_key(v.seed, gen, j); };
+            auto mark = [&](int j) { v.take[j] += 1; };
+            block_select_smallest(w, need, key, pred, mark, sh.sel);
+        }
     } else {
-        auto pred = [&](int j) {
+        if (threadIdx.x == 0) sh.nck = 0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < w; j += LB) {
             const int rp = rhop_of(j);
             const int lo = rho_of(j);
-            return rp > 0 && lo <= Lstar && Lstar < lo + rp;
-        };
-        auto key = [&](int j) { return ((unsigned long long)v.refprio[j] << 32) | (unsigned)j; };
-        auto mark = [&](int j) { v.take[j] += 1; };
-        block_select_smallest(w, r, key, pred, mark, sh.sel);
+            v.take[j] = rp > 0 ? min(rp, max(0, Lstar - lo)) : 0;
+            if (rp > 0 && lo <= Lstar && Lstar < lo + rp) {
+                const int p = atomicAdd(&sh.nck, 1);
+                if (p < CKCAP) sh.ck[p] = ref_key(v.seed, gen, j);
+            }
+        }
+        __syncthreads();
+        const int nC = sh.nck;
+        if (nC <= CKCAP) {
+            auto key = [&](int e) { return sh.ck[e]; };
+            auto pred = [&](int) { return true; };
+            auto mark = [&](int e) { v.take[(int)(sh.ck[e] & 0xffffffffull)] += 1; };
+            block_select_smallest(nC, r, key, pred, mark, sh.sel);
+        } else {
+            auto pred = [&](int j) {
+                const int rp = rhop_of(j);
+                const int lo = rho_of(j);
+                return rp > 0 && lo <= Lstar && Lstar < lo + rp;
+            };
+            auto key = [&](int j) { return ref_key(v.seed, gen, j); };
+            auto mark = [&](int j) { v.take[j] += 1; };
+            block_select_smallest(w, r, key, pred, mark, sh.sel);
+        }
     }
     __syncthreads();
     if (staged) {

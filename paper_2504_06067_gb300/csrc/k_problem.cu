@@ -69,34 +69,64 @@ __global__ void k_refdirs(int m, int p1, int p2, double tau, int w1, int w, doub
     for (int q = 0; q < M4; ++q) Zh[(size_t)t * M4 + q] = q < m ? __double2float_rn(__ddiv_rn(z[q], n)) : 0.0f;
 }
 
-// Objective of rows [row0, row0 + n): a block covers OR = 32 rows with
-// OR * m threads (at least 64).  Warp 0 sums g of its 32 rows (lane = row) in
-// FP64 left to right, fully converged (GB300's FP64 pipe runs at 1/64 of
-// FP32, so divergent FP64 is costly); thread (row, j) forms
-// a_j = sum_v W_jv x_v in FP64 (left to right) and e_j = exp(a_j); the row's
-// denominator adds e_0..e_{m-1} in order; f_j = (1 + g) e_j / den, rounded
-// to FP32.
+// Objective of rows [row0, row0 + n): a block covers OR = 32 rows.
+//   g = sum_{v >= m-1} (x_v - 0.5)^2: each term is formed exactly as a
+//   float-float value (x - 0.5 by Fast2Sum, the square by an FMA product
+//   error) and the terms are added in float-float (TwoSum) by a warp per row
+//   with coalesced loads, then a warp reduction; the float-float sum is
+//   within ~2^-44 relative of the exact sum, so (1 + g) in FP64 matches a
+//   left-to-right FP64 sum to far below the final FP32 rounding.  This keeps
+//   the sum off GB300's FP64 pipe (1/64 of the FP32 rate).
+//   Thread (row, j) forms a_j = sum_v W_jv x_v in FP64 (left to right) and
+//   e_j = exp(a_j); the row's denominator adds e_0..e_{m-1} in order once;
+//   f_j = (1 + g) e_j / den, rounded to FP32.
 constexpr int OR = 32;
+constexpr int OT = 256;
 
-__global__ void k_objective(RunView v, int row0, int n)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__global__ void __launch_bounds__(OT) k_objective(RunView v, int row0, int n)
 {
     __shared__ double sg[OR];
+    __shared__ double sden[OR];
     __shared__ double se[OR * NSGA3_MAX_M];
     const int m = v.m, d = v.d, k = m - 1;
     const int base = blockIdx.x * OR;
-    if (threadIdx.x < OR) {
-        const int rr = threadIdx.x;
-        double g = 0.0;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    for (int rr = warp; rr < OR; rr += OT / 32) {
+        float sh = 0.0f, sl = 0.0f;
         if (base + rr < n) {
             const float* x = v.X + (size_t)(row0 + base + rr) * d;
-            for (int e = k; e < d; ++e) {
-                const double t = __dsub_rn((double)x[e], 0.5);
-                g = __dadd_rn(g, __dmul_rn(t, t));
+            for (int e = k + lane; e < d; e += 32) {
+                const float xv = x[e];
+                const float th = __fsub_rn(xv, 0.5f);
+                // Fast2Sum error of x + (-0.5); zero when x >= 0.25 (Sterbenz)
+                const float tl = xv < 0.25f ? __fsub_rn(xv, __fadd_rn(th, 0.5f)) : 0.0f;
+                const float p = __fmul_rn(th, th);
+                const float pl = __fmaf_rn(th, th, -p) + 2.0f * th * tl;
+                float s1, e1;
+                two_sum(sh, p, s1, e1);
+                sh = s1;
+                sl = sl + (e1 + pl);
             }
         }
-        sg[rr] = g;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
+            float s1, e1;
+            two_sum(sh, oh, s1, e1);
+            sh = s1;
+            sl = sl + (ol + e1);
+        }
+        if (lane == 0) sg[rr] = __dadd_rn((double)sh, (double)sl);
     }
-    for (int idx = threadIdx.x; idx < OR * m; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < OR * m; idx += OT) {
         const int rr = idx / m, j = idx - rr * m;
         if (base + rr >= n) continue;
         const float* x = v.X + (size_t)(row0 + base + rr) * d;
@@ -105,17 +135,20 @@ __global__ void k_objective(RunView v, int row0, int n)
         se[idx] = exp(a);
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < OR * m; idx += blockDim.x) {
+    if (threadIdx.x < OR && base + threadIdx.x < n) {
+        double den = 0.0;
+        for (int t = 0; t < m; ++t) den = __dadd_rn(den, se[threadIdx.x * m + t]);
+        sden[threadIdx.x] = den;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < OR * m; idx += OT) {
         const int rr = idx / m, j = idx - rr * m;
         if (base + rr >= n) continue;
-        double den = 0.0;
-        for (int t = 0; t < m; ++t) den = __dadd_rn(den, se[rr * m + t]);
-        const double f = __dmul_rn(__dadd_rn(1.0, sg[rr]), __ddiv_rn(se[idx], den));
+        const double f = __dmul_rn(__dadd_rn(1.0, sg[rr]), __ddiv_rn(se[idx], sden[rr]));
         v.F[(size_t)(row0 + base + rr) * m + j] = __double2float_rn(f);
     }
 }
 
-static int objective_threads(int m) { return OR * m < 64 ? 64 : OR * m; }
 
 __global__ void k_init(RunView v)
 {
@@ -214,7 +247,7 @@ cudaError_t launch_init(const RunView& v, cudaStream_t s)
     k_init<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_objective<<<(v.N + OR - 1) / OR, objective_threads(v.m), 0, s>>>(v, 0, v.N);
+    k_objective<<<(v.N + OR - 1) / OR, OT, 0, s>>>(v, 0, v.N);
     return cudaGetLastError();
 }
 
@@ -224,6 +257,6 @@ cudaError_t launch_vary_eval(const RunView& v, cudaStream_t s)
     k_vary_eval<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_objective<<<(v.N + OR - 1) / OR, objective_threads(v.m), 0, s>>>(v, v.N, v.N);
+    k_objective<<<(v.N + OR - 1) / OR, OT, 0, s>>>(v, v.N, v.N);
     return cudaGetLastError();
 }
