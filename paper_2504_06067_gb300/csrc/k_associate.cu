@@ -55,13 +55,16 @@ __device__ __forceinline__ double perp_dist(const double* fp, double nf, const d
 }
 
 // f' = (f - z*) / a and |f'| in FP64; FP32 unit vector for the scan
+// small blocks spread the FP64 work over every SM sub-partition
+constexpr int PB = 64;
+
 template <int M>
-__global__ void __launch_bounds__(AB) k_assoc_prep(RunView v)
+__global__ void __launch_bounds__(PB) k_assoc_prep(RunView v)
 {
     constexpr int M4 = (M + 3) & ~3;
     Ctrl* c = v.ctrl;
     if (skip_niche(c)) return;
-    const int s = blockIdx.x * AB + threadIdx.x;
+    const int s = blockIdx.x * PB + threadIdx.x;
     if (s >= c->nT) return;
     const int i = v.Tlist[s];
     double fp[M];
@@ -85,6 +88,7 @@ template <int M>
 __global__ void __launch_bounds__(AB) k_assoc_scan(RunView v)
 {
     constexpr int M4 = (M + 3) & ~3;
+    constexpr int CH = (M4 <= 8) ? 4 : 2;  // blocks whose loads are in flight together
     extern __shared__ __align__(16) float sm[];
     Ctrl* c = v.ctrl;
     if (skip_niche(c)) return;
@@ -144,26 +148,8 @@ __global__ void __launch_bounds__(AB) k_assoc_scan(RunView v)
         float best = -4.0f;
         int nl = 0;
         bool ovf = false;
-        auto scan_block = [&](int b) {
-            const int pos = b * 32 + lane;
-            float qh = -4.0f;
-            int j = -1;
-            if (pos < w) {
-                const float4* z4 = reinterpret_cast<const float4*>(v.blk_z + (size_t)pos * M4);
-                float zz[M4];
-#pragma unroll
-                for (int q4 = 0; q4 < M4 / 4; ++q4) {
-                    const float4 z = __ldg(z4 + q4);
-                    zz[4 * q4 + 0] = z.x;
-                    zz[4 * q4 + 1] = z.y;
-                    zz[4 * q4 + 2] = z.z;
-                    zz[4 * q4 + 3] = z.w;
-                }
-                qh = 0.0f;
-#pragma unroll
-                for (int q = 0; q < M; ++q) qh = fmaf(u[q], zz[q], qh);
-                j = v.blk_j[pos];
-            }
+        // candidate-list update with one block's cosines (qh, j) per lane
+        auto take_block = [&](float qh, int j) {
             // cosines are >= 0, so the float bits order like unsigned ints
             const float wm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(qh, 0.0f))));
             best = fmaxf(best, wm);
@@ -205,7 +191,45 @@ __global__ void __launch_bounds__(AB) k_assoc_scan(RunView v)
             nl += __popc(bal);
             __syncwarp();
         };
-        scan_block(bb);
+        // Scans up to CH blocks with all their loads issued before any use
+        // (the surviving blocks of a point are scanned in a few latency
+        // rounds instead of one round per block).
+        int pend[CH];
+        int npend = 0;
+        auto flush = [&]() {
+            float qh[CH];
+            int jj[CH];
+#pragma unroll
+            for (int t = 0; t < CH; ++t) {
+                const int pos = (t < npend ? pend[t] : 0) * 32 + lane;
+                qh[t] = -4.0f;
+                jj[t] = -1;
+                if (t < npend && pos < w) {
+                    const float4* z4 = reinterpret_cast<const float4*>(v.blk_z + (size_t)pos * M4);
+                    float zz[M4];
+#pragma unroll
+                    for (int q4 = 0; q4 < M4 / 4; ++q4) {
+                        const float4 z = __ldg(z4 + q4);
+                        zz[4 * q4 + 0] = z.x;
+                        zz[4 * q4 + 1] = z.y;
+                        zz[4 * q4 + 2] = z.z;
+                        zz[4 * q4 + 3] = z.w;
+                    }
+                    float a = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < M; ++q) a = fmaf(u[q], zz[q], a);
+                    qh[t] = a;
+                    jj[t] = __ldg(v.blk_j + pos);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+                if (t < npend) take_block(qh[t], jj[t]);
+            npend = 0;
+        };
+        pend[0] = bb;
+        npend = 1;
+        flush();
         for (int base = 0; base < nb; base += 32) {
             const int b = base + lane;
             const bool f = b < nb && b != bb && wbnd[b] + EPS >= best - band;
@@ -213,9 +237,15 @@ __global__ void __launch_bounds__(AB) k_assoc_scan(RunView v)
             while (msk) {
                 const int b2 = base + __ffs(msk) - 1;
                 msk &= msk - 1;
-                if (wbnd[b2] + EPS >= best - band) scan_block(b2);
+                if (wbnd[b2] + EPS >= best - band) {
+#pragma unroll
+                    for (int t = 0; t < CH; ++t)
+                        if (t == npend) pend[t] = b2;
+                    if (++npend == CH) flush();
+                }
             }
         }
+        if (npend) flush();
         // final candidates: q >= best - band
         int cnt = 0;
         for (int e0 = 0; e0 < nl; e0 += 32) {
@@ -394,17 +424,17 @@ cudaError_t attr_m(size_t sm)
 
 cudaError_t launch_assoc_prep(const RunView& v, cudaStream_t s)
 {
-    const int g = (v.n2 + AB - 1) / AB;
+    const int g = (v.n2 + PB - 1) / PB;
     switch (v.m) {
-    case 2: k_assoc_prep<2><<<g, AB, 0, s>>>(v); break;
-    case 3: k_assoc_prep<3><<<g, AB, 0, s>>>(v); break;
-    case 4: k_assoc_prep<4><<<g, AB, 0, s>>>(v); break;
-    case 5: k_assoc_prep<5><<<g, AB, 0, s>>>(v); break;
-    case 6: k_assoc_prep<6><<<g, AB, 0, s>>>(v); break;
-    case 7: k_assoc_prep<7><<<g, AB, 0, s>>>(v); break;
-    case 8: k_assoc_prep<8><<<g, AB, 0, s>>>(v); break;
-    case 9: k_assoc_prep<9><<<g, AB, 0, s>>>(v); break;
-    case 10: k_assoc_prep<10><<<g, AB, 0, s>>>(v); break;
+    case 2: k_assoc_prep<2><<<g, PB, 0, s>>>(v); break;
+    case 3: k_assoc_prep<3><<<g, PB, 0, s>>>(v); break;
+    case 4: k_assoc_prep<4><<<g, PB, 0, s>>>(v); break;
+    case 5: k_assoc_prep<5><<<g, PB, 0, s>>>(v); break;
+    case 6: k_assoc_prep<6><<<g, PB, 0, s>>>(v); break;
+    case 7: k_assoc_prep<7><<<g, PB, 0, s>>>(v); break;
+    case 8: k_assoc_prep<8><<<g, PB, 0, s>>>(v); break;
+    case 9: k_assoc_prep<9><<<g, PB, 0, s>>>(v); break;
+    case 10: k_assoc_prep<10><<<g, PB, 0, s>>>(v); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
