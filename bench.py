@@ -522,12 +522,15 @@ def _serve(n, reqs, budget, max_active, gens_per_launch):
 
     th = threading.Thread(target=producer)
     th.start()
+    progress("serving %d requests (%d slots)" % (len(reqs), max_active))
     while len(infos) < len(reqs) and not errors:
         rid = srv.wait(1000)
         if rid < 0:
             continue
         st, info = srv.fetch(rid)
         infos[rid] = info
+        if len(infos) % 50 == 0:
+            progress("%d / %d runs done" % (len(infos), len(reqs)))
     th.join()
     stats = srv.stats()
     srv.close()

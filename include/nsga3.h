@@ -124,7 +124,8 @@ nsga3_status nsga3_init(nsga3_ctx* ctx, void* stream);
 nsga3_status nsga3_vary(nsga3_ctx* ctx, void* stream);
 
 /* One generation (Alg. 1): variation, merge, selection, next population;
- * advances the counter by one.  One CUDA-graph launch. Needs opts.W. */
+ * advances the counter by one.  One CUDA-graph launch of plain kernel nodes
+ * (every front is peeled inside one cooperative kernel). Needs opts.W. */
 nsga3_status nsga3_step(nsga3_ctx* ctx, void* stream);
 
 /* `generations` calls of nsga3_step. */
@@ -186,13 +187,13 @@ nsga3_status nsga3_get_association(nsga3_ctx* ctx, int32_t* pi, double* dist);
  */
 nsga3_status nsga3_phase_times(nsga3_ctx* ctx, float* ms, int n);
 
-/* Kernel launches made by the last replayed generation or selection
- * (fixed launches plus one per peel pass).  Synchronous. */
+/* Kernel launches made by the last replayed generation or selection (the
+ * peel is one launch whatever the number of fronts).  Synchronous. */
 nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches);
 
 /* Kernel launches made on behalf of ctx since nsga3_create (the set-up
- * kernels excluded): initialisation, variation, every replayed generation or
- * selection and each of their peel passes.  Synchronous. */
+ * kernels excluded): initialisation, variation and every replayed generation
+ * or selection.  Synchronous. */
 nsga3_status nsga3_total_launches(nsga3_ctx* ctx, int64_t* launches);
 
 /* ------------------------------------------------------------------------

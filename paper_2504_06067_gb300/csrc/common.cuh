@@ -41,7 +41,7 @@ enum : uint32_t {
 struct Ctrl {
     uint32_t gen;            // Philox generation counter (word 1 of the counter)
     int32_t status;          // DEV_* of the last failure, 0 if none
-    int32_t k;               // front being built by the current peel pass
+    uint32_t bar_count;      // grid barrier of the peel: arrivals
     int32_t cum;             // members ranked so far
     int32_t l;               // selecting front (first with cum >= N)
     int32_t nS;              // |S| = members of fronts < l
@@ -50,8 +50,8 @@ struct Ctrl {
     int32_t need_niche;      // K < |F_l|
     int32_t fallback;        // normalization used the nadir fallback
     int32_t passes;          // peel passes (kernel launches) in the last selection
-    uint32_t front_size;     // size of the front being built
-    uint32_t chunks_done;    // completion ticket of the peel pass
+    uint32_t pfs[3];         // front sizes of peel passes k mod 3
+    uint32_t bar_gen;        // grid barrier of the peel: generation
     int32_t nT;              // |S u F_l| (association set)
     int32_t Lstar;           // niche level threshold L*
     int32_t rlev;            // refs taken at level L*
@@ -60,8 +60,7 @@ struct Ctrl {
     int32_t recheck_miss;    // debug: association misses found by the full FP64 recheck
     int32_t nlarge;          // references whose partial take needs the block-wide select
     uint32_t peel_rows;      // dominator word-rows in the peel's row lists, all passes
-    uint32_t front_words;    // nonzero mask words of the front being built
-    int32_t peel_more;       // eager mode: 1 if another peel pass is needed
+
     int32_t ncand;           // association candidates written by the scan
     int32_t nslow;           // points sent to the full FP64 association scan
     uint32_t ext_done;       // completion ticket of the extreme-point blocks

@@ -1,13 +1,13 @@
 // engine.cu -- NSGA-III run context, device workspace, CUDA-graph capture of
 // a selection / a generation, and the C ABI declared in include/nsga3.h.
 //
-// A generation is captured once per context as a CUDA graph:
-//   vary+eval -> reset -> sort -> dominance -> WHILE(peel pass) -> post-peel
-//   -> ideal, extremes+solve, prep, scan, level, bucket, pick
-//   -> compaction -> gather -> gen++
-// The WHILE node replays the peel kernel until its last CTA clears the
-// condition (one pass per front); the niching kernels return at once when
-// |S| + |F_l| == N.  A replay never returns to the host.
+// A generation is captured once per context as a CUDA graph of plain
+// kernel nodes:
+//   vary+eval -> reset -> sort -> dominance -> peel (one cooperative launch,
+//   every front) -> post-peel -> ideal, extremes+solve, prep, scan, level,
+//   bucket, pick -> compaction -> gather -> gen++
+// The niching kernels return at once when |S| + |F_l| == N.  A replay never
+// returns to the host.
 #include <cstdarg>
 #include <cstdlib>
 #include <cstdio>
@@ -46,9 +46,8 @@ struct nsga3_ctx {
     RunView vs{};   // selection view (own objective buffer)
     std::vector<void*> allocs;
     cudaGraphExec_t gx_select = nullptr, gx_step = nullptr;
-    cudaStream_t cap = nullptr, cap2 = nullptr;
+    cudaStream_t cap = nullptr;
     cudaEvent_t ev[EV_COUNT] = {};
-    int nsplit = 1;
     int last_kind = 0;  // 1 = select, 2 = step
     long long host_launches = 0;  // kernels launched by calls (peel passes counted on the device)
     DeviceArena* arena = nullptr;  // workspace source (nullptr: cudaMalloc per buffer)
@@ -125,29 +124,6 @@ nsga3_status alloc(nsga3_ctx* ctx, T** p, size_t count)
         if (s_ != NSGA3_OK) return s_;                       \
     } while (0)
 
-// Adds a conditional node after the capture's current dependencies and
-// returns its body graph; later captured work depends on the node.
-nsga3_status add_conditional(nsga3_ctx* ctx, cudaStream_t s, cudaGraphConditionalNodeType type,
-                             unsigned dflt, cudaGraphConditionalHandle* h, cudaGraph_t* body)
-{
-    cudaStreamCaptureStatus st;
-    cudaGraph_t g = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t nd = 0;
-    CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
-    if (st != cudaStreamCaptureStatusActive) return fail(ctx, NSGA3_ECUDA, "stream is not capturing");
-    CK(cudaGraphConditionalHandleCreate(h, g, dflt, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
-    p.conditional.handle = *h;
-    p.conditional.type = type;
-    p.conditional.size = 1;
-    cudaGraphNode_t node;
-    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
-    *body = p.conditional.phGraph_out[0];
-    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-    return NSGA3_OK;
-}
-
 nsga3_status record_event(nsga3_ctx* ctx, cudaStream_t s, int which, bool events)
 {
     if (!events) return NSGA3_OK;
@@ -159,8 +135,7 @@ nsga3_status record_event(nsga3_ctx* ctx, cudaStream_t s, int which, bool events
 }
 
 // Records the selection pipeline of view `v` into the capture running on `s`
-// (`s2` is a spare stream used to capture conditional bodies).
-nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, cudaStream_t s2,
+nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s,
                               bool check_finite, bool events)
 {
     CK(launch_sel_reset(v, s));
@@ -171,21 +146,10 @@ nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, 
     CK(launch_dominance(v, s));
     st = record_event(ctx, s, EV_DOM, events);
     if (st) return st;
-    cudaGraphConditionalHandle h_peel;
-    cudaGraph_t body;
-    st = add_conditional(ctx, s, cudaGraphCondTypeWhile, 1u, &h_peel, &body);
-    if (st) return st;
-    CK(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    {
-        cudaError_t e = launch_peel(v, ctx->nsplit, h_peel, 1, s2);
-        cudaGraph_t tmp;
-        cudaError_t e2 = cudaStreamEndCapture(s2, &tmp);
-        CK(e);
-        CK(e2);
-    }
+    CK(launch_peel(v, ctx->num_sms, s));
     st = record_event(ctx, s, EV_PEEL, events);
     if (st) return st;
-    CK(launch_post_peel(v, 0, 0, s));
+    CK(launch_post_peel(v, s));
     // the niching kernels return at once when no niching is needed: a graph
     // IF node costs more than their empty launches
     CK(launch_norm_ideal(v, s));
@@ -201,14 +165,14 @@ nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, 
     return NSGA3_OK;
 }
 
-nsga3_status record_generation(nsga3_ctx* ctx, cudaStream_t s, cudaStream_t s2, bool events)
+nsga3_status record_generation(nsga3_ctx* ctx, cudaStream_t s, bool events)
 {
     nsga3_status st = record_event(ctx, s, EV_START, events);
     if (st) return st;
     CK(launch_vary_eval(ctx->v, s));
     st = record_event(ctx, s, EV_VARY, events);
     if (st) return st;
-    st = record_selection(ctx, ctx->v, s, s2, false, events);
+    st = record_selection(ctx, ctx->v, s, false, events);
     if (st) return st;
     CK(launch_gather(ctx->v, s));
     CK(launch_bump_gen(ctx->v, s));
@@ -217,7 +181,7 @@ nsga3_status record_generation(nsga3_ctx* ctx, cudaStream_t s, cudaStream_t s2, 
 
 // Eager execution of the same kernels without graphs: the peel loop and
 // the niching branch are decided on the host from the control block.  Used
-// for profiling tools that cannot see inside conditional graphs.
+// for profiling tools that do not profile graph kernel nodes.
 nsga3_status eager_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, bool check_finite)
 {
     CK(launch_sel_reset(v, s));
@@ -228,15 +192,10 @@ nsga3_status eager_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, b
     CK(launch_dominance(v, s));
     st = record_event(ctx, s, EV_DOM, true);
     if (st) return st;
-    int32_t more = 1;
-    for (int pass = 0; more && pass <= ctx->n2; ++pass) {
-        CK(launch_peel(v, ctx->nsplit, 0, 0, s));
-        CK(cudaMemcpyAsync(&more, &v.ctrl->peel_more, sizeof more, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-    }
+    CK(launch_peel(v, ctx->num_sms, s));
     st = record_event(ctx, s, EV_PEEL, true);
     if (st) return st;
-    CK(launch_post_peel(v, 0, 0, s));
+    CK(launch_post_peel(v, s));
     int32_t hdr[2] = {0, 0};  // status, need_niche
     CK(cudaMemcpyAsync(&hdr[0], &v.ctrl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&hdr[1], &v.ctrl->need_niche, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -278,7 +237,7 @@ nsga3_status build_graphs(nsga3_ctx* ctx)
     CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeRelaxed));
     nsga3_status st = record_event(ctx, ctx->cap, EV_START, true);
     if (!st) st = record_event(ctx, ctx->cap, EV_VARY, true);
-    if (!st) st = record_selection(ctx, ctx->vs, ctx->cap, ctx->cap2, true, true);
+    if (!st) st = record_selection(ctx, ctx->vs, ctx->cap, true, true);
     if (!st) st = record_event(ctx, ctx->cap, EV_END, true);
     {
         cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
@@ -293,7 +252,7 @@ nsga3_status build_graphs(nsga3_ctx* ctx)
     g = nullptr;
     if (!ctx->has_W) return NSGA3_OK;
     CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeRelaxed));
-    st = record_generation(ctx, ctx->cap, ctx->cap2, true);
+    st = record_generation(ctx, ctx->cap, true);
     {
         cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
         if (st) {
@@ -504,7 +463,6 @@ nsga3_status setup(nsga3_ctx* ctx)
     int32_t* bj = const_cast<int32_t*>(v.blk_j);
 
     CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
-    CK(cudaStreamCreateWithFlags(&ctx->cap2, cudaStreamNonBlocking));
     for (int e = 0; e < EV_COUNT; ++e) CK(cudaEventCreate(&ctx->ev[e]));
     cudaStream_t s = ctx->cap;
     CK(cudaMemsetAsync(v.ctrl, 0, sizeof(Ctrl), s));
@@ -523,15 +481,19 @@ nsga3_status setup(nsga3_ctx* ctx)
     CK(cudaStreamSynchronize(s));
     {
         std::vector<double> Zh((size_t)w * m);
-        CK(cudaMemcpy(Zh.data(), Zd, Zh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpyAsync(Zh.data(), Zd, Zh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
         std::vector<float> hc, hz;
         std::vector<float2> hr;
         std::vector<int32_t> hj;
         build_ref_blocks(m, w, M4, Zh, hc, hr, hz, hj);
-        CK(cudaMemcpy(bc, hc.data(), hc.size() * sizeof(float), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(br, hr.data(), hr.size() * sizeof(float2), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(bz, hz.data(), hz.size() * sizeof(float), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(bj, hj.data(), hj.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        // copies on the context's own stream: no implicit synchronisation with
+        // other streams of the process (runs of a server keep executing)
+        CK(cudaMemcpyAsync(bc, hc.data(), hc.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(br, hr.data(), hr.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(bz, hz.data(), hz.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(bj, hj.data(), hj.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
         ctx->vs.blk_c = bc;
         ctx->vs.blk_r = br;
         ctx->vs.blk_z = bz;
@@ -552,7 +514,6 @@ nsga3_status setup(nsga3_ctx* ctx)
         cudaGetLastError();
         return fail(ctx, NSGA3_EINVAL, "%d reference directions exceed the association scan's tables", w);
     }
-    ctx->nsplit = peel_nsplit(v, ctx->num_sms);
     return build_graphs(ctx);
 }
 
@@ -563,15 +524,22 @@ nsga3_status init_attributes(nsga3_ctx* ctx)
     std::lock_guard<std::mutex> lk(g_attr_mutex);
     if (g_attr_done) return NSGA3_OK;
     CK(niche_init_attributes());
+    CK(peel_init_attributes());
+    CK(assoc_init_attributes());
     g_attr_done = true;
     return NSGA3_OK;
 }
 
-nsga3_status device_status(nsga3_ctx* ctx, bool clear)
+// Reads (and clears) the sticky device status on `s`, synchronising only s.
+nsga3_status device_status(nsga3_ctx* ctx, cudaStream_t s, bool clear)
 {
     int32_t st = 0;
-    CK(cudaMemcpy(&st, &ctx->v.ctrl->status, sizeof st, cudaMemcpyDeviceToHost));
-    if (clear && st) CK(cudaMemset(&ctx->v.ctrl->status, 0, sizeof st));
+    CK(cudaMemcpyAsync(&st, &ctx->v.ctrl->status, sizeof st, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (clear && st) {
+        CK(cudaMemsetAsync(&ctx->v.ctrl->status, 0, sizeof st, s));
+        CK(cudaStreamSynchronize(s));
+    }
     return (nsga3_status)st;
 }
 
@@ -677,7 +645,6 @@ void ctx_destroy(nsga3_ctx* ctx, bool sync_device)
     for (int e = 0; e < EV_COUNT; ++e)
         if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
-    if (ctx->cap2) cudaStreamDestroy(ctx->cap2);
     for (void* p : ctx->allocs) {
         if (ctx->arena)
             ctx->arena->release(p);
@@ -690,11 +657,8 @@ void ctx_destroy(nsga3_ctx* ctx, bool sync_device)
 
 nsga3_status ctx_launches(nsga3_ctx* ctx, void* stream, long long* launches)
 {
-    unsigned long long passes = 0;
-    cudaStream_t s = (cudaStream_t)stream;
-    CK(cudaMemcpyAsync(&passes, &ctx->v.ctrl->passes_total, sizeof passes, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    *launches = ctx->host_launches + (long long)passes;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    *launches = ctx->host_launches;
     return NSGA3_OK;
 }
 
@@ -770,7 +734,7 @@ nsga3_status nsga3_select(nsga3_ctx* ctx, const float* objs, int32_t* ranks, int
     } else {
         CK(cudaGraphLaunch(ctx->gx_select, s));
     }
-    ctx->host_launches += 19;
+    ctx->host_launches += 20;
     CK(cudaMemcpyAsync(ranks, ctx->vs.rank2, (size_t)ctx->n2 * sizeof(int32_t), cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(selected, ctx->vs.sel, (size_t)ctx->N * sizeof(int32_t), cudaMemcpyDefault, s));
     ctx->last_kind = 1;
@@ -808,7 +772,7 @@ nsga3_status nsga3_step(nsga3_ctx* ctx, void* stream)
     } else {
         CK(cudaGraphLaunch(ctx->gx_step, (cudaStream_t)stream));
     }
-    ctx->host_launches += 22;
+    ctx->host_launches += 23;
     ctx->last_kind = 2;
     return NSGA3_OK;
 }
@@ -844,12 +808,11 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
             ctx->gx_batch = nullptr;
         }
         // one branch per run: fork from the capture stream with events
-        std::vector<cudaStream_t> br(n), br2(n);
+        std::vector<cudaStream_t> br(n);
         std::vector<cudaEvent_t> evs(n + 1);
         nsga3_status st = NSGA3_OK;
         for (int r = 0; r < n && !st; ++r) {
-            if (cudaStreamCreateWithFlags(&br[r], cudaStreamNonBlocking) != cudaSuccess ||
-                cudaStreamCreateWithFlags(&br2[r], cudaStreamNonBlocking) != cudaSuccess)
+            if (cudaStreamCreateWithFlags(&br[r], cudaStreamNonBlocking) != cudaSuccess)
                 st = fail(ctx, NSGA3_ECUDA, "stream creation failed");
         }
         for (int r = 0; r <= n && !st; ++r)
@@ -866,7 +829,7 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
                     st = fail(ctx, NSGA3_ECUDA, "fork wait failed");
                     break;
                 }
-                nsga3_status rs = record_generation(ctxs[r], br[r], br2[r], false);
+                nsga3_status rs = record_generation(ctxs[r], br[r], false);
                 if (rs) {
                     st = rs;
                     ctx->err = ctxs[r]->err;
@@ -885,7 +848,6 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
         }
         for (int r = 0; r < n; ++r) {
             if (br[r]) cudaStreamDestroy(br[r]);
-            if (br2[r]) cudaStreamDestroy(br2[r]);
         }
         for (int r = 0; r <= n; ++r)
             if (evs[r]) cudaEventDestroy(evs[r]);
@@ -896,7 +858,7 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
     for (int g = 0; g < generations; ++g) CK(cudaGraphLaunch(ctx->gx_batch, (cudaStream_t)stream));
     for (int r = 0; r < n; ++r) {
         ctxs[r]->last_kind = 3;
-        ctxs[r]->host_launches += 22LL * generations;
+        ctxs[r]->host_launches += 23LL * generations;
     }
     return NSGA3_OK;
 }
@@ -954,7 +916,7 @@ nsga3_status nsga3_sync(nsga3_ctx* ctx, void* stream)
 {
     if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
     CK(cudaStreamSynchronize((cudaStream_t)stream));
-    return device_status(ctx, true);
+    return device_status(ctx, (cudaStream_t)stream, true);
 }
 
 nsga3_status nsga3_get_selection_info(nsga3_ctx* ctx, int32_t* info)
@@ -1020,25 +982,20 @@ nsga3_status nsga3_phase_times(nsga3_ctx* ctx, float* ms, int n)
 nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches)
 {
     if (!ctx || !launches) return fail(ctx, NSGA3_EINVAL, "null argument");
-    Ctrl c;
     CK(cudaDeviceSynchronize());
-    CK(cudaMemcpy(&c, ctx->v.ctrl, sizeof c, cudaMemcpyDeviceToHost));
-    // reset, 3 sort, dominance, post-peel, 11 niching (they return at once
-    // when no niching is needed), compaction (+ finite check for a selection;
-    // + variation, objective, gather, counter for a generation), and one per
-    // peel pass
-    int fixed = (ctx->last_kind == 1) ? 19 : 22;
-    *launches = fixed + c.passes;
+    // reset, 3 sort, dominance, peel (every pass), post-peel, 11 niching (they
+    // return at once when no niching is needed), compaction (+ finite check
+    // for a selection; + variation, objective, gather, counter for a
+    // generation)
+    *launches = (ctx->last_kind == 1) ? 20 : 23;
     return NSGA3_OK;
 }
 
 nsga3_status nsga3_total_launches(nsga3_ctx* ctx, int64_t* launches)
 {
     if (!ctx || !launches) return fail(ctx, NSGA3_EINVAL, "null argument");
-    unsigned long long passes = 0;
     CK(cudaDeviceSynchronize());
-    CK(cudaMemcpy(&passes, &ctx->v.ctrl->passes_total, sizeof passes, cudaMemcpyDeviceToHost));
-    *launches = ctx->host_launches + (long long)passes;
+    *launches = ctx->host_launches;
     return NSGA3_OK;
 }
 

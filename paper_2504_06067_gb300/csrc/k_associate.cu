@@ -456,28 +456,29 @@ cudaError_t launch_assoc_scan(const RunView& v, int num_sms, cudaStream_t s)
     }
 }
 
-// Shared-memory opt-in of the scan for this run's block count; fails when the
-// block tables do not fit (about 5,000 blocks of 32 references).  The opt-in
-// is a property of the kernel, shared by every context of the process, so it
-// only ever grows (serialised by the caller).
+// The scan's shared-memory opt-in is set once per process, at its maximum,
+// before any launch (changing a kernel's attribute while graphs that launch
+// it run on other streams is avoided); a run only checks that its block
+// tables fit (about 5,000 blocks of 32 references).
+constexpr size_t SCAN_SMEM_MAX = 220 * 1024;
+
 cudaError_t assoc_prepare(const RunView& v)
 {
-    static size_t granted[NSGA3_MAX_M + 1] = {0};
-    const size_t sm = scan_smem(v);
-    if (sm > 220 * 1024) return cudaErrorInvalidValue;
     if (v.m < 2 || v.m > NSGA3_MAX_M) return cudaErrorInvalidValue;
-    if (sm <= granted[v.m]) return cudaSuccess;
-    granted[v.m] = sm;
-    switch (v.m) {
-    case 2: return attr_m<2>(sm);
-    case 3: return attr_m<3>(sm);
-    case 4: return attr_m<4>(sm);
-    case 5: return attr_m<5>(sm);
-    case 6: return attr_m<6>(sm);
-    case 7: return attr_m<7>(sm);
-    case 8: return attr_m<8>(sm);
-    case 9: return attr_m<9>(sm);
-    case 10: return attr_m<10>(sm);
-    default: return cudaErrorInvalidValue;
-    }
+    return scan_smem(v) <= SCAN_SMEM_MAX ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t assoc_init_attributes()
+{
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = attr_m<2>(SCAN_SMEM_MAX);
+    if (e == cudaSuccess) e = attr_m<3>(SCAN_SMEM_MAX);
+    if (e == cudaSuccess) e = attr_m<4>(SCAN_SMEM_MAX);
+    if (e == cudaSuccess) e = attr_m<5>(SCAN_SMEM_MAX);
+    if (e == cudaSuccess) e = attr_m<6>(SCAN_SMEM_MAX);
+    if (e == cudaSuccess) e = attr_m<7>(SCAN_SMEM_MAX);
+    if (e == cudaSuccess) e = attr_m<8>(SCAN_SMEM_MAX);
+    if (e == cudaSuccess) e = attr_m<9>(SCAN_SMEM_MAX);
+    if (e == cudaSuccess) e = attr_m<10>(SCAN_SMEM_MAX);
+    return e;
 }

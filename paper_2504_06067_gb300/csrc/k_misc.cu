@@ -32,7 +32,10 @@ __global__ void k_sel_reset(RunView v)
     }
     if (tid == 0) {
         Ctrl* c = v.ctrl;
-        c->k = 0;
+        c->bar_count = 0u;
+        c->pfs[0] = 0u;
+        c->pfs[1] = 0u;
+        c->pfs[2] = 0u;
         c->cum = 0;
         c->l = -1;
         c->nS = 0;
@@ -41,8 +44,6 @@ __global__ void k_sel_reset(RunView v)
         c->need_niche = 0;
         c->fallback = 0;
         c->passes = 0;
-        c->front_size = 0u;
-        c->chunks_done = 0u;
         c->nT = 0;
         c->Lstar = -1;
         c->rlev = 0;
@@ -56,7 +57,6 @@ __global__ void k_sel_reset(RunView v)
         c->f0lo = 0xffffffffu;
         c->f0hi = 0u;
         c->cmp_done = 0u;
-        c->front_words = 0u;
         c->overflow = 0;
         c->recheck_miss = 0;
         for (int q = 0; q < NSGA3_MAX_M; ++q) c->zmin[q] = 0xffffffffu;

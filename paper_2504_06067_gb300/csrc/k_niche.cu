@@ -261,6 +261,10 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
         const int rp = rhop_of(j);
         if (rp > 0) {
             const int lo = rho_of(j), hi = lo + rp;
+            if (lo < 0 || rp > v.n2) {  // counts out of range: an invariant failed upstream
+                set_status(c, DEV_EINTERNAL);
+                continue;
+            }
             if (lo < LCAP) atomicAdd(&sh.lev[lo], 1);
             if (hi < LCAP) atomicAdd(&sh.lev[hi], -1);
             mymax = max(mymax, hi);
@@ -471,8 +475,15 @@ __global__ void k_bucket(RunView v)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.n2 || v.rank2[i] != c->l) return;
     const int j = v.pi[i];
+    if (j < 0 || j >= v.w) {
+        set_status(c, DEV_EINTERNAL);
+        return;
+    }
     const int p = atomicAdd(&v.cursor[j], 1);
-    v.bucket[v.ref_off[j] + p] = i;
+    if (p < v.rhop[j])
+        v.bucket[v.ref_off[j] + p] = i;
+    else
+        set_status(c, DEV_EINTERNAL);
 }
 
 __device__ __forceinline__ void mark_member(const RunView& v, int i)

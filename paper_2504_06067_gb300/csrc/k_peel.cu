@@ -23,156 +23,193 @@ constexpr int PTMAX = 1024;       // threads per CTA (runtime: 256, 512 or 1024)
 constexpr int PWMAX = PTMAX / 32;
 constexpr int LISTCAP = 2048;
 
-__global__ void __launch_bounds__(PTMAX) k_peel(RunView v, cudaGraphConditionalHandle h, int in_graph)
+// Grid barrier of the cooperative peel, with a bounded wait.  Returns false
+// (and records NSGA3_ETIMEOUT) when the other CTAs did not arrive in time.
+constexpr unsigned SPIN_LIMIT = 1u << 24;
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned x;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(x) : "l"(p) : "memory");
+    return x;
+}
+
+__device__ bool grid_sync(Ctrl* c, int* s_ok)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = ld_acquire(&c->bar_gen);
+        __threadfence();
+        if (atomicAdd(&c->bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(&c->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&c->bar_gen, 1u);
+        } else {
+            unsigned it = 0;
+            while (ld_acquire(&c->bar_gen) == g) {
+                if (++it > SPIN_LIMIT) {
+                    set_status(c, DEV_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+__global__ void __launch_bounds__(PTMAX) k_peel(RunView v)
 {
     __shared__ int red[PWMAX][NSGA3_PEEL_COLS];
     const int PT = blockDim.x, PW = PT >> 5;
     __shared__ uint2 list[LISTCAP];
     __shared__ int nlist;
+    __shared__ int s_ok;
     Ctrl* c = v.ctrl;
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-    if (read_status(c)) {
-        if (blockIdx.x == 0 && tid == 0) {
-            if (in_graph)
-                cudaGraphSetConditional(h, 0);
-            else
-                c->peel_more = 0;
-        }
-        return;
-    }
-    const int k = *(volatile int32_t*)&c->k;
+    if (read_status(c)) return;  // uniform: set only by earlier kernels
     const int nchunks = v.ld / NSGA3_PEEL_COLS;
-    const int chunk = blockIdx.x;
-    const int j0 = chunk * NSGA3_PEEL_COLS;
-    // prefetch this thread's column state (used after the reduction)
-    int my_rank = 0, my_cnt = 0;
-    if (tid < NSGA3_PEEL_COLS && j0 + tid < v.n2) {
-        my_rank = v.srank[j0 + tid];
-        my_cnt = v.cnt[j0 + tid];
-    }
-    // Dominators of a column have f_0 <= its f_0.  Keys are non-decreasing in
-    // bucket order and bcnt[b] is the end of bucket b, so the positions that
-    // can dominate this chunk end at bcnt[key of its last column].
-    const int jl = min(j0 + NSGA3_PEEL_COLS, v.n2) - 1;
-    int lim = 0;
-    if (jl >= j0) lim = (v.bcnt[v.skey[jl]] + 31) >> 5;
-    if (lim > v.NW) lim = v.NW;
+    // every CTA follows the same sequence of front sizes, so each keeps the
+    // pass state itself; CTA 0 also publishes it in ctrl
+    int cum = 0, l = -1;
+    for (int k = 0;; ++k) {
+        // the next pass's front-size slot was last read right after barrier
+        // k - 2, which every CTA has left
+        if (blockIdx.x == 0 && tid == 0) c->pfs[(k + 1) % 3] = 0u;
+        for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+            const int j0 = chunk * NSGA3_PEEL_COLS;
+            // prefetch this thread's column state (used after the reduction)
+            int my_rank = 0, my_cnt = 0;
+            if (tid < NSGA3_PEEL_COLS && j0 + tid < v.n2) {
+                my_rank = __ldcg(&v.srank[j0 + tid]);
+                my_cnt = __ldcg(&v.cnt[j0 + tid]);
+            }
+            // Dominators of a column have f_0 <= its f_0.  Keys are non-decreasing in
+            // bucket order and bcnt[b] is the end of bucket b, so the positions that
+            // can dominate this chunk end at bcnt[key of its last column].
+            const int jl = min(j0 + NSGA3_PEEL_COLS, v.n2) - 1;
+            int lim = 0;
+            if (jl >= j0) lim = (v.bcnt[v.skey[jl]] + 31) >> 5;
+            if (lim > v.NW) lim = v.NW;
 
-    uint32_t rw = (tid < NSGA3_PEEL_COLS / 32) ? v.rem[j0 / 32 + tid] : 0u;
-    const int any_rem = __syncthreads_or(rw != 0u);
+            uint32_t rw = (tid < NSGA3_PEEL_COLS / 32) ? __ldcg(&v.rem[j0 / 32 + tid]) : 0u;
+            const int any_rem = __syncthreads_or(rw != 0u);
 
-    uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    // pass 0 needs no words: the dominance build already counted every
-    // column's dominators into cnt[]
-    if (any_rem && k > 0) {
-        const uint4* base = reinterpret_cast<const uint4*>(v.Dom + j0) + lane;
-        const size_t ld4 = (size_t)v.ld / 4;
-        {
-            const uint32_t* prev = v.front + ((k - 1) & 1) * v.NW;
-            for (int wb = 0; wb < lim; wb += LISTCAP) {
-                const int whe = min(wb + LISTCAP, lim);
-                if (tid == 0) nlist = 0;
-                __syncthreads();
-                for (int w0 = wb + warp * 32; w0 < whe; w0 += PT) {
-                    const int w = w0 + lane;
-                    const uint32_t msk = w < whe ? prev[w] : 0u;
-                    const unsigned bal = __ballot_sync(0xffffffffu, msk != 0u);
-                    int at = 0;
-                    if (lane == 0 && bal) at = atomicAdd(&nlist, __popc(bal));
-                    at = __shfl_sync(0xffffffffu, at, 0);
-                    if (msk) list[at + __popc(bal & ((1u << lane) - 1u))] = make_uint2((unsigned)w, msk);
-                }
-                __syncthreads();
-                const int n = nlist;
-                if (tid == 0) atomicAdd(&c->peel_rows, (unsigned)n);
-                int e = warp;
-                for (; e + 3 * PW < n; e += 4 * PW) {
-                    uint2 L[4];
-                    uint4 x[4];
+            uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+            // pass 0 needs no words: the dominance build already counted every
+            // column's dominators into cnt[]
+            if (any_rem && k > 0) {
+                const uint4* base = reinterpret_cast<const uint4*>(v.Dom + j0) + lane;
+                const size_t ld4 = (size_t)v.ld / 4;
+                {
+                    const uint32_t* prev = v.front + ((k - 1) & 1) * v.NW;
+                    for (int wb = 0; wb < lim; wb += LISTCAP) {
+                        const int whe = min(wb + LISTCAP, lim);
+                        if (tid == 0) nlist = 0;
+                        __syncthreads();
+                        for (int w0 = wb + warp * 32; w0 < whe; w0 += PT) {
+                            const int w = w0 + lane;
+                            const uint32_t msk = w < whe ? __ldcg(&prev[w]) : 0u;
+                            const unsigned bal = __ballot_sync(0xffffffffu, msk != 0u);
+                            int at = 0;
+                            if (lane == 0 && bal) at = atomicAdd(&nlist, __popc(bal));
+                            at = __shfl_sync(0xffffffffu, at, 0);
+                            if (msk) list[at + __popc(bal & ((1u << lane) - 1u))] = make_uint2((unsigned)w, msk);
+                        }
+                        __syncthreads();
+                        const int n = nlist;
+                        if (tid == 0) atomicAdd(&c->peel_rows, (unsigned)n);
+                        int e = warp;
+                        for (; e + 3 * PW < n; e += 4 * PW) {
+                            uint2 L[4];
+                            uint4 x[4];
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        L[t] = list[e + PW * t];
-                        x[t] = __ldg(base + (size_t)L[t].x * ld4);
-                    }
+                            for (int t = 0; t < 4; ++t) {
+                                L[t] = list[e + PW * t];
+                                x[t] = __ldg(base + (size_t)L[t].x * ld4);
+                            }
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        a0 += __popc(x[t].x & L[t].y);
-                        a1 += __popc(x[t].y & L[t].y);
-                        a2 += __popc(x[t].z & L[t].y);
-                        a3 += __popc(x[t].w & L[t].y);
+                            for (int t = 0; t < 4; ++t) {
+                                a0 += __popc(x[t].x & L[t].y);
+                                a1 += __popc(x[t].y & L[t].y);
+                                a2 += __popc(x[t].z & L[t].y);
+                                a3 += __popc(x[t].w & L[t].y);
+                            }
+                        }
+                        for (; e < n; e += PW) {
+                            const uint2 L = list[e];
+                            const uint4 x = __ldg(base + (size_t)L.x * ld4);
+                            a0 += __popc(x.x & L.y);
+                            a1 += __popc(x.y & L.y);
+                            a2 += __popc(x.z & L.y);
+                            a3 += __popc(x.w & L.y);
+                        }
+                        __syncthreads();
                     }
                 }
-                for (; e < n; e += PW) {
-                    const uint2 L = list[e];
-                    const uint4 x = __ldg(base + (size_t)L.x * ld4);
-                    a0 += __popc(x.x & L.y);
-                    a1 += __popc(x.y & L.y);
-                    a2 += __popc(x.z & L.y);
-                    a3 += __popc(x.w & L.y);
+            }
+            red[warp][lane * 4 + 0] = (int)a0;
+            red[warp][lane * 4 + 1] = (int)a1;
+            red[warp][lane * 4 + 2] = (int)a2;
+            red[warp][lane * 4 + 3] = (int)a3;
+            __syncthreads();
+            // this CTA owns its 128 columns: update the counts and rank the new front
+            if (tid < NSGA3_PEEL_COLS) {
+                int sum = 0;
+                for (int w = 0; w < PW; ++w) sum += red[w][tid];
+                const int j = j0 + tid;
+                bool nf = false;
+                if (j < v.n2 && my_rank < 0) {
+                    const int cv = my_cnt - sum;
+                    if (k > 0) v.cnt[j] = cv;
+                    if (cv == 0) {
+                        v.srank[j] = k;
+                        nf = true;
+                    }
                 }
-                __syncthreads();
+                const uint32_t word = __ballot_sync(0xffffffffu, nf);
+                if (lane == 0) {
+                    const int wd = j0 / 32 + warp;
+                    v.front[(k & 1) * v.NW + wd] = word;
+                    v.rem[wd] = __ldcg(&v.rem[wd]) & ~word;
+                    if (word) atomicAdd(&c->pfs[k % 3], (unsigned)__popc(word));
+                }
             }
-        }
-    }
-    red[warp][lane * 4 + 0] = (int)a0;
-    red[warp][lane * 4 + 1] = (int)a1;
-    red[warp][lane * 4 + 2] = (int)a2;
-    red[warp][lane * 4 + 3] = (int)a3;
-    __syncthreads();
-    // this CTA owns its 128 columns: update the counts and rank the new front
-    if (tid < NSGA3_PEEL_COLS) {
-        int sum = 0;
-        for (int w = 0; w < PW; ++w) sum += red[w][tid];
-        const int j = j0 + tid;
-        bool nf = false;
-        if (j < v.n2 && my_rank < 0) {
-            const int cv = my_cnt - sum;
-            if (k > 0) v.cnt[j] = cv;
-            if (cv == 0) {
-                v.srank[j] = k;
-                nf = true;
-            }
-        }
-        const uint32_t word = __ballot_sync(0xffffffffu, nf);
-        if (lane == 0) {
-            const int wd = j0 / 32 + warp;
-            v.front[(k & 1) * v.NW + wd] = word;
-            v.rem[wd] &= ~word;
-            if (word) {
-                atomicAdd(&c->front_size, (unsigned)__popc(word));
-                atomicAdd(&c->front_words, 1u);
-            }
-        }
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid != 0) return;
-    const unsigned g = atomicAdd(&c->chunks_done, 1u);
-    if (g != (unsigned)(nchunks - 1)) return;
 
-    // last chunk of the pass: close front k and decide whether to continue
-    __threadfence();
-    const int fs = (int)atomicAdd(&c->front_size, 0u);
-    const int cum = c->cum + fs;
-    c->cum = cum;
-    c->passes += 1;
-    c->passes_total += 1ull;
-    if (c->l < 0 && cum >= v.N) {
-        c->l = k;
-        c->nFl = fs;
-        c->nS = cum - fs;
-        c->K = v.N - (cum - fs);
-        c->need_niche = c->K < fs ? 1 : 0;
+            __syncthreads();  // red and list are reused by the next chunk
+        }
+        if (!grid_sync(c, &s_ok)) return;
+        // close front k (the same decision in every CTA)
+        const int fs = (int)__ldcg(&c->pfs[k % 3]);
+        const int ncum = cum + fs;
+        bool first = false;
+        if (l < 0 && ncum >= v.N) {
+            l = k;
+            first = true;
+        }
+        const bool broken = fs == 0 && ncum < v.n2;
+        const bool more = !broken && fs > 0 && ncum < v.n2 && (v.full_sort || l < 0);
+        if (blockIdx.x == 0 && tid == 0) {
+            c->cum = ncum;
+            c->passes = k + 1;
+            c->passes_total += 1ull;
+            if (first) {
+                c->l = k;
+                c->nFl = fs;
+                c->nS = cum;
+                c->K = v.N - cum;
+                c->need_niche = (v.N - cum) < fs ? 1 : 0;
+            }
+            if (broken) set_status(c, DEV_EINTERNAL);
+        }
+        cum = ncum;
+        if (!more) break;
     }
-    if (fs == 0 && cum < v.n2) set_status(c, DEV_EINTERNAL);
-    const bool more = fs > 0 && cum < v.n2 && (v.full_sort || c->l < 0);
-    c->front_words = 0u;
-    c->front_size = 0;
-    c->chunks_done = 0;
-    c->k = k + 1;
-    c->peel_more = more ? 1 : 0;
-    __threadfence();
-    if (in_graph) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // ranks back to the original order
@@ -182,32 +219,38 @@ __global__ void k_post_peel(RunView v)
     if (p < v.n2) v.rank2[v.perm[p]] = v.srank[p];
 }
 
+int g_peel_occ = 0;  // resident 512-thread peel CTAs per SM, set at initialisation
+constexpr int PEEL_THREADS = 512;
+
 }  // namespace
 
-// The peel launches one CTA per column chunk; this returns the SM count the
-// launch uses to size its CTAs.
-int peel_nsplit(const RunView& v, int num_sms)
+// One cooperative launch for all passes: at most as many CTAs as can be
+// resident at once (the grid barrier needs them all), at most one per chunk.
+cudaError_t launch_peel(const RunView& v, int num_sms, cudaStream_t s)
 {
-    (void)v;
-    return num_sms;
-}
-
-cudaError_t launch_peel(const RunView& v, int nsplit, cudaGraphConditionalHandle h, int in_graph,
-                        cudaStream_t s)
-{
-    // every chunk's CTA resident in one wave: one 1024-thread CTA per SM fits
-    // (registers), two of 512, four of 256
     const int nchunks = v.ld / NSGA3_PEEL_COLS;
-    const int threads = nchunks <= nsplit ? 1024 : (nchunks <= 2 * nsplit ? 512 : 256);
-    k_peel<<<nchunks, threads, 0, s>>>(v, h, in_graph);
-    return cudaGetLastError();
+    int grid = num_sms * (g_peel_occ > 0 ? g_peel_occ : 1);
+    if (grid > nchunks) grid = nchunks;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(PEEL_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_peel, v);
 }
 
-cudaError_t launch_post_peel(const RunView& v, cudaGraphConditionalHandle h_niche, int in_graph,
-                             cudaStream_t s)
+cudaError_t peel_init_attributes()
 {
-    (void)h_niche;
-    (void)in_graph;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_peel_occ, k_peel, PEEL_THREADS, 0);
+}
+
+cudaError_t launch_post_peel(const RunView& v, cudaStream_t s)
+{
     k_post_peel<<<(v.n2 + 255) / 256, 256, 0, s>>>(v);
     return cudaGetLastError();
 }

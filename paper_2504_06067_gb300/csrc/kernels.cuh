@@ -19,20 +19,18 @@ cudaError_t launch_sel_reset(const RunView& v, cudaStream_t s);
 cudaError_t launch_check_finite(const RunView& v, cudaStream_t s);
 cudaError_t launch_sort(const RunView& v, int num_sms, cudaStream_t s);
 cudaError_t launch_dominance(const RunView& v, cudaStream_t s);
-int peel_nsplit(const RunView& v, int num_sms);
-// in_graph = 1: launched by a graph WHILE node whose handle h it sets;
-// in_graph = 0: eager mode, the decision is left in ctrl->peel_more.
-cudaError_t launch_peel(const RunView& v, int nsplit, cudaGraphConditionalHandle h, int in_graph,
-                        cudaStream_t s);
-// ranks back to original order; in a graph also sets the niching IF handle
-cudaError_t launch_post_peel(const RunView& v, cudaGraphConditionalHandle h_niche, int in_graph,
-                             cudaStream_t s);
+// every peel pass in one cooperative launch (grid barrier between passes)
+cudaError_t launch_peel(const RunView& v, int num_sms, cudaStream_t s);
+cudaError_t peel_init_attributes();
+// ranks back to original order
+cudaError_t launch_post_peel(const RunView& v, cudaStream_t s);
 cudaError_t launch_norm_ideal(const RunView& v, cudaStream_t s);
 cudaError_t launch_norm_extreme(const RunView& v, cudaStream_t s);
 cudaError_t launch_assoc_prep(const RunView& v, cudaStream_t s);
 // scan + FP64 recheck + per-point argmin + FP64 slow path (4 launches)
 cudaError_t launch_assoc_scan(const RunView& v, int num_sms, cudaStream_t s);
 cudaError_t assoc_prepare(const RunView& v);
+cudaError_t assoc_init_attributes();
 cudaError_t launch_level(const RunView& v, cudaStream_t s);
 cudaError_t launch_bucket(const RunView& v, cudaStream_t s);
 cudaError_t launch_pick(const RunView& v, cudaStream_t s);
