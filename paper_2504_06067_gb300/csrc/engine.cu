@@ -179,9 +179,9 @@ nsga3_status record_generation(nsga3_ctx* ctx, cudaStream_t s, bool events)
     return record_event(ctx, s, EV_END, events);
 }
 
-// Eager execution of the same kernels without graphs: the peel loop and
-// the niching branch are decided on the host from the control block.  Used
-// for profiling tools that do not profile graph kernel nodes.
+// Eager execution of the same kernels without graphs (NSGA3_EAGER=1): the
+// niching kernels are launched only when the host reads that niching is
+// needed.  For tools and debugging that want direct launches.
 nsga3_status eager_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, bool check_finite)
 {
     CK(launch_sel_reset(v, s));
