@@ -36,7 +36,7 @@ if ROOT not in sys.path:
 from paper_2504_06067_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "selected sols/s & gens/s (% HBM roofline); batched/served runs/s, p50/p99 vs plain"
-WORKLOADS = {"small": wl.SMALL, "scale": wl.SCALE, "large": wl.LARGE}
+WORKLOADS = {"small": wl.SMALL, "scale": wl.SCALE, "large": wl.LARGE, "huge": wl.HUGE}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
 NUM_SMS = 152
 LANES_PER_SM = 128
@@ -56,6 +56,8 @@ def parse_args(argv=None):
                    help="seconds of oracle work for the cpu_baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--streaming", action="store_true",
+                   help="no dominance matrix: the peel recomputes dominance (required for huge)")
     return p.parse_args(argv)
 
 
@@ -195,7 +197,8 @@ def run_ours(args, world, rank, local):
     cfg = WORKLOADS[args.workload]
     seed = cfg.seed + rank
     W = wl.objective_weights(cfg.m, cfg.seed)
-    opts = n.default_opts(seed=seed, p2=cfg.p2, tau=cfg.tau, W=W.ctypes.data)
+    streaming = 1 if (args.streaming or args.workload == "huge") else 0
+    opts = n.default_opts(seed=seed, p2=cfg.p2, tau=cfg.tau, W=W.ctypes.data, streaming=streaming)
     ctx = n.create(cfg.m, cfg.d, cfg.N, cfg.p1, opts)
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
@@ -332,7 +335,8 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded softmax-simplex objective, W ~ N(0,1); stands in for DTLZ)",
-        "config": {"workload": cfg.name, "m": cfg.m, "N": cfg.N, "d": cfg.d, "refs": cfg.w,
+        "config": {"workload": cfg.name + ("_streaming" if streaming else ""), "m": cfg.m, "N": cfg.N,
+                   "d": cfg.d, "refs": cfg.w,
                    "generations": "timed %d from generation 0" % K,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},

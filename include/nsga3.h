@@ -60,6 +60,9 @@ typedef struct {
     const float* W;         /* host, m x (m-1) row-major weights of the softmax-simplex
                                objective f = (1+g) softmax(W x[:m-1]); NULL: the context
                                only serves nsga3_select / nsga3_set_population */
+    int streaming;          /* 1: no dominance matrix; the peel recomputes the dominance
+                               of each front's members on the fly (device memory O(N)
+                               instead of (2N)^2 / 8 bytes; same results) */
 } nsga3_opts;
 
 /* Fills *o with the defaults above (seed 0, single layer, tau 0.5). */

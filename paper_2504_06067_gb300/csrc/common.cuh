@@ -79,6 +79,7 @@ struct RunView {
     int m, d, N, n2, ld, NW, w, M4;   // M4 = m rounded up to a multiple of 4
     int full_sort;
     int debug_recheck_all;
+    int streaming;         // no Dom matrix: the peel recomputes dominance from Fp
     uint64_t seed;
     float eta_c, eta_m, p_c, p_m;
     Ctrl* ctrl;

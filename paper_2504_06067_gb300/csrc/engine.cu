@@ -364,6 +364,7 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     v.M4 = M4;
     v.full_sort = ctx->opts.full_sort ? 1 : 0;
     v.debug_recheck_all = ctx->opts.debug_recheck_all ? 1 : 0;
+    v.streaming = ctx->opts.streaming ? 1 : 0;
     v.seed = ctx->opts.seed;
     v.eta_c = ctx->opts.eta_c;
     v.eta_m = ctx->opts.eta_m;
@@ -382,7 +383,7 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     AL(v.Xtmp, (size_t)N * d);
     AL(v.Ftmp, (size_t)N * m);
     AL(v.ranktmp, N);
-    AL(v.Dom, (size_t)NW * ld);
+    AL(v.Dom, v.streaming ? (size_t)1 : (size_t)NW * ld);
     AL(v.cnt, ld);
     AL(v.rank2, ld);
     AL(v.srank, ld);
@@ -466,7 +467,7 @@ nsga3_status setup(nsga3_ctx* ctx)
     for (int e = 0; e < EV_COUNT; ++e) CK(cudaEventCreate(&ctx->ev[e]));
     cudaStream_t s = ctx->cap;
     CK(cudaMemsetAsync(v.ctrl, 0, sizeof(Ctrl), s));
-    CK(cudaMemsetAsync(v.Dom, 0, (size_t)NW * ld * sizeof(uint32_t), s));
+    if (!v.streaming) CK(cudaMemsetAsync(v.Dom, 0, (size_t)NW * ld * sizeof(uint32_t), s));
     CK(cudaMemsetAsync(v.rank, 0, (size_t)N * sizeof(int32_t), s));
     CK(cudaMemsetAsync(v.X, 0, (size_t)n2 * d * sizeof(float), s));
     CK(cudaMemsetAsync(v.F, 0, (size_t)ld * m * sizeof(float), s));
@@ -678,6 +679,7 @@ void nsga3_default_opts(nsga3_opts* o)
     o->p_m = -1.0f;
     o->full_sort = 0;
     o->debug_recheck_all = 0;
+    o->streaming = 0;
     o->W = nullptr;
 }
 

@@ -25,6 +25,8 @@
 //
 // Every CTA also popcounts the words it writes and adds each point's
 // dominator count to cnt[] (the peel's first pass then reads no words).
+// In streaming mode (no matrix) only the counts are produced; the peel
+// recomputes the dominance of each front's members (k_peel.cu).
 //
 // Bound: the ALU pipe (sign-bit logic) and instruction issue -- not HBM.
 #include "kernels.cuh"
@@ -176,10 +178,12 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
                 acc1 = __funnelshift_l(oa1, acc1, 1);
             }
             const uint32_t t0 = warp_transpose32(~acc0), t1 = warp_transpose32(~acc1);
-            D[(size_t)jb * v.ld + ib0 * 32 + lane] = 0u;
-            D[(size_t)jb * v.ld + ib1 * 32 + lane] = 0u;
-            D[(size_t)ib0 * v.ld + jb * 32 + lane] = t0;
-            D[(size_t)ib1 * v.ld + jb * 32 + lane] = t1;
+            if (!v.streaming) {
+                D[(size_t)jb * v.ld + ib0 * 32 + lane] = 0u;
+                D[(size_t)jb * v.ld + ib1 * 32 + lane] = 0u;
+                D[(size_t)ib0 * v.ld + jb * 32 + lane] = t0;
+                D[(size_t)ib1 * v.ld + jb * 32 + lane] = t1;
+            }
             const int cc = __popc(t0) + __popc(t1);
             if (cc) atomicAdd(&colcnt[cb * 32 + lane], cc);
             continue;
@@ -207,14 +211,14 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
                 block_full<M, M4>(fi, colp, dij, dji);
             }
             // column i = ib*32 + lane, dominators j in block jb
-            D[(size_t)jb * v.ld + ib * 32 + lane] = dji;
+            if (!v.streaming) D[(size_t)jb * v.ld + ib * 32 + lane] = dji;
             if (r)
                 rc1 += __popc(dji);
             else
                 rc0 += __popc(dji);
             if (jb != ib) {
                 const uint32_t t = warp_transpose32(dij);
-                D[(size_t)ib * v.ld + jb * 32 + lane] = t;
+                if (!v.streaming) D[(size_t)ib * v.ld + jb * 32 + lane] = t;
                 if (t) atomicAdd(&colcnt[cb * 32 + lane], __popc(t));
             }
         }

@@ -15,17 +15,29 @@
 // columns' counts, ranks them and writes their front-mask words.  The last
 // CTA of a pass (ticket) closes the front.  Bound: HBM / L2 bandwidth of the
 // Dom reads.
+#include <math_constants.h>
+
 #include "kernels.cuh"
 
 namespace {
 
-constexpr int PTMAX = 1024;       // threads per CTA (runtime: 256, 512 or 1024)
-constexpr int PWMAX = PTMAX / 32;
+constexpr int PEEL_THREADS = 512;  // threads per CTA
+constexpr int PWMAX = PEEL_THREADS / 32;
 constexpr int LISTCAP = 2048;
 
 // Grid barrier of the cooperative peel, with a bounded wait.  Returns false
-// (and records NSGA3_ETIMEOUT) when the other CTAs did not arrive in time.
-constexpr unsigned SPIN_LIMIT = 1u << 24;
+// (and records NSGA3_ETIMEOUT) when the other CTAs did not arrive within
+// WAIT_NS of device time (the longest legitimate wait is one pass of the
+// slowest CTA: milliseconds with the matrix, up to seconds when streaming
+// the largest populations).
+constexpr unsigned long long WAIT_NS = 20ull * 1000 * 1000 * 1000;
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
 {
@@ -46,14 +58,17 @@ __device__ bool grid_sync(Ctrl* c, int* s_ok)
             __threadfence();
             atomicAdd(&c->bar_gen, 1u);
         } else {
+            const unsigned long long t0 = global_ns();
             unsigned it = 0;
             while (ld_acquire(&c->bar_gen) == g) {
-                if (++it > SPIN_LIMIT) {
+                // the clock is read every 256 polls; the poll count caps the
+                // wait too, should the timer not advance
+                if ((++it & 255u) == 0u && (global_ns() - t0 > WAIT_NS || it > (1u << 30))) {
                     set_status(c, DEV_ETIMEOUT);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(100);
             }
         }
         __threadfence();
@@ -63,13 +78,15 @@ __device__ bool grid_sync(Ctrl* c, int* s_ok)
     return *s_ok != 0;
 }
 
-__global__ void __launch_bounds__(PTMAX) k_peel(RunView v)
+template <bool STREAM>
+__global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v)
 {
     __shared__ int red[PWMAX][NSGA3_PEEL_COLS];
     const int PT = blockDim.x, PW = PT >> 5;
     __shared__ uint2 list[LISTCAP];
     __shared__ int nlist;
     __shared__ int s_ok;
+    __shared__ float rowbuf[STREAM ? PWMAX : 1][32][NSGA3_MAX_M];  // streaming: members of a front word
     Ctrl* c = v.ctrl;
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     if (read_status(c)) return;  // uniform: set only by earlier kernels
@@ -103,7 +120,90 @@ __global__ void __launch_bounds__(PTMAX) k_peel(RunView v)
             uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
             // pass 0 needs no words: the dominance build already counted every
             // column's dominators into cnt[]
-            if (any_rem && k > 0) {
+            if (STREAM && any_rem && k > 0) {
+                // no matrix: every member of front k-1 (up to the row limit)
+                // is tested against this lane's four columns lane*4 .. +3,
+                // with the sign-bit test of the dominance build; a member
+                // whose f_0 is below every f_0 of the chunk needs objectives
+                // 1..m-1 only (f_0 makes the dominance strict)
+                const int m = v.m;
+                float fc[4][NSGA3_MAX_M];
+                float cmin = CUDART_INF_F;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+#pragma unroll
+                    for (int q = 0; q < NSGA3_MAX_M; ++q)
+                        fc[t][q] = q < m ? v.Fp[(size_t)(j0 + lane * 4 + t) * m + q] : 0.0f;
+                    cmin = fminf(cmin, fc[t][0]);  // NaN padding columns are ignored by fminf
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+                float* rb = rowbuf[warp][0];
+                const uint32_t* prev = v.front + ((k - 1) & 1) * v.NW;
+                for (int wb = 0; wb < lim; wb += LISTCAP) {
+                    const int whe = min(wb + LISTCAP, lim);
+                    if (tid == 0) nlist = 0;
+                    __syncthreads();
+                    for (int w0 = wb + warp * 32; w0 < whe; w0 += PT) {
+                        const int w = w0 + lane;
+                        const uint32_t msk = w < whe ? __ldcg(&prev[w]) : 0u;
+                        const unsigned bal = __ballot_sync(0xffffffffu, msk != 0u);
+                        int at = 0;
+                        if (lane == 0 && bal) at = atomicAdd(&nlist, __popc(bal));
+                        at = __shfl_sync(0xffffffffu, at, 0);
+                        if (msk) list[at + __popc(bal & ((1u << lane) - 1u))] = make_uint2((unsigned)w, msk);
+                    }
+                    __syncthreads();
+                    const int n = nlist;
+                    if (tid == 0) atomicAdd(&c->peel_rows, (unsigned)n);
+                    for (int e = warp; e < n; e += PW) {
+                        const uint2 L = list[e];
+                        // the word's members, one per lane, into this warp's row buffer
+                        if ((L.y >> lane) & 1u) {
+                            const size_t p = (size_t)L.x * 32 + lane;
+#pragma unroll
+                            for (int q = 0; q < NSGA3_MAX_M; ++q)
+                                if (q < m) rb[lane * NSGA3_MAX_M + q] = __ldg(&v.Fp[p * m + q]);
+                        }
+                        __syncwarp();
+                        uint32_t mk = L.y;
+                        while (mk) {  // warp-uniform: every lane walks the same rows
+                            const int b = __ffs(mk) - 1;
+                            mk &= mk - 1u;
+                            const float* fi = rb + b * NSGA3_MAX_M;
+                            uint32_t d4[4];
+                            if (fi[0] < cmin) {
+#pragma unroll
+                                for (int t = 0; t < 4; ++t) {
+                                    uint32_t oa = 0u;
+#pragma unroll
+                                    for (int q = 1; q < NSGA3_MAX_M; ++q)
+                                        if (q < m) oa |= __float_as_uint(fc[t][q] - fi[q]);
+                                    d4[t] = (~oa) >> 31;  // no f_iq > f_jq
+                                }
+                            } else {
+#pragma unroll
+                                for (int t = 0; t < 4; ++t) {
+                                    uint32_t oa = 0u, ob = 0u;
+#pragma unroll
+                                    for (int q = 0; q < NSGA3_MAX_M; ++q)
+                                        if (q < m) {
+                                            oa |= __float_as_uint(fc[t][q] - fi[q]);
+                                            ob |= __float_as_uint(fi[q] - fc[t][q]);
+                                        }
+                                    d4[t] = (ob & ~oa) >> 31;  // none greater, some smaller
+                                }
+                            }
+                            a0 += d4[0];
+                            a1 += d4[1];
+                            a2 += d4[2];
+                            a3 += d4[3];
+                        }
+                        __syncwarp();
+                    }
+                    __syncthreads();
+                }
+            } else if (!STREAM && any_rem && k > 0) {
                 const uint4* base = reinterpret_cast<const uint4*>(v.Dom + j0) + lane;
                 const size_t ld4 = (size_t)v.ld / 4;
                 {
@@ -219,8 +319,7 @@ __global__ void k_post_peel(RunView v)
     if (p < v.n2) v.rank2[v.perm[p]] = v.srank[p];
 }
 
-int g_peel_occ = 0;  // resident 512-thread peel CTAs per SM, set at initialisation
-constexpr int PEEL_THREADS = 512;
+int g_peel_occ[2] = {0, 0};  // resident peel CTAs per SM (matrix, streaming), set at start-up
 
 }  // namespace
 
@@ -229,7 +328,8 @@ constexpr int PEEL_THREADS = 512;
 cudaError_t launch_peel(const RunView& v, int num_sms, cudaStream_t s)
 {
     const int nchunks = v.ld / NSGA3_PEEL_COLS;
-    int grid = num_sms * (g_peel_occ > 0 ? g_peel_occ : 1);
+    const int occ = g_peel_occ[v.streaming ? 1 : 0];
+    int grid = num_sms * (occ > 0 ? occ : 1);
     if (grid > nchunks) grid = nchunks;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -241,12 +341,15 @@ cudaError_t launch_peel(const RunView& v, int num_sms, cudaStream_t s)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_peel, v);
+    if (v.streaming) return cudaLaunchKernelEx(&cfg, k_peel<true>, v);
+    return cudaLaunchKernelEx(&cfg, k_peel<false>, v);
 }
 
 cudaError_t peel_init_attributes()
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_peel_occ, k_peel, PEEL_THREADS, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_peel_occ[0], k_peel<false>, PEEL_THREADS, 0);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_peel_occ[1], k_peel<true>, PEEL_THREADS, 0);
 }
 
 cudaError_t launch_post_peel(const RunView& v, cudaStream_t s)

@@ -39,6 +39,7 @@ class nsga3_opts(C.Structure):
         ("full_sort", C.c_int),
         ("debug_recheck_all", C.c_int),
         ("W", C.c_void_p),
+        ("streaming", C.c_int),
     ]
 
 

@@ -43,6 +43,10 @@ SCALE = RunConfig("m5_N10628_d100_p20", m=5, d=100, N=10628, p1=20, generations=
 # Large population: m=10, two layers p1=3 + p2=2 (tau 0.5; 275 directions), N=100,000, d=200.
 LARGE = RunConfig("m10_N100000_d200_p3+2", m=10, d=200, N=100000, p1=3, p2=2, tau=0.5,
                   generations=200)
+# Beyond the dominance matrix (streaming only): m=10, N = 1,000,000 (merged
+# 2N = 2,000,000 would need a 500 GB matrix), same directions as LARGE.
+HUGE = RunConfig("m10_N1000000_d200_p3+2", m=10, d=200, N=1000000, p1=3, p2=2, tau=0.5,
+                 generations=20)
 PLAIN_CONFIGS = (SMALL, SCALE, LARGE)
 
 

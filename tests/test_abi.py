@@ -85,3 +85,12 @@ def test_server_create_without_gpu_fails_cleanly(lib):
     h = C.c_void_p()
     assert n.nsga3_server_create(1 << 20, 4, 8, C.byref(h)) == n.ECUDA and h.value is None
     assert n.nsga3_server_create(1 << 20, 0, 8, C.byref(h)) == n.EINVAL
+
+
+def test_streaming_workspace_has_no_matrix(lib):
+    from paper_2504_06067_gb300 import native as n
+    N = 100000
+    full = n.workspace_bytes(10, 200, N, 3, n.default_opts(p2=2))
+    stream = n.workspace_bytes(10, 200, N, 3, n.default_opts(p2=2, streaming=1))
+    ld = -(-2 * N // 256) * 256
+    assert full - stream == ld * ld // 8 - 256
