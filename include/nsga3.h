@@ -134,11 +134,14 @@ nsga3_status nsga3_step(nsga3_ctx* ctx, void* stream);
 /* `generations` calls of nsga3_step. */
 nsga3_status nsga3_run(nsga3_ctx* ctx, int generations, void* stream);
 
-/* Runs one generation of every context in ctxs[0..n) as one CUDA-graph
- * launch per generation (the runs' kernels overlap on the device), for
- * `generations` generations.  Every context needs opts.W and must live on
- * the current device.  The graph is built on the first call for a given
- * list and reused while the list is unchanged. */
+/* Advances every context in ctxs[0..n) by `generations` generations with
+ * batched CUDA graphs: one graph holds 4 consecutive generations of every
+ * run as parallel branches (a second graph one generation, for the
+ * remainder), so the runs' kernels overlap on the device and small runs run
+ * ahead of large ones between launches.  Results equal each run stepped
+ * alone.  Every context needs opts.W and must live on the current device.
+ * The graphs are built on the first call for a given list and reused while
+ * the list is unchanged. */
 nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* stream);
 
 /* Copies the N parents out: X (any, N x d), F (any, N x m), rank (any, N).

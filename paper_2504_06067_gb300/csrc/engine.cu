@@ -31,6 +31,7 @@ thread_local std::string g_create_error;
 std::mutex g_attr_mutex;
 
 enum { EV_START, EV_VARY, EV_RESET, EV_DOM, EV_PEEL, EV_NICHE, EV_END, EV_COUNT };
+constexpr int BATCH_GENS = 4;  // generations per batched graph launch
 
 __global__ void k_set_gen(Ctrl* c, uint32_t gen) { c->gen = gen; }
 
@@ -57,7 +58,8 @@ struct nsga3_ctx {
     std::string err;
     // batched graph cache
     std::vector<nsga3_ctx*> batch_key;
-    cudaGraphExec_t gx_batch = nullptr;
+    cudaGraphExec_t gx_batch = nullptr;   // BATCH_GENS generations of every run
+    cudaGraphExec_t gx_batch1 = nullptr;  // one generation of every run
 };
 
 namespace {
@@ -641,6 +643,7 @@ void ctx_destroy(nsga3_ctx* ctx, bool sync_device)
     if (!ctx) return;
     if (sync_device) cudaDeviceSynchronize();
     if (ctx->gx_batch) cudaGraphExecDestroy(ctx->gx_batch);
+    if (ctx->gx_batch1) cudaGraphExecDestroy(ctx->gx_batch1);
     if (ctx->gx_select) cudaGraphExecDestroy(ctx->gx_select);
     if (ctx->gx_step) cudaGraphExecDestroy(ctx->gx_step);
     for (int e = 0; e < EV_COUNT; ++e)
@@ -661,6 +664,66 @@ nsga3_status ctx_launches(nsga3_ctx* ctx, void* stream, long long* launches)
     CK(cudaStreamSynchronize((cudaStream_t)stream));
     *launches = ctx->host_launches;
     return NSGA3_OK;
+}
+
+// One graph holding `gens` consecutive generations of every run as parallel
+// branches (fork/join events), the runs with the most dominance work first
+// so that their longer chains start first; a run's next generation depends
+// only on its own previous one, so small runs run ahead within the graph.
+nsga3_status build_batch_graph(nsga3_ctx* ctx, nsga3_ctx** ctxs, int n, int gens, cudaGraphExec_t* out)
+{
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const double wa = (double)ctxs[a]->n2 * ctxs[a]->n2 * ctxs[a]->m;
+        const double wb = (double)ctxs[b]->n2 * ctxs[b]->n2 * ctxs[b]->m;
+        return wa > wb;
+    });
+    std::vector<cudaStream_t> br(n);
+    std::vector<cudaEvent_t> evs(n + 1);
+    nsga3_status st = NSGA3_OK;
+    for (int r = 0; r < n && !st; ++r)
+        if (cudaStreamCreateWithFlags(&br[r], cudaStreamNonBlocking) != cudaSuccess)
+            st = fail(ctx, NSGA3_ECUDA, "stream creation failed");
+    for (int r = 0; r <= n && !st; ++r)
+        if (cudaEventCreateWithFlags(&evs[r], cudaEventDisableTiming) != cudaSuccess)
+            st = fail(ctx, NSGA3_ECUDA, "event creation failed");
+    cudaGraph_t g = nullptr;
+    if (!st) {
+        cudaStream_t s0 = ctx->cap;
+        if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+            st = fail(ctx, NSGA3_ECUDA, "capture begin failed");
+        if (!st && cudaEventRecord(evs[n], s0) != cudaSuccess) st = fail(ctx, NSGA3_ECUDA, "fork failed");
+        for (int t = 0; t < n && !st; ++t) {
+            const int r = order[t];
+            if (cudaStreamWaitEvent(br[r], evs[n], 0) != cudaSuccess) {
+                st = fail(ctx, NSGA3_ECUDA, "fork wait failed");
+                break;
+            }
+            for (int k = 0; k < gens && !st; ++k) {
+                nsga3_status rs = record_generation(ctxs[r], br[r], false);
+                if (rs) {
+                    st = rs;
+                    ctx->err = ctxs[r]->err;
+                }
+            }
+            // join the branch even after a failure so the capture ends cleanly
+            if (cudaEventRecord(evs[r], br[r]) != cudaSuccess || cudaStreamWaitEvent(s0, evs[r], 0) != cudaSuccess) {
+                if (!st) st = fail(ctx, NSGA3_ECUDA, "join failed");
+            }
+        }
+        cudaError_t e = cudaStreamEndCapture(s0, &g);
+        if (!st && e != cudaSuccess) st = fail(ctx, NSGA3_ECUDA, "capture failed: %s", cudaGetErrorString(e));
+        if (!st && cudaGraphInstantiate(out, g, 0) != cudaSuccess)
+            st = fail(ctx, NSGA3_ECUDA, "batched graph instantiation failed");
+        if (g) cudaGraphDestroy(g);
+    }
+    for (int r = 0; r < n; ++r)
+        if (br[r]) cudaStreamDestroy(br[r]);
+    for (int r = 0; r <= n; ++r)
+        if (evs[r]) cudaEventDestroy(evs[r]);
+    cudaGetLastError();
+    return st;
 }
 
 // =============================================================== C ABI ====
@@ -804,60 +867,20 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
         return NSGA3_OK;
     }
     std::vector<nsga3_ctx*> key(ctxs, ctxs + n);
-    if (!ctx->gx_batch || ctx->batch_key != key) {
-        if (ctx->gx_batch) {
-            cudaGraphExecDestroy(ctx->gx_batch);
-            ctx->gx_batch = nullptr;
-        }
-        // one branch per run: fork from the capture stream with events
-        std::vector<cudaStream_t> br(n);
-        std::vector<cudaEvent_t> evs(n + 1);
-        nsga3_status st = NSGA3_OK;
-        for (int r = 0; r < n && !st; ++r) {
-            if (cudaStreamCreateWithFlags(&br[r], cudaStreamNonBlocking) != cudaSuccess)
-                st = fail(ctx, NSGA3_ECUDA, "stream creation failed");
-        }
-        for (int r = 0; r <= n && !st; ++r)
-            if (cudaEventCreateWithFlags(&evs[r], cudaEventDisableTiming) != cudaSuccess)
-                st = fail(ctx, NSGA3_ECUDA, "event creation failed");
-        cudaGraph_t g = nullptr;
-        if (!st) {
-            cudaStream_t s0 = ctx->cap;
-            if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
-                st = fail(ctx, NSGA3_ECUDA, "capture begin failed");
-            if (!st && cudaEventRecord(evs[n], s0) != cudaSuccess) st = fail(ctx, NSGA3_ECUDA, "fork failed");
-            for (int r = 0; r < n && !st; ++r) {
-                if (cudaStreamWaitEvent(br[r], evs[n], 0) != cudaSuccess) {
-                    st = fail(ctx, NSGA3_ECUDA, "fork wait failed");
-                    break;
-                }
-                nsga3_status rs = record_generation(ctxs[r], br[r], false);
-                if (rs) {
-                    st = rs;
-                    ctx->err = ctxs[r]->err;
-                }
-                // join the branch even after a failure so the capture ends cleanly
-                if (cudaEventRecord(evs[r], br[r]) != cudaSuccess ||
-                    cudaStreamWaitEvent(s0, evs[r], 0) != cudaSuccess) {
-                    if (!st) st = fail(ctx, NSGA3_ECUDA, "join failed");
-                }
+    if (!ctx->gx_batch || !ctx->gx_batch1 || ctx->batch_key != key) {
+        for (cudaGraphExec_t* gx : {&ctx->gx_batch, &ctx->gx_batch1})
+            if (*gx) {
+                cudaGraphExecDestroy(*gx);
+                *gx = nullptr;
             }
-            cudaError_t e = cudaStreamEndCapture(s0, &g);
-            if (!st && e != cudaSuccess) st = fail(ctx, NSGA3_ECUDA, "capture failed: %s", cudaGetErrorString(e));
-            if (!st && cudaGraphInstantiate(&ctx->gx_batch, g, 0) != cudaSuccess)
-                st = fail(ctx, NSGA3_ECUDA, "batched graph instantiation failed");
-            if (g) cudaGraphDestroy(g);
-        }
-        for (int r = 0; r < n; ++r) {
-            if (br[r]) cudaStreamDestroy(br[r]);
-        }
-        for (int r = 0; r <= n; ++r)
-            if (evs[r]) cudaEventDestroy(evs[r]);
-        cudaGetLastError();
+        nsga3_status st = build_batch_graph(ctx, ctxs, n, BATCH_GENS, &ctx->gx_batch);
+        if (!st) st = build_batch_graph(ctx, ctxs, n, 1, &ctx->gx_batch1);
         if (st) return st;
         ctx->batch_key = key;
     }
-    for (int g = 0; g < generations; ++g) CK(cudaGraphLaunch(ctx->gx_batch, (cudaStream_t)stream));
+    for (int g = 0; g + BATCH_GENS <= generations; g += BATCH_GENS)
+        CK(cudaGraphLaunch(ctx->gx_batch, (cudaStream_t)stream));
+    for (int g = 0; g < generations % BATCH_GENS; ++g) CK(cudaGraphLaunch(ctx->gx_batch1, (cudaStream_t)stream));
     for (int r = 0; r < n; ++r) {
         ctxs[r]->last_kind = 3;
         ctxs[r]->host_launches += 23LL * generations;
