@@ -63,6 +63,12 @@ typedef struct {
     int streaming;          /* 1: no dominance matrix; the peel recomputes the dominance
                                of each front's members on the fly (device memory O(N)
                                instead of (2N)^2 / 8 bytes; same results) */
+    int norm_history;       /* 1: normalization keeps a running ideal point (minimum over
+                               every merged population so far) and remembers the extreme
+                               points, which stay candidates in later generations; the
+                               history starts empty at nsga3_create and nsga3_init and is
+                               updated by every selection that normalizes.  0: stateless
+                               (ideal and extremes of the current S u F_l only) */
 } nsga3_opts;
 
 /* Fills *o with the defaults above (seed 0, single layer, tau 0.5). */
@@ -175,8 +181,9 @@ nsga3_status nsga3_sync(nsga3_ctx* ctx, void* stream);
 nsga3_status nsga3_get_selection_info(nsga3_ctx* ctx, int32_t* info);
 
 /* Normalization of the last niching selection (synchronous): ideal point
- * zstar[m], intercepts a[m] (FP64), extreme-point indices ext[m]; any may be
- * NULL. */
+ * zstar[m], intercepts a[m] (FP64), extreme-point indices ext[m] (with
+ * opts.norm_history an index 2N + r names the r-th remembered extreme
+ * vector); any may be NULL. */
 nsga3_status nsga3_get_normalization(nsga3_ctx* ctx, double* zstar, double* a, int32_t* ext);
 
 /* Association of the last niching selection (synchronous): pi (any, 2N

@@ -61,6 +61,8 @@ def _load():
         "orc_niche_sequential": (i32, [P, i32, i32, i32, P, P, i32, u64, u32, P]),
         "orc_niche_batched": (i32, [P, i32, i32, i32, P, P, i32, u64, u32, P]),
         "orc_select": (i32, [P, i32, i32, P, i32, u64, u32, i32, i32, P, P, P, P, P]),
+        "orc_select_hist": (i32, [P, i32, i32, P, i32, u64, u32, i32, i32, P, P, P, P, P, P, P, P]),
+        "orc_normalize_hist": (i32, [P, P, i32, i32, i32, P, P, P, P, P, P, P]),
         "orc_vary": (None, [P, P, i32, i32, u64, u32, f64, f64, f32, f32, P]),
         "orc_eval": (None, [P, i32, i32, i32, P, P]),
         "orc_init": (None, [i32, i32, u64, P]),
@@ -161,6 +163,30 @@ def normalize(F, rank, l: int):
     return zstar, a, ext, bool(fb[0])
 
 
+def new_history(m: int) -> dict:
+    """Empty normalization history: running ideal z[m], remembered extreme
+    vectors e[m][m] (FP32), valid flag.  Updated in place by the *_hist calls."""
+    return {"valid": np.zeros(1, dtype=np.int32), "z": np.zeros(m), "e": np.zeros((m, m), dtype=np.float32)}
+
+
+def normalize_hist(F, rank, l: int, history: dict):
+    """Normalization with a running ideal point and remembered extreme points
+    (an option; the paper defines no history).  Extreme indices >= 2N name the
+    remembered vectors.  Updates `history`."""
+    F = _f32(F)
+    rank = _i32(rank)
+    n2, m = F.shape
+    zstar = np.zeros(m)
+    a = np.zeros(m)
+    ext = np.zeros(m, dtype=np.int32)
+    fb = np.zeros(1, dtype=np.int32)
+    rc = _load().orc_normalize_hist(_p(F), _p(rank), n2, m, l, _p(history["valid"]), _p(history["z"]),
+                                    _p(history["e"]), _p(zstar), _p(a), _p(ext), _p(fb))
+    if rc != OK:
+        raise ValueError("normalize_hist: empty normalization set")
+    return zstar, a, ext, bool(fb[0])
+
+
 def associate(F, rank, l: int, zstar, a, Z):
     """pi = argmin_j D_ij and d = min_j D_ij with D from Eq. (2) (Alg. 2)."""
     F = _f32(F)
@@ -187,9 +213,12 @@ def niche(rank, l: int, K: int, pi, dist, w: int, seed: int, gen: int, variant: 
     return picked.astype(bool)
 
 
-def select(F, N: int, Z, seed: int, gen: int, variant: int = 0, full_sort: bool = False):
+def select(F, N: int, Z, seed: int, gen: int, variant: int = 0, full_sort: bool = False,
+           history: dict | None = None):
     """Full environmental selection of N out of the 2N x m objectives.
 
+    With `history` (see new_history) the normalization keeps a running ideal
+    point and remembered extreme points, and `history` is updated in place.
     Returns dict(rank, selected, pi, dist, l, nS, K, nFl, niche, fallback).
     """
     F = _f32(F)
@@ -201,8 +230,13 @@ def select(F, N: int, Z, seed: int, gen: int, variant: int = 0, full_sort: bool 
     pi = np.zeros(n2, dtype=np.int32)
     dist = np.zeros(n2)
     info = np.zeros(6, dtype=np.int32)
-    rc = _load().orc_select(_p(F), N, m, _p(Z), Z.shape[0], seed, gen, variant, int(full_sort),
-                            _p(rank), _p(sel), _p(pi), _p(dist), _p(info))
+    if history is None:
+        rc = _load().orc_select(_p(F), N, m, _p(Z), Z.shape[0], seed, gen, variant, int(full_sort),
+                                _p(rank), _p(sel), _p(pi), _p(dist), _p(info))
+    else:
+        rc = _load().orc_select_hist(_p(F), N, m, _p(Z), Z.shape[0], seed, gen, variant,
+                                     int(full_sort), _p(rank), _p(sel), _p(pi), _p(dist), _p(info),
+                                     _p(history["valid"]), _p(history["z"]), _p(history["e"]))
     if rc != OK:
         raise ValueError("orc_select failed (rc=%d)" % rc)
     keys = ["l", "nS", "K", "nFl", "niche", "fallback"]

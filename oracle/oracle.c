@@ -348,6 +348,128 @@ int orc_normalize(const float *F, const int32_t *rank, int n2, int m, int l,
 }
 
 /* ---------------------------------------------------------------------- */
+/* Normalization with history (an option; the paper defines no history,   */
+/* so this is the reading of a running ideal point and remembered extreme */
+/* points, as several NSGA-III implementations keep them):                */
+/*   z*_q = min(previous z*_q, min over ALL 2N merged points of f_q);     */
+/*   extreme candidates: the members of T = S u F_l in index order, then  */
+/*   the m remembered extreme vectors (candidate index 2N + r), ASF       */
+/*   argmin per axis as in orc_normalize (ties -> lowest index);          */
+/*   E b = 1 with the candidates' vectors, same elimination and fallback  */
+/*   (the nadir fallback still maximises over T);                         */
+/*   afterwards z* and the chosen extreme vectors become the history.     */
+/* The history (hvalid, hz[m], he[m*m] FP32 vectors) is updated only when */
+/* a normalization is computed.                                           */
+/* ---------------------------------------------------------------------- */
+int orc_normalize_hist(const float *F, const int32_t *rank, int n2, int m, int l, int32_t *hvalid,
+                       double *hz, float *he, double *zstar, double *a, int32_t *extremes,
+                       int32_t *fallback)
+{
+    if (m > 64) return ORC_EINVAL;
+    for (int q = 0; q < m; ++q) zstar[q] = *hvalid ? hz[q] : INFINITY;
+    int any = 0;
+    for (int i = 0; i < n2; ++i) {
+        if (rank[i] >= 0 && rank[i] <= l) any = 1;
+        for (int q = 0; q < m; ++q) {
+            double v = (double)F[(size_t)i * m + q];
+            if (v < zstar[q]) zstar[q] = v;
+        }
+    }
+    if (!any) return ORC_EINVAL;
+    for (int q = 0; q < m; ++q) zstar[q] = zstar[q] + 0.0;
+
+    /* candidate c: c < n2 -> row c of F (members of T only), c >= n2 ->
+       remembered vector c - n2 */
+    const int ncand = n2 + (*hvalid ? m : 0);
+    for (int q = 0; q < m; ++q) {
+        double best = INFINITY;
+        int32_t arg = -1;
+        for (int c = 0; c < ncand; ++c) {
+            const float *f;
+            if (c < n2) {
+                if (rank[c] < 0 || rank[c] > l) continue;
+                f = F + (size_t)c * m;
+            } else {
+                f = he + (size_t)(c - n2) * m;
+            }
+            double asf = -INFINITY;
+            for (int r = 0; r < m; ++r) {
+                double ft = (double)f[r] - zstar[r];
+                double wq = (r == q) ? 1.0 : 1e-6;
+                double v = ft / wq;
+                if (v > asf) asf = v;
+            }
+            if (asf < best) { best = asf; arg = c; }
+        }
+        extremes[q] = arg;
+    }
+    float evec[64][64];
+    for (int q = 0; q < m; ++q) {
+        const float *f = extremes[q] < n2 ? F + (size_t)extremes[q] * m : he + (size_t)(extremes[q] - n2) * m;
+        for (int r = 0; r < m; ++r) evec[q][r] = f[r];
+    }
+
+    double A[64][64], rhs[64], b[64];
+    for (int q = 0; q < m; ++q) {
+        for (int r = 0; r < m; ++r) A[q][r] = (double)evec[q][r] - zstar[r];
+        rhs[q] = 1.0;
+    }
+    int ok = 1;
+    for (int c = 0; c < m && ok; ++c) {
+        int p = c;
+        double best = fabs(A[c][c]);
+        for (int r = c + 1; r < m; ++r)
+            if (fabs(A[r][c]) > best) { best = fabs(A[r][c]); p = r; }
+        if (best == 0.0) { ok = 0; break; }
+        if (p != c) {
+            for (int cc = 0; cc < m; ++cc) { double t = A[c][cc]; A[c][cc] = A[p][cc]; A[p][cc] = t; }
+            double t = rhs[c]; rhs[c] = rhs[p]; rhs[p] = t;
+        }
+        for (int r = c + 1; r < m; ++r) {
+            double factor = A[r][c] / A[c][c];
+            for (int cc = c; cc < m; ++cc) {
+                double prod = factor * A[c][cc];
+                A[r][cc] = A[r][cc] - prod;
+            }
+            double prod = factor * rhs[c];
+            rhs[r] = rhs[r] - prod;
+        }
+    }
+    if (ok) {
+        for (int r = m - 1; r >= 0; --r) {
+            double sum = rhs[r];
+            for (int cc = r + 1; cc < m; ++cc) {
+                double prod = A[r][cc] * b[cc];
+                sum = sum - prod;
+            }
+            b[r] = sum / A[r][r];
+        }
+        for (int q = 0; q < m; ++q) {
+            a[q] = 1.0 / b[q];
+            if (!isfinite(a[q]) || a[q] <= 1e-6) ok = 0;
+        }
+    }
+    *fallback = ok ? 0 : 1;
+    if (!ok) {
+        for (int q = 0; q < m; ++q) {
+            double mx = 0.0;
+            for (int i = 0; i < n2; ++i) {
+                if (rank[i] < 0 || rank[i] > l) continue;
+                double ft = (double)F[(size_t)i * m + q] - zstar[q];
+                if (ft > mx) mx = ft;
+            }
+            a[q] = (mx == 0.0) ? 1.0 : mx;
+        }
+    }
+    for (int q = 0; q < m; ++q) {
+        hz[q] = zstar[q];
+        for (int r = 0; r < m; ++r) he[(size_t)q * m + r] = evec[q][r];
+    }
+    *hvalid = 1;
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Association (Alg. 2: perpendicular distances, pi = argmin, d = min;     */
 /* Eq. 2 read as D = |F| * sqrt(1 - cos^2), cos = F.Z / (|F||Z|)).         */
 /* For i in T: f'_q = (f_iq - z*_q) / a_q;  nf = sqrt(sum f'_q^2);          */
@@ -588,9 +710,25 @@ int orc_niche_batched(const int32_t *rank, int n2, int l, int K,
 /* Alg. 2's last line).  variant: 0 = Alg. 1 loop, 1 = Alg. 2 cached loop.  */
 /* info[0..5] = l, |S|, K, |F_l|, niching used, normalization fallback.     */
 /* ---------------------------------------------------------------------- */
+int orc_select_hist(const float *F, int N, int m, const double *Z, int w, uint64_t seed,
+                    uint32_t gen, int variant, int full_sort, int32_t *rank, int32_t *selected,
+                    int32_t *pi_out, double *dist_out, int32_t *info, int32_t *hvalid,
+                    double *hz, float *he);
+
 int orc_select(const float *F, int N, int m, const double *Z, int w, uint64_t seed,
                uint32_t gen, int variant, int full_sort, int32_t *rank, int32_t *selected,
                int32_t *pi_out, double *dist_out, int32_t *info)
+{
+    return orc_select_hist(F, N, m, Z, w, seed, gen, variant, full_sort, rank, selected, pi_out,
+                           dist_out, info, NULL, NULL, NULL);
+}
+
+/* As orc_select; with hvalid != NULL the normalization keeps a history   */
+/* (orc_normalize_hist), else it is the stateless orc_normalize.          */
+int orc_select_hist(const float *F, int N, int m, const double *Z, int w, uint64_t seed,
+                    uint32_t gen, int variant, int full_sort, int32_t *rank, int32_t *selected,
+                    int32_t *pi_out, double *dist_out, int32_t *info, int32_t *hvalid,
+                    double *hz, float *he)
 {
     int n2 = 2 * N;
     for (int i = 0; i < n2 * m; ++i)
@@ -615,7 +753,10 @@ int orc_select(const float *F, int N, int m, const double *Z, int w, uint64_t se
         niche = 1;
         double zstar[64], a[64];
         int32_t ext[64];
-        orc_normalize(F, rank, n2, m, l, zstar, a, ext, &fb);
+        if (hvalid)
+            orc_normalize_hist(F, rank, n2, m, l, hvalid, hz, he, zstar, a, ext, &fb);
+        else
+            orc_normalize(F, rank, n2, m, l, zstar, a, ext, &fb);
         orc_associate(F, rank, n2, m, l, zstar, a, Z, w, pi, dist);
         int rc = variant == 0
                      ? orc_niche_sequential(rank, n2, l, K, pi, dist, w, seed, gen, picked)

@@ -72,6 +72,10 @@ struct Ctrl {
     double a[NSGA3_MAX_M];       // intercepts
     int32_t ext[NSGA3_MAX_M];    // extreme-point indices
     unsigned long long passes_total;  // peel passes since the context was created
+    // normalization history (opts.norm_history), kept across selections
+    int32_t hvalid;                      // 1 once a normalization has been recorded
+    double hz[NSGA3_MAX_M];              // running ideal point
+    float he[NSGA3_MAX_M * NSGA3_MAX_M]; // remembered extreme vectors, row q for axis q
 };
 
 // Device pointers and sizes of one run, passed by value to every kernel.
@@ -80,6 +84,7 @@ struct RunView {
     int full_sort;
     int debug_recheck_all;
     int streaming;         // no Dom matrix: the peel recomputes dominance from Fp
+    int norm_history;      // normalization with a running ideal and remembered extremes
     uint64_t seed;
     float eta_c, eta_m, p_c, p_m;
     Ctrl* ctrl;

@@ -367,6 +367,7 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     v.full_sort = ctx->opts.full_sort ? 1 : 0;
     v.debug_recheck_all = ctx->opts.debug_recheck_all ? 1 : 0;
     v.streaming = ctx->opts.streaming ? 1 : 0;
+    v.norm_history = ctx->opts.norm_history ? 1 : 0;
     v.seed = ctx->opts.seed;
     v.eta_c = ctx->opts.eta_c;
     v.eta_m = ctx->opts.eta_m;
@@ -743,6 +744,7 @@ void nsga3_default_opts(nsga3_opts* o)
     o->full_sort = 0;
     o->debug_recheck_all = 0;
     o->streaming = 0;
+    o->norm_history = 0;
     o->W = nullptr;
 }
 
@@ -812,6 +814,7 @@ nsga3_status nsga3_init(nsga3_ctx* ctx, void* stream)
     if (!ctx->has_W) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W was NULL)");
     cudaStream_t s = (cudaStream_t)stream;
     CK(launch_init(ctx->v, s));
+    CK(cudaMemsetAsync(&ctx->v.ctrl->hvalid, 0, sizeof(int32_t), s));  // a new run starts without history
     k_set_gen<<<1, 1, 0, s>>>(ctx->v.ctrl, 0u);
     CK(cudaGetLastError());
     ctx->host_launches += 3;

@@ -36,8 +36,13 @@ __global__ void __launch_bounds__(NB) k_norm_ideal(RunView v)
     if (lane == 0 && bal) base = atomicAdd(&c->nT, __popc(bal));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (inT) v.Tlist[base + __popc(bal & ((1u << lane) - 1u))] = i;
+    // the running ideal (history option) takes every merged point and the
+    // previous ideal; a minimum over S u F_l otherwise
+    const bool inZ = v.norm_history ? (i < v.n2) : inT;
+    if (v.norm_history && blockIdx.x == 0 && threadIdx.x == 0 && c->hvalid)
+        for (int q = 0; q < v.m; ++q) atomicMin(&c->zmin[q], f2ord((float)c->hz[q]));
     for (int q = 0; q < v.m; ++q) {
-        uint32_t o = inT ? f2ord(v.F[(size_t)i * v.m + q]) : 0xffffffffu;
+        uint32_t o = inZ ? f2ord(v.F[(size_t)i * v.m + q]) : 0xffffffffu;
 #pragma unroll
         for (int s = 16; s > 0; s >>= 1) o = min(o, __shfl_xor_sync(0xffffffffu, o, s));
         if (lane == 0 && o != 0xffffffffu) atomicMin(&c->zmin[q], o);
@@ -84,14 +89,18 @@ __device__ void solve_intercepts(const RunView& v, Ctrl* c, const int* ext, cons
         }
     }
     bool ok = true;
+    const int ncand = v.n2 + ((v.norm_history && c->hvalid) ? M : 0);
 #pragma unroll
     for (int q = 0; q < M; ++q)
-        if (ext[q] < 0 || ext[q] >= v.n2) ok = false;
+        if (ext[q] < 0 || ext[q] >= ncand) ok = false;
     double A[M], rhs = 1.0;
+    float evec[M];  // this lane's extreme vector (a merged point or a remembered one)
     const int er = lane < M ? ext[lane] : 0;
 #pragma unroll
-    for (int q = 0; q < M; ++q)
-        A[q] = (ok && lane < M) ? __dsub_rn((double)v.F[(size_t)er * M + q], zs[q]) : 0.0;
+    for (int q = 0; q < M; ++q) {
+        evec[q] = (ok && lane < M) ? (er < v.n2 ? v.F[(size_t)er * M + q] : c->he[(er - v.n2) * M + q]) : 0.0f;
+        A[q] = (ok && lane < M) ? __dsub_rn((double)evec[q], zs[q]) : 0.0;
+    }
 #pragma unroll
     for (int col = 0; col < M; ++col) {
         if (!ok) break;
@@ -154,6 +163,17 @@ __device__ void solve_intercepts(const RunView& v, Ctrl* c, const int* ext, cons
         c->a[lane] = a;
     }
     if (lane == 0) c->fallback = ok ? 0 : 1;
+    if (v.norm_history) {
+        // the ideal and the extreme vectors become the history (every lane
+        // read its remembered row above, before these writes)
+        __syncwarp();
+        if (lane < M) {
+            c->hz[lane] = zs[lane];
+#pragma unroll
+            for (int q = 0; q < M; ++q) c->he[lane * M + q] = evec[q];
+        }
+        if (lane == 0) c->hvalid = 1;
+    }
 }
 
 // Per-block (min ASF, lowest index) per axis and max of f~; the last block
@@ -291,6 +311,26 @@ __global__ void __launch_bounds__(EB) k_norm_extreme(RunView v)
             n = max(n, on);
         }
         if (lane == 0) {
+            if (v.norm_history && c->hvalid) {
+                // the remembered extreme vectors are candidates 2N + r
+                for (int r = 0; r < m; ++r) {
+                    const float* f = c->he + r * m;
+                    double mx = 0.0, tq = 0.0;
+                    for (int t = 0; t < m; ++t) {
+                        const double ft = __dsub_rn((double)f[t], zs[t]);
+                        if (t == q)
+                            tq = ft;
+                        else if (ft > mx)
+                            mx = ft;
+                    }
+                    const unsigned long long kq = okey(tq), ko = okey(__ddiv_rn(mx, 1e-6));
+                    const unsigned long long asf = kq > ko ? kq : ko;
+                    if (key_less(asf, v.n2 + r, b, bi)) {
+                        b = asf;
+                        bi = v.n2 + r;
+                    }
+                }
+            }
             f_ext[q] = bi;
             f_nad[q] = __longlong_as_double((long long)n);
         }

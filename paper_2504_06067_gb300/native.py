@@ -40,6 +40,7 @@ class nsga3_opts(C.Structure):
         ("debug_recheck_all", C.c_int),
         ("W", C.c_void_p),
         ("streaming", C.c_int),
+        ("norm_history", C.c_int),
     ]
 
 

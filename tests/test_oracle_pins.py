@@ -225,6 +225,70 @@ def test_normalize_singular_fallback(orc):
     assert np.array_equal(a, np.array([7.0, 1.0, 7.0]))
 
 
+# ------------------------------------------- normalization with history --
+def test_normalize_hist_first_call_equals_stateless(orc):
+    """Without history the running ideal over all 2N points equals the ideal
+    over S u F_l (a minimum of every objective is attained by a non-dominated
+    point), so the first call reproduces the stateless normalization."""
+    for kind, seed in (("early", 1), ("late", 2), ("uniform", 3), ("grid", 4)):
+        F = wl.objectives(kind, 200, 4, seed=seed)
+        rank, l = orc.nds(F, 100)
+        h = orc.new_history(4)
+        z1, a1, e1, fb1 = orc.normalize_hist(F, rank, l, h)
+        z0, a0, e0, fb0 = orc.normalize(F, rank, l)
+        assert np.array_equal(z1, z0) and np.array_equal(a1, a0) and np.array_equal(e1, e0)
+        assert fb1 == fb0 and h["valid"][0] == 1
+        assert np.array_equal(h["z"], z0)
+        assert np.array_equal(h["e"], F[e0])
+
+
+def test_normalize_hist_keeps_ideal_and_axis_extremes(orc):
+    """Generation 1 holds the three axis points (1 on one axis, 0 elsewhere):
+    z* = 0 and E = I, so a = (1, 1, 1).  Generation 2 holds interior points
+    only (every objective >= 0.1): the running ideal stays 0, the remembered
+    axis points (ASF 1) beat every interior point (ASF >= 0.1 / 1e-6), so the
+    extremes are the remembered vectors (indices 2N + q) and a = (1, 1, 1)
+    again, where the stateless normalization would move both."""
+    m = 3
+    rng = np.random.default_rng(0)
+    F1 = rng.dirichlet(np.ones(m), size=20).astype(np.float32)
+    F1[:3] = np.eye(m, dtype=np.float32)
+    rank1, l1 = orc.nds(F1, 10)
+    h = orc.new_history(m)
+    z, a, e, fb = orc.normalize_hist(F1, rank1, l1, h)
+    assert np.array_equal(z, np.zeros(m)) and np.array_equal(a, np.ones(m)) and not fb
+    F2 = (0.1 + 0.3 * rng.dirichlet(np.ones(m), size=20)).astype(np.float32)
+    rank2, l2 = orc.nds(F2, 10)
+    z2, a2, e2, fb2 = orc.normalize_hist(F2, rank2, l2, h)
+    assert np.array_equal(z2, np.zeros(m))
+    assert np.array_equal(e2, 20 + np.arange(m)) and np.array_equal(a2, np.ones(m)) and not fb2
+    zs, as_, es, _ = orc.normalize(F2, rank2, l2)
+    assert np.all(zs >= 0.1) and np.all(es < 20)
+
+
+def test_normalize_hist_ideal_is_a_running_minimum(orc):
+    m = 4
+    h = orc.new_history(m)
+    running = np.full(m, np.inf)
+    for g in range(4):
+        F = wl.objectives("early", 100, m, seed=10 + g) + np.float32(g * 0.05)
+        rank, l = orc.nds(F, 50)
+        z, a, e, fb = orc.normalize_hist(F, rank, l, h)
+        running = np.minimum(running, F.astype(np.float64).min(axis=0))
+        assert np.array_equal(z, running + 0.0)
+
+
+def test_select_hist_without_niching_leaves_history(orc):
+    """A selection whose fronts fill N exactly computes no normalization."""
+    m, N = 3, 4
+    F = np.array([[0, 3, 3], [3, 0, 3], [3, 3, 0], [1, 1, 1],
+                  [5, 5, 5], [6, 6, 6], [7, 7, 7], [8, 8, 8]], dtype=np.float32)
+    Z = orc.refdirs(m, 2)
+    h = orc.new_history(m)
+    r = orc.select(F, N, Z, seed=0, gen=0, history=h)
+    assert r["niche"] == 0 and h["valid"][0] == 0
+
+
 # ------------------------------------------------------------ association --
 def test_associate_point_on_direction(orc):
     """A point on direction j (after normalisation) has d = 0 and pi = j."""
