@@ -69,6 +69,12 @@ def _load():
         "orc_generation": (i32, [P, P, P, i32, i32, i32, P, P, i32, u64, u32, f64, f64,
                                  f32, f32, i32]),
         "orc_igd": (f64, [P, i32, i32, P, i32]),
+        "orc_kp_order": (None, [P, P, i32, i32, P]),
+        "orc_kp_eval": (None, [P, i32, i32, i32, P, P, P, P, P]),
+        "orc_kp_init": (None, [i32, i32, u64, P]),
+        "orc_kp_vary": (None, [P, P, i32, i32, u64, u32, f32, f32, P]),
+        "orc_kp_generation": (i32, [P, P, P, i32, i32, i32, P, P, P, P, P, i32, u64, u32, f32, f32]),
+        "orc_hv": (f64, [P, i32, i32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -310,6 +316,84 @@ def igd(P, R) -> float:
     P = _f32(P)
     R = _f64(R)
     return float(_load().orc_igd(_p(P), P.shape[0], P.shape[1], _p(R), R.shape[0]))
+
+
+# ---------------------------------------------- 0-1 knapsack workload -----
+def kp_order(profit, weight):
+    """Repair order: items by ascending best profit/weight ratio (exact), ties lower index."""
+    profit = _i32(profit)
+    weight = _i32(weight)
+    m, d = profit.shape
+    order = np.zeros(d, dtype=np.int32)
+    _load().orc_kp_order(_p(profit), _p(weight), m, d, _p(order))
+    return order
+
+
+def kp_eval(X, profit, weight, cap, order=None):
+    """Repair (in a copy) and evaluate: returns (X repaired, F) with
+    f_j = P_j - sum_v p[j][v] x_v (minimised, integer-valued)."""
+    X = _f32(X).copy()
+    profit, weight, cap = _i32(profit), _i32(weight), _i32(cap)
+    if order is None:
+        order = kp_order(profit, weight)
+    n, d = X.shape
+    m = profit.shape[0]
+    F = np.zeros((n, m), dtype=np.float32)
+    _load().orc_kp_eval(_p(X), n, d, m, _p(profit), _p(weight), _p(cap), _p(_i32(order)), _p(F))
+    return X, F
+
+
+def kp_init(N: int, d: int, seed: int):
+    X = np.zeros((N, d), dtype=np.float32)
+    _load().orc_kp_init(N, d, seed, _p(X))
+    return X
+
+
+def kp_vary(X, rank, seed: int, gen: int, p_c=1.0, p_m=None):
+    """Tournament + uniform crossover + bit-flip mutation (N x d bits -> N x d)."""
+    X = _f32(X)
+    rank = _i32(rank)
+    N, d = X.shape
+    if p_m is None:
+        p_m = float(np.float32(1.0) / np.float32(d))
+    Xc = np.zeros_like(X)
+    _load().orc_kp_vary(_p(X), _p(rank), N, d, seed, gen, float(p_c), float(p_m), _p(Xc))
+    return Xc
+
+
+def kp_run(N: int, d: int, profit, weight, cap, Z, seed: int, generations: int, p_c=1.0, p_m=None):
+    """Init + repair/evaluate + ranks 0, then `generations` knapsack generations."""
+    profit, weight, cap = _i32(profit), _i32(weight), _i32(cap)
+    order = kp_order(profit, weight)
+    m = profit.shape[0]
+    if p_m is None:
+        p_m = float(np.float32(1.0) / np.float32(d))
+    X, F = kp_eval(kp_init(N, d, seed), profit, weight, cap, order)
+    rank = np.zeros(N, dtype=np.int32)
+    Z = _f64(Z)
+    for g in range(generations):
+        rc = _load().orc_kp_generation(_p(X), _p(F), _p(rank), N, d, m, _p(profit), _p(weight), _p(cap),
+                                       _p(order), _p(Z), Z.shape[0], seed, g, float(p_c), float(p_m))
+        if rc != OK:
+            raise ValueError("orc_kp_generation failed (rc=%d)" % rc)
+    return X, F, rank
+
+
+def hv(P, ref) -> float:
+    """Hypervolume (minimisation) of P inside the box below ref, exact for m = 2, 3."""
+    P = _f32(P)
+    ref = _f64(ref)
+    v = float(_load().orc_hv(_p(P), P.shape[0], P.shape[1], _p(ref)))
+    if v < 0:
+        raise ValueError("hv: m must be 2 or 3")
+    return v
+
+
+def normalized_hv(P, fmin, fmax) -> float:
+    """App. E: ref = 1.01 f_max, ideal = 0.9 f_min, HV / prod(ref - ideal)."""
+    ref = 1.01 * _f64(fmax)
+    ideal = 0.9 * _f64(fmin)
+    return hv(P, ref) / float(np.prod(ref - ideal))
 
 
 if __name__ == "__main__":  # pragma: no cover

@@ -926,6 +926,223 @@ int orc_generation(float *X, float *F, int32_t *rank, int N, int d, int m, const
     return rc;
 }
 
+/* ====================================================================== */
+/* Second workload: 0-1 multi-objective knapsack, a reading of the         */
+/* MOKnapsack family the paper evaluates (Sec. IV, App. E); the paper      */
+/* gives no instance, so the instance data are inputs.  m knapsacks share */
+/* d items with integer profits p[j][v] and weights w[j][v] > 0 and       */
+/* capacities c[j].  Objectives (minimised, non-negative):                */
+/*   f_j(x) = P_j - sum_v p[j][v] x_v,   P_j = sum_v p[j][v].             */
+/* Repair to feasibility: items leave in a fixed order (ascending         */
+/* max_j p[j][v] / w[j][v], ties to the lower item) while a knapsack      */
+/* overflows; the repaired x replaces x.  All arithmetic is integer.      */
+/* ====================================================================== */
+
+/* 1 if item a's best profit/weight ratio is below item b's (exact, by    */
+/* cross multiplication), ties broken by index. */
+static int orc_kp_before(const int32_t *p, const int32_t *w, int m, int d, int a, int b)
+{
+    int64_t na = p[a], da = w[a], nb = p[b], db = w[b];
+    for (int j = 1; j < m; ++j) {
+        if ((int64_t)p[(size_t)j * d + a] * da > na * (int64_t)w[(size_t)j * d + a]) {
+            na = p[(size_t)j * d + a];
+            da = w[(size_t)j * d + a];
+        }
+        if ((int64_t)p[(size_t)j * d + b] * db > nb * (int64_t)w[(size_t)j * d + b]) {
+            nb = p[(size_t)j * d + b];
+            db = w[(size_t)j * d + b];
+        }
+    }
+    if (na * db != nb * da) return na * db < nb * da;
+    return a < b;
+}
+
+void orc_kp_order(const int32_t *p, const int32_t *w, int m, int d, int32_t *order)
+{
+    for (int v = 0; v < d; ++v) order[v] = v;
+    for (int i = 1; i < d; ++i) {  /* insertion sort: plain and stable */
+        int32_t x = order[i];
+        int k = i - 1;
+        while (k >= 0 && orc_kp_before(p, w, m, d, x, order[k])) {
+            order[k + 1] = order[k];
+            --k;
+        }
+        order[k + 1] = x;
+    }
+}
+
+void orc_kp_eval(float *X, int n, int d, int m, const int32_t *p, const int32_t *w,
+                 const int32_t *cap, const int32_t *order, float *F)
+{
+    for (int i = 0; i < n; ++i) {
+        float *x = X + (size_t)i * d;
+        int64_t load[64];
+        for (int j = 0; j < m; ++j) {
+            load[j] = 0;
+            for (int v = 0; v < d; ++v)
+                if (x[v] != 0.0f) load[j] += w[(size_t)j * d + v];
+        }
+        for (int k = 0; k < d; ++k) {
+            int over = 0;
+            for (int j = 0; j < m; ++j)
+                if (load[j] > cap[j]) over = 1;
+            if (!over) break;
+            int v = order[k];
+            if (x[v] != 0.0f) {
+                x[v] = 0.0f;
+                for (int j = 0; j < m; ++j) load[j] -= w[(size_t)j * d + v];
+            }
+        }
+        for (int j = 0; j < m; ++j) {
+            int64_t left = 0;
+            for (int v = 0; v < d; ++v)
+                if (x[v] == 0.0f) left += p[(size_t)j * d + v];
+            F[(size_t)i * m + j] = (float)left;
+        }
+    }
+}
+
+/* Initial bits: Philox(i*d + v, 0, 6, 0) word 0 < 0.5 -> item v chosen.   */
+void orc_kp_init(int N, int d, uint64_t seed, float *X)
+{
+    for (int i = 0; i < N; ++i)
+        for (int v = 0; v < d; ++v) {
+            uint32_t o[4];
+            orc_draw(seed, (uint32_t)i * (uint32_t)d + (uint32_t)v, 0, ORC_STREAM_INIT, 0, o);
+            X[(size_t)i * d + v] = ((float)orc_uniform(o[0]) < 0.5f) ? 1.0f : 0.0f;
+        }
+}
+
+/* Binary variation: the tournament and crossover decision of orc_vary;   */
+/* uniform crossover: Philox(q*d + v, gen, 2, 0) word 0 < 0.5 swaps the    */
+/* parents' bits of item v between the children; bit-flip mutation:       */
+/* Philox(q*d + v, gen, 3, 0) word 0 < p_m flips child 2q's bit, word 1   */
+/* < p_m flips child 2q+1's bit.                                           */
+void orc_kp_vary(const float *X, const int32_t *rank, int N, int d, uint64_t seed, uint32_t gen,
+                 float p_c, float p_m, float *Xc)
+{
+    for (int q = 0; q < N / 2; ++q) {
+        uint32_t t[4], cxw[4];
+        orc_draw(seed, (uint32_t)q, gen, ORC_STREAM_TOURNAMENT, 0, t);
+        orc_draw(seed, (uint32_t)q, gen, ORC_STREAM_TOURNAMENT, 1, cxw);
+        uint32_t a1 = orc_bounded(t[0], (uint32_t)N), b1 = orc_bounded(t[1], (uint32_t)N);
+        uint32_t a2 = orc_bounded(t[2], (uint32_t)N), b2 = orc_bounded(t[3], (uint32_t)N);
+        uint32_t p1 = rank[b1] < rank[a1] ? b1 : a1;
+        uint32_t p2 = rank[b2] < rank[a2] ? b2 : a2;
+        int cross = (float)orc_uniform(cxw[0]) < p_c;
+        for (int v = 0; v < d; ++v) {
+            float c1 = X[(size_t)p1 * d + v], c2 = X[(size_t)p2 * d + v];
+            uint32_t s[4], pm[4];
+            orc_draw(seed, (uint32_t)q * (uint32_t)d + (uint32_t)v, gen, ORC_STREAM_SBX, 0, s);
+            if (cross && (float)orc_uniform(s[0]) < 0.5f) { float tt = c1; c1 = c2; c2 = tt; }
+            orc_draw(seed, (uint32_t)q * (uint32_t)d + (uint32_t)v, gen, ORC_STREAM_PM, 0, pm);
+            if ((float)orc_uniform(pm[0]) < p_m) c1 = 1.0f - c1;
+            if ((float)orc_uniform(pm[1]) < p_m) c2 = 1.0f - c2;
+            Xc[(size_t)(2 * q) * d + v] = c1;
+            Xc[(size_t)(2 * q + 1) * d + v] = c2;
+        }
+    }
+}
+
+/* One knapsack generation (Alg. 1): Q = vary(P), repaired and evaluated; */
+/* R = P u Q; select; P' = R[sel].  X, F, rank are overwritten.           */
+int orc_kp_generation(float *X, float *F, int32_t *rank, int N, int d, int m, const int32_t *p,
+                      const int32_t *w, const int32_t *cap, const int32_t *order, const double *Z,
+                      int nz, uint64_t seed, uint32_t gen, float p_c, float p_m)
+{
+    int n2 = 2 * N;
+    float *RX = (float *)malloc((size_t)n2 * d * sizeof(float));
+    float *RF = (float *)malloc((size_t)n2 * m * sizeof(float));
+    int32_t *rr = (int32_t *)malloc((size_t)n2 * sizeof(int32_t));
+    int32_t *sel = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    if (!RX || !RF || !rr || !sel) return ORC_ENOMEM;
+    memcpy(RX, X, (size_t)N * d * sizeof(float));
+    memcpy(RF, F, (size_t)N * m * sizeof(float));
+    orc_kp_vary(X, rank, N, d, seed, gen, p_c, p_m, RX + (size_t)N * d);
+    orc_kp_eval(RX + (size_t)N * d, N, d, m, p, w, cap, order, RF + (size_t)N * m);
+    int rc = orc_select(RF, N, m, Z, nz, seed, gen, 0, 0, rr, sel, NULL, NULL, NULL);
+    if (rc == ORC_OK) {
+        for (int k = 0; k < N; ++k) {
+            memcpy(X + (size_t)k * d, RX + (size_t)sel[k] * d, (size_t)d * sizeof(float));
+            memcpy(F + (size_t)k * m, RF + (size_t)sel[k] * m, (size_t)m * sizeof(float));
+            rank[k] = rr[sel[k]];
+        }
+    }
+    free(RX); free(RF); free(rr); free(sel);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Hypervolume (minimisation) of the points P[n][m] inside the box below  */
+/* ref, exact for m <= 3: m = 2 by a sweep over ascending f_0; m = 3 by    */
+/* slices along f_2, each slice's area by the m = 2 sweep.  Returns -1   */
+/* for m > 3.  App. E normalises it by prod_j (ref_j - ideal_j).          */
+/* ---------------------------------------------------------------------- */
+static int orc_cmp_f0(const void *a, const void *b)
+{
+    const double *x = (const double *)a, *y = (const double *)b;
+    if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;
+    return (x[1] < y[1]) ? -1 : (x[1] > y[1]);
+}
+
+static double orc_hv2(double *pts, int n, const double *ref)
+{
+    qsort(pts, (size_t)n, 2 * sizeof(double), orc_cmp_f0);
+    double area = 0.0, best = ref[1];
+    for (int i = 0; i < n; ++i) {
+        double x = pts[2 * i], y = pts[2 * i + 1];
+        if (x >= ref[0] || y >= best) continue;
+        area += (ref[0] - x) * (best - y);
+        best = y;
+    }
+    return area;
+}
+
+double orc_hv(const float *P, int n, int m, const double *ref)
+{
+    if (m < 2 || m > 3 || n < 0) return -1.0;
+    double *pts = (double *)malloc((size_t)(n > 0 ? n : 1) * 2 * sizeof(double));
+    if (!pts) return -1.0;
+    double hv = 0.0;
+    if (m == 2) {
+        for (int i = 0; i < n; ++i) {
+            pts[2 * i] = P[(size_t)i * m];
+            pts[2 * i + 1] = P[(size_t)i * m + 1];
+        }
+        hv = orc_hv2(pts, n, ref);
+    } else {
+        /* distinct f_2 levels below ref_2, ascending */
+        double *lev = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+        if (!lev) { free(pts); return -1.0; }
+        int nl = 0;
+        for (int i = 0; i < n; ++i)
+            if ((double)P[(size_t)i * m + 2] < ref[2]) lev[nl++] = P[(size_t)i * m + 2];
+        for (int i = 1; i < nl; ++i) {  /* insertion sort */
+            double x = lev[i];
+            int k = i - 1;
+            while (k >= 0 && lev[k] > x) { lev[k + 1] = lev[k]; --k; }
+            lev[k + 1] = x;
+        }
+        for (int t = 0; t < nl; ++t) {
+            if (t > 0 && lev[t] == lev[t - 1]) continue;
+            int k = 0;
+            for (int i = 0; i < n; ++i)
+                if ((double)P[(size_t)i * m + 2] <= lev[t]) {
+                    pts[2 * k] = P[(size_t)i * m];
+                    pts[2 * k + 1] = P[(size_t)i * m + 1];
+                    ++k;
+                }
+            double top = ref[2];
+            for (int u = t + 1; u < nl; ++u)
+                if (lev[u] > lev[t]) { top = lev[u]; break; }
+            hv += orc_hv2(pts, k, ref) * (top - lev[t]);
+        }
+        free(lev);
+    }
+    free(pts);
+    return hv;
+}
+
 /* ---------------------------------------------------------------------- */
 /* IGD: mean over reference-front points of the Euclidean distance to the */
 /* nearest population point (FP64).                                        */

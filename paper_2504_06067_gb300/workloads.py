@@ -48,6 +48,21 @@ LARGE = RunConfig("m10_N100000_d200_p3+2", m=10, d=200, N=100000, p1=3, p2=2, ta
 HUGE = RunConfig("m10_N1000000_d200_p3+2", m=10, d=200, N=1000000, p1=3, p2=2, tau=0.5,
                  generations=20)
 PLAIN_CONFIGS = (SMALL, SCALE, LARGE)
+# 0-1 knapsack workload (binary variables): m = 3 knapsacks, d = 500 items,
+# N = 12,800 (the largest population of the paper's discrete runs), p = 158
+# (12,720 directions).
+KNAPSACK = RunConfig("kp_m3_N12800_d500_p158", m=3, d=500, N=12800, p1=158, generations=100)
+
+
+def knapsack_instance(m: int, d: int, seed: int = 0):
+    """Integer profits and weights uniform in [10, 100] (m x d) and capacities
+    of half the total weight per knapsack: the usual random 0-1 multi-
+    objective knapsack instance.  Returns (profit, weight, capacity) int32."""
+    rng = np.random.default_rng([seed, 13, m, d])
+    profit = rng.integers(10, 101, size=(m, d)).astype(np.int32)
+    weight = rng.integers(10, 101, size=(m, d)).astype(np.int32)
+    capacity = (weight.astype(np.int64).sum(axis=1) // 2).astype(np.int32)
+    return profit, weight, capacity
 
 
 def objective_weights(m: int, seed: int) -> np.ndarray:

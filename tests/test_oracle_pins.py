@@ -531,3 +531,84 @@ def test_small_run_approaches_closed_form_front(orc):
     X0 = orc.init_population(cfg.N, cfg.d, cfg.seed)
     igd_start = orc.igd(orc.evaluate(X0, W), R)
     assert igd_end < 0.1 * igd_start
+
+
+# ------------------------------------------------------ 0-1 knapsack -------
+def test_kp_repair_hand_example(orc):
+    """Two knapsacks, four items.  Best ratios: item 0 max(10/5, 1/1) = 2,
+    item 1 max(1/10, 2/10) = 0.2, item 2 max(6/6, 6/2) = 3, item 3
+    max(4/8, 5/5) = 1, so items leave in the order 1, 3, 0, 2.  With every
+    item chosen the loads (29, 18) exceed the capacities (15, 12): item 1
+    leaves (19, 8), still over in knapsack 0; item 3 leaves (11, 3): done."""
+    profit = np.array([[10, 1, 6, 4], [1, 2, 6, 5]], dtype=np.int32)
+    weight = np.array([[5, 10, 6, 8], [1, 10, 2, 5]], dtype=np.int32)
+    cap = np.array([15, 12], dtype=np.int32)
+    assert np.array_equal(orc.kp_order(profit, weight), [1, 3, 0, 2])
+    X, F = orc.kp_eval(np.ones((1, 4), dtype=np.float32), profit, weight, cap)
+    assert np.array_equal(X[0], [1, 0, 1, 0])
+    # f_j = P_j - profit kept: P = (21, 14), kept (16, 7)
+    assert np.array_equal(F[0], [5, 7])
+
+
+def test_kp_repair_is_feasible_and_minimal(orc):
+    profit, weight, cap = wl.knapsack_instance(4, 60, seed=1)
+    order = orc.kp_order(profit, weight)
+    X0 = orc.kp_init(40, 60, seed=2)
+    X, F = orc.kp_eval(X0, profit, weight, cap, order)
+    W = weight.astype(np.int64)
+    for x0, x in zip(X0, X):
+        assert np.all(W @ x.astype(np.int64) <= cap)               # feasible
+        removed = np.flatnonzero(x0 != x)
+        assert np.all(x0[removed] == 1)                             # only removals
+        if len(removed):
+            pos = {int(v): k for k, v in enumerate(order)}
+            last = max(pos[int(v)] for v in removed)
+            # every chosen item before the last removed one in the order left
+            assert all(x[order[k]] == 0 for k in range(last + 1))
+            back = x.copy()
+            back[order[last]] = 1                                    # minimal prefix
+            assert np.any(W @ back.astype(np.int64) > cap)
+    # objectives: total profit minus profit kept (exact integers)
+    assert np.array_equal(F, (profit.sum(1)[None, :] - X.astype(np.int64) @ profit.T).astype(np.float32))
+
+
+def test_kp_uniform_crossover_conserves_bits(orc):
+    N, d = 40, 64
+    X = orc.kp_init(N, d, seed=3)
+    rank = np.zeros(N, dtype=np.int32)
+    Xc = orc.kp_vary(X, rank, seed=4, gen=0, p_m=0.0)
+    # without mutation every child pair carries, item by item, the bits of
+    # two parents: the pair's column sums are 0, 1 or 2 and appear in X
+    s = Xc[0::2] + Xc[1::2]
+    assert set(np.unique(s).tolist()) <= {0.0, 1.0, 2.0}
+    assert np.array_equal(np.unique(Xc), [0.0, 1.0])
+
+
+def test_kp_bit_flip_rate(orc):
+    N, d = 200, 100
+    X = np.zeros((N, d), dtype=np.float32)
+    rank = np.zeros(N, dtype=np.int32)
+    Xc = orc.kp_vary(X, rank, seed=5, gen=1, p_c=0.0)
+    rate = Xc.mean()
+    assert abs(rate - 1.0 / d) < 0.3 / d
+
+
+def test_hv_closed_forms(orc):
+    assert orc.hv([[1, 2]], [4, 5]) == 3 * 3
+    # staircase: two boxes minus the overlap
+    assert orc.hv([[1, 3], [2, 1]], [4, 5]) == 3 * 2 + 2 * 4 - 2 * 2
+    assert orc.hv([[5, 1]], [4, 5]) == 0.0          # outside the box
+    assert orc.hv([[1, 2, 3]], [2, 4, 7]) == 1 * 2 * 4
+    # two 3-D boxes: inclusion-exclusion
+    a, b, r = np.array([0, 2, 1.0]), np.array([2, 0, 3.0]), np.array([4, 4, 4.0])
+    inter = np.prod(r - np.maximum(a, b))
+    assert abs(orc.hv([a, b], r) - (np.prod(r - a) + np.prod(r - b) - inter)) < 1e-12
+
+
+def test_normalized_hv_app_e(orc):
+    """App. E: ref = 1.01 f_max, ideal = 0.9 f_min; a single point at the
+    ideal-side corner f_min gives prod(1.01 f_max - f_min) / prod(1.01 f_max - 0.9 f_min)."""
+    fmin, fmax = np.array([2.0, 4.0]), np.array([10.0, 20.0])
+    v = orc.normalized_hv([fmin], fmin, fmax)
+    expect = np.prod(1.01 * fmax - fmin) / np.prod(1.01 * fmax - 0.9 * fmin)
+    assert abs(v - expect) < 1e-12 and 0 < v < 1
