@@ -36,7 +36,8 @@ if ROOT not in sys.path:
 from paper_2504_06067_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "selected sols/s & gens/s (% HBM roofline); batched/served runs/s, p50/p99 vs plain"
-WORKLOADS = {"small": wl.SMALL, "scale": wl.SCALE, "large": wl.LARGE, "huge": wl.HUGE}
+WORKLOADS = {"small": wl.SMALL, "scale": wl.SCALE, "large": wl.LARGE, "huge": wl.HUGE,
+             "knapsack": wl.KNAPSACK}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
 NUM_SMS = 152
 LANES_PER_SM = 128
@@ -199,6 +200,11 @@ def run_ours(args, world, rank, local):
     W = wl.objective_weights(cfg.m, cfg.seed)
     streaming = 1 if (args.streaming or args.workload == "huge") else 0
     opts = n.default_opts(seed=seed, p2=cfg.p2, tau=cfg.tau, W=W.ctypes.data, streaming=streaming)
+    if args.workload == "knapsack":
+        kp = wl.knapsack_instance(cfg.m, cfg.d, cfg.seed)
+        opts = n.default_opts(seed=seed, problem=1, kp_profit=kp[0].ctypes.data,
+                              kp_weight=kp[1].ctypes.data, kp_capacity=kp[2].ctypes.data,
+                              streaming=streaming)
     ctx = n.create(cfg.m, cfg.d, cfg.N, cfg.p1, opts)
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
@@ -334,7 +340,9 @@ def run_ours(args, world, rank, local):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "data": "synthetic (seeded softmax-simplex objective, W ~ N(0,1); stands in for DTLZ)",
+        "data": ("synthetic 0-1 knapsack instance (profits, weights U[10, 100], capacity half the "
+                 "weight; stands in for MOKnapsack)" if args.workload == "knapsack" else
+                 "synthetic (seeded softmax-simplex objective, W ~ N(0,1); stands in for DTLZ)"),
         "config": {"workload": cfg.name + ("_streaming" if streaming else ""), "m": cfg.m, "N": cfg.N,
                    "d": cfg.d, "refs": cfg.w,
                    "generations": "timed %d from generation 0" % K,
@@ -639,6 +647,23 @@ def oracle_generations(cfg, budget_s, max_steps=None, warmup=0):
 
     import oracle
     oracle.build()
+    if cfg is wl.KNAPSACK:
+        kp = wl.knapsack_instance(cfg.m, cfg.d, cfg.seed)
+        order = oracle.kp_order(kp[0], kp[1])
+        Z = oracle.refdirs(cfg.m, cfg.p1)
+        X, F = oracle.kp_eval(oracle.kp_init(cfg.N, cfg.d, cfg.seed), *kp)
+        rank = np.zeros(cfg.N, np.int32)
+        times = []
+        t_start = time.perf_counter()
+        g = 0
+        while True:
+            t0 = time.perf_counter()
+            X, F, rank = oracle.kp_generation(X, F, rank, *kp, order, Z, cfg.seed, g)
+            times.append(time.perf_counter() - t0)
+            g += 1
+            if (max_steps is not None and len(times) >= max_steps) or time.perf_counter() - t_start >= budget_s:
+                break
+        return sum(times) / len(times), len(times)
     W = wl.objective_weights(cfg.m, cfg.seed)
     Z = oracle.refdirs(cfg.m, cfg.p1, cfg.p2, cfg.tau)
     X = oracle.init_population(cfg.N, cfg.d, cfg.seed)

@@ -69,6 +69,12 @@ typedef struct {
                                history starts empty at nsga3_create and nsga3_init and is
                                updated by every selection that normalizes.  0: stateless
                                (ideal and extremes of the current S u F_l only) */
+    int problem;            /* 0: softmax-simplex objective (needs W); 1: 0-1 multi-objective
+                               knapsack over d items (needs the kp_* arrays): binary
+                               variables, uniform crossover, bit-flip mutation, repair */
+    const int32_t* kp_profit;   /* host, m x d profits (> 0), read during create only */
+    const int32_t* kp_weight;   /* host, m x d weights (> 0), read during create only */
+    const int32_t* kp_capacity; /* host, m capacities, read during create only */
 } nsga3_opts;
 
 /* Fills *o with the defaults above (seed 0, single layer, tau 0.5). */

@@ -361,6 +361,21 @@ def kp_vary(X, rank, seed: int, gen: int, p_c=1.0, p_m=None):
     return Xc
 
 
+def kp_generation(X, F, rank, profit, weight, cap, order, Z, seed: int, gen: int, p_c=1.0, p_m=None):
+    """One knapsack generation on copies; returns (X, F, rank)."""
+    X, F, rank = _f32(X).copy(), _f32(F).copy(), _i32(rank).copy()
+    profit, weight, cap, order, Z = _i32(profit), _i32(weight), _i32(cap), _i32(order), _f64(Z)
+    N, d = X.shape
+    m = F.shape[1]
+    if p_m is None:
+        p_m = float(np.float32(1.0) / np.float32(d))
+    rc = _load().orc_kp_generation(_p(X), _p(F), _p(rank), N, d, m, _p(profit), _p(weight), _p(cap),
+                                   _p(order), _p(Z), Z.shape[0], seed, gen, float(p_c), float(p_m))
+    if rc != OK:
+        raise ValueError("orc_kp_generation failed (rc=%d)" % rc)
+    return X, F, rank
+
+
 def kp_run(N: int, d: int, profit, weight, cap, Z, seed: int, generations: int, p_c=1.0, p_m=None):
     """Init + repair/evaluate + ranks 0, then `generations` knapsack generations."""
     profit, weight, cap = _i32(profit), _i32(weight), _i32(cap)

@@ -85,6 +85,12 @@ struct RunView {
     int debug_recheck_all;
     int streaming;         // no Dom matrix: the peel recomputes dominance from Fp
     int norm_history;      // normalization with a running ideal and remembered extremes
+    int problem;           // 0 softmax-simplex, 1 0-1 knapsack
+    const int32_t* kp_p;   // m x d profits
+    const int32_t* kp_w;   // m x d weights
+    const int32_t* kp_cap; // m capacities
+    const int32_t* kp_total;  // m total profits
+    const int32_t* kp_order;  // d items in repair order
     uint64_t seed;
     float eta_c, eta_m, p_c, p_m;
     Ctrl* ctrl;

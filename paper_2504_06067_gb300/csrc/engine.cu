@@ -42,7 +42,7 @@ struct nsga3_ctx {
     int m = 0, d = 0, N = 0, n2 = 0, ld = 0, NW = 0, w = 0, M4 = 0, p1 = 0, p2 = 0;
     double tau = 0.5;
     nsga3_opts opts{};
-    bool has_W = false;
+    bool has_obj = false;  // an objective is defined (W, or the knapsack arrays)
     RunView v{};    // generation view (population buffers)
     RunView vs{};   // selection view (own objective buffer)
     std::vector<void*> allocs;
@@ -252,7 +252,7 @@ nsga3_status build_graphs(nsga3_ctx* ctx)
     CK(cudaGraphInstantiate(&ctx->gx_select, g, 0));
     cudaGraphDestroy(g);
     g = nullptr;
-    if (!ctx->has_W) return NSGA3_OK;
+    if (!ctx->has_obj) return NSGA3_OK;
     CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeRelaxed));
     st = record_generation(ctx, ctx->cap, true);
     {
@@ -349,6 +349,31 @@ void build_ref_blocks(int m, int w, int M4, const std::vector<double>& Z, std::v
     }
 }
 
+// Knapsack repair order: items by ascending best profit/weight ratio
+// max_j p[j][v] / w[j][v], compared exactly by cross multiplication, ties to
+// the lower item.
+void kp_repair_order(const int32_t* p, const int32_t* w, int m, int d, std::vector<int32_t>& order)
+{
+    std::vector<int64_t> num(d), den(d);
+    for (int v = 0; v < d; ++v) {
+        num[v] = p[v];
+        den[v] = w[v];
+        for (int j = 1; j < m; ++j) {
+            const int64_t pj = p[(size_t)j * d + v], wj = w[(size_t)j * d + v];
+            if (pj * den[v] > num[v] * wj) {
+                num[v] = pj;
+                den[v] = wj;
+            }
+        }
+    }
+    order.resize(d);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const int64_t l = num[a] * den[b], r = num[b] * den[a];
+        return l < r;
+    });
+}
+
 // Allocates every device buffer of the context (or, in a sizing pass, only
 // counts their bytes).
 nsga3_status setup_alloc(nsga3_ctx* ctx)
@@ -368,6 +393,7 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     v.debug_recheck_all = ctx->opts.debug_recheck_all ? 1 : 0;
     v.streaming = ctx->opts.streaming ? 1 : 0;
     v.norm_history = ctx->opts.norm_history ? 1 : 0;
+    v.problem = ctx->opts.problem;
     v.seed = ctx->opts.seed;
     v.eta_c = ctx->opts.eta_c;
     v.eta_m = ctx->opts.eta_m;
@@ -441,6 +467,19 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     AL(nz, w);
     AL(Zh, (size_t)w * M4);
     AL(Wd, (size_t)m * (m - 1));
+    if (v.problem == 1) {
+        int32_t *kp, *kw, *kc, *kt, *ko;
+        AL(kp, (size_t)m * d);
+        AL(kw, (size_t)m * d);
+        AL(kc, m);
+        AL(kt, m);
+        AL(ko, d);
+        v.kp_p = kp;
+        v.kp_w = kw;
+        v.kp_cap = kc;
+        v.kp_total = kt;
+        v.kp_order = ko;
+    }
     v.Zd = Zd;
     v.nz = nz;
     v.Zh = Zh;
@@ -480,8 +519,25 @@ nsga3_status setup(nsga3_ctx* ctx)
     CK(launch_nan_pad(v, s));
     CK(launch_nan_pad(ctx->vs, s));
     CK(launch_refdirs(v, ctx->p1, ctx->p2, ctx->tau, Zd, nz, Zh, s));
-    if (ctx->has_W)
+    if (ctx->has_obj && v.problem == 0)
         CK(cudaMemcpyAsync(Wd, ctx->opts.W, (size_t)m * (m - 1) * sizeof(float), cudaMemcpyHostToDevice, s));
+    std::vector<int32_t> kp_order, kp_total;
+    if (ctx->has_obj && v.problem == 1) {
+        kp_repair_order(ctx->opts.kp_profit, ctx->opts.kp_weight, m, d, kp_order);
+        kp_total.assign(m, 0);
+        for (int j = 0; j < m; ++j)
+            for (int e = 0; e < d; ++e) kp_total[j] += ctx->opts.kp_profit[(size_t)j * d + e];
+        CK(cudaMemcpyAsync(const_cast<int32_t*>(v.kp_p), ctx->opts.kp_profit, (size_t)m * d * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(const_cast<int32_t*>(v.kp_w), ctx->opts.kp_weight, (size_t)m * d * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(const_cast<int32_t*>(v.kp_cap), ctx->opts.kp_capacity, (size_t)m * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(const_cast<int32_t*>(v.kp_total), kp_total.data(), (size_t)m * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(const_cast<int32_t*>(v.kp_order), kp_order.data(), (size_t)d * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s));
+    }
     CK(cudaStreamSynchronize(s));
     {
         std::vector<double> Zh((size_t)w * m);
@@ -561,6 +617,22 @@ nsga3_status ctx_fields(nsga3_ctx* ctx, int m, int d, int N, int ref_divisions, 
     if ((long long)N * d >= (1LL << 32)) return fail(ctx, NSGA3_EINVAL, "N*d must be < 2^32");
     if (ref_divisions < 1 || o.p2 < 0) return fail(ctx, NSGA3_EINVAL, "bad reference divisions");
     if (!(o.tau >= 0.0 && o.tau <= 1.0)) return fail(ctx, NSGA3_EINVAL, "tau outside [0,1]");
+    if (o.problem != 0 && o.problem != 1) return fail(ctx, NSGA3_EINVAL, "problem %d unknown", o.problem);
+    if (o.problem == 1 && o.kp_profit && o.kp_weight && o.kp_capacity) {
+        // integer sums stay exact: weights below 2^31, objectives (profit
+        // totals) below 2^24 so that FP32 holds them exactly
+        for (int j = 0; j < m; ++j) {
+            long long tp = 0, tw = 0;
+            for (int e = 0; e < d; ++e) {
+                const long long pe = o.kp_profit[(size_t)j * d + e], we = o.kp_weight[(size_t)j * d + e];
+                if (pe <= 0 || we <= 0) return fail(ctx, NSGA3_EINVAL, "knapsack profits and weights must be > 0");
+                tp += pe;
+                tw += we;
+            }
+            if (tp >= (1LL << 24) || tw >= (1LL << 31) || o.kp_capacity[j] < 0)
+                return fail(ctx, NSGA3_EINVAL, "knapsack %d: total profit must be < 2^24, total weight < 2^31", j);
+        }
+    }
     long long w = binom(ref_divisions + m - 1, m - 1) + (o.p2 > 0 ? binom(o.p2 + m - 1, m - 1) : 0);
     if (w < 1 || w > (1LL << 24)) return fail(ctx, NSGA3_EINVAL, "reference set size %lld", w);
     ctx->m = m;
@@ -575,7 +647,8 @@ nsga3_status ctx_fields(nsga3_ctx* ctx, int m, int d, int N, int ref_divisions, 
     ctx->p2 = o.p2;
     ctx->tau = o.tau;
     ctx->opts = o;
-    ctx->has_W = o.W != nullptr;  // W is read during create only
+    // W and the knapsack arrays are read during create only
+    ctx->has_obj = o.problem == 1 ? (o.kp_profit && o.kp_weight && o.kp_capacity) : o.W != nullptr;
     return NSGA3_OK;
 }
 
@@ -811,7 +884,7 @@ nsga3_status nsga3_select(nsga3_ctx* ctx, const float* objs, int32_t* ranks, int
 nsga3_status nsga3_init(nsga3_ctx* ctx, void* stream)
 {
     if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
-    if (!ctx->has_W) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W was NULL)");
+    if (!ctx->has_obj) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W or the knapsack arrays were NULL)");
     cudaStream_t s = (cudaStream_t)stream;
     CK(launch_init(ctx->v, s));
     CK(cudaMemsetAsync(&ctx->v.ctrl->hvalid, 0, sizeof(int32_t), s));  // a new run starts without history
@@ -824,7 +897,7 @@ nsga3_status nsga3_init(nsga3_ctx* ctx, void* stream)
 nsga3_status nsga3_vary(nsga3_ctx* ctx, void* stream)
 {
     if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
-    if (!ctx->has_W) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W was NULL)");
+    if (!ctx->has_obj) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W or the knapsack arrays were NULL)");
     CK(launch_vary_eval(ctx->v, (cudaStream_t)stream));
     ctx->host_launches += 2;
     return NSGA3_OK;
@@ -833,7 +906,7 @@ nsga3_status nsga3_vary(nsga3_ctx* ctx, void* stream)
 nsga3_status nsga3_step(nsga3_ctx* ctx, void* stream)
 {
     if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
-    if (!ctx->has_W) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W was NULL)");
+    if (!ctx->has_obj) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W or the knapsack arrays were NULL)");
     if (ctx->eager) {
         nsga3_status st = eager_generation(ctx, (cudaStream_t)stream);
         if (st) return st;
@@ -860,7 +933,7 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
     nsga3_ctx* ctx = (n > 0 && ctxs) ? ctxs[0] : nullptr;
     if (!ctx || generations < 0) return fail(ctx, NSGA3_EINVAL, "bad arguments");
     for (int r = 0; r < n; ++r)
-        if (!ctxs[r] || !ctxs[r]->has_W) return fail(ctx, NSGA3_EINVAL, "run %d has no objective", r);
+        if (!ctxs[r] || !ctxs[r]->has_obj) return fail(ctx, NSGA3_EINVAL, "run %d has no objective", r);
     if (ctx->eager) {
         for (int g = 0; g < generations; ++g)
             for (int r = 0; r < n; ++r) {

@@ -243,6 +243,7 @@ cudaError_t launch_refdirs(const RunView& v, int p1, int p2, double tau, double*
 
 cudaError_t launch_init(const RunView& v, cudaStream_t s)
 {
+    if (v.problem == 1) return launch_kp_init(v, s);
     long long threads = (long long)v.N * 32;
     k_init<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
@@ -253,6 +254,7 @@ cudaError_t launch_init(const RunView& v, cudaStream_t s)
 
 cudaError_t launch_vary_eval(const RunView& v, cudaStream_t s)
 {
+    if (v.problem == 1) return launch_kp_vary_eval(v, s);
     long long threads = (long long)(v.N / 2) * 32;
     k_vary_eval<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();

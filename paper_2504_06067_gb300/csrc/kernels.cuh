@@ -15,6 +15,9 @@ cudaError_t launch_nan_pad(const RunView& v, cudaStream_t s);
 cudaError_t launch_vary_eval(const RunView& v, cudaStream_t s);
 
 // selection (Alg. 1 sort / Alg. 2)
+// 0-1 knapsack workload (k_knapsack.cu): bits + repair + objectives
+cudaError_t launch_kp_init(const RunView& v, cudaStream_t s);
+cudaError_t launch_kp_vary_eval(const RunView& v, cudaStream_t s);
 cudaError_t launch_sel_reset(const RunView& v, cudaStream_t s);
 cudaError_t launch_check_finite(const RunView& v, cudaStream_t s);
 cudaError_t launch_sort(const RunView& v, int num_sms, cudaStream_t s);

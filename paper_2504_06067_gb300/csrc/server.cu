@@ -475,8 +475,8 @@ nsga3_status nsga3_server_submit(nsga3_server* s, const nsga3_request* req, int6
         set_err(s, "submit: %s", err.c_str());
         return st;
     }
-    if (req->generations < 0 || !req->opts.W) {
-        set_err(s, "submit: generations must be >= 0 and opts.W set");
+    if (req->generations < 0 || !req->opts.W || req->opts.problem != 0) {
+        set_err(s, "submit: generations must be >= 0 and opts.W set (softmax-simplex problem only)");
         return NSGA3_EINVAL;
     }
     q.W.assign(req->opts.W, req->opts.W + (size_t)req->m * (req->m - 1));

@@ -41,6 +41,10 @@ class nsga3_opts(C.Structure):
         ("W", C.c_void_p),
         ("streaming", C.c_int),
         ("norm_history", C.c_int),
+        ("problem", C.c_int),
+        ("kp_profit", C.c_void_p),
+        ("kp_weight", C.c_void_p),
+        ("kp_capacity", C.c_void_p),
     ]
 
 
