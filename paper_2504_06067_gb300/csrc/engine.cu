@@ -151,9 +151,9 @@ nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s,
     CK(launch_peel(v, ctx->num_sms, s));
     st = record_event(ctx, s, EV_PEEL, events);
     if (st) return st;
-    CK(launch_post_peel(v, s));
-    // the niching kernels return at once when no niching is needed: a graph
-    // IF node costs more than their empty launches
+    // ranks back to the original order, then (when niching is needed) the
+    // ideal point; the niching kernels return at once when no niching is
+    // needed: a graph IF node costs more than their empty launches
     CK(launch_norm_ideal(v, s));
     CK(launch_norm_extreme(v, s));
     CK(launch_assoc_prep(v, s));
@@ -176,8 +176,7 @@ nsga3_status record_generation(nsga3_ctx* ctx, cudaStream_t s, bool events)
     if (st) return st;
     st = record_selection(ctx, ctx->v, s, false, events);
     if (st) return st;
-    CK(launch_gather(ctx->v, s));
-    CK(launch_bump_gen(ctx->v, s));
+    CK(launch_gather(ctx->v, s));  // next population and the generation counter
     return record_event(ctx, s, EV_END, events);
 }
 
@@ -197,13 +196,12 @@ nsga3_status eager_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, b
     CK(launch_peel(v, ctx->num_sms, s));
     st = record_event(ctx, s, EV_PEEL, true);
     if (st) return st;
-    CK(launch_post_peel(v, s));
+    CK(launch_norm_ideal(v, s));  // also writes the ranks back in the original order
     int32_t hdr[2] = {0, 0};  // status, need_niche
     CK(cudaMemcpyAsync(&hdr[0], &v.ctrl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&hdr[1], &v.ctrl->need_niche, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (hdr[0] == 0 && hdr[1]) {
-        CK(launch_norm_ideal(v, s));
         CK(launch_norm_extreme(v, s));
         CK(launch_assoc_prep(v, s));
         CK(launch_assoc_scan(v, ctx->num_sms, s));
@@ -226,8 +224,7 @@ nsga3_status eager_generation(nsga3_ctx* ctx, cudaStream_t s)
     if (st) return st;
     st = eager_selection(ctx, ctx->v, s, false);
     if (st) return st;
-    CK(launch_gather(ctx->v, s));
-    CK(launch_bump_gen(ctx->v, s));
+    CK(launch_gather(ctx->v, s));  // next population and the generation counter
     return record_event(ctx, s, EV_END, true);
 }
 
@@ -874,7 +871,7 @@ nsga3_status nsga3_select(nsga3_ctx* ctx, const float* objs, int32_t* ranks, int
     } else {
         CK(cudaGraphLaunch(ctx->gx_select, s));
     }
-    ctx->host_launches += 20;
+    ctx->host_launches += 19;
     CK(cudaMemcpyAsync(ranks, ctx->vs.rank2, (size_t)ctx->n2 * sizeof(int32_t), cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(selected, ctx->vs.sel, (size_t)ctx->N * sizeof(int32_t), cudaMemcpyDefault, s));
     ctx->last_kind = 1;
@@ -913,7 +910,7 @@ nsga3_status nsga3_step(nsga3_ctx* ctx, void* stream)
     } else {
         CK(cudaGraphLaunch(ctx->gx_step, (cudaStream_t)stream));
     }
-    ctx->host_launches += 23;
+    ctx->host_launches += 22;
     ctx->last_kind = 2;
     return NSGA3_OK;
 }
@@ -959,7 +956,7 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
     for (int g = 0; g < generations % BATCH_GENS; ++g) CK(cudaGraphLaunch(ctx->gx_batch1, (cudaStream_t)stream));
     for (int r = 0; r < n; ++r) {
         ctxs[r]->last_kind = 3;
-        ctxs[r]->host_launches += 23LL * generations;
+        ctxs[r]->host_launches += 22LL * generations;
     }
     return NSGA3_OK;
 }
@@ -1084,11 +1081,11 @@ nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches)
 {
     if (!ctx || !launches) return fail(ctx, NSGA3_EINVAL, "null argument");
     CK(cudaDeviceSynchronize());
-    // reset, 3 sort, dominance, peel (every pass), post-peel, 11 niching (they
-    // return at once when no niching is needed), compaction (+ finite check
-    // for a selection; + variation, objective, gather, counter for a
-    // generation)
-    *launches = (ctx->last_kind == 1) ? 20 : 23;
+    // reset, 3 sort, dominance, peel (every pass), 11 niching (the first
+    // also writes the ranks back; the others return at once when no niching
+    // is needed), compaction (+ finite check for a selection; + variation,
+    // objective, gather, commit for a generation)
+    *launches = (ctx->last_kind == 1) ? 19 : 22;
     return NSGA3_OK;
 }
 

@@ -169,9 +169,24 @@ __global__ void k_gather(RunView v)
     if (lane == 0) v.ranktmp[p] = v.rank2[i];
 }
 
-__global__ void k_bump_gen(RunView v)
+// the gathered rows become the parents (one kernel for X, F and rank) and
+// the generation counter advances
+__global__ void k_commit(RunView v)
 {
-    if (read_status(v.ctrl) == 0) v.ctrl->gen += 1u;
+    if (read_status(v.ctrl)) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nx = (long long)v.N * v.d;
+    if ((nx & 3) == 0) {
+        const float4* src = reinterpret_cast<const float4*>(v.Xtmp);
+        float4* dst = reinterpret_cast<float4*>(v.X);
+        for (long long e = t0; e < nx / 4; e += stride) dst[e] = src[e];
+    } else {
+        for (long long e = t0; e < nx; e += stride) v.X[e] = v.Xtmp[e];
+    }
+    for (long long e = t0; e < (long long)v.N * v.m; e += stride) v.F[e] = v.Ftmp[e];
+    for (long long e = t0; e < v.N; e += stride) v.rank[e] = v.ranktmp[e];
+    if (t0 == 0) v.ctrl->gen += 1u;
 }
 
 __global__ void k_nan_pad(RunView v)
@@ -218,16 +233,10 @@ cudaError_t launch_gather(const RunView& v, cudaStream_t s)
     k_gather<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(v.X, v.Xtmp, (size_t)v.N * v.d * sizeof(float), cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(v.F, v.Ftmp, (size_t)v.N * v.m * sizeof(float), cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(v.rank, v.ranktmp, (size_t)v.N * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
-}
-
-cudaError_t launch_bump_gen(const RunView& v, cudaStream_t s)
-{
-    k_bump_gen<<<1, 1, 0, s>>>(v);
+    long long blocks = ((long long)v.N * v.d / 4 + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    if (blocks < 1) blocks = 1;
+    k_commit<<<(unsigned)blocks, 256, 0, s>>>(v);
     return cudaGetLastError();
 }
 

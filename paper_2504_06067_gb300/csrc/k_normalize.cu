@@ -18,19 +18,25 @@ namespace {
 constexpr int NB = 256;   // k_norm_ideal
 constexpr int EB = 128;   // k_norm_extreme: two blocks per SM
 
-// members of T are appended to Tlist; ideal point by order-preserving atomicMin
+// Ranks back to the original order (every selection), then, when niching
+// is needed: members of T are appended to Tlist (in bucket order, which no
+// later step depends on) and the ideal point is taken by order-preserving
+// atomicMin over Fp (-0.0 is stored as +0.0 there).
 __global__ void __launch_bounds__(NB) k_norm_ideal(RunView v)
 {
     Ctrl* c = v.ctrl;
-    if (skip_niche(c)) return;
-    const int l = c->l;
-    const int i = blockIdx.x * NB + threadIdx.x;
-    const int lane = lane_id();
-    bool inT = false;
-    if (i < v.n2) {
-        int r = v.rank2[i];
-        inT = r >= 0 && r <= l;
+    if (read_status(c)) return;
+    const int p = blockIdx.x * NB + threadIdx.x;  // position in bucket order
+    int i = -1, r = -1;
+    if (p < v.n2) {
+        i = v.perm[p];
+        r = v.srank[p];
+        v.rank2[i] = r;
     }
+    if (*(volatile const int32_t*)&c->need_niche == 0) return;  // the same for every thread
+    const int l = c->l;
+    const int lane = lane_id();
+    const bool inT = i >= 0 && r >= 0 && r <= l;
     unsigned bal = __ballot_sync(0xffffffffu, inT);
     int base = 0;
     if (lane == 0 && bal) base = atomicAdd(&c->nT, __popc(bal));
@@ -38,11 +44,11 @@ __global__ void __launch_bounds__(NB) k_norm_ideal(RunView v)
     if (inT) v.Tlist[base + __popc(bal & ((1u << lane) - 1u))] = i;
     // the running ideal (history option) takes every merged point and the
     // previous ideal; a minimum over S u F_l otherwise
-    const bool inZ = v.norm_history ? (i < v.n2) : inT;
+    const bool inZ = v.norm_history ? (p < v.n2) : inT;
     if (v.norm_history && blockIdx.x == 0 && threadIdx.x == 0 && c->hvalid)
         for (int q = 0; q < v.m; ++q) atomicMin(&c->zmin[q], f2ord((float)c->hz[q]));
     for (int q = 0; q < v.m; ++q) {
-        uint32_t o = inZ ? f2ord(v.F[(size_t)i * v.m + q]) : 0xffffffffu;
+        uint32_t o = inZ ? f2ord(v.Fp[(size_t)p * v.m + q]) : 0xffffffffu;
 #pragma unroll
         for (int s = 16; s > 0; s >>= 1) o = min(o, __shfl_xor_sync(0xffffffffu, o, s));
         if (lane == 0 && o != 0xffffffffu) atomicMin(&c->zmin[q], o);

@@ -5,7 +5,7 @@
 // One launch per front, replayed by a CUDA-graph WHILE node; the last CTA
 // of a pass sets the node's condition, so the host never synchronises.
 // Positions are in bucket order of f_0 (k_sort.cu); ranks are written back
-// to the original order by k_post_peel.
+// to the original order by k_norm_ideal.
 //   cnt[j]    = dominators of j, counted by the dominance build
 //   pass k>0: cnt[j] -= popc(Dom[w][j] & front_{k-1}[w]) over the nonzero
 //             words w of the previous front's mask
@@ -312,12 +312,6 @@ __global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v
     }
 }
 
-// ranks back to the original order
-__global__ void k_post_peel(RunView v)
-{
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < v.n2) v.rank2[v.perm[p]] = v.srank[p];
-}
 
 int g_peel_occ[2] = {0, 0};  // resident peel CTAs per SM (matrix, streaming), set at start-up
 
@@ -352,8 +346,3 @@ cudaError_t peel_init_attributes()
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_peel_occ[1], k_peel<true>, PEEL_THREADS, 0);
 }
 
-cudaError_t launch_post_peel(const RunView& v, cudaStream_t s)
-{
-    k_post_peel<<<(v.n2 + 255) / 256, 256, 0, s>>>(v);
-    return cudaGetLastError();
-}

@@ -25,8 +25,6 @@ cudaError_t launch_dominance(const RunView& v, cudaStream_t s);
 // every peel pass in one cooperative launch (grid barrier between passes)
 cudaError_t launch_peel(const RunView& v, int num_sms, cudaStream_t s);
 cudaError_t peel_init_attributes();
-// ranks back to original order
-cudaError_t launch_post_peel(const RunView& v, cudaStream_t s);
 cudaError_t launch_norm_ideal(const RunView& v, cudaStream_t s);
 cudaError_t launch_norm_extreme(const RunView& v, cudaStream_t s);
 cudaError_t launch_assoc_prep(const RunView& v, cudaStream_t s);
@@ -39,7 +37,6 @@ cudaError_t launch_bucket(const RunView& v, cudaStream_t s);
 cudaError_t launch_pick(const RunView& v, cudaStream_t s);
 cudaError_t launch_compact(const RunView& v, cudaStream_t s);
 cudaError_t launch_gather(const RunView& v, cudaStream_t s);
-cudaError_t launch_bump_gen(const RunView& v, cudaStream_t s);
 
 // one-time attribute setup (dynamic shared memory opt-in)
 cudaError_t kernels_init_attributes();
