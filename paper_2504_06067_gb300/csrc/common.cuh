@@ -142,7 +142,6 @@ struct RunView {
     const int32_t* blk_j;  // w          original reference index in block order
     int2* arun;            // n2         candidate run (start, count) per T slot; start -1 = slow
     int2* cand;            // cand_cap   (T slot, reference)
-    double* cdist;         // cand_cap   FP64 distance of each candidate
     int cand_cap;
     int32_t* slow;         // n2         T slots for the full FP64 scan
 };

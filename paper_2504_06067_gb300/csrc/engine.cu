@@ -442,7 +442,6 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     v.cand_cap = 4 * n2 + 64;
     AL(v.arun, n2);
     AL(v.cand, v.cand_cap);
-    AL(v.cdist, v.cand_cap);
     AL(v.slow, n2);
     float* bc;
     float2* br;
@@ -558,7 +557,6 @@ nsga3_status setup(nsga3_ctx* ctx)
         ctx->vs.nblk = v.nblk;
         ctx->vs.arun = v.arun;
         ctx->vs.cand = v.cand;
-        ctx->vs.cdist = v.cdist;
         ctx->vs.cand_cap = v.cand_cap;
         ctx->vs.slow = v.slow;
     }
@@ -871,7 +869,7 @@ nsga3_status nsga3_select(nsga3_ctx* ctx, const float* objs, int32_t* ranks, int
     } else {
         CK(cudaGraphLaunch(ctx->gx_select, s));
     }
-    ctx->host_launches += 19;
+    ctx->host_launches += 18;
     CK(cudaMemcpyAsync(ranks, ctx->vs.rank2, (size_t)ctx->n2 * sizeof(int32_t), cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(selected, ctx->vs.sel, (size_t)ctx->N * sizeof(int32_t), cudaMemcpyDefault, s));
     ctx->last_kind = 1;
@@ -910,7 +908,7 @@ nsga3_status nsga3_step(nsga3_ctx* ctx, void* stream)
     } else {
         CK(cudaGraphLaunch(ctx->gx_step, (cudaStream_t)stream));
     }
-    ctx->host_launches += 22;
+    ctx->host_launches += 21;
     ctx->last_kind = 2;
     return NSGA3_OK;
 }
@@ -956,7 +954,7 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
     for (int g = 0; g < generations % BATCH_GENS; ++g) CK(cudaGraphLaunch(ctx->gx_batch1, (cudaStream_t)stream));
     for (int r = 0; r < n; ++r) {
         ctxs[r]->last_kind = 3;
-        ctxs[r]->host_launches += 22LL * generations;
+        ctxs[r]->host_launches += 21LL * generations;
     }
     return NSGA3_OK;
 }
@@ -1081,11 +1079,11 @@ nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches)
 {
     if (!ctx || !launches) return fail(ctx, NSGA3_EINVAL, "null argument");
     CK(cudaDeviceSynchronize());
-    // reset, 3 sort, dominance, peel (every pass), 11 niching (the first
+    // reset, 3 sort, dominance, peel (every pass), 10 niching (the first
     // also writes the ranks back; the others return at once when no niching
     // is needed), compaction (+ finite check for a selection; + variation,
     // objective, gather, commit for a generation)
-    *launches = (ctx->last_kind == 1) ? 19 : 22;
+    *launches = (ctx->last_kind == 1) ? 18 : 21;
     return NSGA3_OK;
 }
 

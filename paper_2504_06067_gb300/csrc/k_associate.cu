@@ -28,9 +28,10 @@
 // one point: it bounds every block, scans the best-bounded block first, then
 // the blocks that survive the bound.
 //
-// FP64 work (GB300 runs FP64 at 1/64 of the FP32 rate) is kept converged:
-// the scan only writes (point, reference) candidate runs; a separate kernel
-// evaluates one candidate per thread, and a third takes each point's argmin.
+// FP64 work (GB300 runs FP64 at 1/64 of the FP32 rate) stays off the scan:
+// the scan only writes (point, reference) candidate runs; a second kernel
+// evaluates each point's candidates in FP64 (one thread per point) and takes
+// their argmin.
 // A point whose candidate list overflows is rescanned in FP64 over all
 // references by a whole CTA (k_assoc_slow), as is every point in debug mode.
 #include "kernels.cuh"
@@ -276,22 +277,6 @@ __global__ void __launch_bounds__(AB) k_assoc_scan(RunView v)
     }
 }
 
-// one FP64 distance per candidate (converged)
-template <int M>
-__global__ void __launch_bounds__(AB) k_assoc_recheck(RunView v)
-{
-    Ctrl* c = v.ctrl;
-    if (skip_niche(c)) return;
-    const int n = min(c->ncand, v.cand_cap);
-    for (int e = blockIdx.x * AB + threadIdx.x; e < n; e += gridDim.x * AB) {
-        const int2 pj = v.cand[e];
-        double fp[M];
-#pragma unroll
-        for (int q = 0; q < M; ++q) fp[q] = v.fprime[(size_t)pj.x * M + q];
-        v.cdist[e] = perp_dist(fp, v.fnorm[pj.x], v.Zd + (size_t)pj.y * M, v.nz[pj.y], M);
-    }
-}
-
 __device__ __forceinline__ void write_assoc(const RunView& v, Ctrl* c, int i, int j, double d)
 {
     v.pi[i] = j;
@@ -302,23 +287,32 @@ __device__ __forceinline__ void write_assoc(const RunView& v, Ctrl* c, int i, in
         atomicAdd(&v.rhop[j], 1);
 }
 
-// per point: lexicographic (d, j) minimum of its candidates
-__global__ void __launch_bounds__(AB) k_assoc_final(RunView v)
+// per point: FP64 distances of its candidates (usually one to three, so the
+// threads of a warp stay nearly converged on the FP64 pipe) and their
+// lexicographic (d, j) minimum
+constexpr int FB = 128;
+
+template <int M>
+__global__ void __launch_bounds__(FB) k_assoc_final(RunView v)
 {
     Ctrl* c = v.ctrl;
     if (skip_niche(c)) return;
-    const int pt = blockIdx.x * AB + threadIdx.x;
+    const int pt = blockIdx.x * FB + threadIdx.x;
     if (pt >= c->nT) return;
     const int2 run = v.arun[pt];
     if (run.x < 0) return;  // slow path
     double bd = 0.0;
     int bj = 0;
-    if (v.fnorm[pt] != 0.0) {
+    const double nf = v.fnorm[pt];
+    if (nf != 0.0) {
+        double fp[M];
+#pragma unroll
+        for (int q = 0; q < M; ++q) fp[q] = v.fprime[(size_t)pt * M + q];
         bd = CUDART_INF;
         bj = 0x7fffffff;
         for (int e = run.x; e < run.x + run.y; ++e) {
-            const double d = v.cdist[e];
             const int j = v.cand[e].y;
+            const double d = perp_dist(fp, nf, v.Zd + (size_t)j * M, v.nz[j], M);
             if (lex_less(d, j, bd, bj)) {
                 bd = d;
                 bj = j;
@@ -402,12 +396,7 @@ cudaError_t launch_m(const RunView& v, cudaStream_t s, int num_sms)
     k_assoc_scan<M><<<blocks, AB, sm, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    int rb = (v.cand_cap + AB - 1) / AB;
-    if (rb > num_sms * 8) rb = num_sms * 8;
-    k_assoc_recheck<M><<<rb, AB, 0, s>>>(v);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_assoc_final<<<(v.n2 + AB - 1) / AB, AB, 0, s>>>(v);
+    k_assoc_final<M><<<(v.n2 + FB - 1) / FB, FB, 0, s>>>(v);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_assoc_slow<M><<<num_sms, AB, 0, s>>>(v);

@@ -257,20 +257,36 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
     }
     __syncthreads();
     int mymax = 0;
-    for (int j = threadIdx.x; j < w; j += LB) {
-        const int rp = rhop_of(j);
-        if (rp > 0) {
-            const int lo = rho_of(j), hi = lo + rp;
-            if (lo < 0 || rp > v.n2) {  // counts out of range: an invariant failed upstream
+    {
+        // most references share a few level values (rho_j = 0 when S is
+        // empty): lanes with equal values add once per warp (match groups),
+        // so the shared-memory atomics do not serialise on one address
+        const int lane = lane_id();
+        for (int j0 = (threadIdx.x & ~31); j0 < w; j0 += LB) {
+            const int j = j0 + lane;
+            int rp = j < w ? rhop_of(j) : 0;
+            const int lo = j < w ? rho_of(j) : 0;
+            if (rp > 0 && (lo < 0 || rp > v.n2)) {  // counts out of range: an invariant failed upstream
                 set_status(c, DEV_EINTERNAL);
-                continue;
+                rp = 0;
             }
-            if (lo < LCAP) atomicAdd(&sh.lev[lo], 1);
-            if (hi < LCAP) atomicAdd(&sh.lev[hi], -1);
-            mymax = max(mymax, hi);
+            const int hi = lo + rp;
+            const bool add_lo = rp > 0 && lo < LCAP, add_hi = rp > 0 && hi < LCAP;
+            const unsigned m_lo = __ballot_sync(0xffffffffu, add_lo);
+            const unsigned m_hi = __ballot_sync(0xffffffffu, add_hi);
+            if (add_lo) {
+                const unsigned g = __match_any_sync(m_lo, lo);
+                if (lane == __ffs(g) - 1) atomicAdd(&sh.lev[lo], __popc(g));
+            }
+            if (add_hi) {
+                const unsigned g = __match_any_sync(m_hi, hi);
+                if (lane == __ffs(g) - 1) atomicAdd(&sh.lev[hi], -__popc(g));
+            }
+            if (rp > 0) mymax = max(mymax, hi);
         }
     }
-    atomicMax(&sh.maxhi, mymax);
+    mymax = __reduce_max_sync(0xffffffffu, mymax);
+    if ((threadIdx.x & 31) == 0) atomicMax(&sh.maxhi, mymax);
     __syncthreads();
     // n(L) = prefix sum of the difference array; count(L) = prefix sum of n(L)
     {
@@ -295,10 +311,15 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
             sh.lev[L] = loc[t] + off2;  // count(L)
         }
         __syncthreads();
-        for (int t = 0; t < PER; ++t) {
+        // count(L) is non-decreasing: the first L of this thread with
+        // count >= K, then one atomic per warp
+        int myL = LCAP;
+        for (int t = PER - 1; t >= 0; --t) {
             const int L = threadIdx.x * PER + t;
-            if (sh.lev[L] >= K) atomicMin(&sh.Lstar, L);
+            if (sh.lev[L] >= K) myL = L;
         }
+        myL = __reduce_min_sync(0xffffffffu, myL);
+        if ((threadIdx.x & 31) == 0 && myL < LCAP) atomicMin(&sh.Lstar, myL);
         __syncthreads();
     }
     int Lstar = sh.Lstar;
