@@ -164,10 +164,12 @@ static void orc_dd_rec(int m, int p, int q, int left, int *k, double *Z, int64_t
 int64_t orc_refdirs(int m, int p1, int p2, double tau, double *Z)
 {
     if (m < 2 || p1 < 1 || p2 < 0) return -1;
-    int k[64];
+    int *k = (int *)malloc((size_t)m * sizeof(int));
+    if (!k) return -1;
     int64_t row = 0;
     orc_dd_rec(m, p1, 0, p1, k, Z, &row, 0, tau);
     if (p2 > 0) orc_dd_rec(m, p2, 0, p2, k, Z, &row, 1, tau);
+    free(k);
     return row;
 }
 
@@ -253,10 +255,13 @@ int orc_nds(const float *F, int n2, int m, int N, int full_sort, int32_t *rank)
 /*   a_q = max_{i in T} ft_iq for every q, and 1 where that is 0.          */
 /* Outputs zstar[m], a[m], extremes[m]; *fallback = 1 if used.             */
 /* ---------------------------------------------------------------------- */
+/* element (i, j) of the row-major m x m system / extreme vectors */
+#define AQ(i, j) A[(size_t)(i) * m + (j)]
+#define EV(i, j) evec[(size_t)(i) * m + (j)]
+
 int orc_normalize(const float *F, const int32_t *rank, int n2, int m, int l,
                   double *zstar, double *a, int32_t *extremes, int32_t *fallback)
 {
-    if (m > 64) return ORC_EINVAL;
     for (int q = 0; q < m; ++q) zstar[q] = INFINITY;
     int any = 0;
     for (int i = 0; i < n2; ++i) {
@@ -291,28 +296,31 @@ int orc_normalize(const float *F, const int32_t *rank, int n2, int m, int l,
     }
 
     /* Gaussian elimination with partial pivoting on E b = 1 */
-    double A[64][64], rhs[64], b[64];
+    double *A = (double *)malloc((size_t)m * m * sizeof(double));
+    double *rhs = (double *)malloc((size_t)m * sizeof(double));
+    double *b = (double *)malloc((size_t)m * sizeof(double));
+    if (!A || !rhs || !b) { free(A); free(rhs); free(b); return ORC_ENOMEM; }
     for (int q = 0; q < m; ++q) {
         for (int r = 0; r < m; ++r)
-            A[q][r] = (double)F[(size_t)extremes[q] * m + r] - zstar[r];
+            AQ(q, r) = (double)F[(size_t)extremes[q] * m + r] - zstar[r];
         rhs[q] = 1.0;
     }
     int ok = 1;
     for (int c = 0; c < m && ok; ++c) {
         int p = c;
-        double best = fabs(A[c][c]);
+        double best = fabs(AQ(c, c));
         for (int r = c + 1; r < m; ++r)
-            if (fabs(A[r][c]) > best) { best = fabs(A[r][c]); p = r; }
+            if (fabs(AQ(r, c)) > best) { best = fabs(AQ(r, c)); p = r; }
         if (best == 0.0) { ok = 0; break; }
         if (p != c) {
-            for (int cc = 0; cc < m; ++cc) { double t = A[c][cc]; A[c][cc] = A[p][cc]; A[p][cc] = t; }
+            for (int cc = 0; cc < m; ++cc) { double t = AQ(c, cc); AQ(c, cc) = AQ(p, cc); AQ(p, cc) = t; }
             double t = rhs[c]; rhs[c] = rhs[p]; rhs[p] = t;
         }
         for (int r = c + 1; r < m; ++r) {
-            double factor = A[r][c] / A[c][c];
+            double factor = AQ(r, c) / AQ(c, c);
             for (int cc = c; cc < m; ++cc) {
-                double prod = factor * A[c][cc];
-                A[r][cc] = A[r][cc] - prod;
+                double prod = factor * AQ(c, cc);
+                AQ(r, cc) = AQ(r, cc) - prod;
             }
             double prod = factor * rhs[c];
             rhs[r] = rhs[r] - prod;
@@ -322,10 +330,10 @@ int orc_normalize(const float *F, const int32_t *rank, int n2, int m, int l,
         for (int r = m - 1; r >= 0; --r) {
             double s = rhs[r];
             for (int cc = r + 1; cc < m; ++cc) {
-                double prod = A[r][cc] * b[cc];
+                double prod = AQ(r, cc) * b[cc];
                 s = s - prod;
             }
-            b[r] = s / A[r][r];
+            b[r] = s / AQ(r, r);
         }
         for (int q = 0; q < m; ++q) {
             a[q] = 1.0 / b[q];
@@ -344,6 +352,7 @@ int orc_normalize(const float *F, const int32_t *rank, int n2, int m, int l,
             a[q] = (mx == 0.0) ? 1.0 : mx;
         }
     }
+    free(A); free(rhs); free(b);
     return ORC_OK;
 }
 
@@ -365,7 +374,6 @@ int orc_normalize_hist(const float *F, const int32_t *rank, int n2, int m, int l
                        double *hz, float *he, double *zstar, double *a, int32_t *extremes,
                        int32_t *fallback)
 {
-    if (m > 64) return ORC_EINVAL;
     for (int q = 0; q < m; ++q) zstar[q] = *hvalid ? hz[q] : INFINITY;
     int any = 0;
     for (int i = 0; i < n2; ++i) {
@@ -403,33 +411,37 @@ int orc_normalize_hist(const float *F, const int32_t *rank, int n2, int m, int l
         }
         extremes[q] = arg;
     }
-    float evec[64][64];
+    float *evec = (float *)malloc((size_t)m * m * sizeof(float));
+    if (!evec) return ORC_ENOMEM;
     for (int q = 0; q < m; ++q) {
         const float *f = extremes[q] < n2 ? F + (size_t)extremes[q] * m : he + (size_t)(extremes[q] - n2) * m;
-        for (int r = 0; r < m; ++r) evec[q][r] = f[r];
+        for (int r = 0; r < m; ++r) EV(q, r) = f[r];
     }
 
-    double A[64][64], rhs[64], b[64];
+    double *A = (double *)malloc((size_t)m * m * sizeof(double));
+    double *rhs = (double *)malloc((size_t)m * sizeof(double));
+    double *b = (double *)malloc((size_t)m * sizeof(double));
+    if (!A || !rhs || !b) { free(A); free(rhs); free(b); free(evec); return ORC_ENOMEM; }
     for (int q = 0; q < m; ++q) {
-        for (int r = 0; r < m; ++r) A[q][r] = (double)evec[q][r] - zstar[r];
+        for (int r = 0; r < m; ++r) AQ(q, r) = (double)EV(q, r) - zstar[r];
         rhs[q] = 1.0;
     }
     int ok = 1;
     for (int c = 0; c < m && ok; ++c) {
         int p = c;
-        double best = fabs(A[c][c]);
+        double best = fabs(AQ(c, c));
         for (int r = c + 1; r < m; ++r)
-            if (fabs(A[r][c]) > best) { best = fabs(A[r][c]); p = r; }
+            if (fabs(AQ(r, c)) > best) { best = fabs(AQ(r, c)); p = r; }
         if (best == 0.0) { ok = 0; break; }
         if (p != c) {
-            for (int cc = 0; cc < m; ++cc) { double t = A[c][cc]; A[c][cc] = A[p][cc]; A[p][cc] = t; }
+            for (int cc = 0; cc < m; ++cc) { double t = AQ(c, cc); AQ(c, cc) = AQ(p, cc); AQ(p, cc) = t; }
             double t = rhs[c]; rhs[c] = rhs[p]; rhs[p] = t;
         }
         for (int r = c + 1; r < m; ++r) {
-            double factor = A[r][c] / A[c][c];
+            double factor = AQ(r, c) / AQ(c, c);
             for (int cc = c; cc < m; ++cc) {
-                double prod = factor * A[c][cc];
-                A[r][cc] = A[r][cc] - prod;
+                double prod = factor * AQ(c, cc);
+                AQ(r, cc) = AQ(r, cc) - prod;
             }
             double prod = factor * rhs[c];
             rhs[r] = rhs[r] - prod;
@@ -439,10 +451,10 @@ int orc_normalize_hist(const float *F, const int32_t *rank, int n2, int m, int l
         for (int r = m - 1; r >= 0; --r) {
             double sum = rhs[r];
             for (int cc = r + 1; cc < m; ++cc) {
-                double prod = A[r][cc] * b[cc];
+                double prod = AQ(r, cc) * b[cc];
                 sum = sum - prod;
             }
-            b[r] = sum / A[r][r];
+            b[r] = sum / AQ(r, r);
         }
         for (int q = 0; q < m; ++q) {
             a[q] = 1.0 / b[q];
@@ -463,11 +475,15 @@ int orc_normalize_hist(const float *F, const int32_t *rank, int n2, int m, int l
     }
     for (int q = 0; q < m; ++q) {
         hz[q] = zstar[q];
-        for (int r = 0; r < m; ++r) he[(size_t)q * m + r] = evec[q][r];
+        for (int r = 0; r < m; ++r) he[(size_t)q * m + r] = EV(q, r);
     }
     *hvalid = 1;
+    free(A); free(rhs); free(b); free(evec);
     return ORC_OK;
 }
+
+#undef AQ
+#undef EV
 
 /* ---------------------------------------------------------------------- */
 /* Association (Alg. 2: perpendicular distances, pi = argmin, d = min;     */
@@ -483,7 +499,7 @@ void orc_associate(const float *F, const int32_t *rank, int n2, int m, int l,
                    int32_t *pi, double *dist)
 {
     double *nz = (double *)malloc((size_t)(w > 0 ? w : 1) * sizeof(double));
-    double fp[64];
+    double *fp = (double *)malloc((size_t)m * sizeof(double));
     for (int j = 0; j < w; ++j) {
         double s = 0.0;
         for (int q = 0; q < m; ++q) {
@@ -529,6 +545,7 @@ void orc_associate(const float *F, const int32_t *rank, int n2, int m, int l,
         dist[i] = best;
     }
     free(nz);
+    free(fp);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -751,13 +768,16 @@ int orc_select_hist(const float *F, int N, int m, const double *Z, int w, uint64
         for (int i = 0; i < n2; ++i) if (rank[i] == l) picked[i] = 1;
     } else {
         niche = 1;
-        double zstar[64], a[64];
-        int32_t ext[64];
+        double *zstar = (double *)malloc((size_t)m * sizeof(double));
+        double *a = (double *)malloc((size_t)m * sizeof(double));
+        int32_t *ext = (int32_t *)malloc((size_t)m * sizeof(int32_t));
+        if (!zstar || !a || !ext) return ORC_ENOMEM;
         if (hvalid)
             orc_normalize_hist(F, rank, n2, m, l, hvalid, hz, he, zstar, a, ext, &fb);
         else
             orc_normalize(F, rank, n2, m, l, zstar, a, ext, &fb);
         orc_associate(F, rank, n2, m, l, zstar, a, Z, w, pi, dist);
+        free(zstar); free(a); free(ext);
         int rc = variant == 0
                      ? orc_niche_sequential(rank, n2, l, K, pi, dist, w, seed, gen, picked)
                      : orc_niche_batched(rank, n2, l, K, pi, dist, w, seed, gen, picked);
@@ -859,7 +879,8 @@ void orc_vary(const float *X, const int32_t *rank, int N, int d, uint64_t seed, 
 void orc_eval(const float *X, int n, int d, int m, const float *W, float *F)
 {
     int k = m - 1;
-    double e[64];
+    double *e = (double *)malloc((size_t)m * sizeof(double));
+    if (!e) return;
     for (int i = 0; i < n; ++i) {
         const float *x = X + (size_t)i * d;
         double g = 0.0;
@@ -883,6 +904,7 @@ void orc_eval(const float *X, int n, int d, int m, const float *W, float *F)
             F[(size_t)i * m + j] = (float)((1.0 + g) * sj);
         }
     }
+    free(e);
 }
 
 /* x_iv = uniform(Philox(i*d + v, 0, 6, 0) word 0). */
@@ -974,9 +996,10 @@ void orc_kp_order(const int32_t *p, const int32_t *w, int m, int d, int32_t *ord
 void orc_kp_eval(float *X, int n, int d, int m, const int32_t *p, const int32_t *w,
                  const int32_t *cap, const int32_t *order, float *F)
 {
+    int64_t *load = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+    if (!load) return;
     for (int i = 0; i < n; ++i) {
         float *x = X + (size_t)i * d;
-        int64_t load[64];
         for (int j = 0; j < m; ++j) {
             load[j] = 0;
             for (int v = 0; v < d; ++v)
@@ -1000,6 +1023,7 @@ void orc_kp_eval(float *X, int n, int d, int m, const int32_t *p, const int32_t 
             F[(size_t)i * m + j] = (float)left;
         }
     }
+    free(load);
 }
 
 /* Initial bits: Philox(i*d + v, 0, 6, 0) word 0 < 0.5 -> item v chosen.   */

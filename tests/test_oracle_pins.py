@@ -225,6 +225,31 @@ def test_normalize_singular_fallback(orc):
     assert np.array_equal(a, np.array([7.0, 1.0, 7.0]))
 
 
+def _corner_points(n2, m, seed):
+    """Points near the unit simplex and one near each vertex (distinct
+    extremes, a regular intercept system)."""
+    rng = np.random.default_rng([seed, n2, m, 99])
+    F = rng.dirichlet(np.ones(m), size=n2) * (1.0 + rng.exponential(0.05, size=(n2, 1)))
+    C = 0.02 * rng.random((m, m)) / m
+    C[np.arange(m), np.arange(m)] = 0.9 + 0.05 * rng.random(m)
+    F[rng.permutation(n2)[:m]] = C
+    return F.astype(np.float32)
+
+
+@pytest.mark.parametrize("m", [64, 200, 512])
+def test_normalize_many_objectives_matches_lapack(orc, m):
+    """Up to the m = 512 of Table II: the intercepts from the elimination
+    equal 1 / (LAPACK's solution of (E - z*) b = 1) to rounding, the ideal is
+    the column minimum and the m extremes are distinct."""
+    F = _corner_points(2 * m + 100, m, 1)
+    rank = np.zeros(len(F), dtype=np.int32)
+    zstar, a, ext, fb = orc.normalize(F, rank, 0)
+    assert not fb and len(set(ext.tolist())) == m
+    assert np.array_equal(zstar, F.min(0).astype(np.float64))
+    b = np.linalg.solve(F[ext].astype(np.float64) - zstar, np.ones(m))
+    np.testing.assert_allclose(a, 1.0 / b, rtol=1e-12, atol=0)
+
+
 # ------------------------------------------- normalization with history --
 def test_normalize_hist_first_call_equals_stateless(orc):
     """Without history the running ideal over all 2N points equals the ideal
@@ -326,6 +351,36 @@ def test_associate_matches_vector_rejection(orc):
             assert pi[i] == j
         assert abs(dist[i] - rej[pi[i]]) < 1e-9 * max(1.0, np.linalg.norm(fp))
     assert np.all(pi[rank < 0] == -1)
+
+
+def test_associate_many_objectives_vector_rejection(orc):
+    """m = 100: the association equals the nearest direction by the length
+    of the rejection of f' (computed with numpy)."""
+    m = 100
+    Z = orc.refdirs(m, 1, 1, 0.5)
+    F = _corner_points(300, m, 2)
+    rank = np.zeros(300, dtype=np.int32)
+    zstar, a, _, _ = orc.normalize(F, rank, 0)
+    pi, dist = orc.associate(F, rank, 0, zstar, a, Z)
+    Zh = Z / np.linalg.norm(Z, axis=1, keepdims=True)
+    fp = (F.astype(np.float64) - zstar) / a
+    proj = fp @ Zh.T
+    rej = np.sqrt(np.maximum(0.0, np.sum(fp * fp, 1)[:, None] - proj * proj))
+    for i in range(len(F)):
+        srt = np.sort(rej[i])
+        if srt[1] - srt[0] > 1e-9:
+            assert pi[i] == int(np.argmin(rej[i]))
+        assert abs(dist[i] - rej[i, pi[i]]) < 1e-9 * max(1.0, np.linalg.norm(fp[i]))
+
+
+def test_nds_many_objectives_invariants(orc):
+    """m = 300: fronts are antichains and every member of a later front is
+    dominated by some member of the front before."""
+    N = 40
+    for kind in ("early", "chain"):
+        F = wl.objectives(kind, 2 * N, 300, seed=5)
+        rank, l = orc.nds(F, N, full_sort=True)
+        _front_invariants(orc, F, rank, N, True)
 
 
 def test_associate_2d_angle(orc):
