@@ -50,7 +50,8 @@ def parse_args(argv=None):
                    help="timed generations (default: the workload's run length)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served"], default="scale")
+    p.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep"],
+                   default="scale")
     p.add_argument("--runs", type=int, default=64, help="batched: independent runs")
     p.add_argument("--requests", type=int, default=None, help="served: requests of the stream")
     p.add_argument("--cpu-budget", type=float, default=20.0,
@@ -639,6 +640,113 @@ def run_served(args, world, rank, local):
     return line
 
 
+# ------------------------------------------------------ objective sweep ----
+# TensorNSGA-III's seconds per generation in the paper's Table II (DTLZ3,
+# N = 800, d = 1000, 100 generations, on the paper's GPU): context only.
+PAPER_TABLE2_S = {4: 4.334e-3, 8: 4.624e-3, 16: 5.083e-3, 32: 6.514e-3, 64: 8.103e-3,
+                  128: 1.016e-2, 256: 2.348e-2, 512: 3.199e-2}
+
+
+def run_sweep(args, world, rank, local):
+    """Generations per second over m = 4 ... 512 at N = 800, d = 1000 (the
+    shape of Table II); each m is its own run: warm-up, then K timed
+    generations from generation 0, L2 flushed before each."""
+    import torch
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    from paper_2504_06067_gb300 import native as n
+
+    K = args.steps
+    sh = torch.cuda.current_stream().cuda_stream
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    phases = (C.c_float * 7)()
+    launches = C.c_int32()
+    names = ["variation", "reset", "dominance", "peel", "niching", "gather", "total"]
+    rows = []
+    n_launch = 0
+    sampler = ClockSampler(local)
+    sampler.start()
+    for cfg in wl.objective_sweep():
+        progress("sweep m=%d" % cfg.m)
+        W = wl.objective_weights(cfg.m, cfg.seed)
+        ctx = n.create(cfg.m, cfg.d, cfg.N, cfg.p1,
+                       n.default_opts(seed=cfg.seed + rank, W=W.ctypes.data))
+
+        def ok(st):
+            return n.check(st, ctx)
+
+        ok(n.nsga3_init(ctx, sh))
+        for _ in range(args.warmup):
+            ok(n.nsga3_step(ctx, sh))
+        ok(n.nsga3_init(ctx, sh))
+        ok(n.nsga3_sync(ctx, sh))
+        barrier(dist)
+        ms, ph = [], [0.0] * 7
+        for k in range(K):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ok(n.nsga3_step(ctx, sh))
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            ok(n.nsga3_phase_times(ctx, phases, 7))
+            ok(n.nsga3_last_launches(ctx, C.byref(launches)))
+            n_launch += launches.value
+            for t in range(7):
+                ph[t] += phases[t]
+        st = n.nsga3_sync(ctx, sh)
+        n.nsga3_destroy(ctx)
+        if st != n.OK:
+            raise RuntimeError("device status %d (m = %d)" % (st, cfg.m))
+        s_max = reduce_max(dist, sum(ms) / 1e3, "cuda")
+        rows.append({"m": cfg.m, "refs": cfg.w, "ms_per_gen": s_max * 1e3 / K,
+                     "gens_per_s": world * K / s_max,
+                     "phase_ms": {nm: round(ph[i] / K, 5) for i, nm in enumerate(names)},
+                     "paper_table2_ms": PAPER_TABLE2_S[cfg.m] * 1e3})
+    clocks = sampler.stop()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+    top = rows[-1]
+    line = {
+        "metric": "gens/s over the objective sweep (Table II shape: N 800, d 1000, m 4..512)",
+        "value": top["gens_per_s"],
+        "unit": "gens/s at m = %d" % top["m"],
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": top["ms_per_gen"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded softmax-simplex objective, W ~ N(0,1); stands in for DTLZ3)",
+        "config": {"workload": "sweep_N800_d1000_m4-512", "l2": "flushed (256 MB write) before every timed step",
+                   "generations": "timed %d from generation 0 per m" % K,
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "sweep": rows,
+        "roofline": None,
+        "e2e": None,
+        "gpu_launches": n_launch,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        cfg = wl.objective_sweep()[-1]
+        spg, nst = oracle_generations(cfg, args.cpu_budget)
+        line["cpu_baseline"] = {"value": 1.0 / spg, "unit": "gens/s at m = %d" % cfg.m, "cores": 1,
+                                "kind": "oracle",
+                                "sample": "%d generation(s) of %s (FP64 C oracle, single thread)"
+                                          % (nst, cfg.name)}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return line
+
+
 # ----------------------------------------------------------------- oracle ----
 def oracle_generations(cfg, budget_s, max_steps=None, warmup=0):
     """Times oracle generations of `cfg` from a seeded initial population until
@@ -698,7 +806,7 @@ def run_reference(args, world, rank):
     """The oracle as the reference arm, on this workload's metric."""
     if rank != 0:
         return None
-    cfg = WORKLOADS[args.workload]
+    cfg = wl.objective_sweep()[-1] if args.workload == "sweep" else WORKLOADS[args.workload]
     budget = 150.0
     spg, nsteps = oracle_generations(cfg, budget, max_steps=args.steps, warmup=min(args.warmup, 1))
     value = cfg.N / spg
@@ -741,7 +849,7 @@ def main(argv=None):
     args = parse_args(argv)
     world, rank, local = dist_env()
     if args.steps is None:
-        args.steps = {"batched": 300, "served": 0}.get(args.workload)
+        args.steps = {"batched": 300, "served": 0, "sweep": 50}.get(args.workload)
         if args.steps is None:
             args.steps = WORKLOADS[args.workload].generations
     if args.impl == "reference":
@@ -750,6 +858,8 @@ def main(argv=None):
         run_batched(args, world, rank, local)
     elif args.workload == "served":
         run_served(args, world, rank, local)
+    elif args.workload == "sweep":
+        run_sweep(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

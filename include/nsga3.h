@@ -62,7 +62,7 @@ typedef struct {
                                only serves nsga3_select / nsga3_set_population */
     int streaming;          /* 1: no dominance matrix; the peel recomputes the dominance
                                of each front's members on the fly (device memory O(N)
-                               instead of (2N)^2 / 8 bytes; same results) */
+                               instead of (2N)^2 / 8 bytes; same results); m <= 10 */
     int norm_history;       /* 1: normalization keeps a running ideal point (minimum over
                                every merged population so far) and remembers the extreme
                                points, which stay candidates in later generations; the
@@ -71,7 +71,8 @@ typedef struct {
                                (ideal and extremes of the current S u F_l only) */
     int problem;            /* 0: softmax-simplex objective (needs W); 1: 0-1 multi-objective
                                knapsack over d items (needs the kp_* arrays): binary
-                               variables, uniform crossover, bit-flip mutation, repair */
+                               variables, uniform crossover, bit-flip mutation, repair;
+                               m <= 10 */
     const int32_t* kp_profit;   /* host, m x d profits (> 0), read during create only */
     const int32_t* kp_weight;   /* host, m x d weights (> 0), read during create only */
     const int32_t* kp_capacity; /* host, m capacities, read during create only */
@@ -82,7 +83,10 @@ void nsga3_default_opts(nsga3_opts* o);
 
 /*
  * Creates a context for populations of N individuals (merged 2N), m
- * objectives (2 <= m <= 10), d variables (d >= m - 1 when W is given) and
+ * objectives (2 <= m <= 512; the objective sweep of the paper's Table II
+ * reaches 512; kernels are specialised for each m <= 10 and take m at run
+ * time above; with m > 32 the intercept system is eliminated by a
+ * cooperative grid), d variables (d >= m - 1 when W is given) and
  * Das-Dennis divisions ref_divisions >= 1 (Sec. II-C: w points uniform on
  * the unit simplex; opts->p2 > 0 adds an inner layer).  N must be even,
  * 2 <= N and 2N <= 2^21.  Allocates all device workspace (about

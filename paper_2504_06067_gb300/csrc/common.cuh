@@ -15,7 +15,9 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
-#define NSGA3_MAX_M 10
+#define NSGA3_MAX_M 512         // objectives accepted by a context
+#define NSGA3_FAST_M 10         // largest m with kernels specialised for each m
+#define NSGA3_WARP_M 32         // largest m whose intercept system one warp solves
 #define NSGA3_TILE 256          // column tile of the dominance build; ld % 256 == 0
 #define NSGA3_PEEL_COLS 128     // columns per peel chunk (4 per lane, 32 lanes)
 #define SORT_NB 4096            // f_0 buckets of the bucket order
@@ -75,7 +77,6 @@ struct Ctrl {
     // normalization history (opts.norm_history), kept across selections
     int32_t hvalid;                      // 1 once a normalization has been recorded
     double hz[NSGA3_MAX_M];              // running ideal point
-    float he[NSGA3_MAX_M * NSGA3_MAX_M]; // remembered extreme vectors, row q for axis q
 };
 
 // Device pointers and sizes of one run, passed by value to every kernel.
@@ -144,6 +145,14 @@ struct RunView {
     int2* cand;            // cand_cap   (T slot, reference)
     int cand_cap;
     int32_t* slow;         // n2         T slots for the full FP64 scan
+    float* he;             // m x m      remembered extreme vectors (history), row q for axis q
+    // m > NSGA3_FAST_M: extreme points by entry keys, then per-axis blocks
+    unsigned long long* ekey;  // (n2 + m) x 2  ASF keys of the largest / second-largest f~
+    int32_t* er1;              // n2 + m        objective of the largest f~
+    // m > NSGA3_WARP_M: intercepts by the cooperative elimination
+    double* amat;          // m x (m + 1)  [E - z* | 1], rows in original order
+    float* etmp;           // m x m        new extreme vectors (copied to he at the end)
+    double* nadv;          // m            max f~ per axis (nadir fallback)
 };
 
 // ------------------------------------------------------------ Philox ------
@@ -227,4 +236,57 @@ __device__ __forceinline__ bool skip_niche(const Ctrl* c)
 __device__ __forceinline__ bool lex_less(double a, int ia, double b, int ib)
 {
     return a < b || (a == b && ia < ib);
+}
+
+// ------------------------------------------------------ grid barrier ------
+// Barrier of a cooperative launch (every CTA resident), with a bounded
+// wait: returns false and records DEV_ETIMEOUT when the other CTAs did not
+// arrive within GRID_WAIT_NS of device time.  Uses c->bar_count (arrivals,
+// back to 0 after each barrier) and c->bar_gen (generation).
+constexpr unsigned long long GRID_WAIT_NS = 20ull * 1000 * 1000 * 1000;
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned x;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(x) : "l"(p) : "memory");
+    return x;
+}
+
+__device__ __forceinline__ bool grid_sync(Ctrl* c, int* s_ok)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = ld_acquire(&c->bar_gen);
+        __threadfence();
+        if (atomicAdd(&c->bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(&c->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&c->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            unsigned it = 0;
+            while (ld_acquire(&c->bar_gen) == g) {
+                // the clock is read every 256 polls; the poll count caps the
+                // wait too, should the timer not advance
+                if ((++it & 255u) == 0u && (global_ns() - t0 > GRID_WAIT_NS || it > (1u << 30))) {
+                    set_status(c, DEV_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
 }

@@ -64,6 +64,11 @@ struct nsga3_ctx {
 
 namespace {
 
+// kernels of one selection / one generation: m > 10 adds the extreme-point
+// key kernel, m > 32 also the cooperative elimination
+int select_launches(int m) { return 18 + (m > NSGA3_FAST_M ? 1 : 0) + (m > NSGA3_WARP_M ? 1 : 0); }
+int generation_launches(int m) { return select_launches(m) + 3; }
+
 nsga3_status fail(nsga3_ctx* c, nsga3_status s, const char* fmt, ...)
 {
     char buf[512];
@@ -155,7 +160,7 @@ nsga3_status record_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s,
     // ideal point; the niching kernels return at once when no niching is
     // needed: a graph IF node costs more than their empty launches
     CK(launch_norm_ideal(v, s));
-    CK(launch_norm_extreme(v, s));
+    CK(launch_norm_extreme(v, ctx->num_sms, s));
     CK(launch_assoc_prep(v, s));
     CK(launch_assoc_scan(v, ctx->num_sms, s));
     CK(launch_level(v, s));
@@ -202,7 +207,7 @@ nsga3_status eager_selection(nsga3_ctx* ctx, const RunView& v, cudaStream_t s, b
     CK(cudaMemcpyAsync(&hdr[1], &v.ctrl->need_niche, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (hdr[0] == 0 && hdr[1]) {
-        CK(launch_norm_extreme(v, s));
+        CK(launch_norm_extreme(v, ctx->num_sms, s));
         CK(launch_assoc_prep(v, s));
         CK(launch_assoc_scan(v, ctx->num_sms, s));
         CK(launch_level(v, s));
@@ -443,6 +448,16 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     AL(v.arun, n2);
     AL(v.cand, v.cand_cap);
     AL(v.slow, n2);
+    AL(v.he, (size_t)m * m);
+    if (m > NSGA3_FAST_M) {
+        AL(v.ekey, 2 * (size_t)(n2 + m));
+        AL(v.er1, (size_t)(n2 + m));
+    }
+    if (m > NSGA3_WARP_M) {
+        AL(v.amat, (size_t)m * (m + 1));
+        AL(v.etmp, (size_t)m * m);
+        AL(v.nadv, m);
+    }
     float* bc;
     float2* br;
     float* bz;
@@ -581,6 +596,7 @@ nsga3_status init_attributes(nsga3_ctx* ctx)
     CK(niche_init_attributes());
     CK(peel_init_attributes());
     CK(assoc_init_attributes());
+    CK(norm_init_attributes());
     g_attr_done = true;
     return NSGA3_OK;
 }
@@ -613,6 +629,10 @@ nsga3_status ctx_fields(nsga3_ctx* ctx, int m, int d, int N, int ref_divisions, 
     if (ref_divisions < 1 || o.p2 < 0) return fail(ctx, NSGA3_EINVAL, "bad reference divisions");
     if (!(o.tau >= 0.0 && o.tau <= 1.0)) return fail(ctx, NSGA3_EINVAL, "tau outside [0,1]");
     if (o.problem != 0 && o.problem != 1) return fail(ctx, NSGA3_EINVAL, "problem %d unknown", o.problem);
+    if (o.streaming && m > NSGA3_FAST_M)
+        return fail(ctx, NSGA3_EINVAL, "streaming dominance supports m <= %d", NSGA3_FAST_M);
+    if (o.problem == 1 && m > NSGA3_FAST_M)
+        return fail(ctx, NSGA3_EINVAL, "the knapsack workload supports m <= %d", NSGA3_FAST_M);
     if (o.problem == 1 && o.kp_profit && o.kp_weight && o.kp_capacity) {
         // integer sums stay exact: weights below 2^31, objectives (profit
         // totals) below 2^24 so that FP32 holds them exactly
@@ -869,7 +889,7 @@ nsga3_status nsga3_select(nsga3_ctx* ctx, const float* objs, int32_t* ranks, int
     } else {
         CK(cudaGraphLaunch(ctx->gx_select, s));
     }
-    ctx->host_launches += 18;
+    ctx->host_launches += select_launches(ctx->m);
     CK(cudaMemcpyAsync(ranks, ctx->vs.rank2, (size_t)ctx->n2 * sizeof(int32_t), cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(selected, ctx->vs.sel, (size_t)ctx->N * sizeof(int32_t), cudaMemcpyDefault, s));
     ctx->last_kind = 1;
@@ -908,7 +928,7 @@ nsga3_status nsga3_step(nsga3_ctx* ctx, void* stream)
     } else {
         CK(cudaGraphLaunch(ctx->gx_step, (cudaStream_t)stream));
     }
-    ctx->host_launches += 21;
+    ctx->host_launches += generation_launches(ctx->m);
     ctx->last_kind = 2;
     return NSGA3_OK;
 }
@@ -954,7 +974,7 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
     for (int g = 0; g < generations % BATCH_GENS; ++g) CK(cudaGraphLaunch(ctx->gx_batch1, (cudaStream_t)stream));
     for (int r = 0; r < n; ++r) {
         ctxs[r]->last_kind = 3;
-        ctxs[r]->host_launches += 21LL * generations;
+        ctxs[r]->host_launches += (long long)generation_launches(ctxs[r]->m) * generations;
     }
     return NSGA3_OK;
 }
@@ -1081,9 +1101,10 @@ nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches)
     CK(cudaDeviceSynchronize());
     // reset, 3 sort, dominance, peel (every pass), 10 niching (the first
     // also writes the ranks back; the others return at once when no niching
-    // is needed), compaction (+ finite check for a selection; + variation,
-    // objective, gather, commit for a generation)
-    *launches = (ctx->last_kind == 1) ? 18 : 21;
+    // is needed; one or two more for m > 10), compaction (+ finite check
+    // for a selection; + variation, objective, gather, commit for a
+    // generation)
+    *launches = (ctx->last_kind == 1) ? select_launches(ctx->m) : generation_launches(ctx->m);
     return NSGA3_OK;
 }
 

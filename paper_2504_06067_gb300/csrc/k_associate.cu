@@ -34,6 +34,8 @@
 // their argmin.
 // A point whose candidate list overflows is rescanned in FP64 over all
 // references by a whole CTA (k_assoc_slow), as is every point in debug mode.
+// m > 10: no pruning; the cosines come from shared-memory tiles of points
+// and references (k_assoc_scan_gen), with the same band and FP64 kernels.
 #include "kernels.cuh"
 
 namespace {
@@ -329,6 +331,7 @@ __global__ void __launch_bounds__(FB) k_assoc_final(RunView v)
 }
 
 // full FP64 scan of one point per CTA (overflowed lists, debug mode)
+// M = 0: runtime m (f' read from memory)
 template <int M>
 __global__ void __launch_bounds__(AB) k_assoc_slow(RunView v)
 {
@@ -337,17 +340,19 @@ __global__ void __launch_bounds__(AB) k_assoc_slow(RunView v)
     Ctrl* c = v.ctrl;
     if (skip_niche(c)) return;
     const int ns = c->nslow;
+    const int m = M > 0 ? M : v.m;
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     for (int t = blockIdx.x; t < ns; t += gridDim.x) {
         const int pt = v.slow[t];
-        double fp[M];
+        double fr[M > 0 ? M : 1];
 #pragma unroll
-        for (int q = 0; q < M; ++q) fp[q] = v.fprime[(size_t)pt * M + q];
+        for (int q = 0; q < M; ++q) fr[q] = v.fprime[(size_t)pt * M + q];
+        const double* fp = M > 0 ? fr : v.fprime + (size_t)pt * m;
         const double nf = v.fnorm[pt];
         double d0 = CUDART_INF;
         int j0 = 0x7fffffff;
         for (int j = threadIdx.x; j < v.w; j += AB) {
-            const double d = perp_dist(fp, nf, v.Zd + (size_t)j * M, v.nz[j], M);
+            const double d = perp_dist(fp, nf, v.Zd + (size_t)j * m, v.nz[j], m);
             if (lex_less(d, j, d0, j0)) {
                 d0 = d;
                 j0 = j;
@@ -383,6 +388,220 @@ __global__ void __launch_bounds__(AB) k_assoc_slow(RunView v)
         }
         __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------------------
+// m > NSGA3_FAST_M: runtime m, no pruning (the cone bounds lose their grip in
+// many dimensions).  The FP32 cosines of GPTS points against every
+// reference are formed from shared-memory tiles (32 references x GKC
+// objectives, the points' unit vectors likewise) and fed to the same
+// candidate band; the FP64 kernels read f' from memory.
+
+__global__ void __launch_bounds__(PB) k_assoc_prep_gen(RunView v)
+{
+    Ctrl* c = v.ctrl;
+    if (skip_niche(c)) return;
+    const int s = blockIdx.x * PB + threadIdx.x;
+    if (s >= c->nT) return;
+    const int m = v.m, M4 = v.M4;
+    const int i = v.Tlist[s];
+    double* fp = v.fprime + (size_t)s * m;
+    double ss = 0.0;
+    for (int q = 0; q < m; ++q) {
+        const double ft = __dsub_rn((double)v.F[(size_t)i * m + q], c->zstar[q]);
+        const double x = __ddiv_rn(ft, c->a[q]);
+        fp[q] = x;
+        ss = __dadd_rn(ss, __dmul_rn(x, x));
+    }
+    const double nf = __dsqrt_rn(ss);
+    v.fnorm[s] = nf;
+    const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
+    for (int q = 0; q < M4; ++q) v.uhat[(size_t)s * M4 + q] = q < m ? __double2float_rn(fp[q] * inv) : 0.0f;
+}
+
+// candidate-list update of one point with a block of 32 cosines (qh, j) per
+// lane (j = -1: no reference): keeps every reference within band of the best
+// so far; a list that cannot hold them marks the point as overflowed
+__device__ __forceinline__ void band_take(float qh, int j, float band, float& best, int& nl, bool& ovf,
+                                          int* lj, float* lq)
+{
+    const int lane = lane_id();
+    const float wm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(qh, 0.0f))));
+    best = fmaxf(best, wm);
+    const bool keep = j >= 0 && qh >= best - band;
+    unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (nl + __popc(bal) > LC) {  // drop entries that fell out of the band
+        __syncwarp();
+        int kept = 0;
+        for (int e0 = 0; e0 < nl; e0 += 32) {
+            const int e = e0 + lane;
+            const bool k2 = e < nl && lq[e] >= best - band;
+            const unsigned b2 = __ballot_sync(0xffffffffu, k2);
+            int jj = 0;
+            float qq = 0.0f;
+            if (k2) {
+                jj = lj[e];
+                qq = lq[e];
+            }
+            __syncwarp();
+            if (k2) {
+                const int p = kept + __popc(b2 & ((1u << lane) - 1u));
+                lj[p] = jj;
+                lq[p] = qq;
+            }
+            kept += __popc(b2);
+            __syncwarp();
+        }
+        nl = kept;
+        if (nl + __popc(bal) > LC) {
+            ovf = true;
+            bal = 0u;
+        }
+    }
+    if (keep && bal) {
+        const int p = nl + __popc(bal & ((1u << lane) - 1u));
+        lj[p] = j;
+        lq[p] = qh;
+    }
+    nl += __popc(bal);
+    __syncwarp();
+}
+
+constexpr int GPW = 2;           // points per warp
+constexpr int GPTS = 8 * GPW;    // points per CTA
+constexpr int GKC = 64;          // objectives per staged chunk
+
+__global__ void __launch_bounds__(AB) k_assoc_scan_gen(RunView v)
+{
+    __shared__ float Us[GPTS][GKC + 1];
+    __shared__ float Zs[32][GKC + 1];
+    __shared__ int s_lj[8][GPW][LC];
+    __shared__ float s_lq[8][GPW][LC];
+    Ctrl* c = v.ctrl;
+    if (skip_niche(c)) return;
+    const int nT = c->nT, m = v.m, M4 = v.M4, w = v.w;
+    const int lane = lane_id(), warp = threadIdx.x >> 5, tid = threadIdx.x;
+    const float band = 2.0f * (float)(m + 4) * 5.9604644775390625e-08f + 1e-12f;
+    const bool one_chunk = m <= GKC;
+    for (int g0 = blockIdx.x * GPTS; g0 < nT; g0 += gridDim.x * GPTS) {  // CTA-uniform
+        float best[GPW];
+        int nl[GPW];
+        bool ovf[GPW], live[GPW];
+#pragma unroll
+        for (int p = 0; p < GPW; ++p) {
+            const int pt = g0 + warp * GPW + p;
+            best[p] = -4.0f;
+            nl[p] = 0;
+            ovf[p] = false;
+            live[p] = pt < nT && v.fnorm[pt] != 0.0;  // |f'| = 0: every distance is 0
+        }
+        if (one_chunk) {
+            __syncthreads();
+            for (int e = tid; e < GPTS * GKC; e += AB) {
+                const int p = e / GKC, k = e - p * GKC;
+                Us[p][k] = (g0 + p < nT && k < m) ? v.uhat[(size_t)(g0 + p) * M4 + k] : 0.0f;
+            }
+        }
+        for (int r0 = 0; r0 < w; r0 += 32) {
+            float acc[GPW];
+#pragma unroll
+            for (int p = 0; p < GPW; ++p) acc[p] = 0.0f;
+            for (int k0 = 0; k0 < m; k0 += GKC) {
+                __syncthreads();  // the previous tiles are consumed
+                if (!one_chunk)
+                    for (int e = tid; e < GPTS * GKC; e += AB) {
+                        const int p = e / GKC, k = e - p * GKC;
+                        Us[p][k] = (g0 + p < nT && k0 + k < m) ? v.uhat[(size_t)(g0 + p) * M4 + k0 + k] : 0.0f;
+                    }
+                for (int e = tid; e < 32 * GKC; e += AB) {
+                    const int jj = e / GKC, k = e - jj * GKC;
+                    Zs[jj][k] = (r0 + jj < w && k0 + k < m) ? v.Zh[(size_t)(r0 + jj) * M4 + k0 + k] : 0.0f;
+                }
+                __syncthreads();
+                const int kn = min(GKC, m - k0);
+                for (int k = 0; k < kn; ++k) {
+                    const float z = Zs[lane][k];
+#pragma unroll
+                    for (int p = 0; p < GPW; ++p) acc[p] = fmaf(Us[warp * GPW + p][k], z, acc[p]);
+                }
+            }
+            const int j = r0 + lane < w ? r0 + lane : -1;
+#pragma unroll
+            for (int p = 0; p < GPW; ++p)
+                if (live[p]) band_take(acc[p], j, band, best[p], nl[p], ovf[p], s_lj[warp][p], s_lq[warp][p]);
+        }
+#pragma unroll
+        for (int p = 0; p < GPW; ++p) {
+            const int pt = g0 + warp * GPW + p;
+            if (pt >= nT) continue;
+            if (!live[p]) {
+                if (lane == 0) v.arun[pt] = make_int2(0, 0);
+                continue;
+            }
+            const int* lj = s_lj[warp][p];
+            const float* lq = s_lq[warp][p];
+            int cnt = 0;
+            for (int e0 = 0; e0 < nl[p]; e0 += 32) {
+                const int e = e0 + lane;
+                cnt += __popc(__ballot_sync(0xffffffffu, e < nl[p] && lq[e] >= best[p] - band));
+            }
+            int start = 0;
+            if (lane == 0 && !ovf[p]) start = atomicAdd(&c->ncand, cnt);
+            start = __shfl_sync(0xffffffffu, start, 0);
+            if (ovf[p] || start + cnt > v.cand_cap) {
+                if (lane == 0) {
+                    v.arun[pt] = make_int2(-1, 0);
+                    v.slow[atomicAdd(&c->nslow, 1)] = pt;
+                }
+                __syncwarp();
+                continue;
+            }
+            int off = 0;
+            for (int e0 = 0; e0 < nl[p]; e0 += 32) {
+                const int e = e0 + lane;
+                const bool k2 = e < nl[p] && lq[e] >= best[p] - band;
+                const unsigned b2 = __ballot_sync(0xffffffffu, k2);
+                if (k2) v.cand[start + off + __popc(b2 & ((1u << lane) - 1u))] = make_int2(pt, lj[e]);
+                off += __popc(b2);
+            }
+            if (lane == 0) v.arun[pt] = make_int2(start, cnt);
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(FB) k_assoc_final_gen(RunView v)
+{
+    Ctrl* c = v.ctrl;
+    if (skip_niche(c)) return;
+    const int pt = blockIdx.x * FB + threadIdx.x;
+    if (pt >= c->nT) return;
+    const int2 run = v.arun[pt];
+    if (run.x < 0) return;  // slow path
+    const int m = v.m;
+    double bd = 0.0;
+    int bj = 0;
+    const double nf = v.fnorm[pt];
+    if (nf != 0.0) {
+        const double* fp = v.fprime + (size_t)pt * m;
+        bd = CUDART_INF;
+        bj = 0x7fffffff;
+        for (int e = run.x; e < run.x + run.y; ++e) {
+            const int j = v.cand[e].y;
+            const double d = perp_dist(fp, nf, v.Zd + (size_t)j * m, v.nz[j], m);
+            if (lex_less(d, j, bd, bj)) {
+                bd = d;
+                bj = j;
+            }
+        }
+    }
+    if (v.debug_recheck_all) {
+        v.dist[v.Tlist[pt]] = bd;
+        v.pi[v.Tlist[pt]] = bj;
+        v.slow[atomicAdd(&c->nslow, 1)] = pt;
+        return;
+    }
+    write_assoc(v, c, v.Tlist[pt], bj, bd);
 }
 
 size_t scan_smem(const RunView& v) { return (size_t)v.nblk * (v.M4 + 2 + 8) * 4 + 8 * 2 * LC * 4; }
@@ -424,7 +643,10 @@ cudaError_t launch_assoc_prep(const RunView& v, cudaStream_t s)
     case 8: k_assoc_prep<8><<<g, PB, 0, s>>>(v); break;
     case 9: k_assoc_prep<9><<<g, PB, 0, s>>>(v); break;
     case 10: k_assoc_prep<10><<<g, PB, 0, s>>>(v); break;
-    default: return cudaErrorInvalidValue;
+    default:
+        if (v.m < 2 || v.m > NSGA3_MAX_M) return cudaErrorInvalidValue;
+        k_assoc_prep_gen<<<g, PB, 0, s>>>(v);
+        break;
     }
     return cudaGetLastError();
 }
@@ -441,8 +663,19 @@ cudaError_t launch_assoc_scan(const RunView& v, int num_sms, cudaStream_t s)
     case 8: return launch_m<8>(v, s, num_sms);
     case 9: return launch_m<9>(v, s, num_sms);
     case 10: return launch_m<10>(v, s, num_sms);
-    default: return cudaErrorInvalidValue;
+    default: break;
     }
+    if (v.m < 2 || v.m > NSGA3_MAX_M) return cudaErrorInvalidValue;
+    int blocks = (v.n2 + GPTS - 1) / GPTS;
+    if (blocks > num_sms * 8) blocks = num_sms * 8;
+    k_assoc_scan_gen<<<blocks, AB, 0, s>>>(v);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_assoc_final_gen<<<(v.n2 + FB - 1) / FB, FB, 0, s>>>(v);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_assoc_slow<0><<<num_sms, AB, 0, s>>>(v);
+    return cudaGetLastError();
 }
 
 // The scan's shared-memory opt-in is set once per process, at its maximum,
@@ -454,6 +687,7 @@ constexpr size_t SCAN_SMEM_MAX = 220 * 1024;
 cudaError_t assoc_prepare(const RunView& v)
 {
     if (v.m < 2 || v.m > NSGA3_MAX_M) return cudaErrorInvalidValue;
+    if (v.m > NSGA3_FAST_M) return cudaSuccess;  // the generic scan keeps no block tables
     return scan_smem(v) <= SCAN_SMEM_MAX ? cudaSuccess : cudaErrorInvalidValue;
 }
 

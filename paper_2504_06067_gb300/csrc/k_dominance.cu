@@ -28,6 +28,9 @@
 // In streaming mode (no matrix) only the counts are produced; the peel
 // recomputes the dominance of each front's members (k_peel.cu).
 //
+// m > 10 (k_dominance_gen): the same tiles, objectives staged in chunks of
+// 16 and the two sign masks OR-ed over the chunks.
+//
 // Bound: the ALU pipe (sign-bit logic) and instruction issue -- not HBM.
 #include "kernels.cuh"
 
@@ -232,6 +235,148 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
     if (colcnt[t]) atomicAdd(&v.cnt[c0 + t], colcnt[t]);
 }
 
+// m > NSGA3_FAST_M: the objectives are taken in chunks of MC (zero-padded:
+// a zero difference has a clear sign bit and changes neither mask).  Each
+// lane keeps, per row and column block, the 32-bit masks A ("some
+// f_i > f_j") and B ("some f_j > f_i") OR-ed over the chunks; the bits
+// follow from them as in the specialised kernel.
+constexpr int MC = 16;
+
+__global__ void __launch_bounds__(256) k_dominance_gen(RunView v)
+{
+    __shared__ __align__(16) float srow[NSGA3_TILE * MC];
+    __shared__ __align__(16) float scol[NSGA3_TILE * MC];
+    __shared__ int s_tile[2];
+    __shared__ int rowcnt[NSGA3_TILE];
+    __shared__ int colcnt[NSGA3_TILE];
+    if (read_status(v.ctrl)) return;
+    const int m = v.m;
+    rowcnt[threadIdx.x] = 0;
+    colcnt[threadIdx.x] = 0;
+    const int T = v.ld / NSGA3_TILE;
+    if (threadIdx.x == 0) decode_tile(blockIdx.x, T, s_tile[0], s_tile[1]);
+    __syncthreads();
+    const int ti = s_tile[0], tj = s_tile[1];
+    const int r0 = ti * NSGA3_TILE, c0 = tj * NSGA3_TILE;
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const int rp = warp & 3, ch = warp >> 2;
+    const int ib0 = ti * 8 + 2 * rp, ib1 = ib0 + 1;
+    // one-direction blocks from f_0 alone (as in the specialised kernel)
+    float rmax0 = v.Fp[(size_t)(r0 + 2 * rp * 32 + lane) * m];
+    float rmax1 = v.Fp[(size_t)(r0 + (2 * rp + 1) * 32 + lane) * m];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rmax0 = fmaxf(rmax0, __shfl_xor_sync(0xffffffffu, rmax0, o));
+        rmax1 = fmaxf(rmax1, __shfl_xor_sync(0xffffffffu, rmax1, o));
+    }
+    unsigned fastm = 0u;  // bit 2*cbi + r: one-direction block
+#pragma unroll
+    for (int cbi = 0; cbi < 4; ++cbi) {
+        const int jb = tj * 8 + ch * 4 + cbi;
+        float cmin = v.Fp[(size_t)(c0 + (ch * 4 + cbi) * 32 + lane) * m];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+        if (jb != ib0 && rmax0 < cmin) fastm |= 1u << (2 * cbi);
+        if (jb > ib1 && rmax1 < cmin) fastm |= 2u << (2 * cbi);
+    }
+    uint32_t A[4][2], B[4][2];
+#pragma unroll
+    for (int cbi = 0; cbi < 4; ++cbi) {
+        A[cbi][0] = A[cbi][1] = 0u;
+        B[cbi][0] = B[cbi][1] = 0u;
+    }
+    for (int q0 = 0; q0 < m; q0 += MC) {
+        __syncthreads();  // the previous chunk is consumed
+        for (int e = threadIdx.x; e < NSGA3_TILE * MC; e += blockDim.x) {
+            const int p = e / MC, q = q0 + (e - p * MC);
+            srow[e] = q < m ? v.Fp[(size_t)(r0 + p) * m + q] : 0.0f;
+            scol[e] = q < m ? v.Fp[(size_t)(c0 + p) * m + q] : 0.0f;
+        }
+        __syncthreads();
+        float f0[MC], f1[MC];
+#pragma unroll
+        for (int q = 0; q < MC; ++q) {
+            f0[q] = srow[(2 * rp * 32 + lane) * MC + q];
+            f1[q] = srow[((2 * rp + 1) * 32 + lane) * MC + q];
+        }
+#pragma unroll
+        for (int cbi = 0; cbi < 4; ++cbi) {
+            const int cb = ch * 4 + cbi;
+            const int jb = tj * 8 + cb;
+            if (jb < ib0) continue;
+            const float* colp = scol + cb * 32 * MC;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (jb < ib0 + r) continue;
+                const float* fi = r ? f1 : f0;
+                const bool fast = (fastm >> (2 * cbi + r)) & 1u;
+                uint32_t ma = 0u, mb = 0u;
+#pragma unroll 4
+                for (int k = 31; k >= 0; --k) {
+                    const float4* fj4 = reinterpret_cast<const float4*>(colp + k * MC);
+                    float fj[MC];
+#pragma unroll
+                    for (int q4 = 0; q4 < MC / 4; ++q4) {
+                        const float4 t = fj4[q4];
+                        fj[4 * q4 + 0] = t.x;
+                        fj[4 * q4 + 1] = t.y;
+                        fj[4 * q4 + 2] = t.z;
+                        fj[4 * q4 + 3] = t.w;
+                    }
+                    uint32_t oa = 0u, ob = 0u;
+                    if (fast) {  // f_j0 > f_i0 for the whole block: "some f_j > f_i" holds
+#pragma unroll
+                        for (int q = 0; q < MC; ++q) oa |= __float_as_uint(fj[q] - fi[q]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < MC; ++q) {
+                            oa |= __float_as_uint(fj[q] - fi[q]);
+                            ob |= __float_as_uint(fi[q] - fj[q]);
+                        }
+                    }
+                    ma = __funnelshift_l(oa, ma, 1);
+                    mb = __funnelshift_l(ob, mb, 1);
+                }
+                A[cbi][r] |= ma;
+                B[cbi][r] |= mb;
+            }
+        }
+    }
+    uint32_t* D = v.Dom;
+    int rc0 = 0, rc1 = 0;
+#pragma unroll
+    for (int cbi = 0; cbi < 4; ++cbi) {
+        const int cb = ch * 4 + cbi;
+        const int jb = tj * 8 + cb;
+        if (jb < ib0) continue;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int ib = ib0 + r;
+            if (jb < ib) continue;
+            const bool fast = (fastm >> (2 * cbi + r)) & 1u;
+            // i dom j: no f_i > f_j and some f_j > f_i (B is implied in a fast block)
+            const uint32_t dij = fast ? ~A[cbi][r] : (B[cbi][r] & ~A[cbi][r]);
+            const uint32_t dji = fast ? 0u : (A[cbi][r] & ~B[cbi][r]);
+            if (!v.streaming) D[(size_t)jb * v.ld + ib * 32 + lane] = dji;
+            if (r)
+                rc1 += __popc(dji);
+            else
+                rc0 += __popc(dji);
+            if (jb != ib) {
+                const uint32_t t = warp_transpose32(dij);
+                if (!v.streaming) D[(size_t)ib * v.ld + jb * 32 + lane] = t;
+                if (t) atomicAdd(&colcnt[cb * 32 + lane], __popc(t));
+            }
+        }
+    }
+    if (rc0) atomicAdd(&rowcnt[2 * rp * 32 + lane], rc0);
+    if (rc1) atomicAdd(&rowcnt[(2 * rp + 1) * 32 + lane], rc1);
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (rowcnt[t]) atomicAdd(&v.cnt[r0 + t], rowcnt[t]);
+    if (colcnt[t]) atomicAdd(&v.cnt[c0 + t], colcnt[t]);
+}
+
 template <int M>
 cudaError_t launch_dom_m(const RunView& v, cudaStream_t s)
 {
@@ -256,6 +401,12 @@ cudaError_t launch_dominance(const RunView& v, cudaStream_t s)
     case 8: return launch_dom_m<8>(v, s);
     case 9: return launch_dom_m<9>(v, s);
     case 10: return launch_dom_m<10>(v, s);
-    default: return cudaErrorInvalidValue;
+    default: break;
     }
+    if (v.m < 2 || v.m > NSGA3_MAX_M) return cudaErrorInvalidValue;
+    const long long T = v.ld / NSGA3_TILE;
+    const long long tiles = T * (T + 1) / 2;
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_dominance_gen<<<(unsigned)tiles, 256, 0, s>>>(v);
+    return cudaGetLastError();
 }

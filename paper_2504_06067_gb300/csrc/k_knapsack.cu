@@ -79,10 +79,10 @@ __global__ void __launch_bounds__(KB) k_kp_eval(RunView v, int row0, int n)
     float* x = v.X + (size_t)(row0 + r) * d;
     // loads and excess per knapsack (integers; sums below 2^31 by the
     // limits checked at creation)
-    int excess[NSGA3_MAX_M];
+    int excess[NSGA3_FAST_M];
     bool over = false;
 #pragma unroll
-    for (int j = 0; j < NSGA3_MAX_M; ++j) {
+    for (int j = 0; j < NSGA3_FAST_M; ++j) {
         if (j >= m) {
             excess[j] = 0;
             continue;
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(KB) k_kp_eval(RunView v, int row0, int n)
         const bool chosen = k < d && x[item] != 0.0f;
         bool done = true;
 #pragma unroll
-        for (int j = 0; j < NSGA3_MAX_M; ++j) {
+        for (int j = 0; j < NSGA3_FAST_M; ++j) {
             if (j >= m) continue;
             int wv = chosen ? __ldg(&v.kp_w[(size_t)j * d + item]) : 0;
             // inclusive prefix sum over the chunk
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(KB) k_kp_eval(RunView v, int row0, int n)
     __syncwarp();
     // objectives: profit left behind
 #pragma unroll
-    for (int j = 0; j < NSGA3_MAX_M; ++j) {
+    for (int j = 0; j < NSGA3_FAST_M; ++j) {
         if (j >= m) continue;
         int s = 0;
         for (int e = lane; e < d; e += 32)

@@ -59,7 +59,7 @@ __global__ void k_sel_reset(RunView v)
         c->cmp_done = 0u;
         c->overflow = 0;
         c->recheck_miss = 0;
-        for (int q = 0; q < NSGA3_MAX_M; ++q) c->zmin[q] = 0xffffffffu;
+        for (int q = 0; q < v.m; ++q) c->zmin[q] = 0xffffffffu;
     }
 }
 
@@ -165,7 +165,7 @@ __global__ void k_gather(RunView v)
     const float* src = v.X + (size_t)i * v.d;
     float* dst = v.Xtmp + (size_t)p * v.d;
     for (int e = lane; e < v.d; e += 32) dst[e] = src[e];
-    if (lane < v.m) v.Ftmp[(size_t)p * v.m + lane] = v.F[(size_t)i * v.m + lane];
+    for (int q = lane; q < v.m; q += 32) v.Ftmp[(size_t)p * v.m + q] = v.F[(size_t)i * v.m + q];
     if (lane == 0) v.ranktmp[p] = v.rank2[i];
 }
 

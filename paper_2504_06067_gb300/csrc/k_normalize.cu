@@ -80,43 +80,49 @@ __device__ __forceinline__ bool key_less(unsigned long long a, int ia, unsigned 
 // every element sees the same _rn operations in the same order as a serial
 // elimination (factor = A_rc / A_cc, A_rk -= factor * A_ck for k >= c,
 // rhs_r -= factor * rhs_c; back substitution left to right).
+// M <= NSGA3_FAST_M: m = M; M = NSGA3_WARP_M: any m <= 32 at run time
+// (rows and columns >= m are never touched).
 template <int M>
 __device__ void solve_intercepts(const RunView& v, Ctrl* c, const int* ext, const double* nad)
 {
+    const int m = (M <= NSGA3_FAST_M) ? M : v.m;
     const int lane = lane_id();
     double zs[M];
 #pragma unroll
-    for (int q = 0; q < M; ++q) zs[q] = zstar_of(c, q);
+    for (int q = 0; q < M; ++q) zs[q] = q < m ? zstar_of(c, q) : 0.0;
     if (lane == 0) {
 #pragma unroll
-        for (int q = 0; q < M; ++q) {
-            c->zstar[q] = zs[q];
-            c->ext[q] = ext[q];
-        }
+        for (int q = 0; q < M; ++q)
+            if (q < m) {
+                c->zstar[q] = zs[q];
+                c->ext[q] = ext[q];
+            }
     }
     bool ok = true;
-    const int ncand = v.n2 + ((v.norm_history && c->hvalid) ? M : 0);
+    const int ncand = v.n2 + ((v.norm_history && c->hvalid) ? m : 0);
 #pragma unroll
     for (int q = 0; q < M; ++q)
-        if (ext[q] < 0 || ext[q] >= ncand) ok = false;
+        if (q < m && (ext[q] < 0 || ext[q] >= ncand)) ok = false;
     double A[M], rhs = 1.0;
     float evec[M];  // this lane's extreme vector (a merged point or a remembered one)
-    const int er = lane < M ? ext[lane] : 0;
+    const bool row = lane < m;
+    const int er = row ? ext[lane] : 0;
 #pragma unroll
     for (int q = 0; q < M; ++q) {
-        evec[q] = (ok && lane < M) ? (er < v.n2 ? v.F[(size_t)er * M + q] : c->he[(er - v.n2) * M + q]) : 0.0f;
-        A[q] = (ok && lane < M) ? __dsub_rn((double)evec[q], zs[q]) : 0.0;
+        const bool in = ok && row && q < m;
+        evec[q] = in ? (er < v.n2 ? v.F[(size_t)er * m + q] : v.he[(er - v.n2) * m + q]) : 0.0f;
+        A[q] = in ? __dsub_rn((double)evec[q], zs[q]) : 0.0;
     }
 #pragma unroll
     for (int col = 0; col < M; ++col) {
-        if (!ok) break;
+        if (!ok || col >= m) break;
         // pivot: first row >= col of maximal |A[.][col]| (rows in current order)
         int p = col;
         double best = fabs(__shfl_sync(0xffffffffu, A[col], col));
 #pragma unroll
         for (int r = col + 1; r < M; ++r) {
             const double x = fabs(__shfl_sync(0xffffffffu, A[col], r));
-            if (x > best) {
+            if (r < m && x > best) {
                 best = x;
                 p = r;
             }
@@ -142,10 +148,11 @@ __device__ void solve_intercepts(const RunView& v, Ctrl* c, const int* ext, cons
 #pragma unroll
         for (int q = 0; q < M; ++q) piv[q] = __shfl_sync(0xffffffffu, A[q], col);
         const double prhs = __shfl_sync(0xffffffffu, rhs, col);
-        if (lane > col && lane < M) {
+        if (lane > col && lane < m) {
             const double factor = __ddiv_rn(A[col], piv[col]);
 #pragma unroll
-            for (int q = col; q < M; ++q) A[q] = __dsub_rn(A[q], __dmul_rn(factor, piv[q]));
+            for (int q = col; q < M; ++q)
+                if (q < m) A[q] = __dsub_rn(A[q], __dmul_rn(factor, piv[q]));
             rhs = __dsub_rn(rhs, __dmul_rn(factor, prhs));
         }
     }
@@ -154,17 +161,21 @@ __device__ void solve_intercepts(const RunView& v, Ctrl* c, const int* ext, cons
         double b = 0.0;  // lane r ends with b_r
 #pragma unroll
         for (int r = M - 1; r >= 0; --r) {
+            if (r >= m) continue;
             double s = rhs;
 #pragma unroll
-            for (int cc = r + 1; cc < M; ++cc) s = __dsub_rn(s, __dmul_rn(A[cc], __shfl_sync(0xffffffffu, b, cc)));
+            for (int cc = r + 1; cc < M; ++cc) {
+                const double bc = __shfl_sync(0xffffffffu, b, cc);
+                if (cc < m) s = __dsub_rn(s, __dmul_rn(A[cc], bc));
+            }
             const double br = __ddiv_rn(s, A[r]);
             if (lane == r) b = br;
         }
-        a = lane < M ? __ddiv_rn(1.0, b) : 1.0;
-        const bool bad = lane < M && (!isfinite(a) || a <= 1e-6);
+        a = lane < m ? __ddiv_rn(1.0, b) : 1.0;
+        const bool bad = lane < m && (!isfinite(a) || a <= 1e-6);
         if (__any_sync(0xffffffffu, bad)) ok = false;
     }
-    if (lane < M) {
+    if (lane < m) {
         if (!ok) a = (nad[lane] == 0.0) ? 1.0 : nad[lane];
         c->a[lane] = a;
     }
@@ -173,10 +184,11 @@ __device__ void solve_intercepts(const RunView& v, Ctrl* c, const int* ext, cons
         // the ideal and the extreme vectors become the history (every lane
         // read its remembered row above, before these writes)
         __syncwarp();
-        if (lane < M) {
+        if (lane < m) {
             c->hz[lane] = zs[lane];
 #pragma unroll
-            for (int q = 0; q < M; ++q) c->he[lane * M + q] = evec[q];
+            for (int q = 0; q < M; ++q)
+                if (q < m) v.he[lane * m + q] = evec[q];
         }
         if (lane == 0) c->hvalid = 1;
     }
@@ -187,12 +199,12 @@ __device__ void solve_intercepts(const RunView& v, Ctrl* c, const int* ext, cons
 template <int M>
 __global__ void __launch_bounds__(EB) k_norm_extreme(RunView v)
 {
-    __shared__ unsigned long long s_key[EB / 32][NSGA3_MAX_M];
-    __shared__ int s_idx[EB / 32][NSGA3_MAX_M];
-    __shared__ unsigned long long s_nad[EB / 32][NSGA3_MAX_M];
+    __shared__ unsigned long long s_key[EB / 32][NSGA3_FAST_M];
+    __shared__ int s_idx[EB / 32][NSGA3_FAST_M];
+    __shared__ unsigned long long s_nad[EB / 32][NSGA3_FAST_M];
     __shared__ unsigned s_ticket;
-    __shared__ int f_ext[NSGA3_MAX_M];
-    __shared__ double f_nad[NSGA3_MAX_M];
+    __shared__ int f_ext[NSGA3_FAST_M];
+    __shared__ double f_nad[NSGA3_FAST_M];
     Ctrl* c = v.ctrl;
     if (skip_niche(c)) return;
     constexpr int m = M;
@@ -320,7 +332,7 @@ __global__ void __launch_bounds__(EB) k_norm_extreme(RunView v)
             if (v.norm_history && c->hvalid) {
                 // the remembered extreme vectors are candidates 2N + r
                 for (int r = 0; r < m; ++r) {
-                    const float* f = c->he + r * m;
+                    const float* f = v.he + r * m;
                     double mx = 0.0, tq = 0.0;
                     for (int t = 0; t < m; ++t) {
                         const double ft = __dsub_rn((double)f[t], zs[t]);
@@ -348,6 +360,338 @@ __global__ void __launch_bounds__(EB) k_norm_extreme(RunView v)
     }
 }
 
+// ---------------------------------------------------------------------------
+// m > NSGA3_FAST_M.  The candidates of the extreme-point search are "entries":
+// the members of T (index = merged index) and, with history, the remembered
+// vectors (index 2N + r).  k_ext_keys gives each entry the two ASF keys it
+// can have: fl(max_r f~_r / 1e-6) and, for the axis of that maximum (first
+// index), fl(second largest / 1e-6).  k_ext_axis takes QG axes per block:
+// ASF_q = max(f~_q, that key) per entry, (min, lowest index) per axis, and
+// the nadir maxima over the members; the last block reduces the blocks and
+// either solves the intercepts with one warp (m <= NSGA3_WARP_M) or leaves
+// E and the nadir to the cooperative elimination below.
+constexpr int GB = 128;  // threads per block of the m > NSGA3_FAST_M kernels
+constexpr int QG = 8;    // axes per block of k_ext_axis
+
+__device__ __forceinline__ const float* entry_row(const RunView& v, int s, int nT, int& idx)
+{
+    if (s < nT) {
+        idx = v.Tlist[s];
+        return v.F + (size_t)idx * v.m;
+    }
+    idx = v.n2 + (s - nT);
+    return v.he + (size_t)(s - nT) * v.m;
+}
+
+__device__ __forceinline__ int history_entries(const RunView& v, const Ctrl* c)
+{
+    return (v.norm_history && c->hvalid) ? v.m : 0;
+}
+
+__global__ void __launch_bounds__(GB) k_ext_keys(RunView v)
+{
+    Ctrl* c = v.ctrl;
+    if (skip_niche(c)) return;
+    const int m = v.m, nT = c->nT;
+    const int ne = nT + history_entries(v, c);
+    for (int s = blockIdx.x * GB + threadIdx.x; s < ne; s += gridDim.x * GB) {
+        int idx;
+        const float* f = entry_row(v, s, nT, idx);
+        unsigned long long m1 = 0ull, m2 = 0ull;  // f~ >= 0: keys order like values
+        int r1 = 0;
+        for (int r = 0; r < m; ++r) {
+            const unsigned long long kr = okey(__dsub_rn((double)f[r], zstar_of(c, r)));
+            if (kr > m1) {
+                m2 = m1;
+                m1 = kr;
+                r1 = r;
+            } else if (kr > m2) {
+                m2 = kr;
+            }
+        }
+        v.ekey[2 * (size_t)s] = okey(__ddiv_rn(__longlong_as_double((long long)m1), 1e-6));
+        v.ekey[2 * (size_t)s + 1] = okey(__ddiv_rn(__longlong_as_double((long long)m2), 1e-6));
+        v.er1[s] = r1;
+    }
+}
+
+// grid (parts, ceil(m / QG))
+__global__ void __launch_bounds__(GB) k_ext_axis(RunView v)
+{
+    __shared__ unsigned long long s_key[GB / 32][QG];
+    __shared__ int s_idx[GB / 32][QG];
+    __shared__ unsigned long long s_nad[GB / 32][QG];
+    __shared__ unsigned s_ticket;
+    __shared__ int f_ext[NSGA3_WARP_M];
+    __shared__ double f_nad[NSGA3_WARP_M];
+    Ctrl* c = v.ctrl;
+    if (skip_niche(c)) return;
+    const int m = v.m, nT = c->nT;
+    const int ne = nT + history_entries(v, c);
+    const int parts = gridDim.x;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const int q0 = blockIdx.y * QG;
+    double zs[QG];
+    unsigned long long best[QG], nad[QG];
+    int bidx[QG];
+#pragma unroll
+    for (int t = 0; t < QG; ++t) {
+        zs[t] = q0 + t < m ? zstar_of(c, q0 + t) : 0.0;
+        best[t] = ~0ull;
+        bidx[t] = 0x7fffffff;
+        nad[t] = 0ull;
+    }
+    for (int s = blockIdx.x * GB + threadIdx.x; s < ne; s += parts * GB) {
+        int idx;
+        const float* f = entry_row(v, s, nT, idx);
+        const unsigned long long k1 = v.ekey[2 * (size_t)s], k2 = v.ekey[2 * (size_t)s + 1];
+        const int r1 = v.er1[s];
+#pragma unroll
+        for (int t = 0; t < QG; ++t) {
+            const int q = q0 + t;
+            if (q >= m) break;
+            const unsigned long long kq = okey(__dsub_rn((double)f[q], zs[t]));
+            const unsigned long long other = (q == r1) ? k2 : k1;
+            const unsigned long long asf = kq > other ? kq : other;
+            if (key_less(asf, idx, best[t], bidx[t])) {
+                best[t] = asf;
+                bidx[t] = idx;
+            }
+            if (s < nT) nad[t] = max(nad[t], kq);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < QG; ++t) {
+        unsigned long long b = best[t], n = nad[t];
+        int bi = bidx[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            const unsigned long long on = __shfl_xor_sync(0xffffffffu, n, o);
+            if (key_less(ob, oi, b, bi)) {
+                b = ob;
+                bi = oi;
+            }
+            n = max(n, on);
+        }
+        if (lane == 0) {
+            s_key[warp][t] = b;
+            s_idx[warp][t] = bi;
+            s_nad[warp][t] = n;
+        }
+    }
+    __syncthreads();
+    unsigned long long* pk = reinterpret_cast<unsigned long long*>(v.ext_part);
+    unsigned long long* pn = reinterpret_cast<unsigned long long*>(v.nad_part);
+    if (threadIdx.x < QG && q0 + (int)threadIdx.x < m) {
+        const int t = threadIdx.x, q = q0 + t;
+        unsigned long long b = s_key[0][t], n = s_nad[0][t];
+        int bi = s_idx[0][t];
+        for (int w = 1; w < GB / 32; ++w) {
+            if (key_less(s_key[w][t], s_idx[w][t], b, bi)) {
+                b = s_key[w][t];
+                bi = s_idx[w][t];
+            }
+            n = max(n, s_nad[w][t]);
+        }
+        pk[(size_t)blockIdx.x * m + q] = b;
+        v.ext_idx[(size_t)blockIdx.x * m + q] = bi;
+        pn[(size_t)blockIdx.x * m + q] = n;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_ticket = atomicAdd(&c->ext_done, 1u);
+    __syncthreads();
+    if (s_ticket != gridDim.x * gridDim.y - 1) return;
+    __threadfence();
+    // last block: one warp per axis over the parts
+    for (int q = warp; q < m; q += GB / 32) {
+        unsigned long long b = ~0ull, n = 0ull;
+        int bi = 0x7fffffff;
+        for (int p = lane; p < parts; p += 32) {
+            const unsigned long long pb = __ldcg(&pk[(size_t)p * m + q]);
+            const int pi = __ldcg(&v.ext_idx[(size_t)p * m + q]);
+            if (key_less(pb, pi, b, bi)) {
+                b = pb;
+                bi = pi;
+            }
+            n = max(n, __ldcg(&pn[(size_t)p * m + q]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            const unsigned long long on = __shfl_xor_sync(0xffffffffu, n, o);
+            if (key_less(ob, oi, b, bi)) {
+                b = ob;
+                bi = oi;
+            }
+            n = max(n, on);
+        }
+        if (lane == 0) {
+            const double nq = __longlong_as_double((long long)n);
+            if (m <= NSGA3_WARP_M) {
+                f_ext[q] = bi;
+                f_nad[q] = nq;
+            } else {
+                c->ext[q] = bi;
+                v.nadv[q] = nq;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) c->ext_done = 0u;
+    if (m <= NSGA3_WARP_M && warp == 0) solve_intercepts<NSGA3_WARP_M>(v, c, f_ext, f_nad);
+}
+
+// m > NSGA3_WARP_M: the elimination of the warp solver spread over a
+// cooperative grid.  The augmented rows [E - z* | 1] live in amat (original
+// row order); every CTA keeps the same current row order ord[] and takes
+// the same pivot (first maximal |A[.][col]| in that order), so a pivot step
+// needs one grid barrier: a warp per remaining row forms its factor and
+// updates columns col+1 .. m (m = the right-hand side) with the same _rn
+// operations as the serial elimination (column col is not needed again).
+// Reads of amat bypass L1 (other SMs write it between barriers).  The back
+// substitution (left to right, as in the warp solver) runs in CTA 0.
+constexpr int SB = 256;
+
+__global__ void __launch_bounds__(SB) k_solve_coop(RunView v)
+{
+    __shared__ int ord[NSGA3_MAX_M];
+    __shared__ double sb[NSGA3_MAX_M];
+    __shared__ double red_x[SB / 32];
+    __shared__ int red_p[SB / 32];
+    __shared__ int s_ok, s_piv;
+    Ctrl* c = v.ctrl;
+    if (skip_niche(c)) return;
+    const int m = v.m, ld = m + 1;
+    const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    const int gw = blockIdx.x * (SB / 32) + warp, nw = gridDim.x * (SB / 32);
+    double* A = v.amat;
+    const int ncand = v.n2 + ((v.norm_history && c->hvalid) ? m : 0);
+    bool bad_ext = false;
+    for (int q = tid; q < m; q += SB) {
+        const int e = c->ext[q];
+        bad_ext |= e < 0 || e >= ncand;
+        ord[q] = q;
+        if (blockIdx.x == 0) c->zstar[q] = zstar_of(c, q);
+    }
+    const bool ext_ok = !__syncthreads_or(bad_ext);
+    bool ok = ext_ok;
+    if (ok) {
+        // rows of the system and the new extreme vectors (warp per row)
+        for (int q = gw; q < m; q += nw) {
+            const int er = c->ext[q];
+            const float* f = er < v.n2 ? v.F + (size_t)er * m : v.he + (size_t)(er - v.n2) * m;
+            for (int k = lane; k < m; k += 32) {
+                const float ev = f[k];
+                v.etmp[(size_t)q * m + k] = ev;
+                A[(size_t)q * ld + k] = __dsub_rn((double)ev, zstar_of(c, k));
+            }
+            if (lane == 0) A[(size_t)q * ld + m] = 1.0;
+        }
+        if (!grid_sync(c, &s_ok)) return;
+        for (int col = 0; col < m; ++col) {
+            // pivot (every CTA): the first position p >= col of maximal
+            // |A[ord[p]][col]|; a NaN never replaces the running maximum
+            double bx = -1.0;
+            int bp = 0x7fffffff;
+            for (int p = col + 1 + tid; p < m; p += SB) {
+                const double x = fabs(__ldcg(&A[(size_t)ord[p] * ld + col]));
+                if (x > bx) {  // positions ascend per thread: the first maximum stays
+                    bx = x;
+                    bp = p;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ox = __shfl_xor_sync(0xffffffffu, bx, o);
+                const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+                if (ox > bx || (ox == bx && op < bp)) {
+                    bx = ox;
+                    bp = op;
+                }
+            }
+            if (lane == 0) {
+                red_x[warp] = bx;
+                red_p[warp] = bp;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                for (int w = 1; w < SB / 32; ++w)
+                    if (red_x[w] > bx || (red_x[w] == bx && red_p[w] < bp)) {
+                        bx = red_x[w];
+                        bp = red_p[w];
+                    }
+                const double x0 = fabs(__ldcg(&A[(size_t)ord[col] * ld + col]));
+                int p = col;
+                double best = x0;
+                if (x0 == x0 && bp != 0x7fffffff && bx > x0) {  // x0 NaN: col stays
+                    p = bp;
+                    best = bx;
+                }
+                s_piv = p;
+                s_ok = best == 0.0 ? 0 : 1;
+                if (p != col) {
+                    const int t = ord[col];
+                    ord[col] = ord[p];
+                    ord[p] = t;
+                }
+            }
+            __syncthreads();
+            if (!s_ok) {
+                ok = false;
+                break;
+            }
+            const int P = ord[col];
+            const double pv = __ldcg(&A[(size_t)P * ld + col]);
+            for (int pos = col + 1 + gw; pos < m; pos += nw) {
+                const int r = ord[pos];
+                const double factor = __ddiv_rn(__ldcg(&A[(size_t)r * ld + col]), pv);
+                for (int k = col + 1 + lane; k <= m; k += 32)
+                    A[(size_t)r * ld + k] = __dsub_rn(__ldcg(&A[(size_t)r * ld + k]),
+                                                      __dmul_rn(factor, __ldcg(&A[(size_t)P * ld + k])));
+            }
+            if (!grid_sync(c, &s_ok)) return;
+        }
+    }
+    if (blockIdx.x != 0) return;
+    // CTA 0: back substitution, intercepts, fallback, history
+    if (ok && warp == 0) {
+        for (int r = m - 1; r >= 0; --r) {
+            const int R = ord[r];
+            if (lane == 0) {
+                double s = __ldcg(&A[(size_t)R * ld + m]);
+                for (int cc = r + 1; cc < m; ++cc) s = __dsub_rn(s, __dmul_rn(__ldcg(&A[(size_t)R * ld + cc]), sb[cc]));
+                sb[r] = __ddiv_rn(s, __ldcg(&A[(size_t)R * ld + r]));
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    bool bad = false;
+    if (ok)
+        for (int q = tid; q < m; q += SB) {
+            const double a = __ddiv_rn(1.0, sb[q]);
+            bad |= !isfinite(a) || a <= 1e-6;
+            sb[q] = a;
+        }
+    ok = ok && !__syncthreads_or(bad);
+    for (int q = tid; q < m; q += SB) {
+        const double nq = v.nadv[q];
+        c->a[q] = ok ? sb[q] : (nq == 0.0 ? 1.0 : nq);
+    }
+    if (tid == 0) c->fallback = ok ? 0 : 1;
+    if (v.norm_history) {
+        for (int q = tid; q < m; q += SB) c->hz[q] = zstar_of(c, q);
+        // the staged extreme vectors (zero rows, as in the warp solver, when
+        // an extreme index was invalid and nothing was staged)
+        for (int e = tid; e < m * m; e += SB) v.he[e] = ext_ok ? v.etmp[e] : 0.0f;
+        if (tid == 0) c->hvalid = 1;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_norm_ideal(const RunView& v, cudaStream_t s)
@@ -356,8 +700,49 @@ cudaError_t launch_norm_ideal(const RunView& v, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_norm_extreme(const RunView& v, cudaStream_t s)
+static int g_solve_occ = 0;  // resident k_solve_coop CTAs per SM, set at start-up
+
+static cudaError_t launch_norm_extreme_gen(const RunView& v, int num_sms, cudaStream_t s)
 {
+    if (v.m <= NSGA3_FAST_M || v.m > NSGA3_MAX_M) return cudaErrorInvalidValue;
+    const int qgroups = (v.m + QG - 1) / QG;
+    int parts = (2 * num_sms + qgroups - 1) / qgroups;
+    if (parts > v.ext_parts) parts = v.ext_parts;
+    if (parts > (v.n2 + v.m + GB - 1) / GB) parts = (v.n2 + v.m + GB - 1) / GB;
+    if (parts < 1) parts = 1;
+    int kb = (v.n2 + v.m + GB - 1) / GB;
+    if (kb > 4 * num_sms) kb = 4 * num_sms;
+    k_ext_keys<<<kb, GB, 0, s>>>(v);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_ext_axis<<<dim3(parts, qgroups), GB, 0, s>>>(v);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || v.m <= NSGA3_WARP_M) return e;
+    // one warp per remaining row at the first step, every CTA resident
+    int grid = (v.m - 1 + SB / 32 - 1) / (SB / 32);
+    const int cap = num_sms * (g_solve_occ > 0 ? g_solve_occ : 1);
+    if (grid > cap) grid = cap;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(SB);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_solve_coop, v);
+}
+
+cudaError_t norm_init_attributes()
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_solve_occ, k_solve_coop, SB, 0);
+}
+
+cudaError_t launch_norm_extreme(const RunView& v, int num_sms, cudaStream_t s)
+{
+    if (v.m > NSGA3_FAST_M) return launch_norm_extreme_gen(v, num_sms, s);
     switch (v.m) {
     case 2: k_norm_extreme<2><<<v.ext_parts, EB, 0, s>>>(v); break;
     case 3: k_norm_extreme<3><<<v.ext_parts, EB, 0, s>>>(v); break;

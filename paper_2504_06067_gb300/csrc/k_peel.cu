@@ -2,8 +2,9 @@
 // (Alg. 1 line 3: fronts F_1, F_2, ... until |F_1| + ... + |F_l| >= N,
 // splitting R_t into S = F_1..F_{l-1}, F_l and F_drop; Sec. II-C).
 //
-// One launch per front, replayed by a CUDA-graph WHILE node; the last CTA
-// of a pass sets the node's condition, so the host never synchronises.
+// One cooperative launch runs every pass: the CTAs meet at a grid barrier
+// (common.cuh) after each pass and all take the same decision from the
+// front size, so the host never synchronises.
 // Positions are in bucket order of f_0 (k_sort.cu); ranks are written back
 // to the original order by k_norm_ideal.
 //   cnt[j]    = dominators of j, counted by the dominance build
@@ -12,9 +13,8 @@
 //   front_k   = { j unranked : cnt[j] == 0 }, rank2[j] = k
 // A CTA of 32 warps owns 128 columns (uint4 per lane); its warps split the
 // dominator rows and meet in shared memory, so the CTA alone updates its
-// columns' counts, ranks them and writes their front-mask words.  The last
-// CTA of a pass (ticket) closes the front.  Bound: HBM / L2 bandwidth of the
-// Dom reads.
+// columns' counts, ranks them and writes their front-mask words.  Bound:
+// HBM / L2 bandwidth of the Dom reads.
 #include <math_constants.h>
 
 #include "kernels.cuh"
@@ -25,59 +25,6 @@ constexpr int PEEL_THREADS = 512;  // threads per CTA
 constexpr int PWMAX = PEEL_THREADS / 32;
 constexpr int LISTCAP = 2048;
 
-// Grid barrier of the cooperative peel, with a bounded wait.  Returns false
-// (and records NSGA3_ETIMEOUT) when the other CTAs did not arrive within
-// WAIT_NS of device time (the longest legitimate wait is one pass of the
-// slowest CTA: milliseconds with the matrix, up to seconds when streaming
-// the largest populations).
-constexpr unsigned long long WAIT_NS = 20ull * 1000 * 1000 * 1000;
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
-{
-    unsigned x;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(x) : "l"(p) : "memory");
-    return x;
-}
-
-__device__ bool grid_sync(Ctrl* c, int* s_ok)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned g = ld_acquire(&c->bar_gen);
-        __threadfence();
-        if (atomicAdd(&c->bar_count, 1u) == gridDim.x - 1) {
-            atomicExch(&c->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&c->bar_gen, 1u);
-        } else {
-            const unsigned long long t0 = global_ns();
-            unsigned it = 0;
-            while (ld_acquire(&c->bar_gen) == g) {
-                // the clock is read every 256 polls; the poll count caps the
-                // wait too, should the timer not advance
-                if ((++it & 255u) == 0u && (global_ns() - t0 > WAIT_NS || it > (1u << 30))) {
-                    set_status(c, DEV_ETIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(100);
-            }
-        }
-        __threadfence();
-        *s_ok = ok;
-    }
-    __syncthreads();
-    return *s_ok != 0;
-}
-
 template <bool STREAM>
 __global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v)
 {
@@ -86,7 +33,7 @@ __global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v
     __shared__ uint2 list[LISTCAP];
     __shared__ int nlist;
     __shared__ int s_ok;
-    __shared__ float rowbuf[STREAM ? PWMAX : 1][32][NSGA3_MAX_M];  // streaming: members of a front word
+    __shared__ float rowbuf[STREAM ? PWMAX : 1][32][NSGA3_FAST_M];  // streaming: members of a front word
     Ctrl* c = v.ctrl;
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     if (read_status(c)) return;  // uniform: set only by earlier kernels
@@ -127,12 +74,12 @@ __global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v
                 // whose f_0 is below every f_0 of the chunk needs objectives
                 // 1..m-1 only (f_0 makes the dominance strict)
                 const int m = v.m;
-                float fc[4][NSGA3_MAX_M];
+                float fc[4][NSGA3_FAST_M];
                 float cmin = CUDART_INF_F;
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
 #pragma unroll
-                    for (int q = 0; q < NSGA3_MAX_M; ++q)
+                    for (int q = 0; q < NSGA3_FAST_M; ++q)
                         fc[t][q] = q < m ? v.Fp[(size_t)(j0 + lane * 4 + t) * m + q] : 0.0f;
                     cmin = fminf(cmin, fc[t][0]);  // NaN padding columns are ignored by fminf
                 }
@@ -162,22 +109,22 @@ __global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v
                         if ((L.y >> lane) & 1u) {
                             const size_t p = (size_t)L.x * 32 + lane;
 #pragma unroll
-                            for (int q = 0; q < NSGA3_MAX_M; ++q)
-                                if (q < m) rb[lane * NSGA3_MAX_M + q] = __ldg(&v.Fp[p * m + q]);
+                            for (int q = 0; q < NSGA3_FAST_M; ++q)
+                                if (q < m) rb[lane * NSGA3_FAST_M + q] = __ldg(&v.Fp[p * m + q]);
                         }
                         __syncwarp();
                         uint32_t mk = L.y;
                         while (mk) {  // warp-uniform: every lane walks the same rows
                             const int b = __ffs(mk) - 1;
                             mk &= mk - 1u;
-                            const float* fi = rb + b * NSGA3_MAX_M;
+                            const float* fi = rb + b * NSGA3_FAST_M;
                             uint32_t d4[4];
                             if (fi[0] < cmin) {
 #pragma unroll
                                 for (int t = 0; t < 4; ++t) {
                                     uint32_t oa = 0u;
 #pragma unroll
-                                    for (int q = 1; q < NSGA3_MAX_M; ++q)
+                                    for (int q = 1; q < NSGA3_FAST_M; ++q)
                                         if (q < m) oa |= __float_as_uint(fc[t][q] - fi[q]);
                                     d4[t] = (~oa) >> 31;  // no f_iq > f_jq
                                 }
@@ -186,7 +133,7 @@ __global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v
                                 for (int t = 0; t < 4; ++t) {
                                     uint32_t oa = 0u, ob = 0u;
 #pragma unroll
-                                    for (int q = 0; q < NSGA3_MAX_M; ++q)
+                                    for (int q = 0; q < NSGA3_FAST_M; ++q)
                                         if (q < m) {
                                             oa |= __float_as_uint(fc[t][q] - fi[q]);
                                             ob |= __float_as_uint(fi[q] - fc[t][q]);

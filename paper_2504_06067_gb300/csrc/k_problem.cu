@@ -38,7 +38,7 @@ __global__ void k_refdirs(int m, int p1, int p2, double tau, int w1, int w, doub
     const bool inner = t >= w1;
     const int p = inner ? p2 : p1;
     long long idx = inner ? t - w1 : t;
-    int k[NSGA3_MAX_M];
+    double* z = Zd + (size_t)t * m;  // first the composition k, then k / p
     int left = p;
     for (int q = 0; q < m - 1; ++q) {
         int val = 0;
@@ -47,21 +47,19 @@ __global__ void k_refdirs(int m, int p1, int p2, double tau, int w1, int w, doub
             if (idx < n) break;
             idx -= n;
         }
-        k[q] = val;
+        z[q] = (double)val;
         left -= val;
     }
-    k[m - 1] = left;
-    double z[NSGA3_MAX_M];
+    z[m - 1] = (double)left;
     double s = 0.0;
     for (int q = 0; q < m; ++q) {
-        double zq = __ddiv_rn((double)k[q], (double)p);
+        double zq = __ddiv_rn(z[q], (double)p);
         if (inner) {
             const double a = __ddiv_rn(__dsub_rn(1.0, tau), (double)m);
             const double b = __dmul_rn(tau, zq);
             zq = __dadd_rn(a, b);
         }
         z[q] = zq;
-        Zd[(size_t)t * m + q] = zq;
         s = __dadd_rn(s, __dmul_rn(zq, zq));
     }
     const double n = __dsqrt_rn(s);
@@ -69,7 +67,7 @@ __global__ void k_refdirs(int m, int p1, int p2, double tau, int w1, int w, doub
     for (int q = 0; q < M4; ++q) Zh[(size_t)t * M4 + q] = q < m ? __double2float_rn(__ddiv_rn(z[q], n)) : 0.0f;
 }
 
-// Objective of rows [row0, row0 + n): a block covers OR = 32 rows.
+// Objective of rows [row0, row0 + n): a block covers R = obj_rows(m) rows.
 //   g = sum_{v >= m-1} (x_v - 0.5)^2: each term is formed exactly as a
 //   float-float value (x - 0.5 by Fast2Sum, the square by an FMA product
 //   error) and the terms are added in float-float (TwoSum) by a warp per row
@@ -83,6 +81,15 @@ __global__ void k_refdirs(int m, int p1, int p2, double tau, int w1, int w, doub
 constexpr int OR = 32;
 constexpr int OT = 256;
 
+// rows per block: 32, fewer when m is large (shared memory holds R x m
+// exponentials, at most 32 KB)
+inline int obj_rows(int m)
+{
+    int r = 4096 / m;
+    return r < 1 ? 1 : (r > OR ? OR : r);
+}
+inline size_t obj_smem(int m) { return (size_t)obj_rows(m) * (m + 2) * sizeof(double); }
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
     s = __fadd_rn(a, b);
@@ -90,15 +97,16 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-__global__ void __launch_bounds__(OT) k_objective(RunView v, int row0, int n)
+__global__ void __launch_bounds__(OT) k_objective(RunView v, int row0, int n, int R)
 {
-    __shared__ double sg[OR];
-    __shared__ double sden[OR];
-    __shared__ double se[OR * NSGA3_MAX_M];
+    extern __shared__ double sobj[];
+    double* sg = sobj;        // R
+    double* sden = sg + R;    // R
+    double* se = sden + R;    // R x m
     const int m = v.m, d = v.d, k = m - 1;
-    const int base = blockIdx.x * OR;
+    const int base = blockIdx.x * R;
     const int lane = lane_id(), warp = threadIdx.x >> 5;
-    for (int rr = warp; rr < OR; rr += OT / 32) {
+    for (int rr = warp; rr < R; rr += OT / 32) {
         float sh = 0.0f, sl = 0.0f;
         if (base + rr < n) {
             const float* x = v.X + (size_t)(row0 + base + rr) * d;
@@ -126,7 +134,7 @@ __global__ void __launch_bounds__(OT) k_objective(RunView v, int row0, int n)
         }
         if (lane == 0) sg[rr] = __dadd_rn((double)sh, (double)sl);
     }
-    for (int idx = threadIdx.x; idx < OR * m; idx += OT) {
+    for (int idx = threadIdx.x; idx < R * m; idx += OT) {
         const int rr = idx / m, j = idx - rr * m;
         if (base + rr >= n) continue;
         const float* x = v.X + (size_t)(row0 + base + rr) * d;
@@ -135,13 +143,13 @@ __global__ void __launch_bounds__(OT) k_objective(RunView v, int row0, int n)
         se[idx] = exp(a);
     }
     __syncthreads();
-    if (threadIdx.x < OR && base + threadIdx.x < n) {
+    if (threadIdx.x < R && base + threadIdx.x < n) {
         double den = 0.0;
         for (int t = 0; t < m; ++t) den = __dadd_rn(den, se[threadIdx.x * m + t]);
         sden[threadIdx.x] = den;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < OR * m; idx += OT) {
+    for (int idx = threadIdx.x; idx < R * m; idx += OT) {
         const int rr = idx / m, j = idx - rr * m;
         if (base + rr >= n) continue;
         const double f = __dmul_rn(__dadd_rn(1.0, sg[rr]), __ddiv_rn(se[idx], sden[rr]));
@@ -248,7 +256,8 @@ cudaError_t launch_init(const RunView& v, cudaStream_t s)
     k_init<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_objective<<<(v.N + OR - 1) / OR, OT, 0, s>>>(v, 0, v.N);
+    const int R = obj_rows(v.m);
+    k_objective<<<(v.N + R - 1) / R, OT, obj_smem(v.m), s>>>(v, 0, v.N, R);
     return cudaGetLastError();
 }
 
@@ -259,6 +268,7 @@ cudaError_t launch_vary_eval(const RunView& v, cudaStream_t s)
     k_vary_eval<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_objective<<<(v.N + OR - 1) / OR, OT, 0, s>>>(v, v.N, v.N);
+    const int R = obj_rows(v.m);
+    k_objective<<<(v.N + R - 1) / R, OT, obj_smem(v.m), s>>>(v, v.N, v.N, R);
     return cudaGetLastError();
 }

@@ -26,7 +26,10 @@ cudaError_t launch_dominance(const RunView& v, cudaStream_t s);
 cudaError_t launch_peel(const RunView& v, int num_sms, cudaStream_t s);
 cudaError_t peel_init_attributes();
 cudaError_t launch_norm_ideal(const RunView& v, cudaStream_t s);
-cudaError_t launch_norm_extreme(const RunView& v, cudaStream_t s);
+// extreme points and intercepts: one launch (m <= 10), two (m <= 32) or
+// three with the cooperative elimination (m > 32)
+cudaError_t launch_norm_extreme(const RunView& v, int num_sms, cudaStream_t s);
+cudaError_t norm_init_attributes();
 cudaError_t launch_assoc_prep(const RunView& v, cudaStream_t s);
 // scan + FP64 recheck + per-point argmin + FP64 slow path (4 launches)
 cudaError_t launch_assoc_scan(const RunView& v, int num_sms, cudaStream_t s);

@@ -42,7 +42,7 @@ NoAllocScratch* g_na_ptr[64] = {nullptr};
 __global__ void __launch_bounds__(NA_T) k_rank_noalloc(const float* __restrict__ F, int n, int m,
                                                        int32_t* __restrict__ ranks, NoAllocScratch* S)
 {
-    __shared__ float scol[32 * NSGA3_MAX_M];
+    __shared__ float scol[32 * NSGA3_FAST_M];
     __shared__ int ccnt[32];
     __shared__ unsigned s_ticket;
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nwarps = NA_T / 32;
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(NA_T) k_rank_noalloc(const float* __restrict__
     // warp w: row blocks I = w, w + nwarps, ...; lane = row i, ballot over rows per column
     for (int I = warp; I < W; I += nwarps) {
         const int i = I * 32 + lane;
-        float fi[NSGA3_MAX_M];
+        float fi[NSGA3_FAST_M];
         for (int q = 0; q < m; ++q) fi[q] = i < n ? F[(size_t)i * m + q] : 0.0f;
         uint32_t keep = 0u;
         for (int k = 0; k < 32; ++k) {
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(NA_T) k_rank_noalloc(const float* __restrict__
 
 extern "C" nsga3_status nsga3_rank_noalloc(const float* objs, int n, int m, int32_t* ranks, void* stream)
 {
-    if (!objs || !ranks || n < 1 || n > NA_N || m < 2 || m > NSGA3_MAX_M) return NSGA3_EINVAL;
+    if (!objs || !ranks || n < 1 || n > NA_N || m < 2 || m > NSGA3_FAST_M) return NSGA3_EINVAL;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= 64) {

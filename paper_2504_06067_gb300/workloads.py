@@ -54,6 +54,17 @@ PLAIN_CONFIGS = (SMALL, SCALE, LARGE)
 KNAPSACK = RunConfig("kp_m3_N12800_d500_p158", m=3, d=500, N=12800, p1=158, generations=100)
 
 
+# Objective sweep in the shape of the paper's Table II (N = 800, d = 1000,
+# m = 4 ... 512; its runs use DTLZ3, here the softmax-simplex objective):
+# single-layer Das-Dennis directions with the largest p whose set fits N.
+SWEEP_M = (4, 8, 16, 32, 64, 128, 256, 512)
+
+
+def objective_sweep(N: int = 800, d: int = 1000, generations: int = 100):
+    return [RunConfig("sweep_m%d_N%d_d%d_p%d" % (m, N, d, largest_p(m, N)), m=m, d=d, N=N,
+                      p1=largest_p(m, N), generations=generations) for m in SWEEP_M]
+
+
 def knapsack_instance(m: int, d: int, seed: int = 0):
     """Integer profits and weights uniform in [10, 100] (m x d) and capacities
     of half the total weight per knapsack: the usual random 0-1 multi-

@@ -77,6 +77,19 @@ def test_workspace_bytes_without_gpu(lib):
     assert n.nsga3_workspace_bytes(3, 12, 91, 12, C.byref(o), C.byref(out)) == n.EINVAL
 
 
+def test_many_objectives_workspace(lib):
+    """m up to 512 is accepted (Table II's sweep); m > 32 adds the m x (m+1)
+    elimination matrix; streaming and the knapsack stop at m = 10."""
+    from paper_2504_06067_gb300 import native as n
+    b32 = n.workspace_bytes(32, 1000, 800, 2)
+    b512 = n.workspace_bytes(512, 1000, 800, 1)
+    assert b512 > 512 * 513 * 8 and b32 > 0
+    out = C.c_uint64()
+    for m, o in ((513, n.default_opts()), (11, n.default_opts(streaming=1)),
+                 (11, n.default_opts(problem=1))):
+        assert n.nsga3_workspace_bytes(m, 1000, 800, 1, C.byref(o), C.byref(out)) == n.EINVAL
+
+
 def test_server_create_without_gpu_fails_cleanly(lib):
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():

@@ -129,6 +129,10 @@ def test_bad_arguments(n):
     import ctypes as C
     h = C.c_void_p()
     o = n.default_opts()
-    for args in ((1, 3, 10, 4), (11, 3, 10, 4), (3, 3, 9, 4), (3, 3, 10, 0), (3, 3, 0, 4)):
+    for args in ((1, 3, 10, 4), (513, 3, 10, 4), (3, 3, 9, 4), (3, 3, 10, 0), (3, 3, 0, 4)):
         assert n.nsga3_create(*args, C.byref(o), C.byref(h)) == n.EINVAL
+        assert h.value is None
+    # streaming and the knapsack workload stop at m = 10
+    for o in (n.default_opts(streaming=1), n.default_opts(problem=1)):
+        assert n.nsga3_create(11, 12, 10, 1, C.byref(o), C.byref(h)) == n.EINVAL
         assert h.value is None
