@@ -53,6 +53,8 @@ def parse_args(argv=None):
     p.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep"],
                    default="scale")
     p.add_argument("--runs", type=int, default=64, help="batched: independent runs")
+    p.add_argument("--sweep-m", type=str, default=None,
+                   help="sweep: comma-separated subset of m (default: all of 4 ... 512)")
     p.add_argument("--requests", type=int, default=None, help="served: requests of the stream")
     p.add_argument("--cpu-budget", type=float, default=20.0,
                    help="seconds of oracle work for the cpu_baseline sample")
@@ -667,7 +669,10 @@ def run_sweep(args, world, rank, local):
     n_launch = 0
     sampler = ClockSampler(local)
     sampler.start()
+    only = None if not args.sweep_m else {int(x) for x in args.sweep_m.split(",")}
     for cfg in wl.objective_sweep():
+        if only is not None and cfg.m not in only:
+            continue
         progress("sweep m=%d" % cfg.m)
         W = wl.objective_weights(cfg.m, cfg.seed)
         ctx = n.create(cfg.m, cfg.d, cfg.N, cfg.p1,

@@ -249,7 +249,9 @@ int orc_nds(const float *F, int n2, int m, int N, int full_sort, int32_t *rank)
 /*   extreme e_q = argmin_{i in T} max_r ft_ir / w_qr, w_qr = 1 (r == q),  */
 /*                 1e-6 otherwise; ties -> lowest index;                   */
 /*   solve E b = 1 (rows of E = ft at the extremes) by Gaussian            */
-/*   elimination with partial pivoting (first maximal |pivot|);            */
+/*   elimination with partial pivoting (first maximal |pivot|); back       */
+/*   substitution subtracts the known terms of a row from the highest      */
+/*   column down: b_r = (rhs_r - A_r,m-1 b_m-1 - ... - A_r,r+1 b_r+1)/A_rr; */
 /*   intercept a_q = 1 / b_q;                                              */
 /*   fallback when a pivot is 0, an a_q is not finite or a_q <= 1e-6:      */
 /*   a_q = max_{i in T} ft_iq for every q, and 1 where that is 0.          */
@@ -329,7 +331,7 @@ int orc_normalize(const float *F, const int32_t *rank, int n2, int m, int l,
     if (ok) {
         for (int r = m - 1; r >= 0; --r) {
             double s = rhs[r];
-            for (int cc = r + 1; cc < m; ++cc) {
+            for (int cc = m - 1; cc > r; --cc) {
                 double prod = AQ(r, cc) * b[cc];
                 s = s - prod;
             }
@@ -450,7 +452,7 @@ int orc_normalize_hist(const float *F, const int32_t *rank, int n2, int m, int l
     if (ok) {
         for (int r = m - 1; r >= 0; --r) {
             double sum = rhs[r];
-            for (int cc = r + 1; cc < m; ++cc) {
+            for (int cc = m - 1; cc > r; --cc) {
                 double prod = AQ(r, cc) * b[cc];
                 sum = sum - prod;
             }

@@ -54,6 +54,7 @@ struct Ctrl {
     int32_t passes;          // peel passes (kernel launches) in the last selection
     uint32_t pfs[3];         // front sizes of peel passes k mod 3
     uint32_t bar_gen;        // grid barrier of the peel: generation
+    uint32_t sbar;           // arrivals at the barriers of the cooperative elimination
     int32_t nT;              // |S u F_l| (association set)
     int32_t Lstar;           // niche level threshold L*
     int32_t rlev;            // refs taken at level L*
@@ -135,6 +136,7 @@ struct RunView {
     const double* nz;      // w
     const float* Zh;       // w x M4
     const float* Wobj;     // m x (m-1)
+    const float* Wt;       // (m-1) x m  W transposed (m > NSGA3_FAST_M)
     // association scan: references reordered into compact blocks of 32
     int nblk;              // ceil(w / 32)
     const float* blk_c;    // nblk x M4  unit cone centres (FP32)
@@ -145,14 +147,21 @@ struct RunView {
     int2* cand;            // cand_cap   (T slot, reference)
     int cand_cap;
     int32_t* slow;         // n2         T slots for the full FP64 scan
+    double* cdist;         // cand_cap   FP64 distance of each candidate (m > NSGA3_FAST_M)
     float* he;             // m x m      remembered extreme vectors (history), row q for axis q
     // m > NSGA3_FAST_M: extreme points by entry keys, then per-axis blocks
     unsigned long long* ekey;  // (n2 + m) x 2  ASF keys of the largest / second-largest f~
     int32_t* er1;              // n2 + m        objective of the largest f~
+    double* nadv;              // m     max f~ per axis (nadir fallback)
     // m > NSGA3_WARP_M: intercepts by the cooperative elimination
     double* amat;          // m x (m + 1)  [E - z* | 1], rows in original order
     float* etmp;           // m x m        new extreme vectors (copied to he at the end)
-    double* nadv;          // m            max f~ per axis (nadir fallback)
+    // m > NSGA3_FAST_M with few tiles: the objective chunks of a tile are
+    // split over dom_ks CTAs, which OR their sign masks into dpa / dpb
+    // (NW x ld, laid out like Dom; zero between selections)
+    int dom_ks;
+    uint32_t* dpa;         // "some f_i > f_j" bits of row i against column block jb
+    uint32_t* dpb;         // "some f_j > f_i"
 };
 
 // ------------------------------------------------------------ Philox ------
@@ -257,6 +266,33 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
     unsigned x;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(x) : "l"(p) : "memory");
     return x;
+}
+
+// Counting barrier: the k-th barrier of a launch waits until *ctr reaches
+// k * gridDim.x (*ctr is zero at launch): one atomic on the arrival path and
+// a tight poll, for kernels that meet at a barrier many times per launch.
+__device__ __forceinline__ bool grid_sync_count(Ctrl* c, unsigned* ctr, unsigned target, int* s_ok)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        if (atomicAdd(ctr, 1u) + 1u < target) {
+            const unsigned long long t0 = global_ns();
+            unsigned it = 0;
+            while (ld_acquire(ctr) < target) {
+                if ((++it & 1023u) == 0u && (global_ns() - t0 > GRID_WAIT_NS || it > (1u << 30))) {
+                    set_status(c, DEV_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
 }
 
 __device__ __forceinline__ bool grid_sync(Ctrl* c, int* s_ok)

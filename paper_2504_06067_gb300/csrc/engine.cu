@@ -64,10 +64,22 @@ struct nsga3_ctx {
 
 namespace {
 
-// kernels of one selection / one generation: m > 10 adds the extreme-point
-// key kernel, m > 32 also the cooperative elimination
-int select_launches(int m) { return 18 + (m > NSGA3_FAST_M ? 1 : 0) + (m > NSGA3_WARP_M ? 1 : 0); }
-int generation_launches(int m) { return select_launches(m) + 3; }
+// kernels of one selection / one generation: m > 10 adds five (ideal point,
+// extreme-point keys and reduction, |f'|, candidate distances), m > 32 the
+// cooperative elimination, and a split dominance build (few tiles) its
+// finishing kernel
+int select_launches(const nsga3_ctx* ctx)
+{
+    const int m = ctx->m;
+    return 18 + (m > NSGA3_FAST_M ? 5 : 0) + (m > NSGA3_WARP_M ? 1 : 0) + (ctx->v.dom_ks > 1 ? 1 : 0);
+}
+// the softmax-simplex objective's dot-product kernel (m > 10)
+int objective_dot_launches(const nsga3_ctx* ctx) { return ctx->m > NSGA3_FAST_M && ctx->v.problem == 0 ? 1 : 0; }
+int generation_launches(const nsga3_ctx* ctx)
+{
+    // + variation, objective, gather, commit
+    return select_launches(ctx) + 3 + objective_dot_launches(ctx);
+}
 
 nsga3_status fail(nsga3_ctx* c, nsga3_status s, const char* fmt, ...)
 {
@@ -406,6 +418,17 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     v.ext_parts = (n2 + 127) / 128;
     if (v.ext_parts > 2 * ctx->num_sms) v.ext_parts = 2 * ctx->num_sms;
     if (v.ext_parts > 512) v.ext_parts = 512;
+    // m > 10 with fewer tiles than two per SM: split each tile's objective
+    // chunks over dom_ks CTAs (k_dominance_gen + k_dom_finish)
+    v.dom_ks = 1;
+    if (m > NSGA3_FAST_M) {
+        const long long T = ld / NSGA3_TILE, tiles = T * (T + 1) / 2;
+        const long long nch = (m + 15) / 16, want = 2LL * ctx->num_sms;
+        if (tiles < want && nch > 1) {
+            const long long ks = (want + tiles - 1) / tiles;
+            v.dom_ks = (int)(ks < nch ? ks : nch);
+        }
+    }
 
     AL(v.ctrl, 1);
     AL(v.X, (size_t)n2 * d);
@@ -450,13 +473,20 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     AL(v.slow, n2);
     AL(v.he, (size_t)m * m);
     if (m > NSGA3_FAST_M) {
+        AL(v.cdist, v.cand_cap);
+        AL(v.nadv, m);
+    }
+    if (v.dom_ks > 1) {
+        AL(v.dpa, (size_t)NW * ld);
+        AL(v.dpb, (size_t)NW * ld);
+    }
+    if (m > NSGA3_FAST_M) {
         AL(v.ekey, 2 * (size_t)(n2 + m));
         AL(v.er1, (size_t)(n2 + m));
     }
     if (m > NSGA3_WARP_M) {
         AL(v.amat, (size_t)m * (m + 1));
         AL(v.etmp, (size_t)m * m);
-        AL(v.nadv, m);
     }
     float* bc;
     float2* br;
@@ -478,6 +508,11 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     AL(nz, w);
     AL(Zh, (size_t)w * M4);
     AL(Wd, (size_t)m * (m - 1));
+    if (m > NSGA3_FAST_M && v.problem == 0) {
+        float* Wt;
+        AL(Wt, (size_t)m * (m - 1));
+        v.Wt = Wt;
+    }
     if (v.problem == 1) {
         int32_t *kp, *kw, *kc, *kt, *ko;
         AL(kp, (size_t)m * d);
@@ -521,6 +556,10 @@ nsga3_status setup(nsga3_ctx* ctx)
     cudaStream_t s = ctx->cap;
     CK(cudaMemsetAsync(v.ctrl, 0, sizeof(Ctrl), s));
     if (!v.streaming) CK(cudaMemsetAsync(v.Dom, 0, (size_t)NW * ld * sizeof(uint32_t), s));
+    if (v.dom_ks > 1) {
+        CK(cudaMemsetAsync(v.dpa, 0, (size_t)NW * ld * sizeof(uint32_t), s));
+        CK(cudaMemsetAsync(v.dpb, 0, (size_t)NW * ld * sizeof(uint32_t), s));
+    }
     CK(cudaMemsetAsync(v.rank, 0, (size_t)N * sizeof(int32_t), s));
     CK(cudaMemsetAsync(v.X, 0, (size_t)n2 * d * sizeof(float), s));
     CK(cudaMemsetAsync(v.F, 0, (size_t)ld * m * sizeof(float), s));
@@ -530,8 +569,17 @@ nsga3_status setup(nsga3_ctx* ctx)
     CK(launch_nan_pad(v, s));
     CK(launch_nan_pad(ctx->vs, s));
     CK(launch_refdirs(v, ctx->p1, ctx->p2, ctx->tau, Zd, nz, Zh, s));
-    if (ctx->has_obj && v.problem == 0)
+    std::vector<float> Wt_host;
+    if (ctx->has_obj && v.problem == 0) {
         CK(cudaMemcpyAsync(Wd, ctx->opts.W, (size_t)m * (m - 1) * sizeof(float), cudaMemcpyHostToDevice, s));
+        if (v.Wt) {  // (m-1) x m: the objective kernel reads a row of W^T per variable
+            Wt_host.resize((size_t)m * (m - 1));
+            for (int j = 0; j < m; ++j)
+                for (int e = 0; e < m - 1; ++e) Wt_host[(size_t)e * m + j] = ctx->opts.W[(size_t)j * (m - 1) + e];
+            CK(cudaMemcpyAsync(const_cast<float*>(v.Wt), Wt_host.data(), Wt_host.size() * sizeof(float),
+                               cudaMemcpyHostToDevice, s));
+        }
+    }
     std::vector<int32_t> kp_order, kp_total;
     if (ctx->has_obj && v.problem == 1) {
         kp_repair_order(ctx->opts.kp_profit, ctx->opts.kp_weight, m, d, kp_order);
@@ -704,7 +752,7 @@ nsga3_status ctx_create(int m, int d, int N, int ref_divisions, const nsga3_opts
 nsga3_status ctx_workspace_bytes(int m, int d, int N, int ref_divisions, const nsga3_opts* opts, int num_sms,
                                  size_t* bytes, std::string* err)
 {
-    nsga3_ctx c;
+    nsga3_ctx c{};
     c.count_only = true;
     nsga3_status st = ctx_fields(&c, m, d, N, ref_divisions, opts);
     if (!st) {
@@ -889,7 +937,7 @@ nsga3_status nsga3_select(nsga3_ctx* ctx, const float* objs, int32_t* ranks, int
     } else {
         CK(cudaGraphLaunch(ctx->gx_select, s));
     }
-    ctx->host_launches += select_launches(ctx->m);
+    ctx->host_launches += select_launches(ctx);
     CK(cudaMemcpyAsync(ranks, ctx->vs.rank2, (size_t)ctx->n2 * sizeof(int32_t), cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(selected, ctx->vs.sel, (size_t)ctx->N * sizeof(int32_t), cudaMemcpyDefault, s));
     ctx->last_kind = 1;
@@ -905,7 +953,7 @@ nsga3_status nsga3_init(nsga3_ctx* ctx, void* stream)
     CK(cudaMemsetAsync(&ctx->v.ctrl->hvalid, 0, sizeof(int32_t), s));  // a new run starts without history
     k_set_gen<<<1, 1, 0, s>>>(ctx->v.ctrl, 0u);
     CK(cudaGetLastError());
-    ctx->host_launches += 3;
+    ctx->host_launches += 3 + objective_dot_launches(ctx);
     return NSGA3_OK;
 }
 
@@ -914,7 +962,7 @@ nsga3_status nsga3_vary(nsga3_ctx* ctx, void* stream)
     if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
     if (!ctx->has_obj) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W or the knapsack arrays were NULL)");
     CK(launch_vary_eval(ctx->v, (cudaStream_t)stream));
-    ctx->host_launches += 2;
+    ctx->host_launches += 2 + objective_dot_launches(ctx);
     return NSGA3_OK;
 }
 
@@ -928,7 +976,7 @@ nsga3_status nsga3_step(nsga3_ctx* ctx, void* stream)
     } else {
         CK(cudaGraphLaunch(ctx->gx_step, (cudaStream_t)stream));
     }
-    ctx->host_launches += generation_launches(ctx->m);
+    ctx->host_launches += generation_launches(ctx);
     ctx->last_kind = 2;
     return NSGA3_OK;
 }
@@ -974,7 +1022,7 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
     for (int g = 0; g < generations % BATCH_GENS; ++g) CK(cudaGraphLaunch(ctx->gx_batch1, (cudaStream_t)stream));
     for (int r = 0; r < n; ++r) {
         ctxs[r]->last_kind = 3;
-        ctxs[r]->host_launches += (long long)generation_launches(ctxs[r]->m) * generations;
+        ctxs[r]->host_launches += (long long)generation_launches(ctxs[r]) * generations;
     }
     return NSGA3_OK;
 }
@@ -1104,7 +1152,7 @@ nsga3_status nsga3_last_launches(nsga3_ctx* ctx, int32_t* launches)
     // is needed; one or two more for m > 10), compaction (+ finite check
     // for a selection; + variation, objective, gather, commit for a
     // generation)
-    *launches = (ctx->last_kind == 1) ? select_launches(ctx->m) : generation_launches(ctx->m);
+    *launches = (ctx->last_kind == 1) ? select_launches(ctx) : generation_launches(ctx);
     return NSGA3_OK;
 }
 

@@ -34,8 +34,7 @@
 // their argmin.
 // A point whose candidate list overflows is rescanned in FP64 over all
 // references by a whole CTA (k_assoc_slow), as is every point in debug mode.
-// m > 10: no pruning; the cosines come from shared-memory tiles of points
-// and references (k_assoc_scan_gen), with the same band and FP64 kernels.
+// m > 10: no pruning (k_assoc_scan_gen), the same band and FP64 kernels.
 #include "kernels.cuh"
 
 namespace {
@@ -49,6 +48,22 @@ __device__ __forceinline__ double perp_dist(const double* fp, double nf, const d
 {
     if (nf == 0.0) return 0.0;
     double dot = 0.0;
+    for (int q = 0; q < m; ++q) dot = __dadd_rn(dot, __dmul_rn(fp[q], Zj[q]));
+    const double den = __dmul_rn(nf, nzj);
+    const double cth = __ddiv_rn(dot, den);
+    double one_m = __dsub_rn(1.0, __dmul_rn(cth, cth));
+    if (one_m < 0.0) one_m = 0.0;
+    return __dmul_rn(nf, __dsqrt_rn(one_m));
+}
+
+// the same for a run-time m with both rows in memory: sixteen loads of
+// each row in flight
+__device__ __forceinline__ double perp_dist_mem(const double* fp, double nf, const double* Zj, double nzj,
+                                                int m)
+{
+    if (nf == 0.0) return 0.0;
+    double dot = 0.0;
+#pragma unroll 16
     for (int q = 0; q < m; ++q) dot = __dadd_rn(dot, __dmul_rn(fp[q], Zj[q]));
     const double den = __dmul_rn(nf, nzj);
     const double cth = __ddiv_rn(dot, den);
@@ -392,45 +407,75 @@ __global__ void __launch_bounds__(AB) k_assoc_slow(RunView v)
 
 // ---------------------------------------------------------------------------
 // m > NSGA3_FAST_M: runtime m, no pruning (the cone bounds lose their grip in
-// many dimensions).  The FP32 cosines of GPTS points against every
-// reference are formed from shared-memory tiles (32 references x GKC
-// objectives, the points' unit vectors likewise) and fed to the same
-// candidate band; the FP64 kernels read f' from memory.
+// many dimensions).  A CTA keeps the unit vectors of GPP points in shared
+// memory; each warp forms the FP32 cosines of all of them against its
+// tiles of 32 references (a lane per reference, read as float4 through the
+// read-only cache) and feeds them to the same candidate band; the FP64
+// kernels read f' from memory and keep their pipe full (a thread per point
+// or per candidate for the sequential sums).
 
-__global__ void __launch_bounds__(PB) k_assoc_prep_gen(RunView v)
+// f' = (f - z*) / a for every element (a thread per element: the divisions
+// spread over every SM), then per point (a thread per point: the FP64 pipe
+// serves 32 points per warp instruction) the squares added left to right,
+// |f'| and the FP32 unit vector
+__global__ void __launch_bounds__(256) k_assoc_prep_elem(RunView v)
 {
     Ctrl* c = v.ctrl;
     if (skip_niche(c)) return;
-    const int s = blockIdx.x * PB + threadIdx.x;
-    if (s >= c->nT) return;
-    const int m = v.m, M4 = v.M4;
+    const int m = v.m;
+    const long long e = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (e >= (long long)c->nT * m) return;
+    const int s = (int)(e / m), q = (int)(e - (long long)s * m);
     const int i = v.Tlist[s];
-    double* fp = v.fprime + (size_t)s * m;
+    v.fprime[e] = __ddiv_rn(__dsub_rn((double)v.F[(size_t)i * m + q], c->zstar[q]), c->a[q]);
+}
+
+// one warp per CTA, 32 points: the rows come in through a 32 x 32 tile
+// (coalesced loads), lane p adds the squares of point p left to right
+__global__ void __launch_bounds__(32) k_assoc_prep_norm(RunView v)
+{
+    __shared__ double tile[32][33];
+    Ctrl* c = v.ctrl;
+    if (skip_niche(c)) return;
+    const int nT = c->nT, s0 = blockIdx.x * 32, lane = threadIdx.x;
+    if (s0 >= nT) return;
+    const int m = v.m, M4 = v.M4, np = min(32, nT - s0);
+    const double* base = v.fprime + (size_t)s0 * m;
     double ss = 0.0;
-    for (int q = 0; q < m; ++q) {
-        const double ft = __dsub_rn((double)v.F[(size_t)i * m + q], c->zstar[q]);
-        const double x = __ddiv_rn(ft, c->a[q]);
-        fp[q] = x;
-        ss = __dadd_rn(ss, __dmul_rn(x, x));
+    for (int q0 = 0; q0 < m; q0 += 32) {
+        const int nq = min(32, m - q0);
+#pragma unroll 8
+        for (int p = 0; p < np; ++p) tile[p][lane] = lane < nq ? base[(size_t)p * m + q0 + lane] : 0.0;
+        __syncwarp();
+        if (lane < np)
+            for (int t = 0; t < nq; ++t) ss = __dadd_rn(ss, __dmul_rn(tile[lane][t], tile[lane][t]));
+        __syncwarp();
     }
     const double nf = __dsqrt_rn(ss);
-    v.fnorm[s] = nf;
+    if (lane < np) v.fnorm[s0 + lane] = nf;
     const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
-    for (int q = 0; q < M4; ++q) v.uhat[(size_t)s * M4 + q] = q < m ? __double2float_rn(fp[q] * inv) : 0.0f;
+    for (int p = 0; p < np; ++p) {
+        const double ip = __shfl_sync(0xffffffffu, inv, p);
+#pragma unroll 8
+        for (int q = lane; q < M4; q += 32)
+            v.uhat[(size_t)(s0 + p) * M4 + q] = q < m ? __double2float_rn(base[(size_t)p * m + q] * ip) : 0.0f;
+    }
 }
+
+constexpr int GW = 8;  // warps per CTA of the m > NSGA3_FAST_M scan
 
 // candidate-list update of one point with a block of 32 cosines (qh, j) per
 // lane (j = -1: no reference): keeps every reference within band of the best
 // so far; a list that cannot hold them marks the point as overflowed
 __device__ __forceinline__ void band_take(float qh, int j, float band, float& best, int& nl, bool& ovf,
-                                          int* lj, float* lq)
+                                          int* lj, float* lq, int cap)
 {
     const int lane = lane_id();
     const float wm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(qh, 0.0f))));
     best = fmaxf(best, wm);
     const bool keep = j >= 0 && qh >= best - band;
     unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (nl + __popc(bal) > LC) {  // drop entries that fell out of the band
+    if (nl + __popc(bal) > cap) {  // drop entries that fell out of the band
         __syncwarp();
         int kept = 0;
         for (int e0 = 0; e0 < nl; e0 += 32) {
@@ -453,7 +498,7 @@ __device__ __forceinline__ void band_take(float qh, int j, float band, float& be
             __syncwarp();
         }
         nl = kept;
-        if (nl + __popc(bal) > LC) {
+        if (nl + __popc(bal) > cap) {
             ovf = true;
             bal = 0u;
         }
@@ -467,128 +512,162 @@ __device__ __forceinline__ void band_take(float qh, int j, float band, float& be
     __syncwarp();
 }
 
-constexpr int GPW = 2;           // points per warp
-constexpr int GPTS = 8 * GPW;    // points per CTA
-constexpr int GKC = 64;          // objectives per staged chunk
+constexpr int GPP = 8;   // points per CTA (every warp works on all of them)
+constexpr int LCW = 64;  // candidate slots per warp and point
 
-__global__ void __launch_bounds__(AB) k_assoc_scan_gen(RunView v)
+// dynamic shared memory: the points' unit vectors (GPP x M4) and the lists
+size_t scan_gen_smem(int M4) { return (size_t)GPP * M4 * 4 + (size_t)GW * GPP * LCW * 8; }
+
+// The CTA's warps split the references (warp w takes the tiles of 32
+// references w, w + GW, ...) and keep a candidate list per point; the lists
+// are then merged against the best cosine over all warps.
+__global__ void __launch_bounds__(GW * 32) k_assoc_scan_gen(RunView v)
 {
-    __shared__ float Us[GPTS][GKC + 1];
-    __shared__ float Zs[32][GKC + 1];
-    __shared__ int s_lj[8][GPW][LC];
-    __shared__ float s_lq[8][GPW][LC];
+    extern __shared__ __align__(16) float sgen[];
+    __shared__ float s_best[GW][GPP];
+    __shared__ int s_nl[GW][GPP];
+    __shared__ int s_ovf[GW][GPP];
     Ctrl* c = v.ctrl;
     if (skip_niche(c)) return;
     const int nT = c->nT, m = v.m, M4 = v.M4, w = v.w;
     const int lane = lane_id(), warp = threadIdx.x >> 5, tid = threadIdx.x;
+    float* Us = sgen;                                                // GPP x M4
+    int* lists = reinterpret_cast<int*>(sgen + (size_t)GPP * M4);   // GW x GPP x (LCW ints, LCW floats)
     const float band = 2.0f * (float)(m + 4) * 5.9604644775390625e-08f + 1e-12f;
-    const bool one_chunk = m <= GKC;
-    for (int g0 = blockIdx.x * GPTS; g0 < nT; g0 += gridDim.x * GPTS) {  // CTA-uniform
-        float best[GPW];
-        int nl[GPW];
-        bool ovf[GPW], live[GPW];
+    for (int g0 = blockIdx.x * GPP; g0 < nT; g0 += gridDim.x * GPP) {  // CTA-uniform
+        __syncthreads();  // the previous group is merged
+        for (int e = tid; e < GPP * M4; e += GW * 32) {
+            const int p = e / M4;
+            Us[e] = g0 + p < nT ? v.uhat[(size_t)g0 * M4 + e] : 0.0f;
+        }
+        __syncthreads();
+        float best[GPP];
+        int nl[GPP];
+        bool ovf[GPP], live[GPP];
 #pragma unroll
-        for (int p = 0; p < GPW; ++p) {
-            const int pt = g0 + warp * GPW + p;
+        for (int p = 0; p < GPP; ++p) {
             best[p] = -4.0f;
             nl[p] = 0;
             ovf[p] = false;
-            live[p] = pt < nT && v.fnorm[pt] != 0.0;  // |f'| = 0: every distance is 0
+            live[p] = g0 + p < nT && v.fnorm[g0 + p] != 0.0;  // |f'| = 0: every distance is 0
         }
-        if (one_chunk) {
-            __syncthreads();
-            for (int e = tid; e < GPTS * GKC; e += AB) {
-                const int p = e / GKC, k = e - p * GKC;
-                Us[p][k] = (g0 + p < nT && k < m) ? v.uhat[(size_t)(g0 + p) * M4 + k] : 0.0f;
-            }
-        }
-        for (int r0 = 0; r0 < w; r0 += 32) {
-            float acc[GPW];
+        for (int r0 = warp * 32; r0 < w; r0 += GW * 32) {
+            const int j = r0 + lane;
+            const float4* z4 = reinterpret_cast<const float4*>(v.Zh + (size_t)(j < w ? j : w - 1) * M4);
+            float acc[GPP];
 #pragma unroll
-            for (int p = 0; p < GPW; ++p) acc[p] = 0.0f;
-            for (int k0 = 0; k0 < m; k0 += GKC) {
-                __syncthreads();  // the previous tiles are consumed
-                if (!one_chunk)
-                    for (int e = tid; e < GPTS * GKC; e += AB) {
-                        const int p = e / GKC, k = e - p * GKC;
-                        Us[p][k] = (g0 + p < nT && k0 + k < m) ? v.uhat[(size_t)(g0 + p) * M4 + k0 + k] : 0.0f;
-                    }
-                for (int e = tid; e < 32 * GKC; e += AB) {
-                    const int jj = e / GKC, k = e - jj * GKC;
-                    Zs[jj][k] = (r0 + jj < w && k0 + k < m) ? v.Zh[(size_t)(r0 + jj) * M4 + k0 + k] : 0.0f;
-                }
-                __syncthreads();
-                const int kn = min(GKC, m - k0);
-                for (int k = 0; k < kn; ++k) {
-                    const float z = Zs[lane][k];
+            for (int p = 0; p < GPP; ++p) acc[p] = 0.0f;
+#pragma unroll 8
+            for (int k4 = 0; k4 < M4 / 4; ++k4) {
+                const float4 z = __ldg(z4 + k4);
 #pragma unroll
-                    for (int p = 0; p < GPW; ++p) acc[p] = fmaf(Us[warp * GPW + p][k], z, acc[p]);
+                for (int p = 0; p < GPP; ++p) {
+                    const float4 u = reinterpret_cast<const float4*>(Us + (size_t)p * M4)[k4];
+                    acc[p] = fmaf(u.x, z.x, acc[p]);
+                    acc[p] = fmaf(u.y, z.y, acc[p]);
+                    acc[p] = fmaf(u.z, z.z, acc[p]);
+                    acc[p] = fmaf(u.w, z.w, acc[p]);
                 }
             }
-            const int j = r0 + lane < w ? r0 + lane : -1;
 #pragma unroll
-            for (int p = 0; p < GPW; ++p)
-                if (live[p]) band_take(acc[p], j, band, best[p], nl[p], ovf[p], s_lj[warp][p], s_lq[warp][p]);
+            for (int p = 0; p < GPP; ++p)
+                if (live[p]) {
+                    int* lj = lists + (size_t)(warp * GPP + p) * 2 * LCW;
+                    band_take(acc[p], j < w ? j : -1, band, best[p], nl[p], ovf[p], lj,
+                              reinterpret_cast<float*>(lj + LCW), LCW);
+                }
         }
+        if (lane == 0)
 #pragma unroll
-        for (int p = 0; p < GPW; ++p) {
-            const int pt = g0 + warp * GPW + p;
-            if (pt >= nT) continue;
-            if (!live[p]) {
-                if (lane == 0) v.arun[pt] = make_int2(0, 0);
-                continue;
+            for (int p = 0; p < GPP; ++p) {
+                s_best[warp][p] = best[p];
+                s_nl[warp][p] = nl[p];
+                s_ovf[warp][p] = ovf[p] ? 1 : 0;
             }
-            const int* lj = s_lj[warp][p];
-            const float* lq = s_lq[warp][p];
-            int cnt = 0;
-            for (int e0 = 0; e0 < nl[p]; e0 += 32) {
+        __syncthreads();
+        // merge: warp p takes point p
+        const int p = warp;
+        const int pt = g0 + p;
+        if (p >= GPP || pt >= nT) continue;
+        if (!live[p]) {
+            if (lane == 0) v.arun[pt] = make_int2(0, 0);
+            continue;
+        }
+        float gb = s_best[0][p];
+        bool govf = false;
+        for (int q = 0; q < GW; ++q) {
+            gb = fmaxf(gb, s_best[q][p]);
+            govf = govf || s_ovf[q][p];
+        }
+        int cnt = 0;
+        for (int q = 0; q < GW; ++q) {
+            const int* lj = lists + (size_t)(q * GPP + p) * 2 * LCW;
+            const float* lq = reinterpret_cast<const float*>(lj + LCW);
+            const int n = s_nl[q][p];
+            for (int e0 = 0; e0 < n; e0 += 32) {
                 const int e = e0 + lane;
-                cnt += __popc(__ballot_sync(0xffffffffu, e < nl[p] && lq[e] >= best[p] - band));
+                cnt += __popc(__ballot_sync(0xffffffffu, e < n && lq[e] >= gb - band));
             }
-            int start = 0;
-            if (lane == 0 && !ovf[p]) start = atomicAdd(&c->ncand, cnt);
-            start = __shfl_sync(0xffffffffu, start, 0);
-            if (ovf[p] || start + cnt > v.cand_cap) {
-                if (lane == 0) {
-                    v.arun[pt] = make_int2(-1, 0);
-                    v.slow[atomicAdd(&c->nslow, 1)] = pt;
-                }
-                __syncwarp();
-                continue;
+        }
+        int start = 0;
+        if (lane == 0 && !govf) start = atomicAdd(&c->ncand, cnt);
+        start = __shfl_sync(0xffffffffu, start, 0);
+        if (govf || start + cnt > v.cand_cap) {
+            if (lane == 0) {
+                v.arun[pt] = make_int2(-1, 0);
+                v.slow[atomicAdd(&c->nslow, 1)] = pt;
             }
-            int off = 0;
-            for (int e0 = 0; e0 < nl[p]; e0 += 32) {
+            continue;
+        }
+        int off = 0;
+        for (int q = 0; q < GW; ++q) {
+            const int* lj = lists + (size_t)(q * GPP + p) * 2 * LCW;
+            const float* lq = reinterpret_cast<const float*>(lj + LCW);
+            const int n = s_nl[q][p];
+            for (int e0 = 0; e0 < n; e0 += 32) {
                 const int e = e0 + lane;
-                const bool k2 = e < nl[p] && lq[e] >= best[p] - band;
+                const bool k2 = e < n && lq[e] >= gb - band;
                 const unsigned b2 = __ballot_sync(0xffffffffu, k2);
                 if (k2) v.cand[start + off + __popc(b2 & ((1u << lane) - 1u))] = make_int2(pt, lj[e]);
                 off += __popc(b2);
             }
-            if (lane == 0) v.arun[pt] = make_int2(start, cnt);
-            __syncwarp();
         }
+        if (lane == 0) v.arun[pt] = make_int2(start, cnt);
     }
 }
 
-__global__ void __launch_bounds__(FB) k_assoc_final_gen(RunView v)
+// a thread per candidate (the FP64 pipe of a warp instruction serves 32
+// candidates): its FP64 distance, the same left-to-right evaluation
+__global__ void __launch_bounds__(32) k_assoc_cand_dist(RunView v)
 {
     Ctrl* c = v.ctrl;
     if (skip_niche(c)) return;
-    const int pt = blockIdx.x * FB + threadIdx.x;
+    const int e = blockIdx.x * 32 + threadIdx.x;
+    // ncand counts reservations, also those that did not fit (their points
+    // went to the slow path): only the first cand_cap slots exist
+    if (e >= min(c->ncand, v.cand_cap)) return;
+    const int2 pj = v.cand[e];
+    const double nf = v.fnorm[pj.x];
+    v.cdist[e] = perp_dist_mem(v.fprime + (size_t)pj.x * v.m, nf, v.Zd + (size_t)pj.y * v.m, v.nz[pj.y], v.m);
+}
+
+// a thread per point: lexicographic (d, j) minimum over its candidates
+__global__ void __launch_bounds__(256) k_assoc_final_gen(RunView v)
+{
+    Ctrl* c = v.ctrl;
+    if (skip_niche(c)) return;
+    const int pt = blockIdx.x * 256 + threadIdx.x;
     if (pt >= c->nT) return;
     const int2 run = v.arun[pt];
     if (run.x < 0) return;  // slow path
-    const int m = v.m;
     double bd = 0.0;
     int bj = 0;
-    const double nf = v.fnorm[pt];
-    if (nf != 0.0) {
-        const double* fp = v.fprime + (size_t)pt * m;
+    if (v.fnorm[pt] != 0.0) {
         bd = CUDART_INF;
         bj = 0x7fffffff;
         for (int e = run.x; e < run.x + run.y; ++e) {
+            const double d = v.cdist[e];
             const int j = v.cand[e].y;
-            const double d = perp_dist(fp, nf, v.Zd + (size_t)j * m, v.nz[j], m);
             if (lex_less(d, j, bd, bj)) {
                 bd = d;
                 bj = j;
@@ -645,8 +724,13 @@ cudaError_t launch_assoc_prep(const RunView& v, cudaStream_t s)
     case 10: k_assoc_prep<10><<<g, PB, 0, s>>>(v); break;
     default:
         if (v.m < 2 || v.m > NSGA3_MAX_M) return cudaErrorInvalidValue;
-        k_assoc_prep_gen<<<g, PB, 0, s>>>(v);
+    {
+        k_assoc_prep_elem<<<(unsigned)(((long long)v.n2 * v.m + 255) / 256), 256, 0, s>>>(v);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_assoc_prep_norm<<<(v.n2 + 31) / 32, 32, 0, s>>>(v);
         break;
+    }
     }
     return cudaGetLastError();
 }
@@ -666,12 +750,16 @@ cudaError_t launch_assoc_scan(const RunView& v, int num_sms, cudaStream_t s)
     default: break;
     }
     if (v.m < 2 || v.m > NSGA3_MAX_M) return cudaErrorInvalidValue;
-    int blocks = (v.n2 + GPTS - 1) / GPTS;
+    int blocks = (v.n2 + GPP - 1) / GPP;
     if (blocks > num_sms * 8) blocks = num_sms * 8;
-    k_assoc_scan_gen<<<blocks, AB, 0, s>>>(v);
+    k_assoc_scan_gen<<<blocks, GW * 32, scan_gen_smem(v.M4), s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_assoc_final_gen<<<(v.n2 + FB - 1) / FB, FB, 0, s>>>(v);
+    // one warp per CTA: the few candidates of a selection spread over every SM
+    k_assoc_cand_dist<<<(v.cand_cap + 31) / 32, 32, 0, s>>>(v);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_assoc_final_gen<<<(v.n2 + 255) / 256, 256, 0, s>>>(v);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_assoc_slow<0><<<num_sms, AB, 0, s>>>(v);
@@ -703,5 +791,8 @@ cudaError_t assoc_init_attributes()
     if (e == cudaSuccess) e = attr_m<8>(SCAN_SMEM_MAX);
     if (e == cudaSuccess) e = attr_m<9>(SCAN_SMEM_MAX);
     if (e == cudaSuccess) e = attr_m<10>(SCAN_SMEM_MAX);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_assoc_scan_gen, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)scan_gen_smem(NSGA3_MAX_M));
     return e;
 }

@@ -239,8 +239,24 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
 // a zero difference has a clear sign bit and changes neither mask).  Each
 // lane keeps, per row and column block, the 32-bit masks A ("some
 // f_i > f_j") and B ("some f_j > f_i") OR-ed over the chunks; the bits
-// follow from them as in the specialised kernel.
+// follow from them as in the specialised kernel.  With v.dom_ks > 1 the
+// chunks of a tile are split over gridDim.y CTAs that OR their masks into
+// dpa / dpb, and k_dom_finish forms the bits.
 constexpr int MC = 16;
+
+// one-direction test of row block ib against column block jb (warp-wide):
+// every f_i0 of the rows below every f_j0 of the columns
+__device__ __forceinline__ bool one_direction(const RunView& v, int ib, int jb)
+{
+    float rmax = v.Fp[(size_t)(ib * 32 + lane_id()) * v.m];
+    float cmin = v.Fp[(size_t)(jb * 32 + lane_id()) * v.m];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+    }
+    return jb > ib && rmax < cmin;
+}
 
 __global__ void __launch_bounds__(256) k_dominance_gen(RunView v)
 {
@@ -262,22 +278,12 @@ __global__ void __launch_bounds__(256) k_dominance_gen(RunView v)
     const int rp = warp & 3, ch = warp >> 2;
     const int ib0 = ti * 8 + 2 * rp, ib1 = ib0 + 1;
     // one-direction blocks from f_0 alone (as in the specialised kernel)
-    float rmax0 = v.Fp[(size_t)(r0 + 2 * rp * 32 + lane) * m];
-    float rmax1 = v.Fp[(size_t)(r0 + (2 * rp + 1) * 32 + lane) * m];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        rmax0 = fmaxf(rmax0, __shfl_xor_sync(0xffffffffu, rmax0, o));
-        rmax1 = fmaxf(rmax1, __shfl_xor_sync(0xffffffffu, rmax1, o));
-    }
     unsigned fastm = 0u;  // bit 2*cbi + r: one-direction block
 #pragma unroll
     for (int cbi = 0; cbi < 4; ++cbi) {
         const int jb = tj * 8 + ch * 4 + cbi;
-        float cmin = v.Fp[(size_t)(c0 + (ch * 4 + cbi) * 32 + lane) * m];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
-        if (jb != ib0 && rmax0 < cmin) fastm |= 1u << (2 * cbi);
-        if (jb > ib1 && rmax1 < cmin) fastm |= 2u << (2 * cbi);
+        if (one_direction(v, ib0, jb)) fastm |= 1u << (2 * cbi);
+        if (one_direction(v, ib1, jb)) fastm |= 2u << (2 * cbi);
     }
     uint32_t A[4][2], B[4][2];
 #pragma unroll
@@ -285,8 +291,12 @@ __global__ void __launch_bounds__(256) k_dominance_gen(RunView v)
         A[cbi][0] = A[cbi][1] = 0u;
         B[cbi][0] = B[cbi][1] = 0u;
     }
-    for (int q0 = 0; q0 < m; q0 += MC) {
+    // objective range of this CTA: all of them, or its share of the chunks
+    const int nch = (m + MC - 1) / MC, per = (nch + gridDim.y - 1) / gridDim.y;
+    const int qbeg = blockIdx.y * per * MC, qend = min(m, qbeg + per * MC);
+    for (int q0 = qbeg; q0 < qend; q0 += MC) {
         __syncthreads();  // the previous chunk is consumed
+#pragma unroll 4
         for (int e = threadIdx.x; e < NSGA3_TILE * MC; e += blockDim.x) {
             const int p = e / MC, q = q0 + (e - p * MC);
             srow[e] = q < m ? v.Fp[(size_t)(r0 + p) * m + q] : 0.0f;
@@ -342,6 +352,21 @@ __global__ void __launch_bounds__(256) k_dominance_gen(RunView v)
             }
         }
     }
+    if (gridDim.y > 1) {  // partial masks: OR-ed over the CTAs of the tile
+#pragma unroll
+        for (int cbi = 0; cbi < 4; ++cbi) {
+            const int jb = tj * 8 + ch * 4 + cbi;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int ib = ib0 + r;
+                if (jb < ib) continue;
+                const size_t at = (size_t)jb * v.ld + ib * 32 + lane;
+                if (A[cbi][r]) atomicOr(&v.dpa[at], A[cbi][r]);
+                if (B[cbi][r]) atomicOr(&v.dpb[at], B[cbi][r]);
+            }
+        }
+        return;
+    }
     uint32_t* D = v.Dom;
     int rc0 = 0, rc1 = 0;
 #pragma unroll
@@ -377,6 +402,33 @@ __global__ void __launch_bounds__(256) k_dominance_gen(RunView v)
     if (colcnt[t]) atomicAdd(&v.cnt[c0 + t], colcnt[t]);
 }
 
+// bits of block pair (ib, jb >= ib) from the OR-ed masks (warp per pair);
+// the masks are cleared for the next selection
+__global__ void __launch_bounds__(256) k_dom_finish(RunView v)
+{
+    if (read_status(v.ctrl)) return;
+    const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int NW = v.NW;
+    if (t >= (long long)NW * (NW + 1) / 2) return;
+    int ib, jb;
+    decode_tile(t, NW, ib, jb);
+    const int lane = lane_id();
+    const size_t at = (size_t)jb * v.ld + ib * 32 + lane;
+    const uint32_t a = v.dpa[at], b = v.dpb[at];
+    v.dpa[at] = 0u;
+    v.dpb[at] = 0u;
+    const bool fast = one_direction(v, ib, jb);
+    const uint32_t dij = fast ? ~a : (b & ~a);
+    const uint32_t dji = fast ? 0u : (a & ~b);
+    v.Dom[at] = dji;
+    if (dji) atomicAdd(&v.cnt[ib * 32 + lane], __popc(dji));
+    if (jb != ib) {
+        const uint32_t tr = warp_transpose32(dij);
+        v.Dom[(size_t)ib * v.ld + jb * 32 + lane] = tr;
+        if (tr) atomicAdd(&v.cnt[jb * 32 + lane], __popc(tr));
+    }
+}
+
 template <int M>
 cudaError_t launch_dom_m(const RunView& v, cudaStream_t s)
 {
@@ -407,6 +459,11 @@ cudaError_t launch_dominance(const RunView& v, cudaStream_t s)
     const long long T = v.ld / NSGA3_TILE;
     const long long tiles = T * (T + 1) / 2;
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_dominance_gen<<<(unsigned)tiles, 256, 0, s>>>(v);
+    const int ks = v.dom_ks > 1 ? v.dom_ks : 1;
+    k_dominance_gen<<<dim3((unsigned)tiles, ks), 256, 0, s>>>(v);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || ks == 1) return e;
+    const long long pairs = (long long)v.NW * (v.NW + 1) / 2;
+    k_dom_finish<<<(unsigned)((pairs * 32 + 255) / 256), 256, 0, s>>>(v);
     return cudaGetLastError();
 }

@@ -33,6 +33,7 @@ __global__ void k_sel_reset(RunView v)
     if (tid == 0) {
         Ctrl* c = v.ctrl;
         c->bar_count = 0u;
+        c->sbar = 0u;
         c->pfs[0] = 0u;
         c->pfs[1] = 0u;
         c->pfs[2] = 0u;

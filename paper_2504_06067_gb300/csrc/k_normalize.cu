@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(NB) k_norm_ideal(RunView v)
     const bool inZ = v.norm_history ? (p < v.n2) : inT;
     if (v.norm_history && blockIdx.x == 0 && threadIdx.x == 0 && c->hvalid)
         for (int q = 0; q < v.m; ++q) atomicMin(&c->zmin[q], f2ord((float)c->hz[q]));
+    if (v.m > NSGA3_FAST_M) return;  // k_zmin_gen
     for (int q = 0; q < v.m; ++q) {
         uint32_t o = inZ ? f2ord(v.Fp[(size_t)p * v.m + q]) : 0xffffffffu;
 #pragma unroll
@@ -79,7 +80,8 @@ __device__ __forceinline__ bool key_less(unsigned long long a, int ia, unsigned 
 // (row-swapped) system, so each elimination step updates every row at once;
 // every element sees the same _rn operations in the same order as a serial
 // elimination (factor = A_rc / A_cc, A_rk -= factor * A_ck for k >= c,
-// rhs_r -= factor * rhs_c; back substitution left to right).
+// rhs_r -= factor * rhs_c; back substitution from the last unknown, each
+// row's known terms subtracted from the highest column down).
 // M <= NSGA3_FAST_M: m = M; M = NSGA3_WARP_M: any m <= 32 at run time
 // (rows and columns >= m are never touched).
 template <int M>
@@ -158,18 +160,16 @@ __device__ void solve_intercepts(const RunView& v, Ctrl* c, const int* ext, cons
     }
     double a = 0.0;
     if (ok) {
+        // back substitution column by column from the last unknown: every
+        // lane subtracts A_ir b_r as soon as b_r is known, so row i meets its
+        // terms from the highest column down, as the serial loop does
         double b = 0.0;  // lane r ends with b_r
 #pragma unroll
         for (int r = M - 1; r >= 0; --r) {
             if (r >= m) continue;
-            double s = rhs;
-#pragma unroll
-            for (int cc = r + 1; cc < M; ++cc) {
-                const double bc = __shfl_sync(0xffffffffu, b, cc);
-                if (cc < m) s = __dsub_rn(s, __dmul_rn(A[cc], bc));
-            }
-            const double br = __ddiv_rn(s, A[r]);
+            const double br = __shfl_sync(0xffffffffu, lane == r ? __ddiv_rn(rhs, A[r]) : 0.0, r);
             if (lane == r) b = br;
+            if (lane < r) rhs = __dsub_rn(rhs, __dmul_rn(A[r], br));
         }
         a = lane < m ? __ddiv_rn(1.0, b) : 1.0;
         const bool bad = lane < m && (!isfinite(a) || a <= 1e-6);
@@ -367,9 +367,10 @@ __global__ void __launch_bounds__(EB) k_norm_extreme(RunView v)
 // can have: fl(max_r f~_r / 1e-6) and, for the axis of that maximum (first
 // index), fl(second largest / 1e-6).  k_ext_axis takes QG axes per block:
 // ASF_q = max(f~_q, that key) per entry, (min, lowest index) per axis, and
-// the nadir maxima over the members; the last block reduces the blocks and
-// either solves the intercepts with one warp (m <= NSGA3_WARP_M) or leaves
-// E and the nadir to the cooperative elimination below.
+// the nadir maxima over the members; k_ext_reduce reduces the blocks (a warp
+// per axis) and either solves the intercepts with one warp
+// (m <= NSGA3_WARP_M) or leaves E and the nadir to the cooperative
+// elimination below.
 constexpr int GB = 128;  // threads per block of the m > NSGA3_FAST_M kernels
 constexpr int QG = 8;    // axes per block of k_ext_axis
 
@@ -388,18 +389,45 @@ __device__ __forceinline__ int history_entries(const RunView& v, const Ctrl* c)
     return (v.norm_history && c->hvalid) ? v.m : 0;
 }
 
+// ideal point for m > NSGA3_FAST_M: thread per objective over a chunk of
+// positions (coalesced across objectives), order-preserving atomicMin
+constexpr int ZP = 32;  // positions per chunk
+
+__global__ void __launch_bounds__(128) k_zmin_gen(RunView v)
+{
+    Ctrl* c = v.ctrl;
+    if (skip_niche(c)) return;
+    const int m = v.m, q = blockIdx.x * 128 + threadIdx.x;
+    if (q >= m) return;
+    const int l = c->l;
+    const int p0 = blockIdx.y * ZP, p1 = min(v.n2, p0 + ZP);
+    uint32_t o = 0xffffffffu;
+#pragma unroll 8
+    for (int p = p0; p < p1; ++p) {
+        const int r = v.srank[p];
+        const bool in = v.norm_history ? true : (r >= 0 && r <= l);
+        if (in) o = min(o, f2ord(v.Fp[(size_t)p * m + q]));
+    }
+    if (o != 0xffffffffu) atomicMin(&c->zmin[q], o);
+}
+
+// a warp per entry: lane-wise (largest key, second largest, first index of
+// the largest) over r = lane, lane + 32, ..., merged across the lanes; the
+// result is that of one pass over r = 0 .. m-1 (largest, the largest of the
+// rest counting a repeated maximum, its first index)
 __global__ void __launch_bounds__(GB) k_ext_keys(RunView v)
 {
     Ctrl* c = v.ctrl;
     if (skip_niche(c)) return;
-    const int m = v.m, nT = c->nT;
+    const int m = v.m, nT = c->nT, lane = lane_id();
     const int ne = nT + history_entries(v, c);
-    for (int s = blockIdx.x * GB + threadIdx.x; s < ne; s += gridDim.x * GB) {
+    const int nw = gridDim.x * (GB / 32);
+    for (int s = (blockIdx.x * GB + threadIdx.x) >> 5; s < ne; s += nw) {
         int idx;
         const float* f = entry_row(v, s, nT, idx);
         unsigned long long m1 = 0ull, m2 = 0ull;  // f~ >= 0: keys order like values
-        int r1 = 0;
-        for (int r = 0; r < m; ++r) {
+        int r1 = 0x7fffffff;                      // none while m1 == 0
+        for (int r = lane; r < m; r += 32) {
             const unsigned long long kr = okey(__dsub_rn((double)f[r], zstar_of(c, r)));
             if (kr > m1) {
                 m2 = m1;
@@ -409,9 +437,27 @@ __global__ void __launch_bounds__(GB) k_ext_keys(RunView v)
                 m2 = kr;
             }
         }
-        v.ekey[2 * (size_t)s] = okey(__ddiv_rn(__longlong_as_double((long long)m1), 1e-6));
-        v.ekey[2 * (size_t)s + 1] = okey(__ddiv_rn(__longlong_as_double((long long)m2), 1e-6));
-        v.er1[s] = r1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long om1 = __shfl_xor_sync(0xffffffffu, m1, o);
+            const unsigned long long om2 = __shfl_xor_sync(0xffffffffu, m2, o);
+            const int or1 = __shfl_xor_sync(0xffffffffu, r1, o);
+            if (om1 > m1) {
+                m2 = max(om2, m1);
+                m1 = om1;
+                r1 = or1;
+            } else if (om1 < m1) {
+                m2 = max(m2, om1);
+            } else if (m1 > 0ull) {  // the maximum occurs on both sides
+                m2 = m1;
+                r1 = min(r1, or1);
+            }
+        }
+        if (lane == 0) {
+            v.ekey[2 * (size_t)s] = okey(__ddiv_rn(__longlong_as_double((long long)m1), 1e-6));
+            v.ekey[2 * (size_t)s + 1] = okey(__ddiv_rn(__longlong_as_double((long long)m2), 1e-6));
+            v.er1[s] = m1 > 0ull ? r1 : 0;
+        }
     }
 }
 
@@ -421,9 +467,6 @@ __global__ void __launch_bounds__(GB) k_ext_axis(RunView v)
     __shared__ unsigned long long s_key[GB / 32][QG];
     __shared__ int s_idx[GB / 32][QG];
     __shared__ unsigned long long s_nad[GB / 32][QG];
-    __shared__ unsigned s_ticket;
-    __shared__ int f_ext[NSGA3_WARP_M];
-    __shared__ double f_nad[NSGA3_WARP_M];
     Ctrl* c = v.ctrl;
     if (skip_niche(c)) return;
     const int m = v.m, nT = c->nT;
@@ -499,24 +542,33 @@ __global__ void __launch_bounds__(GB) k_ext_axis(RunView v)
         v.ext_idx[(size_t)blockIdx.x * m + q] = bi;
         pn[(size_t)blockIdx.x * m + q] = n;
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_ticket = atomicAdd(&c->ext_done, 1u);
-    __syncthreads();
-    if (s_ticket != gridDim.x * gridDim.y - 1) return;
-    __threadfence();
-    // last block: one warp per axis over the parts
-    for (int q = warp; q < m; q += GB / 32) {
+}
+
+// per axis (a warp each) the (min, lowest index) over the parts and the
+// nadir maximum; with m <= NSGA3_WARP_M the last CTA solves the intercepts
+// with one warp, else the cooperative elimination follows
+__global__ void __launch_bounds__(256) k_ext_reduce(RunView v, int parts)
+{
+    __shared__ unsigned s_ticket;
+    __shared__ int f_ext[NSGA3_WARP_M];
+    __shared__ double f_nad[NSGA3_WARP_M];
+    Ctrl* c = v.ctrl;
+    if (skip_niche(c)) return;
+    const int m = v.m, lane = lane_id();
+    const int q = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const unsigned long long* pk = reinterpret_cast<const unsigned long long*>(v.ext_part);
+    const unsigned long long* pn = reinterpret_cast<const unsigned long long*>(v.nad_part);
+    if (q < m) {
         unsigned long long b = ~0ull, n = 0ull;
         int bi = 0x7fffffff;
         for (int p = lane; p < parts; p += 32) {
-            const unsigned long long pb = __ldcg(&pk[(size_t)p * m + q]);
-            const int pi = __ldcg(&v.ext_idx[(size_t)p * m + q]);
+            const unsigned long long pb = pk[(size_t)p * m + q];
+            const int pi = v.ext_idx[(size_t)p * m + q];
             if (key_less(pb, pi, b, bi)) {
                 b = pb;
                 bi = pi;
             }
-            n = max(n, __ldcg(&pn[(size_t)p * m + q]));
+            n = max(n, pn[(size_t)p * m + q]);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -530,19 +582,24 @@ __global__ void __launch_bounds__(GB) k_ext_axis(RunView v)
             n = max(n, on);
         }
         if (lane == 0) {
-            const double nq = __longlong_as_double((long long)n);
-            if (m <= NSGA3_WARP_M) {
-                f_ext[q] = bi;
-                f_nad[q] = nq;
-            } else {
-                c->ext[q] = bi;
-                v.nadv[q] = nq;
-            }
+            c->ext[q] = bi;
+            v.nadv[q] = __longlong_as_double((long long)n);
         }
+    }
+    if (m > NSGA3_WARP_M) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_ticket = atomicAdd(&c->ext_done, 1u);
+    __syncthreads();
+    if (s_ticket != gridDim.x - 1) return;
+    __threadfence();
+    if (threadIdx.x < m) {
+        f_ext[threadIdx.x] = __ldcg(&c->ext[threadIdx.x]);
+        f_nad[threadIdx.x] = __ldcg(&v.nadv[threadIdx.x]);
     }
     __syncthreads();
     if (threadIdx.x == 0) c->ext_done = 0u;
-    if (m <= NSGA3_WARP_M && warp == 0) solve_intercepts<NSGA3_WARP_M>(v, c, f_ext, f_nad);
+    if (threadIdx.x < 32) solve_intercepts<NSGA3_WARP_M>(v, c, f_ext, f_nad);
 }
 
 // m > NSGA3_WARP_M: the elimination of the warp solver spread over a
@@ -553,21 +610,26 @@ __global__ void __launch_bounds__(GB) k_ext_axis(RunView v)
 // updates columns col+1 .. m (m = the right-hand side) with the same _rn
 // operations as the serial elimination (column col is not needed again).
 // Reads of amat bypass L1 (other SMs write it between barriers).  The back
-// substitution (left to right, as in the warp solver) runs in CTA 0.
+// substitution (the order of the warp solver) runs in CTA 0.
 constexpr int SB = 256;
+static_assert(NSGA3_MAX_M <= 2 * SB, "the back substitution keeps two rows per thread");
 
 __global__ void __launch_bounds__(SB) k_solve_coop(RunView v)
 {
     __shared__ int ord[NSGA3_MAX_M];
     __shared__ double sb[NSGA3_MAX_M];
+    __shared__ double colv[NSGA3_MAX_M];  // column col of the rows, by position
     __shared__ double red_x[SB / 32];
     __shared__ int red_p[SB / 32];
     __shared__ int s_ok, s_piv;
     Ctrl* c = v.ctrl;
     if (skip_niche(c)) return;
     const int m = v.m, ld = m + 1;
+    unsigned nbar = 0;  // barriers passed (c->sbar is zero at launch: k_sel_reset)
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-    const int gw = blockIdx.x * (SB / 32) + warp, nw = gridDim.x * (SB / 32);
+    // rows go to the CTAs in turn, so that the FP64 work of a step spreads
+    // over every SM of the grid
+    const int gw = warp * gridDim.x + blockIdx.x, nw = gridDim.x * (SB / 32);
     double* A = v.amat;
     const int ncand = v.n2 + ((v.norm_history && c->hvalid) ? m : 0);
     bool bad_ext = false;
@@ -591,15 +653,19 @@ __global__ void __launch_bounds__(SB) k_solve_coop(RunView v)
             }
             if (lane == 0) A[(size_t)q * ld + m] = 1.0;
         }
-        if (!grid_sync(c, &s_ok)) return;
+        if (!grid_sync_count(c, &c->sbar, ++nbar * gridDim.x, &s_ok)) return;
         for (int col = 0; col < m; ++col) {
             // pivot (every CTA): the first position p >= col of maximal
             // |A[ord[p]][col]|; a NaN never replaces the running maximum
+            // (the column's values stay in colv for the factors below)
             double bx = -1.0;
             int bp = 0x7fffffff;
-            for (int p = col + 1 + tid; p < m; p += SB) {
-                const double x = fabs(__ldcg(&A[(size_t)ord[p] * ld + col]));
-                if (x > bx) {  // positions ascend per thread: the first maximum stays
+#pragma unroll 2
+            for (int p = col + tid; p < m; p += SB) {
+                const double val = __ldcg(&A[(size_t)ord[p] * ld + col]);
+                colv[p] = val;
+                const double x = fabs(val);
+                if (p > col && x > bx) {  // positions ascend per thread: the first maximum stays
                     bx = x;
                     bp = p;
                 }
@@ -624,7 +690,7 @@ __global__ void __launch_bounds__(SB) k_solve_coop(RunView v)
                         bx = red_x[w];
                         bp = red_p[w];
                     }
-                const double x0 = fabs(__ldcg(&A[(size_t)ord[col] * ld + col]));
+                const double x0 = fabs(colv[col]);
                 int p = col;
                 double best = x0;
                 if (x0 == x0 && bp != 0x7fffffff && bx > x0) {  // x0 NaN: col stays
@@ -644,29 +710,43 @@ __global__ void __launch_bounds__(SB) k_solve_coop(RunView v)
                 ok = false;
                 break;
             }
-            const int P = ord[col];
-            const double pv = __ldcg(&A[(size_t)P * ld + col]);
+            const int P = ord[col], pp = s_piv;
+            const double pv = colv[pp];  // the pivot row's value (read at its old position)
             for (int pos = col + 1 + gw; pos < m; pos += nw) {
                 const int r = ord[pos];
-                const double factor = __ddiv_rn(__ldcg(&A[(size_t)r * ld + col]), pv);
+                // the row now at pp came from position col
+                const double factor = __ddiv_rn(pos == pp ? colv[col] : colv[pos], pv);
+#pragma unroll 4  // four pairs of loads in flight (L2 round trips dominate a step)
                 for (int k = col + 1 + lane; k <= m; k += 32)
                     A[(size_t)r * ld + k] = __dsub_rn(__ldcg(&A[(size_t)r * ld + k]),
                                                       __dmul_rn(factor, __ldcg(&A[(size_t)P * ld + k])));
             }
-            if (!grid_sync(c, &s_ok)) return;
+            if (!grid_sync_count(c, &c->sbar, ++nbar * gridDim.x, &s_ok)) return;
         }
     }
     if (blockIdx.x != 0) return;
-    // CTA 0: back substitution, intercepts, fallback, history
-    if (ok && warp == 0) {
+    // CTA 0: back substitution column by column from the last unknown (as
+    // in the warp solver); thread t keeps the partial sums of positions t
+    // and t + SB and loads the next column's elements a step ahead
+    if (ok) {
+        const int i0 = tid, i1 = tid + SB;
+        const size_t R0 = i0 < m ? (size_t)ord[i0] * ld : 0, R1 = i1 < m ? (size_t)ord[i1] * ld : 0;
+        double s0 = i0 < m ? __ldcg(&A[R0 + m]) : 0.0, s1 = i1 < m ? __ldcg(&A[R1 + m]) : 0.0;
+        const double d0 = i0 < m ? __ldcg(&A[R0 + i0]) : 1.0, d1 = i1 < m ? __ldcg(&A[R1 + i1]) : 1.0;
+        double c0 = i0 < m - 1 ? __ldcg(&A[R0 + m - 1]) : 0.0;
+        double c1 = i1 < m - 1 ? __ldcg(&A[R1 + m - 1]) : 0.0;
         for (int r = m - 1; r >= 0; --r) {
-            const int R = ord[r];
-            if (lane == 0) {
-                double s = __ldcg(&A[(size_t)R * ld + m]);
-                for (int cc = r + 1; cc < m; ++cc) s = __dsub_rn(s, __dmul_rn(__ldcg(&A[(size_t)R * ld + cc]), sb[cc]));
-                sb[r] = __ddiv_rn(s, __ldcg(&A[(size_t)R * ld + r]));
+            if (i0 == r) sb[r] = __ddiv_rn(s0, d0);
+            if (i1 == r) sb[r] = __ddiv_rn(s1, d1);
+            __syncthreads();
+            const double br = sb[r];
+            const double u0 = c0, u1 = c1;
+            if (r > 0) {
+                c0 = i0 < r - 1 ? __ldcg(&A[R0 + r - 1]) : 0.0;
+                c1 = i1 < r - 1 ? __ldcg(&A[R1 + r - 1]) : 0.0;
             }
-            __syncwarp();
+            if (i0 < r) s0 = __dsub_rn(s0, __dmul_rn(u0, br));
+            if (i1 < r) s1 = __dsub_rn(s1, __dmul_rn(u1, br));
         }
     }
     __syncthreads();
@@ -710,16 +790,24 @@ static cudaError_t launch_norm_extreme_gen(const RunView& v, int num_sms, cudaSt
     if (parts > v.ext_parts) parts = v.ext_parts;
     if (parts > (v.n2 + v.m + GB - 1) / GB) parts = (v.n2 + v.m + GB - 1) / GB;
     if (parts < 1) parts = 1;
-    int kb = (v.n2 + v.m + GB - 1) / GB;
-    if (kb > 4 * num_sms) kb = 4 * num_sms;
-    k_ext_keys<<<kb, GB, 0, s>>>(v);
+    k_zmin_gen<<<dim3((v.m + 127) / 128, (v.n2 + ZP - 1) / ZP), 128, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int kb = (v.n2 + v.m + GB / 32 - 1) / (GB / 32);
+    if (kb > 8 * num_sms) kb = 8 * num_sms;
+    k_ext_keys<<<kb, GB, 0, s>>>(v);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_ext_axis<<<dim3(parts, qgroups), GB, 0, s>>>(v);
     e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_ext_reduce<<<(v.m + 7) / 8, 256, 0, s>>>(v, parts);
+    e = cudaGetLastError();
     if (e != cudaSuccess || v.m <= NSGA3_WARP_M) return e;
-    // one warp per remaining row at the first step, every CTA resident
-    int grid = (v.m - 1 + SB / 32 - 1) / (SB / 32);
+    // a CTA per SM (the FP64 pipe of every SM), at most a row per CTA at the
+    // first step; every CTA resident
+    int grid = v.m - 1;
+    if (grid > num_sms) grid = num_sms;
     const int cap = num_sms * (g_solve_occ > 0 ? g_solve_occ : 1);
     if (grid > cap) grid = cap;
     cudaLaunchConfig_t cfg = {};

@@ -17,7 +17,8 @@
 //   Children go to rows N + 2q and N + 2q + 1.  FP32 arithmetic.
 // Objective (the softmax-simplex family): k = m - 1,
 //   g = sum_{v >= k} (x_v - 0.5)^2, f_j = (1 + g) softmax(W x[0:k])_j,
-//   evaluated in FP64 (sums left to right) and rounded to FP32.
+//   evaluated in FP64 (sums left to right) and rounded to FP32; for m > 10
+//   the products W x are summed as compensated FP32 dot products.
 #include "kernels.cuh"
 
 namespace {
@@ -81,12 +82,14 @@ __global__ void k_refdirs(int m, int p1, int p2, double tau, int w1, int w, doub
 constexpr int OR = 32;
 constexpr int OT = 256;
 
-// rows per block: 32, fewer when m is large (shared memory holds R x m
-// exponentials, at most 32 KB)
+// rows per block: 32 for m <= 10; above, about 256 (row, objective) pairs
+// per block, one per thread, so that the FP64 dot products of many
+// objectives spread over the whole GPU (R x m exponentials in shared memory)
 inline int obj_rows(int m)
 {
-    int r = 4096 / m;
-    return r < 1 ? 1 : (r > OR ? OR : r);
+    if (m <= NSGA3_FAST_M) return OR;
+    const int r = OT / m;
+    return r < 1 ? 1 : r;
 }
 inline size_t obj_smem(int m) { return (size_t)obj_rows(m) * (m + 2) * sizeof(double); }
 
@@ -95,6 +98,58 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// m > NSGA3_FAST_M: a_j = sum_v W_jv x_v for RB rows x 128 objectives per
+// CTA as compensated FP32 dot products (each product split exactly into
+// p + e by an FMA, the sum carried as a float-float pair by TwoSum; Ogita,
+// Rump and Oishi's Dot2), then e_j = exp(a_j) in FP64 into v.fprime (free
+// during the variation).  Dot2's error, about (k 2^-24)^2 of sum |W x|, is
+// far below the FP32 rounding of f: the FP64 evaluation of the m
+// exponentials' products would take the FP64 pipe (1/64 of FP32) for
+// m (m-1) N operations.
+constexpr int RB = 4;     // rows per CTA
+constexpr int DT = 128;   // objectives per CTA
+
+__global__ void __launch_bounds__(DT) k_obj_dot(RunView v, int row0, int n)
+{
+    extern __shared__ float xs[];  // RB x k
+    const int m = v.m, d = v.d, k = m - 1;
+    const int base = blockIdx.x * RB;
+    const int rows = min(RB, n - base);
+    for (int e = threadIdx.x; e < RB * k; e += DT) {
+        const int r = e / k, c = e - r * k;
+        xs[e] = r < rows ? v.X[(size_t)(row0 + base + r) * d + c] : 0.0f;
+    }
+    __syncthreads();
+    const int j = blockIdx.y * DT + threadIdx.x;
+    if (j >= m) return;
+    float hi[RB], lo[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        hi[r] = 0.0f;
+        lo[r] = 0.0f;
+    }
+#pragma unroll 8
+    for (int e = 0; e < k; ++e) {
+        const float w = __ldg(&v.Wt[(size_t)e * m + j]);
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            const float x = xs[r * k + e];
+            const float p = __fmul_rn(w, x);
+            const float pe = __fmaf_rn(w, x, -p);  // w x = p + pe exactly
+            float s1, t1;
+            two_sum(hi[r], p, s1, t1);
+            hi[r] = s1;
+            lo[r] = __fadd_rn(lo[r], __fadd_rn(t1, pe));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+        if (r < rows) {
+            const double a = __dadd_rn((double)hi[r], (double)lo[r]);
+            v.fprime[(size_t)(base + r) * m + j] = exp(a);
+        }
 }
 
 __global__ void __launch_bounds__(OT) k_objective(RunView v, int row0, int n, int R)
@@ -137,6 +192,10 @@ __global__ void __launch_bounds__(OT) k_objective(RunView v, int row0, int n, in
     for (int idx = threadIdx.x; idx < R * m; idx += OT) {
         const int rr = idx / m, j = idx - rr * m;
         if (base + rr >= n) continue;
+        if (m > NSGA3_FAST_M) {  // exponentials from k_obj_dot
+            se[idx] = v.fprime[(size_t)(base + rr) * m + j];
+            continue;
+        }
         const float* x = v.X + (size_t)(row0 + base + rr) * d;
         double a = 0.0;
         for (int e = 0; e < k; ++e) a = __dadd_rn(a, __dmul_rn((double)v.Wobj[j * k + e], (double)x[e]));
@@ -233,6 +292,14 @@ __global__ void k_vary_eval(RunView v)
     }
 }
 
+cudaError_t launch_obj_dot(const RunView& v, int row0, int n, cudaStream_t s)
+{
+    if (!v.Wt) return cudaErrorInvalidValue;
+    const size_t sm = (size_t)RB * (v.m - 1) * sizeof(float);
+    k_obj_dot<<<dim3((n + RB - 1) / RB, (v.m + DT - 1) / DT), DT, sm, s>>>(v, row0, n);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_refdirs(const RunView& v, int p1, int p2, double tau, double* Zd, double* nz,
@@ -256,6 +323,10 @@ cudaError_t launch_init(const RunView& v, cudaStream_t s)
     k_init<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (v.m > NSGA3_FAST_M) {
+        e = launch_obj_dot(v, 0, v.N, s);
+        if (e != cudaSuccess) return e;
+    }
     const int R = obj_rows(v.m);
     k_objective<<<(v.N + R - 1) / R, OT, obj_smem(v.m), s>>>(v, 0, v.N, R);
     return cudaGetLastError();
@@ -268,6 +339,10 @@ cudaError_t launch_vary_eval(const RunView& v, cudaStream_t s)
     k_vary_eval<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (v.m > NSGA3_FAST_M) {
+        e = launch_obj_dot(v, v.N, v.N, s);
+        if (e != cudaSuccess) return e;
+    }
     const int R = obj_rows(v.m);
     k_objective<<<(v.N + R - 1) / R, OT, obj_smem(v.m), s>>>(v, v.N, v.N, R);
     return cudaGetLastError();

@@ -139,6 +139,28 @@ __global__ void __launch_bounds__(256) k_sort_scatter(RunView v)
     for (int q = 0; q < m; ++q) v.Fp[(size_t)pos * m + q] = v.F[(size_t)i * m + q] + 0.0f;
 }
 
+// m > NSGA3_FAST_M: a warp per point (lane 0 takes the position, the lanes
+// copy the row)
+__global__ void __launch_bounds__(256) k_sort_scatter_rows(RunView v)
+{
+    Ctrl* c = v.ctrl;
+    if (read_status(c)) return;
+    const int i = (blockIdx.x * 256 + threadIdx.x) >> 5;
+    if (i >= v.n2) return;
+    const int lane = lane_id(), m = v.m;
+    int pos = 0;
+    if (lane == 0) {
+        float lo, scale;
+        range_of(c, lo, scale);
+        const int b = bucket_of(v.F[(size_t)i * m] + 0.0f, lo, scale);
+        pos = atomicAdd(&v.bcnt[b], 1);
+        v.perm[pos] = i;
+        v.skey[pos] = (uint32_t)b;
+    }
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+    for (int q = lane; q < m; q += 32) v.Fp[(size_t)pos * m + q] = v.F[(size_t)i * m + q] + 0.0f;
+}
+
 }  // namespace
 
 cudaError_t launch_sort(const RunView& v, int num_sms, cudaStream_t s)
@@ -151,6 +173,9 @@ cudaError_t launch_sort(const RunView& v, int num_sms, cudaStream_t s)
     k_sort_hist<<<blocks, SB, 0, s>>>(v);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_sort_scatter<<<(v.n2 + 255) / 256, 256, 0, s>>>(v);
+    if (v.m > NSGA3_FAST_M)
+        k_sort_scatter_rows<<<(unsigned)(((long long)v.n2 * 32 + 255) / 256), 256, 0, s>>>(v);
+    else
+        k_sort_scatter<<<(v.n2 + 255) / 256, 256, 0, s>>>(v);
     return cudaGetLastError();
 }

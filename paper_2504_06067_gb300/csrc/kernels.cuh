@@ -26,8 +26,9 @@ cudaError_t launch_dominance(const RunView& v, cudaStream_t s);
 cudaError_t launch_peel(const RunView& v, int num_sms, cudaStream_t s);
 cudaError_t peel_init_attributes();
 cudaError_t launch_norm_ideal(const RunView& v, cudaStream_t s);
-// extreme points and intercepts: one launch (m <= 10), two (m <= 32) or
-// three with the cooperative elimination (m > 32)
+// extreme points and intercepts: one launch (m <= 10); above, the ideal
+// point, entry keys and per-axis blocks (three launches), plus the
+// cooperative elimination for m > 32
 cudaError_t launch_norm_extreme(const RunView& v, int num_sms, cudaStream_t s);
 cudaError_t norm_init_attributes();
 cudaError_t launch_assoc_prep(const RunView& v, cudaStream_t s);

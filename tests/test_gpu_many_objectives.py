@@ -154,6 +154,15 @@ def test_generations_many(n, orc, cfg):
             assert np.array_equal(Xn, RX[sel]) and np.array_equal(Fn, RF[sel])
             assert np.array_equal(rn, ref["rank"][sel])
         import ctypes as C
+        import torch
         k = C.c_int32()
         r.check(n.nsga3_last_launches(r.ctx, C.byref(k)))
-        assert k.value == 21 + 1 + (1 if cfg.m > 32 else 0)
+        # + ideal point, entry keys and their reduction, |f'|, candidate
+        # distances; + the cooperative elimination (m > 32);
+        # + the finishing kernel of a split dominance build (fewer tiles than
+        # two per SM and more than one objective chunk)
+        T = -(-2 * cfg.N // 256)
+        split = T * (T + 1) // 2 < 2 * torch.cuda.get_device_properties(0).multi_processor_count \
+            and cfg.m > 16
+        # + the objective's dot-product kernel
+        assert k.value == 21 + 5 + (1 if cfg.m > 32 else 0) + (1 if split else 0) + 1
