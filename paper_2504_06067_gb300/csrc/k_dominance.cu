@@ -69,6 +69,29 @@ __device__ __forceinline__ void decode_tile(long long t, int T, int& ti, int& tj
     tj = r + (int)(t - start(r));
 }
 
+// Sign bit set iff some f_iq > f_jq for q = 1 .. M-1 (the one-direction
+// test).  The sign bits are OR-ed three at a time on the integer pipe; when
+// the M-1 differences are an even number, the first two are first combined
+// by fminf on the FP32 pipe (the minimum is negative iff one of them is;
+// differences are never -0.0 because -0.0 is staged as +0.0), which saves
+// one integer operation per pair and row.
+template <int M>
+__device__ __forceinline__ uint32_t any_greater(const float* fj, const float* fi)
+{
+    uint32_t oa;
+    int q0;
+    if (M >= 3 && (M - 1) % 2 == 0) {
+        oa = __float_as_uint(fminf(fj[1] - fi[1], fj[2] - fi[2]));
+        q0 = 3;
+    } else {
+        oa = 0u;
+        q0 = 1;
+    }
+#pragma unroll
+    for (int q = q0; q < M; ++q) oa |= __float_as_uint(fj[q] - fi[q]);
+    return oa;
+}
+
 // one 32-column block against one row block, both directions (ties in f_0)
 template <int M, int M4>
 __device__ __forceinline__ void block_full(const float* fi, const float* colp, uint32_t& dij, uint32_t& dji)
@@ -171,12 +194,7 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
                     fj[4 * q4 + 2] = t.z;
                     fj[4 * q4 + 3] = t.w;
                 }
-                uint32_t oa0 = 0u, oa1 = 0u;
-#pragma unroll
-                for (int q = 1; q < M; ++q) {
-                    oa0 |= __float_as_uint(fj[q] - f0[q]);
-                    oa1 |= __float_as_uint(fj[q] - f1[q]);
-                }
+                const uint32_t oa0 = any_greater<M>(fj, f0), oa1 = any_greater<M>(fj, f1);
                 acc0 = __funnelshift_l(oa0, acc0, 1);  // sign set: some f_iq > f_jq
                 acc1 = __funnelshift_l(oa1, acc1, 1);
             }
@@ -203,10 +221,7 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
 #pragma unroll 4
                 for (int k = 31; k >= 0; --k) {
                     const float* fj = colp + k * M4;
-                    uint32_t oa = 0u;
-#pragma unroll
-                    for (int q = 1; q < M; ++q) oa |= __float_as_uint(fj[q] - fi[q]);
-                    acc = __funnelshift_l(oa, acc, 1);
+                    acc = __funnelshift_l(any_greater<M>(fj, fi), acc, 1);
                 }
                 dij = ~acc;
                 dji = 0u;
