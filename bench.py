@@ -50,11 +50,11 @@ def parse_args(argv=None):
                    help="timed generations (default: the workload's run length)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep"],
+    p.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep", "popsweep"],
                    default="scale")
     p.add_argument("--runs", type=int, default=64, help="batched: independent runs")
     p.add_argument("--sweep-m", type=str, default=None,
-                   help="sweep: comma-separated subset of m (default: all of 4 ... 512)")
+                   help="sweep / popsweep: comma-separated subset of m (or of N)")
     p.add_argument("--requests", type=int, default=None, help="served: requests of the stream")
     p.add_argument("--cpu-budget", type=float, default=20.0,
                    help="seconds of oracle work for the cpu_baseline sample")
@@ -647,12 +647,17 @@ def run_served(args, world, rank, local):
 # N = 800, d = 1000, 100 generations, on the paper's GPU): context only.
 PAPER_TABLE2_S = {4: 4.334e-3, 8: 4.624e-3, 16: 5.083e-3, 32: 6.514e-3, 64: 8.103e-3,
                   128: 1.016e-2, 256: 2.348e-2, 512: 3.199e-2}
+# ... and in Table I (DTLZ3, m = 6, d = 500, population N)
+PAPER_TABLE1_S = {50: 1.120e-3, 100: 1.135e-3, 200: 1.121e-3, 400: 1.243e-3, 800: 1.493e-3,
+                  1600: 2.063e-3, 3200: 4.886e-3, 6400: 1.575e-2, 12800: 5.966e-2}
 
 
 def run_sweep(args, world, rank, local):
     """Generations per second over m = 4 ... 512 at N = 800, d = 1000 (the
-    shape of Table II); each m is its own run: warm-up, then K timed
-    generations from generation 0, L2 flushed before each."""
+    shape of Table II; --workload sweep) or over N = 50 ... 12,800 at m = 6,
+    d = 500 (Table I; --workload popsweep); each point is its own run:
+    warm-up, then K timed generations from generation 0, L2 flushed before
+    each."""
     import torch
     torch.cuda.set_device(local)
     dist = dist_init(world, "nccl")
@@ -669,11 +674,13 @@ def run_sweep(args, world, rank, local):
     n_launch = 0
     sampler = ClockSampler(local)
     sampler.start()
+    pop = args.workload == "popsweep"
+    cfgs = wl.population_sweep() if pop else wl.objective_sweep()
     only = None if not args.sweep_m else {int(x) for x in args.sweep_m.split(",")}
-    for cfg in wl.objective_sweep():
-        if only is not None and cfg.m not in only:
+    for cfg in cfgs:
+        if only is not None and (cfg.N if pop else cfg.m) not in only:
             continue
-        progress("sweep m=%d" % cfg.m)
+        progress("sweep m=%d N=%d" % (cfg.m, cfg.N))
         W = wl.objective_weights(cfg.m, cfg.seed)
         ctx = n.create(cfg.m, cfg.d, cfg.N, cfg.p1,
                        n.default_opts(seed=cfg.seed + rank, W=W.ctypes.data))
@@ -707,10 +714,14 @@ def run_sweep(args, world, rank, local):
         if st != n.OK:
             raise RuntimeError("device status %d (m = %d)" % (st, cfg.m))
         s_max = reduce_max(dist, sum(ms) / 1e3, "cuda")
-        rows.append({"m": cfg.m, "refs": cfg.w, "ms_per_gen": s_max * 1e3 / K,
-                     "gens_per_s": world * K / s_max,
-                     "phase_ms": {nm: round(ph[i] / K, 5) for i, nm in enumerate(names)},
-                     "paper_table2_ms": PAPER_TABLE2_S[cfg.m] * 1e3})
+        row = {"m": cfg.m, "N": cfg.N, "refs": cfg.w, "ms_per_gen": s_max * 1e3 / K,
+               "gens_per_s": world * K / s_max, "sols_per_s": world * K * cfg.N / s_max,
+               "phase_ms": {nm: round(ph[i] / K, 5) for i, nm in enumerate(names)}}
+        if pop:
+            row["paper_table1_ms"] = PAPER_TABLE1_S[cfg.N] * 1e3
+        else:
+            row["paper_table2_ms"] = PAPER_TABLE2_S[cfg.m] * 1e3
+        rows.append(row)
     clocks = sampler.stop()
     if rank != 0:
         if dist is not None:
@@ -718,9 +729,10 @@ def run_sweep(args, world, rank, local):
         return None
     top = rows[-1]
     line = {
-        "metric": "gens/s over the objective sweep (Table II shape: N 800, d 1000, m 4..512)",
+        "metric": ("gens/s over the population sweep (Table I shape: m 6, d 500, N 50..12800)" if pop else
+                   "gens/s over the objective sweep (Table II shape: N 800, d 1000, m 4..512)"),
         "value": top["gens_per_s"],
-        "unit": "gens/s at m = %d" % top["m"],
+        "unit": ("gens/s at N = %d" % top["N"]) if pop else ("gens/s at m = %d" % top["m"]),
         "n_gpus": world,
         "steps": K,
         "warmup": args.warmup,
@@ -730,7 +742,8 @@ def run_sweep(args, world, rank, local):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded softmax-simplex objective, W ~ N(0,1); stands in for DTLZ3)",
-        "config": {"workload": "sweep_N800_d1000_m4-512", "l2": "flushed (256 MB write) before every timed step",
+        "config": {"workload": "popsweep_m6_d500_N50-12800" if pop else "sweep_N800_d1000_m4-512",
+                   "l2": "flushed (256 MB write) before every timed step",
                    "generations": "timed %d from generation 0 per m" % K,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "sweep": rows,
@@ -740,9 +753,9 @@ def run_sweep(args, world, rank, local):
         "clocks": clocks,
     }
     if not args.no_cpu_baseline and world == 1:
-        cfg = wl.objective_sweep()[-1]
+        cfg = cfgs[-1]
         spg, nst = oracle_generations(cfg, args.cpu_budget)
-        line["cpu_baseline"] = {"value": 1.0 / spg, "unit": "gens/s at m = %d" % cfg.m, "cores": 1,
+        line["cpu_baseline"] = {"value": 1.0 / spg, "unit": line["unit"], "cores": 1,
                                 "kind": "oracle",
                                 "sample": "%d generation(s) of %s (FP64 C oracle, single thread)"
                                           % (nst, cfg.name)}
@@ -811,7 +824,8 @@ def run_reference(args, world, rank):
     """The oracle as the reference arm, on this workload's metric."""
     if rank != 0:
         return None
-    cfg = wl.objective_sweep()[-1] if args.workload == "sweep" else WORKLOADS[args.workload]
+    cfg = ({"sweep": wl.objective_sweep, "popsweep": wl.population_sweep}[args.workload]()[-1]
+           if args.workload in ("sweep", "popsweep") else WORKLOADS[args.workload])
     budget = 150.0
     spg, nsteps = oracle_generations(cfg, budget, max_steps=args.steps, warmup=min(args.warmup, 1))
     value = cfg.N / spg
@@ -854,7 +868,7 @@ def main(argv=None):
     args = parse_args(argv)
     world, rank, local = dist_env()
     if args.steps is None:
-        args.steps = {"batched": 300, "served": 0, "sweep": 50}.get(args.workload)
+        args.steps = {"batched": 300, "served": 0, "sweep": 50, "popsweep": 50}.get(args.workload)
         if args.steps is None:
             args.steps = WORKLOADS[args.workload].generations
     if args.impl == "reference":
@@ -863,7 +877,7 @@ def main(argv=None):
         run_batched(args, world, rank, local)
     elif args.workload == "served":
         run_served(args, world, rank, local)
-    elif args.workload == "sweep":
+    elif args.workload in ("sweep", "popsweep"):
         run_sweep(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)

@@ -65,6 +65,16 @@ def objective_sweep(N: int = 800, d: int = 1000, generations: int = 100):
                       p1=largest_p(m, N), generations=generations) for m in SWEEP_M]
 
 
+# Population sweep in the shape of the paper's Table I (m = 6, d = 500,
+# N = 50 ... 12,800; its runs use DTLZ3, here the softmax-simplex objective).
+POP_SWEEP_N = (50, 100, 200, 400, 800, 1600, 3200, 6400, 12800)
+
+
+def population_sweep(m: int = 6, d: int = 500, generations: int = 100):
+    return [RunConfig("popsweep_m%d_N%d_d%d_p%d" % (m, N, d, largest_p(m, N)), m=m, d=d, N=N,
+                      p1=largest_p(m, N), generations=generations) for N in POP_SWEEP_N]
+
+
 def knapsack_instance(m: int, d: int, seed: int = 0):
     """Integer profits and weights uniform in [10, 100] (m x d) and capacities
     of half the total weight per knapsack: the usual random 0-1 multi-
