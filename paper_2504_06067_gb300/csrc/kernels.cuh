@@ -27,12 +27,14 @@ cudaError_t launch_peel(const RunView& v, int num_sms, cudaStream_t s);
 cudaError_t peel_init_attributes();
 cudaError_t launch_norm_ideal(const RunView& v, cudaStream_t s);
 // extreme points and intercepts: one launch (m <= 10); above, the ideal
-// point, entry keys and per-axis blocks (three launches), plus the
-// cooperative elimination for m > 32
+// point, entry keys, per-axis blocks and their reduction (four launches),
+// plus the cooperative elimination for m > 32
 cudaError_t launch_norm_extreme(const RunView& v, int num_sms, cudaStream_t s);
 cudaError_t norm_init_attributes();
 cudaError_t launch_assoc_prep(const RunView& v, cudaStream_t s);
-// scan + FP64 recheck + per-point argmin + FP64 slow path (4 launches)
+// FP32 candidate scan, FP64 distances and per-point argmin, FP64 slow path
+// (three launches; four for m > 10, where the distances are a kernel of
+// their own); f' and |f'| are launch_assoc_prep (one launch, two for m > 10)
 cudaError_t launch_assoc_scan(const RunView& v, int num_sms, cudaStream_t s);
 cudaError_t assoc_prepare(const RunView& v);
 cudaError_t assoc_init_attributes();
