@@ -43,7 +43,6 @@ enum : uint32_t {
 struct Ctrl {
     uint32_t gen;            // Philox generation counter (word 1 of the counter)
     int32_t status;          // DEV_* of the last failure, 0 if none
-    uint32_t bar_count;      // grid barrier of the peel: arrivals
     int32_t cum;             // members ranked so far
     int32_t l;               // selecting front (first with cum >= N)
     int32_t nS;              // |S| = members of fronts < l
@@ -52,9 +51,9 @@ struct Ctrl {
     int32_t need_niche;      // K < |F_l|
     int32_t fallback;        // normalization used the nadir fallback
     int32_t passes;          // peel passes (kernel launches) in the last selection
-    uint32_t pfs[3];         // front sizes of peel passes k mod 3
-    uint32_t bar_gen;        // grid barrier of the peel: generation
     uint32_t sbar;           // arrivals at the barriers of the cooperative elimination
+    unsigned long long pbar; // peel barrier: arrivals << 32 | points ranked so far
+    unsigned long long prel; // peel barrier release: passes closed << 32 | points ranked
     int32_t nT;              // |S u F_l| (association set)
     int32_t Lstar;           // niche level threshold L*
     int32_t rlev;            // refs taken at level L*
@@ -247,11 +246,10 @@ __device__ __forceinline__ bool lex_less(double a, int ia, double b, int ib)
     return a < b || (a == b && ia < ib);
 }
 
-// ------------------------------------------------------ grid barrier ------
-// Barrier of a cooperative launch (every CTA resident), with a bounded
-// wait: returns false and records DEV_ETIMEOUT when the other CTAs did not
-// arrive within GRID_WAIT_NS of device time.  Uses c->bar_count (arrivals,
-// back to 0 after each barrier) and c->bar_gen (generation).
+// ------------------------------------------------------ grid barriers -----
+// Barriers of a cooperative launch (every CTA resident), with a bounded
+// wait: they return false and record DEV_ETIMEOUT when the other CTAs did
+// not arrive within GRID_WAIT_NS of device time.
 constexpr unsigned long long GRID_WAIT_NS = 20ull * 1000 * 1000 * 1000;
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -266,6 +264,57 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
     unsigned x;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(x) : "l"(p) : "memory");
     return x;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p)
+{
+    unsigned long long x;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];\n" : "=l"(x) : "l"(p) : "memory");
+    return x;
+}
+
+__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long x)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;\n" ::"l"(p), "l"(x) : "memory");
+}
+
+// Summing barrier of the peel: pass k's barrier adds (1 << 32) + add (this
+// CTA's new front members) to *bar; the CTA whose addition completes the
+// (k+1) * gridDim.x arrivals holds the running total of every CTA's adds
+// (no CTA can add for pass k+1 before that) and releases it with the pass
+// number in *rel, which the others poll.  Returns the total (< 2^32) or,
+// on a timeout, ~0ull.  *bar and *rel are zero at launch.
+__device__ __forceinline__ unsigned long long grid_sync_sum(Ctrl* c, unsigned long long* bar, unsigned long long* rel,
+                                                           unsigned k, unsigned add, unsigned long long* s_val)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long val;
+        __threadfence();
+        const unsigned long long inc = (1ull << 32) | add;
+        const unsigned long long now = atomicAdd(bar, inc) + inc;
+        if ((now >> 32) == (unsigned long long)(k + 1) * gridDim.x) {
+            val = now & 0xffffffffull;
+            __threadfence();  // the arrivals' writes before the release
+            st_release64(rel, ((unsigned long long)(k + 1) << 32) | val);
+        } else {
+            const unsigned long long t0 = global_ns();
+            unsigned it = 0;
+            unsigned long long r;
+            while (((r = ld_acquire64(rel)) >> 32) < (unsigned long long)(k + 1)) {
+                if ((++it & 1023u) == 0u && (global_ns() - t0 > GRID_WAIT_NS || it > (1u << 30))) {
+                    set_status(c, DEV_ETIMEOUT);
+                    r = ~0ull;
+                    break;
+                }
+            }
+            val = r == ~0ull ? ~0ull : (r & 0xffffffffull);
+        }
+        __threadfence();
+        *s_val = val;
+    }
+    __syncthreads();
+    return *s_val;
 }
 
 // Counting barrier: the k-th barrier of a launch waits until *ctr reaches
@@ -286,38 +335,6 @@ __device__ __forceinline__ bool grid_sync_count(Ctrl* c, unsigned* ctr, unsigned
                     ok = 0;
                     break;
                 }
-            }
-        }
-        __threadfence();
-        *s_ok = ok;
-    }
-    __syncthreads();
-    return *s_ok != 0;
-}
-
-__device__ __forceinline__ bool grid_sync(Ctrl* c, int* s_ok)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned g = ld_acquire(&c->bar_gen);
-        __threadfence();
-        if (atomicAdd(&c->bar_count, 1u) == gridDim.x - 1) {
-            atomicExch(&c->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&c->bar_gen, 1u);
-        } else {
-            const unsigned long long t0 = global_ns();
-            unsigned it = 0;
-            while (ld_acquire(&c->bar_gen) == g) {
-                // the clock is read every 256 polls; the poll count caps the
-                // wait too, should the timer not advance
-                if ((++it & 255u) == 0u && (global_ns() - t0 > GRID_WAIT_NS || it > (1u << 30))) {
-                    set_status(c, DEV_ETIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(100);
             }
         }
         __threadfence();

@@ -32,11 +32,9 @@ __global__ void k_sel_reset(RunView v)
     }
     if (tid == 0) {
         Ctrl* c = v.ctrl;
-        c->bar_count = 0u;
         c->sbar = 0u;
-        c->pfs[0] = 0u;
-        c->pfs[1] = 0u;
-        c->pfs[2] = 0u;
+        c->pbar = 0ull;
+        c->prel = 0ull;
         c->cum = 0;
         c->l = -1;
         c->nS = 0;

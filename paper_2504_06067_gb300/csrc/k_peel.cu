@@ -32,7 +32,8 @@ __global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v
     const int PT = blockDim.x, PW = PT >> 5;
     __shared__ uint2 list[LISTCAP];
     __shared__ int nlist;
-    __shared__ int s_ok;
+    __shared__ unsigned s_fs;             // this CTA's members of the front of this pass
+    __shared__ unsigned long long s_cum;  // points ranked, from the barrier
     __shared__ float rowbuf[STREAM ? PWMAX : 1][32][NSGA3_FAST_M];  // streaming: members of a front word
     Ctrl* c = v.ctrl;
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
@@ -42,9 +43,8 @@ __global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v
     // pass state itself; CTA 0 also publishes it in ctrl
     int cum = 0, l = -1;
     for (int k = 0;; ++k) {
-        // the next pass's front-size slot was last read right after barrier
-        // k - 2, which every CTA has left
-        if (blockIdx.x == 0 && tid == 0) c->pfs[(k + 1) % 3] = 0u;
+        if (tid == 0) s_fs = 0u;  // read after the barrier's first __syncthreads
+        __syncthreads();
         for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
             const int j0 = chunk * NSGA3_PEEL_COLS;
             // prefetch this thread's column state (used after the reduction)
@@ -224,16 +224,18 @@ __global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v
                     const int wd = j0 / 32 + warp;
                     v.front[(k & 1) * v.NW + wd] = word;
                     v.rem[wd] = __ldcg(&v.rem[wd]) & ~word;
-                    if (word) atomicAdd(&c->pfs[k % 3], (unsigned)__popc(word));
+                    if (word) atomicAdd(&s_fs, (unsigned)__popc(word));
                 }
             }
 
             __syncthreads();  // red and list are reused by the next chunk
         }
-        if (!grid_sync(c, &s_ok)) return;
+        // the barrier returns the points ranked after pass k
+        const unsigned long long tot = grid_sync_sum(c, &c->pbar, &c->prel, (unsigned)k, s_fs, &s_cum);
+        if (tot == ~0ull) return;
         // close front k (the same decision in every CTA)
-        const int fs = (int)__ldcg(&c->pfs[k % 3]);
-        const int ncum = cum + fs;
+        const int ncum = (int)tot;
+        const int fs = ncum - cum;
         bool first = false;
         if (l < 0 && ncum >= v.N) {
             l = k;
