@@ -76,6 +76,10 @@ typedef struct {
     const int32_t* kp_profit;   /* host, m x d profits (> 0), read during create only */
     const int32_t* kp_weight;   /* host, m x d weights (> 0), read during create only */
     const int32_t* kp_capacity; /* host, m capacities, read during create only */
+    int wait_ms;            /* budget of every device-side wait (the grid barriers of the
+                               cooperative kernels), in ms of device time; past it the
+                               kernel records NSGA3_ETIMEOUT and returns (default 20,000;
+                               <= 0: the default) */
 } nsga3_opts;
 
 /* Fills *o with the defaults above (seed 0, single layer, tau 0.5). */
@@ -99,6 +103,17 @@ nsga3_status nsga3_create(int m, int d, int N, int ref_divisions, const nsga3_op
 
 /* Frees the context and its device memory (synchronises its work). */
 void nsga3_destroy(nsga3_ctx* ctx);
+
+/*
+ * Self-test of the device-side wait budget (no counterpart in the paper):
+ * enqueues one single-CTA kernel that waits, with the same bounded wait as
+ * the grid barriers, on a control word that nothing sets.  When opts.wait_ms
+ * of device time have passed it records NSGA3_ETIMEOUT in the context and
+ * returns; the next nsga3_sync reports (and clears) it and the context stays
+ * usable.  Asynchronous on `stream`; never faults or traps.
+ * Errors: EINVAL (null context), ECUDA (launch).
+ */
+nsga3_status nsga3_wait_probe(nsga3_ctx* ctx, void* stream);
 
 /* Device bytes nsga3_create allocates for these arguments (each buffer
  * rounded up to 256 bytes); no allocation and no device work.  Without a

@@ -54,6 +54,7 @@ struct Ctrl {
     uint32_t sbar;           // arrivals at the barriers of the cooperative elimination
     unsigned long long pbar; // peel barrier: arrivals << 32 | points ranked so far
     unsigned long long prel; // peel barrier release: passes closed << 32 | points ranked
+    uint32_t never;          // a word nothing sets (the wait self-test polls it)
     int32_t nT;              // |S u F_l| (association set)
     int32_t Lstar;           // niche level threshold L*
     int32_t rlev;            // refs taken at level L*
@@ -87,6 +88,7 @@ struct RunView {
     int streaming;         // no Dom matrix: the peel recomputes dominance from Fp
     int norm_history;      // normalization with a running ideal and remembered extremes
     int problem;           // 0 softmax-simplex, 1 0-1 knapsack
+    unsigned long long wait_ns;  // budget of every device-side wait
     const int32_t* kp_p;   // m x d profits
     const int32_t* kp_w;   // m x d weights
     const int32_t* kp_cap; // m capacities
@@ -248,9 +250,8 @@ __device__ __forceinline__ bool lex_less(double a, int ia, double b, int ib)
 
 // ------------------------------------------------------ grid barriers -----
 // Barriers of a cooperative launch (every CTA resident), with a bounded
-// wait: they return false and record DEV_ETIMEOUT when the other CTAs did
-// not arrive within GRID_WAIT_NS of device time.
-constexpr unsigned long long GRID_WAIT_NS = 20ull * 1000 * 1000 * 1000;
+// wait: they give up and record DEV_ETIMEOUT when the other CTAs did not
+// arrive within the run's wait budget (RunView::wait_ns) of device time.
 
 __device__ __forceinline__ unsigned long long global_ns()
 {
@@ -278,6 +279,24 @@ __device__ __forceinline__ void st_release64(unsigned long long* p, unsigned lon
     asm volatile("st.release.gpu.global.u64 [%0], %1;\n" ::"l"(p), "l"(x) : "memory");
 }
 
+// Polls `done` until it returns true or wait_ns of device time have passed
+// (the clock is read every 1,024 polls; the poll count caps the wait too,
+// should the timer not advance); on expiry records DEV_ETIMEOUT and returns
+// false.  Every device-side wait goes through it.
+template <class Done>
+__device__ __forceinline__ bool bounded_wait(Ctrl* c, unsigned long long wait_ns, Done done)
+{
+    const unsigned long long t0 = global_ns();
+    unsigned it = 0;
+    while (!done()) {
+        if ((++it & 1023u) == 0u && (global_ns() - t0 > wait_ns || it > (1u << 30))) {
+            set_status(c, DEV_ETIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
 // Summing barrier of the peel: pass k's barrier adds (1 << 32) + add (this
 // CTA's new front members) to *bar; the CTA whose addition completes the
 // (k+1) * gridDim.x arrivals holds the running total of every CTA's adds
@@ -285,7 +304,8 @@ __device__ __forceinline__ void st_release64(unsigned long long* p, unsigned lon
 // number in *rel, which the others poll.  Returns the total (< 2^32) or,
 // on a timeout, ~0ull.  *bar and *rel are zero at launch.
 __device__ __forceinline__ unsigned long long grid_sync_sum(Ctrl* c, unsigned long long* bar, unsigned long long* rel,
-                                                           unsigned k, unsigned add, unsigned long long* s_val)
+                                                           unsigned k, unsigned add, unsigned long long wait_ns,
+                                                           unsigned long long* s_val)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -298,17 +318,9 @@ __device__ __forceinline__ unsigned long long grid_sync_sum(Ctrl* c, unsigned lo
             __threadfence();  // the arrivals' writes before the release
             st_release64(rel, ((unsigned long long)(k + 1) << 32) | val);
         } else {
-            const unsigned long long t0 = global_ns();
-            unsigned it = 0;
-            unsigned long long r;
-            while (((r = ld_acquire64(rel)) >> 32) < (unsigned long long)(k + 1)) {
-                if ((++it & 1023u) == 0u && (global_ns() - t0 > GRID_WAIT_NS || it > (1u << 30))) {
-                    set_status(c, DEV_ETIMEOUT);
-                    r = ~0ull;
-                    break;
-                }
-            }
-            val = r == ~0ull ? ~0ull : (r & 0xffffffffull);
+            unsigned long long r = 0;
+            const bool ok = bounded_wait(c, wait_ns, [&] { return ((r = ld_acquire64(rel)) >> 32) >= k + 1ull; });
+            val = ok ? (r & 0xffffffffull) : ~0ull;
         }
         __threadfence();
         *s_val = val;
@@ -320,23 +332,15 @@ __device__ __forceinline__ unsigned long long grid_sync_sum(Ctrl* c, unsigned lo
 // Counting barrier: the k-th barrier of a launch waits until *ctr reaches
 // k * gridDim.x (*ctr is zero at launch): one atomic on the arrival path and
 // a tight poll, for kernels that meet at a barrier many times per launch.
-__device__ __forceinline__ bool grid_sync_count(Ctrl* c, unsigned* ctr, unsigned target, int* s_ok)
+__device__ __forceinline__ bool grid_sync_count(Ctrl* c, unsigned* ctr, unsigned target, unsigned long long wait_ns,
+                                                int* s_ok)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         __threadfence();
-        if (atomicAdd(ctr, 1u) + 1u < target) {
-            const unsigned long long t0 = global_ns();
-            unsigned it = 0;
-            while (ld_acquire(ctr) < target) {
-                if ((++it & 1023u) == 0u && (global_ns() - t0 > GRID_WAIT_NS || it > (1u << 30))) {
-                    set_status(c, DEV_ETIMEOUT);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
+        if (atomicAdd(ctr, 1u) + 1u < target)
+            ok = bounded_wait(c, wait_ns, [&] { return ld_acquire(ctr) >= target; }) ? 1 : 0;
         __threadfence();
         *s_ok = ok;
     }

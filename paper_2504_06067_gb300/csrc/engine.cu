@@ -408,6 +408,7 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     v.streaming = ctx->opts.streaming ? 1 : 0;
     v.norm_history = ctx->opts.norm_history ? 1 : 0;
     v.problem = ctx->opts.problem;
+    v.wait_ns = (unsigned long long)(ctx->opts.wait_ms > 0 ? ctx->opts.wait_ms : 20000) * 1000000ull;
     v.seed = ctx->opts.seed;
     v.eta_c = ctx->opts.eta_c;
     v.eta_m = ctx->opts.eta_m;
@@ -882,6 +883,7 @@ void nsga3_default_opts(nsga3_opts* o)
     o->streaming = 0;
     o->norm_history = 0;
     o->W = nullptr;
+    o->wait_ms = 20000;
 }
 
 nsga3_status nsga3_create(int m, int d, int N, int ref_divisions, const nsga3_opts* opts,
@@ -1073,6 +1075,14 @@ nsga3_status nsga3_get_counter(nsga3_ctx* ctx, uint64_t* gen, void* stream)
     uint32_t g = 0;
     CK(cudaMemcpy(&g, &ctx->v.ctrl->gen, sizeof g, cudaMemcpyDeviceToHost));
     *gen = g;
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_wait_probe(nsga3_ctx* ctx, void* stream)
+{
+    if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
+    CK(launch_wait_probe(ctx->v, (cudaStream_t)stream));
+    ctx->host_launches += 1;
     return NSGA3_OK;
 }
 

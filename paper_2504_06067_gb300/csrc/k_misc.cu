@@ -200,7 +200,22 @@ __global__ void k_nan_pad(RunView v)
         v.skey[p] = 0xffffffffu;
 }
 
+// the wait self-test: one thread waits, with the barriers' bounded wait, for
+// a word nothing sets
+__global__ void k_wait_probe(RunView v)
+{
+    if (threadIdx.x != 0) return;
+    Ctrl* c = v.ctrl;
+    bounded_wait(c, v.wait_ns, [&] { return ld_acquire(&c->never) != 0u; });
+}
+
 }  // namespace
+
+cudaError_t launch_wait_probe(const RunView& v, cudaStream_t s)
+{
+    k_wait_probe<<<1, 32, 0, s>>>(v);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sel_reset(const RunView& v, cudaStream_t s)
 {

@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(SB) k_solve_coop(RunView v)
             }
             if (lane == 0) A[(size_t)q * ld + m] = 1.0;
         }
-        if (!grid_sync_count(c, &c->sbar, ++nbar * gridDim.x, &s_ok)) return;
+        if (!grid_sync_count(c, &c->sbar, ++nbar * gridDim.x, v.wait_ns, &s_ok)) return;
         for (int col = 0; col < m; ++col) {
             // pivot (every CTA): the first position p >= col of maximal
             // |A[ord[p]][col]|; a NaN never replaces the running maximum
@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(SB) k_solve_coop(RunView v)
                     A[(size_t)r * ld + k] = __dsub_rn(__ldcg(&A[(size_t)r * ld + k]),
                                                       __dmul_rn(factor, __ldcg(&A[(size_t)P * ld + k])));
             }
-            if (!grid_sync_count(c, &c->sbar, ++nbar * gridDim.x, &s_ok)) return;
+            if (!grid_sync_count(c, &c->sbar, ++nbar * gridDim.x, v.wait_ns, &s_ok)) return;
         }
     }
     if (blockIdx.x != 0) return;

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v
             __syncthreads();  // red and list are reused by the next chunk
         }
         // the barrier returns the points ranked after pass k
-        const unsigned long long tot = grid_sync_sum(c, &c->pbar, &c->prel, (unsigned)k, s_fs, &s_cum);
+        const unsigned long long tot = grid_sync_sum(c, &c->pbar, &c->prel, (unsigned)k, s_fs, v.wait_ns, &s_cum);
         if (tot == ~0ull) return;
         // close front k (the same decision in every CTA)
         const int ncum = (int)tot;

@@ -19,6 +19,8 @@ cudaError_t launch_vary_eval(const RunView& v, cudaStream_t s);
 cudaError_t launch_kp_init(const RunView& v, cudaStream_t s);
 cudaError_t launch_kp_vary_eval(const RunView& v, cudaStream_t s);
 cudaError_t launch_sel_reset(const RunView& v, cudaStream_t s);
+// the device-wait self-test (nsga3_wait_probe)
+cudaError_t launch_wait_probe(const RunView& v, cudaStream_t s);
 cudaError_t launch_check_finite(const RunView& v, cudaStream_t s);
 cudaError_t launch_sort(const RunView& v, int num_sms, cudaStream_t s);
 cudaError_t launch_dominance(const RunView& v, cudaStream_t s);

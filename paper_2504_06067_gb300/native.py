@@ -45,6 +45,7 @@ class nsga3_opts(C.Structure):
         ("kp_profit", C.c_void_p),
         ("kp_weight", C.c_void_p),
         ("kp_capacity", C.c_void_p),
+        ("wait_ms", C.c_int),
     ]
 
 
@@ -89,6 +90,7 @@ _SIGS = {
     "nsga3_set_counter": (_I, [_CTX, C.c_uint64, _P]),
     "nsga3_get_counter": (_I, [_CTX, C.POINTER(C.c_uint64), _P]),
     "nsga3_sync": (_I, [_CTX, _P]),
+    "nsga3_wait_probe": (_I, [_CTX, _P]),
     "nsga3_get_selection_info": (_I, [_CTX, _P]),
     "nsga3_get_normalization": (_I, [_CTX, _P, _P, _P]),
     "nsga3_get_association": (_I, [_CTX, _P, _P]),

@@ -136,3 +136,24 @@ def test_bad_arguments(n):
     for o in (n.default_opts(streaming=1), n.default_opts(problem=1)):
         assert n.nsga3_create(11, 12, 10, 1, C.byref(o), C.byref(h)) == n.EINVAL
         assert h.value is None
+
+
+def test_wait_budget_expires_cleanly(n, orc):
+    """Failure detection without a fault: a device wait on a word nothing
+    sets gives up after opts.wait_ms of device time and records
+    NSGA3_ETIMEOUT; nsga3_sync reports it once, and the same context then
+    selects like the oracle."""
+    import time
+    m, N, p = 3, 92, 12
+    Z = orc.refdirs(m, p)
+    with Run(n, m, m + 1, N, p, seed=2, wait_ms=300) as r:
+        t0 = time.time()
+        r.check(n.nsga3_wait_probe(r.ctx, None))
+        assert r.sync() == n.ETIMEOUT
+        assert 0.25 <= time.time() - t0 < 30.0
+        assert r.sync() == n.OK
+        F = wl.objectives("early", 2 * N, m, seed=1)
+        st, rank, sel = r.select(F, gen=1)
+        assert st == 0
+        ref = orc.select(F, N, Z, seed=2, gen=1)
+        assert np.array_equal(rank, ref["rank"]) and np.array_equal(sel, ref["selected"])
