@@ -155,12 +155,32 @@ __global__ void __launch_bounds__(AB) k_assoc_scan(RunView v)
                 bb = b;
             }
         }
-        // bounds are >= 0 (u, c_b, cos r >= 0): their bits order like unsigned ints
+        // The first scan takes the best-bounded blocks of up to CH lanes (each
+        // lane's best, in decreasing order of bound), all loads in flight
+        // together, so that `best` is near its final value before the bound
+        // filters the rest; the blocks taken are marked scanned (bound -4).
+        // Bounds are >= 0 (u, c_b, cos r >= 0): their bits order like
+        // unsigned ints.
+        int first[CH];
+        int nfirst = 0;
         {
-            const unsigned mx = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(bmax, 0.0f)));
-            const unsigned cand = (__float_as_uint(fmaxf(bmax, 0.0f)) == mx) ? (unsigned)bb : 0xffffffffu;
-            bb = (int)__reduce_min_sync(0xffffffffu, cand);
+            unsigned mine = (bb == 0x7fffffff) ? 0u : __float_as_uint(fmaxf(bmax, 0.0f)) + 1u;  // 0: none
+#pragma unroll
+            for (int t = 0; t < CH; ++t) {
+                const unsigned mx = __reduce_max_sync(0xffffffffu, mine);
+                first[t] = -1;
+                if (mx == 0u) continue;
+                const unsigned cand = (mine == mx) ? (unsigned)bb : 0xffffffffu;
+                const int b = (int)__reduce_min_sync(0xffffffffu, cand);
+                first[t] = b;
+                nfirst = t + 1;
+                if (bb == b) mine = 0u;  // this lane's best is taken
+            }
         }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < CH; ++t)
+            if (lane == 0 && first[t] >= 0) wbnd[first[t]] = -4.0f;
         __syncwarp();
         // phase 2: scan the best-bounded block, then every block the bound cannot exclude
         float best = -4.0f;
@@ -245,12 +265,13 @@ __global__ void __launch_bounds__(AB) k_assoc_scan(RunView v)
                 if (t < npend) take_block(qh[t], jj[t]);
             npend = 0;
         };
-        pend[0] = bb;
-        npend = 1;
+#pragma unroll
+        for (int t = 0; t < CH; ++t) pend[t] = first[t] >= 0 ? first[t] : 0;
+        npend = nfirst;
         flush();
         for (int base = 0; base < nb; base += 32) {
             const int b = base + lane;
-            const bool f = b < nb && b != bb && wbnd[b] + EPS >= best - band;
+            const bool f = b < nb && wbnd[b] + EPS >= best - band;
             unsigned msk = __ballot_sync(0xffffffffu, f);
             while (msk) {
                 const int b2 = base + __ffs(msk) - 1;
