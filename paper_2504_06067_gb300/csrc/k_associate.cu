@@ -125,11 +125,27 @@ __global__ void __launch_bounds__(AB) k_assoc_scan(RunView v)
     const float band = 2.0f * (float)(M + 4) * 5.9604644775390625e-08f + 1e-12f;
     const int w = v.w;
 
-    for (int pt = blockIdx.x * 8 + warp; pt < nT; pt += gridDim.x * 8) {
+    // the next point's unit vector and |f'| are loaded while this one is
+    // scanned
+    const int pstride = gridDim.x * 8;
+    float un[M];
+    double nfn = 0.0;
+    {
+        const int p0 = blockIdx.x * 8 + warp;
+#pragma unroll
+        for (int q = 0; q < M; ++q) un[q] = p0 < nT ? v.uhat[(size_t)p0 * M4 + q] : 0.0f;
+        if (p0 < nT) nfn = v.fnorm[p0];
+    }
+    for (int pt = blockIdx.x * 8 + warp; pt < nT; pt += pstride) {
         float u[M];
 #pragma unroll
-        for (int q = 0; q < M; ++q) u[q] = v.uhat[(size_t)pt * M4 + q];
-        if (v.fnorm[pt] == 0.0) {  // every distance is 0: handled by the finalisation
+        for (int q = 0; q < M; ++q) u[q] = un[q];
+        const double nf = nfn;
+        const int pn = pt + pstride;
+#pragma unroll
+        for (int q = 0; q < M; ++q) un[q] = pn < nT ? v.uhat[(size_t)pn * M4 + q] : 0.0f;
+        if (pn < nT) nfn = v.fnorm[pn];
+        if (nf == 0.0) {  // every distance is 0: handled by the finalisation
             if (lane == 0) v.arun[pt] = make_int2(0, 0);
             continue;
         }
