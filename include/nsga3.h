@@ -1,13 +1,12 @@
 /*
  * nsga3.h -- C ABI of the GB300 NSGA-III environmental-selection engine.
  *
- * The method is the per-generation NSGA-III step of arXiv 2504.06067:
- * variation of the parents (Alg. 1 line 1), merge R_t = P_t u Q_t (line 2),
- * non-dominated sorting into F_s, F_l, F_drop (line 3), normalization and
- * association with reference points (line 5; Alg. 2 lines 1-4, Eq. 2),
- * niche counts (line 6; Alg. 2 lines 5-7) and niche selection of the last
- * front (lines 7-19; Alg. 2 lines 8-26).  All objectives are minimised
- * (Eq. 1).
+ * The method is the per-generation NSGA-III step of arXiv 2504.06067
+ * (Alg. 1, in its tensorized form Alg. 2): variation of the parents, merge
+ * R_t = P_t u Q_t, non-dominated sorting into F_s, F_l, F_drop,
+ * normalization and association with reference points (Eq. 2), niche
+ * counts and niche selection of the last front.  All objectives are
+ * minimised (Eq. 1).
  *
  * Conventions for every call:
  *   - Objective matrices are FP32, row-major, one row per individual.
@@ -135,7 +134,7 @@ nsga3_status nsga3_get_refs(nsga3_ctx* ctx, double* Z);
 
 /*
  * Environmental selection of N out of the merged 2N individuals (Alg. 1
- * lines 3-19, Alg. 2).
+ * from the non-dominated sort on, Alg. 2).
  *   objs      any, 2N x m FP32 objectives (minimised); read before return
  *             on the stream.
  *   ranks     any, 2N int32 out: 0-based front index for fronts F_1..F_l,
@@ -152,7 +151,7 @@ nsga3_status nsga3_select(nsga3_ctx* ctx, const float* objs, int32_t* ranks, int
  * parent ranks 0; generation counter 0.  Needs opts.W. */
 nsga3_status nsga3_init(nsga3_ctx* ctx, void* stream);
 
-/* Variation + objective only (Alg. 1 line 1): children of the current
+/* Variation + objective only (Alg. 1, the crossover and mutation step): children of the current
  * parents into rows N..2N-1 of the merged population (see
  * nsga3_get_children).  Does not advance the counter.  Needs opts.W. */
 nsga3_status nsga3_vary(nsga3_ctx* ctx, void* stream);

@@ -9,8 +9,8 @@
  *
  * Every routine follows the paper's definitions step by step, in the
  * paper's order, with no blocking, fusion or reordering:
- *   - dominance and non-dominated sorting:  Sec. II-C, Alg. 1 (line "Non-
- *     dominated-sort"), minimisation as in Eq. (1);
+ *   - dominance and non-dominated sorting:  Sec. II-C, Alg. 1 (the
+ *     non-dominated sort), minimisation as in Eq. (1);
  *   - reference directions: Sec. II-C (points uniform on the unit simplex,
  *     w close to n), Das-Dennis lattice;
  *   - normalization: Alg. 1 "using normalized objectives" / Alg. 2 "Normalize";

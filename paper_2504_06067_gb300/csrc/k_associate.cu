@@ -1,7 +1,7 @@
 // k_associate.cu -- association of S u F_l with the reference directions
-// (Alg. 2 lines 2-4, Eq. 2 read as the perpendicular distance
+// (Alg. 2, Eq. 2 read as the perpendicular distance
 // D_ij = |f'| sqrt(1 - cos^2), pi_i = argmin_j D_ij, d_i = min_j D_ij) and
-// the niche counts rho (over S) and rho' (over F_l) of Alg. 2 lines 5-6.
+// the niche counts rho (over S) and rho' (over F_l) of Alg. 2.
 //
 // Exactness.  The FP64 distance is evaluated operation for operation like a
 // plain CPU evaluation (_rn intrinsics, left-to-right sums), but only for

@@ -1,5 +1,5 @@
-// k_dominance.cu -- bit-packed Pareto-dominance matrix (Alg. 1 line 3,
-// "Non-dominated-sort"; dominance for minimisation, Eq. 1).
+// k_dominance.cu -- bit-packed Pareto-dominance matrix (Alg. 1, the
+// non-dominated sort; dominance for minimisation, Eq. 1).
 //
 // Dom[I][j] (u32, word-major, I = i / 32) holds bit (i mod 32) = "i
 // dominates j": a column j's dominators are NW words with j contiguous

@@ -1,5 +1,5 @@
-// k_niche.cu -- niche selection of K = N - |S| members of F_l (Alg. 1 lines
-// 7-19; Alg. 2 lines 7-26).
+// k_niche.cu -- niche selection of K = N - |S| members of F_l (the niching
+// loop of Alg. 1; its cached batched form in Alg. 2).
 //
 // The paper's loop takes, round after round, one member from every
 // reference of minimum niche count (the cache tensor Q and cursor s of

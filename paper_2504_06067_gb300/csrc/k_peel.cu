@@ -1,5 +1,5 @@
 // k_peel.cu -- non-dominated front peeling over the bit-packed matrix
-// (Alg. 1 line 3: fronts F_1, F_2, ... until |F_1| + ... + |F_l| >= N,
+// (Alg. 1, the non-dominated sort: fronts F_1, F_2, ... until |F_1| + ... + |F_l| >= N,
 // splitting R_t into S = F_1..F_{l-1}, F_l and F_drop; Sec. II-C).
 //
 // One cooperative launch runs every pass: the CTAs meet at a grid barrier

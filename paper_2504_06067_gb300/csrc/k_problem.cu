@@ -5,7 +5,7 @@
 // lexicographic order of k, optional inner layer (1 - tau)/m + tau z; one
 // thread unranks one composition.  FP64 with _rn intrinsics.
 //
-// Variation (Alg. 1 line 1; Sec. III-A), one warp per offspring pair q:
+// Variation (Alg. 1, crossover and mutation; Sec. III-A), one warp per offspring pair q:
 //   tournament: Philox(q, gen, 1, 0) -> a1, b1, a2, b2 in [0, N); the lower
 //   front wins, ties keep the first drawn; Philox(q, gen, 1, 1) word 0 < p_c
 //   lets the pair cross.  SBX per variable v (Philox(q*d+v, gen, 2, 0)):

@@ -1,5 +1,5 @@
 // k_sort.cu -- bucket order of the merged population by its first objective,
-// used by the dominance build and the front peel (Alg. 1 line 3).
+// used by the dominance build and the front peel (Alg. 1, the non-dominated sort).
 //
 // Dominance needs f_i0 <= f_j0, so when every point of a row block has a
 // smaller f_0 than every point of a column block only "row dominates column"
