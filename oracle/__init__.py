@@ -155,7 +155,7 @@ def nds(F, N: int, full_sort: bool = False):
 
 
 def normalize(F, rank, l: int):
-    """Ideal point, ASF extremes and intercepts over S u F_l (Alg. 2 "Normalize")."""
+    """Ideal point, ASF extremes and intercepts over S u F_l (the normalization of Alg. 2)."""
     F = _f32(F)
     rank = _i32(rank)
     n2, m = F.shape

@@ -13,7 +13,7 @@
  *     non-dominated sort), minimisation as in Eq. (1);
  *   - reference directions: Sec. II-C (points uniform on the unit simplex,
  *     w close to n), Das-Dennis lattice;
- *   - normalization: Alg. 1 "using normalized objectives" / Alg. 2 "Normalize";
+ *   - normalization: the normalization step of Alg. 1 and Alg. 2;
  *     the paper gives no formula, so the Deb & Jain (NSGA-III) reading is
  *     used: ideal point, ASF extreme points, hyperplane intercepts;
  *   - perpendicular distance and association: Eq. (2) (read with cos^2,
@@ -242,7 +242,7 @@ int orc_nds(const float *F, int n2, int m, int N, int full_sort, int32_t *rank)
 }
 
 /* ---------------------------------------------------------------------- */
-/* Normalization (Alg. 1 "normalized objectives", Alg. 2 "Normalize").     */
+/* Normalization (the normalization step of Alg. 1 and Alg. 2).           */
 /* Reading (Deb & Jain NSGA-III, stateless, current generation only):      */
 /*   T = S u F_l (rank in [0, l]);                                         */
 /*   ideal  z*_q = min_{i in T} f_iq;  translated ft_iq = f_iq - z*_q;     */
@@ -553,9 +553,9 @@ void orc_associate(const float *F, const int32_t *rank, int n2, int m, int l,
 /* ---------------------------------------------------------------------- */
 /* Niche selection.  Inputs: rank (l = selecting front), pi, dist; picks   */
 /* K = N - |S| members of F_l.  Random choices are realised by fixed       */
-/* Philox priorities of this generation: "randomly select a reference      */
-/* point among those of minimum niche count" takes the one of smallest     */
-/* (ref priority, j); "randomly select an individual" takes the remaining  */
+/* Philox priorities of this generation: the random pick of a reference   */
+/* among those of minimum niche count takes the one of smallest            */
+/* (ref priority, j); the random pick of a member takes the remaining      */
 /* member of smallest (member priority, i).  picked[i] = 1 for chosen i.   */
 /* ---------------------------------------------------------------------- */
 

@@ -1,4 +1,4 @@
-// k_normalize.cu -- "Normalize" of Alg. 1 and Alg. 2, read as
+// k_normalize.cu -- the normalization step of Alg. 1 and Alg. 2, read as
 // the NSGA-III normalization of Deb & Jain (the paper gives no formula):
 //   T = S u F_l;  z*_q = min_T f_q;  f~ = f - z*;
 //   e_q = argmin_T max_r f~_r / w_qr  (w_qr = 1 if r == q else 1e-6, ties ->

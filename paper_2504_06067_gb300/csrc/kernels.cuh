@@ -11,7 +11,7 @@ cudaError_t launch_refdirs(const RunView& v, int p1, int p2, double tau, double*
 cudaError_t launch_init(const RunView& v, cudaStream_t s);
 cudaError_t launch_nan_pad(const RunView& v, cudaStream_t s);
 
-// variation + objective (Alg. 1 "Crossover+Mutation", Sec. III-A)
+// variation + objective (Alg. 1, crossover and mutation; Sec. III-A)
 cudaError_t launch_vary_eval(const RunView& v, cudaStream_t s);
 
 // selection (Alg. 1 sort / Alg. 2)
