@@ -166,3 +166,13 @@ def test_generations_many(n, orc, cfg):
             and cfg.m > 16
         # + the objective's dot-product kernel
         assert k.value == 21 + 5 + (1 if cfg.m > 32 else 0) + (1 if split else 0) + 1
+
+
+@pytest.mark.parametrize("m,N", [(11, 2), (33, 2), (64, 6), (512, 4)])
+def test_tiny_population_many_objectives(n, orc, m, N):
+    """Fewer merged points than objectives (the extreme-point system is then
+    singular and falls back to the nadir): same results as the oracle."""
+    Z = orc.refdirs(m, 1)
+    with Run(n, m, m + 1, N, 1, seed=6) as r:
+        for s, kind in enumerate(("uniform", "early", "corners")):
+            _compare(orc, r, _inputs(kind, 2 * N, m, s), Z, seed=6, gen=s + 1)
