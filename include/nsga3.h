@@ -79,6 +79,10 @@ typedef struct {
                                cooperative kernels), in ms of device time; past it the
                                kernel records NSGA3_ETIMEOUT and returns (default 20,000;
                                <= 0: the default) */
+    int phase_timing;       /* CUDA events recorded inside the graphs for nsga3_phase_times:
+                               0 (default) none; 1 around the dominance build and the
+                               front peel only; 2 around every phase.  Each event node
+                               adds a few microseconds to every replay */
 } nsga3_opts;
 
 /* Fills *o with the defaults above (seed 0, single layer, tau 0.5). */
@@ -221,6 +225,9 @@ nsga3_status nsga3_get_association(nsga3_ctx* ctx, int32_t* pi, double* dist);
  *   ms[2] dominance matrix kernel, ms[3] front peel (all passes),
  *   ms[4] normalization + association + niching, ms[5] compaction + gather,
  *   ms[6] whole graph.  Synchronous; n is the capacity of ms (up to 7).
+ * Phases that opts.phase_timing does not time read -1 (with phase_timing
+ * 1 only ms[2] and ms[3] are measured).  Errors: EINVAL with phase_timing 0 (eager
+ * execution, NSGA3_EAGER=1, times every phase whatever the option).
  */
 nsga3_status nsga3_phase_times(nsga3_ctx* ctx, float* ms, int n);
 

@@ -55,6 +55,7 @@ struct nsga3_ctx {
     bool count_only = false;       // sizing pass: count bytes, allocate nothing
     size_t counted = 0;
     bool eager = false; // NSGA3_EAGER=1: no graphs, host-driven peel loop (profiling)
+    unsigned ev_mask = 0; // bit e set: event e is recorded (opts.phase_timing; eager: all)
     std::string err;
     // batched graph cache
     std::vector<nsga3_ctx*> batch_key;
@@ -143,9 +144,11 @@ nsga3_status alloc(nsga3_ctx* ctx, T** p, size_t count)
         if (s_ != NSGA3_OK) return s_;                       \
     } while (0)
 
+// Timing events are recorded only where opts.phase_timing asks for them: an
+// event node in a graph costs a few microseconds of every replay
 nsga3_status record_event(nsga3_ctx* ctx, cudaStream_t s, int which, bool events)
 {
-    if (!events) return NSGA3_OK;
+    if (!events || !((ctx->ev_mask >> which) & 1u)) return NSGA3_OK;
     if (ctx->eager)
         CK(cudaEventRecord(ctx->ev[which], s));
     else
@@ -678,6 +681,8 @@ nsga3_status ctx_fields(nsga3_ctx* ctx, int m, int d, int N, int ref_divisions, 
     if (ref_divisions < 1 || o.p2 < 0) return fail(ctx, NSGA3_EINVAL, "bad reference divisions");
     if (!(o.tau >= 0.0 && o.tau <= 1.0)) return fail(ctx, NSGA3_EINVAL, "tau outside [0,1]");
     if (o.problem != 0 && o.problem != 1) return fail(ctx, NSGA3_EINVAL, "problem %d unknown", o.problem);
+    if (o.phase_timing < 0 || o.phase_timing > 2)
+        return fail(ctx, NSGA3_EINVAL, "phase_timing %d outside [0, 2]", o.phase_timing);
     if (o.streaming && m > NSGA3_FAST_M)
         return fail(ctx, NSGA3_EINVAL, "streaming dominance supports m <= %d", NSGA3_FAST_M);
     if (o.problem == 1 && m > NSGA3_FAST_M)
@@ -732,6 +737,10 @@ nsga3_status ctx_create(int m, int d, int N, int ref_divisions, const nsga3_opts
     if (!st) {
         const char* e = getenv("NSGA3_EAGER");
         ctx->eager = e && e[0] == '1';
+        const int pt = ctx->opts.phase_timing;
+        ctx->ev_mask = (ctx->eager || pt == 2) ? (1u << EV_COUNT) - 1u
+                       : pt == 1               ? (1u << EV_RESET) | (1u << EV_DOM) | (1u << EV_PEEL)
+                                               : 0u;
         if (cudaGetDevice(&ctx->device) != cudaSuccess ||
             cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
             cudaGetLastError();
@@ -884,6 +893,7 @@ void nsga3_default_opts(nsga3_opts* o)
     o->norm_history = 0;
     o->W = nullptr;
     o->wait_ms = 20000;
+    o->phase_timing = 0;
 }
 
 nsga3_status nsga3_create(int m, int d, int N, int ref_divisions, const nsga3_opts* opts,
@@ -1141,13 +1151,19 @@ nsga3_status nsga3_get_association(nsga3_ctx* ctx, int32_t* pi, double* dist)
 nsga3_status nsga3_phase_times(nsga3_ctx* ctx, float* ms, int n)
 {
     if (!ctx || !ms || n < 1) return fail(ctx, NSGA3_EINVAL, "bad arguments");
-    CK(cudaEventSynchronize(ctx->ev[EV_END]));
+    if (!ctx->ev_mask) return fail(ctx, NSGA3_EINVAL, "phase timing is off (opts.phase_timing = 0)");
+    // the last event that the graphs record closes the timed phases
+    int last = EV_COUNT - 1;
+    while (!((ctx->ev_mask >> last) & 1u)) --last;
+    CK(cudaEventSynchronize(ctx->ev[last]));
     const int pairs[7][2] = {{EV_START, EV_VARY}, {EV_VARY, EV_RESET}, {EV_RESET, EV_DOM},
                              {EV_DOM, EV_PEEL},   {EV_PEEL, EV_NICHE}, {EV_NICHE, EV_END},
                              {EV_START, EV_END}};
     for (int t = 0; t < n && t < 7; ++t) {
-        float x = 0.0f;
-        CK(cudaEventElapsedTime(&x, ctx->ev[pairs[t][0]], ctx->ev[pairs[t][1]]));
+        const unsigned need = (1u << pairs[t][0]) | (1u << pairs[t][1]);
+        float x = -1.0f;  // a phase whose events are not recorded
+        if ((ctx->ev_mask & need) == need)
+            CK(cudaEventElapsedTime(&x, ctx->ev[pairs[t][0]], ctx->ev[pairs[t][1]]));
         ms[t] = x;
     }
     return NSGA3_OK;

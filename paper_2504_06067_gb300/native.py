@@ -46,6 +46,7 @@ class nsga3_opts(C.Structure):
         ("kp_weight", C.c_void_p),
         ("kp_capacity", C.c_void_p),
         ("wait_ms", C.c_int),
+        ("phase_timing", C.c_int),
     ]
 
 

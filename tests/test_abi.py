@@ -90,6 +90,17 @@ def test_many_objectives_workspace(lib):
         assert n.nsga3_workspace_bytes(m, 1000, 800, 1, C.byref(o), C.byref(out)) == n.EINVAL
 
 
+def test_phase_timing_option(lib):
+    """opts.phase_timing defaults to 0 (no timing events in the graphs) and
+    takes 0, 1 or 2."""
+    from paper_2504_06067_gb300 import native as n
+    assert n.default_opts().phase_timing == 0
+    out = C.c_uint64()
+    for lv, want in ((0, n.OK), (1, n.OK), (2, n.OK), (-1, n.EINVAL), (3, n.EINVAL)):
+        o = n.default_opts(phase_timing=lv)
+        assert n.nsga3_workspace_bytes(3, 12, 92, 12, C.byref(o), C.byref(out)) == want
+
+
 def test_server_create_without_gpu_fails_cleanly(lib):
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():

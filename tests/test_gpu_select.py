@@ -157,3 +157,36 @@ def test_wait_budget_expires_cleanly(n, orc):
         assert st == 0
         ref = orc.select(F, N, Z, seed=2, gen=1)
         assert np.array_equal(rank, ref["rank"]) and np.array_equal(sel, ref["selected"])
+
+
+def test_phase_timing_levels(n):
+    """opts.phase_timing: 0 records no timing events in the graphs (phase
+    times are refused), 1 times the dominance build and the peel, 2 every
+    phase; the event nodes change nothing in the results."""
+    import ctypes as C
+    import os
+    m, d, N, p = 3, 4, 92, 12
+    W = wl.objective_weights(m, 1)
+    pops = []
+    for lv in (0, 1, 2):
+        with Run(n, m, d, N, p, seed=3, W=W, phase_timing=lv) as r:
+            r.check(n.nsga3_init(r.ctx, None))
+            for _ in range(3):
+                r.check(n.nsga3_step(r.ctx, None))
+            assert r.sync() == 0
+            ms = (C.c_float * 7)()
+            st = n.nsga3_phase_times(r.ctx, ms, 7)
+            v = list(ms)
+            if lv == 0:
+                if os.environ.get("NSGA3_EAGER") != "1":  # eager execution times every phase
+                    assert st == n.EINVAL
+            else:
+                assert st == n.OK and v[2] > 0 and v[3] > 0
+                if lv == 1:
+                    assert all(v[t] == -1.0 for t in (0, 1, 4, 5, 6))
+                else:
+                    assert min(v) >= 0 and v[6] >= v[2] + v[3] - 1e-3
+            pops.append(r.population())
+    for P in pops[1:]:
+        for a, b in zip(pops[0], P):
+            assert np.array_equal(a, b)
