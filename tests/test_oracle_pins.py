@@ -667,3 +667,140 @@ def test_normalized_hv_app_e(orc):
     v = orc.normalized_hv([fmin], fmin, fmax)
     expect = np.prod(1.01 * fmax - fmin) / np.prod(1.01 * fmax - 0.9 * fmin)
     assert abs(v - expect) < 1e-12 and 0 < v < 1
+
+
+# -------------------------------------- pins that planted mistakes need --
+# Each of these closes a gap that a planted mistake in the oracle
+# (tests/test_oracle_mutants.py) slipped through.
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_normalize_with_row_exchanges_matches_lapack(orc, seed):
+    """Members spread over the inside of the simplex (m = 12, Dirichlet(2))
+    give extreme vectors whose matrix is not diagonally dominant, so partial
+    pivoting exchanges rows (LAPACK's LU permutation is not the identity);
+    the intercepts still equal 1 / LAPACK's solution of (E - z*) b = 1."""
+    sl = pytest.importorskip("scipy.linalg")
+    m = 12
+    rng = np.random.default_rng([m, seed])
+    F = rng.dirichlet(np.full(m, 2.0), size=300).astype(np.float32)
+    rank = np.zeros(len(F), dtype=np.int32)
+    zstar, a, ext, fb = orc.normalize(F, rank, 0)
+    E = F[ext].astype(np.float64) - zstar
+    P, _, _ = sl.lu(E)
+    assert not np.array_equal(P, np.eye(m))  # the system needs row exchanges
+    assert not fb and len(set(ext.tolist())) == m
+    np.testing.assert_allclose(a, 1.0 / np.linalg.solve(E, np.ones(m)), rtol=1e-9, atol=0)
+
+
+def test_sbx_spread_factor_distribution(orc):
+    """SBX's spread factor beta = |c1 - c2| / |x1 - x2| has the published
+    density (Deb and Agrawal, 1995) 0.5 (eta+1) beta^eta on [0, 1] and
+    0.5 (eta+1) beta^-(eta+2) above 1, i.e. the distribution function
+    beta^(eta+1) / 2 below 1 and 1 - beta^-(eta+1) / 2 above.  Two parents
+    0.45 and 0.55 in every variable (children clip only for beta > 10);
+    crossed variables of the pairs whose parents differ; Kolmogorov-Smirnov
+    distance against that law."""
+    eta, d = 2.0, 400
+    X = np.empty((2, d), dtype=np.float32)
+    X[0], X[1] = 0.45, 0.55
+    rank = np.zeros(2, dtype=np.int32)
+    gap = float(X[1, 0]) - float(X[0, 0])
+    betas = []
+    for gen in range(80):
+        C = orc.vary(X, rank, seed=11, gen=gen, eta_c=eta, p_m=0.0).astype(np.float64)
+        diff = np.abs(C[0] - C[1])
+        if not diff.any():
+            continue  # both parents are the same individual
+        crossed = diff != gap
+        inside = (C[0] > 0) & (C[0] < 1) & (C[1] > 0) & (C[1] < 1)
+        betas.append(diff[crossed & inside] / gap)
+    beta = np.sort(np.concatenate(betas))
+    n = len(beta)
+    assert n > 4000
+    law = np.where(beta <= 1.0, 0.5 * beta ** (eta + 1), 1.0 - 0.5 * beta ** -(eta + 1))
+    ecdf_hi = np.arange(1, n + 1) / n
+    ks = max(np.max(ecdf_hi - law), np.max(law - (ecdf_hi - 1.0 / n)))
+    assert ks < 1.95 / math.sqrt(n)  # the 0.1 % critical value
+
+
+def test_polynomial_mutation_symmetric_at_centre(orc):
+    """Bounded polynomial mutation of y = 0.5 on [0, 1]: the two branches
+    mirror each other (the distances to both bounds are equal), so the
+    mutated values rise as often as they fall, by the same amounts in law,
+    and stay inside [0, 1]."""
+    N, d = 200, 100
+    X = np.full((N, d), 0.5, dtype=np.float32)
+    rank = np.zeros(N, dtype=np.int32)
+    C = orc.vary(X, rank, seed=4, gen=1, p_c=0.0, p_m=0.3).astype(np.float64)
+    dlt = (C - 0.5)[C != 0.5]
+    assert len(dlt) > 0.25 * N * d and C.min() >= 0.0 and C.max() <= 1.0
+    assert abs(np.mean(dlt > 0) - 0.5) < 0.03
+    up, down = np.sort(dlt[dlt > 0]), np.sort(-dlt[dlt < 0])
+    # two-sample Kolmogorov-Smirnov distance between rises and falls
+    grid = np.concatenate([up, down])
+    ks = np.max(np.abs(np.searchsorted(up, grid, side="right") / len(up)
+                       - np.searchsorted(down, grid, side="right") / len(down)))
+    assert ks < 1.95 * math.sqrt(1.0 / len(up) + 1.0 / len(down))
+
+
+def test_tournament_winner_distribution(orc):
+    """Binary tournament on two uniform draws: with half the parents in
+    front 0 and half in front 1 a winner is in front 0 with probability
+    1 - (1/2)^2 = 3/4, for the first and for the second parent of a pair;
+    with one front every parent is equally likely to win.  Without
+    crossover and mutation the children are copies of the winners."""
+    N, d = 400, 3
+    X = np.tile(((np.arange(N) + 0.5) / N)[:, None], (1, d)).astype(np.float32)
+    rng = np.random.default_rng(5)
+    two = rng.permutation(np.repeat([0, 1], N // 2)).astype(np.int32)
+    one = np.zeros(N, dtype=np.int32)
+    front0 = [0, 0]
+    upper = 0
+    for gen in range(10):
+        C = orc.vary(X, two, seed=21, gen=gen, p_c=0.0, p_m=0.0)
+        idx = np.rint(C[:, 0].astype(np.float64) * N - 0.5).astype(int)
+        assert np.array_equal(C, X[idx])
+        for h in (0, 1):
+            front0[h] += int(np.sum(two[idx[h::2]] == 0))
+        C = orc.vary(X, one, seed=22, gen=gen, p_c=0.0, p_m=0.0)
+        idx = np.rint(C[:, 0].astype(np.float64) * N - 0.5).astype(int)
+        upper += int(np.sum(idx >= N // 2))
+    for h in (0, 1):
+        assert abs(front0[h] / (10 * N // 2) - 0.75) < 0.04
+    assert abs(upper / (10 * N) - 0.5) < 0.04
+
+
+def test_objective_hand_example(orc):
+    """m = 3, k = 2 with W's rows e_0, e_1 and 0: W x[:2] = (x_0, x_1, 0), so
+    f = (1 + g) (e^x0, e^x1, 1) / (e^x0 + e^x1 + 1) with g the squared
+    distance of x[2:] to 0.5."""
+    W = np.array([[1, 0], [0, 1], [0, 0]], dtype=np.float32)
+    X = np.array([[0.25, 0.75, 0.5, 0.5, 0.5],
+                  [1.0, 0.0, 0.0, 0.5, 1.0]], dtype=np.float32)
+    F = orc.evaluate(X, W).astype(np.float64)
+    g = np.array([0.0, 0.25 + 0.25])
+    for x, f, gi in zip(X.astype(np.float64), F, g):
+        e = np.array([math.exp(x[0]), math.exp(x[1]), 1.0])
+        np.testing.assert_allclose(f, (1.0 + gi) * e / e.sum(), rtol=1e-6, atol=0)
+
+
+def test_kp_repair_keeps_an_exact_fit(orc):
+    """The hand example's four items with capacities equal to their full
+    loads (29, 18): every knapsack is exactly full, which is feasible, so
+    the repair removes nothing and nothing is left over."""
+    profit = np.array([[10, 1, 6, 4], [1, 2, 6, 5]], dtype=np.int32)
+    weight = np.array([[5, 10, 6, 8], [1, 10, 2, 5]], dtype=np.int32)
+    X, F = orc.kp_eval(np.ones((1, 4), dtype=np.float32), profit, weight,
+                       np.array([29, 18], dtype=np.int32))
+    assert np.array_equal(X[0], [1, 1, 1, 1]) and np.array_equal(F[0], [0, 0])
+
+
+def test_kp_bit_flip_flips_ones_and_zeros(orc):
+    """Bit-flip mutation changes a one as often as a zero: all-zero and
+    all-one populations both change in about a p_m fraction of their bits."""
+    N, d, pm = 200, 100, 0.1
+    rank = np.zeros(N, dtype=np.int32)
+    for v in (0.0, 1.0):
+        X = np.full((N, d), v, dtype=np.float32)
+        C = orc.kp_vary(X, rank, seed=3, gen=1, p_c=0.0, p_m=pm)
+        assert abs(np.mean(C != X) - pm) < 0.01
