@@ -40,6 +40,7 @@ MUTANTS = [
     ("dominance_not_strict", "if (x < y) any_lt = 1;", "if (x <= y) any_lt = 1;", 1),
     ("dominance_maximises", "if (!(x <= y)) all_le = 0;", "if (!(x >= y)) all_le = 0;", 1),
     ("last_front_off_by_one", "if (l < 0 && cum >= N) l = k;", "if (l < 0 && cum > N) l = k;", 1),
+    ("das_dennis_no_inner_layer", "if (p2 > 0) orc_dd_rec(m, p2, 0, p2, k, Z, &row, 1, tau);", "", 1),
     # normalization
     ("asf_weights_swapped", "double wq = (r == q) ? 1.0 : 1e-6;",
      "double wq = (r == q) ? 1e-6 : 1.0;", 2),
@@ -52,16 +53,28 @@ MUTANTS = [
      "double prod = AQ(cc, r) * b[cc];", 2),
     ("intercept_not_inverted", "a[q] = 1.0 / b[q];", "a[q] = b[q];", 2),
     ("fallback_zero_span", "a[q] = (mx == 0.0) ? 1.0 : mx;", "a[q] = mx;", 2),
+    # normalization with history
+    ("history_not_kept", "*hvalid = 1;", "*hvalid = 0;", 1),
+    ("history_ideal_restarts", "for (int q = 0; q < m; ++q) zstar[q] = *hvalid ? hz[q] : INFINITY;",
+     "for (int q = 0; q < m; ++q) zstar[q] = INFINITY;", 1),
+    ("history_vectors_ignored", "const int ncand = n2 + (*hvalid ? m : 0);", "const int ncand = n2;", 1),
     # association (Eq. 2)
     ("cosine_not_squared", "double cc = c * c;", "double cc = c;", 1),
     ("point_not_normalised", "fp[q] = ft / a[q];", "fp[q] = ft;", 1),
     ("direction_norm_squared", "nz[j] = sqrt(s);", "nz[j] = s;", 1),
+    ("association_last_minimum", "if (D < best) { best = D; arg = j; }",
+     "if (D <= best) { best = D; arg = j; }", 1),
     # niching (Alg. 1 loop and Alg. 2 cached loop)
     ("niche_farthest_member", "if (t < 0 || dist[i] < dist[t]) t = i;",
      "if (t < 0 || dist[i] > dist[t]) t = i;", 2),
     ("niche_largest_count", "if (v < 0 || rho[j] < rho[v] ||", "if (v < 0 || rho[j] > rho[v] ||", 1),
     ("niche_member_priority_max", "if (t < 0 || pr < bp) { t = i; bp = pr; }",
      "if (t < 0 || pr > bp) { t = i; bp = pr; }", 1),
+    ("batched_first_batch_unsorted", "orc_sort_batch(B, nb, rprio);\n    int keep = nb < K ? nb : K;",
+     "int keep = nb < K ? nb : K;", 1),
+    ("batched_queue_reversed", "while (y >= lo && (mprio[Q[y]] > mprio[v] ||",
+     "while (y >= lo && (mprio[Q[y]] < mprio[v] ||", 1),
+    ("selection_one_short", "int K = N - nS;", "int K = N - nS - 1;", 1),
     # variation (Sec. III-A): tournament, SBX, polynomial mutation
     ("tournament_prefers_worse", "uint32_t p1 = rank[b1] < rank[a1] ? b1 : a1;",
      "uint32_t p1 = rank[b1] > rank[a1] ? b1 : a1;", 2),
@@ -70,8 +83,12 @@ MUTANTS = [
     ("sbx_spread_exponent", "double e = 1.0 / (eta_c + 1.0);", "double e = 1.0 / eta_c;", 1),
     ("sbx_upper_branch", "pow(1.0 / (2.0 * (1.0 - u)), e)", "pow(1.0 / (2.0 * u), e)", 1),
     ("mutation_upper_sign", "dq = 1.0 - pow(val, mp);", "dq = pow(val, mp) - 1.0;", 1),
+    ("sbx_never_swapped", "if ((float)orc_uniform(s[2]) < 0.5f) { double tt = c1; c1 = c2; c2 = tt; }",
+     "", 1),
+    ("mutation_lower_distance", "double xy = 1.0 - d1;", "double xy = 1.0 - d2;", 1),
     # objective
     ("softmax_not_divided", "double sj = e[j] / den;", "double sj = e[j];", 1),
+    ("softmax_without_exp", "e[j] = exp(s);", "e[j] = s;", 1),
     ("distance_not_centred", "double t = (double)x[v] - 0.5;", "double t = (double)x[v];", 1),
     ("distance_skips_first", "for (int v = k; v < d; ++v) {", "for (int v = k + 1; v < d; ++v) {", 1),
     ("weights_transposed", "double pr = (double)W[j * k + v] * (double)x[v];",
@@ -84,9 +101,16 @@ MUTANTS = [
      "if (x[v] != 0.0f) left += p[(size_t)j * d + v];", 1),
     ("bit_set_not_flipped", "if ((float)orc_uniform(pm[0]) < p_m) c1 = 1.0f - c1;",
      "if ((float)orc_uniform(pm[0]) < p_m) c1 = 1.0f;", 1),
+    ("uniform_crossover_missing",
+     "if (cross && (float)orc_uniform(s[0]) < 0.5f) { float tt = c1; c1 = c2; c2 = tt; }", "", 1),
+    ("knapsack_init_biased", "X[(size_t)i * d + v] = ((float)orc_uniform(o[0]) < 0.5f) ? 1.0f : 0.0f;",
+     "X[(size_t)i * d + v] = ((float)orc_uniform(o[0]) < 0.25f) ? 1.0f : 0.0f;", 1),
     # indicators
     ("hv_full_height", "area += (ref[0] - x) * (best - y);", "area += (ref[0] - x) * (ref[1] - y);", 1),
     ("igd_squared", "acc = acc + sqrt(best);", "acc = acc + best;", 1),
+    ("hv_slice_height", "double top = ref[2];", "double top = lev[t];", 1),
+    ("igd_over_population", "return nr > 0 ? acc / (double)nr : 0.0;",
+     "return nr > 0 ? acc / (double)np : 0.0;", 1),
 ]
 
 

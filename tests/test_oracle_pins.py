@@ -417,7 +417,9 @@ def _niche_case(orc, kind, N, m, p, seed):
 def test_niche_alg1_equals_alg2(orc, kind, seed):
     """The Alg. 1 while-loop and the Alg. 2 cached batched loop (with the
     last batch truncated in shuffled-reference order) pick identical sets."""
-    for N, m, p in ((40, 3, 6), (64, 5, 3), (30, 4, 4)):
+    # (30, 3, 12): more directions (91) than N, so the first batch (the
+    # references without a member in S) is itself truncated
+    for N, m, p in ((40, 3, 6), (64, 5, 3), (30, 4, 4), (30, 3, 12)):
         F, Z, rank, l, K, nFl, pi, dist = _niche_case(orc, kind, N, m, p, seed)
         if K == nFl:
             continue
@@ -804,3 +806,56 @@ def test_kp_bit_flip_flips_ones_and_zeros(orc):
         X = np.full((N, d), v, dtype=np.float32)
         C = orc.kp_vary(X, rank, seed=3, gen=1, p_c=0.0, p_m=pm)
         assert abs(np.mean(C != X) - pm) < 0.01
+
+
+def test_associate_ties_go_to_the_first_direction(orc):
+    """A point on the bisector of two directions is equally far from both
+    (the two distances are the same rounded operations); pi takes the first
+    of the minimal distances, in either order of the directions."""
+    F = np.array([[1.0, 1.0], [2.0, 2.0]], dtype=np.float32)
+    rank = np.zeros(2, dtype=np.int32)
+    for Z in (np.array([[1.0, 0.0], [0.0, 1.0]]), np.array([[0.0, 1.0], [1.0, 0.0]])):
+        pi, dist = orc.associate(F, rank, 0, np.zeros(2), np.ones(2), Z)
+        assert pi.tolist() == [0, 0]
+        np.testing.assert_allclose(dist, [1.0, 2.0], rtol=1e-15)
+
+
+def test_polynomial_mutation_bounded_form_stays_inside(orc):
+    """The bounded polynomial mutation scales its perturbation to the
+    distances from y to the bounds, so from y = 0.1 or 0.9 a mutated value
+    reaches 0 or 1 only for u = 0 exactly: none lands on a bound."""
+    N, d = 200, 100
+    rank = np.zeros(N, dtype=np.int32)
+    for y in (0.1, 0.9):
+        X = np.full((N, d), y, dtype=np.float32)
+        C = orc.vary(X, rank, seed=6, gen=2, p_c=0.0, p_m=0.5)
+        moved = C[C != X]
+        assert len(moved) > 0.4 * N * d
+        assert moved.min() > 0.0 and moved.max() < 1.0
+
+
+def test_kp_uniform_crossover_mixes_parents(orc):
+    """Uniform crossover takes each item from either parent with
+    probability 1/2: from an all-ones and an all-zeros parent, a pair with
+    different parents gets complementary children with about half their
+    bits set."""
+    d = 400
+    X = np.zeros((2, d), dtype=np.float32)
+    X[0] = 1.0
+    rank = np.zeros(2, dtype=np.int32)
+    mixed = 0
+    for gen in range(40):
+        C = orc.kp_vary(X, rank, seed=7, gen=gen, p_c=1.0, p_m=0.0)
+        if np.all(C[0] + C[1] == 1.0):
+            mixed += 1
+            assert abs(C[0].mean() - 0.5) < 0.1
+        else:
+            assert np.array_equal(C[0], C[1])  # both children of one parent
+    assert mixed >= 10
+
+
+def test_kp_init_fair_bits(orc):
+    """Initial knapsack bits are fair coins."""
+    X = orc.kp_init(200, 100, seed=8)
+    assert set(np.unique(X).tolist()) <= {0.0, 1.0}
+    assert abs(X.mean() - 0.5) < 0.01
