@@ -21,7 +21,8 @@
 // "i dom j" bits gathered over j are row words and are transposed in-warp
 // (32 x 32 bit transpose by five shuffle stages) into Dom[ib][j].
 // Padding rows/columns hold NaN: both differences of a pair with a padding
-// point are the same NaN, so neither direction gets a bit.
+// point are the same NaN, so neither direction gets a bit; column blocks of
+// padding only (the last tile column) skip the test and write zero words.
 //
 // Every CTA also popcounts the words it writes and adds each point's
 // dominator count to cnt[] (the peel's first pass then reads no words).
@@ -225,6 +226,11 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
                 }
                 dij = ~acc;
                 dji = 0u;
+            } else if (jb * 32 >= v.n2) {
+                // a column block of padding only: no bit either way (the
+                // NaN differences would give the same zeros)
+                dij = 0u;
+                dji = 0u;
             } else {
                 block_full<M, M4>(fi, colp, dij, dji);
             }
@@ -329,6 +335,7 @@ __global__ void __launch_bounds__(256) k_dominance_gen(RunView v)
             const int cb = ch * 4 + cbi;
             const int jb = tj * 8 + cb;
             if (jb < ib0) continue;
+            if (jb * 32 >= v.n2) continue;  // padding only: the masks stay 0, no bit
             const float* colp = scol + cb * 32 * MC;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
