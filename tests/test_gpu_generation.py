@@ -85,6 +85,38 @@ def test_step_selects_like_oracle(n, orc, cfg):
         assert r.counter() == 4
 
 
+def test_bench_workload_generations_match_oracle(n, orc):
+    """The default bench workload (m = 5, N = 10,628, d = 100, 10,626
+    directions) in the configuration bench.py times (its seed and weights,
+    events around the dominance build and the peel): the initial population
+    equals the oracle's, the children are within X_TOL of the oracle's
+    variation of the same parents and their objectives within F_RTOL, and
+    two generations select exactly the oracle's next populations."""
+    cfg = wl.SCALE
+    W = wl.objective_weights(cfg.m, cfg.seed)
+    Z = orc.refdirs(cfg.m, cfg.p1, cfg.p2, cfg.tau)
+    with Run(n, cfg.m, cfg.d, cfg.N, cfg.p1, p2=cfg.p2, tau=cfg.tau, seed=cfg.seed, W=W,
+             phase_timing=1) as r:
+        r.check(n.nsga3_init(r.ctx, None))
+        X, F, rank = r.population()
+        assert np.array_equal(X, orc.init_population(cfg.N, cfg.d, cfg.seed))
+        np.testing.assert_allclose(F, orc.evaluate(X, W), rtol=F_RTOL, atol=0)
+        for g in range(2):
+            X, F, rank = r.population()
+            r.check(n.nsga3_step(r.ctx, None))
+            assert r.sync() == 0
+            Xc, Fc = r.children()
+            Xo = orc.vary(X, rank, seed=cfg.seed, gen=g)
+            assert np.max(np.abs(Xc.astype(np.float64) - Xo)) <= X_TOL
+            np.testing.assert_allclose(Fc, orc.evaluate(Xc, W), rtol=F_RTOL, atol=0)
+            Xn, Fn, rn = r.population()
+            RX, RF = np.vstack([X, Xc]), np.vstack([F, Fc])
+            ref = orc.select(RF, cfg.N, Z, seed=cfg.seed, gen=g)
+            sel = ref["selected"]
+            assert np.array_equal(Xn, RX[sel]) and np.array_equal(Fn, RF[sel])
+            assert np.array_equal(rn, ref["rank"][sel])
+
+
 def test_runs_are_deterministic_and_resume(n, orc):
     cfg = CFGS[1]
     W = wl.objective_weights(cfg.m, 0)
