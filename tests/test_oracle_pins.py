@@ -859,3 +859,55 @@ def test_kp_init_fair_bits(orc):
     X = orc.kp_init(200, 100, seed=8)
     assert set(np.unique(X).tolist()) <= {0.0, 1.0}
     assert abs(X.mean() - 0.5) < 0.01
+
+
+def _closed_form_niche(orc, rank, l, K, pi, dist, w, seed, gen):
+    """The closed form of the niching loop, written from its definition: a
+    reference j with rho_j members in S orders its F_l members (the nearest
+    first, ties to the lower index, when rho_j = 0; the rest by member
+    priority, then index); the member at position t has level rho_j + t;
+    L* is the K-th smallest level; every member below L* is taken and, at
+    L*, the members of the references of smallest (priority, j)."""
+    S = (rank >= 0) & (rank < l)
+    rho = np.bincount(pi[S], minlength=w)
+    Fl = np.flatnonzero(rank == l)
+    mp = {int(i): orc.member_priority(seed, gen, int(i)) for i in Fl}
+    levels = []
+    for j in range(w):
+        mem = [int(i) for i in Fl if pi[i] == j]
+        order = sorted(mem, key=lambda i: (mp[i], i))
+        if rho[j] == 0 and mem:
+            near = min(mem, key=lambda i: (dist[i], i))
+            order = [near] + [i for i in order if i != near]
+        levels += [(int(rho[j]) + t, j, i) for t, i in enumerate(order)]
+    Lstar = sorted(L for L, _, _ in levels)[K - 1]
+    taken = [i for L, _, i in levels if L < Lstar]
+    at = sorted((orc.ref_priority(seed, gen, j), j, i) for L, j, i in levels if L == Lstar)
+    taken += [i for _, _, i in at[:K - len(taken)]]
+    picked = np.zeros(len(rank), dtype=bool)
+    picked[taken] = True
+    return picked
+
+
+@pytest.mark.parametrize("case", range(60))
+def test_niche_closed_form_equals_the_loops(orc, case):
+    """Random niching problems (few references, tied distances, S members
+    stacked on some references, every K from 1 to |F_l|): the closed form
+    of the batched loop that the kernels compute picks the same set as the
+    literal Alg. 1 loop and the Alg. 2 cached loop."""
+    rng = np.random.default_rng([case, 77])
+    n2 = int(rng.integers(6, 70))
+    w = int(rng.integers(1, 14))
+    l = int(rng.integers(0, 4))
+    rank = rng.integers(0, l + 2, size=n2).astype(np.int32)
+    rank[rng.random(n2) < 0.1] = -1
+    rank[int(rng.integers(n2))] = l  # F_l is never empty
+    pi = rng.integers(0, max(1, w // 2) if case % 3 == 0 else w, size=n2).astype(np.int32)
+    dist = rng.integers(0, 4, size=n2) * 0.25
+    nFl = int((rank == l).sum())
+    seed, gen = int(rng.integers(1 << 30)), int(rng.integers(100))
+    for K in sorted({1, nFl, int(rng.integers(1, nFl + 1))}):
+        want = _closed_form_niche(orc, rank, l, K, pi, dist, w, seed, gen)
+        assert want.sum() == K
+        for variant in (0, 1):
+            assert np.array_equal(orc.niche(rank, l, K, pi, dist, w, seed, gen, variant), want)
