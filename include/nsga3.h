@@ -174,9 +174,17 @@ nsga3_status nsga3_run(nsga3_ctx* ctx, int generations, void* stream);
  * remainder), so the runs' kernels overlap on the device and small runs run
  * ahead of large ones between launches.  Results equal each run stepped
  * alone.  Every context needs opts.W and must live on the current device.
- * The graphs are built on the first call for a given list and reused while
- * the list is unchanged. */
+ * The graphs are kept by ctxs[0] and rebuilt whenever the list differs from
+ * the one they were built for; lists are compared by the contexts' creation
+ * serials (unique for the life of the process), not by address, so a
+ * context created where a destroyed one lived never inherits its graphs.
+ * Errors: EINVAL (n < 1, a NULL context or one without an objective, a
+ * context listed twice, generations < 0), ECUDA. */
 nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* stream);
+
+/* How many times ctx (as ctxs[0] of nsga3_run_batch) has built its batched
+ * graphs (diagnostics; no device work).  Errors: EINVAL (NULL argument). */
+nsga3_status nsga3_batch_graph_builds(const nsga3_ctx* ctx, int64_t* builds);
 
 /* Copies the N parents out: X (any, N x d), F (any, N x m), rank (any, N).
  * Any pointer may be NULL to skip it. */
@@ -339,7 +347,11 @@ void nsga3_server_destroy(nsga3_server* srv);
  * GPU on which this library is loaded holds until the process exits.  The
  * first call on a device, with that device current, looks up the array's
  * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Every call on a device shares the array, which keeps the
+ * stream capture.  The address is cached per device for the life of the
+ * process: after cudaDeviceReset (or any other reset of the device's primary
+ * context) the library's device symbols may be reloaded elsewhere, so this
+ * entry point must not be called again in that process.  Every call on a
+ * device shares the array, which keeps the
  * last call's contents; each call clears what must start at zero itself.
  * Calls whose executions overlap on the GPU (other streams, other host
  * threads) race on the array: order them on one stream or with events.

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <mutex>
 #include <numeric>
@@ -32,6 +33,11 @@ std::mutex g_attr_mutex;
 
 enum { EV_START, EV_VARY, EV_RESET, EV_DOM, EV_PEEL, EV_NICHE, EV_END, EV_COUNT };
 constexpr int BATCH_GENS = 4;  // generations per batched graph launch
+
+// Creation serials: every context gets the next value, never reused in the
+// life of the process, so a destroyed context and a new one that happens to
+// occupy the same host address are told apart.
+std::atomic<unsigned long long> g_ctx_serial{0};
 
 __global__ void k_set_gen(Ctrl* c, uint32_t gen) { c->gen = gen; }
 
@@ -57,10 +63,14 @@ struct nsga3_ctx {
     bool eager = false; // NSGA3_EAGER=1: no graphs, host-driven peel loop (profiling)
     unsigned ev_mask = 0; // bit e set: event e is recorded (opts.phase_timing; eager: all)
     std::string err;
-    // batched graph cache
-    std::vector<nsga3_ctx*> batch_key;
+    unsigned long long serial = 0;  // creation serial (g_ctx_serial)
+    // batched graph cache: the graphs hold the device buffers of every run in
+    // the list, so they are keyed by the runs' creation serials (a pointer of
+    // a destroyed run can be handed out again by the allocator)
+    std::vector<unsigned long long> batch_key;
     cudaGraphExec_t gx_batch = nullptr;   // BATCH_GENS generations of every run
     cudaGraphExec_t gx_batch1 = nullptr;  // one generation of every run
+    long long batch_builds = 0;           // times the batched graphs were (re)built
 };
 
 namespace {
@@ -732,6 +742,7 @@ nsga3_status ctx_create(int m, int d, int N, int ref_divisions, const nsga3_opts
     }
     *out = nullptr;
     nsga3_ctx* ctx = new nsga3_ctx();
+    ctx->serial = ++g_ctx_serial;
     ctx->arena = arena;
     nsga3_status st = ctx_fields(ctx, m, d, N, ref_divisions, opts);
     if (!st) {
@@ -1007,8 +1018,19 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
 {
     nsga3_ctx* ctx = (n > 0 && ctxs) ? ctxs[0] : nullptr;
     if (!ctx || generations < 0) return fail(ctx, NSGA3_EINVAL, "bad arguments");
-    for (int r = 0; r < n; ++r)
+    std::vector<unsigned long long> key(n);
+    for (int r = 0; r < n; ++r) {
         if (!ctxs[r] || !ctxs[r]->has_obj) return fail(ctx, NSGA3_EINVAL, "run %d has no objective", r);
+        key[r] = ctxs[r]->serial;
+    }
+    {
+        // a run listed twice would be two concurrent branches on the same
+        // buffers and barrier words
+        std::vector<unsigned long long> sorted(key);
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+            return fail(ctx, NSGA3_EINVAL, "a context appears more than once in the list");
+    }
     if (ctx->eager) {
         for (int g = 0; g < generations; ++g)
             for (int r = 0; r < n; ++r) {
@@ -1017,17 +1039,18 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
             }
         return NSGA3_OK;
     }
-    std::vector<nsga3_ctx*> key(ctxs, ctxs + n);
     if (!ctx->gx_batch || !ctx->gx_batch1 || ctx->batch_key != key) {
         for (cudaGraphExec_t* gx : {&ctx->gx_batch, &ctx->gx_batch1})
             if (*gx) {
                 cudaGraphExecDestroy(*gx);
                 *gx = nullptr;
             }
+        ctx->batch_key.clear();
         nsga3_status st = build_batch_graph(ctx, ctxs, n, BATCH_GENS, &ctx->gx_batch);
         if (!st) st = build_batch_graph(ctx, ctxs, n, 1, &ctx->gx_batch1);
         if (st) return st;
         ctx->batch_key = key;
+        ++ctx->batch_builds;
     }
     for (int g = 0; g + BATCH_GENS <= generations; g += BATCH_GENS)
         CK(cudaGraphLaunch(ctx->gx_batch, (cudaStream_t)stream));
@@ -1036,6 +1059,13 @@ nsga3_status nsga3_run_batch(nsga3_ctx** ctxs, int n, int generations, void* str
         ctxs[r]->last_kind = 3;
         ctxs[r]->host_launches += (long long)generation_launches(ctxs[r]) * generations;
     }
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_batch_graph_builds(const nsga3_ctx* ctx, int64_t* builds)
+{
+    if (!ctx || !builds) return NSGA3_EINVAL;
+    *builds = ctx->batch_builds;
     return NSGA3_OK;
 }
 

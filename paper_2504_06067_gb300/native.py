@@ -85,6 +85,7 @@ _SIGS = {
     "nsga3_step": (_I, [_CTX, _P]),
     "nsga3_run": (_I, [_CTX, _I, _P]),
     "nsga3_run_batch": (_I, [C.POINTER(_CTX), _I, _I, _P]),
+    "nsga3_batch_graph_builds": (_I, [_CTX, C.POINTER(C.c_int64)]),
     "nsga3_get_population": (_I, [_CTX, _P, _P, _P, _P]),
     "nsga3_set_population": (_I, [_CTX, _P, _P, _P, _P]),
     "nsga3_get_children": (_I, [_CTX, _P, _P, _P]),
@@ -150,6 +151,13 @@ def create(m, d, N, ref_divisions, opts=None):
 def run_batch(ctxs, generations, stream=0):
     arr = (_CTX * len(ctxs))(*ctxs)
     return nsga3_run_batch(arr, len(ctxs), generations, stream)
+
+
+def batch_graph_builds(ctx):
+    """nsga3_batch_graph_builds: times ctx built its batched graphs."""
+    b = C.c_int64()
+    check(nsga3_batch_graph_builds(ctx, C.byref(b)), ctx)
+    return b.value
 
 
 def rank_noalloc(objs_ptr, n, m, ranks_ptr, stream=0):

@@ -196,3 +196,51 @@ def test_batched_runs_equal_single_runs(n, orc):
     finally:
         for _, _, r in runs:
             r.close()
+
+
+def test_batched_graphs_follow_context_identity_not_address(n, orc):
+    """The batched graphs are cached by the runs' creation serials: after a
+    member is destroyed and a new context takes its place in the list (at the
+    same host address or not), the next call rebuilds the graphs before any
+    launch (checked with generations = 0, which launches nothing), and the
+    populations then equal each run stepped alone.  A list naming one context
+    twice is rejected without any launch."""
+    cfgs = [c for c in wl.batched_configs(n_runs=8, generations=3) if c.N <= 2000][:3]
+    assert len(cfgs) == 3
+    Ws = [wl.objective_weights(c.m, c.seed) for c in cfgs]
+    runs = [Run(n, c.m, c.d, c.N, c.p1, seed=c.seed, W=W) for c, W in zip(cfgs, Ws)]
+    try:
+        for r in runs:
+            r.check(n.nsga3_init(r.ctx, None))
+        lead = runs[0]
+        n.check(n.run_batch([r.ctx for r in runs], 2, None), lead.ctx)
+        assert n.batch_graph_builds(lead.ctx) == 1
+        n.check(n.run_batch([r.ctx for r in runs], 0, None), lead.ctx)
+        assert n.batch_graph_builds(lead.ctx) == 1  # same list: graphs reused
+        assert n.run_batch([runs[0].ctx, runs[1].ctx, runs[0].ctx], 1, None) == n.EINVAL
+        assert b"more than once" in n.nsga3_last_error(lead.ctx)
+        for r in runs:
+            assert r.sync() == 0
+        # replace member 1 by a new context of the same sizes and seed
+        old_addr = runs[1].ctx
+        runs[1].close()
+        c, W = cfgs[1], Ws[1]
+        runs[1] = Run(n, c.m, c.d, c.N, c.p1, seed=c.seed, W=W)
+        runs[1].check(n.nsga3_init(runs[1].ctx, None))
+        runs[1].check(n.nsga3_run(runs[1].ctx, 2, None))  # catch up with the others
+        same_address = runs[1].ctx == old_addr
+        n.check(n.run_batch([r.ctx for r in runs], 0, None), lead.ctx)
+        assert n.batch_graph_builds(lead.ctx) == 2, "graphs not rebuilt (same address: %s)" % same_address
+        n.check(n.run_batch([r.ctx for r in runs], 3, None), lead.ctx)
+        for (c, W), r in zip(zip(cfgs, Ws), runs):
+            assert r.sync() == 0
+            got = r.population()
+            with Run(n, c.m, c.d, c.N, c.p1, seed=c.seed, W=W) as alone:
+                alone.check(n.nsga3_init(alone.ctx, None))
+                alone.check(n.nsga3_run(alone.ctx, 5, None))
+                exp = alone.population()
+            for u, v in zip(got, exp):
+                assert np.array_equal(u, v)
+    finally:
+        for r in runs:
+            r.close()
