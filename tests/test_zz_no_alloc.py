@@ -1,7 +1,8 @@
 """nsga3_rank_noalloc (workspace in a static device array, no allocation)
-against the context-based entry point: the front index of every point from
-nsga3_rank_noalloc equals the ranks nsga3_select returns with full_sort = 1,
-over two calls in a row that share the static workspace.
+against the context-based entry point and the oracle: the front index of
+every point from nsga3_rank_noalloc equals the ranks nsga3_select returns
+with full_sort = 1 and the oracle's non-dominated sort (Alg. 1), over two
+calls in a row that share the static workspace.
 
 Collected last on purpose: it must pass both alone in a fresh process and
 after every other GPU test has run in the same process."""
@@ -54,22 +55,67 @@ PAIRS = [
 
 
 @pytest.mark.parametrize("pair", PAIRS, ids=lambda p: "%s%d-then-%s%d" % (p[0][0], p[0][1], p[1][0], p[1][1]))
-def test_two_calls_match_select(env, pair):
+def test_two_calls_match_select(env, orc, pair):
     torch, native = env
     for kind, n, m in pair:
         F = wl.objectives(kind, n, m, seed=n + m).astype(np.float32)
         got = _noalloc_ranks(torch, native, F)
         exp = _select_ranks(native, F)
         assert np.array_equal(got, exp), (kind, n, m)
+        ora, _ = orc.nds(F, n // 2, full_sort=True)
+        assert np.array_equal(got, ora), (kind, n, m)
 
 
-def test_repeated_call_same_input(env):
+def test_repeated_call_same_input(env, orc):
     torch, native = env
     F = wl.objectives("early", 2048, 3, seed=5).astype(np.float32)
     a = _noalloc_ranks(torch, native, F)
     b = _noalloc_ranks(torch, native, F)
     assert np.array_equal(a, b)
     assert np.array_equal(a, _select_ranks(native, F))
+    assert np.array_equal(a, orc.nds(F, 1024, full_sort=True)[0])
+
+
+def _fronts_by_rule(F):
+    """Front index of every row by the stated rule, brute force in numpy:
+    i dominates j iff f_i <= f_j everywhere and < somewhere (IEEE, so a NaN
+    in either row makes both comparisons false); fronts are peeled one by
+    one from the rows no remaining row dominates."""
+    n = len(F)
+    le = np.all(F[:, None, :] <= F[None, :, :], axis=2)
+    lt = np.any(F[:, None, :] < F[None, :, :], axis=2)
+    dom = le & lt
+    rank = np.full(n, -1, np.int32)
+    k = 0
+    while (rank < 0).any():
+        rem = rank < 0
+        front = rem & ~np.any(dom & rem[:, None], axis=0)
+        assert front.any()
+        rank[front] = k
+        k += 1
+    return rank
+
+
+def test_nan_rows_neither_dominate_nor_are_dominated(env, orc):
+    """Rows holding a NaN objective form part of the first front and never
+    push another row back, as the header states; checked against the rule
+    written out in numpy and against the oracle's sort."""
+    torch, native = env
+    n, m = 33, 3
+    F = wl.objectives("early", 34, m, seed=2)[:n].astype(np.float32)
+    nan_rows = [0, 5, 17, 32]
+    F[nan_rows[0], 1] = np.nan
+    F[nan_rows[1], :] = np.nan
+    F[nan_rows[2], 0] = np.nan
+    F[nan_rows[3], 2] = np.nan
+    got = _noalloc_ranks(torch, native, F)
+    rule = _fronts_by_rule(F)
+    assert np.array_equal(got, rule)
+    assert np.all(got[nan_rows] == 0)
+    assert np.array_equal(got, orc.nds(F, n, full_sort=True)[0])
+    # without the NaN rows the other rows keep the ranks of the finite set
+    keep = np.setdiff1d(np.arange(n), nan_rows)
+    assert np.array_equal(got[keep], _fronts_by_rule(F[keep]))
 
 
 def test_ragged_sizes_against_oracle(env, orc):
