@@ -27,16 +27,25 @@ OK, EINVAL, ENOMEM = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so next to it (gcc, no FMA contraction)."""
+    """Compile oracle.c into liboracle.so next to it (gcc, no FMA contraction),
+    with OpenMP when the compiler has it (the parallel loops give the same
+    results bit for bit; without OpenMP the build is single-threaded)."""
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + ".tmp.%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+            "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(base, check=True)
     os.replace(tmp, _LIB)
     return _LIB
+
+
+def threads() -> int:
+    """Host threads the oracle's parallel loops use (1 without OpenMP)."""
+    return int(_load().orc_threads())
 
 
 def _load():
@@ -62,6 +71,7 @@ def _load():
         "orc_refdirs": (i64, [i32, i32, i32, f64, P]),
         "orc_dominates": (i32, [P, P, i32]),
         "orc_nds": (i32, [P, i32, i32, i32, i32, P]),
+        "orc_threads": (i32, []),
         "orc_normalize": (i32, [P, P, i32, i32, i32, P, P, P, P]),
         "orc_associate": (None, [P, P, i32, i32, i32, P, P, P, i32, P, P]),
         "orc_niche_sequential": (i32, [P, i32, i32, i32, P, P, i32, u64, u32, P]),

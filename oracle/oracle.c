@@ -28,11 +28,21 @@
  * Compile with -ffp-contract=off (no FMA contraction) and without
  * -ffast-math: every FP64 operation is a separately rounded IEEE operation
  * in the order written.
+ *
+ * With -fopenmp the loops whose iterations are independent -- the
+ * dominator count and the per-front sweep of the non-dominated sort (one
+ * iteration per member j) and the association (one iteration per member
+ * i) -- run on all host cores.  Each iteration does exactly the serial
+ * arithmetic and writes only its own outputs, so the results are the same
+ * bit for bit with any number of threads.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_EINVAL 1
@@ -201,12 +211,16 @@ int orc_nds(const float *F, int n2, int m, int N, int full_sort, int32_t *rank)
 {
     int *cnt = (int *)calloc((size_t)n2 > 0 ? (size_t)n2 : 1, sizeof(int));
     int *front = (int *)malloc(((size_t)n2 > 0 ? (size_t)n2 : 1) * sizeof(int));
-    int *next = (int *)malloc(((size_t)n2 > 0 ? (size_t)n2 : 1) * sizeof(int));
-    if (!cnt || !front || !next) { free(cnt); free(front); free(next); return -1; }
+    if (!cnt || !front) { free(cnt); free(front); return -1; }
     for (int j = 0; j < n2; ++j) rank[j] = -1;
-    for (int i = 0; i < n2; ++i)
-        for (int j = 0; j < n2; ++j)
-            if (orc_dominates(F + (size_t)i * m, F + (size_t)j * m, m)) cnt[j]++;
+    /* dominator count of every member j */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int j = 0; j < n2; ++j) {
+        int c = 0;
+        for (int i = 0; i < n2; ++i)
+            if (orc_dominates(F + (size_t)i * m, F + (size_t)j * m, m)) c++;
+        cnt[j] = c;
+    }
     int nf = 0;
     for (int j = 0; j < n2; ++j)
         if (cnt[j] == 0) front[nf++] = j;
@@ -216,29 +230,33 @@ int orc_nds(const float *F, int n2, int m, int N, int full_sort, int32_t *rank)
         cum += nf;
         if (l < 0 && cum >= N) l = k;
         if (!full_sort && cum >= N) break;
+        /* every unranked member loses the dominators that front k held */
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int j = 0; j < n2; ++j) {
+            if (rank[j] != -1) continue;
+            for (int t = 0; t < nf; ++t)
+                if (orc_dominates(F + (size_t)front[t] * m, F + (size_t)j * m, m)) cnt[j]--;
+        }
+        /* the next front: unranked members left with no dominator, in
+           ascending index order */
         int nn = 0;
-        for (int t = 0; t < nf; ++t) {
-            int i = front[t];
-            for (int j = 0; j < n2; ++j) {
-                if (rank[j] != -1) continue;
-                if (orc_dominates(F + (size_t)i * m, F + (size_t)j * m, m)) {
-                    cnt[j]--;
-                    if (cnt[j] == 0) next[nn++] = j;
-                }
-            }
-        }
-        /* keep each front in ascending index order */
-        for (int a = 1; a < nn; ++a) {
-            int v = next[a], b = a - 1;
-            while (b >= 0 && next[b] > v) { next[b + 1] = next[b]; --b; }
-            next[b + 1] = v;
-        }
-        memcpy(front, next, (size_t)nn * sizeof(int));
+        for (int j = 0; j < n2; ++j)
+            if (rank[j] == -1 && cnt[j] == 0) front[nn++] = j;
         nf = nn;
         ++k;
     }
-    free(cnt); free(front); free(next);
+    free(cnt); free(front);
     return l;
+}
+
+/* Host threads the parallel loops use (1 without OpenMP). */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* ---------------------------------------------------------------------- */
@@ -501,7 +519,6 @@ void orc_associate(const float *F, const int32_t *rank, int n2, int m, int l,
                    int32_t *pi, double *dist)
 {
     double *nz = (double *)malloc((size_t)(w > 0 ? w : 1) * sizeof(double));
-    double *fp = (double *)malloc((size_t)m * sizeof(double));
     for (int j = 0; j < w; ++j) {
         double s = 0.0;
         for (int q = 0; q < m; ++q) {
@@ -510,44 +527,49 @@ void orc_associate(const float *F, const int32_t *rank, int n2, int m, int l,
         }
         nz[j] = sqrt(s);
     }
-    for (int i = 0; i < n2; ++i) {
-        pi[i] = -1;
-        dist[i] = 0.0;
-        if (rank[i] < 0 || rank[i] > l) continue;
-        double s = 0.0;
-        for (int q = 0; q < m; ++q) {
-            double ft = (double)F[(size_t)i * m + q] - zstar[q];
-            fp[q] = ft / a[q];
-            double sq = fp[q] * fp[q];
-            s = s + sq;
-        }
-        double nf = sqrt(s);
-        double best = INFINITY;
-        int32_t arg = -1;
-        for (int j = 0; j < w; ++j) {
-            double D;
-            if (nf == 0.0) {
-                D = 0.0;
-            } else {
-                double dot = 0.0;
-                for (int q = 0; q < m; ++q) {
-                    double pr = fp[q] * Z[(size_t)j * m + q];
-                    dot = dot + pr;
-                }
-                double den = nf * nz[j];
-                double c = dot / den;
-                double cc = c * c;
-                double one_m = 1.0 - cc;
-                if (one_m < 0.0) one_m = 0.0;
-                D = nf * sqrt(one_m);
+#pragma omp parallel
+    {
+        double *fp = (double *)malloc((size_t)m * sizeof(double));
+#pragma omp for schedule(dynamic, 16)
+        for (int i = 0; i < n2; ++i) {
+            pi[i] = -1;
+            dist[i] = 0.0;
+            if (rank[i] < 0 || rank[i] > l) continue;
+            double s = 0.0;
+            for (int q = 0; q < m; ++q) {
+                double ft = (double)F[(size_t)i * m + q] - zstar[q];
+                fp[q] = ft / a[q];
+                double sq = fp[q] * fp[q];
+                s = s + sq;
             }
-            if (D < best) { best = D; arg = j; }
+            double nf = sqrt(s);
+            double best = INFINITY;
+            int32_t arg = -1;
+            for (int j = 0; j < w; ++j) {
+                double D;
+                if (nf == 0.0) {
+                    D = 0.0;
+                } else {
+                    double dot = 0.0;
+                    for (int q = 0; q < m; ++q) {
+                        double pr = fp[q] * Z[(size_t)j * m + q];
+                        dot = dot + pr;
+                    }
+                    double den = nf * nz[j];
+                    double c = dot / den;
+                    double cc = c * c;
+                    double one_m = 1.0 - cc;
+                    if (one_m < 0.0) one_m = 0.0;
+                    D = nf * sqrt(one_m);
+                }
+                if (D < best) { best = D; arg = j; }
+            }
+            pi[i] = arg;
+            dist[i] = best;
         }
-        pi[i] = arg;
-        dist[i] = best;
+        free(fp);
     }
     free(nz);
-    free(fp);
 }
 
 /* ---------------------------------------------------------------------- */

@@ -40,6 +40,11 @@ MUTANTS = [
     ("dominance_not_strict", "if (x < y) any_lt = 1;", "if (x <= y) any_lt = 1;", 1),
     ("dominance_maximises", "if (!(x <= y)) all_le = 0;", "if (!(x >= y)) all_le = 0;", 1),
     ("last_front_off_by_one", "if (l < 0 && cum >= N) l = k;", "if (l < 0 && cum > N) l = k;", 1),
+    ("front_sweep_clears_count",
+     "if (orc_dominates(F + (size_t)front[t] * m, F + (size_t)j * m, m)) cnt[j]--;",
+     "if (orc_dominates(F + (size_t)front[t] * m, F + (size_t)j * m, m)) cnt[j] = 0;", 1),
+    ("dominator_count_one_sided", "for (int i = 0; i < n2; ++i)\n            if (orc_dominates(",
+     "for (int i = 0; i < j; ++i)\n            if (orc_dominates(", 1),
     ("das_dennis_no_inner_layer", "if (p2 > 0) orc_dd_rec(m, p2, 0, p2, k, Z, &row, 1, tau);", "", 1),
     # normalization
     ("asf_weights_swapped", "double wq = (r == q) ? 1.0 : 1e-6;",
