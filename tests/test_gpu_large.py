@@ -2,14 +2,15 @@
 2N = 200,000, a 5.0 GB bit matrix), two-layer directions p1 = 3, p2 = 2
 (w = 275), d = 200, in the launch configuration bench.py times.
 
-The oracle's non-dominated sort is O((2N)^2 m) and too slow at this size,
-so the GPU ranks are checked by the properties that define them, on sampled
-points against all 200,000: a point of front k is dominated by no point of
-front >= k (nor of F_drop) and, for k > 0, by some point of front k-1; a
-point of F_drop is dominated by some point of F_l.  Given those ranks, the
-oracle computes the rest of the selection in full (normalization,
-association of every point of S u F_l, niching) and the GPU must match it
-bit for bit."""
+The ranks of all 200,000 merged points are compared element by element with
+the oracle's non-dominated sort (Alg. 1; O((2N)^2 m), run on every host core
+through the oracle's OpenMP loops, about a minute).  The sampled checks of
+the front definition stay as an independent cross-check (a point of front
+k is dominated by no point of front >= k nor of F_drop and, for k > 0, by
+some point of front k-1; a point of F_drop is dominated by some point of
+F_l).  Given those ranks, the oracle computes the rest of the selection in
+full (normalization, association of every point of S u F_l, niching) and
+the GPU must match it bit for bit."""
 import numpy as np
 import pytest
 
@@ -80,6 +81,16 @@ def test_front_sizes_and_l(large):
     assert info["nS"] == (cum[-2] if l > 0 else 0) and info["nFl"] == sizes[-1]
 
 
+def test_all_ranks_equal_the_oracle(large, orc):
+    """Every one of the 2N = 200,000 ranks (front index, -1 for F_drop)
+    equals the oracle's sort of the same FP32 objectives."""
+    rank, info = large["rank"], large["info"]
+    ref, l = orc.nds(large["RF"], CFG.N)
+    assert l == info["l"]
+    bad = np.flatnonzero(rank != ref)
+    assert len(bad) == 0, (len(bad), bad[:10], rank[bad[:10]], ref[bad[:10]])
+
+
 def test_sampled_ranks_satisfy_the_front_definition(large):
     RF, rank = large["RF"], large["rank"]
     l = large["info"]["l"]
@@ -137,9 +148,10 @@ def test_niching_matches_oracle(large, orc):
     assert np.array_equal(sel, exp)
 
 
-def test_full_sort_many_fronts_at_full_size(large):
-    """2N = 200,000 points with many fronts (m = 3, full_sort): sampled ranks
-    of every depth satisfy the front definition."""
+def test_full_sort_many_fronts_at_full_size(large, orc):
+    """2N = 200,000 points with many fronts (m = 3, full_sort): every rank
+    equals the oracle's full sort, and sampled ranks of every depth satisfy
+    the front definition."""
     n = large["n"]
     N = CFG.N
     RF = wl.objectives("early", 2 * N, 3, seed=7)
@@ -147,6 +159,8 @@ def test_full_sort_many_fronts_at_full_size(large):
         st, rank, sel = r.select(RF)
         assert st == 0
     assert rank.min() == 0 and rank.max() > 10
+    ref, _ = orc.nds(RF, N, full_sort=True)
+    assert np.array_equal(rank, ref), int(np.count_nonzero(rank != ref))
     sizes = np.bincount(rank)
     assert sizes.sum() == 2 * N and np.all(sizes > 0)
     rng = np.random.default_rng(1)
