@@ -216,6 +216,61 @@ nsga3_status nsga3_sync(nsga3_ctx* ctx, void* stream);
  */
 nsga3_status nsga3_get_selection_info(nsga3_ctx* ctx, int32_t* info);
 
+/* Capacity paths the niching kernels took in the last selection
+ * (synchronous; diagnostics for tests of the paths that only large or
+ * skewed inputs reach): a bit mask of
+ *   NSGA3_PATH_UNSTAGED  more than 12,288 references: the level kernel reads
+ *                        the niche counts from global memory
+ *   NSGA3_PATH_DEEP      the level threshold L* is 4,096 or more (binary
+ *                        search instead of the level histogram)
+ *   NSGA3_PATH_CKOVER    more than 4,096 references hold a level-L* member
+ *                        (with NSGA3_PATH_UNSTAGED)
+ *   NSGA3_PATH_BINOVER   a radix bin of the level kernel held more than
+ *                        1,024 reference keys
+ *   NSGA3_PATH_LARGE     a partial take from a reference of more than 32
+ *                        members (block-wide member selection)
+ *   NSGA3_PATH_RADIX     the block-wide selection ran an 8-bit radix pass
+ *   NSGA3_PATH_RADIX2    ... and a second one.
+ * Errors: EINVAL (NULL argument), ECUDA. */
+#define NSGA3_PATH_UNSTAGED 1u
+#define NSGA3_PATH_DEEP 2u
+#define NSGA3_PATH_CKOVER 4u
+#define NSGA3_PATH_BINOVER 8u
+#define NSGA3_PATH_LARGE 16u
+#define NSGA3_PATH_RADIX 32u
+#define NSGA3_PATH_RADIX2 64u
+nsga3_status nsga3_get_selection_paths(nsga3_ctx* ctx, uint32_t* paths);
+
+/* Self-test of the block-wide selection routine that the niching kernels
+ * use to take the smallest (priority, index) keys (Alg. 2's random pick of
+ * references and members, read as the smallest Philox priorities): one
+ * CTA marks the `need` smallest of n unique 64-bit keys.
+ *   keys   device, n unique uint64 keys
+ *   marks  device, n uint32 outputs: 1 for the need smallest keys, else 0
+ *   paths  device, one uint32 output: NSGA3_PATH_RADIX / _RADIX2 bits of
+ *          the radix passes the routine ran
+ * Asynchronous on `stream`; allocates nothing.  Errors: EINVAL (NULL
+ * pointer, n < 1, need outside [0, n]), ECUDA (launch).  Sets no message
+ * for nsga3_last_error. */
+nsga3_status nsga3_select_smallest_probe(const uint64_t* keys, int n, int need, uint32_t* marks,
+                                         uint32_t* paths, void* stream);
+
+/* Measured instruction-issue ceiling of the dominance build (no counterpart
+ * in the paper; used as the denominator of its roofline): a kernel issues
+ * the dominance test's instruction mix -- two FP32 subtractions and one
+ * 3-input logic operation on their sign bits per step, eight independent
+ * chains per thread, no memory traffic -- on blocks_per_sm x (SM count)
+ * CTAs of 256 threads, `iters` steps per chain, `reps` timed launches after
+ * one warm-up launch (CUDA events on `stream`).  *instr_per_s receives the
+ * thread-instructions per second of the fastest launch, *best_ms (may be
+ * NULL) its time.  in_scratch: device, at least 256 bytes the caller owns
+ * (the kernel reads 32 floats from its start and may write one word at
+ * byte 128).  Synchronous.  Errors: EINVAL (NULL pointer, blocks_per_sm
+ * outside [1, 64], iters or reps < 1), ECUDA.  Sets no message for
+ * nsga3_last_error. */
+nsga3_status nsga3_issue_probe(int blocks_per_sm, int iters, int reps, double* instr_per_s, float* best_ms,
+                               void* in_scratch, void* stream);
+
 /* Normalization of the last niching selection (synchronous): ideal point
  * zstar[m], intercepts a[m] (FP64), extreme-point indices ext[m] (with
  * opts.norm_history an index 2N + r names the r-th remembered extreme

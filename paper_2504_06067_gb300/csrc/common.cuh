@@ -22,6 +22,16 @@
 #define NSGA3_PEEL_COLS 128     // columns per peel chunk (4 per lane, 32 lanes)
 #define SORT_NB 4096            // f_0 buckets of the bucket order
 
+// Capacity paths of the niching kernels (Ctrl::npath, reported by
+// nsga3_get_selection_paths; same values as NSGA3_PATH_* in nsga3.h)
+#define NPATH_UNSTAGED 1u   // more references than k_level stages in shared memory
+#define NPATH_DEEP 2u       // L* beyond the shared level histogram (binary search)
+#define NPATH_CKOVER 4u     // more level-L* references than the staged key list holds
+#define NPATH_BINOVER 8u    // a 12-bit radix bin of k_level held more keys than the exact rank
+#define NPATH_LARGE 16u     // a partial take from a reference of more than 32 members
+#define NPATH_RADIX 32u     // the block-wide select ran an 8-bit radix pass
+#define NPATH_RADIX2 64u    // ... and a second one
+
 // device status codes (same values as the C ABI's nsga3_status)
 #define DEV_OK 0
 #define DEV_ENONFINITE 4
@@ -63,12 +73,15 @@ struct Ctrl {
     int32_t recheck_miss;    // debug: association misses found by the full FP64 recheck
     int32_t nlarge;          // references whose partial take needs the block-wide select
     uint32_t peel_rows;      // dominator word-rows in the peel's row lists, all passes
+    uint32_t npath;          // NPATH_* bits: capacity paths the niching kernels took
 
     int32_t ncand;           // association candidates written by the scan
     int32_t nslow;           // points sent to the full FP64 association scan
     uint32_t ext_done;       // completion ticket of the extreme-point blocks
     uint32_t sort_done;      // completion ticket of the bucket histogram
     uint32_t f0lo, f0hi;     // range of f_0 as order-preserving uint
+    uint32_t range_done;     // completion ticket of the sort's range / threshold blocks
+    float thr[NSGA3_FAST_M]; // per-objective thresholds of the sort keys' codes (m <= 10)
     uint32_t cmp_done;       // completion ticket of the compaction blocks
     uint32_t zmin[NSGA3_MAX_M];  // ideal point as order-preserving uint of FP32
     double zstar[NSGA3_MAX_M];   // ideal point (FP64, +0.0 for zero)

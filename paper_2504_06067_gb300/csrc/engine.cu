@@ -1155,6 +1155,69 @@ nsga3_status nsga3_get_selection_info(nsga3_ctx* ctx, int32_t* info)
     return NSGA3_OK;
 }
 
+nsga3_status nsga3_get_selection_paths(nsga3_ctx* ctx, uint32_t* paths)
+{
+    if (!ctx || !paths) return fail(ctx, NSGA3_EINVAL, "null argument");
+    CK(cudaDeviceSynchronize());
+    uint32_t p = 0;
+    CK(cudaMemcpy(&p, &ctx->v.ctrl->npath, sizeof p, cudaMemcpyDeviceToHost));
+    *paths = p;
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_select_smallest_probe(const uint64_t* keys, int n, int need, uint32_t* marks,
+                                         uint32_t* paths, void* stream)
+{
+    if (!keys || !marks || !paths || n < 1 || need < 0 || need > n) return NSGA3_EINVAL;
+    cudaError_t e = launch_select_probe(reinterpret_cast<const unsigned long long*>(keys), n, need, marks,
+                                        paths, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return NSGA3_ECUDA;
+    }
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_issue_probe(int blocks_per_sm, int iters, int reps, double* instr_per_s, float* best_ms,
+                               void* in_scratch, void* stream)
+{
+    if (!instr_per_s || !in_scratch || blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1 || reps < 1)
+        return NSGA3_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return NSGA3_ECUDA;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int blocks = blocks_per_sm * sms;
+    const float* in = static_cast<const float*>(in_scratch);
+    uint32_t* sink = reinterpret_cast<uint32_t*>(static_cast<char*>(in_scratch) + 128);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float best = 1e30f;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = launch_issue_probe(in, blocks, iters, sink, s);  // warm-up
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = launch_issue_probe(in, blocks, iters, sink, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) best = ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return NSGA3_ECUDA;
+    }
+    *instr_per_s = issue_probe_instructions(blocks, iters) / (best * 1e-3);
+    if (best_ms) *best_ms = best;
+    return NSGA3_OK;
+}
+
 nsga3_status nsga3_get_normalization(nsga3_ctx* ctx, double* zstar, double* a, int32_t* ext)
 {
     if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");

@@ -48,6 +48,7 @@ __global__ void k_sel_reset(RunView v)
         c->rlev = 0;
         c->nsel = 0;
         c->nlarge = 0;
+        c->npath = 0u;
         c->peel_rows = 0u;
         c->ncand = 0;
         c->nslow = 0;

@@ -116,7 +116,8 @@ struct SelShared {
 // to one digit bucket until at most EXACT remain, which are then ranked
 // pairwise.  Every thread of the block must call it.
 template <class Key, class Pred, class Mark>
-__device__ void block_select_smallest(int n, int need, Key key, Pred pred, Mark mark, SelShared& sh)
+__device__ void block_select_smallest(int n, int need, Key key, Pred pred, Mark mark, SelShared& sh,
+                                      unsigned* paths)
 {
     unsigned long long prefix = 0ull, pmask = 0ull;
     int shift = 56;
@@ -156,6 +157,7 @@ __device__ void block_select_smallest(int n, int need, Key key, Pred pred, Mark 
             __syncthreads();
             return;
         }
+        if (paths && threadIdx.x == 0) atomicOr(paths, shift == 56 ? NPATH_RADIX : NPATH_RADIX2);
         for (int t = threadIdx.x; t < 256; t += blockDim.x) sh.hist[t] = 0;
         __syncthreads();
         for (int e = threadIdx.x; e < n; e += blockDim.x) {
@@ -328,6 +330,7 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
         before = Lstar > 0 ? sh.lev[Lstar - 1] : 0;
     } else {
         // deep levels: binary search with block-reduced counts
+        if (threadIdx.x == 0) atomicOr(&c->npath, NPATH_DEEP);
         auto count_le = [&](int L) {
             int s = 0;
             for (int j = threadIdx.x; j < w; j += LB) {
@@ -422,16 +425,20 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
         } else {
             // more than EXACT keys share the bin (not expected for Philox
             // priorities): select among them generically
+            if (threadIdx.x == 0) atomicOr(&c->npath, NPATH_BINOVER);
             auto pred = [&](int j) {
                 const int rp = sh.rr[j].y, lo = sh.rr[j].x;
                 return rp > 0 && lo <= Lstar && Lstar < lo + rp && (int)(ref_key(v.seed, gen, j) >> 52) == b;
             };
             auto key = [&](int j) { return ref_key(v.seed, gen, j); };
             auto mark = [&](int j) { v.take[j] += 1; };
-            block_select_smallest(w, need, key, pred, mark, sh.sel);
+            block_select_smallest(w, need, key, pred, mark, sh.sel, &c->npath);
         }
     } else {
-        if (threadIdx.x == 0) sh.nck = 0;
+        if (threadIdx.x == 0) {
+            sh.nck = 0;
+            atomicOr(&c->npath, NPATH_UNSTAGED);
+        }
         __syncthreads();
         for (int j = threadIdx.x; j < w; j += LB) {
             const int rp = rhop_of(j);
@@ -448,8 +455,9 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
             auto key = [&](int e) { return sh.ck[e]; };
             auto pred = [&](int) { return true; };
             auto mark = [&](int e) { v.take[(int)(sh.ck[e] & 0xffffffffull)] += 1; };
-            block_select_smallest(nC, r, key, pred, mark, sh.sel);
+            block_select_smallest(nC, r, key, pred, mark, sh.sel, &c->npath);
         } else {
+            if (threadIdx.x == 0) atomicOr(&c->npath, NPATH_CKOVER);
             auto pred = [&](int j) {
                 const int rp = rhop_of(j);
                 const int lo = rho_of(j);
@@ -457,7 +465,7 @@ __global__ void __launch_bounds__(LB) k_level(RunView v)
             };
             auto key = [&](int j) { return ref_key(v.seed, gen, j); };
             auto mark = [&](int j) { v.take[j] += 1; };
-            block_select_smallest(w, r, key, pred, mark, sh.sel);
+            block_select_smallest(w, r, key, pred, mark, sh.sel, &c->npath);
         }
     }
     __syncthreads();
@@ -571,6 +579,7 @@ __global__ void __launch_bounds__(256) k_pick(RunView v)
         } else if (lane == 0) {
             const int p = atomicAdd(&c->nlarge, 1);
             v.large[p] = make_int4(j, need, excl, 0);
+            atomicOr(&c->npath, NPATH_LARGE);
         }
     }
 }
@@ -594,9 +603,25 @@ __global__ void __launch_bounds__(512) k_pick_large(RunView v)
             return ((unsigned long long)mem_prio(v.seed, gen, i) << 32) | (unsigned)i;
         };
         auto mark = [&](int e) { mark_member(v, mem[e]); };
-        block_select_smallest(cnt, need, key, pred, mark, sh);
+        block_select_smallest(cnt, need, key, pred, mark, sh, &c->npath);
         __syncthreads();
     }
+}
+
+// Self-test of block_select_smallest on caller keys (one CTA): marks[e] = 1
+// for the `need` smallest of keys[0..n), 0 otherwise; *paths gets the radix
+// pass bits.
+__global__ void __launch_bounds__(512) k_select_probe(const unsigned long long* keys, int n, int need,
+                                                      uint32_t* marks, unsigned* paths)
+{
+    __shared__ SelShared sh;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) marks[e] = 0u;
+    if (threadIdx.x == 0) *paths = 0u;
+    __syncthreads();
+    auto pred = [&](int) { return true; };
+    auto key = [&](int e) { return keys[e]; };
+    auto mark = [&](int e) { marks[e] = 1u; };
+    block_select_smallest(n, need, key, pred, mark, sh, paths);
 }
 
 }  // namespace
@@ -621,6 +646,13 @@ cudaError_t launch_pick(const RunView& v, cudaStream_t s)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_pick_large<<<16, 512, 0, s>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_probe(const unsigned long long* keys, int n, int need, uint32_t* marks,
+                                unsigned* paths, cudaStream_t s)
+{
+    k_select_probe<<<1, 512, 0, s>>>(keys, n, need, marks, paths);
     return cudaGetLastError();
 }
 

@@ -43,8 +43,15 @@ cudaError_t assoc_init_attributes();
 cudaError_t launch_level(const RunView& v, cudaStream_t s);
 cudaError_t launch_bucket(const RunView& v, cudaStream_t s);
 cudaError_t launch_pick(const RunView& v, cudaStream_t s);
+// self-test of the block-wide selection of the smallest keys (one CTA)
+cudaError_t launch_select_probe(const unsigned long long* keys, int n, int need, uint32_t* marks,
+                                unsigned* paths, cudaStream_t s);
 cudaError_t launch_compact(const RunView& v, cudaStream_t s);
 cudaError_t launch_gather(const RunView& v, cudaStream_t s);
+
+// issue-rate probe of the dominance test's FADD / LOP3 mix (k_probe.cu)
+double issue_probe_instructions(int blocks, int iters);
+cudaError_t launch_issue_probe(const float* in, int blocks, int iters, uint32_t* sink, cudaStream_t s);
 
 // one-time attribute setup (dynamic shared memory opt-in)
 cudaError_t kernels_init_attributes();

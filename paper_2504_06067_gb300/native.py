@@ -23,6 +23,9 @@ _lib = C.CDLL(LIB_PATH)
 NOALLOC_MAX_N = 2048  # NSGA3_NOALLOC_MAX_N
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, EINTERNAL = range(8)
+# NSGA3_PATH_* bits of nsga3_get_selection_paths
+PATH_UNSTAGED, PATH_DEEP, PATH_CKOVER, PATH_BINOVER, PATH_LARGE, PATH_RADIX, PATH_RADIX2 = (
+    1, 2, 4, 8, 16, 32, 64)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE",
                 5: "ETIMEOUT", 6: "ESTATE", 7: "EINTERNAL"}
 
@@ -95,6 +98,9 @@ _SIGS = {
     "nsga3_wait_probe": (_I, [_CTX, _P]),
     "nsga3_get_selection_info": (_I, [_CTX, _P]),
     "nsga3_get_normalization": (_I, [_CTX, _P, _P, _P]),
+    "nsga3_get_selection_paths": (_I, [_CTX, C.POINTER(C.c_uint32)]),
+    "nsga3_select_smallest_probe": (_I, [_P, _I, _I, _P, _P, _P]),
+    "nsga3_issue_probe": (_I, [_I, _I, _I, C.POINTER(C.c_double), C.POINTER(C.c_float), _P, _P]),
     "nsga3_get_association": (_I, [_CTX, _P, _P]),
     "nsga3_phase_times": (_I, [_CTX, _P, _I]),
     "nsga3_last_launches": (_I, [_CTX, _P]),
@@ -158,6 +164,16 @@ def batch_graph_builds(ctx):
     b = C.c_int64()
     check(nsga3_batch_graph_builds(ctx, C.byref(b)), ctx)
     return b.value
+
+
+def issue_probe(scratch_ptr, blocks_per_sm=8, iters=20000, reps=5, stream=0):
+    """nsga3_issue_probe: (thread-instructions per second, best launch ms)."""
+    r = C.c_double()
+    ms = C.c_float()
+    st = nsga3_issue_probe(blocks_per_sm, iters, reps, C.byref(r), C.byref(ms), scratch_ptr, stream)
+    if st != OK:
+        raise NSGA3Error(st, "nsga3_issue_probe failed")
+    return r.value, ms.value
 
 
 def rank_noalloc(objs_ptr, n, m, ranks_ptr, stream=0):

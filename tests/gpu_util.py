@@ -54,6 +54,11 @@ class Run:
                 "overflow", "recheck_miss", "peel_rows"]
         return dict(zip(keys, (int(x) for x in a)))
 
+    def paths(self):
+        p = C.c_uint32()
+        self.check(self.n.nsga3_get_selection_paths(self.ctx, C.byref(p)))
+        return p.value
+
     def normalization(self):
         z = np.zeros(self.m)
         a = np.zeros(self.m)
