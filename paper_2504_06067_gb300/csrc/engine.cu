@@ -86,10 +86,18 @@ int select_launches(const nsga3_ctx* ctx)
 }
 // the softmax-simplex objective's dot-product kernel (m > 10)
 int objective_dot_launches(const nsga3_ctx* ctx) { return ctx->m > NSGA3_FAST_M && ctx->v.problem == 0 ? 1 : 0; }
+// variation + objective: one fused kernel for the softmax-simplex objective
+// with m <= 10; variation, dot products and objective above; variation and
+// evaluation (with repair) for the knapsack
+int variation_launches(const nsga3_ctx* ctx)
+{
+    if (ctx->v.problem == 0 && ctx->m <= NSGA3_FAST_M) return 1;
+    return 2 + objective_dot_launches(ctx);
+}
 int generation_launches(const nsga3_ctx* ctx)
 {
-    // + variation, objective, gather, commit
-    return select_launches(ctx) + 3 + objective_dot_launches(ctx);
+    // the selection without its finite check, + variation, gather, commit
+    return select_launches(ctx) - 1 + variation_launches(ctx) + 2;
 }
 
 nsga3_status fail(nsga3_ctx* c, nsga3_status s, const char* fmt, ...)
@@ -985,7 +993,7 @@ nsga3_status nsga3_vary(nsga3_ctx* ctx, void* stream)
     if (!ctx) return fail(ctx, NSGA3_EINVAL, "null context");
     if (!ctx->has_obj) return fail(ctx, NSGA3_ESTATE, "context has no objective (opts.W or the knapsack arrays were NULL)");
     CK(launch_vary_eval(ctx->v, (cudaStream_t)stream));
-    ctx->host_launches += 2 + objective_dot_launches(ctx);
+    ctx->host_launches += variation_launches(ctx);
     return NSGA3_OK;
 }
 

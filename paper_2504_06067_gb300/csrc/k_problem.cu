@@ -230,6 +230,11 @@ __global__ void k_init(RunView v)
     if (lane == 0) v.rank[i] = 0;
 }
 
+// Bounded polynomial mutation (Deb and Goyal): y + dq with
+// dq = val^(1/(eta+1)) - 1 (lower branch) or 1 - val^(1/(eta+1)) (upper
+// branch).  val^e - 1 is formed as expm1(e log val), which keeps dq
+// accurate relative to itself; pow(val, e) - 1 would lose the bits of dq
+// below the ulp of 1 when val is near 1.
 __device__ __forceinline__ float pm_mutate(float y, float u, float eta_m)
 {
     const float mp = 1.0f / (eta_m + 1.0f);
@@ -237,23 +242,26 @@ __device__ __forceinline__ float pm_mutate(float y, float u, float eta_m)
     if (u < 0.5f) {
         const float xy = 1.0f - y;
         const float val = 2.0f * u + (1.0f - 2.0f * u) * powf(xy, eta_m + 1.0f);
-        dq = powf(val, mp) - 1.0f;
+        dq = expm1f(mp * logf(val));
     } else {
         const float xy = 1.0f - (1.0f - y);
         const float val = 2.0f * (1.0f - u) + 2.0f * (u - 0.5f) * powf(xy, eta_m + 1.0f);
-        dq = 1.0f - powf(val, mp);
+        dq = -expm1f(mp * logf(val));
     }
     y = y + dq;
     return fminf(fmaxf(y, 0.0f), 1.0f);
 }
 
-__global__ void k_vary_eval(RunView v)
+// Variation of one pair (one warp, lanes over the variables): binary
+// tournament on rank (first drawn wins ties), SBX with per-variable
+// crossover and child swap, polynomial mutation, clip to [0, 1].  Calls
+// out(var, c1, c2) for every variable in lane order var = lane + 32 t.
+// SBX is written c1,2 = (y1 + y2)/2 -/+ (beta/2)(y2 - y1) with one FMA, the
+// same value as ((1 + beta) y1 + (1 - beta) y2)/2 with fewer roundings.
+template <class Out>
+__device__ __forceinline__ void vary_pair(const RunView& v, int q, uint32_t gen, Out out)
 {
-    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (q >= v.N / 2) return;
-    if (read_status(v.ctrl)) return;
     const int lane = lane_id();
-    const uint32_t gen = v.ctrl->gen;
     const int N = v.N, d = v.d;
     const U4 t = philox((uint32_t)q, gen, RNG_TOURNAMENT, 0u, v.seed);
     const U4 cx = philox((uint32_t)q, gen, RNG_TOURNAMENT, 1u, v.seed);
@@ -263,9 +271,6 @@ __global__ void k_vary_eval(RunView v)
     const uint32_t p2 = v.rank[b2] < v.rank[a2] ? b2 : a2;
     const bool cross = u01(cx.x) < v.p_c;
     const float e = 1.0f / (v.eta_c + 1.0f);
-    const int c0 = 2 * q, c1i = 2 * q + 1;  // children rows N + c0, N + c1i
-    float* x0 = v.X + (size_t)(N + c0) * d;
-    float* x1 = v.X + (size_t)(N + c1i) * d;
     for (int var = lane; var < d; var += 32) {
         const float y1 = v.X[(size_t)p1 * d + var], y2 = v.X[(size_t)p2 * d + var];
         float c1 = y1, c2 = y2;
@@ -273,8 +278,9 @@ __global__ void k_vary_eval(RunView v)
         if (cross && u01(sb.y) < 0.5f) {
             const float u = u01(sb.x);
             const float beta = (u <= 0.5f) ? powf(2.0f * u, e) : powf(1.0f / (2.0f * (1.0f - u)), e);
-            c1 = 0.5f * ((1.0f + beta) * y1 + (1.0f - beta) * y2);
-            c2 = 0.5f * ((1.0f - beta) * y1 + (1.0f + beta) * y2);
+            const float mid = 0.5f * (y1 + y2), hb = 0.5f * beta, dy = y2 - y1;
+            c1 = fmaf(-hb, dy, mid);
+            c2 = fmaf(hb, dy, mid);
             if (u01(sb.z) < 0.5f) {
                 const float tmp = c1;
                 c1 = c2;
@@ -287,8 +293,103 @@ __global__ void k_vary_eval(RunView v)
         const U4 pm = philox((uint32_t)q * (uint32_t)d + (uint32_t)var, gen, RNG_PM, 0u, v.seed);
         if (mut0) c1 = pm_mutate(c1, u01(pm.x), v.eta_m);
         if (u01(pm.y) < v.p_m) c2 = pm_mutate(c2, u01(pm.z), v.eta_m);
+        out(var, c1, c2);
+    }
+}
+
+// Variation only (m > 10: the objective follows in k_obj_dot + k_objective).
+__global__ void k_vary(RunView v)
+{
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= v.N / 2) return;
+    if (read_status(v.ctrl)) return;
+    const uint32_t gen = v.ctrl->gen;
+    float* x0 = v.X + (size_t)(v.N + 2 * q) * v.d;
+    float* x1 = v.X + (size_t)(v.N + 2 * q + 1) * v.d;
+    vary_pair(v, q, gen, [&](int var, float c1, float c2) {
         x0[var] = c1;
         x1[var] = c2;
+    });
+}
+
+// g term (x - 0.5)^2 of one variable added into a float-float sum (sh, sl):
+// x - 0.5 by Fast2Sum (exact when x >= 0.25), the square's error by an FMA
+__device__ __forceinline__ void g_add(float xv, float& sh, float& sl)
+{
+    const float th = __fsub_rn(xv, 0.5f);
+    const float tl = xv < 0.25f ? __fsub_rn(xv, __fadd_rn(th, 0.5f)) : 0.0f;
+    const float p = __fmul_rn(th, th);
+    const float pl = __fmaf_rn(th, th, -p) + 2.0f * th * tl;
+    float s1, e1;
+    two_sum(sh, p, s1, e1);
+    sh = s1;
+    sl = sl + (e1 + pl);
+}
+
+// Variation fused with the softmax-simplex objective (m <= 10): one warp
+// per pair; each lane keeps its children's first m - 1 variables and its
+// float-float partial sums of g while it writes the children, then the warp
+// reduces g, lanes 0..m-1 (child 0) and 16..16+m-1 (child 1) form
+// a_j = sum_e W_je x_e (FP64, left to right, x_e by shuffle) and exp(a_j),
+// every lane adds e_0..e_{m-1} in order, and lane j writes
+// f_j = (1 + g) e_j / den rounded to FP32.  The children are never read back.
+template <int M>
+__global__ void __launch_bounds__(256) k_vary_eval(RunView v)
+{
+    constexpr int K = M - 1;
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= v.N / 2) return;
+    if (read_status(v.ctrl)) return;
+    const int lane = lane_id();
+    const uint32_t gen = v.ctrl->gen;
+    const int N = v.N;
+    float* x0 = v.X + (size_t)(N + 2 * q) * v.d;
+    float* x1 = v.X + (size_t)(N + 2 * q + 1) * v.d;
+    float gh0 = 0.0f, gl0 = 0.0f, gh1 = 0.0f, gl1 = 0.0f;
+    float xk0 = 0.0f, xk1 = 0.0f;
+    vary_pair(v, q, gen, [&](int var, float c1, float c2) {
+        x0[var] = c1;
+        x1[var] = c2;
+        if (var < K) {
+            xk0 = c1;
+            xk1 = c2;
+        } else {
+            g_add(c1, gh0, gl0);
+            g_add(c2, gh1, gl1);
+        }
+    });
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float s1, e1;
+        const float oh0 = __shfl_xor_sync(0xffffffffu, gh0, o), ol0 = __shfl_xor_sync(0xffffffffu, gl0, o);
+        two_sum(gh0, oh0, s1, e1);
+        gh0 = s1;
+        gl0 = gl0 + (ol0 + e1);
+        const float oh1 = __shfl_xor_sync(0xffffffffu, gh1, o), ol1 = __shfl_xor_sync(0xffffffffu, gl1, o);
+        two_sum(gh1, oh1, s1, e1);
+        gh1 = s1;
+        gl1 = gl1 + (ol1 + e1);
+    }
+    const int j = lane & 15;
+    const bool second = lane >= 16;
+    double a = 0.0;
+#pragma unroll
+    for (int e = 0; e < K; ++e) {
+        const float xe0 = __shfl_sync(0xffffffffu, xk0, e);
+        const float xe1 = __shfl_sync(0xffffffffu, xk1, e);
+        if (j < M) a = __dadd_rn(a, __dmul_rn((double)v.Wobj[j * K + e], (double)(second ? xe1 : xe0)));
+    }
+    const double ex = j < M ? exp(a) : 0.0;
+    double den0 = 0.0, den1 = 0.0;
+#pragma unroll
+    for (int t = 0; t < M; ++t) {
+        den0 = __dadd_rn(den0, __shfl_sync(0xffffffffu, ex, t));
+        den1 = __dadd_rn(den1, __shfl_sync(0xffffffffu, ex, 16 + t));
+    }
+    if (j < M) {
+        const double g = second ? __dadd_rn((double)gh1, (double)gl1) : __dadd_rn((double)gh0, (double)gl0);
+        const double f = __dmul_rn(__dadd_rn(1.0, g), __ddiv_rn(ex, second ? den1 : den0));
+        v.F[(size_t)(N + 2 * q + (second ? 1 : 0)) * M + j] = __double2float_rn(f);
     }
 }
 
@@ -336,13 +437,26 @@ cudaError_t launch_vary_eval(const RunView& v, cudaStream_t s)
 {
     if (v.problem == 1) return launch_kp_vary_eval(v, s);
     long long threads = (long long)(v.N / 2) * 32;
-    k_vary_eval<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(v);
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    if (v.m <= NSGA3_FAST_M) {
+        switch (v.m) {
+        case 2: k_vary_eval<2><<<blocks, 256, 0, s>>>(v); break;
+        case 3: k_vary_eval<3><<<blocks, 256, 0, s>>>(v); break;
+        case 4: k_vary_eval<4><<<blocks, 256, 0, s>>>(v); break;
+        case 5: k_vary_eval<5><<<blocks, 256, 0, s>>>(v); break;
+        case 6: k_vary_eval<6><<<blocks, 256, 0, s>>>(v); break;
+        case 7: k_vary_eval<7><<<blocks, 256, 0, s>>>(v); break;
+        case 8: k_vary_eval<8><<<blocks, 256, 0, s>>>(v); break;
+        case 9: k_vary_eval<9><<<blocks, 256, 0, s>>>(v); break;
+        default: k_vary_eval<10><<<blocks, 256, 0, s>>>(v); break;
+        }
+        return cudaGetLastError();
+    }
+    k_vary<<<blocks, 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (v.m > NSGA3_FAST_M) {
-        e = launch_obj_dot(v, v.N, v.N, s);
-        if (e != cudaSuccess) return e;
-    }
+    e = launch_obj_dot(v, v.N, v.N, s);
+    if (e != cudaSuccess) return e;
     const int R = obj_rows(v.m);
     k_objective<<<(v.N + R - 1) / R, OT, obj_smem(v.m), s>>>(v, v.N, v.N, R);
     return cudaGetLastError();

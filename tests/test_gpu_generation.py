@@ -10,11 +10,32 @@ from gpu_util import Run
 
 pytestmark = pytest.mark.gpu
 
-# Children are FP32 in [0, 1]; the GPU evaluates SBX / PM with FP32 powf and
-# the oracle in FP64, so they agree to 1e-6 of the variable range.  The
-# objective is evaluated in FP64 on both sides and rounded to FP32.
-X_TOL = 1e-6
+# Children are FP32 in [0, 1].  The GPU evaluates SBX and polynomial
+# mutation in FP32 (powf for the spread factor beta, expm1/log for the
+# mutation step), the oracle in FP64.  The error of beta (an ulp or two of a
+# value up to 2.14) reaches a child as 0.5 |y2 - y1| d(beta), an ABSOLUTE
+# error that does not shrink with the child: SBX forms a child near 0 as the
+# difference of two terms near |y2 - y1|.  So the children are held to 1e-6
+# relative where |x| >= X_FLOOR and to the absolute bound 1e-6 X_FLOOR below
+# it.  Measured on the GB300 over 15 variations (m = 3 ... 10, up to 4 M
+# children): at most 1 ulp (1.2e-7 in [0.5, 1), 6e-8 below 0.5), so at most
+# 6e-7 relative from 0.1 up, and 6e-8 absolute below.  The objective is
+# evaluated in FP64 on both sides and rounded to FP32.
+X_RTOL = 1e-6
+X_FLOOR = 0.1
 F_RTOL = 1e-6
+
+
+def assert_children_close(Xc, Xo):
+    """|Xc - Xo| <= X_RTOL max(|Xo|, X_FLOOR), element by element."""
+    Xc = np.asarray(Xc, np.float64)
+    Xo = np.asarray(Xo, np.float64)
+    err = np.abs(Xc - Xo)
+    bound = X_RTOL * np.maximum(np.abs(Xo), X_FLOOR)
+    bad = np.flatnonzero(err > bound)
+    assert len(bad) == 0, ("%d children outside the bound; worst err %.3g at |x| = %.3g; max abs err %.3g"
+                           % (len(bad), err.flat[bad[np.argmax(err.flat[bad])]],
+                              abs(Xo.flat[bad[np.argmax(err.flat[bad])]]), err.max()))
 
 
 @pytest.fixture(scope="module")
@@ -57,7 +78,7 @@ def test_variation_matches_oracle(n, orc, cfg, gen):
         r.check(n.nsga3_vary(r.ctx, None))
         Xc, Fc = r.children()
     Xo = orc.vary(X, rank, seed=3, gen=gen)
-    assert np.max(np.abs(Xc.astype(np.float64) - Xo)) <= X_TOL
+    assert_children_close(Xc, Xo)
     # objective of the GPU's own children, evaluated by the oracle
     np.testing.assert_allclose(Fc, orc.evaluate(Xc, W), rtol=F_RTOL, atol=0)
 
@@ -89,8 +110,9 @@ def test_bench_workload_generations_match_oracle(n, orc):
     """The default bench workload (m = 5, N = 10,628, d = 100, 10,626
     directions) in the configuration bench.py times (its seed and weights,
     events around the dominance build and the peel): the initial population
-    equals the oracle's, the children are within X_TOL of the oracle's
-    variation of the same parents and their objectives within F_RTOL, and
+    equals the oracle's, the children are within X_RTOL relative (above
+    X_FLOOR) of the oracle's variation of the same parents and their
+    objectives within F_RTOL, and
     two generations select exactly the oracle's next populations."""
     cfg = wl.SCALE
     W = wl.objective_weights(cfg.m, cfg.seed)
@@ -107,7 +129,7 @@ def test_bench_workload_generations_match_oracle(n, orc):
             assert r.sync() == 0
             Xc, Fc = r.children()
             Xo = orc.vary(X, rank, seed=cfg.seed, gen=g)
-            assert np.max(np.abs(Xc.astype(np.float64) - Xo)) <= X_TOL
+            assert_children_close(Xc, Xo)
             np.testing.assert_allclose(Fc, orc.evaluate(Xc, W), rtol=F_RTOL, atol=0)
             Xn, Fn, rn = r.population()
             RX, RF = np.vstack([X, Xc]), np.vstack([F, Fc])
