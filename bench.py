@@ -5,15 +5,23 @@ One step = one generation of a plain NSGA-III run: variation + objective,
 then the environmental selection over the merged 2N x m objectives
 (dominance matrix, front peel, normalization, association, niching) and the
 gather of the next population, as one CUDA-graph launch of the C-ABI
-library.  Default workload: m = 5, p = 20 (10,626 Das-Dennis directions),
-N = 10,628, d = 100, the 500-generation run timed from generation 0 after
-warm-up generations on the same context (re-initialised).
+library.
+
+Default (no --workload): the headline line on the largest single-GPU
+configuration, m = 10, two-layer directions p1 = 3 + p2 = 2 (275), N =
+100,000, d = 200, 200 generations timed from generation 0 after warm-up
+generations on the same context (re-initialised), with sub-records for the
+m = 5, N = 10,628 run ("secondary"), the 64 batched runs ("batched"), a
+prefix of the served request stream ("served"), the measured issue ceiling
+of the dominance build ("issue_probe") and the oracle on the host cores
+("cpu_baseline").
 
 Metric: selected solutions per second (N x generations / device time), plus
 generations per second.  The L2 cache is flushed (256 MB write) before every
 timed step; each step is timed by CUDA events on the launching stream.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+        [--workload headline|small|scale|large|huge|knapsack|batched|served|sweep|popsweep|select]
 Multi-GPU (torchrun): each rank advances an independent replica (seed + rank),
 "scaling": "weak"; rank 0 prints the line.
 """
@@ -50,14 +58,18 @@ def parse_args(argv=None):
                    help="timed generations (default: the workload's run length)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep", "popsweep"],
-                   default="scale")
+    p.add_argument("--workload", choices=["headline"] + sorted(WORKLOADS) +
+                   ["batched", "served", "sweep", "popsweep", "select"], default="headline")
     p.add_argument("--runs", type=int, default=64, help="batched: independent runs")
     p.add_argument("--sweep-m", type=str, default=None,
                    help="sweep / popsweep: comma-separated subset of m (or of N)")
     p.add_argument("--requests", type=int, default=None, help="served: requests of the stream")
+    p.add_argument("--served-prefix", type=int, default=100,
+                   help="headline: requests of the served stream in the served record")
+    p.add_argument("--no-batched", action="store_true", help="headline: skip the batched record")
+    p.add_argument("--no-served", action="store_true", help="headline: skip the served record")
     p.add_argument("--cpu-budget", type=float, default=20.0,
-                   help="seconds of oracle work for the cpu_baseline sample")
+                   help="seconds of oracle work for the cpu_baseline sample (at least one generation)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--streaming", action="store_true",
@@ -227,17 +239,17 @@ def phase_breakdown(n, make_ctx, K, warmup, flush, stream):
     return {nm: round(tot[i] / K, 5) for i, nm in enumerate(PHASE_NAMES)}
 
 
-def run_ours(args, world, rank, local):
-    import torch
-    torch.cuda.set_device(local)
-    dist = dist_init(world, "nccl")
-    from paper_2504_06067_gb300 import native as n
-
-    cfg = WORKLOADS[args.workload]
-    seed = cfg.seed + rank
+def plain_measure(n, torch, cfg, K, warmup, stream, flush, seed, events, e2e_steps, dist, world,
+                  kp=None, streaming=0):
+    """Times K generations of one plain run of `cfg` from generation 0 (after
+    `warmup` generations on the same context, re-initialised), L2 flushed
+    before each, CUDA events on the launching stream around each step.  The
+    timed graph carries events around the dominance build and the peel when
+    `events` is 1 (none when 0).  Then `e2e_steps` generations through the C
+    ABI with the parents uploaded from and the next population read back to
+    pinned host memory inside the timed region.  Returns a dict; the phase
+    breakdown is a separate pass (phase_breakdown)."""
     W = wl.objective_weights(cfg.m, cfg.seed)
-    streaming = 1 if (args.streaming or args.workload == "huge") else 0
-    kp = wl.knapsack_instance(cfg.m, cfg.d, cfg.seed) if args.workload == "knapsack" else None
 
     def make_ctx(level):
         if kp is not None:
@@ -249,139 +261,192 @@ def run_ours(args, world, rank, local):
                                   streaming=streaming, phase_timing=level)
         return n.create(cfg.m, cfg.d, cfg.N, cfg.p1, opts)
 
-    # the timed graph carries events around the dominance build and the
-    # peel only (the two candidates for the dominant kernel)
-    ctx = make_ctx(1)
-    stream = torch.cuda.current_stream()
+    ctx = make_ctx(events)
     sh = stream.cuda_stream
     info = (C.c_int32 * 13)()
     phases = (C.c_float * 7)()
     launches = C.c_int32()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def ok(st):
         return n.check(st, ctx)
 
-    # warm-up generations, then restart the run from generation 0
-    ok(n.nsga3_init(ctx, sh))
-    for _ in range(args.warmup):
-        ok(n.nsga3_step(ctx, sh))
-    ok(n.nsga3_sync(ctx, sh))
-    ok(n.nsga3_init(ctx, sh))
-    ok(n.nsga3_sync(ctx, sh))
-
-    K = args.steps
-    ph_tot = [0.0] * 7
-    peel_rows = 0
-    passes = 0
-    niche_steps = 0
-    assoc_pairs = 0
-    n_launch = 0
-    step_ms = []
-    sampler = ClockSampler(local)
-    sampler.start()
-    barrier(dist)
-    torch.cuda.synchronize()
-    for k in range(K):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ok(n.nsga3_step(ctx, sh))
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        ok(n.nsga3_phase_times(ctx, phases, 7))
-        ok(n.nsga3_get_selection_info(ctx, info))
-        ok(n.nsga3_last_launches(ctx, C.byref(launches)))
-        for t in range(7):
-            ph_tot[t] += phases[t]
-        passes += info[6]
-        peel_rows += info[12]
-        n_launch += launches.value
-        if info[4]:
-            niche_steps += 1
-            assoc_pairs += info[7] * n.nsga3_num_refs(ctx)
-    torch.cuda.synchronize()
-    barrier(dist)
-    clocks = sampler.stop()
-    st = n.nsga3_sync(ctx, sh)
-    if st != n.OK:
-        raise RuntimeError("device status %d after the timed run" % st)
-    total_s = sum(step_ms) / 1e3
-    value, total_s_max = job_rate(dist, world, cfg.N * K, total_s, "cuda")
-
-    # end to end through the C ABI with pinned host buffers: upload the
-    # parents, one generation, read the next population back
-    e2e = None
-    if not args.no_e2e:
-        Xh = torch.empty((cfg.N, cfg.d), dtype=torch.float32).pin_memory()
-        Fh = torch.empty((cfg.N, cfg.m), dtype=torch.float32).pin_memory()
-        Rh = torch.empty(cfg.N, dtype=torch.int32).pin_memory()
+    try:
         ok(n.nsga3_init(ctx, sh))
-        ok(n.nsga3_get_population(ctx, Xh.data_ptr(), Fh.data_ptr(), Rh.data_ptr(), sh))
+        for _ in range(warmup):
+            ok(n.nsga3_step(ctx, sh))
         ok(n.nsga3_sync(ctx, sh))
-        e2e_ms = []
-        Ke = min(K, 200)
-        for k in range(Ke):
+        ok(n.nsga3_init(ctx, sh))
+        ok(n.nsga3_sync(ctx, sh))
+        dom_ms = peel_ms = 0.0
+        peel_rows = passes = niche_steps = n_launch = 0
+        step_ms = []
+        barrier(dist)
+        torch.cuda.synchronize()
+        for k in range(K):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ok(n.nsga3_set_population(ctx, Xh.data_ptr(), Fh.data_ptr(), Rh.data_ptr(), sh))
             ok(n.nsga3_step(ctx, sh))
-            ok(n.nsga3_get_population(ctx, Xh.data_ptr(), Fh.data_ptr(), Rh.data_ptr(), sh))
             e1.record(stream)
             e1.synchronize()
-            e2e_ms.append(e0.elapsed_time(e1))
-        ok(n.nsga3_sync(ctx, sh))
-        e_s = reduce_max(dist, sum(e2e_ms) / 1e3, "cuda")
-        per_step = cfg.N * (cfg.d + cfg.m + 1) * 4
-        e2e = {"value": world * cfg.N * Ke / e_s, "unit": "sols/s", "h2d_bytes_per_step": per_step,
-               "d2h_bytes_per_step": per_step, "steps": Ke,
-               "gens_per_s": Ke / e_s}
-    n.nsga3_destroy(ctx)
-    breakdown = phase_breakdown(n, make_ctx, K, args.warmup, flush, stream)
+            step_ms.append(e0.elapsed_time(e1))
+            if events:
+                ok(n.nsga3_phase_times(ctx, phases, 7))
+                dom_ms += phases[2]
+                peel_ms += phases[3]
+            ok(n.nsga3_get_selection_info(ctx, info))
+            ok(n.nsga3_last_launches(ctx, C.byref(launches)))
+            passes += info[6]
+            peel_rows += info[12]
+            n_launch += launches.value
+            if info[4]:
+                niche_steps += 1
+        torch.cuda.synchronize()
+        barrier(dist)
+        st = n.nsga3_sync(ctx, sh)
+        if st != n.OK:
+            raise RuntimeError("device status %d after the timed run of %s" % (st, cfg.name))
+        total_s = sum(step_ms) / 1e3
+        value, total_s_max = job_rate(dist, world, cfg.N * K, total_s, "cuda")
+        out = {"value": value, "gens_per_s": world * K / total_s_max, "ms_per_step": total_s_max * 1e3 / K,
+               "steps": K, "peel_passes_per_step": passes / K, "peel_rows": peel_rows,
+               "niching_steps": niche_steps, "gpu_launches": n_launch,
+               "timed_events": "dominance build and peel" if events else "none"}
+        if events:
+            out["timed_region_ms"] = {"dominance": dom_ms / K, "peel": peel_ms / K}
+        if e2e_steps:
+            Xh = torch.empty((cfg.N, cfg.d), dtype=torch.float32).pin_memory()
+            Fh = torch.empty((cfg.N, cfg.m), dtype=torch.float32).pin_memory()
+            Rh = torch.empty(cfg.N, dtype=torch.int32).pin_memory()
+            ok(n.nsga3_init(ctx, sh))
+            ok(n.nsga3_get_population(ctx, Xh.data_ptr(), Fh.data_ptr(), Rh.data_ptr(), sh))
+            ok(n.nsga3_sync(ctx, sh))
+            e2e_ms = []
+            Ke = min(K, e2e_steps)
+            for k in range(Ke):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ok(n.nsga3_set_population(ctx, Xh.data_ptr(), Fh.data_ptr(), Rh.data_ptr(), sh))
+                ok(n.nsga3_step(ctx, sh))
+                ok(n.nsga3_get_population(ctx, Xh.data_ptr(), Fh.data_ptr(), Rh.data_ptr(), sh))
+                e1.record(stream)
+                e1.synchronize()
+                e2e_ms.append(e0.elapsed_time(e1))
+            ok(n.nsga3_sync(ctx, sh))
+            e_s = reduce_max(dist, sum(e2e_ms) / 1e3, "cuda")
+            per_step = cfg.N * (cfg.d + cfg.m + 1) * 4
+            out["e2e"] = {"value": world * cfg.N * Ke / e_s, "unit": "sols/s", "h2d_bytes_per_step": per_step,
+                          "d2h_bytes_per_step": per_step, "steps": Ke, "gens_per_s": world * Ke / e_s}
+    finally:
+        n.nsga3_destroy(ctx)
+    return out, make_ctx
 
+
+def issue_probe(n, torch, stream):
+    """The measured issue ceiling of the dominance test's FADD / LOP3 mix
+    (nsga3_issue_probe), with the SM clock sampled while it runs."""
+    scratch = torch.rand(64, dtype=torch.float32, device="cuda")
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    rate, ms = n.issue_probe(scratch.data_ptr(), blocks_per_sm=8, iters=400000, reps=5,
+                             stream=stream.cuda_stream)
+    clocks = sampler.stop()
+    return {"instr_per_s": rate, "unit": "thread-instructions/s", "best_launch_ms": ms,
+            "mix": "2 FP32 subtractions + 1 three-input LOP3 per step, 8 chains per thread, "
+                   "8 CTAs of 256 threads per SM, no memory traffic; fastest of 5 launches",
+            "clocks": clocks,
+            "per_sm_per_clock": (rate / NUM_SMS / (clocks["sm_mhz"] * 1e6)) if clocks.get("sm_mhz") else None}
+
+
+def roofline_of(cfg, avg_ms, peel_rows_per_step, probe, peaks, peak_kind):
+    """Roofline of the dominant kernel (the dominance build, bound by issue,
+    or the peel, bound by memory) from its average launch time."""
+    n2 = 2 * cfg.N
+    pairs = n2 * (n2 - 1) / 2
+    if avg_ms["dominance"] >= avg_ms["peel"]:
+        ops = pairs * 2 * cfg.m  # FP32 compares: all(f_i <= f_j) and all(f_j <= f_i)
+        achieved = ops / (avg_ms["dominance"] / 1e3) / 1e12
+        if probe is not None:
+            peak = probe["instr_per_s"] / 1e12
+            src = "measured: nsga3_issue_probe (the FADD / LOP3 mix of the test, all SMs, no memory)"
+        else:
+            clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
+            peak = NUM_SMS * LANES_PER_SM * clk / 1e12
+            src = "152 SMs x 128 lanes x %.0f MHz (max SM clock, %s)" % (clk / 1e6, peak_kind)
+        return {"kernel": "k_dominance<%d>" % cfg.m if cfg.m <= 10 else "k_dominance_gen", "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "T/s (compares; issue slots)",
+                "frac": achieved / peak, "peak_source": src,
+                "algorithmic": "n2(n2-1)/2 pairs x 2m FP32 compares per launch (%.4g)" % ops,
+                "launch_ms": avg_ms["dominance"],
+                "traffic": ncu_traffic("k_dominance", cfg.name)}
+    bytes_read = peel_rows_per_step * 128 * 4.0  # row segments of 128 columns
+    achieved = bytes_read / (avg_ms["peel"] / 1e3) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    return {"kernel": "k_peel (all passes of one selection)", "bound": "hbm", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": "hbm_gbs (%s)" % peak_kind,
+            "algorithmic": "dominator row segments read (128 columns x 4 B each), all passes",
+            "launch_ms": avg_ms["peel"], "traffic": ncu_traffic("k_peel", cfg.name)}
+
+
+def plain_record(n, torch, cfg, K, args, stream, flush, seed, events, dist, world, probe, kp=None,
+                 streaming=0, phases=True):
+    """plain_measure + the phase pass + the roofline, as one record."""
+    res, make_ctx = plain_measure(n, torch, cfg, K, args.warmup, stream, flush, seed, events,
+                                  0 if args.no_e2e else 200, dist, world, kp=kp, streaming=streaming)
+    breakdown = phase_breakdown(n, make_ctx, K, args.warmup, flush, stream) if phases else None
+    peaks, peak_kind = measured_peaks()
+    avg = res.get("timed_region_ms") or {"dominance": breakdown["dominance"], "peel": breakdown["peel"]}
+    src = "CUDA events inside the timed graph" if "timed_region_ms" in res else \
+        "the phase pass (events around every phase)"
+    roof = roofline_of(cfg, avg, res["peel_rows"] / K, probe, peaks, peak_kind)
+    roof["launch_ms_source"] = src
+    res["phase_ms"] = breakdown
+    res["roofline"] = roof
+    return res
+
+
+def cfg_dict(cfg, streaming=0):
+    return {"workload": cfg.name + ("_streaming" if streaming else ""), "m": cfg.m, "N": cfg.N,
+            "d": cfg.d, "refs": cfg.w}
+
+
+def run_ours(args, world, rank, local):
+    """A single plain workload (--workload small|scale|large|huge|knapsack)."""
+    import torch
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    from paper_2504_06067_gb300 import native as n
+
+    cfg = WORKLOADS[args.workload]
+    seed = cfg.seed + rank
+    streaming = 1 if (args.streaming or args.workload == "huge") else 0
+    kp = wl.knapsack_instance(cfg.m, cfg.d, cfg.seed) if args.workload == "knapsack" else None
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    probe = issue_probe(n, torch, stream)
+    K = args.steps
+    sampler = ClockSampler(local)
+    sampler.start()
+    res = plain_record(n, torch, cfg, K, args, stream, flush, seed, 1, dist, world, probe, kp=kp,
+                       streaming=streaming)
+    clocks = sampler.stop()
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return None
-
-    peaks, peak_kind = measured_peaks()
-    avg = {nm: ph_tot[i] / K for i, nm in enumerate(PHASE_NAMES)}
-    # dominant kernel by time: the dominance build (ALU) or the peel (HBM)
-    n2 = 2 * cfg.N
-    pairs = n2 * (n2 - 1) / 2
-    clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
-    if avg["dominance"] >= avg["peel"]:
-        ops = pairs * 2 * cfg.m  # FP32 compares: all(f_i <= f_j) and all(f_j <= f_i)
-        achieved = ops / (avg["dominance"] / 1e3) / 1e12
-        peak = NUM_SMS * LANES_PER_SM * clk / 1e12
-        roof = {"kernel": "k_dominance", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "Tcompare/s", "frac": achieved / peak,
-                "peak_source": "152 SMs x 128 lanes x %.0f MHz (max SM clock, %s)" % (clk / 1e6, peak_kind),
-                "algorithmic": "n2(n2-1)/2 pairs x 2m compares per launch",
-                "traffic": ncu_traffic("k_dominance", cfg.name)}
-    else:
-        bytes_read = peel_rows / K * 128 * 4.0  # row segments of 128 columns
-        per_launch_s = avg["peel"] / 1e3
-        achieved = bytes_read / per_launch_s / 1e9
-        peak = peaks.get("hbm_gbs", 6800.0)
-        roof = {"kernel": "k_peel (all passes of one selection)", "bound": "hbm", "achieved": achieved,
-                "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": "hbm_gbs (%s)" % peak_kind,
-                "algorithmic": "dominator row segments read (128 columns x 4 B each), all passes",
-                "traffic": ncu_traffic("k_peel", cfg.name)}
     line = {
         "metric": METRIC,
-        "value": value,
+        "value": res["value"],
         "unit": "sols/s",
-        "gens_per_s": world * K / total_s_max,
+        "gens_per_s": res["gens_per_s"],
         "n_gpus": world,
         "steps": K,
         "warmup": args.warmup,
-        "ms_per_step": total_s_max * 1e3 / K,
+        "ms_per_step": res["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -389,20 +454,19 @@ def run_ours(args, world, rank, local):
         "data": ("synthetic 0-1 knapsack instance (profits, weights U[10, 100], capacity half the "
                  "weight; stands in for MOKnapsack)" if args.workload == "knapsack" else
                  "synthetic (seeded softmax-simplex objective, W ~ N(0,1); stands in for DTLZ)"),
-        "config": {"workload": cfg.name + ("_streaming" if streaming else ""), "m": cfg.m, "N": cfg.N,
-                   "d": cfg.d, "refs": cfg.w,
-                   "generations": "timed %d from generation 0" % K,
-                   "l2": "flushed (256 MB write) before every timed step",
-                   "timing": "events around the dominance build and the peel inside the timed "
-                             "graph; phase_ms from a second pass with an event around every phase",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "phase_ms": breakdown,
-        "timed_region_ms": {"dominance": round(avg["dominance"], 5), "peel": round(avg["peel"], 5)},
-        "peel_passes_per_step": passes / K,
-        "niching_steps": niche_steps,
-        "roofline": roof,
-        "e2e": e2e,
-        "gpu_launches": n_launch,
+        "config": dict(cfg_dict(cfg, streaming), generations="timed %d from generation 0" % K,
+                       l2="flushed (256 MB write) before every timed step",
+                       timing="events around the dominance build and the peel inside the timed "
+                              "graph; phase_ms from a second pass with an event around every phase",
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "phase_ms": res["phase_ms"],
+        "timed_region_ms": res.get("timed_region_ms"),
+        "peel_passes_per_step": res["peel_passes_per_step"],
+        "niching_steps": res["niching_steps"],
+        "roofline": res["roofline"],
+        "issue_probe": probe,
+        "e2e": res.get("e2e"),
+        "gpu_launches": res["gpu_launches"],
         "clocks": clocks,
     }
     if not args.no_cpu_baseline and world == 1:
@@ -413,29 +477,112 @@ def run_ours(args, world, rank, local):
     return line
 
 
-# ---------------------------------------------------------------- batched ----
-def run_batched(args, world, rank, local):
-    """64 uneven independent runs (N log-uniform in [100, 20000], m in
-    {3, 5, 8}, d = m + 19): one batched CUDA graph per generation against the
-    plain path (each run alone, one graph launch per generation, runs one
-    after another).  A step is one generation of every run; both arms time
-    initialisation + `steps` generations of all runs, and the batched arm
-    also the read-back of every final population (e2e)."""
-    import numpy as np
+def run_headline(args, world, rank, local):
+    """The default line: m = 10, N = 100,000 (the largest single-GPU
+    configuration) as the headline, with the m = 5, N = 10,628 run, the 64
+    batched runs, a prefix of the served request stream, the issue probe and
+    the oracle on the host cores as sub-records."""
     import torch
     torch.cuda.set_device(local)
     dist = dist_init(world, "nccl")
     from paper_2504_06067_gb300 import native as n
 
-    gens = args.steps
-    cfgs = wl.batched_configs(n_runs=args.runs, seed=0, generations=gens)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    progress("issue probe")
+    probe = issue_probe(n, torch, stream)
+    cfg = wl.LARGE
+    K = args.steps
+    progress("headline %s: %d generations" % (cfg.name, K))
+    sampler = ClockSampler(local)
+    sampler.start()
+    # events around the dominance build and the peel in the timed graph: about
+    # 15 us of a 13.6 ms generation, and they time the dominant kernel live
+    head = plain_record(n, torch, cfg, K, args, stream, flush, cfg.seed + rank, 1, dist, world, probe)
+    clocks = sampler.stop()
+    progress("secondary %s" % wl.SCALE.name)
+    sec_cfg = wl.SCALE
+    sec = plain_record(n, torch, sec_cfg, sec_cfg.generations, args, stream, flush, sec_cfg.seed + rank, 0,
+                       dist, world, probe)
+    sec_line = {"value": sec["value"], "unit": "sols/s", "gens_per_s": sec["gens_per_s"],
+                "ms_per_step": sec["ms_per_step"], "steps": sec["steps"],
+                "config": dict(cfg_dict(sec_cfg), l2="flushed (256 MB write) before every timed step",
+                               timing="no event nodes in the timed graph; phase_ms and the roofline's "
+                                      "launch time from a second pass with an event around every phase"),
+                "phase_ms": sec["phase_ms"], "roofline": sec["roofline"], "e2e": sec.get("e2e"),
+                "peel_passes_per_step": sec["peel_passes_per_step"], "gpu_launches": sec["gpu_launches"]}
+    del flush
+    torch.cuda.empty_cache()
+    batched = None
+    if not args.no_batched:
+        progress("batched")
+        batched = batched_core(n, torch, stream, args.runs, 300, max(args.warmup, 1), dist, world, rank)
+    served = None
+    if not args.no_served:
+        progress("served")
+        served = served_core(n, torch, args.served_prefix, dist, world, rank)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+    line = {
+        "metric": METRIC,
+        "value": head["value"],
+        "unit": "sols/s",
+        "gens_per_s": head["gens_per_s"],
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded softmax-simplex objective, W ~ N(0,1); stands in for DTLZ)",
+        "config": dict(cfg_dict(cfg), generations="timed %d from generation 0" % K,
+                       l2="flushed (256 MB write) before every timed step",
+                       timing="events around the dominance build and the peel inside the timed "
+                              "graph; phase_ms from a second pass with an event around every phase",
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "phase_ms": head["phase_ms"],
+        "timed_region_ms": head.get("timed_region_ms"),
+        "peel_passes_per_step": head["peel_passes_per_step"],
+        "niching_steps": head["niching_steps"],
+        "roofline": head["roofline"],
+        "issue_probe": probe,
+        "e2e": head.get("e2e"),
+        "gpu_launches": head["gpu_launches"],
+        "clocks": clocks,
+        "secondary": sec_line,
+        "batched": batched,
+        "served": served,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        progress("cpu baseline")
+        line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_budget)
+        line["secondary"]["cpu_baseline"] = cpu_baseline(sec_cfg, args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return line
+
+
+# ---------------------------------------------------------------- batched ----
+def batched_core(n, torch, stream, n_runs, gens, warmup, dist, world, rank):
+    """64 uneven independent runs (N log-uniform in [100, 20000], m in
+    {3, 5, 8}, d = m + 19): one batched CUDA graph per generation against the
+    plain path (each run alone, one graph launch per generation, runs one
+    after another).  Both arms time initialisation + `gens` generations of
+    all runs, and the read-back of every final population (e2e); the same
+    runs then go through the run server (one stream per run).  Returns the
+    record (rank 0) or None."""
+    cfgs = wl.batched_configs(n_runs=n_runs, seed=0, generations=gens)
     Ws = [wl.objective_weights(c.m, c.seed) for c in cfgs]
     ctxs = []
     progress("creating %d contexts" % len(cfgs))
     for c, W in zip(cfgs, Ws):
         o = n.default_opts(seed=c.seed + 1000003 * rank, W=W.ctypes.data)
         ctxs.append(n.create(c.m, c.d, c.N, c.p1, o))
-    stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     hosts = [(torch.empty((c.N, c.d), dtype=torch.float32).pin_memory(),
               torch.empty((c.N, c.m), dtype=torch.float32).pin_memory(),
@@ -463,40 +610,41 @@ def run_batched(args, world, rank, local):
         for x, (X, F, R) in zip(ctxs, hosts):
             n.check(n.nsga3_get_population(x, X.data_ptr(), F.data_ptr(), R.data_ptr(), sh), x)
 
-    # warm-up: build every graph (the batched one included)
-    progress("warm-up")
-    for x in ctxs:
-        n.check(n.nsga3_init(x, sh), x)
-    n.check(n.run_batch(ctxs, max(args.warmup, 1), sh), ctxs[0])
-    for x in ctxs:
-        n.check(n.nsga3_run(x, max(args.warmup, 1), sh), x)
-    torch.cuda.synchronize()
-
-    sampler = ClockSampler(local)
-    sampler.start()
-    res = {}
-    for arm, fn in (("plain", plain), ("batched", batched)):
-        progress("%s arm" % arm)
-        barrier(dist)
-        torch.cuda.synchronize()
-        l0 = launches()
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        w0 = time.perf_counter()
-        e0.record(stream)
-        fn()
-        e1.record(stream)
-        read_back()
-        e2.record(stream)
-        e2.synchronize()
-        wall = time.perf_counter() - w0
-        res[arm] = {"s": reduce_max(dist, e0.elapsed_time(e1) / 1e3, "cuda"),
-                    "e2e_s": reduce_max(dist, e0.elapsed_time(e2) / 1e3, "cuda"),
-                    "wall_s": wall, "launches": launches() - l0,
-                    "pop": [tuple(t.clone() for t in h) for h in hosts]}
+    try:
+        # warm-up: build every graph (the batched one included)
+        progress("warm-up")
         for x in ctxs:
-            st = n.nsga3_sync(x, sh)
-            if st != n.OK:
-                raise RuntimeError("device status %d in the %s arm" % (st, arm))
+            n.check(n.nsga3_init(x, sh), x)
+        n.check(n.run_batch(ctxs, warmup, sh), ctxs[0])
+        for x in ctxs:
+            n.check(n.nsga3_run(x, warmup, sh), x)
+        torch.cuda.synchronize()
+        res = {}
+        for arm, fn in (("plain", plain), ("batched", batched)):
+            progress("%s arm" % arm)
+            barrier(dist)
+            torch.cuda.synchronize()
+            l0 = launches()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            w0 = time.perf_counter()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            read_back()
+            e2.record(stream)
+            e2.synchronize()
+            wall = time.perf_counter() - w0
+            res[arm] = {"s": reduce_max(dist, e0.elapsed_time(e1) / 1e3, "cuda"),
+                        "e2e_s": reduce_max(dist, e0.elapsed_time(e2) / 1e3, "cuda"),
+                        "wall_s": wall, "launches": launches() - l0,
+                        "pop": [tuple(t.clone() for t in h) for h in hosts]}
+            for x in ctxs:
+                st = n.nsga3_sync(x, sh)
+                if st != n.OK:
+                    raise RuntimeError("device status %d in the %s arm" % (st, arm))
+    finally:
+        for x in ctxs:
+            n.nsga3_destroy(x)
     # the same runs through the run server: every run on its own stream,
     # no per-generation join between runs
     torch.cuda.synchronize()
@@ -507,37 +655,24 @@ def run_batched(args, world, rank, local):
     sinf, _ = _serve(n, reqs, budget, len(cfgs), 8)
     server_s = time.perf_counter() - w0
     server_span = max(i.t_done for i in sinf.values()) - min(i.t_submit for i in sinf.values())
-    clocks = sampler.stop()
     same = all(all(torch.equal(a, b) for a, b in zip(p, q))
                for p, q in zip(res["plain"]["pop"], res["batched"]["pop"]))
-    for x in ctxs:
-        n.nsga3_destroy(x)
     if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
         return None
     R = len(cfgs)
     b, p = res["batched"], res["plain"]
     dom_bytes = sum((2 * c.N) ** 2 / 8 for c in cfgs)
-    line = {
-        "metric": METRIC,
+    return {
         "value": world * R / b["s"],
         "unit": "runs/s",
-        "n_gpus": world,
         "steps": gens,
-        "warmup": max(args.warmup, 1),
+        "warmup": warmup,
         "ms_per_step": b["s"] * 1e3 / gens,
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f32",
-        "data": "synthetic (seeded softmax-simplex objectives)",
         "config": {"workload": "batched_%druns_%dgens" % (R, gens), "runs": R,
                    "N": [c.N for c in cfgs], "m": [c.m for c in cfgs],
                    "d": "m + 19", "seeds": "0..%d" % (R - 1),
                    "l2": "not flushed: the runs' bit matrices alone hold %.2f GB, above the "
-                         "129 MB L2" % (dom_bytes / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                         "129 MB L2" % (dom_bytes / 1e9)},
         "plain": {"value": world * R / p["s"], "unit": "runs/s", "ms": p["s"] * 1e3,
                   "gpu_launches": p["launches"]},
         "batched_vs_plain": p["s"] / b["s"],
@@ -552,8 +687,30 @@ def run_batched(args, world, rank, local):
                 "note": "inputs are (m, d, N, seed, W) set at creation; the final populations "
                         "are read back into pinned host memory inside the timed region"},
         "gpu_launches": b["launches"],
-        "clocks": clocks,
     }
+
+
+def run_batched(args, world, rank, local):
+    """--workload batched: the batched record as its own line."""
+    import torch
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    from paper_2504_06067_gb300 import native as n
+
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    sampler.start()
+    rec = batched_core(n, torch, stream, args.runs, args.steps, max(args.warmup, 1), dist, world, rank)
+    clocks = sampler.stop()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+    line = {"metric": METRIC, "n_gpus": world, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded softmax-simplex objectives)"}
+    line.update(rec)
+    line["config"]["parallelism"] = "replicas" if world > 1 else "single GPU"
+    line["clocks"] = clocks
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -614,64 +771,53 @@ def _latency_summary(infos, reqs):
             "sols_per_s": work / (t_last - t_first), "requests": len(infos)}
 
 
-def run_served(args, world, rank, local):
+def served_core(n, torch, n_req, dist, world, rank, n_plain=None):
     """A Poisson stream of run requests (40 per second; N log-uniform in
-    [100, 50000], m in 3..10, 50..1000 generations, d = m + 29) served by the
-    continuous-batching server (64 slots, 8 generations per launch batch),
-    against the plain path (the same server with one slot: one run at a time,
-    in arrival order).  Latency = completion - arrival on the server clock;
-    runs/s = requests / (last completion - first arrival)."""
-    import torch
-    torch.cuda.set_device(local)
-    dist = dist_init(world, "nccl")
-    from paper_2504_06067_gb300 import native as n
-
-    n_req = args.requests or 400
+    [100, 50000], m in 3..10, 50..1000 generations, d = m + 29): its first
+    `n_req` requests served by the continuous-batching server (64 slots, 8
+    generations per launch batch), against the plain path on the first
+    `n_plain` (default all) requests (the same server with one slot: one run
+    at a time, in arrival order).  Latency = completion - arrival on the
+    server clock; runs/s = requests / (last completion - first arrival).
+    Returns the record (rank 0) or None."""
     reqs_all = wl.served_requests(n_req=n_req, rate_hz=40.0, seed=rank)
-    n_plain = min(n_req, 100)
+    n_plain = n_req if n_plain is None else min(n_plain, n_req)
     free, total = torch.cuda.mem_get_info()
     budget = int(min(0.7 * free, 160e9))
     # warm-up: one small run through each kind of server
     warm = [(0.0, wl.RunConfig("w", m=3, d=32, N=100, p1=12, generations=5, seed=0))]
     _serve(n, warm, budget // 8, 2, 8)
-    sampler = ClockSampler(local)
-    sampler.start()
     barrier(dist)
-    plain_inf, plain_stats = _serve(n, reqs_all[:n_plain], budget, 1, 8)
-    served_small, _ = _serve(n, reqs_all[:n_plain], budget, 64, 8)
+    plain_inf, _ = _serve(n, reqs_all[:n_plain], budget, 1, 8)
+    served_small = None
+    if n_plain < n_req:
+        served_small, _ = _serve(n, reqs_all[:n_plain], budget, 64, 8)
     served_inf, served_stats = _serve(n, reqs_all, budget, 64, 8)
+    if served_small is None:
+        served_small = served_inf
     barrier(dist)
-    clocks = sampler.stop()
     plain = _latency_summary(plain_inf, reqs_all[:n_plain])
     same = _latency_summary(served_small, reqs_all[:n_plain])
     full = _latency_summary(served_inf, reqs_all)
     makespan = reduce_max(dist, full["makespan_s"], "cuda")
     if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
         return None
-    line = {
-        "metric": METRIC,
+    rec = {
         "value": world * full["requests"] / makespan,
         "unit": "runs/s",
-        "n_gpus": world,
         "steps": full["requests"],
-        "warmup": 1,
-        "ms_per_step": makespan * 1e3 / full["requests"],
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f32",
-        "data": "synthetic (seeded softmax-simplex objectives, Poisson arrivals)",
         "config": {"workload": "served_%dreq_40hz" % n_req, "requests": n_req, "rate_hz": 40.0,
+                   "stream": "the first %d requests of the seeded 2,000-request stream" % n_req,
                    "N": "log-uniform [100, 50000]", "m": "3..10", "generations": "50..1000",
                    "d": "m + 29", "slots": 64, "gens_per_launch": 8, "budget_bytes": budget,
-                   "l2": "not flushed: concurrent runs' working sets exceed the 129 MB L2",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "l2": "not flushed: concurrent runs' working sets exceed the 129 MB L2"},
         "served": full,
-        "served_first_%d" % n_plain: same,
-        "plain_first_%d" % n_plain: plain,
+        "plain": plain,
         "served_vs_plain_runs_per_s": same["runs_per_s"] / plain["runs_per_s"],
+        "p50_s": full["p50_s"],
+        "p99_s": full["p99_s"],
+        "plain_p50_s": plain["p50_s"],
+        "plain_p99_s": plain["p99_s"],
         "peak_active": served_stats["peak_active"],
         "peak_bytes": served_stats["peak_bytes"],
         "e2e": {"value": world * full["requests"] / makespan, "unit": "runs/s",
@@ -680,8 +826,36 @@ def run_served(args, world, rank, local):
                 "note": "the server API is host-to-host: requests in, final populations out in host "
                         "memory; value and e2e are the same measurement"},
         "gpu_launches": served_stats["launches"],
-        "clocks": clocks,
     }
+    if n_plain < n_req:
+        rec["served_first_%d" % n_plain] = same
+    return rec
+
+
+def run_served(args, world, rank, local):
+    """--workload served: the served record as its own line (plain path on
+    the first 100 requests)."""
+    import torch
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    from paper_2504_06067_gb300 import native as n
+
+    n_req = args.requests or 400
+    sampler = ClockSampler(local)
+    sampler.start()
+    rec = served_core(n, torch, n_req, dist, world, rank, n_plain=100)
+    clocks = sampler.stop()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+    line = {"metric": METRIC, "n_gpus": world, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded softmax-simplex objectives, Poisson arrivals)"}
+    line.update(rec)
+    line["ms_per_step"] = 1e3 / rec["value"]
+    line["config"]["parallelism"] = "replicas" if world > 1 else "single GPU"
+    line["clocks"] = clocks
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -802,11 +976,12 @@ def run_sweep(args, world, rank, local):
     }
     if not args.no_cpu_baseline and world == 1:
         cfg = cfgs[-1]
+        import oracle
         spg, nst = oracle_generations(cfg, args.cpu_budget)
-        line["cpu_baseline"] = {"value": 1.0 / spg, "unit": line["unit"], "cores": 1,
+        line["cpu_baseline"] = {"value": 1.0 / spg, "unit": line["unit"], "cores": oracle.threads(),
                                 "kind": "oracle",
-                                "sample": "%d generation(s) of %s (FP64 C oracle, single thread)"
-                                          % (nst, cfg.name)}
+                                "sample": "%d generation(s) of %s (FP64 C oracle, OpenMP on %d threads)"
+                                          % (nst, cfg.name, oracle.threads())}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -862,21 +1037,37 @@ def oracle_generations(cfg, budget_s, max_steps=None, warmup=0):
 
 
 def cpu_baseline(cfg, budget_s):
+    import oracle
     spg, n = oracle_generations(cfg, budget_s)
-    return {"value": cfg.N / spg, "unit": "sols/s", "cores": 1, "kind": "oracle",
-            "sample": "%d generation(s) of %s from generation 0 (FP64 C oracle, single thread, "
-                      "%d host cores on the box)" % (n, cfg.name, os.cpu_count() or 0)}
+    return {"value": cfg.N / spg, "unit": "sols/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d generation(s) of %s from generation 0 (FP64 C oracle; OpenMP over the "
+                      "sort's and the association's independent loops on %d threads, %d host "
+                      "cores on the box)" % (n, cfg.name, oracle.threads(), os.cpu_count() or 0)}
+
+
+def reference_cfg(args):
+    if args.workload in ("sweep", "popsweep"):
+        return {"sweep": wl.objective_sweep, "popsweep": wl.population_sweep}[args.workload]()[-1]
+    if args.workload in ("headline", "select"):
+        return wl.LARGE
+    if args.workload in ("batched", "served"):
+        return wl.SCALE
+    return WORKLOADS[args.workload]
 
 
 def run_reference(args, world, rank):
-    """The oracle as the reference arm, on this workload's metric."""
+    """The oracle as the reference arm, on this workload's metric: whole
+    generations from generation 0 of the same seeded run, as many of the
+    requested steps as a 150 s budget allows (at least one)."""
     if rank != 0:
         return None
-    cfg = ({"sweep": wl.objective_sweep, "popsweep": wl.population_sweep}[args.workload]()[-1]
-           if args.workload in ("sweep", "popsweep") else WORKLOADS[args.workload])
+    import oracle
+    oracle.build()
+    cfg = reference_cfg(args)
     budget = 150.0
-    spg, nsteps = oracle_generations(cfg, budget, max_steps=args.steps, warmup=min(args.warmup, 1))
+    spg, nsteps = oracle_generations(cfg, budget, max_steps=args.steps, warmup=0)
     value = cfg.N / spg
+    cores = oracle.threads()
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -885,20 +1076,166 @@ def run_reference(args, world, rank):
         "gens_per_s": 1.0 / spg,
         "n_gpus": world,
         "steps": nsteps,
-        "warmup": min(args.warmup, 1),
+        "warmup": 0,
         "ms_per_step": spg * 1e3,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "data": "synthetic (seeded softmax-simplex objective)",
-        "config": {"workload": cfg.name, "m": cfg.m, "N": cfg.N, "d": cfg.d, "refs": cfg.w,
-                   "generations": "%d timed of the requested %d (150 s budget)" % (nsteps, args.steps)},
-        "cpu_baseline": {"value": value, "unit": "sols/s", "cores": 1, "kind": "oracle",
-                         "sample": "%d generation(s) of %s from generation 1" % (nsteps, cfg.name)},
+        "data": "synthetic (seeded softmax-simplex objective, W ~ N(0,1); stands in for DTLZ)",
+        "config": dict(cfg_dict(cfg), generations="timed %d from generation 0" % args.steps,
+                       l2="flushed (256 MB write) before every timed step",
+                       timing="events around the dominance build and the peel inside the timed "
+                              "graph; phase_ms from a second pass with an event around every phase",
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "reference_steps": "%d generation(s) from generation 0 of the requested %d (150 s budget); "
+                           "the oracle keeps no state between runs, so no warm-up generation" %
+                           (nsteps, args.steps),
+        "cpu_baseline": {"value": value, "unit": "sols/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d generation(s) of %s from generation 0 (FP64 C oracle, OpenMP "
+                                   "on %d threads)" % (nsteps, cfg.name, cores)},
         "e2e": {"value": value, "unit": "sols/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return line
+
+
+# ------------------------------------------------------ selection alone ----
+SELECT_KINDS = ("equal", "dups", "chain", "simplex")
+
+
+def run_select(args, world, rank, local):
+    """Selection microbenchmark: nsga3_select alone (selected sols/s = N /
+    the time of one selection, objectives already on the device) on merged
+    objective matrices saved from the plain runs of m3_N92, m5_N10628 and
+    m10_N100000 at generations 0, mid and last, and on adversarial sets
+    (all equal, many duplicates, a chain of one point per front, a single
+    simplex front) of the m5_N10628 and m10_N100000 shapes; beside it the
+    oracle's selection of the same matrices on the host cores (where it
+    fits the budget), which must select the same indices."""
+    import numpy as np
+    import torch
+
+    import oracle
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    from paper_2504_06067_gb300 import native as n
+    oracle.build()
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    K = args.steps
+    rows = []
+    n_launch = 0
+    sampler = ClockSampler(local)
+    sampler.start()
+    cpu_left = args.cpu_budget * 6
+    for cfg in (wl.SMALL, wl.SCALE, wl.LARGE):
+        W = wl.objective_weights(cfg.m, cfg.seed)
+        mats = []
+        progress("select: saving %s objectives" % cfg.name)
+        ctx = n.create(cfg.m, cfg.d, cfg.N, cfg.p1,
+                       n.default_opts(seed=cfg.seed, p2=cfg.p2, tau=cfg.tau, W=W.ctypes.data))
+        try:
+            Fp = np.zeros((cfg.N, cfg.m), np.float32)
+            Fc = np.zeros((cfg.N, cfg.m), np.float32)
+            n.check(n.nsga3_init(ctx, sh), ctx)
+            g = 0
+            for want in (0, cfg.generations // 2, cfg.generations):
+                n.check(n.nsga3_run(ctx, want - g, sh), ctx)
+                g = want
+                n.check(n.nsga3_get_population(ctx, None, Fp.ctypes.data, None, sh), ctx)
+                n.check(n.nsga3_vary(ctx, sh), ctx)
+                n.check(n.nsga3_get_children(ctx, None, Fc.ctypes.data, sh), ctx)
+                n.check(n.nsga3_sync(ctx, sh), ctx)
+                mats.append(("generation %d" % want, want, np.vstack([Fp, Fc]).copy()))
+        finally:
+            n.nsga3_destroy(ctx)
+        if cfg is not wl.SMALL:
+            for kind in SELECT_KINDS:
+                mats.append((kind, 0, wl.objectives(kind, 2 * cfg.N, cfg.m, seed=cfg.seed)))
+        Z = oracle.refdirs(cfg.m, cfg.p1, cfg.p2, cfg.tau)
+        ctx = n.create(cfg.m, cfg.d, cfg.N, cfg.p1, n.default_opts(seed=cfg.seed, p2=cfg.p2, tau=cfg.tau))
+        try:
+            dF = torch.empty((2 * cfg.N, cfg.m), dtype=torch.float32, device="cuda")
+            dr = torch.empty(2 * cfg.N, dtype=torch.int32, device="cuda")
+            ds = torch.empty(cfg.N, dtype=torch.int32, device="cuda")
+            info = (C.c_int32 * 13)()
+            launches = C.c_int32()
+            for label, gen, F in mats:
+                progress("select: %s %s" % (cfg.name, label))
+                dF.copy_(torch.from_numpy(F))
+                for _ in range(3):
+                    n.check(n.nsga3_set_counter(ctx, gen, sh), ctx)
+                    n.check(n.nsga3_select(ctx, dF.data_ptr(), dr.data_ptr(), ds.data_ptr(), sh), ctx)
+                n.check(n.nsga3_sync(ctx, sh), ctx)
+                ms = []
+                for _ in range(K):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    n.check(n.nsga3_select(ctx, dF.data_ptr(), dr.data_ptr(), ds.data_ptr(), sh), ctx)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                    n.check(n.nsga3_last_launches(ctx, C.byref(launches)), ctx)
+                    n_launch += launches.value
+                st = n.nsga3_sync(ctx, sh)
+                if st != n.OK:
+                    raise RuntimeError("device status %d (%s %s)" % (st, cfg.name, label))
+                n.check(n.nsga3_get_selection_info(ctx, info), ctx)
+                t = reduce_max(dist, statistics.median(ms) / 1e3, "cuda")
+                row = {"workload": cfg.name, "objectives": label, "N": cfg.N, "m": cfg.m,
+                       "ms": t * 1e3, "selected_sols_per_s": world * cfg.N / t,
+                       "fronts_to_l": info[0] + 1, "niching": bool(info[4]), "peel_passes": info[6]}
+                # the oracle beside it while the budget lasts (the m10 sort takes about a minute)
+                if rank == 0 and world == 1 and (cpu_left > 0 or cfg is wl.SMALL):
+                    t0 = time.perf_counter()
+                    ref = oracle.select(F, cfg.N, Z, seed=cfg.seed, gen=gen)
+                    ot = time.perf_counter() - t0
+                    cpu_left -= ot
+                    same = (np.array_equal(dr.cpu().numpy(), ref["rank"]) and
+                            np.array_equal(ds.cpu().numpy(), ref["selected"]))
+                    row["oracle"] = {"s": ot, "selected_sols_per_s": cfg.N / ot, "cores": oracle.threads(),
+                                     "identical": bool(same)}
+                rows.append(row)
+        finally:
+            n.nsga3_destroy(ctx)
+    clocks = sampler.stop()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+    head = [r for r in rows if r["workload"] == wl.LARGE.name and r["objectives"].startswith("generation")]
+    top = head[-1]
+    line = {
+        "metric": "selected sols/s of nsga3_select alone (N / one selection)",
+        "value": top["selected_sols_per_s"],
+        "unit": "sols/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": 3,
+        "ms_per_step": top["ms"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "objectives saved from seeded softmax-simplex runs (generations 0, mid, last) and "
+                "seeded adversarial sets",
+        "config": {"workload": "select_m3_m5_m10", "value_of": "%s %s" % (top["workload"], top["objectives"]),
+                   "l2": "flushed (256 MB write) before every timed selection",
+                   "timing": "median of %d selections per matrix (CUDA events; the copy of the "
+                             "objectives into the context, the graph and the copies of ranks and "
+                             "indices out, all device to device)" % K,
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "rows": rows,
+        "gpu_launches": n_launch,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
     return line
 
 
@@ -916,17 +1253,22 @@ def main(argv=None):
     args = parse_args(argv)
     world, rank, local = dist_env()
     if args.steps is None:
-        args.steps = {"batched": 300, "served": 0, "sweep": 50, "popsweep": 50}.get(args.workload)
+        args.steps = {"headline": wl.LARGE.generations, "batched": 300, "served": 0, "sweep": 50,
+                      "popsweep": 50, "select": 20}.get(args.workload)
         if args.steps is None:
             args.steps = WORKLOADS[args.workload].generations
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "headline":
+        run_headline(args, world, rank, local)
     elif args.workload == "batched":
         run_batched(args, world, rank, local)
     elif args.workload == "served":
         run_served(args, world, rank, local)
     elif args.workload in ("sweep", "popsweep"):
         run_sweep(args, world, rank, local)
+    elif args.workload == "select":
+        run_select(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

@@ -67,3 +67,17 @@ def test_reference_arm_line_on_cpu():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["config"]["workload"] == "m3_N92_d12_p12"
+
+
+def test_default_workload_is_the_large_configuration():
+    """With no flags bench.py measures m = 10, N = 100,000 (the largest
+    single-GPU configuration), and the reference arm times the oracle on that
+    same configuration with the same config keys."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2504_06067_gb300 import workloads as wl
+    args = bench.parse_args([])
+    assert args.workload == "headline" and args.warmup >= 3
+    assert bench.reference_cfg(args) is wl.LARGE
+    assert bench.cfg_dict(wl.LARGE)["workload"] == "m10_N100000_d200_p3+2"
+    assert wl.LARGE.N == 100000 and wl.LARGE.m == 10 and wl.LARGE.generations == 200
