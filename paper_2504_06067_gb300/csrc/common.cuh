@@ -20,7 +20,10 @@
 #define NSGA3_WARP_M 32         // largest m whose intercept system one warp solves
 #define NSGA3_TILE 256          // column tile of the dominance build; ld % 256 == 0
 #define NSGA3_PEEL_COLS 128     // columns per peel chunk (4 per lane, 32 lanes)
-#define SORT_NB 4096            // f_0 buckets of the bucket order
+#define SORT_NB 4096            // sort keys of the f_0 bucket order (m > 10)
+#define SORT_KMAX 65536         // largest number of sort keys (m <= 10: 2^kbits keys)
+#define SORT_QB 1024            // histogram bins per objective for the level thresholds
+#define SORT_LMAX 7             // level thresholds per objective (3 bits of level)
 
 // Capacity paths of the niching kernels (Ctrl::npath, reported by
 // nsga3_get_selection_paths; same values as NSGA3_PATH_* in nsga3.h)
@@ -80,8 +83,9 @@ struct Ctrl {
     uint32_t ext_done;       // completion ticket of the extreme-point blocks
     uint32_t sort_done;      // completion ticket of the bucket histogram
     uint32_t f0lo, f0hi;     // range of f_0 as order-preserving uint
-    uint32_t range_done;     // completion ticket of the sort's range / threshold blocks
-    float thr[NSGA3_FAST_M]; // per-objective thresholds of the sort keys' codes (m <= 10)
+    uint32_t thr_done;       // completion ticket of the sort's threshold histogram blocks
+    uint32_t omin[NSGA3_FAST_M], omax[NSGA3_FAST_M];  // objective ranges (order-preserving uint)
+    float thr[NSGA3_FAST_M][SORT_LMAX];               // level thresholds of the sort keys (m <= 10)
     uint32_t cmp_done;       // completion ticket of the compaction blocks
     uint32_t zmin[NSGA3_MAX_M];  // ideal point as order-preserving uint of FP32
     double zstar[NSGA3_MAX_M];   // ideal point (FP64, +0.0 for zero)
@@ -121,9 +125,17 @@ struct RunView {
     int32_t* rank2;    // ld   merged ranks (original order)
     int32_t* srank;    // ld   merged ranks in bucket order (peel)
     int32_t* perm;     // ld   bucket order position -> original index
-    uint32_t* skey;    // ld   bucket of each position (0xffffffff for padding)
+    uint32_t* skey;    // ld   sort key of each position (0xffffffff for padding)
     float* Fp;         // ld x m objectives in bucket order, -0.0 as +0.0, NaN padding
-    int32_t* bcnt;     // SORT_NB bucket counts, then offsets / cursors
+    int32_t* bcnt;     // nkeys + 1 key counts, then offsets / cursors
+    int kbits;         // bits of a sort key (nkeys = 2^kbits)
+    int lbits;         // bits of level per objective in a sort key (m <= 10)
+    int32_t* qhist;    // m x SORT_QB objective histograms (level thresholds)
+    float* bbox;       // NW x 2 M4: per 32-position block min, then max of each objective
+    uint32_t* bkey;    // NW x 2: per block smallest, largest sort key
+    uint8_t* dnz;      // NW x NB8 bits: Dom block (I, J) has a nonzero word (m <= 10, matrix);
+                       // null: every Dom word is written
+    int NB8;           // bytes of dnz per dominator block row = ceil(NW / 8)
     uint32_t* rem;     // NW   not-yet-ranked mask
     uint32_t* front;   // 2 x NW  ping-pong front masks
     uint32_t* chunk_lim;   // ld / NSGA3_PEEL_COLS dominator row blocks a column chunk reads

@@ -82,7 +82,8 @@ namespace {
 int select_launches(const nsga3_ctx* ctx)
 {
     const int m = ctx->m;
-    return 18 + (m > NSGA3_FAST_M ? 5 : 0) + (m > NSGA3_WARP_M ? 1 : 0) + (ctx->v.dom_ks > 1 ? 1 : 0);
+    // m <= 10: + the sort's level thresholds and the dominance build's block boxes
+    return 18 + (m > NSGA3_FAST_M ? 5 : 2) + (m > NSGA3_WARP_M ? 1 : 0) + (ctx->v.dom_ks > 1 ? 1 : 0);
 }
 // the softmax-simplex objective's dot-product kernel (m > 10)
 int objective_dot_launches(const nsga3_ctx* ctx) { return ctx->m > NSGA3_FAST_M && ctx->v.problem == 0 ? 1 : 0; }
@@ -466,7 +467,27 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     AL(v.perm, ld);
     AL(v.skey, ld);
     AL(v.Fp, (size_t)ld * m);
-    AL(v.bcnt, SORT_NB + 1);
+    // sort keys (k_sort.cu): m <= 10 interleaves lbits of level per objective
+    // (Morton order), truncated to kbits, about n2 / 2 keys; above, 4,096 f_0 buckets
+    if (m <= NSGA3_FAST_M) {
+        v.lbits = m <= 5 ? 3 : 2;
+        int lg = 0;
+        while ((2 << lg) <= n2) ++lg;  // floor(log2(n2))
+        int kb = lg - 1;
+        kb = kb < 8 ? 8 : kb > 16 ? 16 : kb;
+        v.kbits = kb < v.lbits * m ? kb : v.lbits * m;
+    } else {
+        v.lbits = 0;
+        v.kbits = 12;
+    }
+    AL(v.bcnt, (1 << v.kbits) + 1);
+    v.NB8 = (NW + 7) / 8;
+    if (m <= NSGA3_FAST_M) {
+        AL(v.qhist, (size_t)m * SORT_QB);
+        AL(v.bbox, (size_t)NW * 2 * M4);
+        AL(v.bkey, (size_t)NW * 2);
+        if (!v.streaming) AL(v.dnz, (size_t)NW * v.NB8);
+    }
     AL(v.rem, NW);
     AL(v.front, 2 * NW);
     AL(v.chunk_lim, ld / NSGA3_PEEL_COLS);

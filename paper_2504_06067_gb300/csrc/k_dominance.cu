@@ -70,23 +70,23 @@ __device__ __forceinline__ void decode_tile(long long t, int T, int& ti, int& tj
     tj = r + (int)(t - start(r));
 }
 
-// Sign bit set iff some f_iq > f_jq for q = 1 .. M-1 (the one-direction
+// Sign bit set iff some f_iq > f_jq for q = Q0 .. M-1 (the one-direction
 // test).  The sign bits are OR-ed three at a time on the integer pipe; when
-// the M-1 differences are an even number, the first two are first combined
+// the M-Q0 differences are an even number, the first two are first combined
 // by fminf on the FP32 pipe (the minimum is negative iff one of them is;
 // differences are never -0.0 because -0.0 is staged as +0.0), which saves
 // one integer operation per pair and row.
-template <int M>
+template <int Q0, int M>
 __device__ __forceinline__ uint32_t any_greater(const float* fj, const float* fi)
 {
     uint32_t oa;
     int q0;
-    if (M >= 3 && (M - 1) % 2 == 0) {
-        oa = __float_as_uint(fminf(fj[1] - fi[1], fj[2] - fi[2]));
-        q0 = 3;
+    if (M - Q0 >= 2 && (M - Q0) % 2 == 0) {
+        oa = __float_as_uint(fminf(fj[Q0] - fi[Q0], fj[Q0 + 1] - fi[Q0 + 1]));
+        q0 = Q0 + 2;
     } else {
         oa = 0u;
-        q0 = 1;
+        q0 = Q0;
     }
 #pragma unroll
     for (int q = q0; q < M; ++q) oa |= __float_as_uint(fj[q] - fi[q]);
@@ -126,6 +126,113 @@ __device__ __forceinline__ void block_full(const float* fi, const float* colp, u
     }
 }
 
+// "Some f_iq > f_jq" bits of one or two row lanes against the 32 columns of
+// a block (bit k for column k), objectives Q0 .. M-1; with two rows every
+// column load serves both.
+template <int Q0, int M, int M4, bool TWO>
+__device__ __forceinline__ void block_one_dir(const float* f0, const float* f1, const float* colp, uint32_t& acc0,
+                                              uint32_t& acc1)
+{
+    acc0 = 0u;
+    acc1 = 0u;
+#pragma unroll 4
+    for (int k = 31; k >= 0; --k) {
+        const float4* fj4 = reinterpret_cast<const float4*>(colp + k * M4);
+        float fj[M4];
+#pragma unroll
+        for (int q4 = 0; q4 < M4 / 4; ++q4) {
+            const float4 t = fj4[q4];
+            fj[4 * q4 + 0] = t.x;
+            fj[4 * q4 + 1] = t.y;
+            fj[4 * q4 + 2] = t.z;
+            fj[4 * q4 + 3] = t.w;
+        }
+        acc0 = __funnelshift_l(any_greater<Q0, M>(fj, f0), acc0, 1);  // sign set: some f_iq > f_jq
+        if (TWO) acc1 = __funnelshift_l(any_greater<Q0, M>(fj, f1), acc1, 1);
+    }
+}
+
+// How a (row block, column block) pair is tested.
+enum : int {
+    BP_SKIP = 0,   // lower block triangle (done by the transposed tile)
+    BP_ZERO,       // no dominance either way: no test, no words
+    BP_FAST0,      // only "row dom column": every row f_0 below every column f_0, objectives 1..M-1
+    BP_FASTK,      // only "row dom column", objectives 0..M-1
+    BP_FASTR,      // only "column dom row", objectives 0..M-1
+    BP_FULL        // both directions tested
+};
+
+// Per 32-position block of the key order (k_sort.cu): the smallest and
+// largest value of every objective (NaN padding ignored; NaN for a block of
+// padding only) and the smallest and largest sort key.  One warp per block.
+__global__ void __launch_bounds__(256) k_block_box(RunView v)
+{
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= v.NW) return;
+    if (read_status(v.ctrl)) return;
+    const int lane = lane_id(), m = v.m, M4 = v.M4;
+    const int p = b * 32 + lane;
+    float* box = v.bbox + (size_t)b * 2 * M4;
+    for (int q = 0; q < m; ++q) {
+        float lo = v.Fp[(size_t)p * m + q], hi = lo;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            box[q] = lo;
+            box[M4 + q] = hi;
+        }
+    }
+    const uint32_t k = v.skey[p];
+    const uint32_t kmin = __reduce_min_sync(0xffffffffu, k), kmax = __reduce_max_sync(0xffffffffu, k);
+    if (lane == 0) {
+        v.bkey[2 * b] = kmin;
+        v.bkey[2 * b + 1] = kmax;
+    }
+}
+
+// Mode of block pair (ib, jb) from the blocks' boxes and keys (warp-wide:
+// lane q < M compares objective q).  Row i can dominate column j only if
+// f_iq <= f_jq for every q, so some row of I can dominate some column of J
+// only if min_I q <= max_J q for every q (fwd), and symmetrically (bwd); when
+// a box test fails, some objective separates every pair of the two blocks,
+// so their vectors differ and the other direction's dominance needs no
+// strictness test.  Dominators never have a larger sort key, so every key
+// of I below every key of J also rules out "column dom row".
+template <int M>
+__device__ __forceinline__ int block_pair_mode(const RunView& v, int ib, int jb)
+{
+    if (jb < ib) return BP_SKIP;
+    if (jb == ib) return BP_FULL;
+    if (jb * 32 >= v.n2) return BP_ZERO;  // a column block of padding only
+    constexpr int M4 = (M + 3) & ~3;
+    const int lane = lane_id();
+    const float* bi = v.bbox + (size_t)ib * 2 * M4;
+    const float* bj = v.bbox + (size_t)jb * 2 * M4;
+    const int q = lane < M ? lane : 0;
+    const float imin = bi[q], imax = bi[M4 + q], jmin = bj[q], jmax = bj[M4 + q];
+    // NaN boxes (padding only) fail every comparison: no dominance
+    const bool fwd = __all_sync(0xffffffffu, lane >= M || imin <= jmax);
+    const bool bwd = __all_sync(0xffffffffu, lane >= M || jmin <= imax) && !(v.bkey[2 * ib + 1] < v.bkey[2 * jb]);
+    const bool f0sep = __shfl_sync(0xffffffffu, imax < jmin, 0);  // every row f_0 below every column f_0
+    if (!fwd && !bwd) return BP_ZERO;
+    if (fwd && f0sep) return BP_FAST0;
+    if (fwd && !bwd) return BP_FASTK;
+    if (!fwd) return BP_FASTR;
+    return BP_FULL;
+}
+
+// Words of Dom block (dominator block of the word row, 32 columns): written
+// only when one of them is nonzero, and the block's bit in dnz records it.
+__device__ __forceinline__ void put_block(const RunView& v, size_t at, uint32_t word, unsigned* nzw, int byte, int bit)
+{
+    if (!__any_sync(0xffffffffu, word != 0u)) return;
+    if (!v.streaming) v.Dom[at] = word;
+    if (lane_id() == 0 && nzw) atomicOr(&nzw[byte >> 2], 1u << (8 * (byte & 3) + bit));
+}
+
 template <int M>
 __global__ void __launch_bounds__(256) k_dominance(RunView v)
 {
@@ -135,123 +242,129 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
     __shared__ int s_tile[2];
     __shared__ int rowcnt[NSGA3_TILE];  // dominators found for the tile's row points
     __shared__ int colcnt[NSGA3_TILE];  // ... for its column points
+    __shared__ unsigned nzw[4];         // dnz bytes: 0..7 row blocks (I, J), 8..15 column blocks (J, I)
     if (read_status(v.ctrl)) return;
     rowcnt[threadIdx.x] = 0;
     colcnt[threadIdx.x] = 0;
+    if (threadIdx.x < 4) nzw[threadIdx.x] = 0u;
     const int T = v.ld / NSGA3_TILE;
     if (threadIdx.x == 0) decode_tile(blockIdx.x, T, s_tile[0], s_tile[1]);
     __syncthreads();
     const int ti = s_tile[0], tj = s_tile[1];
     const int r0 = ti * NSGA3_TILE, c0 = tj * NSGA3_TILE;
-    // Fp holds -0.0 as +0.0, so equal values subtract to +0.0
-    for (int e = threadIdx.x; e < NSGA3_TILE * M; e += blockDim.x) {
-        int p = e / M, q = e - p * M;
-        srow[p * M4 + q] = v.Fp[(size_t)r0 * M + e];
-        scol[p * M4 + q] = v.Fp[(size_t)c0 * M + e];
-    }
-    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = lane_id();
     // warp = (row pair rp, column half ch): row blocks 2rp, 2rp+1 of the tile
     // against column blocks 4ch .. 4ch+3; every column load serves two rows
     const int rp = warp & 3, ch = warp >> 2;
     const int ib0 = ti * 8 + 2 * rp, ib1 = ib0 + 1;
-    float f0[M], f1[M];
+    unsigned modes = 0u;  // 4 bits per (column block cbi, row r): bits 8 cbi + 4 r
+    bool work = false;
 #pragma unroll
-    for (int q = 0; q < M; ++q) {
-        f0[q] = srow[(2 * rp * 32 + lane) * M4 + q];
-        f1[q] = srow[((2 * rp + 1) * 32 + lane) * M4 + q];
-    }
-    float rmax0 = f0[0], rmax1 = f1[0];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        rmax0 = fmaxf(rmax0, __shfl_xor_sync(0xffffffffu, rmax0, o));
-        rmax1 = fmaxf(rmax1, __shfl_xor_sync(0xffffffffu, rmax1, o));
-    }
-    uint32_t* D = v.Dom;
-    int rc0 = 0, rc1 = 0;  // dominators of row points ib0*32+lane, ib1*32+lane in this tile
     for (int cbi = 0; cbi < 4; ++cbi) {
-        const int cb = ch * 4 + cbi;
-        const int jb = tj * 8 + cb;
-        if (jb < ib0) continue;  // lower block triangle: done by the transposed tile
-        const float* colp = scol + cb * 32 * M4;
-        float cmin = colp[lane * M4];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
-        // every row's f_0 below every column's f_0: only "row dom column" can
-        // hold, f_i0 < f_j0 makes it strict, and objectives 1..m-1 decide it
-        const bool fast0 = jb != ib0 && rmax0 < cmin;
-        const bool fast1 = jb > ib1 && rmax1 < cmin;
-        if (fast0 && fast1) {
-            uint32_t acc0 = 0u, acc1 = 0u;
-#pragma unroll 4
-            for (int k = 31; k >= 0; --k) {
-                const float4* fj4 = reinterpret_cast<const float4*>(colp + k * M4);
-                float fj[M4];
-#pragma unroll
-                for (int q4 = 0; q4 < M4 / 4; ++q4) {
-                    const float4 t = fj4[q4];
-                    fj[4 * q4 + 0] = t.x;
-                    fj[4 * q4 + 1] = t.y;
-                    fj[4 * q4 + 2] = t.z;
-                    fj[4 * q4 + 3] = t.w;
-                }
-                const uint32_t oa0 = any_greater<M>(fj, f0), oa1 = any_greater<M>(fj, f1);
-                acc0 = __funnelshift_l(oa0, acc0, 1);  // sign set: some f_iq > f_jq
-                acc1 = __funnelshift_l(oa1, acc1, 1);
-            }
-            const uint32_t t0 = warp_transpose32(~acc0), t1 = warp_transpose32(~acc1);
-            if (!v.streaming) {
-                D[(size_t)jb * v.ld + ib0 * 32 + lane] = 0u;
-                D[(size_t)jb * v.ld + ib1 * 32 + lane] = 0u;
-                D[(size_t)ib0 * v.ld + jb * 32 + lane] = t0;
-                D[(size_t)ib1 * v.ld + jb * 32 + lane] = t1;
-            }
-            const int cc = __popc(t0) + __popc(t1);
-            if (cc) atomicAdd(&colcnt[cb * 32 + lane], cc);
-            continue;
+        const int jb = tj * 8 + ch * 4 + cbi;
+        const int a = block_pair_mode<M>(v, ib0, jb), b = block_pair_mode<M>(v, ib1, jb);
+        modes |= ((unsigned)a | ((unsigned)b << 4)) << (8 * cbi);
+        work = work || a > BP_ZERO || b > BP_ZERO;
+    }
+    // a tile without any block pair to test writes no word and stages nothing
+    const bool tile_work = __syncthreads_or(work);
+    unsigned* nz = v.dnz ? nzw : nullptr;
+    if (tile_work) {
+        // Fp holds -0.0 as +0.0, so equal values subtract to +0.0
+        for (int e = threadIdx.x; e < NSGA3_TILE * M; e += blockDim.x) {
+            int p = e / M, q = e - p * M;
+            srow[p * M4 + q] = v.Fp[(size_t)r0 * M + e];
+            scol[p * M4 + q] = v.Fp[(size_t)c0 * M + e];
         }
+        __syncthreads();
+        float f0[M], f1[M];
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int ib = r ? ib1 : ib0;
-            if (jb < ib) continue;
-            const float* fi = r ? f1 : f0;
-            const bool fast = r ? fast1 : fast0;
-            uint32_t dij, dji;
-            if (fast) {
-                uint32_t acc = 0u;
+        for (int q = 0; q < M; ++q) {
+            f0[q] = srow[(2 * rp * 32 + lane) * M4 + q];
+            f1[q] = srow[((2 * rp + 1) * 32 + lane) * M4 + q];
+        }
+        int rc0 = 0, rc1 = 0;  // dominators of row points ib0*32+lane, ib1*32+lane in this tile
+        for (int cbi = 0; cbi < 4; ++cbi) {
+            const int cb = ch * 4 + cbi;
+            const int jb = tj * 8 + cb;
+            const int mode0 = (modes >> (8 * cbi)) & 15u, mode1 = (modes >> (8 * cbi + 4)) & 15u;
+            if (mode0 == BP_SKIP && mode1 == BP_SKIP) continue;
+            const float* colp = scol + cb * 32 * M4;
+            if (mode0 == mode1 && (mode0 == BP_FAST0 || mode0 == BP_FASTK)) {
+                // both rows the same one-direction test: one pass over the columns
+                uint32_t acc0, acc1;
+                if (mode0 == BP_FAST0)
+                    block_one_dir<1, M, M4, true>(f0, f1, colp, acc0, acc1);
+                else
+                    block_one_dir<0, M, M4, true>(f0, f1, colp, acc0, acc1);
+                const uint32_t t0 = warp_transpose32(~acc0), t1 = warp_transpose32(~acc1);
+                put_block(v, (size_t)ib0 * v.ld + jb * 32 + lane, t0, nz, 2 * rp, cb);
+                put_block(v, (size_t)ib1 * v.ld + jb * 32 + lane, t1, nz, 2 * rp + 1, cb);
+                const int cc = __popc(t0) + __popc(t1);
+                if (cc) atomicAdd(&colcnt[cb * 32 + lane], cc);
+                continue;
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int ib = r ? ib1 : ib0;
+                const int mode = r ? mode1 : mode0;
+                if (mode == BP_SKIP || mode == BP_ZERO) continue;
+                const float* fi = r ? f1 : f0;
+                uint32_t dij = 0u, dji = 0u;
+                if (mode == BP_FAST0 || mode == BP_FASTK) {
+                    uint32_t acc, unused;
+                    if (mode == BP_FAST0)
+                        block_one_dir<1, M, M4, false>(fi, fi, colp, acc, unused);
+                    else
+                        block_one_dir<0, M, M4, false>(fi, fi, colp, acc, unused);
+                    dij = ~acc;
+                } else if (mode == BP_FASTR) {
+                    // column j dominates row i: no f_jq > f_iq (the vectors differ)
+                    uint32_t acc = 0u;
 #pragma unroll 4
-                for (int k = 31; k >= 0; --k) {
-                    const float* fj = colp + k * M4;
-                    acc = __funnelshift_l(any_greater<M>(fj, fi), acc, 1);
+                    for (int k = 31; k >= 0; --k) {
+                        const float* fj = colp + k * M4;
+                        acc = __funnelshift_l(any_greater<0, M>(fi, fj), acc, 1);
+                    }
+                    dji = ~acc;
+                } else {
+                    block_full<M, M4>(fi, colp, dij, dji);
                 }
-                dij = ~acc;
-                dji = 0u;
-            } else if (jb * 32 >= v.n2) {
-                // a column block of padding only: no bit either way (the
-                // NaN differences would give the same zeros)
-                dij = 0u;
-                dji = 0u;
-            } else {
-                block_full<M, M4>(fi, colp, dij, dji);
+                // column i = ib*32 + lane, dominators j in block jb: Dom block (jb, ib)
+                const int ri = 2 * rp + r;
+                if (jb != ib) {
+                    put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, 8 + cb, ri);
+                    const uint32_t t = warp_transpose32(dij);
+                    put_block(v, (size_t)ib * v.ld + jb * 32 + lane, t, nz, ri, cb);
+                    if (t) atomicAdd(&colcnt[cb * 32 + lane], __popc(t));
+                } else {
+                    put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, ri, cb);
+                }
+                if (r)
+                    rc1 += __popc(dji);
+                else
+                    rc0 += __popc(dji);
             }
-            // column i = ib*32 + lane, dominators j in block jb
-            if (!v.streaming) D[(size_t)jb * v.ld + ib * 32 + lane] = dji;
-            if (r)
-                rc1 += __popc(dji);
-            else
-                rc0 += __popc(dji);
-            if (jb != ib) {
-                const uint32_t t = warp_transpose32(dij);
-                if (!v.streaming) D[(size_t)ib * v.ld + jb * 32 + lane] = t;
-                if (t) atomicAdd(&colcnt[cb * 32 + lane], __popc(t));
-            }
+        }
+        if (rc0) atomicAdd(&rowcnt[2 * rp * 32 + lane], rc0);
+        if (rc1) atomicAdd(&rowcnt[(2 * rp + 1) * 32 + lane], rc1);
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (v.dnz) {
+        // this tile owns bytes dnz[I][tj] (I a row block) and dnz[J][ti] (J a
+        // column block), one byte each; on the diagonal they are the same bytes
+        const unsigned char* nzb = reinterpret_cast<const unsigned char*>(nzw);
+        if (t < 8) {
+            unsigned char x = nzb[t];
+            if (ti == tj) x |= nzb[8 + t];
+            v.dnz[(size_t)(ti * 8 + t) * v.NB8 + tj] = x;
+        } else if (t < 16 && ti != tj) {
+            v.dnz[(size_t)(tj * 8 + (t - 8)) * v.NB8 + ti] = nzb[t];
         }
     }
-    if (rc0) atomicAdd(&rowcnt[2 * rp * 32 + lane], rc0);
-    if (rc1) atomicAdd(&rowcnt[(2 * rp + 1) * 32 + lane], rc1);
-    __syncthreads();
+    if (!tile_work) return;
     // dominator counts of the peel's first pass: one global add per point of the tile
-    const int t = threadIdx.x;
     if (rowcnt[t]) atomicAdd(&v.cnt[r0 + t], rowcnt[t]);
     if (colcnt[t]) atomicAdd(&v.cnt[c0 + t], colcnt[t]);
 }
@@ -457,6 +570,9 @@ cudaError_t launch_dom_m(const RunView& v, cudaStream_t s)
     long long T = v.ld / NSGA3_TILE;
     long long tiles = T * (T + 1) / 2;
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_block_box<<<(unsigned)(((long long)v.NW * 32 + 255) / 256), 256, 0, s>>>(v);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     k_dominance<M><<<(unsigned)tiles, 256, 0, s>>>(v);
     return cudaGetLastError();
 }

@@ -14,7 +14,9 @@ __global__ void k_sel_reset(RunView v)
         v.rank2[j] = -1;
         v.srank[j] = -1;
     }
-    for (int b = tid; b < SORT_NB; b += stride) v.bcnt[b] = 0;
+    for (int b = tid; b <= (1 << v.kbits); b += stride) v.bcnt[b] = 0;
+    if (v.qhist)
+        for (int b = tid; b < v.m * SORT_QB; b += stride) v.qhist[b] = 0;
     for (int wd = tid; wd < v.NW; wd += stride) {
         const int lo = wd * 32;
         uint32_t m = 0u;
@@ -56,6 +58,11 @@ __global__ void k_sel_reset(RunView v)
         c->sort_done = 0u;
         c->f0lo = 0xffffffffu;
         c->f0hi = 0u;
+        c->thr_done = 0u;
+        for (int q = 0; q < NSGA3_FAST_M; ++q) {
+            c->omin[q] = 0xffffffffu;
+            c->omax[q] = 0u;
+        }
         c->cmp_done = 0u;
         c->overflow = 0;
         c->recheck_miss = 0;

@@ -53,9 +53,10 @@ __global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v
                 my_rank = __ldcg(&v.srank[j0 + tid]);
                 my_cnt = __ldcg(&v.cnt[j0 + tid]);
             }
-            // Dominators of a column have f_0 <= its f_0.  Keys are non-decreasing in
-            // bucket order and bcnt[b] is the end of bucket b, so the positions that
-            // can dominate this chunk end at bcnt[key of its last column].
+            // Dominators of a column have a sort key <= its key (k_sort.cu).  Keys
+            // are non-decreasing in position order and bcnt[b] is the end of key b,
+            // so the positions that can dominate this chunk end at bcnt[key of its
+            // last column].
             const int jl = min(j0 + NSGA3_PEEL_COLS, v.n2) - 1;
             int lim = 0;
             if (jl >= j0) lim = (v.bcnt[v.skey[jl]] + 31) >> 5;
@@ -153,6 +154,17 @@ __global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v
             } else if (!STREAM && any_rem && k > 0) {
                 const uint4* base = reinterpret_cast<const uint4*>(v.Dom + j0) + lane;
                 const size_t ld4 = (size_t)v.ld / 4;
+                // with the block bitmap (m <= 10) only the Dom blocks whose bit
+                // is set were written this selection: the lane's column block
+                // J = j0 / 32 + lane / 8 is read from dominator block w only if
+                // bit J of dnz[w] is set
+                const int Jb = j0 / 32 + (lane >> 3);
+                const uint8_t* nzrow = v.dnz ? v.dnz + (Jb >> 3) : nullptr;
+                const unsigned nzbit = 1u << (Jb & 7);
+                auto load = [&](unsigned w) -> uint4 {
+                    if (nzrow && !(nzrow[(size_t)w * v.NB8] & nzbit)) return make_uint4(0u, 0u, 0u, 0u);
+                    return __ldg(base + (size_t)w * ld4);
+                };
                 {
                     const uint32_t* prev = v.front + ((k - 1) & 1) * v.NW;
                     for (int wb = 0; wb < lim; wb += LISTCAP) {
@@ -178,7 +190,7 @@ __global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v
 #pragma unroll
                             for (int t = 0; t < 4; ++t) {
                                 L[t] = list[e + PW * t];
-                                x[t] = __ldg(base + (size_t)L[t].x * ld4);
+                                x[t] = load(L[t].x);
                             }
 #pragma unroll
                             for (int t = 0; t < 4; ++t) {
@@ -190,7 +202,7 @@ __global__ void __launch_bounds__(PEEL_THREADS, STREAM ? 1 : 2) k_peel(RunView v
                         }
                         for (; e < n; e += PW) {
                             const uint2 L = list[e];
-                            const uint4 x = __ldg(base + (size_t)L.x * ld4);
+                            const uint4 x = load(L.x);
                             a0 += __popc(x.x & L.y);
                             a1 += __popc(x.y & L.y);
                             a2 += __popc(x.z & L.y);

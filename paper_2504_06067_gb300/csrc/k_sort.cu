@@ -1,15 +1,26 @@
-// k_sort.cu -- bucket order of the merged population by its first objective,
-// used by the dominance build and the front peel (Alg. 1, the non-dominated sort).
+// k_sort.cu -- sort keys of the merged population, used by the dominance
+// build and the front peel (Alg. 1, the non-dominated sort).
 //
-// Dominance needs f_i0 <= f_j0, so when every point of a row block has a
-// smaller f_0 than every point of a column block only "row dominates column"
-// can hold, and that half of the test is done with m - 1 subtractions.  A
-// counting sort into SORT_NB buckets of f_0 over [min f_0, max f_0] (a
-// monotone key) makes such disjoint block pairs the common case.  Ties and
-// order inside a bucket do not matter: every pair is still tested exactly.
-//   k_sort_range    min / max of f_0 (order-preserving atomics)
-//   k_sort_hist     bucket histogram; the last CTA turns it into offsets
-//   k_sort_scatter  perm[pos] = i, skey[pos] = bucket, Fp = F in bucket order
+// For m <= 10 every objective q is cut into L = 2^lbits levels by L - 1
+// thresholds near its quantiles (from a histogram of the selection's own
+// values), and a point's key interleaves the bits of its m levels from the
+// top bit down (Morton order), truncated to kbits.  A point i can dominate
+// j only if f_iq <= f_jq for every q, so only if every level of i is at most
+// the level of j, and then every prefix of the interleaved bits of i is at
+// most that of j: dominators never have a larger key, equal vectors have
+// equal keys, and points with nearby keys are close in every objective, so
+// 32-point blocks of the key order have small bounding boxes that let the
+// dominance build rule out most block pairs.  Any thresholds would be
+// correct; quantiles balance the levels.  For m > 10 the key is one of 4,096
+// buckets of f_0.  A counting sort into the 2^kbits keys orders the points;
+// ties and order inside a key do not matter: every pair that can dominate is
+// still tested exactly.
+//   k_sort_range    per-objective min / max (order-preserving atomics)
+//   k_sort_thr      per-objective histograms over [min, max] in the
+//                   order-preserving integer space (about equal steps of
+//                   relative size); the last CTA turns them into thresholds
+//   k_sort_hist     key histogram; the last CTA turns it into offsets
+//   k_sort_scatter  perm[pos] = i, skey[pos] = key, Fp = F in key order
 //                   with -0.0 written as +0.0
 #include "kernels.cuh"
 
@@ -17,84 +28,202 @@ namespace {
 
 constexpr int SB = 1024;
 
-__device__ __forceinline__ int bucket_of(float f, float lo, float scale)
+__device__ __forceinline__ int bucket_of(float f, float lo, float scale, int nb)
 {
     float t = (f - lo) * scale;
     int b = (int)t;
     if (!(t >= 0.0f)) b = 0;
-    return b > SORT_NB - 1 ? SORT_NB - 1 : b;
+    return b > nb - 1 ? nb - 1 : b;
 }
 
-__device__ __forceinline__ void range_of(const Ctrl* c, float& lo, float& scale)
+__device__ __forceinline__ void range_of(const Ctrl* c, int nb, float& lo, float& scale)
 {
     lo = ord2f(c->f0lo);
     const float hi = ord2f(c->f0hi);
     const float span = hi - lo;
-    scale = (span > 0.0f && span < 3.0e38f) ? (float)SORT_NB / span : 0.0f;
+    scale = (span > 0.0f && span < 3.0e38f) ? (float)nb / span : 0.0f;
 }
 
+// sort key of point i (see the file comment)
+__device__ __forceinline__ uint32_t key_of(const RunView& v, const Ctrl* c, int i)
+{
+    const int m = v.m;
+    const float* f = v.F + (size_t)i * m;
+    if (m > NSGA3_FAST_M) {
+        float lo, scale;
+        range_of(c, SORT_NB, lo, scale);
+        return (uint32_t)bucket_of(f[0] + 0.0f, lo, scale, SORT_NB);
+    }
+    const int lb = v.lbits, nthr = (1 << lb) - 1;
+    uint32_t lev[NSGA3_FAST_M];
+#pragma unroll
+    for (int q = 0; q < NSGA3_FAST_M; ++q) {
+        uint32_t l = 0u;
+        if (q < m) {
+            const float x = f[q];
+            for (int k = 0; k < nthr; ++k) l += x > c->thr[q][k] ? 1u : 0u;
+        }
+        lev[q] = l;
+    }
+    uint32_t key = 0u;
+    for (int b = lb - 1; b >= 0; --b)
+#pragma unroll
+        for (int q = 0; q < NSGA3_FAST_M; ++q)
+            if (q < m) key = (key << 1) | ((lev[q] >> b) & 1u);
+    return key >> (lb * m - v.kbits);
+}
+
+// m <= 10: min / max of every objective; above, of f_0
 __global__ void __launch_bounds__(SB) k_sort_range(RunView v)
 {
-    __shared__ uint32_t smin, smax;
+    __shared__ uint32_t smin[NSGA3_FAST_M], smax[NSGA3_FAST_M];
     Ctrl* c = v.ctrl;
     if (read_status(c)) return;
-    if (threadIdx.x == 0) {
-        smin = 0xffffffffu;
-        smax = 0u;
+    const int m = v.m, mr = m <= NSGA3_FAST_M ? m : 1;
+    if (threadIdx.x < NSGA3_FAST_M) {
+        smin[threadIdx.x] = 0xffffffffu;
+        smax[threadIdx.x] = 0u;
     }
     __syncthreads();
-    uint32_t lo = 0xffffffffu, hi = 0u;
+    uint32_t lo[NSGA3_FAST_M], hi[NSGA3_FAST_M];
+#pragma unroll
+    for (int q = 0; q < NSGA3_FAST_M; ++q) {
+        lo[q] = 0xffffffffu;
+        hi[q] = 0u;
+    }
     for (int i = blockIdx.x * SB + threadIdx.x; i < v.n2; i += gridDim.x * SB) {
-        const uint32_t o = f2ord(v.F[(size_t)i * v.m] + 0.0f);
-        lo = min(lo, o);
-        hi = max(hi, o);
+        const float* f = v.F + (size_t)i * m;
+#pragma unroll
+        for (int q = 0; q < NSGA3_FAST_M; ++q)
+            if (q < mr) {
+                const uint32_t o = f2ord(f[q] + 0.0f);
+                lo[q] = min(lo[q], o);
+                hi[q] = max(hi[q], o);
+            }
     }
 #pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, s));
-        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, s));
+    for (int q = 0; q < NSGA3_FAST_M; ++q)
+        if (q < mr) {
+            const uint32_t a = __reduce_min_sync(0xffffffffu, lo[q]), b = __reduce_max_sync(0xffffffffu, hi[q]);
+            if (lane_id() == 0) {
+                atomicMin(&smin[q], a);
+                atomicMax(&smax[q], b);
+            }
+        }
+    __syncthreads();
+    if (threadIdx.x < mr) {
+        atomicMin(&c->omin[threadIdx.x], smin[threadIdx.x]);
+        atomicMax(&c->omax[threadIdx.x], smax[threadIdx.x]);
+        if (threadIdx.x == 0) {
+            atomicMin(&c->f0lo, smin[0]);
+            atomicMax(&c->f0hi, smax[0]);
+        }
     }
-    if (lane_id() == 0) {
-        atomicMin(&smin, lo);
-        atomicMax(&smax, hi);
+}
+
+// bin of an order-preserving value o in [omin, omin + span) (span >= 1)
+__device__ __forceinline__ int qbin(uint32_t o, uint32_t omin, unsigned long long span)
+{
+    return (int)(((unsigned long long)(o - omin) * SORT_QB) / span);
+}
+
+// m <= 10: level thresholds.  Bin e of objective q holds the values whose
+// order-preserving codes o satisfy floor((o - omin) QB / span) = e; the
+// threshold of level k + 1 is the largest value of the first bin whose
+// cumulative count reaches (k + 1) n2 / L.
+__global__ void __launch_bounds__(SB) k_sort_thr(RunView v)
+{
+    __shared__ int h[NSGA3_FAST_M * SORT_QB];
+    __shared__ unsigned ticket;
+    Ctrl* c = v.ctrl;
+    if (read_status(c)) return;
+    const int m = v.m;
+    for (int b = threadIdx.x; b < m * SORT_QB; b += SB) h[b] = 0;
+    __syncthreads();
+    uint32_t omin[NSGA3_FAST_M];
+    unsigned long long span[NSGA3_FAST_M];
+#pragma unroll
+    for (int q = 0; q < NSGA3_FAST_M; ++q) {
+        omin[q] = q < m ? c->omin[q] : 0u;
+        span[q] = q < m ? (unsigned long long)(c->omax[q] - omin[q]) + 1ull : 1ull;
+    }
+    for (int i = blockIdx.x * SB + threadIdx.x; i < v.n2; i += gridDim.x * SB) {
+        const float* f = v.F + (size_t)i * m;
+#pragma unroll
+        for (int q = 0; q < NSGA3_FAST_M; ++q)
+            if (q < m) atomicAdd(&h[q * SORT_QB + qbin(f2ord(f[q] + 0.0f), omin[q], span[q])], 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicMin(&c->f0lo, smin);
-        atomicMax(&c->f0hi, smax);
+    for (int b = threadIdx.x; b < m * SORT_QB; b += SB)
+        if (h[b]) atomicAdd(&v.qhist[b], h[b]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) ticket = atomicAdd(&c->thr_done, 1u);
+    __syncthreads();
+    if (ticket != gridDim.x - 1) return;
+    __threadfence();
+    // last CTA: warp q scans objective q's bins (32 per lane)
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    if (warp >= m) return;
+    const int q = warp, L = 1 << v.lbits;
+    constexpr int PER = SORT_QB / 32;
+    int loc[PER];
+    int s = 0;
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+        loc[t] = __ldcg(&v.qhist[q * SORT_QB + lane * PER + t]);
+        s += loc[t];
+    }
+    int inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const int before = inc - s;
+    for (int k = 0; k + 1 < L; ++k) {
+        const long long target = ((long long)(k + 1) * v.n2 + L - 1) / L;  // ceil((k + 1) n2 / L)
+        int e = -1;
+        if (before < target && target <= inc) {
+            int run = before;
+            for (int t = 0; t < PER; ++t) {
+                run += loc[t];
+                if (run >= target) {
+                    e = lane * PER + t;
+                    break;
+                }
+            }
+        }
+        const unsigned who = __ballot_sync(0xffffffffu, e >= 0);
+        const int eb = __shfl_sync(0xffffffffu, e, who ? __ffs(who) - 1 : 0);
+        if (lane == 0) {
+            // largest code of bin eb: omin + ceil((eb + 1) span / QB) - 1
+            const unsigned long long hiw = ((unsigned long long)(eb + 1) * span[q] + SORT_QB - 1) / SORT_QB;
+            c->thr[q][k] = who ? ord2f(omin[q] + (uint32_t)(hiw - 1ull)) : ord2f(omin[q] + (uint32_t)(span[q] - 1ull));
+        }
     }
 }
 
 __global__ void __launch_bounds__(SB) k_sort_hist(RunView v)
 {
-    __shared__ int h[SORT_NB];
     __shared__ int scratch[40];
     __shared__ unsigned ticket;
     Ctrl* c = v.ctrl;
     if (read_status(c)) return;
-    for (int b = threadIdx.x; b < SORT_NB; b += SB) h[b] = 0;
-    __syncthreads();
-    float lo, scale;
-    range_of(c, lo, scale);
     for (int i = blockIdx.x * SB + threadIdx.x; i < v.n2; i += gridDim.x * SB)
-        atomicAdd(&h[bucket_of(v.F[(size_t)i * v.m] + 0.0f, lo, scale)], 1);
-    __syncthreads();
-    for (int b = threadIdx.x; b < SORT_NB; b += SB)
-        if (h[b]) atomicAdd(&v.bcnt[b], h[b]);
+        atomicAdd(&v.bcnt[key_of(v, c, i)], 1);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) ticket = atomicAdd(&c->sort_done, 1u);
     __syncthreads();
     if (ticket != gridDim.x - 1) return;
-    // last CTA: exclusive scan of the counts (SORT_NB / SB per thread)
+    // last CTA: exclusive scan of the counts, a contiguous run per thread
     __threadfence();
-    constexpr int PER = SORT_NB / SB;
-    int loc[PER];
+    const int nk = 1 << v.kbits;
+    const int per = (nk + SB - 1) / SB;
+    const int b0 = min(nk, (int)threadIdx.x * per), b1 = min(nk, b0 + per);
     int s = 0;
-    for (int t = 0; t < PER; ++t) {
-        loc[t] = __ldcg(&v.bcnt[threadIdx.x * PER + t]);
-        s += loc[t];
-    }
+    for (int b = b0; b < b1; ++b) s += __ldcg(&v.bcnt[b]);
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     int inc = s;
 #pragma unroll
@@ -116,9 +245,10 @@ __global__ void __launch_bounds__(SB) k_sort_hist(RunView v)
     }
     __syncthreads();
     int run = scratch[warp] + inc - s;
-    for (int t = 0; t < PER; ++t) {
-        v.bcnt[threadIdx.x * PER + t] = run;
-        run += loc[t];
+    for (int b = b0; b < b1; ++b) {
+        const int cnt = __ldcg(&v.bcnt[b]);
+        v.bcnt[b] = run;
+        run += cnt;
     }
     if (threadIdx.x == 0) c->sort_done = 0u;
 }
@@ -129,10 +259,8 @@ __global__ void __launch_bounds__(256) k_sort_scatter(RunView v)
     if (read_status(c)) return;
     const int i = blockIdx.x * 256 + threadIdx.x;
     if (i >= v.n2) return;
-    float lo, scale;
-    range_of(c, lo, scale);
     const int m = v.m;
-    const int b = bucket_of(v.F[(size_t)i * m] + 0.0f, lo, scale);
+    const uint32_t b = key_of(v, c, i);
     const int pos = atomicAdd(&v.bcnt[b], 1);
     v.perm[pos] = i;
     v.skey[pos] = (uint32_t)b;
@@ -150,9 +278,7 @@ __global__ void __launch_bounds__(256) k_sort_scatter_rows(RunView v)
     const int lane = lane_id(), m = v.m;
     int pos = 0;
     if (lane == 0) {
-        float lo, scale;
-        range_of(c, lo, scale);
-        const int b = bucket_of(v.F[(size_t)i * m] + 0.0f, lo, scale);
+        const uint32_t b = key_of(v, c, i);
         pos = atomicAdd(&v.bcnt[b], 1);
         v.perm[pos] = i;
         v.skey[pos] = (uint32_t)b;
@@ -170,6 +296,11 @@ cudaError_t launch_sort(const RunView& v, int num_sms, cudaStream_t s)
     k_sort_range<<<blocks, SB, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (v.m <= NSGA3_FAST_M) {
+        k_sort_thr<<<blocks, SB, 0, s>>>(v);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     k_sort_hist<<<blocks, SB, 0, s>>>(v);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -117,4 +117,6 @@ def test_streaming_workspace_has_no_matrix(lib):
     full = n.workspace_bytes(10, 200, N, 3, n.default_opts(p2=2))
     stream = n.workspace_bytes(10, 200, N, 3, n.default_opts(p2=2, streaming=1))
     ld = -(-2 * N // 256) * 256
-    assert full - stream == ld * ld // 8 - 256
+    NW = ld // 32
+    bitmap = -(-NW * (-(-NW // 8)) // 256) * 256  # one bit per 32 x 32 block of the matrix
+    assert full - stream == ld * ld // 8 - 256 + bitmap
