@@ -77,6 +77,10 @@ struct Ctrl {
     int32_t nlarge;          // references whose partial take needs the block-wide select
     uint32_t peel_rows;      // dominator word-rows in the peel's row lists, all passes
     uint32_t npath;          // NPATH_* bits: capacity paths the niching kernels took
+    int32_t ntile;           // tiles listed in tlist by k_tile_plan
+    unsigned long long domstat[6];  // block pairs of the dominance build by mode (zero, f_0
+                                    // one-direction, row-dom-column, column-dom-row, both),
+                                    // and tiles with nothing to test (m <= 10)
 
     int32_t ncand;           // association candidates written by the scan
     int32_t nslow;           // points sent to the full FP64 association scan
@@ -126,6 +130,7 @@ struct RunView {
     int32_t* srank;    // ld   merged ranks in bucket order (peel)
     int32_t* perm;     // ld   bucket order position -> original index
     uint32_t* skey;    // ld   sort key of each position (0xffffffff for padding)
+    uint32_t* pkey;    // n2   sort key of each point (original order)
     float* Fp;         // ld x m objectives in bucket order, -0.0 as +0.0, NaN padding
     int32_t* bcnt;     // nkeys + 1 key counts, then offsets / cursors
     int kbits;         // bits of a sort key (nkeys = 2^kbits)
@@ -136,6 +141,10 @@ struct RunView {
     uint8_t* dnz;      // NW x NB8 bits: Dom block (I, J) has a nonzero word (m <= 10, matrix);
                        // null: every Dom word is written
     int NB8;           // bytes of dnz per dominator block row = ceil(NW / 8)
+    float* tbox;       // (ld / 256) x 2 M4: per 256-position tile min, then max of each objective
+    uint32_t* tkey;    // (ld / 256) x 2: per tile smallest, largest sort key
+    int32_t* tlist;    // tiles of the dominance build with block pairs to test (k_tile_plan)
+    int num_sms;
     uint32_t* rem;     // NW   not-yet-ranked mask
     uint32_t* front;   // 2 x NW  ping-pong front masks
     uint32_t* chunk_lim;   // ld / NSGA3_PEEL_COLS dominator row blocks a column chunk reads

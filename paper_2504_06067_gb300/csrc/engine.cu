@@ -82,8 +82,8 @@ namespace {
 int select_launches(const nsga3_ctx* ctx)
 {
     const int m = ctx->m;
-    // m <= 10: + the sort's level thresholds and the dominance build's block boxes
-    return 18 + (m > NSGA3_FAST_M ? 5 : 2) + (m > NSGA3_WARP_M ? 1 : 0) + (ctx->v.dom_ks > 1 ? 1 : 0);
+    // m <= 10: + the sort's level thresholds, the dominance build's boxes and tile plan
+    return 18 + (m > NSGA3_FAST_M ? 5 : 3) + (m > NSGA3_WARP_M ? 1 : 0) + (ctx->v.dom_ks > 1 ? 1 : 0);
 }
 // the softmax-simplex objective's dot-product kernel (m > 10)
 int objective_dot_launches(const nsga3_ctx* ctx) { return ctx->m > NSGA3_FAST_M && ctx->v.problem == 0 ? 1 : 0; }
@@ -425,6 +425,7 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     v.NW = NW;
     v.w = w;
     v.M4 = M4;
+    v.num_sms = ctx->num_sms > 0 ? ctx->num_sms : 1;
     v.full_sort = ctx->opts.full_sort ? 1 : 0;
     v.debug_recheck_all = ctx->opts.debug_recheck_all ? 1 : 0;
     v.streaming = ctx->opts.streaming ? 1 : 0;
@@ -466,6 +467,7 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     AL(v.srank, ld);
     AL(v.perm, ld);
     AL(v.skey, ld);
+    AL(v.pkey, n2);
     AL(v.Fp, (size_t)ld * m);
     // sort keys (k_sort.cu): m <= 10 interleaves lbits of level per objective
     // (Morton order), truncated to kbits, about n2 / 2 keys; above, 4,096 f_0 buckets
@@ -486,6 +488,10 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
         AL(v.qhist, (size_t)m * SORT_QB);
         AL(v.bbox, (size_t)NW * 2 * M4);
         AL(v.bkey, (size_t)NW * 2);
+        const size_t T = (size_t)ld / NSGA3_TILE;
+        AL(v.tbox, T * 2 * M4);
+        AL(v.tkey, T * 2);
+        AL(v.tlist, T * (T + 1) / 2);
         if (!v.streaming) AL(v.dnz, (size_t)NW * v.NB8);
     }
     AL(v.rem, NW);
@@ -1191,6 +1197,16 @@ nsga3_status nsga3_get_selection_paths(nsga3_ctx* ctx, uint32_t* paths)
     uint32_t p = 0;
     CK(cudaMemcpy(&p, &ctx->v.ctrl->npath, sizeof p, cudaMemcpyDeviceToHost));
     *paths = p;
+    return NSGA3_OK;
+}
+
+nsga3_status nsga3_get_dominance_stats(nsga3_ctx* ctx, int64_t* stats)
+{
+    if (!ctx || !stats) return fail(ctx, NSGA3_EINVAL, "null argument");
+    CK(cudaDeviceSynchronize());
+    unsigned long long d[6];
+    CK(cudaMemcpy(d, ctx->v.ctrl->domstat, sizeof d, cudaMemcpyDeviceToHost));
+    for (int t = 0; t < 6; ++t) stats[t] = (int64_t)d[t];
     return NSGA3_OK;
 }
 

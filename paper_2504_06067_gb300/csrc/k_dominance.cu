@@ -164,13 +164,15 @@ enum : int {
 
 // Per 32-position block of the key order (k_sort.cu): the smallest and
 // largest value of every objective (NaN padding ignored; NaN for a block of
-// padding only) and the smallest and largest sort key.  One warp per block.
+// padding only) and the smallest and largest sort key; one warp per block,
+// one CTA per 256-position tile, which also records the tile's box and keys.
 __global__ void __launch_bounds__(256) k_block_box(RunView v)
 {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (b >= v.NW) return;
+    __shared__ float slo[8][NSGA3_FAST_M], shi[8][NSGA3_FAST_M];
+    __shared__ uint32_t skmin[8], skmax[8];
     if (read_status(v.ctrl)) return;
-    const int lane = lane_id(), m = v.m, M4 = v.M4;
+    const int lane = lane_id(), warp = threadIdx.x >> 5, m = v.m, M4 = v.M4;
+    const int b = blockIdx.x * 8 + warp;
     const int p = b * 32 + lane;
     float* box = v.bbox + (size_t)b * 2 * M4;
     for (int q = 0; q < m; ++q) {
@@ -183,6 +185,8 @@ __global__ void __launch_bounds__(256) k_block_box(RunView v)
         if (lane == 0) {
             box[q] = lo;
             box[M4 + q] = hi;
+            slo[warp][q] = lo;
+            shi[warp][q] = hi;
         }
     }
     const uint32_t k = v.skey[p];
@@ -190,7 +194,64 @@ __global__ void __launch_bounds__(256) k_block_box(RunView v)
     if (lane == 0) {
         v.bkey[2 * b] = kmin;
         v.bkey[2 * b + 1] = kmax;
+        skmin[warp] = kmin;
+        skmax[warp] = kmax;
     }
+    __syncthreads();
+    if (threadIdx.x < m) {
+        const int q = threadIdx.x;
+        float lo = slo[0][q], hi = shi[0][q];
+        for (int w = 1; w < 8; ++w) {
+            lo = fminf(lo, slo[w][q]);
+            hi = fmaxf(hi, shi[w][q]);
+        }
+        v.tbox[(size_t)blockIdx.x * 2 * M4 + q] = lo;
+        v.tbox[(size_t)blockIdx.x * 2 * M4 + M4 + q] = hi;
+    }
+    if (threadIdx.x == 32) {
+        uint32_t lo = skmin[0], hi = skmax[0];
+        for (int w = 1; w < 8; ++w) {
+            lo = min(lo, skmin[w]);
+            hi = max(hi, skmax[w]);
+        }
+        v.tkey[2 * blockIdx.x] = lo;
+        v.tkey[2 * blockIdx.x + 1] = hi;
+    }
+}
+
+// The tiles (ti <= tj) whose block pairs can hold a dominance go on a list
+// for the dominance build; the rest need no test at all: their bitmap
+// bytes stay zero (k_sel_reset clears the bitmap) and their points gain no
+// dominator.  One thread per tile, the same tests as a block pair's on the
+// tiles' boxes and keys; diagonal tiles are always listed.
+template <int M>
+__global__ void __launch_bounds__(256) k_tile_plan(RunView v)
+{
+    constexpr int M4 = (M + 3) & ~3;
+    const int T = v.ld / NSGA3_TILE;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    Ctrl* c = v.ctrl;
+    if (t >= (long long)T * (T + 1) / 2) return;
+    if (read_status(c)) return;
+    int ti, tj;
+    decode_tile(t, T, ti, tj);
+    bool work = ti == tj;
+    if (!work && tj * NSGA3_TILE < v.n2) {
+        const float* bi = v.tbox + (size_t)ti * 2 * M4;
+        const float* bj = v.tbox + (size_t)tj * 2 * M4;
+        bool fwd = true, bwd = true;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+            fwd = fwd && bi[q] <= bj[M4 + q];
+            bwd = bwd && bj[q] <= bi[M4 + q];
+        }
+        bwd = bwd && !(v.tkey[2 * ti + 1] < v.tkey[2 * tj]);
+        work = fwd || bwd;
+    }
+    if (work)
+        v.tlist[atomicAdd(&c->ntile, 1)] = (int32_t)t;
+    else
+        atomicAdd(&c->domstat[5], 1ull);
 }
 
 // Mode of block pair (ib, jb) from the blocks' boxes and keys (warp-wide:
@@ -233,6 +294,14 @@ __device__ __forceinline__ void put_block(const RunView& v, size_t at, uint32_t 
     if (lane_id() == 0 && nzw) atomicOr(&nzw[byte >> 2], 1u << (8 * (byte & 3) + bit));
 }
 
+// A CTA takes a 256 x 256 tile of the upper block triangle (8 x 8 blocks of
+// 32).  Its warps first decide the tile's block pairs from the boxes and put
+// the ones to test on a shared list, both-way tests first (they cost about
+// twice a one-way test), then take list entries in turn: block pairs differ
+// widely in cost after the pruning, and a warp that runs out of entries
+// leaves the rest to the others instead of idling at the tile's barrier.
+// Per entry the warp's lanes hold the 32 rows' objectives in registers and
+// the columns are broadcast from shared memory.
 template <int M>
 __global__ void __launch_bounds__(256) k_dominance(RunView v)
 {
@@ -243,33 +312,56 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
     __shared__ int rowcnt[NSGA3_TILE];  // dominators found for the tile's row points
     __shared__ int colcnt[NSGA3_TILE];  // ... for its column points
     __shared__ unsigned nzw[4];         // dnz bytes: 0..7 row blocks (I, J), 8..15 column blocks (J, I)
+    __shared__ unsigned mcount[6];      // block pairs of this tile by mode
+    __shared__ unsigned short work[64]; // block pairs to test: (mode << 6) | (row block << 3) | column block
+    __shared__ int nfull, none;         // both-way entries from the front, one-way from the back
     if (read_status(v.ctrl)) return;
+    const int T = v.ld / NSGA3_TILE;
+    const int ntile = *(volatile const int32_t*)&v.ctrl->ntile;
+    // persistent: the CTAs take the listed tiles in turn
+    for (int it = blockIdx.x; it < ntile; it += gridDim.x) {
     rowcnt[threadIdx.x] = 0;
     colcnt[threadIdx.x] = 0;
     if (threadIdx.x < 4) nzw[threadIdx.x] = 0u;
-    const int T = v.ld / NSGA3_TILE;
-    if (threadIdx.x == 0) decode_tile(blockIdx.x, T, s_tile[0], s_tile[1]);
+    if (threadIdx.x < 6) mcount[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) {
+        nfull = 0;
+        none = 0;
+        decode_tile(v.tlist[it], T, s_tile[0], s_tile[1]);
+    }
     __syncthreads();
     const int ti = s_tile[0], tj = s_tile[1];
     const int r0 = ti * NSGA3_TILE, c0 = tj * NSGA3_TILE;
     const int warp = threadIdx.x >> 5, lane = lane_id();
-    // warp = (row pair rp, column half ch): row blocks 2rp, 2rp+1 of the tile
-    // against column blocks 4ch .. 4ch+3; every column load serves two rows
-    const int rp = warp & 3, ch = warp >> 2;
-    const int ib0 = ti * 8 + 2 * rp, ib1 = ib0 + 1;
-    unsigned modes = 0u;  // 4 bits per (column block cbi, row r): bits 8 cbi + 4 r
-    bool work = false;
+    // warp w decides row blocks 2 (w & 3), +1 against column blocks 4 (w >> 2) .. +3
+    {
+        const int rp = warp & 3, ch = warp >> 2;
 #pragma unroll
-    for (int cbi = 0; cbi < 4; ++cbi) {
-        const int jb = tj * 8 + ch * 4 + cbi;
-        const int a = block_pair_mode<M>(v, ib0, jb), b = block_pair_mode<M>(v, ib1, jb);
-        modes |= ((unsigned)a | ((unsigned)b << 4)) << (8 * cbi);
-        work = work || a > BP_ZERO || b > BP_ZERO;
+        for (int cbi = 0; cbi < 4; ++cbi) {
+            const int cb = ch * 4 + cbi;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int ri = 2 * rp + r;
+                const int mode = block_pair_mode<M>(v, ti * 8 + ri, tj * 8 + cb);
+                if (lane == 0) {
+                    if (mode > BP_SKIP) atomicAdd(&mcount[mode - 1], 1u);
+                    const unsigned short e = (unsigned short)((mode << 6) | (ri << 3) | cb);
+                    if (mode == BP_FULL)
+                        work[atomicAdd(&nfull, 1)] = e;
+                    else if (mode > BP_ZERO)
+                        work[63 - atomicAdd(&none, 1)] = e;
+                }
+            }
+        }
     }
-    // a tile without any block pair to test writes no word and stages nothing
-    const bool tile_work = __syncthreads_or(work);
+    __syncthreads();
+    const int nf = nfull, no = none, nwork = nf + no;
+    if (threadIdx.x < 5 && mcount[threadIdx.x])
+        atomicAdd(&v.ctrl->domstat[threadIdx.x], (unsigned long long)mcount[threadIdx.x]);
+
     unsigned* nz = v.dnz ? nzw : nullptr;
-    if (tile_work) {
+    if (nwork > 0) {
+        // a tile without any block pair to test stages nothing
         // Fp holds -0.0 as +0.0, so equal values subtract to +0.0
         for (int e = threadIdx.x; e < NSGA3_TILE * M; e += blockDim.x) {
             int p = e / M, q = e - p * M;
@@ -277,77 +369,54 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
             scol[p * M4 + q] = v.Fp[(size_t)c0 * M + e];
         }
         __syncthreads();
-        float f0[M], f1[M];
+        for (int t = warp; t < nwork; t += 8) {
+            const unsigned e = work[t < nf ? t : 64 - nwork + t];
+            const int mode = e >> 6, ri = (e >> 3) & 7, cb = e & 7;
+            const int ib = ti * 8 + ri, jb = tj * 8 + cb;
+            float fi[M];
 #pragma unroll
-        for (int q = 0; q < M; ++q) {
-            f0[q] = srow[(2 * rp * 32 + lane) * M4 + q];
-            f1[q] = srow[((2 * rp + 1) * 32 + lane) * M4 + q];
-        }
-        int rc0 = 0, rc1 = 0;  // dominators of row points ib0*32+lane, ib1*32+lane in this tile
-        for (int cbi = 0; cbi < 4; ++cbi) {
-            const int cb = ch * 4 + cbi;
-            const int jb = tj * 8 + cb;
-            const int mode0 = (modes >> (8 * cbi)) & 15u, mode1 = (modes >> (8 * cbi + 4)) & 15u;
-            if (mode0 == BP_SKIP && mode1 == BP_SKIP) continue;
+            for (int q = 0; q < M; ++q) fi[q] = srow[(ri * 32 + lane) * M4 + q];
             const float* colp = scol + cb * 32 * M4;
-            if (mode0 == mode1 && (mode0 == BP_FAST0 || mode0 == BP_FASTK)) {
-                // both rows the same one-direction test: one pass over the columns
-                uint32_t acc0, acc1;
-                if (mode0 == BP_FAST0)
-                    block_one_dir<1, M, M4, true>(f0, f1, colp, acc0, acc1);
-                else
-                    block_one_dir<0, M, M4, true>(f0, f1, colp, acc0, acc1);
-                const uint32_t t0 = warp_transpose32(~acc0), t1 = warp_transpose32(~acc1);
-                put_block(v, (size_t)ib0 * v.ld + jb * 32 + lane, t0, nz, 2 * rp, cb);
-                put_block(v, (size_t)ib1 * v.ld + jb * 32 + lane, t1, nz, 2 * rp + 1, cb);
-                const int cc = __popc(t0) + __popc(t1);
-                if (cc) atomicAdd(&colcnt[cb * 32 + lane], cc);
-                continue;
-            }
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int ib = r ? ib1 : ib0;
-                const int mode = r ? mode1 : mode0;
-                if (mode == BP_SKIP || mode == BP_ZERO) continue;
-                const float* fi = r ? f1 : f0;
-                uint32_t dij = 0u, dji = 0u;
-                if (mode == BP_FAST0 || mode == BP_FASTK) {
-                    uint32_t acc, unused;
-                    if (mode == BP_FAST0)
-                        block_one_dir<1, M, M4, false>(fi, fi, colp, acc, unused);
-                    else
-                        block_one_dir<0, M, M4, false>(fi, fi, colp, acc, unused);
-                    dij = ~acc;
-                } else if (mode == BP_FASTR) {
+            uint32_t dij = 0u, dji = 0u;
+            if (mode == BP_FAST0 || mode == BP_FASTK || mode == BP_FASTR) {
+                // One direction only: "no f_iq > f_jq" (or the reverse) decides,
+                // and a NaN padding point would pass it (its differences are
+                // NaN with a clear sign bit), so the bits of padding rows and
+                // columns are masked (the two-way test needs no mask: a NaN
+                // gives the same sign both ways, hence no bit).
+                const int cv = v.n2 - jb * 32;
+                const uint32_t colvalid = cv >= 32 ? 0xffffffffu : (cv > 0 ? (1u << cv) - 1u : 0u);
+                const bool rowvalid = ib * 32 + lane < v.n2;
+                uint32_t acc = 0u, unused;
+                if (mode == BP_FAST0) {
+                    block_one_dir<1, M, M4, false>(fi, fi, colp, acc, unused);
+                    dij = rowvalid ? ~acc & colvalid : 0u;
+                } else if (mode == BP_FASTK) {
+                    block_one_dir<0, M, M4, false>(fi, fi, colp, acc, unused);
+                    dij = rowvalid ? ~acc & colvalid : 0u;
+                } else {
                     // column j dominates row i: no f_jq > f_iq (the vectors differ)
-                    uint32_t acc = 0u;
 #pragma unroll 4
                     for (int k = 31; k >= 0; --k) {
                         const float* fj = colp + k * M4;
                         acc = __funnelshift_l(any_greater<0, M>(fi, fj), acc, 1);
                     }
-                    dji = ~acc;
-                } else {
-                    block_full<M, M4>(fi, colp, dij, dji);
+                    dji = rowvalid ? ~acc & colvalid : 0u;
                 }
-                // column i = ib*32 + lane, dominators j in block jb: Dom block (jb, ib)
-                const int ri = 2 * rp + r;
-                if (jb != ib) {
-                    put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, 8 + cb, ri);
-                    const uint32_t t = warp_transpose32(dij);
-                    put_block(v, (size_t)ib * v.ld + jb * 32 + lane, t, nz, ri, cb);
-                    if (t) atomicAdd(&colcnt[cb * 32 + lane], __popc(t));
-                } else {
-                    put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, ri, cb);
-                }
-                if (r)
-                    rc1 += __popc(dji);
-                else
-                    rc0 += __popc(dji);
+            } else {
+                block_full<M, M4>(fi, colp, dij, dji);
             }
+            // column i = ib*32 + lane, dominators j in block jb: Dom block (jb, ib)
+            if (jb != ib) {
+                put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, 8 + cb, ri);
+                const uint32_t tr = warp_transpose32(dij);
+                put_block(v, (size_t)ib * v.ld + jb * 32 + lane, tr, nz, ri, cb);
+                if (tr) atomicAdd(&colcnt[cb * 32 + lane], __popc(tr));
+            } else {
+                put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, ri, cb);
+            }
+            if (dji) atomicAdd(&rowcnt[ri * 32 + lane], __popc(dji));
         }
-        if (rc0) atomicAdd(&rowcnt[2 * rp * 32 + lane], rc0);
-        if (rc1) atomicAdd(&rowcnt[(2 * rp + 1) * 32 + lane], rc1);
     }
     __syncthreads();
     const int t = threadIdx.x;
@@ -363,10 +432,13 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
             v.dnz[(size_t)(tj * 8 + (t - 8)) * v.NB8 + ti] = nzb[t];
         }
     }
-    if (!tile_work) return;
-    // dominator counts of the peel's first pass: one global add per point of the tile
-    if (rowcnt[t]) atomicAdd(&v.cnt[r0 + t], rowcnt[t]);
-    if (colcnt[t]) atomicAdd(&v.cnt[c0 + t], colcnt[t]);
+    if (nwork > 0) {
+        // dominator counts of the peel's first pass: one global add per point of the tile
+        if (rowcnt[t]) atomicAdd(&v.cnt[r0 + t], rowcnt[t]);
+        if (colcnt[t]) atomicAdd(&v.cnt[c0 + t], colcnt[t]);
+    }
+    __syncthreads();  // the shared arrays are reset for the next tile
+    }
 }
 
 // m > NSGA3_FAST_M: the objectives are taken in chunks of MC (zero-padded:
@@ -570,10 +642,16 @@ cudaError_t launch_dom_m(const RunView& v, cudaStream_t s)
     long long T = v.ld / NSGA3_TILE;
     long long tiles = T * (T + 1) / 2;
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_block_box<<<(unsigned)(((long long)v.NW * 32 + 255) / 256), 256, 0, s>>>(v);
+    k_block_box<<<(unsigned)T, 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_dominance<M><<<(unsigned)tiles, 256, 0, s>>>(v);
+    k_tile_plan<M><<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(v);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // persistent CTAs over the listed tiles (four resident per SM)
+    long long grid = 4LL * v.num_sms;
+    if (grid > tiles) grid = tiles;
+    k_dominance<M><<<(unsigned)grid, 256, 0, s>>>(v);
     return cudaGetLastError();
 }
 

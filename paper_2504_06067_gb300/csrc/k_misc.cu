@@ -17,6 +17,12 @@ __global__ void k_sel_reset(RunView v)
     for (int b = tid; b <= (1 << v.kbits); b += stride) v.bcnt[b] = 0;
     if (v.qhist)
         for (int b = tid; b < v.m * SORT_QB; b += stride) v.qhist[b] = 0;
+    if (v.dnz) {
+        // the block bitmap starts empty: only tiles with block pairs to test write bytes
+        const long long nb = (long long)v.NW * v.NB8;  // 8 T^2 bytes, T = ld / 256
+        uint2* z = reinterpret_cast<uint2*>(v.dnz);
+        for (long long e = tid; e < nb / 8; e += stride) z[e] = make_uint2(0u, 0u);
+    }
     for (int wd = tid; wd < v.NW; wd += stride) {
         const int lo = wd * 32;
         uint32_t m = 0u;
@@ -51,6 +57,8 @@ __global__ void k_sel_reset(RunView v)
         c->nsel = 0;
         c->nlarge = 0;
         c->npath = 0u;
+        c->ntile = 0;
+        for (int t = 0; t < 6; ++t) c->domstat[t] = 0ull;
         c->peel_rows = 0u;
         c->ncand = 0;
         c->nslow = 0;

@@ -99,6 +99,7 @@ _SIGS = {
     "nsga3_get_selection_info": (_I, [_CTX, _P]),
     "nsga3_get_normalization": (_I, [_CTX, _P, _P, _P]),
     "nsga3_get_selection_paths": (_I, [_CTX, C.POINTER(C.c_uint32)]),
+    "nsga3_get_dominance_stats": (_I, [_CTX, _P]),
     "nsga3_select_smallest_probe": (_I, [_P, _I, _I, _P, _P, _P]),
     "nsga3_issue_probe": (_I, [_I, _I, _I, C.POINTER(C.c_double), C.POINTER(C.c_float), _P, _P]),
     "nsga3_get_association": (_I, [_CTX, _P, _P]),
