@@ -330,9 +330,18 @@ __device__ __forceinline__ void g_add(float xv, float& sh, float& sl)
 // per pair; each lane keeps its children's first m - 1 variables and its
 // float-float partial sums of g while it writes the children, then the warp
 // reduces g, lanes 0..m-1 (child 0) and 16..16+m-1 (child 1) form
-// a_j = sum_e W_je x_e (FP64, left to right, x_e by shuffle) and exp(a_j),
-// every lane adds e_0..e_{m-1} in order, and lane j writes
-// f_j = (1 + g) e_j / den rounded to FP32.  The children are never read back.
+// a_j = sum_e W_je x_e and e_j = exp(a_j), every lane adds e_0..e_{m-1} in
+// order, and lane j writes f_j = (1 + g) e_j / den rounded to FP32.  The
+// children are never read back.
+//
+// The arithmetic is FP32 with error-free transformations instead of FP64
+// (1/64 of the FP32 rate on GB300): a_j as a compensated dot product
+// (TwoProduct by FMA, TwoSum; Ogita, Rump and Oishi's Dot2) a_hi + a_lo;
+// e_j = expf(a_hi) (1 + a_lo), so the rounding of a never reaches the
+// exponential (an absolute error of a becomes a relative error of e_j);
+// den and 1 + g as float-float sums; one correctly rounded division.  The
+// result is within about 4 ulp (2.4e-7) of (1 + g) e_j / den: expf's 2 ulp,
+// the division's and the last product's half ulp.
 template <int M>
 __global__ void __launch_bounds__(256) k_vary_eval(RunView v)
 {
@@ -372,24 +381,46 @@ __global__ void __launch_bounds__(256) k_vary_eval(RunView v)
     }
     const int j = lane & 15;
     const bool second = lane >= 16;
-    double a = 0.0;
+    float ah = 0.0f, al = 0.0f;
 #pragma unroll
     for (int e = 0; e < K; ++e) {
         const float xe0 = __shfl_sync(0xffffffffu, xk0, e);
         const float xe1 = __shfl_sync(0xffffffffu, xk1, e);
-        if (j < M) a = __dadd_rn(a, __dmul_rn((double)v.Wobj[j * K + e], (double)(second ? xe1 : xe0)));
+        if (j < M) {
+            const float w = v.Wobj[j * K + e], x = second ? xe1 : xe0;
+            const float p = __fmul_rn(w, x);
+            const float pe = __fmaf_rn(w, x, -p);
+            float s1, e1;
+            two_sum(ah, p, s1, e1);
+            ah = s1;
+            al = al + (e1 + pe);
+        }
     }
-    const double ex = j < M ? exp(a) : 0.0;
-    double den0 = 0.0, den1 = 0.0;
+    float ex = 0.0f;
+    if (j < M) {
+        const float E = expf(ah);
+        ex = __fmaf_rn(E, al, E);
+    }
+    float dh0 = 0.0f, dl0 = 0.0f, dh1 = 0.0f, dl1 = 0.0f;
 #pragma unroll
     for (int t = 0; t < M; ++t) {
-        den0 = __dadd_rn(den0, __shfl_sync(0xffffffffu, ex, t));
-        den1 = __dadd_rn(den1, __shfl_sync(0xffffffffu, ex, 16 + t));
+        float s1, e1;
+        two_sum(dh0, __shfl_sync(0xffffffffu, ex, t), s1, e1);
+        dh0 = s1;
+        dl0 += e1;
+        two_sum(dh1, __shfl_sync(0xffffffffu, ex, 16 + t), s1, e1);
+        dh1 = s1;
+        dl1 += e1;
     }
     if (j < M) {
-        const double g = second ? __dadd_rn((double)gh1, (double)gl1) : __dadd_rn((double)gh0, (double)gl0);
-        const double f = __dmul_rn(__dadd_rn(1.0, g), __ddiv_rn(ex, second ? den1 : den0));
-        v.F[(size_t)(N + 2 * q + (second ? 1 : 0)) * M + j] = __double2float_rn(f);
+        const float dh = second ? dh1 : dh0, dl = second ? dl1 : dl0;
+        float r = __fdiv_rn(ex, dh);
+        r = __fmaf_rn(-r, __fdiv_rn(dl, dh), r);  // e / (dh + dl)
+        const float gh = second ? gh1 : gh0, gl = second ? gl1 : gl0;
+        float Gh, Ge;
+        two_sum(1.0f, gh, Gh, Ge);
+        const float Gl = Ge + gl;  // 1 + g = Gh + Gl
+        v.F[(size_t)(N + 2 * q + (second ? 1 : 0)) * M + j] = __fmaf_rn(r, Gh, r * Gl);
     }
 }
 
