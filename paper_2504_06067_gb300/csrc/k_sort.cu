@@ -15,11 +15,16 @@
 // buckets of f_0.  A counting sort into the 2^kbits keys orders the points;
 // ties and order inside a key do not matter: every pair that can dominate is
 // still tested exactly.
-//   k_sort_range    per-objective min / max (order-preserving atomics)
-//   k_sort_thr      per-objective histograms over [min, max] in the
-//                   order-preserving integer space (about equal steps of
+// The thresholds (and, for m > 10, the f_0 range of the buckets) come from a
+// fixed sample of at most 8,192 points, every (n2 / 8,192)-th: they only
+// steer how well the blocks prune, and a value outside the sample's range
+// still gets a monotone key (levels count thresholds, buckets are clamped).
+//   k_sort_range    per-objective min / max of the sample (order-preserving atomics)
+//   k_sort_thr      per-objective histograms of the sample over [min, max] in
+//                   the order-preserving integer space (about equal steps of
 //                   relative size); the last CTA turns them into thresholds
-//   k_sort_hist     key histogram; the last CTA turns it into offsets
+//   k_sort_hist     every point's key (kept in pkey) and the key histogram;
+//                   the last CTA turns it into offsets
 //   k_sort_scatter  perm[pos] = i, skey[pos] = key, Fp = F in key order
 //                   with -0.0 written as +0.0
 #include "kernels.cuh"
@@ -27,6 +32,10 @@
 namespace {
 
 constexpr int SB = 1024;
+constexpr int SAMPLE = 8192;  // points that set the thresholds and the f_0 range
+
+// stride of the threshold sample
+__device__ __forceinline__ int sample_stride(int n2) { return n2 > SAMPLE ? (n2 + SAMPLE - 1) / SAMPLE : 1; }
 
 __device__ __forceinline__ int bucket_of(float f, float lo, float scale, int nb)
 {
@@ -44,8 +53,9 @@ __device__ __forceinline__ void range_of(const Ctrl* c, int nb, float& lo, float
     scale = (span > 0.0f && span < 3.0e38f) ? (float)nb / span : 0.0f;
 }
 
-// sort key of point i (see the file comment)
-__device__ __forceinline__ uint32_t key_of(const RunView& v, const Ctrl* c, int i)
+// sort key of point i (see the file comment); thr: the level thresholds
+// (m <= 10), staged by the caller
+__device__ __forceinline__ uint32_t key_of(const RunView& v, const Ctrl* c, const float (*thr)[SORT_LMAX], int i)
 {
     const int m = v.m;
     const float* f = v.F + (size_t)i * m;
@@ -61,7 +71,7 @@ __device__ __forceinline__ uint32_t key_of(const RunView& v, const Ctrl* c, int 
         uint32_t l = 0u;
         if (q < m) {
             const float x = f[q];
-            for (int k = 0; k < nthr; ++k) l += x > c->thr[q][k] ? 1u : 0u;
+            for (int k = 0; k < nthr; ++k) l += x > thr[q][k] ? 1u : 0u;
         }
         lev[q] = l;
     }
@@ -91,7 +101,8 @@ __global__ void __launch_bounds__(SB) k_sort_range(RunView v)
         lo[q] = 0xffffffffu;
         hi[q] = 0u;
     }
-    for (int i = blockIdx.x * SB + threadIdx.x; i < v.n2; i += gridDim.x * SB) {
+    const int st = sample_stride(v.n2);
+    for (int i = (blockIdx.x * SB + threadIdx.x) * st; i < v.n2; i += gridDim.x * SB * st) {
         const float* f = v.F + (size_t)i * m;
 #pragma unroll
         for (int q = 0; q < NSGA3_FAST_M; ++q)
@@ -147,7 +158,8 @@ __global__ void __launch_bounds__(SB) k_sort_thr(RunView v)
         omin[q] = q < m ? c->omin[q] : 0u;
         span[q] = q < m ? (unsigned long long)(c->omax[q] - omin[q]) + 1ull : 1ull;
     }
-    for (int i = blockIdx.x * SB + threadIdx.x; i < v.n2; i += gridDim.x * SB) {
+    const int st = sample_stride(v.n2);
+    for (int i = (blockIdx.x * SB + threadIdx.x) * st; i < v.n2; i += gridDim.x * SB * st) {
         const float* f = v.F + (size_t)i * m;
 #pragma unroll
         for (int q = 0; q < NSGA3_FAST_M; ++q)
@@ -181,8 +193,9 @@ __global__ void __launch_bounds__(SB) k_sort_thr(RunView v)
         if (lane >= o) inc += y;
     }
     const int before = inc - s;
+    const int ns = (v.n2 + sample_stride(v.n2) - 1) / sample_stride(v.n2);  // points sampled
     for (int k = 0; k + 1 < L; ++k) {
-        const long long target = ((long long)(k + 1) * v.n2 + L - 1) / L;  // ceil((k + 1) n2 / L)
+        const long long target = ((long long)(k + 1) * ns + L - 1) / L;  // ceil((k + 1) ns / L)
         int e = -1;
         if (before < target && target <= inc) {
             int run = before;
@@ -208,10 +221,17 @@ __global__ void __launch_bounds__(SB) k_sort_hist(RunView v)
 {
     __shared__ int scratch[40];
     __shared__ unsigned ticket;
+    __shared__ float thr[NSGA3_FAST_M][SORT_LMAX];
     Ctrl* c = v.ctrl;
     if (read_status(c)) return;
-    for (int i = blockIdx.x * SB + threadIdx.x; i < v.n2; i += gridDim.x * SB)
-        atomicAdd(&v.bcnt[key_of(v, c, i)], 1);
+    if (threadIdx.x < NSGA3_FAST_M * SORT_LMAX)
+        thr[threadIdx.x / SORT_LMAX][threadIdx.x % SORT_LMAX] = c->thr[threadIdx.x / SORT_LMAX][threadIdx.x % SORT_LMAX];
+    __syncthreads();
+    for (int i = blockIdx.x * SB + threadIdx.x; i < v.n2; i += gridDim.x * SB) {
+        const uint32_t key = key_of(v, c, thr, i);
+        v.pkey[i] = key;
+        atomicAdd(&v.bcnt[key], 1);
+    }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) ticket = atomicAdd(&c->sort_done, 1u);
@@ -219,11 +239,14 @@ __global__ void __launch_bounds__(SB) k_sort_hist(RunView v)
     if (ticket != gridDim.x - 1) return;
     // last CTA: exclusive scan of the counts, a contiguous run per thread
     __threadfence();
-    const int nk = 1 << v.kbits;
-    const int per = (nk + SB - 1) / SB;
+    const int nk = 1 << v.kbits;  // >= 256: a multiple of 4
+    const int per = ((nk + SB - 1) / SB + 3) & ~3;
     const int b0 = min(nk, (int)threadIdx.x * per), b1 = min(nk, b0 + per);
     int s = 0;
-    for (int b = b0; b < b1; ++b) s += __ldcg(&v.bcnt[b]);
+    for (int b = b0; b < b1; b += 4) {
+        const int4 x = __ldcg(reinterpret_cast<const int4*>(v.bcnt + b));
+        s += x.x + x.y + x.z + x.w;
+    }
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     int inc = s;
 #pragma unroll
@@ -245,10 +268,15 @@ __global__ void __launch_bounds__(SB) k_sort_hist(RunView v)
     }
     __syncthreads();
     int run = scratch[warp] + inc - s;
-    for (int b = b0; b < b1; ++b) {
-        const int cnt = __ldcg(&v.bcnt[b]);
-        v.bcnt[b] = run;
-        run += cnt;
+    for (int b = b0; b < b1; b += 4) {
+        const int4 x = __ldcg(reinterpret_cast<const int4*>(v.bcnt + b));
+        int4 y;
+        y.x = run;
+        y.y = run + x.x;
+        y.z = y.y + x.y;
+        y.w = y.z + x.z;
+        run = y.w + x.w;
+        *reinterpret_cast<int4*>(v.bcnt + b) = y;
     }
     if (threadIdx.x == 0) c->sort_done = 0u;
 }
@@ -260,7 +288,7 @@ __global__ void __launch_bounds__(256) k_sort_scatter(RunView v)
     const int i = blockIdx.x * 256 + threadIdx.x;
     if (i >= v.n2) return;
     const int m = v.m;
-    const uint32_t b = key_of(v, c, i);
+    const uint32_t b = v.pkey[i];
     const int pos = atomicAdd(&v.bcnt[b], 1);
     v.perm[pos] = i;
     v.skey[pos] = (uint32_t)b;
@@ -278,7 +306,7 @@ __global__ void __launch_bounds__(256) k_sort_scatter_rows(RunView v)
     const int lane = lane_id(), m = v.m;
     int pos = 0;
     if (lane == 0) {
-        const uint32_t b = key_of(v, c, i);
+        const uint32_t b = v.pkey[i];
         pos = atomicAdd(&v.bcnt[b], 1);
         v.perm[pos] = i;
         v.skey[pos] = (uint32_t)b;
