@@ -59,8 +59,13 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=["headline"] + sorted(WORKLOADS) +
-                   ["batched", "served", "sweep", "popsweep", "select"], default="headline")
+                   ["batched", "served", "sweep", "popsweep", "select", "custom"], default="headline")
     p.add_argument("--runs", type=int, default=64, help="batched: independent runs")
+    p.add_argument("--m", type=int, default=10, help="custom: objectives")
+    p.add_argument("--N", type=int, default=30000, help="custom: population")
+    p.add_argument("--d", type=int, default=200, help="custom: variables")
+    p.add_argument("--p1", type=int, default=3, help="custom: Das-Dennis divisions")
+    p.add_argument("--p2", type=int, default=2, help="custom: inner-layer divisions (0: one layer)")
     p.add_argument("--sweep-m", type=str, default=None,
                    help="sweep / popsweep: comma-separated subset of m (or of N)")
     p.add_argument("--requests", type=int, default=None, help="served: requests of the stream")
@@ -279,6 +284,8 @@ def plain_measure(n, torch, cfg, K, warmup, stream, flush, seed, events, e2e_ste
         ok(n.nsga3_sync(ctx, sh))
         dom_ms = peel_ms = 0.0
         peel_rows = passes = niche_steps = n_launch = 0
+        dstat = (C.c_int64 * 6)()
+        dsum = [0] * 6
         step_ms = []
         barrier(dist)
         torch.cuda.synchronize()
@@ -297,6 +304,9 @@ def plain_measure(n, torch, cfg, K, warmup, stream, flush, seed, events, e2e_ste
                 peel_ms += phases[3]
             ok(n.nsga3_get_selection_info(ctx, info))
             ok(n.nsga3_last_launches(ctx, C.byref(launches)))
+            ok(n.nsga3_get_dominance_stats(ctx, dstat))
+            for t in range(6):
+                dsum[t] += dstat[t]
             passes += info[6]
             peel_rows += info[12]
             n_launch += launches.value
@@ -312,6 +322,7 @@ def plain_measure(n, torch, cfg, K, warmup, stream, flush, seed, events, e2e_ste
         out = {"value": value, "gens_per_s": world * K / total_s_max, "ms_per_step": total_s_max * 1e3 / K,
                "steps": K, "peel_passes_per_step": passes / K, "peel_rows": peel_rows,
                "niching_steps": niche_steps, "gpu_launches": n_launch,
+               "domstat": [x / K for x in dsum] if cfg.m <= 10 else None,
                "timed_events": "dominance build and peel" if events else "none"}
         if events:
             out["timed_region_ms"] = {"dominance": dom_ms / K, "peel": peel_ms / K}
@@ -361,14 +372,24 @@ def issue_probe(n, torch, stream):
             "per_sm_per_clock": (rate / NUM_SMS / (clocks["sm_mhz"] * 1e6)) if clocks.get("sm_mhz") else None}
 
 
-def roofline_of(cfg, avg_ms, peel_rows_per_step, probe, peaks, peak_kind):
+def roofline_of(cfg, avg_ms, peel_rows_per_step, probe, peaks, peak_kind, domstat=None):
     """Roofline of the dominant kernel (the dominance build, bound by issue,
-    or the peel, bound by memory) from its average launch time."""
+    or the peel, bound by memory) from its average launch time.  The
+    dominance build (m <= 10) tests only the block pairs its bounding boxes
+    cannot rule out: the units one launch processes are those pairs (2m
+    compares each, as for every pair), counted by the kernel
+    (nsga3_get_dominance_stats); the rate over all n2(n2-1)/2 pairs is
+    reported beside it."""
     n2 = 2 * cfg.N
     pairs = n2 * (n2 - 1) / 2
     if avg_ms["dominance"] >= avg_ms["peel"]:
-        ops = pairs * 2 * cfg.m  # FP32 compares: all(f_i <= f_j) and all(f_j <= f_i)
-        achieved = ops / (avg_ms["dominance"] / 1e3) / 1e12
+        all_ops = pairs * 2 * cfg.m  # FP32 compares: all(f_i <= f_j) and all(f_j <= f_i)
+        tested = None
+        if domstat is not None and sum(domstat[:5]) > 0:
+            tested = min(pairs, 1024.0 * sum(domstat[1:5]))
+        ops = (tested if tested is not None else pairs) * 2 * cfg.m
+        sec = avg_ms["dominance"] / 1e3
+        achieved = ops / sec / 1e12
         if probe is not None:
             peak = probe["instr_per_s"] / 1e12
             src = "measured: nsga3_issue_probe (the FADD / LOP3 mix of the test, all SMs, no memory)"
@@ -376,12 +397,23 @@ def roofline_of(cfg, avg_ms, peel_rows_per_step, probe, peaks, peak_kind):
             clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
             peak = NUM_SMS * LANES_PER_SM * clk / 1e12
             src = "152 SMs x 128 lanes x %.0f MHz (max SM clock, %s)" % (clk / 1e6, peak_kind)
-        return {"kernel": "k_dominance<%d>" % cfg.m if cfg.m <= 10 else "k_dominance_gen", "bound": "alu",
+        roof = {"kernel": "k_dominance<%d>" % cfg.m if cfg.m <= 10 else "k_dominance_gen", "bound": "alu",
                 "achieved": achieved, "peak": peak, "unit": "T/s (compares; issue slots)",
                 "frac": achieved / peak, "peak_source": src,
-                "algorithmic": "n2(n2-1)/2 pairs x 2m FP32 compares per launch (%.4g)" % ops,
+                "algorithmic": ("tested pairs x 2m FP32 compares per launch (%.4g; 1,024 pairs per "
+                                "tested 32 x 32 block pair)" % ops) if tested is not None else
+                               "n2(n2-1)/2 pairs x 2m FP32 compares per launch (%.4g)" % ops,
                 "launch_ms": avg_ms["dominance"],
                 "traffic": ncu_traffic("k_dominance", cfg.name)}
+        if tested is not None:
+            tot = float(sum(domstat[:5]))
+            roof["pairs_tested_frac"] = tested / pairs
+            roof["block_pairs"] = {"zero": domstat[0] / tot, "one_direction_f0": domstat[1] / tot,
+                                   "row_dom_col": domstat[2] / tot, "col_dom_row": domstat[3] / tot,
+                                   "both": domstat[4] / tot, "tiles_skipped": int(domstat[5])}
+            roof["all_pairs_compare_rate"] = all_ops / sec / 1e12
+            roof["dense_matrix_gbs"] = (n2 * n2 / 8 + n2 * cfg.m * 4) / sec / 1e9
+        return roof
     bytes_read = peel_rows_per_step * 128 * 4.0  # row segments of 128 columns
     achieved = bytes_read / (avg_ms["peel"] / 1e3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
@@ -402,7 +434,7 @@ def plain_record(n, torch, cfg, K, args, stream, flush, seed, events, dist, worl
     avg = res.get("timed_region_ms") or {"dominance": breakdown["dominance"], "peel": breakdown["peel"]}
     src = "CUDA events inside the timed graph" if "timed_region_ms" in res else \
         "the phase pass (events around every phase)"
-    roof = roofline_of(cfg, avg, res["peel_rows"] / K, probe, peaks, peak_kind)
+    roof = roofline_of(cfg, avg, res["peel_rows"] / K, probe, peaks, peak_kind, res.get("domstat"))
     roof["launch_ms_source"] = src
     res["phase_ms"] = breakdown
     res["roofline"] = roof
@@ -421,7 +453,13 @@ def run_ours(args, world, rank, local):
     dist = dist_init(world, "nccl")
     from paper_2504_06067_gb300 import native as n
 
-    cfg = WORKLOADS[args.workload]
+    if args.workload == "custom":
+        cfg = wl.RunConfig("custom_m%d_N%d_d%d_p%d%s" % (args.m, args.N, args.d, args.p1,
+                                                         "+%d" % args.p2 if args.p2 else ""),
+                           m=args.m, d=args.d, N=args.N, p1=args.p1, p2=args.p2, tau=0.5,
+                           generations=args.steps)
+    else:
+        cfg = WORKLOADS[args.workload]
     seed = cfg.seed + rank
     streaming = 1 if (args.streaming or args.workload == "huge") else 0
     kp = wl.knapsack_instance(cfg.m, cfg.d, cfg.seed) if args.workload == "knapsack" else None
@@ -469,7 +507,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": res["gpu_launches"],
         "clocks": clocks,
     }
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.workload != "custom":
         line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_budget)
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -1256,7 +1294,7 @@ def main(argv=None):
         args.steps = {"headline": wl.LARGE.generations, "batched": 300, "served": 0, "sweep": 50,
                       "popsweep": 50, "select": 20}.get(args.workload)
         if args.steps is None:
-            args.steps = WORKLOADS[args.workload].generations
+            args.steps = WORKLOADS[args.workload].generations if args.workload in WORKLOADS else 20
     if args.impl == "reference":
         run_reference(args, world, rank)
     elif args.workload == "headline":
