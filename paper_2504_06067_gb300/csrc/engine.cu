@@ -82,8 +82,10 @@ namespace {
 int select_launches(const nsga3_ctx* ctx)
 {
     const int m = ctx->m;
-    // m <= 10: + the sort's level thresholds, the dominance build's boxes and tile plan
-    return 18 + (m > NSGA3_FAST_M ? 5 : 3) + (m > NSGA3_WARP_M ? 1 : 0) + (ctx->v.dom_ks > 1 ? 1 : 0);
+    // m <= 10: + the sort's level thresholds, the dominance build's boxes and tile plan;
+    // - three association kernels with few reference directions (one fused kernel)
+    return 18 + (m > NSGA3_FAST_M ? 5 : 3) + (m > NSGA3_WARP_M ? 1 : 0) + (ctx->v.dom_ks > 1 ? 1 : 0) -
+           (assoc_small(ctx->v) ? 3 : 0);
 }
 // the softmax-simplex objective's dot-product kernel (m > 10)
 int objective_dot_launches(const nsga3_ctx* ctx) { return ctx->m > NSGA3_FAST_M && ctx->v.problem == 0 ? 1 : 0; }

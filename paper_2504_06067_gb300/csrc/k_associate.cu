@@ -720,11 +720,99 @@ __global__ void __launch_bounds__(256) k_assoc_final_gen(RunView v)
     write_assoc(v, c, v.Tlist[pt], bj, bd);
 }
 
+// Few reference directions (w <= ASSOC_SMALL_W, m <= 10): the whole
+// association of a point in one thread, every direction's FP32 unit vector
+// in shared memory (read by all threads of a warp at once).  f' and |f'| in
+// FP64 as k_assoc_prep computes them, the best FP32 cosine over all
+// directions, a second pass over the directions within the band of it (the
+// candidates), their FP64 distances and the lexicographic (d, j) minimum:
+// the same candidates, band and FP64 operations as the pruned path, so the
+// same exact result, in one launch instead of four.
+constexpr int SB_T = 128;
+
+template <int M>
+__global__ void __launch_bounds__(SB_T) k_assoc_small(RunView v)
+{
+    constexpr int M4 = (M + 3) & ~3;
+    extern __shared__ __align__(16) float zs[];  // w x M4 unit directions, original order
+    Ctrl* c = v.ctrl;
+    if (skip_niche(c)) return;
+    const int w = v.w;
+    for (int e = threadIdx.x; e < w * M4; e += SB_T) zs[e] = v.Zh[e];
+    __syncthreads();
+    const int s = blockIdx.x * SB_T + threadIdx.x;
+    if (s >= c->nT) return;
+    const int i = v.Tlist[s];
+    double fp[M];
+    double ss = 0.0;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+        const double ft = __dsub_rn((double)v.F[(size_t)i * M + q], c->zstar[q]);
+        fp[q] = __ddiv_rn(ft, c->a[q]);
+        ss = __dadd_rn(ss, __dmul_rn(fp[q], fp[q]));
+    }
+    const double nf = __dsqrt_rn(ss);
+    double bd = 0.0;
+    int bj = 0;
+    if (nf != 0.0 || v.debug_recheck_all) {
+        const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
+        float u[M];
+#pragma unroll
+        for (int q = 0; q < M; ++q) u[q] = __double2float_rn(fp[q] * inv);
+        float best = -1.0f;
+        for (int j = 0; j < w; ++j) {
+            const float* z = zs + j * M4;
+            float dq = 0.0f;
+#pragma unroll
+            for (int q = 0; q < M; ++q) dq = fmaf(u[q], z[q], dq);
+            best = fmaxf(best, dq);
+        }
+        const float band = 2.0f * (float)(M + 4) * 5.9604644775390625e-08f + 1e-12f;
+        bd = CUDART_INF;
+        bj = 0x7fffffff;
+        for (int j = 0; j < w; ++j) {
+            const float* z = zs + j * M4;
+            float dq = 0.0f;
+#pragma unroll
+            for (int q = 0; q < M; ++q) dq = fmaf(u[q], z[q], dq);
+            if (dq >= best - band) {
+                const double d = perp_dist(fp, nf, v.Zd + (size_t)j * M, v.nz[j], M);
+                if (lex_less(d, j, bd, bj)) {
+                    bd = d;
+                    bj = j;
+                }
+            }
+        }
+        if (v.debug_recheck_all) {
+            // every direction in FP64: the band must not have missed the minimum
+            double fd = CUDART_INF;
+            int fj = 0x7fffffff;
+            for (int j = 0; j < w; ++j) {
+                const double d = perp_dist(fp, nf, v.Zd + (size_t)j * M, v.nz[j], M);
+                if (lex_less(d, j, fd, fj)) {
+                    fd = d;
+                    fj = j;
+                }
+            }
+            if (fj != bj || fd != bd) atomicAdd(&c->recheck_miss, 1);
+            bd = fd;
+            bj = fj;
+        }
+    }
+    write_assoc(v, c, i, bj, bd);
+}
+
+size_t small_smem(const RunView& v) { return (size_t)v.w * v.M4 * sizeof(float); }
+
 size_t scan_smem(const RunView& v) { return (size_t)v.nblk * (v.M4 + 2 + 8) * 4 + 8 * 2 * LC * 4; }
 
 template <int M>
 cudaError_t launch_m(const RunView& v, cudaStream_t s, int num_sms)
 {
+    if (assoc_small(v)) {
+        k_assoc_small<M><<<(v.n2 + SB_T - 1) / SB_T, SB_T, small_smem(v), s>>>(v);
+        return cudaGetLastError();
+    }
     const size_t sm = scan_smem(v);
     int blocks = (v.n2 + 7) / 8;
     if (blocks > num_sms * 8) blocks = num_sms * 8;
@@ -748,6 +836,7 @@ cudaError_t attr_m(size_t sm)
 
 cudaError_t launch_assoc_prep(const RunView& v, cudaStream_t s)
 {
+    if (assoc_small(v)) return cudaSuccess;  // k_assoc_small forms f' itself
     const int g = (v.n2 + PB - 1) / PB;
     switch (v.m) {
     case 2: k_assoc_prep<2><<<g, PB, 0, s>>>(v); break;

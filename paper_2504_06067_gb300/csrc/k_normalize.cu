@@ -48,11 +48,21 @@ __global__ void __launch_bounds__(NB) k_norm_ideal(RunView v)
     if (v.norm_history && blockIdx.x == 0 && threadIdx.x == 0 && c->hvalid)
         for (int q = 0; q < v.m; ++q) atomicMin(&c->zmin[q], f2ord((float)c->hz[q]));
     if (v.m > NSGA3_FAST_M) return;  // k_zmin_gen
+    // the block's minimum per objective first (warps, then shared memory),
+    // one atomic per block and objective: the ideal point's m words are
+    // every block's target
+    __shared__ uint32_t smin[NB / 32][NSGA3_FAST_M];
+    const int warp = threadIdx.x >> 5;
     for (int q = 0; q < v.m; ++q) {
         uint32_t o = inZ ? f2ord(v.Fp[(size_t)p * v.m + q]) : 0xffffffffu;
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) o = min(o, __shfl_xor_sync(0xffffffffu, o, s));
-        if (lane == 0 && o != 0xffffffffu) atomicMin(&c->zmin[q], o);
+        o = __reduce_min_sync(0xffffffffu, o);
+        if (lane == 0) smin[warp][q] = o;
+    }
+    __syncthreads();
+    if (threadIdx.x < v.m) {
+        uint32_t o = smin[0][threadIdx.x];
+        for (int w = 1; w < NB / 32; ++w) o = min(o, smin[w][threadIdx.x]);
+        if (o != 0xffffffffu) atomicMin(&c->zmin[threadIdx.x], o);
     }
 }
 

@@ -34,6 +34,10 @@ cudaError_t launch_norm_ideal(const RunView& v, cudaStream_t s);
 cudaError_t launch_norm_extreme(const RunView& v, int num_sms, cudaStream_t s);
 cudaError_t norm_init_attributes();
 cudaError_t launch_assoc_prep(const RunView& v, cudaStream_t s);
+// at most this many reference directions (and m <= 10): the association is
+// one kernel with every direction in shared memory (k_assoc_small)
+#define ASSOC_SMALL_W 512
+inline bool assoc_small(const RunView& v) { return v.m <= NSGA3_FAST_M && v.w <= ASSOC_SMALL_W; }
 // FP32 candidate scan, FP64 distances and per-point argmin, FP64 slow path
 // (three launches; four for m > 10, where the distances are a kernel of
 // their own); f' and |f'| are launch_assoc_prep (one launch, two for m > 10)
