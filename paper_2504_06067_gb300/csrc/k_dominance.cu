@@ -295,90 +295,131 @@ __device__ __forceinline__ void put_block(const RunView& v, size_t at, uint32_t 
 }
 
 // A CTA takes a 256 x 256 tile of the upper block triangle (8 x 8 blocks of
-// 32).  Its warps first decide the tile's block pairs from the boxes and put
-// the ones to test on a shared list, both-way tests first (they cost about
-// twice a one-way test), then take list entries in turn: block pairs differ
-// widely in cost after the pruning, and a warp that runs out of entries
-// leaves the rest to the others instead of idling at the tile's barrier.
-// Per entry the warp's lanes hold the 32 rows' objectives in registers and
-// the columns are broadcast from shared memory.
+// 32) from the tile list.  The boxes and keys of the tile's 16 blocks are
+// staged in shared memory; 64 threads decide the 64 block pairs; the pairs
+// to test go on a shared work list, where two row blocks (2r, 2r + 1) that
+// take the same one-direction test against one column block form a single
+// entry (one column broadcast from shared memory then serves 64 pairs), and
+// the costlier entries (both-way tests, row pairs) come first.  The warps
+// take entries in turn: block pairs differ widely in cost after the pruning,
+// and a fixed assignment left warps idle at the tile's barrier.  Per entry
+// the lanes hold their rows' objectives in registers.
 template <int M>
-__global__ void __launch_bounds__(256) k_dominance(RunView v)
+__global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
 {
     constexpr int M4 = (M + 3) & ~3;
     __shared__ __align__(16) float srow[NSGA3_TILE * M4];
     __shared__ __align__(16) float scol[NSGA3_TILE * M4];
+    __shared__ float sbox[16][2 * M4];  // blocks 0..7 rows, 8..15 columns: min, then max
+    __shared__ uint32_t skey[16][2];
+    __shared__ unsigned char smode[64];
     __shared__ int s_tile[2];
     __shared__ int rowcnt[NSGA3_TILE];  // dominators found for the tile's row points
     __shared__ int colcnt[NSGA3_TILE];  // ... for its column points
     __shared__ unsigned nzw[4];         // dnz bytes: 0..7 row blocks (I, J), 8..15 column blocks (J, I)
     __shared__ unsigned mcount[6];      // block pairs of this tile by mode
-    __shared__ unsigned short work[64]; // block pairs to test: (mode << 6) | (row block << 3) | column block
-    __shared__ int nfull, none;         // both-way entries from the front, one-way from the back
+    // entries: (mode << 7) | (pair << 6) | (row block << 3) | column block
+    __shared__ unsigned short work[64];
+    __shared__ int nheavy, nlight;      // heavy entries from the front, light ones from the back
     if (read_status(v.ctrl)) return;
     const int T = v.ld / NSGA3_TILE;
     const int ntile = *(volatile const int32_t*)&v.ctrl->ntile;
+    const int warp = threadIdx.x >> 5, lane = lane_id();
     // persistent: the CTAs take the listed tiles in turn
     for (int it = blockIdx.x; it < ntile; it += gridDim.x) {
-    rowcnt[threadIdx.x] = 0;
-    colcnt[threadIdx.x] = 0;
-    if (threadIdx.x < 4) nzw[threadIdx.x] = 0u;
-    if (threadIdx.x < 6) mcount[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) {
-        nfull = 0;
-        none = 0;
-        decode_tile(v.tlist[it], T, s_tile[0], s_tile[1]);
-    }
-    __syncthreads();
-    const int ti = s_tile[0], tj = s_tile[1];
-    const int r0 = ti * NSGA3_TILE, c0 = tj * NSGA3_TILE;
-    const int warp = threadIdx.x >> 5, lane = lane_id();
-    // warp w decides row blocks 2 (w & 3), +1 against column blocks 4 (w >> 2) .. +3
-    {
-        const int rp = warp & 3, ch = warp >> 2;
+        rowcnt[threadIdx.x] = 0;
+        colcnt[threadIdx.x] = 0;
+        if (threadIdx.x < 4) nzw[threadIdx.x] = 0u;
+        if (threadIdx.x < 6) mcount[threadIdx.x] = 0u;
+        if (threadIdx.x == 0) {
+            nheavy = 0;
+            nlight = 0;
+            decode_tile(v.tlist[it], T, s_tile[0], s_tile[1]);
+        }
+        __syncthreads();
+        const int ti = s_tile[0], tj = s_tile[1];
+        const int r0 = ti * NSGA3_TILE, c0 = tj * NSGA3_TILE;
+        for (int e = threadIdx.x; e < 16 * 2 * M4; e += blockDim.x) {
+            const int b = e / (2 * M4), k = e - b * 2 * M4;
+            const int blk = b < 8 ? ti * 8 + b : tj * 8 + (b - 8);
+            sbox[b][k] = v.bbox[(size_t)blk * 2 * M4 + k];
+        }
+        if (threadIdx.x < 32) {
+            const int b = threadIdx.x >> 1;
+            const int blk = b < 8 ? ti * 8 + b : tj * 8 + (b - 8);
+            skey[b][threadIdx.x & 1] = v.bkey[2 * blk + (threadIdx.x & 1)];
+        }
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            // block pair (row block ri, column block cb) of the tile (see
+            // block_pair_mode for the tests)
+            const int ri = threadIdx.x >> 3, cb = threadIdx.x & 7;
+            const int ib = ti * 8 + ri, jb = tj * 8 + cb;
+            int mode;
+            if (jb < ib)
+                mode = BP_SKIP;
+            else if (jb == ib)
+                mode = BP_FULL;
+            else if (jb * 32 >= v.n2)
+                mode = BP_ZERO;  // a column block of padding only
+            else {
+                const float* bi = sbox[ri];
+                const float* bj = sbox[8 + cb];
+                bool fwd = true, bwd = true;
 #pragma unroll
-        for (int cbi = 0; cbi < 4; ++cbi) {
-            const int cb = ch * 4 + cbi;
+                for (int q = 0; q < M; ++q) {
+                    fwd = fwd && bi[q] <= bj[M4 + q];  // NaN (padding only) fails
+                    bwd = bwd && bj[q] <= bi[M4 + q];
+                }
+                bwd = bwd && !(skey[ri][1] < skey[8 + cb][0]);
+                const bool f0sep = bi[M4] < bj[0];
+                mode = (!fwd && !bwd) ? BP_ZERO
+                       : (fwd && f0sep) ? BP_FAST0
+                       : (fwd && !bwd)  ? BP_FASTK
+                       : !fwd           ? BP_FASTR
+                                        : BP_FULL;
+            }
+            smode[threadIdx.x] = (unsigned char)mode;
+            if (mode > BP_SKIP) atomicAdd(&mcount[mode - 1], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // row pair rp = (2 rp, 2 rp + 1) against column block cb
+            const int rp = threadIdx.x >> 3, cb = threadIdx.x & 7;
+            const int a = smode[(2 * rp) * 8 + cb], b = smode[(2 * rp + 1) * 8 + cb];
+            if (a == b && (a == BP_FAST0 || a == BP_FASTK)) {
+                work[atomicAdd(&nheavy, 1)] = (unsigned short)((a << 7) | (1 << 6) | ((2 * rp) << 3) | cb);
+            } else {
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int ri = 2 * rp + r;
-                const int mode = block_pair_mode<M>(v, ti * 8 + ri, tj * 8 + cb);
-                if (lane == 0) {
-                    if (mode > BP_SKIP) atomicAdd(&mcount[mode - 1], 1u);
-                    const unsigned short e = (unsigned short)((mode << 6) | (ri << 3) | cb);
-                    if (mode == BP_FULL)
-                        work[atomicAdd(&nfull, 1)] = e;
-                    else if (mode > BP_ZERO)
-                        work[63 - atomicAdd(&none, 1)] = e;
+                for (int r = 0; r < 2; ++r) {
+                    const int md = r ? b : a;
+                    const unsigned short e = (unsigned short)((md << 7) | ((2 * rp + r) << 3) | cb);
+                    if (md == BP_FULL)
+                        work[atomicAdd(&nheavy, 1)] = e;
+                    else if (md > BP_ZERO)
+                        work[63 - atomicAdd(&nlight, 1)] = e;
                 }
             }
         }
-    }
-    __syncthreads();
-    const int nf = nfull, no = none, nwork = nf + no;
-    if (threadIdx.x < 5 && mcount[threadIdx.x])
-        atomicAdd(&v.ctrl->domstat[threadIdx.x], (unsigned long long)mcount[threadIdx.x]);
-
-    unsigned* nz = v.dnz ? nzw : nullptr;
-    if (nwork > 0) {
-        // a tile without any block pair to test stages nothing
-        // Fp holds -0.0 as +0.0, so equal values subtract to +0.0
-        for (int e = threadIdx.x; e < NSGA3_TILE * M; e += blockDim.x) {
-            int p = e / M, q = e - p * M;
-            srow[p * M4 + q] = v.Fp[(size_t)r0 * M + e];
-            scol[p * M4 + q] = v.Fp[(size_t)c0 * M + e];
-        }
         __syncthreads();
-        for (int t = warp; t < nwork; t += 8) {
-            const unsigned e = work[t < nf ? t : 64 - nwork + t];
-            const int mode = e >> 6, ri = (e >> 3) & 7, cb = e & 7;
-            const int ib = ti * 8 + ri, jb = tj * 8 + cb;
-            float fi[M];
-#pragma unroll
-            for (int q = 0; q < M; ++q) fi[q] = srow[(ri * 32 + lane) * M4 + q];
-            const float* colp = scol + cb * 32 * M4;
-            uint32_t dij = 0u, dji = 0u;
-            if (mode == BP_FAST0 || mode == BP_FASTK || mode == BP_FASTR) {
+        const int nh = nheavy, nl = nlight, nwork = nh + nl;
+        if (threadIdx.x < 5 && mcount[threadIdx.x])
+            atomicAdd(&v.ctrl->domstat[threadIdx.x], (unsigned long long)mcount[threadIdx.x]);
+        unsigned* nz = v.dnz ? nzw : nullptr;
+        if (nwork > 0) {
+            // a tile without any block pair to test stages nothing
+            // Fp holds -0.0 as +0.0, so equal values subtract to +0.0
+            for (int e = threadIdx.x; e < NSGA3_TILE * M; e += blockDim.x) {
+                const int p = e / M, q = e - p * M;
+                srow[p * M4 + q] = v.Fp[(size_t)r0 * M + e];
+                scol[p * M4 + q] = v.Fp[(size_t)c0 * M + e];
+            }
+            __syncthreads();
+            for (int t = warp; t < nwork; t += 8) {
+                const unsigned e = work[t < nh ? t : 64 - nwork + t];
+                const int mode = e >> 7, two = (e >> 6) & 1, ri = (e >> 3) & 7, cb = e & 7;
+                const int ib = ti * 8 + ri, jb = tj * 8 + cb;
+                const float* colp = scol + cb * 32 * M4;
                 // One direction only: "no f_iq > f_jq" (or the reverse) decides,
                 // and a NaN padding point would pass it (its differences are
                 // NaN with a clear sign bit), so the bits of padding rows and
@@ -386,58 +427,85 @@ __global__ void __launch_bounds__(256) k_dominance(RunView v)
                 // gives the same sign both ways, hence no bit).
                 const int cv = v.n2 - jb * 32;
                 const uint32_t colvalid = cv >= 32 ? 0xffffffffu : (cv > 0 ? (1u << cv) - 1u : 0u);
-                const bool rowvalid = ib * 32 + lane < v.n2;
-                uint32_t acc = 0u, unused;
-                if (mode == BP_FAST0) {
-                    block_one_dir<1, M, M4, false>(fi, fi, colp, acc, unused);
-                    dij = rowvalid ? ~acc & colvalid : 0u;
-                } else if (mode == BP_FASTK) {
-                    block_one_dir<0, M, M4, false>(fi, fi, colp, acc, unused);
-                    dij = rowvalid ? ~acc & colvalid : 0u;
-                } else {
-                    // column j dominates row i: no f_jq > f_iq (the vectors differ)
-#pragma unroll 4
-                    for (int k = 31; k >= 0; --k) {
-                        const float* fj = colp + k * M4;
-                        acc = __funnelshift_l(any_greater<0, M>(fi, fj), acc, 1);
+                if (two) {
+                    // rows ri and ri + 1, "row dominates column" only
+                    float f0[M], f1[M];
+#pragma unroll
+                    for (int q = 0; q < M; ++q) {
+                        f0[q] = srow[(ri * 32 + lane) * M4 + q];
+                        f1[q] = srow[((ri + 1) * 32 + lane) * M4 + q];
                     }
-                    dji = rowvalid ? ~acc & colvalid : 0u;
+                    uint32_t acc0, acc1;
+                    if (mode == BP_FAST0)
+                        block_one_dir<1, M, M4, true>(f0, f1, colp, acc0, acc1);
+                    else
+                        block_one_dir<0, M, M4, true>(f0, f1, colp, acc0, acc1);
+                    const uint32_t d0 = ib * 32 + lane < v.n2 ? ~acc0 & colvalid : 0u;
+                    const uint32_t d1 = (ib + 1) * 32 + lane < v.n2 ? ~acc1 & colvalid : 0u;
+                    const uint32_t t0 = warp_transpose32(d0), t1 = warp_transpose32(d1);
+                    put_block(v, (size_t)ib * v.ld + jb * 32 + lane, t0, nz, ri, cb);
+                    put_block(v, (size_t)(ib + 1) * v.ld + jb * 32 + lane, t1, nz, ri + 1, cb);
+                    const int cc = __popc(t0) + __popc(t1);
+                    if (cc) atomicAdd(&colcnt[cb * 32 + lane], cc);
+                    continue;
                 }
-            } else {
-                block_full<M, M4>(fi, colp, dij, dji);
+                float fi[M];
+#pragma unroll
+                for (int q = 0; q < M; ++q) fi[q] = srow[(ri * 32 + lane) * M4 + q];
+                uint32_t dij = 0u, dji = 0u;
+                if (mode == BP_FAST0 || mode == BP_FASTK || mode == BP_FASTR) {
+                    const bool rowvalid = ib * 32 + lane < v.n2;
+                    uint32_t acc = 0u, unused;
+                    if (mode == BP_FAST0) {
+                        block_one_dir<1, M, M4, false>(fi, fi, colp, acc, unused);
+                        dij = rowvalid ? ~acc & colvalid : 0u;
+                    } else if (mode == BP_FASTK) {
+                        block_one_dir<0, M, M4, false>(fi, fi, colp, acc, unused);
+                        dij = rowvalid ? ~acc & colvalid : 0u;
+                    } else {
+                        // column j dominates row i: no f_jq > f_iq (the vectors differ)
+#pragma unroll 4
+                        for (int k = 31; k >= 0; --k) {
+                            const float* fj = colp + k * M4;
+                            acc = __funnelshift_l(any_greater<0, M>(fi, fj), acc, 1);
+                        }
+                        dji = rowvalid ? ~acc & colvalid : 0u;
+                    }
+                } else {
+                    block_full<M, M4>(fi, colp, dij, dji);
+                }
+                // column i = ib*32 + lane, dominators j in block jb: Dom block (jb, ib)
+                if (jb != ib) {
+                    put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, 8 + cb, ri);
+                    const uint32_t tr = warp_transpose32(dij);
+                    put_block(v, (size_t)ib * v.ld + jb * 32 + lane, tr, nz, ri, cb);
+                    if (tr) atomicAdd(&colcnt[cb * 32 + lane], __popc(tr));
+                } else {
+                    put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, ri, cb);
+                }
+                if (dji) atomicAdd(&rowcnt[ri * 32 + lane], __popc(dji));
             }
-            // column i = ib*32 + lane, dominators j in block jb: Dom block (jb, ib)
-            if (jb != ib) {
-                put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, 8 + cb, ri);
-                const uint32_t tr = warp_transpose32(dij);
-                put_block(v, (size_t)ib * v.ld + jb * 32 + lane, tr, nz, ri, cb);
-                if (tr) atomicAdd(&colcnt[cb * 32 + lane], __popc(tr));
-            } else {
-                put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, ri, cb);
+        }
+        __syncthreads();
+        const int t = threadIdx.x;
+        if (v.dnz) {
+            // this tile owns bytes dnz[I][tj] (I a row block) and dnz[J][ti] (J a
+            // column block), one byte each; on the diagonal they are the same bytes
+            const unsigned char* nzb = reinterpret_cast<const unsigned char*>(nzw);
+            if (t < 8) {
+                unsigned char x = nzb[t];
+                if (ti == tj) x |= nzb[8 + t];
+                v.dnz[(size_t)(ti * 8 + t) * v.NB8 + tj] = x;
+            } else if (t < 16 && ti != tj) {
+                v.dnz[(size_t)(tj * 8 + (t - 8)) * v.NB8 + ti] = nzb[t];
             }
-            if (dji) atomicAdd(&rowcnt[ri * 32 + lane], __popc(dji));
         }
-    }
-    __syncthreads();
-    const int t = threadIdx.x;
-    if (v.dnz) {
-        // this tile owns bytes dnz[I][tj] (I a row block) and dnz[J][ti] (J a
-        // column block), one byte each; on the diagonal they are the same bytes
-        const unsigned char* nzb = reinterpret_cast<const unsigned char*>(nzw);
-        if (t < 8) {
-            unsigned char x = nzb[t];
-            if (ti == tj) x |= nzb[8 + t];
-            v.dnz[(size_t)(ti * 8 + t) * v.NB8 + tj] = x;
-        } else if (t < 16 && ti != tj) {
-            v.dnz[(size_t)(tj * 8 + (t - 8)) * v.NB8 + ti] = nzb[t];
+        if (nwork > 0) {
+            // dominator counts of the peel's first pass: one global add per point of the tile
+            if (rowcnt[t]) atomicAdd(&v.cnt[r0 + t], rowcnt[t]);
+            if (colcnt[t]) atomicAdd(&v.cnt[c0 + t], colcnt[t]);
         }
-    }
-    if (nwork > 0) {
-        // dominator counts of the peel's first pass: one global add per point of the tile
-        if (rowcnt[t]) atomicAdd(&v.cnt[r0 + t], rowcnt[t]);
-        if (colcnt[t]) atomicAdd(&v.cnt[c0 + t], colcnt[t]);
-    }
-    __syncthreads();  // the shared arrays are reset for the next tile
+        __syncthreads();  // the shared arrays are reset for the next tile
     }
 }
 
@@ -648,8 +716,13 @@ cudaError_t launch_dom_m(const RunView& v, cudaStream_t s)
     k_tile_plan<M><<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(v);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // persistent CTAs over the listed tiles (four resident per SM)
-    long long grid = 4LL * v.num_sms;
+    // persistent CTAs over the listed tiles, as many as are resident at once
+    static int occ = 0;  // per M; the same value whatever the run
+    if (occ <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dominance<M>, 256, 0) != cudaSuccess) {
+        cudaGetLastError();
+        occ = 4;
+    }
+    long long grid = (long long)(occ > 0 ? occ : 4) * v.num_sms;
     if (grid > tiles) grid = tiles;
     k_dominance<M><<<(unsigned)grid, 256, 0, s>>>(v);
     return cudaGetLastError();
