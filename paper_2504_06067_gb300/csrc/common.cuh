@@ -145,6 +145,9 @@ struct RunView {
     uint32_t* tkey;    // (ld / 256) x 2: per tile smallest, largest sort key
     int32_t* tlist;    // tiles of the dominance build with block pairs to test (k_tile_plan)
     int num_sms;
+    int shared_gpu;    // 1: the run shares the GPU with others (batched graphs, the run
+                       // server): the cooperative peel takes fewer CTAs, so that it can
+                       // start while other runs' kernels hold part of every SM
     uint32_t* rem;     // NW   not-yet-ranked mask
     uint32_t* front;   // 2 x NW  ping-pong front masks
     uint32_t* chunk_lim;   // ld / NSGA3_PEEL_COLS dominator row blocks a column chunk reads

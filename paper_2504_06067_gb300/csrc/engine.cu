@@ -64,6 +64,7 @@ struct nsga3_ctx {
     unsigned ev_mask = 0; // bit e set: event e is recorded (opts.phase_timing; eager: all)
     std::string err;
     unsigned long long serial = 0;  // creation serial (g_ctx_serial)
+    bool shared_gpu = false;        // runs side by side with others (RunView::shared_gpu)
     // batched graph cache: the graphs hold the device buffers of every run in
     // the list, so they are keyed by the runs' creation serials (a pointer of
     // a destroyed run can be handed out again by the allocator)
@@ -428,6 +429,7 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     v.w = w;
     v.M4 = M4;
     v.num_sms = ctx->num_sms > 0 ? ctx->num_sms : 1;
+    v.shared_gpu = ctx->shared_gpu ? 1 : 0;
     v.full_sort = ctx->opts.full_sort ? 1 : 0;
     v.debug_recheck_all = ctx->opts.debug_recheck_all ? 1 : 0;
     v.streaming = ctx->opts.streaming ? 1 : 0;
@@ -771,7 +773,7 @@ nsga3_status ctx_fields(nsga3_ctx* ctx, int m, int d, int N, int ref_divisions, 
 }  // namespace
 
 nsga3_status ctx_create(int m, int d, int N, int ref_divisions, const nsga3_opts* opts, DeviceArena* arena,
-                        nsga3_ctx** out, std::string* err)
+                        nsga3_ctx** out, std::string* err, bool shared_gpu)
 {
     if (!out) {
         if (err) *err = "out is NULL";
@@ -781,6 +783,7 @@ nsga3_status ctx_create(int m, int d, int N, int ref_divisions, const nsga3_opts
     nsga3_ctx* ctx = new nsga3_ctx();
     ctx->serial = ++g_ctx_serial;
     ctx->arena = arena;
+    ctx->shared_gpu = shared_gpu;
     nsga3_status st = ctx_fields(ctx, m, d, N, ref_divisions, opts);
     if (!st) {
         const char* e = getenv("NSGA3_EAGER");
@@ -895,6 +898,9 @@ nsga3_status build_batch_graph(nsga3_ctx* ctx, nsga3_ctx** ctxs, int n, int gens
                 st = fail(ctx, NSGA3_ECUDA, "fork wait failed");
                 break;
             }
+            // the runs of a batched graph share the GPU
+            const int shared = ctxs[r]->v.shared_gpu;
+            ctxs[r]->v.shared_gpu = 1;
             for (int k = 0; k < gens && !st; ++k) {
                 nsga3_status rs = record_generation(ctxs[r], br[r], false);
                 if (rs) {
@@ -902,6 +908,7 @@ nsga3_status build_batch_graph(nsga3_ctx* ctx, nsga3_ctx** ctxs, int n, int gens
                     ctx->err = ctxs[r]->err;
                 }
             }
+            ctxs[r]->v.shared_gpu = shared;
             // join the branch even after a failure so the capture ends cleanly
             if (cudaEventRecord(evs[r], br[r]) != cudaSuccess || cudaStreamWaitEvent(s0, evs[r], 0) != cudaSuccess) {
                 if (!st) st = fail(ctx, NSGA3_ECUDA, "join failed");

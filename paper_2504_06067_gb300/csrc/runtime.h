@@ -40,9 +40,11 @@ private:
 };
 
 // Context creation with optional arena (nullptr: cudaMalloc per buffer).
-// On failure *err holds the message and *out is nullptr.
+// shared_gpu: the run will share the GPU with other runs (its cooperative
+// launches take fewer CTAs).  On failure *err holds the message and *out is
+// nullptr.
 nsga3_status ctx_create(int m, int d, int N, int ref_divisions, const nsga3_opts* opts, DeviceArena* arena,
-                        nsga3_ctx** out, std::string* err);
+                        nsga3_ctx** out, std::string* err, bool shared_gpu = false);
 
 // Device bytes ctx_create allocates for these arguments (each buffer rounded
 // up to DeviceArena::kAlign), computed without touching the device when

@@ -313,7 +313,8 @@ void worker_main(nsga3_server* s)
             o.W = q.W.empty() ? nullptr : q.W.data();
             nsga3_ctx* ctx = nullptr;
             std::string cerr;
-            nsga3_status cst = ctx_create(q.r.m, q.r.d, q.r.N, q.r.ref_divisions, &o, s->arena, &ctx, &cerr);
+            nsga3_status cst = ctx_create(q.r.m, q.r.d, q.r.N, q.r.ref_divisions, &o, s->arena, &ctx, &cerr,
+                                          s->max_active > 1);
             if (cst == NSGA3_ENOMEM) {
                 // fragmented arena: keep the request at the head, retry after a release
                 std::lock_guard<std::mutex> lk(s->mu);
