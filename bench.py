@@ -835,6 +835,14 @@ def served_core(n, torch, n_req, dist, world, rank, n_plain=None):
         served_small = served_inf
     barrier(dist)
     plain = _latency_summary(plain_inf, reqs_all[:n_plain])
+    # each run's time alone (one slot: admitted when the previous run left)
+    solo = sorted((i.t_done - i.t_admit for i in plain_inf.values()), reverse=True)
+    arrive = {rid: t for rid, (t, _) in enumerate(reqs_all[:n_plain])}
+    bound = max(arrive[rid] + (i.t_done - i.t_admit) for rid, i in plain_inf.items())
+    plain["solo_s_total"] = sum(solo)
+    plain["solo_s_largest10"] = [round(x, 3) for x in solo[:10]]
+    plain["largest10_work_share"] = sum(solo[:10]) / sum(solo)
+    plain["makespan_lower_bound_s"] = bound
     same = _latency_summary(served_small, reqs_all[:n_plain])
     full = _latency_summary(served_inf, reqs_all)
     makespan = reduce_max(dist, full["makespan_s"], "cuda")
