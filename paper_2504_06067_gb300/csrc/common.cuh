@@ -185,6 +185,11 @@ struct RunView {
     int2* cand;            // cand_cap   (T slot, reference)
     int cand_cap;
     int32_t* slow;         // n2         T slots for the full FP64 scan
+    // tiled association (null: the pruned scan): per work item (a tile of T
+    // slots x a range of reference blocks) and slot, ASSOC_K entries
+    // (block maximum of the FP32 cosines as float bits, block; -1 empty, -2 overflow)
+    int2* aent;
+    int assoc_grid;        // CTAs of the tiled scan (the entries' layout depends on it)
     double* cdist;         // cand_cap   FP64 distance of each candidate (m > NSGA3_FAST_M)
     float* he;             // m x m      remembered extreme vectors (history), row q for axis q
     // m > NSGA3_FAST_M: extreme points by entry keys, then per-axis blocks

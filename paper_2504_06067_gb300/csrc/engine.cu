@@ -80,6 +80,24 @@ namespace {
 // extreme-point keys and reduction, |f'|, candidate distances), m > 32 the
 // cooperative elimination, and a split dominance build (few tiles) its
 // finishing kernel
+// Association of more than ASSOC_SMALL_W directions (m <= 10): the tiled
+// scan (every FP32 cosine at the FMA rate) or the pruned scan (cone bounds
+// per block of 32 directions).  Both give the same association.  The cone
+// bounds skip most blocks up to m = 6 (the pruned scan is as fast or faster
+// there: m = 5 and 10,626 directions 0.12 against 0.16 ms of niching per
+// generation, m = 6 and 2,002 directions 0.133 against 0.137 ms); from m = 7
+// they skip few and the tiled scan wins (m = 8 and 11,440 directions 0.79
+// against 0.29 ms, m = 10 and 2,002 directions 0.31 against 0.21 ms).
+// NSGA3_ASSOC=tile|scan overrides the choice for every context a process
+// creates.
+bool assoc_tile_wanted(int m)
+{
+    const char* e = getenv("NSGA3_ASSOC");
+    if (e && strcmp(e, "scan") == 0) return false;
+    if (e && strcmp(e, "tile") == 0) return true;
+    return m >= 7;
+}
+
 int select_launches(const nsga3_ctx* ctx)
 {
     const int m = ctx->m;
@@ -524,6 +542,12 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     AL(v.arun, n2);
     AL(v.cand, v.cand_cap);
     AL(v.slow, n2);
+    v.aent = nullptr;
+    v.assoc_grid = 0;
+    if (m <= NSGA3_FAST_M && w > ASSOC_SMALL_W && assoc_tile_wanted(m)) {
+        v.assoc_grid = assoc_tile_grid(v.num_sms);
+        AL(v.aent, assoc_tile_entries(n2, v.num_sms));
+    }
     AL(v.he, (size_t)m * m);
     if (m > NSGA3_FAST_M) {
         AL(v.cdist, v.cand_cap);

@@ -802,6 +802,350 @@ __global__ void __launch_bounds__(SB_T) k_assoc_small(RunView v)
     write_assoc(v, c, i, bj, bd);
 }
 
+// ---------------------------------------------------------------------------
+// Tiled scan (m <= 10, more than ASSOC_SMALL_W directions).  Where the cone
+// bounds prune little (several objectives: a block's cone and a point's
+// distance to its nearest direction are comparable), every cosine is formed,
+// at the FP32 FMA rate: a CTA holds TP = TT x TP_P points in registers and
+// streams the reference blocks of its range through shared memory (each
+// direction read once per CTA by a broadcast load, then TP_P x m FMAs per
+// thread).  A work item is (a tile of TP slots, a range of reference
+// blocks); the ranges are chosen so that the items fill the grid.  Per
+// point and item the scan keeps the largest block maximum (the item's best
+// cosine) and up to ASSOC_K blocks whose maximum is within the band of it
+// (a block is taken when its maximum is within the band of the best so
+// far, replacing a block that has fallen out of the band; none free: the
+// point overflows to the FP64 scan).  The block holding the exact argmin
+// has a maximum within the band of every later best, so it is never
+// replaced.  k_assoc_final_tile takes the best over the items, rescans the
+// blocks within the band of it (FP32, then FP64 for the directions within
+// the band, as the pruned path does) and writes the association.
+constexpr int TT = 128;     // threads per CTA
+constexpr int TP_P = 4;     // points per thread
+constexpr int TP = TT * TP_P;
+constexpr int TCB = 8;      // reference blocks per shared-memory chunk
+constexpr int TOCC = 4;     // CTAs per SM (the grid, and the register bound)
+constexpr int ASSOC_K = 4;  // entries per point and item
+
+// tiles of T slots, items per tile (splits) and blocks per split: the same
+// on the device for both kernels (from nT) and on the host for the maximum.
+// The split count minimises the waves of the grid times the blocks an item
+// scans, over at most twice the count that fills the grid once (so that
+// items <= 2 (grid + ntile)).
+__host__ __device__ __forceinline__ void tile_split(int nT, int nb, int grid, int& ntile, int& S, int& bps)
+{
+    ntile = (nT + TP - 1) / TP;
+    S = 1;
+    bps = nb;
+    if (ntile == 0 || nb == 0) return;
+    const int fill = (grid + ntile - 1) / ntile;
+    const int smax = min(nb, 2 * fill);
+    long long best = -1;
+    for (int t = 1; t <= smax; ++t) {
+        const int b = (nb + t - 1) / t;
+        const int st = (nb + b - 1) / b;
+        const long long cost = (long long)(((long long)ntile * st + grid - 1) / grid) * b;
+        if (best < 0 || cost < best) {
+            best = cost;
+            S = st;
+            bps = b;
+        }
+    }
+}
+
+// Two points' cosines with one direction in one instruction: FP32 pairs
+// (fma.rn.f32x2 rounds each lane once, as fmaf does), the points' unit
+// vectors packed by pairs, each direction component duplicated in shared
+// memory.  Packing and unpacking are register moves.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void f2_unpack(unsigned long long x, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x));
+}
+
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ float fmax3f(float a, float b, float c)
+{
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+template <int M>
+__global__ void __launch_bounds__(TT, TOCC) k_assoc_tile(RunView v)
+{
+    static_assert(TP_P % 2 == 0, "points are packed by pairs");
+    constexpr int M4 = (M + 3) & ~3;
+    constexpr int ZQ = (M + 1) / 2;  // 16-byte words per staged direction: (z0, z0, z1, z1), ...
+    constexpr int PP = TP_P / 2;
+    __shared__ ulonglong2 zs[TCB * 32 * ZQ];
+    __shared__ float slm[TP_P][ASSOC_K][TT];  // candidate blocks of each point: maximum, block
+    __shared__ int slk[TP_P][ASSOC_K][TT];
+    Ctrl* c = v.ctrl;
+    if (skip_niche(c)) return;
+    const int nT = c->nT;
+    const int nb = v.nblk, w = v.w;
+    int ntile, S, bps;
+    tile_split(nT, nb, gridDim.x, ntile, S, bps);
+    const int items = ntile * S;
+    const float band = 2.0f * (float)(M + 4) * 5.9604644775390625e-08f + 1e-12f;
+    const int tid = threadIdx.x;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int tile = it / S, sp = it - (it / S) * S;
+        const int b0 = sp * bps;
+        const int b1 = min(nb, b0 + bps);
+        unsigned long long u2[PP][M];
+#pragma unroll
+        for (int pp = 0; pp < PP; ++pp) {
+            const int sa = tile * TP + (2 * pp) * TT + tid;
+            const int sb = sa + TT;
+            const float* ra = v.uhat + (size_t)sa * M4;
+            const float* rb = v.uhat + (size_t)sb * M4;
+#pragma unroll
+            for (int t = 0; t < M; ++t)
+                u2[pp][t] = f2_pack(sa < nT ? ra[t] : 0.0f, sb < nT ? rb[t] : 0.0f);
+        }
+        float lbest[TP_P];
+        unsigned ovf = 0u;
+#pragma unroll
+        for (int k = 0; k < TP_P; ++k) {
+            lbest[k] = -4.0f;
+#pragma unroll
+            for (int e = 0; e < ASSOC_K; ++e) {
+                slm[k][e][tid] = -4.0f;
+                slk[k][e][tid] = -1;
+            }
+        }
+        for (int cb = b0; cb < b1; cb += TCB) {
+            const int nbk = min(TCB, b1 - cb);
+            __syncthreads();  // the previous chunk is consumed
+            // padding directions (position >= w) get -1 components: their
+            // cosine with a unit vector of non-negative components is <= -1
+            for (int e = tid; e < nbk * 32 * ZQ; e += TT) {
+                const int r = e / ZQ, q2 = e - r * ZQ;
+                const int pos = cb * 32 + r;
+                float2 a = make_float2(-1.0f, -1.0f);
+                if (pos < w) a = __ldg(reinterpret_cast<const float2*>(v.blk_z + (size_t)pos * M4) + q2);
+                zs[e] = make_ulonglong2(f2_pack(a.x, a.x), f2_pack(a.y, a.y));
+            }
+            __syncthreads();
+            for (int bb = 0; bb < nbk; ++bb) {
+                float bm[TP_P];
+#pragma unroll
+                for (int k = 0; k < TP_P; ++k) bm[k] = -4.0f;
+                const ulonglong2* zb = zs + bb * 32 * ZQ;
+#pragma unroll 2
+                for (int r = 0; r < 32; r += 2) {
+                    ulonglong2 za[ZQ], zc[ZQ];
+#pragma unroll
+                    for (int q2 = 0; q2 < ZQ; ++q2) {
+                        za[q2] = zb[r * ZQ + q2];
+                        zc[q2] = zb[(r + 1) * ZQ + q2];
+                    }
+#pragma unroll
+                    for (int pp = 0; pp < PP; ++pp) {
+                        unsigned long long qa = 0ull, qc = 0ull;
+#pragma unroll
+                        for (int t = 0; t < M; ++t) {
+                            qa = f2_fma(u2[pp][t], (t & 1) ? za[t >> 1].y : za[t >> 1].x, qa);
+                            qc = f2_fma(u2[pp][t], (t & 1) ? zc[t >> 1].y : zc[t >> 1].x, qc);
+                        }
+                        float a0, a1, c0, c1;
+                        f2_unpack(qa, a0, a1);
+                        f2_unpack(qc, c0, c1);
+                        bm[2 * pp] = fmax3f(bm[2 * pp], a0, c0);
+                        bm[2 * pp + 1] = fmax3f(bm[2 * pp + 1], a1, c1);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < TP_P; ++k) {
+                    if (bm[k] >= lbest[k] - band) {
+                        const float thr = fmaxf(lbest[k], bm[k]) - band;
+                        int slot = -1;
+#pragma unroll
+                        for (int e = 0; e < ASSOC_K; ++e)
+                            if (slot < 0 && (slk[k][e][tid] < 0 || slm[k][e][tid] < thr)) slot = e;
+                        if (slot < 0) {
+                            ovf |= 1u << k;
+                        } else {
+                            slm[k][slot][tid] = bm[k];
+                            slk[k][slot][tid] = cb + bb;
+                        }
+                    }
+                    lbest[k] = fmaxf(lbest[k], bm[k]);
+                }
+            }
+        }
+        // point k of this thread is T slot tile * TP + k * TT + tid (pairs:
+        // points 2 pp and 2 pp + 1 are TT slots apart)
+#pragma unroll
+        for (int k = 0; k < TP_P; ++k) {
+            const int l = k * TT + tid;
+            if (tile * TP + l >= nT) continue;
+            int4* dst = reinterpret_cast<int4*>(v.aent + ((size_t)it * TP + l) * ASSOC_K);
+            if ((ovf >> k) & 1u) {
+                dst[0] = make_int4(0, -2, 0, -2);
+                dst[1] = make_int4(0, -2, 0, -2);
+            } else {
+                dst[0] = make_int4(__float_as_int(slm[k][0][tid]), slk[k][0][tid],
+                                   __float_as_int(slm[k][1][tid]), slk[k][1][tid]);
+                dst[1] = make_int4(__float_as_int(slm[k][2][tid]), slk[k][2][tid],
+                                   __float_as_int(slm[k][3][tid]), slk[k][3][tid]);
+            }
+        }
+    }
+}
+
+static_assert(ASSOC_K == 4, "the entries of a point are written as two int4");
+
+// per point (a thread per T slot): the best cosine over the items, the
+// blocks within the band of it rescanned in FP32, the FP64 distances of
+// their directions within the band and the lexicographic (d, j) minimum.
+// The blocks and then the candidate directions of each thread are listed
+// first (shared memory, a column per thread), so that a warp runs as many
+// rescans and FP64 evaluations as its busiest thread needs rather than the
+// union of its threads' positions.  A point with more than FT_BLK blocks or
+// FT_CAND candidates takes the FP64 scan over all directions.
+constexpr int FT_BLK = 8;
+constexpr int FT_CAND = 16;
+
+template <int M>
+__global__ void __launch_bounds__(FB) k_assoc_final_tile(RunView v)
+{
+    constexpr int M4 = (M + 3) & ~3;
+    constexpr int Q4 = M4 / 4;
+    // a block's directions in groups of RC, every load of a group in flight
+    // together (a thread's blocks are its own: the loads do not coalesce,
+    // so round trips, not bytes, set the time)
+    constexpr int RC = M4 <= 8 ? 8 : 4;
+    __shared__ int sblk[FT_BLK][FB];
+    __shared__ int scand[FT_CAND][FB];
+    Ctrl* c = v.ctrl;
+    if (skip_niche(c)) return;
+    const int nT = c->nT;
+    const int tid = threadIdx.x;
+    const int s = blockIdx.x * FB + tid;
+    if (s >= nT) return;
+    int ntile, S, bps;
+    tile_split(nT, v.nblk, v.assoc_grid, ntile, S, bps);
+    const int tile = s / TP, l = s - tile * TP;
+    const double nf = v.fnorm[s];
+    double bd = 0.0;
+    int bj = 0;
+    if (nf != 0.0) {
+        const float band = 2.0f * (float)(M + 4) * 5.9604644775390625e-08f + 1e-12f;
+        float gbest = -4.0f;
+        bool ovf = false;
+        for (int sp = 0; sp < S; ++sp) {
+            const int4* e = reinterpret_cast<const int4*>(v.aent + ((size_t)(tile * S + sp) * TP + l) * ASSOC_K);
+            const int4 x0 = e[0], x1 = e[1];
+            const int bk[4] = {x0.y, x0.w, x1.y, x1.w};
+            const int bv[4] = {x0.x, x0.z, x1.x, x1.z};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (bk[k] == -2) ovf = true;
+                if (bk[k] >= 0) gbest = fmaxf(gbest, __int_as_float(bv[k]));
+            }
+        }
+        const float thr = gbest - band;
+        int nblk = 0;
+        for (int sp = 0; sp < S && !ovf; ++sp) {
+            const int4* e = reinterpret_cast<const int4*>(v.aent + ((size_t)(tile * S + sp) * TP + l) * ASSOC_K);
+            const int4 x0 = e[0], x1 = e[1];
+            const int bk[4] = {x0.y, x0.w, x1.y, x1.w};
+            const int bv[4] = {x0.x, x0.z, x1.x, x1.z};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (bk[k] < 0 || __int_as_float(bv[k]) < thr) continue;
+                if (nblk == FT_BLK) {
+                    ovf = true;
+                } else {
+                    sblk[nblk][tid] = bk[k];
+                    ++nblk;
+                }
+            }
+        }
+        float u[M];
+#pragma unroll
+        for (int q = 0; q < M; ++q) u[q] = v.uhat[(size_t)s * M4 + q];
+        int ncand = 0;
+        const float4* bz4 = reinterpret_cast<const float4*>(v.blk_z);
+        for (int i = 0; i < nblk && !ovf; ++i) {
+            const int base = sblk[i][tid] * 32;
+            for (int r0 = 0; r0 < 32; r0 += RC) {
+                float qv[RC];
+#pragma unroll
+                for (int t = 0; t < RC; ++t) {
+                    const int pos = min(base + r0 + t, v.w - 1);
+                    float z[M4];
+#pragma unroll
+                    for (int q4 = 0; q4 < Q4; ++q4) {
+                        const float4 a = __ldg(bz4 + (size_t)pos * Q4 + q4);
+                        z[4 * q4 + 0] = a.x;
+                        z[4 * q4 + 1] = a.y;
+                        z[4 * q4 + 2] = a.z;
+                        z[4 * q4 + 3] = a.w;
+                    }
+                    float q = 0.0f;
+#pragma unroll
+                    for (int t2 = 0; t2 < M; ++t2) q = fmaf(u[t2], z[t2], q);
+                    qv[t] = q;
+                }
+#pragma unroll
+                for (int t = 0; t < RC; ++t) {
+                    const int pos = base + r0 + t;
+                    if (pos >= v.w || qv[t] < thr) continue;
+                    if (ncand == FT_CAND) {
+                        ovf = true;
+                    } else {
+                        scand[ncand][tid] = pos;
+                        ++ncand;
+                    }
+                }
+            }
+        }
+        if (ovf) {
+            v.arun[s] = make_int2(-1, 0);
+            v.slow[atomicAdd(&c->nslow, 1)] = s;
+            return;
+        }
+        double fp[M];
+#pragma unroll
+        for (int q = 0; q < M; ++q) fp[q] = v.fprime[(size_t)s * M + q];
+        bd = CUDART_INF;
+        bj = 0x7fffffff;
+        for (int i = 0; i < ncand; ++i) {
+            const int j = v.blk_j[scand[i][tid]];
+            const double d = perp_dist(fp, nf, v.Zd + (size_t)j * M, v.nz[j], M);
+            if (lex_less(d, j, bd, bj)) {
+                bd = d;
+                bj = j;
+            }
+        }
+    }
+    if (v.debug_recheck_all) {
+        v.dist[v.Tlist[s]] = bd;  // compared by k_assoc_slow
+        v.pi[v.Tlist[s]] = bj;
+        v.arun[s] = make_int2(0, 0);
+        v.slow[atomicAdd(&c->nslow, 1)] = s;
+        return;
+    }
+    write_assoc(v, c, v.Tlist[s], bj, bd);
+}
+
 size_t small_smem(const RunView& v) { return (size_t)v.w * v.M4 * sizeof(float); }
 
 size_t scan_smem(const RunView& v) { return (size_t)v.nblk * (v.M4 + 2 + 8) * 4 + 8 * 2 * LC * 4; }
@@ -811,6 +1155,16 @@ cudaError_t launch_m(const RunView& v, cudaStream_t s, int num_sms)
 {
     if (assoc_small(v)) {
         k_assoc_small<M><<<(v.n2 + SB_T - 1) / SB_T, SB_T, small_smem(v), s>>>(v);
+        return cudaGetLastError();
+    }
+    if (v.aent) {
+        k_assoc_tile<M><<<v.assoc_grid, TT, 0, s>>>(v);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_assoc_final_tile<M><<<(v.n2 + FB - 1) / FB, FB, 0, s>>>(v);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_assoc_slow<M><<<num_sms, AB, 0, s>>>(v);
         return cudaGetLastError();
     }
     const size_t sm = scan_smem(v);
@@ -833,6 +1187,16 @@ cudaError_t attr_m(size_t sm)
 }
 
 }  // namespace
+
+int assoc_tile_grid(int num_sms) { return (num_sms > 0 ? num_sms : 1) * TOCC; }
+
+size_t assoc_tile_entries(int n2, int num_sms)
+{
+    // items = ntile x S <= ntile x 2 ceil(grid / ntile) <= 2 (grid + ntile)
+    // for every nT <= n2
+    const size_t ntile = ((size_t)n2 + TP - 1) / TP;
+    return 2 * ((size_t)assoc_tile_grid(num_sms) + ntile) * TP * ASSOC_K;
+}
 
 cudaError_t launch_assoc_prep(const RunView& v, cudaStream_t s)
 {

@@ -43,6 +43,11 @@ inline bool assoc_small(const RunView& v) { return v.m <= NSGA3_FAST_M && v.w <=
 // their own); f' and |f'| are launch_assoc_prep (one launch, two for m > 10)
 cudaError_t launch_assoc_scan(const RunView& v, int num_sms, cudaStream_t s);
 cudaError_t assoc_prepare(const RunView& v);
+// tiled association scan (m <= 10, more than ASSOC_SMALL_W directions):
+// its grid for a device of num_sms SMs and the int2 entries it writes for
+// at most n2 points
+int assoc_tile_grid(int num_sms);
+size_t assoc_tile_entries(int n2, int num_sms);
 cudaError_t assoc_init_attributes();
 cudaError_t launch_level(const RunView& v, cudaStream_t s);
 cudaError_t launch_bucket(const RunView& v, cudaStream_t s);
