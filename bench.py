@@ -634,10 +634,14 @@ def batched_core(n, torch, stream, n_runs, gens, warmup, dist, world, rank):
             s += tot.value
         return s
 
+    run_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in ctxs]
+
     def plain():
-        for x in ctxs:
+        for x, (a, b) in zip(ctxs, run_ev):
+            a.record(stream)
             n.check(n.nsga3_init(x, sh), x)
             n.check(n.nsga3_run(x, gens, sh), x)
+            b.record(stream)
 
     def batched():
         for x in ctxs:
@@ -695,6 +699,10 @@ def batched_core(n, torch, stream, n_runs, gens, warmup, dist, world, rank):
     server_span = max(i.t_done for i in sinf.values()) - min(i.t_submit for i in sinf.values())
     same = all(all(torch.equal(a, b) for a, b in zip(p, q))
                for p, q in zip(res["plain"]["pop"], res["batched"]["pop"]))
+    # each run's device time alone (plain arm): how the batched time compares
+    # with the largest run (a lower bound) and with the sum of all runs
+    solo = [a.elapsed_time(b) / 1e3 for a, b in run_ev]
+    big = [t for t, c in zip(solo, cfgs) if c.N >= 3000]
     if rank != 0:
         return None
     R = len(cfgs)
@@ -714,6 +722,8 @@ def batched_core(n, torch, stream, n_runs, gens, warmup, dist, world, rank):
         "plain": {"value": world * R / p["s"], "unit": "runs/s", "ms": p["s"] * 1e3,
                   "gpu_launches": p["launches"]},
         "batched_vs_plain": p["s"] / b["s"],
+        "plain_solo_s": {"largest_run": max(solo), "runs_N_ge_3000": sum(big), "runs_N_lt_3000": sum(solo) - sum(big),
+                         "largest5": sorted((round(t, 4) for t in solo), reverse=True)[:5]},
         "server_streams": {"value": world * R / server_span, "unit": "runs/s", "wall_s": server_s,
                            "note": "the same runs submitted at once to the run server (one stream "
                                    "per run, 8 generations per launch batch, no join per generation)"},
