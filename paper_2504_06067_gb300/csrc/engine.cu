@@ -722,6 +722,7 @@ nsga3_status init_attributes(nsga3_ctx* ctx)
     CK(peel_init_attributes());
     CK(assoc_init_attributes());
     CK(norm_init_attributes());
+    CK(dom_init_attributes());
     g_attr_done = true;
     return NSGA3_OK;
 }

@@ -294,66 +294,114 @@ __device__ __forceinline__ void put_block(const RunView& v, size_t at, uint32_t 
     if (lane_id() == 0 && nzw) atomicOr(&nzw[byte >> 2], 1u << (8 * (byte & 3) + bit));
 }
 
-// A CTA takes a 256 x 256 tile of the upper block triangle (8 x 8 blocks of
-// 32) from the tile list.  The boxes and keys of the tile's 16 blocks are
-// staged in shared memory; 64 threads decide the 64 block pairs; the pairs
-// to test go on a shared work list, where two row blocks (2r, 2r + 1) that
-// take the same one-direction test against one column block form a single
-// entry (one column broadcast from shared memory then serves 64 pairs), and
-// the costlier entries (both-way tests, row pairs) come first.  The warps
-// take entries in turn: block pairs differ widely in cost after the pruning,
-// and a fixed assignment left warps idle at the tile's barrier.  Per entry
-// the lanes hold their rows' objectives in registers.
+// Asynchronous copies into shared memory (cp.async: the data lands while
+// the CTA keeps working; wait_all + a barrier make it visible to all).
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Shared memory of k_dominance (dynamic): two buffers, each holding a
+// tile's 256 row points, 256 column points (M4 floats each) and its 16
+// block boxes and key ranges.
+template <int M>
+__host__ __device__ constexpr size_t dom_buf_floats()
+{
+    return (size_t)2 * NSGA3_TILE * ((M + 3) & ~3) + 16 * 2 * ((M + 3) & ~3) + 16 * 2;
+}
+template <int M>
+__host__ __device__ constexpr size_t dom_smem_bytes()
+{
+    return 2 * dom_buf_floats<M>() * sizeof(float);
+}
+
+// A CTA takes 256 x 256 tiles of the upper block triangle (8 x 8 blocks of
+// 32) from the tile list, two at a time in flight: while its warps test the
+// block pairs of one tile, the points, block boxes and key ranges of its
+// next tile are copied into the other buffer (cp.async).  Between the two
+// tiles one warp decides the next tile's 64 block pairs from the staged
+// boxes and puts the pairs to test on a shared work list, where two row
+// blocks (2r, 2r + 1) that take the same one-direction test against one
+// column block form a single entry (one column broadcast from shared memory
+// then serves 64 pairs), and the costlier entries (both-way tests, row
+// pairs) come first; the other warps meanwhile flush the finished tile's
+// dominator counts and bitmap bytes.  Two barriers per tile.  The warps take
+// entries in turn: block pairs differ widely in cost after the pruning, and
+// a fixed assignment left warps idle at the tile's barrier.  Per entry the
+// lanes hold their rows' objectives in registers.
 template <int M>
 __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
 {
     constexpr int M4 = (M + 3) & ~3;
-    __shared__ __align__(16) float srow[NSGA3_TILE * M4];
-    __shared__ __align__(16) float scol[NSGA3_TILE * M4];
-    __shared__ float sbox[16][2 * M4];  // blocks 0..7 rows, 8..15 columns: min, then max
-    __shared__ uint32_t skey[16][2];
+    constexpr size_t BUF = dom_buf_floats<M>();
+    extern __shared__ __align__(16) float dsm[];
     __shared__ unsigned char smode[64];
-    __shared__ int s_tile[2];
     __shared__ int rowcnt[NSGA3_TILE];  // dominators found for the tile's row points
     __shared__ int colcnt[NSGA3_TILE];  // ... for its column points
-    __shared__ unsigned nzw[4];         // dnz bytes: 0..7 row blocks (I, J), 8..15 column blocks (J, I)
-    __shared__ unsigned mcount[6];      // block pairs of this tile by mode
+    __shared__ unsigned nzw[2][4];      // per buffer, dnz bytes: 0..7 row blocks (I, J), 8..15 column blocks (J, I)
     // entries: (mode << 7) | (pair << 6) | (row block << 3) | column block
     __shared__ unsigned short work[64];
     __shared__ int nheavy, nlight;      // heavy entries from the front, light ones from the back
     if (read_status(v.ctrl)) return;
     const int T = v.ld / NSGA3_TILE;
     const int ntile = *(volatile const int32_t*)&v.ctrl->ntile;
-    const int warp = threadIdx.x >> 5, lane = lane_id();
-    // persistent: the CTAs take the listed tiles in turn
-    for (int it = blockIdx.x; it < ntile; it += gridDim.x) {
-        rowcnt[threadIdx.x] = 0;
-        colcnt[threadIdx.x] = 0;
-        if (threadIdx.x < 4) nzw[threadIdx.x] = 0u;
-        if (threadIdx.x < 6) mcount[threadIdx.x] = 0u;
-        if (threadIdx.x == 0) {
-            nheavy = 0;
-            nlight = 0;
-            decode_tile(v.tlist[it], T, s_tile[0], s_tile[1]);
-        }
-        __syncthreads();
-        const int ti = s_tile[0], tj = s_tile[1];
-        const int r0 = ti * NSGA3_TILE, c0 = tj * NSGA3_TILE;
-        for (int e = threadIdx.x; e < 16 * 2 * M4; e += blockDim.x) {
-            const int b = e / (2 * M4), k = e - b * 2 * M4;
+    if ((int)blockIdx.x >= ntile) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
+    auto srow_of = [&](int buf) { return dsm + buf * BUF; };
+    auto scol_of = [&](int buf) { return dsm + buf * BUF + NSGA3_TILE * M4; };
+    auto sbox_of = [&](int buf) { return dsm + buf * BUF + 2 * NSGA3_TILE * M4; };  // [16][2 M4]
+    auto skey_of = [&](int buf) {
+        return reinterpret_cast<uint32_t*>(dsm + buf * BUF + 2 * NSGA3_TILE * M4 + 16 * 2 * M4);  // [16][2]
+    };
+    // copies of tile `it` into buffer `buf` (every thread issues its share)
+    auto prefetch = [&](int it, int buf) {
+        int ti, tj;
+        decode_tile(v.tlist[it], T, ti, tj);
+        float* sb = sbox_of(buf);
+        for (int e = tid; e < 16 * (2 * M4 / 4); e += blockDim.x) {
+            const int b = e / (2 * M4 / 4), k4 = e - b * (2 * M4 / 4);
             const int blk = b < 8 ? ti * 8 + b : tj * 8 + (b - 8);
-            sbox[b][k] = v.bbox[(size_t)blk * 2 * M4 + k];
+            cp_async16(sb + b * 2 * M4 + 4 * k4, v.bbox + (size_t)blk * 2 * M4 + 4 * k4);
         }
-        if (threadIdx.x < 32) {
-            const int b = threadIdx.x >> 1;
-            const int blk = b < 8 ? ti * 8 + b : tj * 8 + (b - 8);
-            skey[b][threadIdx.x & 1] = v.bkey[2 * blk + (threadIdx.x & 1)];
+        if (tid < 16) {
+            const int blk = tid < 8 ? ti * 8 + tid : tj * 8 + (tid - 8);
+            cp_async8(skey_of(buf) + 2 * tid, v.bkey + 2 * (size_t)blk);
         }
-        __syncthreads();
-        if (threadIdx.x < 64) {
-            // block pair (row block ri, column block cb) of the tile (see
-            // block_pair_mode for the tests)
-            const int ri = threadIdx.x >> 3, cb = threadIdx.x & 7;
+        // Fp holds -0.0 as +0.0, so equal values subtract to +0.0
+        float* dr = srow_of(buf);
+        float* dc = scol_of(buf);
+        const float* gr = v.Fp + (size_t)ti * NSGA3_TILE * M;
+        const float* gc = v.Fp + (size_t)tj * NSGA3_TILE * M;
+        for (int e = tid; e < NSGA3_TILE * M; e += blockDim.x) {
+            const int p = e / M, q = e - p * M;
+            cp_async4(dr + p * M4 + q, gr + e);
+            cp_async4(dc + p * M4 + q, gc + e);
+        }
+        cp_async_commit();
+    };
+    // one warp: the modes of the 64 block pairs of the tile in `buf` (see
+    // block_pair_mode for the tests) and the work list
+    auto decide = [&](int buf, int ti, int tj) {
+        const float* sb = sbox_of(buf);
+        const uint32_t* sk = skey_of(buf);
+        unsigned cnt5 = 0u;  // lane q < 5: block pairs of mode q + 1
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int pidx = lane + 32 * h;
+            const int ri = pidx >> 3, cb = pidx & 7;
             const int ib = ti * 8 + ri, jb = tj * 8 + cb;
             int mode;
             if (jb < ib)
@@ -363,15 +411,15 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
             else if (jb * 32 >= v.n2)
                 mode = BP_ZERO;  // a column block of padding only
             else {
-                const float* bi = sbox[ri];
-                const float* bj = sbox[8 + cb];
+                const float* bi = sb + ri * 2 * M4;
+                const float* bj = sb + (8 + cb) * 2 * M4;
                 bool fwd = true, bwd = true;
 #pragma unroll
                 for (int q = 0; q < M; ++q) {
                     fwd = fwd && bi[q] <= bj[M4 + q];  // NaN (padding only) fails
                     bwd = bwd && bj[q] <= bi[M4 + q];
                 }
-                bwd = bwd && !(skey[ri][1] < skey[8 + cb][0]);
+                bwd = bwd && !(sk[2 * ri + 1] < sk[2 * (8 + cb)]);
                 const bool f0sep = bi[M4] < bj[0];
                 mode = (!fwd && !bwd) ? BP_ZERO
                        : (fwd && f0sep) ? BP_FAST0
@@ -379,133 +427,172 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
                        : !fwd           ? BP_FASTR
                                         : BP_FULL;
             }
-            smode[threadIdx.x] = (unsigned char)mode;
-            if (mode > BP_SKIP) atomicAdd(&mcount[mode - 1], 1u);
-        }
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            // row pair rp = (2 rp, 2 rp + 1) against column block cb
-            const int rp = threadIdx.x >> 3, cb = threadIdx.x & 7;
-            const int a = smode[(2 * rp) * 8 + cb], b = smode[(2 * rp + 1) * 8 + cb];
-            if (a == b && (a == BP_FAST0 || a == BP_FASTK)) {
-                work[atomicAdd(&nheavy, 1)] = (unsigned short)((a << 7) | (1 << 6) | ((2 * rp) << 3) | cb);
-            } else {
+            smode[pidx] = (unsigned char)mode;
 #pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const int md = r ? b : a;
-                    const unsigned short e = (unsigned short)((md << 7) | ((2 * rp + r) << 3) | cb);
-                    if (md == BP_FULL)
-                        work[atomicAdd(&nheavy, 1)] = e;
-                    else if (md > BP_ZERO)
-                        work[63 - atomicAdd(&nlight, 1)] = e;
-                }
+            for (int md = 1; md <= 5; ++md) {
+                const unsigned c = __popc(__ballot_sync(0xffffffffu, mode == md));
+                if (lane == md - 1) cnt5 += c;
             }
         }
-        __syncthreads();
+        if (lane < 5 && cnt5) atomicAdd(&v.ctrl->domstat[lane], (unsigned long long)cnt5);
+        __syncwarp();
+        // row pair rp = (2 rp, 2 rp + 1) against column block cb
+        const int rp = lane >> 3, cb = lane & 7;
+        const int a = smode[(2 * rp) * 8 + cb], b = smode[(2 * rp + 1) * 8 + cb];
+        const bool pair = a == b && (a == BP_FAST0 || a == BP_FASTK);
+        const int hcnt = pair ? 1 : (a == BP_FULL) + (b == BP_FULL);
+        const int lcnt = pair ? 0 : (a > BP_ZERO && a != BP_FULL) + (b > BP_ZERO && b != BP_FULL);
+        int hoff = hcnt, loff = lcnt;  // inclusive scans over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, hoff, o);
+            const int y = __shfl_up_sync(0xffffffffu, loff, o);
+            if (lane >= o) {
+                hoff += x;
+                loff += y;
+            }
+        }
+        const int htot = __shfl_sync(0xffffffffu, hoff, 31), ltot = __shfl_sync(0xffffffffu, loff, 31);
+        hoff -= hcnt;
+        loff -= lcnt;
+        if (pair) {
+            work[hoff] = (unsigned short)((a << 7) | (1 << 6) | ((2 * rp) << 3) | cb);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int md = r ? b : a;
+                const unsigned short e = (unsigned short)((md << 7) | ((2 * rp + r) << 3) | cb);
+                if (md == BP_FULL)
+                    work[hoff++] = e;
+                else if (md > BP_ZERO)
+                    work[63 - loff++] = e;
+            }
+        }
+        if (lane == 0) {
+            nheavy = htot;
+            nlight = ltot;
+        }
+    };
+
+    int cur = 0;
+    int it = blockIdx.x;
+    int ti, tj;
+    decode_tile(v.tlist[it], T, ti, tj);
+    prefetch(it, 0);
+    rowcnt[tid] = 0;
+    colcnt[tid] = 0;
+    if (tid < 8) nzw[tid >> 2][tid & 3] = 0u;
+    cp_async_wait_all();
+    __syncthreads();
+    if (warp == 0) decide(0, ti, tj);
+    __syncthreads();
+    for (;;) {
+        const int nit = it + gridDim.x;
+        const bool more = nit < ntile;
+        if (more) prefetch(nit, cur ^ 1);  // the other buffer's tile was finished a tile ago
         const int nh = nheavy, nl = nlight, nwork = nh + nl;
-        if (threadIdx.x < 5 && mcount[threadIdx.x])
-            atomicAdd(&v.ctrl->domstat[threadIdx.x], (unsigned long long)mcount[threadIdx.x]);
-        unsigned* nz = v.dnz ? nzw : nullptr;
-        if (nwork > 0) {
-            // a tile without any block pair to test stages nothing
-            // Fp holds -0.0 as +0.0, so equal values subtract to +0.0
-            for (int e = threadIdx.x; e < NSGA3_TILE * M; e += blockDim.x) {
-                const int p = e / M, q = e - p * M;
-                srow[p * M4 + q] = v.Fp[(size_t)r0 * M + e];
-                scol[p * M4 + q] = v.Fp[(size_t)c0 * M + e];
-            }
-            __syncthreads();
-            for (int t = warp; t < nwork; t += 8) {
-                const unsigned e = work[t < nh ? t : 64 - nwork + t];
-                const int mode = e >> 7, two = (e >> 6) & 1, ri = (e >> 3) & 7, cb = e & 7;
-                const int ib = ti * 8 + ri, jb = tj * 8 + cb;
-                const float* colp = scol + cb * 32 * M4;
-                // One direction only: "no f_iq > f_jq" (or the reverse) decides,
-                // and a NaN padding point would pass it (its differences are
-                // NaN with a clear sign bit), so the bits of padding rows and
-                // columns are masked (the two-way test needs no mask: a NaN
-                // gives the same sign both ways, hence no bit).
-                const int cv = v.n2 - jb * 32;
-                const uint32_t colvalid = cv >= 32 ? 0xffffffffu : (cv > 0 ? (1u << cv) - 1u : 0u);
-                if (two) {
-                    // rows ri and ri + 1, "row dominates column" only
-                    float f0[M], f1[M];
+        unsigned* nz = v.dnz ? nzw[cur] : nullptr;
+        const float* srow = srow_of(cur);
+        const float* scol = scol_of(cur);
+        for (int t = warp; t < nwork; t += 8) {
+            const unsigned e = work[t < nh ? t : 64 - nwork + t];
+            const int mode = e >> 7, two = (e >> 6) & 1, ri = (e >> 3) & 7, cb = e & 7;
+            const int ib = ti * 8 + ri, jb = tj * 8 + cb;
+            const float* colp = scol + cb * 32 * M4;
+            // One direction only: "no f_iq > f_jq" (or the reverse) decides,
+            // and a NaN padding point would pass it (its differences are
+            // NaN with a clear sign bit), so the bits of padding rows and
+            // columns are masked (the two-way test needs no mask: a NaN
+            // gives the same sign both ways, hence no bit).
+            const int cv = v.n2 - jb * 32;
+            const uint32_t colvalid = cv >= 32 ? 0xffffffffu : (cv > 0 ? (1u << cv) - 1u : 0u);
+            if (two) {
+                // rows ri and ri + 1, "row dominates column" only
+                float f0[M], f1[M];
 #pragma unroll
-                    for (int q = 0; q < M; ++q) {
-                        f0[q] = srow[(ri * 32 + lane) * M4 + q];
-                        f1[q] = srow[((ri + 1) * 32 + lane) * M4 + q];
-                    }
-                    uint32_t acc0, acc1;
-                    if (mode == BP_FAST0)
-                        block_one_dir<1, M, M4, true>(f0, f1, colp, acc0, acc1);
-                    else
-                        block_one_dir<0, M, M4, true>(f0, f1, colp, acc0, acc1);
-                    const uint32_t d0 = ib * 32 + lane < v.n2 ? ~acc0 & colvalid : 0u;
-                    const uint32_t d1 = (ib + 1) * 32 + lane < v.n2 ? ~acc1 & colvalid : 0u;
-                    const uint32_t t0 = warp_transpose32(d0), t1 = warp_transpose32(d1);
-                    put_block(v, (size_t)ib * v.ld + jb * 32 + lane, t0, nz, ri, cb);
-                    put_block(v, (size_t)(ib + 1) * v.ld + jb * 32 + lane, t1, nz, ri + 1, cb);
-                    const int cc = __popc(t0) + __popc(t1);
-                    if (cc) atomicAdd(&colcnt[cb * 32 + lane], cc);
-                    continue;
+                for (int q = 0; q < M; ++q) {
+                    f0[q] = srow[(ri * 32 + lane) * M4 + q];
+                    f1[q] = srow[((ri + 1) * 32 + lane) * M4 + q];
                 }
-                float fi[M];
+                uint32_t acc0, acc1;
+                if (mode == BP_FAST0)
+                    block_one_dir<1, M, M4, true>(f0, f1, colp, acc0, acc1);
+                else
+                    block_one_dir<0, M, M4, true>(f0, f1, colp, acc0, acc1);
+                const uint32_t d0 = ib * 32 + lane < v.n2 ? ~acc0 & colvalid : 0u;
+                const uint32_t d1 = (ib + 1) * 32 + lane < v.n2 ? ~acc1 & colvalid : 0u;
+                const uint32_t t0 = warp_transpose32(d0), t1 = warp_transpose32(d1);
+                put_block(v, (size_t)ib * v.ld + jb * 32 + lane, t0, nz, ri, cb);
+                put_block(v, (size_t)(ib + 1) * v.ld + jb * 32 + lane, t1, nz, ri + 1, cb);
+                const int cc = __popc(t0) + __popc(t1);
+                if (cc) atomicAdd(&colcnt[cb * 32 + lane], cc);
+                continue;
+            }
+            float fi[M];
 #pragma unroll
-                for (int q = 0; q < M; ++q) fi[q] = srow[(ri * 32 + lane) * M4 + q];
-                uint32_t dij = 0u, dji = 0u;
-                if (mode == BP_FAST0 || mode == BP_FASTK || mode == BP_FASTR) {
-                    const bool rowvalid = ib * 32 + lane < v.n2;
-                    uint32_t acc = 0u, unused;
-                    if (mode == BP_FAST0) {
-                        block_one_dir<1, M, M4, false>(fi, fi, colp, acc, unused);
-                        dij = rowvalid ? ~acc & colvalid : 0u;
-                    } else if (mode == BP_FASTK) {
-                        block_one_dir<0, M, M4, false>(fi, fi, colp, acc, unused);
-                        dij = rowvalid ? ~acc & colvalid : 0u;
-                    } else {
-                        // column j dominates row i: no f_jq > f_iq (the vectors differ)
+            for (int q = 0; q < M; ++q) fi[q] = srow[(ri * 32 + lane) * M4 + q];
+            uint32_t dij = 0u, dji = 0u;
+            if (mode == BP_FAST0 || mode == BP_FASTK || mode == BP_FASTR) {
+                const bool rowvalid = ib * 32 + lane < v.n2;
+                uint32_t acc = 0u, unused;
+                if (mode == BP_FAST0) {
+                    block_one_dir<1, M, M4, false>(fi, fi, colp, acc, unused);
+                    dij = rowvalid ? ~acc & colvalid : 0u;
+                } else if (mode == BP_FASTK) {
+                    block_one_dir<0, M, M4, false>(fi, fi, colp, acc, unused);
+                    dij = rowvalid ? ~acc & colvalid : 0u;
+                } else {
+                    // column j dominates row i: no f_jq > f_iq (the vectors differ)
 #pragma unroll 4
-                        for (int k = 31; k >= 0; --k) {
-                            const float* fj = colp + k * M4;
-                            acc = __funnelshift_l(any_greater<0, M>(fi, fj), acc, 1);
-                        }
-                        dji = rowvalid ? ~acc & colvalid : 0u;
+                    for (int k = 31; k >= 0; --k) {
+                        const float* fj = colp + k * M4;
+                        acc = __funnelshift_l(any_greater<0, M>(fi, fj), acc, 1);
                     }
-                } else {
-                    block_full<M, M4>(fi, colp, dij, dji);
+                    dji = rowvalid ? ~acc & colvalid : 0u;
                 }
-                // column i = ib*32 + lane, dominators j in block jb: Dom block (jb, ib)
-                if (jb != ib) {
-                    put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, 8 + cb, ri);
-                    const uint32_t tr = warp_transpose32(dij);
-                    put_block(v, (size_t)ib * v.ld + jb * 32 + lane, tr, nz, ri, cb);
-                    if (tr) atomicAdd(&colcnt[cb * 32 + lane], __popc(tr));
-                } else {
-                    put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, ri, cb);
-                }
-                if (dji) atomicAdd(&rowcnt[ri * 32 + lane], __popc(dji));
+            } else {
+                block_full<M, M4>(fi, colp, dij, dji);
             }
+            // column i = ib*32 + lane, dominators j in block jb: Dom block (jb, ib)
+            if (jb != ib) {
+                put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, 8 + cb, ri);
+                const uint32_t tr = warp_transpose32(dij);
+                put_block(v, (size_t)ib * v.ld + jb * 32 + lane, tr, nz, ri, cb);
+                if (tr) atomicAdd(&colcnt[cb * 32 + lane], __popc(tr));
+            } else {
+                put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, ri, cb);
+            }
+            if (dji) atomicAdd(&rowcnt[ri * 32 + lane], __popc(dji));
         }
-        __syncthreads();
-        const int t = threadIdx.x;
+        cp_async_wait_all();
+        __syncthreads();  // the tile's tests are done and the next tile is staged
         if (v.dnz) {
             // this tile owns bytes dnz[I][tj] (I a row block) and dnz[J][ti] (J a
             // column block), one byte each; on the diagonal they are the same bytes
-            const unsigned char* nzb = reinterpret_cast<const unsigned char*>(nzw);
-            if (t < 8) {
-                unsigned char x = nzb[t];
-                if (ti == tj) x |= nzb[8 + t];
-                v.dnz[(size_t)(ti * 8 + t) * v.NB8 + tj] = x;
-            } else if (t < 16 && ti != tj) {
-                v.dnz[(size_t)(tj * 8 + (t - 8)) * v.NB8 + ti] = nzb[t];
+            const unsigned char* nzb = reinterpret_cast<const unsigned char*>(nzw[cur]);
+            if (tid < 8) {
+                unsigned char x = nzb[tid];
+                if (ti == tj) x |= nzb[8 + tid];
+                v.dnz[(size_t)(ti * 8 + tid) * v.NB8 + tj] = x;
+            } else if (tid < 16 && ti != tj) {
+                v.dnz[(size_t)(tj * 8 + (tid - 8)) * v.NB8 + ti] = nzb[tid];
             }
         }
-        if (nwork > 0) {
-            // dominator counts of the peel's first pass: one global add per point of the tile
-            if (rowcnt[t]) atomicAdd(&v.cnt[r0 + t], rowcnt[t]);
-            if (colcnt[t]) atomicAdd(&v.cnt[c0 + t], colcnt[t]);
+        if (tid >= 32 && tid < 36) nzw[cur ^ 1][tid - 32] = 0u;  // the next tile's bytes
+        // dominator counts of the peel's first pass: one global add per point of the tile
+        {
+            const int rc = rowcnt[tid], cc = colcnt[tid];
+            if (rc) atomicAdd(&v.cnt[ti * NSGA3_TILE + tid], rc);
+            if (cc) atomicAdd(&v.cnt[tj * NSGA3_TILE + tid], cc);
+            rowcnt[tid] = 0;
+            colcnt[tid] = 0;
         }
-        __syncthreads();  // the shared arrays are reset for the next tile
+        if (!more) break;
+        decode_tile(v.tlist[nit], T, ti, tj);
+        if (warp == 0) decide(cur ^ 1, ti, tj);
+        __syncthreads();  // the work list and the cleared counts are ready
+        cur ^= 1;
+        it = nit;
     }
 }
 
@@ -718,17 +805,39 @@ cudaError_t launch_dom_m(const RunView& v, cudaStream_t s)
     if (e != cudaSuccess) return e;
     // persistent CTAs over the listed tiles, as many as are resident at once
     static int occ = 0;  // per M; the same value whatever the run
-    if (occ <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dominance<M>, 256, 0) != cudaSuccess) {
+    if (occ <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dominance<M>, 256,
+                                                                  dom_smem_bytes<M>()) != cudaSuccess) {
         cudaGetLastError();
         occ = 4;
     }
     long long grid = (long long)(occ > 0 ? occ : 4) * v.num_sms;
     if (grid > tiles) grid = tiles;
-    k_dominance<M><<<(unsigned)grid, 256, 0, s>>>(v);
+    k_dominance<M><<<(unsigned)grid, 256, dom_smem_bytes<M>(), s>>>(v);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+template <int M>
+cudaError_t dom_attr_m()
+{
+    return cudaFuncSetAttribute(k_dominance<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dom_smem_bytes<M>());
+}
+
+cudaError_t dom_init_attributes()
+{
+    cudaError_t e = dom_attr_m<2>();
+    if (e == cudaSuccess) e = dom_attr_m<3>();
+    if (e == cudaSuccess) e = dom_attr_m<4>();
+    if (e == cudaSuccess) e = dom_attr_m<5>();
+    if (e == cudaSuccess) e = dom_attr_m<6>();
+    if (e == cudaSuccess) e = dom_attr_m<7>();
+    if (e == cudaSuccess) e = dom_attr_m<8>();
+    if (e == cudaSuccess) e = dom_attr_m<9>();
+    if (e == cudaSuccess) e = dom_attr_m<10>();
+    return e;
+}
 
 cudaError_t launch_dominance(const RunView& v, cudaStream_t s)
 {

@@ -24,6 +24,7 @@ cudaError_t launch_wait_probe(const RunView& v, cudaStream_t s);
 cudaError_t launch_check_finite(const RunView& v, cudaStream_t s);
 cudaError_t launch_sort(const RunView& v, int num_sms, cudaStream_t s);
 cudaError_t launch_dominance(const RunView& v, cudaStream_t s);
+cudaError_t dom_init_attributes();
 // every peel pass in one cooperative launch (grid barrier between passes)
 cudaError_t launch_peel(const RunView& v, int num_sms, cudaStream_t s);
 cudaError_t peel_init_attributes();
