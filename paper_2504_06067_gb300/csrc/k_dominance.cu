@@ -330,18 +330,19 @@ __host__ __device__ constexpr size_t dom_smem_bytes()
 
 // A CTA takes 256 x 256 tiles of the upper block triangle (8 x 8 blocks of
 // 32) from the tile list, two at a time in flight: while its warps test the
-// block pairs of one tile, the points, block boxes and key ranges of its
-// next tile are copied into the other buffer (cp.async).  Between the two
-// tiles one warp decides the next tile's 64 block pairs from the staged
-// boxes and puts the pairs to test on a shared work list, where two row
-// blocks (2r, 2r + 1) that take the same one-direction test against one
+// block pairs of one tile, the points of its next tile are copied into the
+// other buffer (cp.async), and warp 0 first copies the next tile's 16 block
+// boxes and key ranges itself, decides its 64 block pairs from them and
+// puts the pairs to test on the next work list, then joins the tests.  Two
+// row blocks (2r, 2r + 1) that take the same one-direction test against one
 // column block form a single entry (one column broadcast from shared memory
 // then serves 64 pairs), and the costlier entries (both-way tests, row
-// pairs) come first; the other warps meanwhile flush the finished tile's
-// dominator counts and bitmap bytes.  Two barriers per tile.  The warps take
-// entries in turn: block pairs differ widely in cost after the pruning, and
-// a fixed assignment left warps idle at the tile's barrier.  Per entry the
-// lanes hold their rows' objectives in registers.
+// pairs) come first; the warps take entries from a shared counter, so
+// block pairs of very different cost after the pruning balance over the
+// warps.  One barrier per tile: after it the threads flush the finished
+// tile's dominator counts and bitmap bytes (both kept per buffer) and go on
+// to the next tile.  Per entry the lanes hold their rows' objectives in
+// registers.
 template <int M>
 __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
 {
@@ -349,12 +350,13 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
     constexpr size_t BUF = dom_buf_floats<M>();
     extern __shared__ __align__(16) float dsm[];
     __shared__ unsigned char smode[64];
-    __shared__ int rowcnt[NSGA3_TILE];  // dominators found for the tile's row points
-    __shared__ int colcnt[NSGA3_TILE];  // ... for its column points
-    __shared__ unsigned nzw[2][4];      // per buffer, dnz bytes: 0..7 row blocks (I, J), 8..15 column blocks (J, I)
+    __shared__ int rowcnt[2][NSGA3_TILE];  // per buffer: dominators found for the tile's row points
+    __shared__ int colcnt[2][NSGA3_TILE];  // ... for its column points
+    __shared__ unsigned nzw[2][4];         // per buffer, dnz bytes: 0..7 row blocks (I, J), 8..15 column blocks (J, I)
     // entries: (mode << 7) | (pair << 6) | (row block << 3) | column block
-    __shared__ unsigned short work[64];
-    __shared__ int nheavy, nlight;      // heavy entries from the front, light ones from the back
+    __shared__ unsigned short work[2][64];
+    __shared__ int nheavy[2], nlight[2];   // heavy entries from the front, light ones from the back
+    __shared__ int taken[2];               // entries handed out
     if (read_status(v.ctrl)) return;
     const int T = v.ld / NSGA3_TILE;
     const int ntile = *(volatile const int32_t*)&v.ctrl->ntile;
@@ -366,21 +368,9 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
     auto skey_of = [&](int buf) {
         return reinterpret_cast<uint32_t*>(dsm + buf * BUF + 2 * NSGA3_TILE * M4 + 16 * 2 * M4);  // [16][2]
     };
-    // copies of tile `it` into buffer `buf` (every thread issues its share)
-    auto prefetch = [&](int it, int buf) {
-        int ti, tj;
-        decode_tile(v.tlist[it], T, ti, tj);
-        float* sb = sbox_of(buf);
-        for (int e = tid; e < 16 * (2 * M4 / 4); e += blockDim.x) {
-            const int b = e / (2 * M4 / 4), k4 = e - b * (2 * M4 / 4);
-            const int blk = b < 8 ? ti * 8 + b : tj * 8 + (b - 8);
-            cp_async16(sb + b * 2 * M4 + 4 * k4, v.bbox + (size_t)blk * 2 * M4 + 4 * k4);
-        }
-        if (tid < 16) {
-            const int blk = tid < 8 ? ti * 8 + tid : tj * 8 + (tid - 8);
-            cp_async8(skey_of(buf) + 2 * tid, v.bkey + 2 * (size_t)blk);
-        }
-        // Fp holds -0.0 as +0.0, so equal values subtract to +0.0
+    // the points of tile (ti, tj) into buffer `buf` (every thread its share);
+    // Fp holds -0.0 as +0.0, so equal values subtract to +0.0
+    auto copy_points = [&](int ti, int tj, int buf) {
         float* dr = srow_of(buf);
         float* dc = scol_of(buf);
         const float* gr = v.Fp + (size_t)ti * NSGA3_TILE * M;
@@ -392,11 +382,24 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
         }
         cp_async_commit();
     };
-    // one warp: the modes of the 64 block pairs of the tile in `buf` (see
-    // block_pair_mode for the tests) and the work list
-    auto decide = [&](int buf, int ti, int tj) {
-        const float* sb = sbox_of(buf);
-        const uint32_t* sk = skey_of(buf);
+    // warp 0: the boxes and keys of tile (ti, tj) into buffer `buf`, waited for
+    // (a warp's own copies), then the modes of its 64 block pairs (see
+    // block_pair_mode for the tests) and its work list
+    auto decide = [&](int ti, int tj, int buf) {
+        float* sb = sbox_of(buf);
+        uint32_t* sk = skey_of(buf);
+        for (int e = lane; e < 16 * (2 * M4 / 4); e += 32) {
+            const int b = e / (2 * M4 / 4), k4 = e - b * (2 * M4 / 4);
+            const int blk = b < 8 ? ti * 8 + b : tj * 8 + (b - 8);
+            cp_async16(sb + b * 2 * M4 + 4 * k4, v.bbox + (size_t)blk * 2 * M4 + 4 * k4);
+        }
+        if (lane < 16) {
+            const int blk = lane < 8 ? ti * 8 + lane : tj * 8 + (lane - 8);
+            cp_async8(sk + 2 * lane, v.bkey + 2 * (size_t)blk);
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncwarp();
         unsigned cnt5 = 0u;  // lane q < 5: block pairs of mode q + 1
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -456,21 +459,22 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
         hoff -= hcnt;
         loff -= lcnt;
         if (pair) {
-            work[hoff] = (unsigned short)((a << 7) | (1 << 6) | ((2 * rp) << 3) | cb);
+            work[buf][hoff] = (unsigned short)((a << 7) | (1 << 6) | ((2 * rp) << 3) | cb);
         } else {
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 const int md = r ? b : a;
                 const unsigned short e = (unsigned short)((md << 7) | ((2 * rp + r) << 3) | cb);
                 if (md == BP_FULL)
-                    work[hoff++] = e;
+                    work[buf][hoff++] = e;
                 else if (md > BP_ZERO)
-                    work[63 - loff++] = e;
+                    work[buf][63 - loff++] = e;
             }
         }
         if (lane == 0) {
-            nheavy = htot;
-            nlight = ltot;
+            nheavy[buf] = htot;
+            nlight[buf] = ltot;
+            taken[buf] = 0;
         }
     };
 
@@ -478,24 +482,36 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
     int it = blockIdx.x;
     int ti, tj;
     decode_tile(v.tlist[it], T, ti, tj);
-    prefetch(it, 0);
-    rowcnt[tid] = 0;
-    colcnt[tid] = 0;
+    copy_points(ti, tj, 0);
+    rowcnt[0][tid] = 0;
+    colcnt[0][tid] = 0;
+    rowcnt[1][tid] = 0;
+    colcnt[1][tid] = 0;
     if (tid < 8) nzw[tid >> 2][tid & 3] = 0u;
+    if (warp == 0) decide(ti, tj, 0);
     cp_async_wait_all();
-    __syncthreads();
-    if (warp == 0) decide(0, ti, tj);
     __syncthreads();
     for (;;) {
         const int nit = it + gridDim.x;
         const bool more = nit < ntile;
-        if (more) prefetch(nit, cur ^ 1);  // the other buffer's tile was finished a tile ago
-        const int nh = nheavy, nl = nlight, nwork = nh + nl;
+        int nti = ti, ntj = tj;
+        if (more) {
+            decode_tile(v.tlist[nit], T, nti, ntj);
+            copy_points(nti, ntj, cur ^ 1);  // the other buffer's tile was finished a tile ago
+            if (warp == 0) decide(nti, ntj, cur ^ 1);
+        }
+        const int nh = nheavy[cur], nl = nlight[cur], nwork = nh + nl;
         unsigned* nz = v.dnz ? nzw[cur] : nullptr;
         const float* srow = srow_of(cur);
         const float* scol = scol_of(cur);
-        for (int t = warp; t < nwork; t += 8) {
-            const unsigned e = work[t < nh ? t : 64 - nwork + t];
+        int* rcnt = rowcnt[cur];
+        int* ccnt = colcnt[cur];
+        for (;;) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(&taken[cur], 1);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= nwork) break;
+            const unsigned e = work[cur][t < nh ? t : 64 - nwork + t];
             const int mode = e >> 7, two = (e >> 6) & 1, ri = (e >> 3) & 7, cb = e & 7;
             const int ib = ti * 8 + ri, jb = tj * 8 + cb;
             const float* colp = scol + cb * 32 * M4;
@@ -525,7 +541,7 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
                 put_block(v, (size_t)ib * v.ld + jb * 32 + lane, t0, nz, ri, cb);
                 put_block(v, (size_t)(ib + 1) * v.ld + jb * 32 + lane, t1, nz, ri + 1, cb);
                 const int cc = __popc(t0) + __popc(t1);
-                if (cc) atomicAdd(&colcnt[cb * 32 + lane], cc);
+                if (cc) atomicAdd(&ccnt[cb * 32 + lane], cc);
                 continue;
             }
             float fi[M];
@@ -558,41 +574,52 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
                 put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, 8 + cb, ri);
                 const uint32_t tr = warp_transpose32(dij);
                 put_block(v, (size_t)ib * v.ld + jb * 32 + lane, tr, nz, ri, cb);
-                if (tr) atomicAdd(&colcnt[cb * 32 + lane], __popc(tr));
+                if (tr) atomicAdd(&ccnt[cb * 32 + lane], __popc(tr));
             } else {
                 put_block(v, (size_t)jb * v.ld + ib * 32 + lane, dji, nz, ri, cb);
             }
-            if (dji) atomicAdd(&rowcnt[ri * 32 + lane], __popc(dji));
+            if (dji) atomicAdd(&rcnt[ri * 32 + lane], __popc(dji));
         }
         cp_async_wait_all();
-        __syncthreads();  // the tile's tests are done and the next tile is staged
-        if (v.dnz) {
+        __syncthreads();  // the tile's tests are done, the next tile is staged and decided
+        if (warp == 0) {
             // this tile owns bytes dnz[I][tj] (I a row block) and dnz[J][ti] (J a
-            // column block), one byte each; on the diagonal they are the same bytes
-            const unsigned char* nzb = reinterpret_cast<const unsigned char*>(nzw[cur]);
-            if (tid < 8) {
-                unsigned char x = nzb[tid];
-                if (ti == tj) x |= nzb[8 + tid];
-                v.dnz[(size_t)(ti * 8 + tid) * v.NB8 + tj] = x;
-            } else if (tid < 16 && ti != tj) {
-                v.dnz[(size_t)(tj * 8 + (tid - 8)) * v.NB8 + ti] = nzb[tid];
+            // column block), one byte each; on the diagonal they are the same
+            // bytes.  Lane 0 reads and clears the buffer's words (no other
+            // thread touches them before the buffer's next tile, a barrier later).
+            unsigned long long lo = 0ull, hi = 0ull;  // bytes 0..7 and 8..15
+            if (lane == 0) {
+                lo = (unsigned long long)nzw[cur][0] | ((unsigned long long)nzw[cur][1] << 32);
+                hi = (unsigned long long)nzw[cur][2] | ((unsigned long long)nzw[cur][3] << 32);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) nzw[cur][k] = 0u;
+            }
+            lo = __shfl_sync(0xffffffffu, lo, 0);
+            hi = __shfl_sync(0xffffffffu, hi, 0);
+            if (v.dnz) {
+                const int b8 = 8 * (lane & 7);
+                const unsigned char rb = (unsigned char)(lo >> b8), cbyte = (unsigned char)(hi >> b8);
+                if (lane < 8) {
+                    const unsigned char x = (ti == tj) ? (unsigned char)(rb | cbyte) : rb;
+                    v.dnz[(size_t)(ti * 8 + lane) * v.NB8 + tj] = x;
+                } else if (lane < 16 && ti != tj) {
+                    v.dnz[(size_t)(tj * 8 + (lane - 8)) * v.NB8 + ti] = cbyte;
+                }
             }
         }
-        if (tid >= 32 && tid < 36) nzw[cur ^ 1][tid - 32] = 0u;  // the next tile's bytes
         // dominator counts of the peel's first pass: one global add per point of the tile
         {
-            const int rc = rowcnt[tid], cc = colcnt[tid];
+            const int rc = rcnt[tid], cc = ccnt[tid];
             if (rc) atomicAdd(&v.cnt[ti * NSGA3_TILE + tid], rc);
             if (cc) atomicAdd(&v.cnt[tj * NSGA3_TILE + tid], cc);
-            rowcnt[tid] = 0;
-            colcnt[tid] = 0;
+            rcnt[tid] = 0;
+            ccnt[tid] = 0;
         }
         if (!more) break;
-        decode_tile(v.tlist[nit], T, ti, tj);
-        if (warp == 0) decide(cur ^ 1, ti, tj);
-        __syncthreads();  // the work list and the cleared counts are ready
         cur ^= 1;
         it = nit;
+        ti = nti;
+        tj = ntj;
     }
 }
 
