@@ -37,6 +37,13 @@ import sys
 import tempfile
 import time
 
+# Runs on separate streams (the run server: one stream per admitted run) share
+# the device's hardware work queues, 8 unless the process asks for more
+# before CUDA starts; with 64 runs in flight, 8 queues serialise kernels of
+# unrelated runs (the served prefix: 14.4 -> 15.4 runs/s with 32).  Graph
+# branches (batched runs) and single-stream runs are not affected.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)

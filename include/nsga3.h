@@ -350,7 +350,10 @@ typedef struct {
 
 /* Creates a server on the current device: one cudaMalloc of memory_budget
  * bytes, max_active slot streams (1..1024) and the worker thread.
- * max_active = 1 serves one run at a time (the plain path).
+ * max_active = 1 serves one run at a time (the plain path).  The slot
+ * streams share the device's hardware work queues (8 unless the process sets
+ * CUDA_DEVICE_MAX_CONNECTIONS, up to 32, before CUDA is initialised); with
+ * more slots than queues, kernels of unrelated runs can wait on one another.
  * Errors: EINVAL, ENOMEM (the budget cannot be allocated), ECUDA. */
 nsga3_status nsga3_server_create(uint64_t memory_budget, int max_active, int gens_per_launch,
                                  nsga3_server** out);
