@@ -291,8 +291,8 @@ def plain_measure(n, torch, cfg, K, warmup, stream, flush, seed, events, e2e_ste
         ok(n.nsga3_sync(ctx, sh))
         dom_ms = peel_ms = 0.0
         peel_rows = passes = niche_steps = n_launch = 0
-        dstat = (C.c_int64 * 6)()
-        dsum = [0] * 6
+        dstat = (C.c_int64 * 8)()
+        dsum = [0] * 8
         step_ms = []
         barrier(dist)
         torch.cuda.synchronize()
@@ -312,7 +312,7 @@ def plain_measure(n, torch, cfg, K, warmup, stream, flush, seed, events, e2e_ste
             ok(n.nsga3_get_selection_info(ctx, info))
             ok(n.nsga3_last_launches(ctx, C.byref(launches)))
             ok(n.nsga3_get_dominance_stats(ctx, dstat))
-            for t in range(6):
+            for t in range(8):
                 dsum[t] += dstat[t]
             passes += info[6]
             peel_rows += info[12]
@@ -382,18 +382,18 @@ def issue_probe(n, torch, stream):
 def roofline_of(cfg, avg_ms, peel_rows_per_step, probe, peaks, peak_kind, domstat=None):
     """Roofline of the dominant kernel (the dominance build, bound by issue,
     or the peel, bound by memory) from its average launch time.  The
-    dominance build (m <= 10) tests only the block pairs its bounding boxes
-    cannot rule out: the units one launch processes are those pairs (2m
-    compares each, as for every pair), counted by the kernel
-    (nsga3_get_dominance_stats); the rate over all n2(n2-1)/2 pairs is
-    reported beside it."""
+    dominance build (m <= 10) tests only the pairs that its block boxes and
+    its per-entry row and column tests cannot rule out: the units one launch
+    processes are the (lane, column) pairs it tests (2m compares each, as
+    for every pair), counted by the kernel (nsga3_get_dominance_stats); the
+    rate over all n2(n2-1)/2 pairs is reported beside it."""
     n2 = 2 * cfg.N
     pairs = n2 * (n2 - 1) / 2
     if avg_ms["dominance"] >= avg_ms["peel"]:
         all_ops = pairs * 2 * cfg.m  # FP32 compares: all(f_i <= f_j) and all(f_j <= f_i)
         tested = None
         if domstat is not None and sum(domstat[:5]) > 0:
-            tested = min(pairs, 1024.0 * sum(domstat[1:5]))
+            tested = min(pairs, float(domstat[6]))
         ops = (tested if tested is not None else pairs) * 2 * cfg.m
         sec = avg_ms["dominance"] / 1e3
         achieved = ops / sec / 1e12
@@ -407,14 +407,16 @@ def roofline_of(cfg, avg_ms, peel_rows_per_step, probe, peaks, peak_kind, domsta
         roof = {"kernel": "k_dominance<%d>" % cfg.m if cfg.m <= 10 else "k_dominance_gen", "bound": "alu",
                 "achieved": achieved, "peak": peak, "unit": "T/s (compares; issue slots)",
                 "frac": achieved / peak, "peak_source": src,
-                "algorithmic": ("tested pairs x 2m FP32 compares per launch (%.4g; 1,024 pairs per "
-                                "tested 32 x 32 block pair)" % ops) if tested is not None else
+                "algorithmic": ("tested pairs x 2m FP32 compares per launch (%.4g; the (lane, column) "
+                                "pairs the kernel tests, counted by it)" % ops) if tested is not None else
                                "n2(n2-1)/2 pairs x 2m FP32 compares per launch (%.4g)" % ops,
                 "launch_ms": avg_ms["dominance"],
                 "traffic": ncu_traffic("k_dominance", cfg.name)}
         if tested is not None:
             tot = float(sum(domstat[:5]))
             roof["pairs_tested_frac"] = tested / pairs
+            roof["block_pair_pairs_frac"] = min(pairs, 1024.0 * sum(domstat[1:5])) / pairs
+            roof["live_pairs_frac"] = float(domstat[7]) / pairs
             roof["block_pairs"] = {"zero": domstat[0] / tot, "one_direction_f0": domstat[1] / tot,
                                    "row_dom_col": domstat[2] / tot, "col_dom_row": domstat[3] / tot,
                                    "both": domstat[4] / tot, "tiles_skipped": int(domstat[5])}

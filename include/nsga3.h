@@ -242,12 +242,15 @@ nsga3_status nsga3_get_selection_info(nsga3_ctx* ctx, int32_t* info);
 nsga3_status nsga3_get_selection_paths(nsga3_ctx* ctx, uint32_t* paths);
 
 /* Work of the dominance build in the last selection (synchronous;
- * diagnostics, m <= 10, zeros above): stats[0..5] = block pairs (32 x 32
+ * diagnostics, m <= 10, zeros above): stats[0..7] = block pairs (32 x 32
  * points, upper triangle) ruled out without a test, tested in one direction
  * with objectives 1..m-1 (every row f_0 below every column f_0), tested in
  * the "row dominates column" direction only, in the "column dominates row"
- * direction only, tested both ways, and 256 x 256 tiles with no block pair
- * to test.  Errors: EINVAL (NULL argument), ECUDA. */
+ * direction only, tested both ways, 256 x 256 tiles with no block pair to
+ * test, the (lane, column) point pairs the kernel compared (one-direction
+ * block pairs compare only their live rows and columns), and the pairs of
+ * a live row and a live column among them.  stats must hold 8 values.
+ * Errors: EINVAL (NULL argument), ECUDA. */
 nsga3_status nsga3_get_dominance_stats(nsga3_ctx* ctx, int64_t* stats);
 
 /* Self-test of the block-wide selection routine that the niching kernels

@@ -78,9 +78,10 @@ struct Ctrl {
     uint32_t peel_rows;      // dominator word-rows in the peel's row lists, all passes
     uint32_t npath;          // NPATH_* bits: capacity paths the niching kernels took
     int32_t ntile;           // tiles listed in tlist by k_tile_plan
-    unsigned long long domstat[6];  // block pairs of the dominance build by mode (zero, f_0
+    unsigned long long domstat[8];  // block pairs of the dominance build by mode (zero, f_0
                                     // one-direction, row-dom-column, column-dom-row, both),
-                                    // and tiles with nothing to test (m <= 10)
+                                    // tiles with nothing to test, (lane, column) pairs
+                                    // tested and live pairs among them (m <= 10)
 
     int32_t ncand;           // association candidates written by the scan
     int32_t nslow;           // points sent to the full FP64 association scan

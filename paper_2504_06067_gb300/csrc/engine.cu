@@ -1238,9 +1238,9 @@ nsga3_status nsga3_get_dominance_stats(nsga3_ctx* ctx, int64_t* stats)
 {
     if (!ctx || !stats) return fail(ctx, NSGA3_EINVAL, "null argument");
     CK(cudaDeviceSynchronize());
-    unsigned long long d[6];
+    unsigned long long d[8];
     CK(cudaMemcpy(d, ctx->v.ctrl->domstat, sizeof d, cudaMemcpyDeviceToHost));
-    for (int t = 0; t < 6; ++t) stats[t] = (int64_t)d[t];
+    for (int t = 0; t < 8; ++t) stats[t] = (int64_t)d[t];
     return NSGA3_OK;
 }
 

@@ -126,32 +126,6 @@ __device__ __forceinline__ void block_full(const float* fi, const float* colp, u
     }
 }
 
-// "Some f_iq > f_jq" bits of one or two row lanes against the 32 columns of
-// a block (bit k for column k), objectives Q0 .. M-1; with two rows every
-// column load serves both.
-template <int Q0, int M, int M4, bool TWO>
-__device__ __forceinline__ void block_one_dir(const float* f0, const float* f1, const float* colp, uint32_t& acc0,
-                                              uint32_t& acc1)
-{
-    acc0 = 0u;
-    acc1 = 0u;
-#pragma unroll 4
-    for (int k = 31; k >= 0; --k) {
-        const float4* fj4 = reinterpret_cast<const float4*>(colp + k * M4);
-        float fj[M4];
-#pragma unroll
-        for (int q4 = 0; q4 < M4 / 4; ++q4) {
-            const float4 t = fj4[q4];
-            fj[4 * q4 + 0] = t.x;
-            fj[4 * q4 + 1] = t.y;
-            fj[4 * q4 + 2] = t.z;
-            fj[4 * q4 + 3] = t.w;
-        }
-        acc0 = __funnelshift_l(any_greater<Q0, M>(fj, f0), acc0, 1);  // sign set: some f_iq > f_jq
-        if (TWO) acc1 = __funnelshift_l(any_greater<Q0, M>(fj, f1), acc1, 1);
-    }
-}
-
 // How a (row block, column block) pair is tested.
 enum : int {
     BP_SKIP = 0,   // lower block triangle (done by the transposed tile)
@@ -294,6 +268,173 @@ __device__ __forceinline__ void put_block(const RunView& v, size_t at, uint32_t 
     if (lane_id() == 0 && nzw) atomicOr(&nzw[byte >> 2], 1u << (8 * (byte & 3) + bit));
 }
 
+// Position of the (t+1)-th set bit of x (t < popc(x)): a binary search on
+// the popcounts of halving windows.
+__device__ __forceinline__ int nth_set_bit(uint32_t x, int t)
+{
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const int c = __popc((x >> pos) & ((1u << s) - 1u));
+        if (t >= c) {
+            t -= c;
+            pos += s;
+        }
+    }
+    return pos;
+}
+
+// Order-preserving map of FP32 to int32 (an involution: the same map turns
+// it back): positive values keep their bits, negative ones flip the
+// magnitude bits.  INT_MAX maps back to a NaN.
+__device__ __forceinline__ int f2s(float x)
+{
+    const int i = __float_as_int(x);
+    return i ^ ((i >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float s2f(int s) { return __int_as_float(s ^ ((s >> 31) & 0x7fffffff)); }
+
+// "Some f_iq > f_jq" bits of one or two row lanes against the live columns
+// of a block: bit t for the t-th live column, whose float offset in the
+// staged block lane t holds in `off`.
+template <int M, int M4, bool TWO>
+__device__ __forceinline__ void live_one_dir(const float* f0, const float* f1, const float* colp, int off, int nl,
+                                             uint32_t& acc0, uint32_t& acc1)
+{
+    acc0 = 0u;
+    acc1 = 0u;
+#pragma unroll 2
+    for (int t = nl - 1; t >= 0; --t) {
+        const float4* fj4 = reinterpret_cast<const float4*>(colp + __shfl_sync(0xffffffffu, off, t));
+        float fj[M4];
+#pragma unroll
+        for (int q4 = 0; q4 < M4 / 4; ++q4) {
+            const float4 x = fj4[q4];
+            fj[4 * q4 + 0] = x.x;
+            fj[4 * q4 + 1] = x.y;
+            fj[4 * q4 + 2] = x.z;
+            fj[4 * q4 + 3] = x.w;
+        }
+        acc0 = __funnelshift_l(any_greater<0, M>(fj, f0), acc0, 1);
+        if (TWO) acc1 = __funnelshift_l(any_greater<0, M>(fj, f1), acc1, 1);
+    }
+}
+
+template <int M, int M4>
+__device__ __forceinline__ void load_row(float (&f)[M], const float* p)
+{
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int q4 = 0; q4 < M4 / 4; ++q4) {
+        const float4 x = p4[q4];
+        if (4 * q4 + 0 < M) f[4 * q4 + 0] = x.x;
+        if (4 * q4 + 1 < M) f[4 * q4 + 1] = x.y;
+        if (4 * q4 + 2 < M) f[4 * q4 + 2] = x.z;
+        if (4 * q4 + 3 < M) f[4 * q4 + 3] = x.w;
+    }
+}
+
+// One-direction entry, "row dominates column": row block ib (and ib + 1
+// when `two`) against column block jb, lane = row.  The test is "no
+// f_iq > f_jq" over every objective (when every row f_0 is below every
+// column f_0, objective 0 never sets a sign and strictness is implied;
+// otherwise some objective separates the blocks, so the vectors differ).
+// Before any pairwise test the entry narrows both sides:
+//  - a row can dominate some column of J only if f_iq <= max_J q for every
+//    q (the column block's box); the other rows are dead (NaN padding rows
+//    fail too);
+//  - a column j can be dominated by a live row only if
+//    min over live rows of f_iq <= f_jq for every q; the other columns are
+//    dead (NaN padding columns fail too).
+// Only live columns are tested (the warp walks them in order, each column
+// broadcast from shared memory), and the live rows are packed onto the
+// lanes when they fit in one warp (always for one row block); otherwise
+// each lane tests its row of both blocks.  The bits come back in place by
+// shuffles: row words through the packing slots, column words through the
+// live columns' ranks after the transpose.  `ev` counts the (lane, column)
+// pairs tested in units of 32, `lv` the (live row, live column) pairs among
+// them.
+template <int M, int M4>
+__device__ __forceinline__ void entry_row_dom_col(const RunView& v, const float* srow, const float* colp,
+                                                  const float* cbox, int ri, bool two, int ib, int jb, int cb,
+                                                  unsigned* nz, int* ccnt, uint32_t& ev, uint32_t& lv)
+{
+    const int lane = lane_id();
+    const uint32_t lt = (1u << lane) - 1u;
+    float f0[M], f1[M];
+    load_row<M, M4>(f0, srow + (ri * 32 + lane) * M4);
+    if (two) {
+        load_row<M, M4>(f1, srow + ((ri + 1) * 32 + lane) * M4);
+    } else {
+#pragma unroll
+        for (int q = 0; q < M; ++q) f1[q] = f0[q];
+    }
+    bool l0 = true, l1 = two;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+        const float h = cbox[M4 + q];
+        l0 = l0 && f0[q] <= h;
+        l1 = l1 && f1[q] <= h;
+    }
+    // column test against the per-objective minimum of the live rows (no
+    // live row: the minimum is NaN and every column is dead)
+    float cj[M];
+    load_row<M, M4>(cj, colp + lane * M4);
+    // (every lane takes part in every reduction: none sits in a condition)
+    bool cl = true;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+        const int o = min(l0 ? f2s(f0[q]) : 0x7fffffff, l1 ? f2s(f1[q]) : 0x7fffffff);
+        const float lmin = s2f(__reduce_min_sync(0xffffffffu, o));
+        cl = cl && lmin <= cj[q];
+    }
+    const uint32_t live = __ballot_sync(0xffffffffu, cl);
+    if (!live) return;
+    const int nl = __popc(live);
+    const uint32_t low = nl == 32 ? 0xffffffffu : (1u << nl) - 1u;
+    const int off = lane < nl ? nth_set_bit(live, lane) * M4 : 0;  // lane t: the t-th live column
+    const uint32_t b0 = __ballot_sync(0xffffffffu, l0);
+    const uint32_t b1 = __ballot_sync(0xffffffffu, l1);
+    const int n0 = __popc(b0), nr = n0 + __popc(b1);
+    uint32_t d0, d1;
+    if (nr <= 32) {
+        // pack the live rows onto the lanes (block ib first)
+        const bool first = lane < n0;
+        const int src = lane < nr ? nth_set_bit(first ? b0 : b1, first ? lane : lane - n0) : 0;
+        float fp[M];
+        load_row<M, M4>(fp, srow + ((ri + (first ? 0 : 1)) * 32 + src) * M4);
+        uint32_t acc, unused;
+        live_one_dir<M, M4, false>(fp, fp, colp, off, nl, acc, unused);
+        const uint32_t R = ~acc & low;
+        const uint32_t r0 = __shfl_sync(0xffffffffu, R, __popc(b0 & lt));
+        const uint32_t r1 = __shfl_sync(0xffffffffu, R, (n0 + __popc(b1 & lt)) & 31);
+        d0 = l0 ? r0 : 0u;
+        d1 = l1 ? r1 : 0u;
+        ev += nl;
+    } else {
+        uint32_t acc0, acc1;
+        live_one_dir<M, M4, true>(f0, f1, colp, off, nl, acc0, acc1);
+        d0 = l0 ? ~acc0 & low : 0u;
+        d1 = l1 ? ~acc1 & low : 0u;
+        ev += 2 * nl;
+    }
+    lv += nr * nl;
+    // column words: lane t of the transpose holds the t-th live column
+    const int rk = __popc(live & lt);
+    const bool mine = (live >> lane) & 1u;
+    uint32_t w0 = __shfl_sync(0xffffffffu, warp_transpose32(d0), rk & 31);
+    w0 = mine ? w0 : 0u;
+    put_block(v, (size_t)ib * v.ld + jb * 32 + lane, w0, nz, ri, cb);
+    int cc = __popc(w0);
+    if (two) {
+        uint32_t w1 = __shfl_sync(0xffffffffu, warp_transpose32(d1), rk & 31);
+        w1 = mine ? w1 : 0u;
+        put_block(v, (size_t)(ib + 1) * v.ld + jb * 32 + lane, w1, nz, ri + 1, cb);
+        cc += __popc(w1);
+    }
+    if (cc) atomicAdd(&ccnt[cb * 32 + lane], cc);
+}
+
 // Asynchronous copies into shared memory (cp.async: the data lands while
 // the CTA keeps working; wait_all + a barrier make it visible to all).
 __device__ __forceinline__ void cp_async4(void* dst, const void* src)
@@ -357,6 +498,7 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
     __shared__ unsigned short work[2][64];
     __shared__ int nheavy[2], nlight[2];   // heavy entries from the front, light ones from the back
     __shared__ int taken[2];               // entries handed out
+    __shared__ unsigned long long stat[2]; // pairs tested (units of 32), live pairs
     if (read_status(v.ctrl)) return;
     const int T = v.ld / NSGA3_TILE;
     const int ntile = *(volatile const int32_t*)&v.ctrl->ntile;
@@ -481,6 +623,7 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
     int cur = 0;
     int it = blockIdx.x;
     int ti, tj;
+    uint32_t ev = 0u, lv = 0u;  // this tile's pairs tested (units of 32) and live pairs (warp-uniform)
     decode_tile(v.tlist[it], T, ti, tj);
     copy_points(ti, tj, 0);
     rowcnt[0][tid] = 0;
@@ -488,6 +631,7 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
     rowcnt[1][tid] = 0;
     colcnt[1][tid] = 0;
     if (tid < 8) nzw[tid >> 2][tid & 3] = 0u;
+    if (tid < 2) stat[tid] = 0ull;
     if (warp == 0) decide(ti, tj, 0);
     cp_async_wait_all();
     __syncthreads();
@@ -522,50 +666,28 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
             // gives the same sign both ways, hence no bit).
             const int cv = v.n2 - jb * 32;
             const uint32_t colvalid = cv >= 32 ? 0xffffffffu : (cv > 0 ? (1u << cv) - 1u : 0u);
-            if (two) {
-                // rows ri and ri + 1, "row dominates column" only
-                float f0[M], f1[M];
-#pragma unroll
-                for (int q = 0; q < M; ++q) {
-                    f0[q] = srow[(ri * 32 + lane) * M4 + q];
-                    f1[q] = srow[((ri + 1) * 32 + lane) * M4 + q];
-                }
-                uint32_t acc0, acc1;
-                if (mode == BP_FAST0)
-                    block_one_dir<1, M, M4, true>(f0, f1, colp, acc0, acc1);
-                else
-                    block_one_dir<0, M, M4, true>(f0, f1, colp, acc0, acc1);
-                const uint32_t d0 = ib * 32 + lane < v.n2 ? ~acc0 & colvalid : 0u;
-                const uint32_t d1 = (ib + 1) * 32 + lane < v.n2 ? ~acc1 & colvalid : 0u;
-                const uint32_t t0 = warp_transpose32(d0), t1 = warp_transpose32(d1);
-                put_block(v, (size_t)ib * v.ld + jb * 32 + lane, t0, nz, ri, cb);
-                put_block(v, (size_t)(ib + 1) * v.ld + jb * 32 + lane, t1, nz, ri + 1, cb);
-                const int cc = __popc(t0) + __popc(t1);
-                if (cc) atomicAdd(&ccnt[cb * 32 + lane], cc);
+            if (mode == BP_FAST0 || mode == BP_FASTK) {
+                // "row dominates column" only, one row block or two
+                const float* cbox = sbox_of(cur) + (8 + cb) * 2 * M4;
+                entry_row_dom_col<M, M4>(v, srow, colp, cbox, ri, two, ib, jb, cb, nz, ccnt, ev, lv);
                 continue;
             }
+            ev += 32u;
+            lv += 1024u;
             float fi[M];
 #pragma unroll
             for (int q = 0; q < M; ++q) fi[q] = srow[(ri * 32 + lane) * M4 + q];
             uint32_t dij = 0u, dji = 0u;
-            if (mode == BP_FAST0 || mode == BP_FASTK || mode == BP_FASTR) {
+            if (mode == BP_FASTR) {
+                // column j dominates row i: no f_jq > f_iq (the vectors differ)
                 const bool rowvalid = ib * 32 + lane < v.n2;
-                uint32_t acc = 0u, unused;
-                if (mode == BP_FAST0) {
-                    block_one_dir<1, M, M4, false>(fi, fi, colp, acc, unused);
-                    dij = rowvalid ? ~acc & colvalid : 0u;
-                } else if (mode == BP_FASTK) {
-                    block_one_dir<0, M, M4, false>(fi, fi, colp, acc, unused);
-                    dij = rowvalid ? ~acc & colvalid : 0u;
-                } else {
-                    // column j dominates row i: no f_jq > f_iq (the vectors differ)
+                uint32_t acc = 0u;
 #pragma unroll 4
-                    for (int k = 31; k >= 0; --k) {
-                        const float* fj = colp + k * M4;
-                        acc = __funnelshift_l(any_greater<0, M>(fi, fj), acc, 1);
-                    }
-                    dji = rowvalid ? ~acc & colvalid : 0u;
+                for (int k = 31; k >= 0; --k) {
+                    const float* fj = colp + k * M4;
+                    acc = __funnelshift_l(any_greater<0, M>(fi, fj), acc, 1);
                 }
+                dji = rowvalid ? ~acc & colvalid : 0u;
             } else {
                 block_full<M, M4>(fi, colp, dij, dji);
             }
@@ -580,6 +702,12 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
             }
             if (dji) atomicAdd(&rcnt[ri * 32 + lane], __popc(dji));
         }
+        if (lane == 0 && ev) {
+            atomicAdd(&stat[0], (unsigned long long)ev);
+            atomicAdd(&stat[1], (unsigned long long)lv);
+        }
+        ev = 0u;
+        lv = 0u;
         cp_async_wait_all();
         __syncthreads();  // the tile's tests are done, the next tile is staged and decided
         if (warp == 0) {
@@ -620,6 +748,10 @@ __global__ void __launch_bounds__(256, M <= 8 ? 5 : 4) k_dominance(RunView v)
         it = nit;
         ti = nti;
         tj = ntj;
+    }
+    if (tid == 0 && stat[0]) {
+        atomicAdd(&v.ctrl->domstat[6], 32ull * stat[0]);
+        atomicAdd(&v.ctrl->domstat[7], stat[1]);
     }
 }
 

@@ -58,7 +58,7 @@ __global__ void k_sel_reset(RunView v)
         c->nlarge = 0;
         c->npath = 0u;
         c->ntile = 0;
-        for (int t = 0; t < 6; ++t) c->domstat[t] = 0ull;
+        for (int t = 0; t < 8; ++t) c->domstat[t] = 0ull;
         c->peel_rows = 0u;
         c->ncand = 0;
         c->nslow = 0;
