@@ -294,29 +294,85 @@ __device__ __forceinline__ int f2s(float x)
 }
 __device__ __forceinline__ float s2f(int s) { return __int_as_float(s ^ ((s >> 31) & 0x7fffffff)); }
 
+// Objectives in FP32 pairs: sub.rn.f32x2 forms two exact differences in
+// one instruction (each lane rounds once, as the scalar subtraction).
+// Columns are loaded from shared memory straight into 64-bit pairs, and
+// the sign words are OR-ed three at a time (lop3).
+__device__ __forceinline__ unsigned long long p2_pack(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void p2_sub(unsigned long long a, unsigned long long b, uint32_t& lo, uint32_t& hi)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(d));
+}
+__device__ __forceinline__ uint32_t or3(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, 0xFE;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+// one column's staged objectives as M4 / 2 pairs (shared-memory byte address)
+template <int M4>
+__device__ __forceinline__ void lds_col(uint32_t a, unsigned long long (&c)[M4 / 2])
+{
+#pragma unroll
+    for (int q4 = 0; q4 < M4 / 4; ++q4)
+        asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(c[2 * q4]), "=l"(c[2 * q4 + 1]) : "r"(a + 16 * q4));
+}
+
+// A row's objectives as pairs (p[k] = f_2k, f_2k+1) and the last one alone
+// when M is odd.
+template <int M>
+struct RowPairs {
+    unsigned long long p[M / 2];
+    float last;
+};
+template <int M>
+__device__ __forceinline__ void make_pairs(RowPairs<M>& r, const float (&f)[M])
+{
+#pragma unroll
+    for (int k = 0; k < M / 2; ++k) r.p[k] = p2_pack(f[2 * k], f[2 * k + 1]);
+    r.last = (M & 1) ? f[M - 1] : 0.0f;
+}
+// sign bit set iff some f_iq > f_jq (f_j - f_i < 0 for some q)
+template <int M, int M4>
+__device__ __forceinline__ uint32_t any_greater_p(const unsigned long long (&c)[M4 / 2], const RowPairs<M>& r)
+{
+    constexpr int W = 2 * (M / 2) + (M & 1);
+    uint32_t w[W];
+#pragma unroll
+    for (int k = 0; k < M / 2; ++k) p2_sub(c[k], r.p[k], w[2 * k], w[2 * k + 1]);
+    if (M & 1) {
+        uint32_t lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(c[M / 2]));
+        w[W - 1] = __float_as_uint(__uint_as_float(lo) - r.last);
+    }
+    uint32_t acc = w[0];
+#pragma unroll
+    for (int i = 1; i < W; i += 2) acc = (i + 1 < W) ? or3(acc, w[i], w[i + 1]) : (acc | w[i]);
+    return acc;
+}
+
 // "Some f_iq > f_jq" bits of one or two row lanes against the live columns
-// of a block: bit t for the t-th live column, whose float offset in the
-// staged block lane t holds in `off`.
+// of a block: bit t for the t-th live column, whose shared-memory byte
+// address lane t holds in `addr`.
 template <int M, int M4, bool TWO>
-__device__ __forceinline__ void live_one_dir(const float* f0, const float* f1, const float* colp, int off, int nl,
+__device__ __forceinline__ void live_one_dir(const RowPairs<M>& r0, const RowPairs<M>& r1, uint32_t addr, int nl,
                                              uint32_t& acc0, uint32_t& acc1)
 {
     acc0 = 0u;
     acc1 = 0u;
 #pragma unroll 2
     for (int t = nl - 1; t >= 0; --t) {
-        const float4* fj4 = reinterpret_cast<const float4*>(colp + __shfl_sync(0xffffffffu, off, t));
-        float fj[M4];
-#pragma unroll
-        for (int q4 = 0; q4 < M4 / 4; ++q4) {
-            const float4 x = fj4[q4];
-            fj[4 * q4 + 0] = x.x;
-            fj[4 * q4 + 1] = x.y;
-            fj[4 * q4 + 2] = x.z;
-            fj[4 * q4 + 3] = x.w;
-        }
-        acc0 = __funnelshift_l(any_greater<0, M>(fj, f0), acc0, 1);
-        if (TWO) acc1 = __funnelshift_l(any_greater<0, M>(fj, f1), acc1, 1);
+        unsigned long long c[M4 / 2];
+        lds_col<M4>(__shfl_sync(0xffffffffu, addr, t), c);
+        acc0 = __funnelshift_l(any_greater_p<M, M4>(c, r0), acc0, 1);
+        if (TWO) acc1 = __funnelshift_l(any_greater_p<M, M4>(c, r1), acc1, 1);
     }
 }
 
@@ -347,9 +403,9 @@ __device__ __forceinline__ void load_row(float (&f)[M], const float* p)
 //    min over live rows of f_iq <= f_jq for every q; the other columns are
 //    dead (NaN padding columns fail too).
 // Only live columns are tested (the warp walks them in order, each column
-// broadcast from shared memory), and the live rows are packed onto the
-// lanes when they fit in one warp (always for one row block); otherwise
-// each lane tests its row of both blocks.  The bits come back in place by
+// broadcast from shared memory); with two row blocks the live rows are
+// packed onto the lanes when they fit in one warp, otherwise each lane
+// tests its row of both blocks.  The bits come back in place by
 // shuffles: row words through the packing slots, column words through the
 // live columns' ranks after the transpose.  `ev` counts the (lane, column)
 // pairs tested in units of 32, `lv` the (live row, live column) pairs among
@@ -369,66 +425,95 @@ __device__ __forceinline__ void entry_row_dom_col(const RunView& v, const float*
 #pragma unroll
         for (int q = 0; q < M; ++q) f1[q] = f0[q];
     }
+    float h[M];
+    load_row<M, M4>(h, cbox + M4);  // the column block's maxima
     bool l0 = true, l1 = two;
 #pragma unroll
     for (int q = 0; q < M; ++q) {
-        const float h = cbox[M4 + q];
-        l0 = l0 && f0[q] <= h;
-        l1 = l1 && f1[q] <= h;
+        l0 = l0 && f0[q] <= h[q];
+        l1 = l1 && f1[q] <= h[q];
     }
     // column test against the per-objective minimum of the live rows (no
     // live row: the minimum is NaN and every column is dead)
     float cj[M];
     load_row<M, M4>(cj, colp + lane * M4);
     // (every lane takes part in every reduction: none sits in a condition)
+    const bool anyl = l0 || l1;
     bool cl = true;
 #pragma unroll
     for (int q = 0; q < M; ++q) {
-        const int o = min(l0 ? f2s(f0[q]) : 0x7fffffff, l1 ? f2s(f1[q]) : 0x7fffffff);
-        const float lmin = s2f(__reduce_min_sync(0xffffffffu, o));
+        const float fm = fminf(l0 ? f0[q] : __int_as_float(0x7f800000), l1 ? f1[q] : __int_as_float(0x7f800000));
+        const float lmin = s2f(__reduce_min_sync(0xffffffffu, anyl ? f2s(fm) : 0x7fffffff));
         cl = cl && lmin <= cj[q];
     }
     const uint32_t live = __ballot_sync(0xffffffffu, cl);
     if (!live) return;
     const int nl = __popc(live);
     const uint32_t low = nl == 32 ? 0xffffffffu : (1u << nl) - 1u;
-    const int off = lane < nl ? nth_set_bit(live, lane) * M4 : 0;  // lane t: the t-th live column
+    // lane t: shared-memory byte address of the t-th live column
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(colp) +
+                          (uint32_t)(lane < nl ? nth_set_bit(live, lane) : 0) * (uint32_t)(M4 * 4);
     const uint32_t b0 = __ballot_sync(0xffffffffu, l0);
     const uint32_t b1 = __ballot_sync(0xffffffffu, l1);
     const int n0 = __popc(b0), nr = n0 + __popc(b1);
     uint32_t d0, d1;
-    if (nr <= 32) {
-        // pack the live rows onto the lanes (block ib first)
-        const bool first = lane < n0;
-        const int src = lane < nr ? nth_set_bit(first ? b0 : b1, first ? lane : lane - n0) : 0;
+    if (!two || nr <= 32) {
+        // one row per lane: the entry's row block as it is, or the live rows
+        // of both blocks packed onto the lanes (block ib first)
         float fp[M];
-        load_row<M, M4>(fp, srow + ((ri + (first ? 0 : 1)) * 32 + src) * M4);
+        const bool first = lane < n0;
+        if (two) {
+            const int src = lane < nr ? nth_set_bit(first ? b0 : b1, first ? lane : lane - n0) : 0;
+            load_row<M, M4>(fp, srow + ((ri + (first ? 0 : 1)) * 32 + src) * M4);
+        } else {
+#pragma unroll
+            for (int q = 0; q < M; ++q) fp[q] = f0[q];
+        }
+        RowPairs<M> rp;
+        make_pairs<M>(rp, fp);
         uint32_t acc, unused;
-        live_one_dir<M, M4, false>(fp, fp, colp, off, nl, acc, unused);
+        live_one_dir<M, M4, false>(rp, rp, addr, nl, acc, unused);
         const uint32_t R = ~acc & low;
-        const uint32_t r0 = __shfl_sync(0xffffffffu, R, __popc(b0 & lt));
-        const uint32_t r1 = __shfl_sync(0xffffffffu, R, (n0 + __popc(b1 & lt)) & 31);
-        d0 = l0 ? r0 : 0u;
-        d1 = l1 ? r1 : 0u;
+        if (two) {
+            const uint32_t r0 = __shfl_sync(0xffffffffu, R, __popc(b0 & lt));
+            const uint32_t r1 = __shfl_sync(0xffffffffu, R, (n0 + __popc(b1 & lt)) & 31);
+            d0 = l0 ? r0 : 0u;
+            d1 = l1 ? r1 : 0u;
+        } else {
+            d0 = l0 ? R : 0u;
+            d1 = 0u;
+        }
         ev += nl;
     } else {
+        RowPairs<M> rp0, rp1;
+        make_pairs<M>(rp0, f0);
+        make_pairs<M>(rp1, f1);
         uint32_t acc0, acc1;
-        live_one_dir<M, M4, true>(f0, f1, colp, off, nl, acc0, acc1);
+        live_one_dir<M, M4, true>(rp0, rp1, addr, nl, acc0, acc1);
         d0 = l0 ? ~acc0 & low : 0u;
         d1 = l1 ? ~acc1 & low : 0u;
         ev += 2 * nl;
     }
     lv += nr * nl;
-    // column words: lane t of the transpose holds the t-th live column
+    // column words: lane t of the transpose holds the t-th live column (with
+    // two row blocks and at most 16 live columns one transpose serves both:
+    // lanes 0..15 the first block, 16..31 the second)
     const int rk = __popc(live & lt);
     const bool mine = (live >> lane) & 1u;
-    uint32_t w0 = __shfl_sync(0xffffffffu, warp_transpose32(d0), rk & 31);
+    uint32_t w0, w1 = 0u;
+    if (two && nl <= 16) {
+        const uint32_t tw = warp_transpose32(d0 | (d1 << 16));
+        w0 = __shfl_sync(0xffffffffu, tw, rk & 15);
+        w1 = __shfl_sync(0xffffffffu, tw, 16 + (rk & 15));
+    } else {
+        w0 = __shfl_sync(0xffffffffu, warp_transpose32(d0), rk & 31);
+        if (two) w1 = __shfl_sync(0xffffffffu, warp_transpose32(d1), rk & 31);
+    }
     w0 = mine ? w0 : 0u;
+    w1 = mine ? w1 : 0u;
     put_block(v, (size_t)ib * v.ld + jb * 32 + lane, w0, nz, ri, cb);
     int cc = __popc(w0);
     if (two) {
-        uint32_t w1 = __shfl_sync(0xffffffffu, warp_transpose32(d1), rk & 31);
-        w1 = mine ? w1 : 0u;
         put_block(v, (size_t)(ib + 1) * v.ld + jb * 32 + lane, w1, nz, ri + 1, cb);
         cc += __popc(w1);
     }

@@ -179,7 +179,13 @@ __global__ void k_gather(RunView v)
     const int i = v.sel[p];
     const float* src = v.X + (size_t)i * v.d;
     float* dst = v.Xtmp + (size_t)p * v.d;
-    for (int e = lane; e < v.d; e += 32) dst[e] = src[e];
+    if ((v.d & 3) == 0) {  // rows start on 16-byte boundaries: 16-byte copies
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        for (int e = lane; e < v.d / 4; e += 32) d4[e] = __ldg(s4 + e);
+    } else {
+        for (int e = lane; e < v.d; e += 32) dst[e] = src[e];
+    }
     for (int q = lane; q < v.m; q += 32) v.Ftmp[(size_t)p * v.m + q] = v.F[(size_t)i * v.m + q];
     if (lane == 0) v.ranktmp[p] = v.rank2[i];
 }

@@ -238,16 +238,14 @@ __global__ void k_init(RunView v)
 __device__ __forceinline__ float pm_mutate(float y, float u, float eta_m)
 {
     const float mp = 1.0f / (eta_m + 1.0f);
-    float dq;
-    if (u < 0.5f) {
-        const float xy = 1.0f - y;
-        const float val = 2.0f * u + (1.0f - 2.0f * u) * powf(xy, eta_m + 1.0f);
-        dq = expm1f(mp * logf(val));
-    } else {
-        const float xy = 1.0f - (1.0f - y);
-        const float val = 2.0f * (1.0f - u) + 2.0f * (u - 0.5f) * powf(xy, eta_m + 1.0f);
-        dq = -expm1f(mp * logf(val));
-    }
+    // one powf, logf and expm1f on the chosen branch's operands (the same
+    // values as calling them in each branch)
+    const bool lo = u < 0.5f;
+    const float xy = lo ? 1.0f - y : 1.0f - (1.0f - y);
+    const float pw = powf(xy, eta_m + 1.0f);
+    const float val = lo ? 2.0f * u + (1.0f - 2.0f * u) * pw : 2.0f * (1.0f - u) + 2.0f * (u - 0.5f) * pw;
+    const float ex = expm1f(mp * logf(val));
+    const float dq = lo ? ex : -ex;
     y = y + dq;
     return fminf(fmaxf(y, 0.0f), 1.0f);
 }
@@ -277,7 +275,9 @@ __device__ __forceinline__ void vary_pair(const RunView& v, int q, uint32_t gen,
         const U4 sb = philox((uint32_t)q * (uint32_t)d + (uint32_t)var, gen, RNG_SBX, 0u, v.seed);
         if (cross && u01(sb.y) < 0.5f) {
             const float u = u01(sb.x);
-            const float beta = (u <= 0.5f) ? powf(2.0f * u, e) : powf(1.0f / (2.0f * (1.0f - u)), e);
+            // one powf on the chosen base (the same value as either branch's call)
+            const float base = (u <= 0.5f) ? 2.0f * u : 1.0f / (2.0f * (1.0f - u));
+            const float beta = powf(base, e);
             const float mid = 0.5f * (y1 + y2), hb = 0.5f * beta, dy = y2 - y1;
             c1 = fmaf(-hb, dy, mid);
             c2 = fmaf(hb, dy, mid);
