@@ -437,14 +437,20 @@ __device__ __forceinline__ void entry_row_dom_col(const RunView& v, const float*
     // live row: the minimum is NaN and every column is dead)
     float cj[M];
     load_row<M, M4>(cj, colp + lane * M4);
-    // (every lane takes part in every reduction: none sits in a condition)
+    // (every lane takes part in every reduction and vote: none sits in a
+    // condition that differs between lanes).  No live row: nothing to test.
+    // With more than six objectives a vote after the first five ends the
+    // entry early when no column is left (most entries that end without a
+    // live column do so by then).
     const bool anyl = l0 || l1;
+    if (!__any_sync(0xffffffffu, anyl)) return;
     bool cl = true;
 #pragma unroll
     for (int q = 0; q < M; ++q) {
         const float fm = fminf(l0 ? f0[q] : __int_as_float(0x7f800000), l1 ? f1[q] : __int_as_float(0x7f800000));
         const float lmin = s2f(__reduce_min_sync(0xffffffffu, anyl ? f2s(fm) : 0x7fffffff));
         cl = cl && lmin <= cj[q];
+        if (M > 6 && q == 4 && !__any_sync(0xffffffffu, cl)) return;
     }
     const uint32_t live = __ballot_sync(0xffffffffu, cl);
     if (!live) return;

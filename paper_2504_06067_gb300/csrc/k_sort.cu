@@ -239,13 +239,23 @@ __global__ void __launch_bounds__(SB) k_sort_hist(RunView v)
     if (ticket != gridDim.x - 1) return;
     // last CTA: exclusive scan of the counts, a contiguous run per thread
     __threadfence();
-    const int nk = 1 << v.kbits;  // >= 256: a multiple of 4
-    const int per = ((nk + SB - 1) / SB + 3) & ~3;
+    const int nk = 1 << v.kbits;  // >= 256: a multiple of 4, at most 2^16
+    const int per = ((nk + SB - 1) / SB + 3) & ~3;  // <= 64
     const int b0 = min(nk, (int)threadIdx.x * per), b1 = min(nk, b0 + per);
+    // the thread's run read in batches of 8 vectors, each batch's loads
+    // issued before their first use
+    constexpr int RUN4 = ((1 << 16) / SB + 3) / 4, BAT = 8;
     int s = 0;
-    for (int b = b0; b < b1; b += 4) {
-        const int4 x = __ldcg(reinterpret_cast<const int4*>(v.bcnt + b));
-        s += x.x + x.y + x.z + x.w;
+#pragma unroll
+    for (int h = 0; h < RUN4; h += BAT) {
+        int4 xs[BAT];
+#pragma unroll
+        for (int t = 0; t < BAT; ++t) {
+            const int b = b0 + 4 * (h + t);
+            xs[t] = b < b1 ? __ldcg(reinterpret_cast<const int4*>(v.bcnt + b)) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int t = 0; t < BAT; ++t) s += xs[t].x + xs[t].y + xs[t].z + xs[t].w;
     }
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     int inc = s;
@@ -268,15 +278,26 @@ __global__ void __launch_bounds__(SB) k_sort_hist(RunView v)
     }
     __syncthreads();
     int run = scratch[warp] + inc - s;
-    for (int b = b0; b < b1; b += 4) {
-        const int4 x = __ldcg(reinterpret_cast<const int4*>(v.bcnt + b));
-        int4 y;
-        y.x = run;
-        y.y = run + x.x;
-        y.z = y.y + x.y;
-        y.w = y.z + x.z;
-        run = y.w + x.w;
-        *reinterpret_cast<int4*>(v.bcnt + b) = y;
+#pragma unroll
+    for (int h = 0; h < RUN4; h += BAT) {
+        int4 xs[BAT];
+#pragma unroll
+        for (int t = 0; t < BAT; ++t) {
+            const int b = b0 + 4 * (h + t);
+            xs[t] = b < b1 ? __ldcg(reinterpret_cast<const int4*>(v.bcnt + b)) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int t = 0; t < BAT; ++t) {
+            const int4 x = xs[t];
+            int4 y;
+            y.x = run;
+            y.y = run + x.x;
+            y.z = y.y + x.y;
+            y.w = y.z + x.z;
+            run = y.w + x.w;
+            const int b = b0 + 4 * (h + t);
+            if (b < b1) *reinterpret_cast<int4*>(v.bcnt + b) = y;
+        }
     }
     if (threadIdx.x == 0) c->sort_done = 0u;
 }
