@@ -66,7 +66,7 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=["headline"] + sorted(WORKLOADS) +
-                   ["batched", "served", "sweep", "popsweep", "select", "custom"], default="headline")
+                   ["batched", "served", "sweep", "popsweep", "select", "custom", "shapes"], default="headline")
     p.add_argument("--runs", type=int, default=64, help="batched: independent runs")
     p.add_argument("--m", type=int, default=10, help="custom: objectives")
     p.add_argument("--N", type=int, default=30000, help="custom: population")
@@ -1169,6 +1169,85 @@ def run_reference(args, world, rank):
 SELECT_KINDS = ("equal", "dups", "chain", "simplex")
 
 
+def run_shapes(args, world, rank, local):
+    """Launch-shape sweep (--workload shapes): for (m, 2N) buckets of the
+    configurations' shapes, every persistent-CTA count of the dominance
+    build and of the cooperative peel (nsga3_opts.dom_ctas_per_sm,
+    peel_ctas_per_sm), each its own run from generation 0: warm-up, then K
+    generations with events around the dominance build and the peel, L2
+    flushed before each.  The final populations of every setting of a bucket
+    must be identical (the shapes change no result); the fastest setting is
+    reported beside the default (0: all resident)."""
+    import hashlib
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2504_06067_gb300 import native as n
+
+    K = args.steps
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    phases = (C.c_float * 7)()
+    buckets = [wl.RunConfig("shape_m3_N2000", m=3, d=22, N=2000, p1=wl.largest_p(3, 2000), generations=K),
+               wl.SCALE,
+               wl.RunConfig("shape_m8_N10000", m=8, d=27, N=10000, p1=wl.largest_p(8, 10000), generations=K),
+               wl.RunConfig("shape_m10_N30000", m=10, d=200, N=30000, p1=3, p2=2, generations=K),
+               wl.LARGE]
+    sampler = ClockSampler(local)
+    sampler.start()
+    out = []
+    for cfg in buckets:
+        W = wl.objective_weights(cfg.m, cfg.seed)
+        res = {}
+        digests = set()
+        dom_max = 5 if cfg.m <= 8 else 4
+        settings = [(dc, 0) for dc in range(0, dom_max + 1)] + [(0, pc) for pc in (1, 2)]
+        for dc, pc in settings:
+            progress("shapes %s dom_ctas=%d peel_ctas=%d" % (cfg.name, dc, pc))
+            opts = n.default_opts(seed=cfg.seed, p2=cfg.p2, tau=cfg.tau, W=W.ctypes.data, phase_timing=1,
+                                  dom_ctas_per_sm=dc, peel_ctas_per_sm=pc)
+            ctx = n.create(cfg.m, cfg.d, cfg.N, cfg.p1, opts)
+            try:
+                n.check(n.nsga3_init(ctx, sh), ctx)
+                for _ in range(args.warmup):
+                    n.check(n.nsga3_step(ctx, sh), ctx)
+                n.check(n.nsga3_init(ctx, sh), ctx)
+                dom = peel = step = 0.0
+                for _ in range(K):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    n.check(n.nsga3_step(ctx, sh), ctx)
+                    e1.record(stream)
+                    e1.synchronize()
+                    step += e0.elapsed_time(e1)
+                    n.check(n.nsga3_phase_times(ctx, phases, 7), ctx)
+                    dom += phases[2]
+                    peel += phases[3]
+                X = np.zeros((cfg.N, cfg.d), np.float32)
+                F = np.zeros((cfg.N, cfg.m), np.float32)
+                R = np.zeros(cfg.N, np.int32)
+                n.check(n.nsga3_get_population(ctx, X.ctypes.data, F.ctypes.data, R.ctypes.data, sh), ctx)
+                n.check(n.nsga3_sync(ctx, sh), ctx)
+                digests.add(hashlib.sha256(X.tobytes() + F.tobytes() + R.tobytes()).hexdigest())
+            finally:
+                n.nsga3_destroy(ctx)
+            res["dom%d_peel%d" % (dc, pc)] = {"dominance_ms": dom / K, "peel_ms": peel / K, "step_ms": step / K}
+        best_dom = min((k for k in res if k.endswith("_peel0")), key=lambda k: res[k]["dominance_ms"])
+        best_peel = min(("dom0_peel0", "dom0_peel1", "dom0_peel2"), key=lambda k: res[k]["peel_ms"])
+        out.append({"workload": cfg.name, "m": cfg.m, "N": cfg.N, "settings": res,
+                    "fastest_dominance": best_dom, "fastest_peel": best_peel,
+                    "identical_populations": len(digests) == 1})
+    clocks = sampler.stop()
+    if rank == 0:
+        print(json.dumps({"metric": "launch-shape sweep (dominance build and front peel CTAs per SM)",
+                          "steps": K, "warmup": args.warmup, "buckets": out, "clocks": clocks,
+                          "note": "dom0 / peel0 = the default (every CTA that fits at once); times are the "
+                                  "phase events of generations 0..K-1, L2 flushed before each"}))
+
+
 def run_select(args, world, rank, local):
     """Selection microbenchmark: nsga3_select alone (selected sols/s = N /
     the time of one selection, objectives already on the device) on merged
@@ -1319,7 +1398,7 @@ def main(argv=None):
     world, rank, local = dist_env()
     if args.steps is None:
         args.steps = {"headline": wl.LARGE.generations, "batched": 300, "served": 0, "sweep": 50,
-                      "popsweep": 50, "select": 20}.get(args.workload)
+                      "popsweep": 50, "select": 20, "shapes": 10}.get(args.workload)
         if args.steps is None:
             args.steps = WORKLOADS[args.workload].generations if args.workload in WORKLOADS else 20
     if args.impl == "reference":
@@ -1334,6 +1413,8 @@ def main(argv=None):
         run_sweep(args, world, rank, local)
     elif args.workload == "select":
         run_select(args, world, rank, local)
+    elif args.workload == "shapes":
+        run_shapes(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

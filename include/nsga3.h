@@ -83,6 +83,13 @@ typedef struct {
                                0 (default) none; 1 around the dominance build and the
                                front peel only; 2 around every phase.  Each event node
                                adds a few microseconds to every replay */
+    int dom_ctas_per_sm;    /* launch shape of the dominance build (m <= 10): persistent
+                               CTAs per SM, 0 (default) = as many as are resident at once;
+                               larger values are clamped to that.  Results do not depend
+                               on it (a tuning knob, swept by bench.py --workload shapes) */
+    int peel_ctas_per_sm;   /* launch shape of the cooperative front peel: CTAs per SM,
+                               0 (default) = as many as are resident at once; larger values
+                               are clamped to that.  Results do not depend on it */
 } nsga3_opts;
 
 /* Fills *o with the defaults above (seed 0, single layer, tau 0.5). */

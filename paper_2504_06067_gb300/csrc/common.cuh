@@ -204,6 +204,8 @@ struct RunView {
     // split over dom_ks CTAs, which OR their sign masks into dpa / dpb
     // (NW x ld, laid out like Dom; zero between selections)
     int dom_ks;
+    int dom_ctas;          // dominance build: persistent CTAs per SM (0: all resident)
+    int peel_ctas;         // front peel: cooperative CTAs per SM (0: all resident)
     uint32_t* dpa;         // "some f_i > f_j" bits of row i against column block jb
     uint32_t* dpb;         // "some f_j > f_i"
 };

@@ -453,6 +453,8 @@ nsga3_status setup_alloc(nsga3_ctx* ctx)
     v.streaming = ctx->opts.streaming ? 1 : 0;
     v.norm_history = ctx->opts.norm_history ? 1 : 0;
     v.problem = ctx->opts.problem;
+    v.dom_ctas = ctx->opts.dom_ctas_per_sm;
+    v.peel_ctas = ctx->opts.peel_ctas_per_sm;
     v.wait_ns = (unsigned long long)(ctx->opts.wait_ms > 0 ? ctx->opts.wait_ms : 20000) * 1000000ull;
     v.seed = ctx->opts.seed;
     v.eta_c = ctx->opts.eta_c;
@@ -757,6 +759,8 @@ nsga3_status ctx_fields(nsga3_ctx* ctx, int m, int d, int N, int ref_divisions, 
     if (o.problem != 0 && o.problem != 1) return fail(ctx, NSGA3_EINVAL, "problem %d unknown", o.problem);
     if (o.phase_timing < 0 || o.phase_timing > 2)
         return fail(ctx, NSGA3_EINVAL, "phase_timing %d outside [0, 2]", o.phase_timing);
+    if (o.dom_ctas_per_sm < 0 || o.dom_ctas_per_sm > 64 || o.peel_ctas_per_sm < 0 || o.peel_ctas_per_sm > 64)
+        return fail(ctx, NSGA3_EINVAL, "CTAs per SM outside [0, 64]");
     if (o.streaming && m > NSGA3_FAST_M)
         return fail(ctx, NSGA3_EINVAL, "streaming dominance supports m <= %d", NSGA3_FAST_M);
     if (o.problem == 1 && m > NSGA3_FAST_M)

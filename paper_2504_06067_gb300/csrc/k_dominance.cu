@@ -1060,7 +1060,9 @@ cudaError_t launch_dom_m(const RunView& v, cudaStream_t s)
         cudaGetLastError();
         occ = 4;
     }
-    long long grid = (long long)(occ > 0 ? occ : 4) * v.num_sms;
+    int per_sm = occ > 0 ? occ : 4;
+    if (v.dom_ctas > 0 && v.dom_ctas < per_sm) per_sm = v.dom_ctas;  // launch-shape option
+    long long grid = (long long)per_sm * v.num_sms;
     if (grid > tiles) grid = tiles;
     k_dominance<M><<<(unsigned)grid, 256, dom_smem_bytes<M>(), s>>>(v);
     return cudaGetLastError();

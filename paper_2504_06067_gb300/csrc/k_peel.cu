@@ -283,8 +283,10 @@ int g_peel_occ[2] = {0, 0};  // resident peel CTAs per SM (matrix, streaming), s
 cudaError_t launch_peel(const RunView& v, int num_sms, cudaStream_t s)
 {
     const int nchunks = v.ld / NSGA3_PEEL_COLS;
-    const int occ = g_peel_occ[v.streaming ? 1 : 0];
-    int grid = num_sms * (occ > 0 ? occ : 1);
+    int occ = g_peel_occ[v.streaming ? 1 : 0];
+    if (occ <= 0) occ = 1;
+    if (v.peel_ctas > 0 && v.peel_ctas < occ) occ = v.peel_ctas;  // launch-shape option
+    int grid = num_sms * occ;
     if (v.shared_gpu) {
         // a quarter of the chunks per pass at most: every CTA of a cooperative
         // launch must be resident at once, which a mix of runs rarely allows

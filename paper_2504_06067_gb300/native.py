@@ -50,6 +50,8 @@ class nsga3_opts(C.Structure):
         ("kp_capacity", C.c_void_p),
         ("wait_ms", C.c_int),
         ("phase_timing", C.c_int),
+        ("dom_ctas_per_sm", C.c_int),
+        ("peel_ctas_per_sm", C.c_int),
     ]
 
 

@@ -120,3 +120,15 @@ def test_streaming_workspace_has_no_matrix(lib):
     NW = ld // 32
     bitmap = -(-NW * (-(-NW // 8)) // 256) * 256  # one bit per 32 x 32 block of the matrix
     assert full - stream == ld * ld // 8 - 256 + bitmap
+
+
+def test_launch_shape_options(lib):
+    """opts.dom_ctas_per_sm and opts.peel_ctas_per_sm default to 0 (every CTA
+    that fits at once) and take 0 ... 64."""
+    from paper_2504_06067_gb300 import native as n
+    o = n.default_opts()
+    assert o.dom_ctas_per_sm == 0 and o.peel_ctas_per_sm == 0
+    out = C.c_uint64()
+    for dc, pc, want in ((0, 0, n.OK), (1, 2, n.OK), (64, 64, n.OK), (-1, 0, n.EINVAL), (0, 65, n.EINVAL)):
+        o = n.default_opts(dom_ctas_per_sm=dc, peel_ctas_per_sm=pc)
+        assert n.nsga3_workspace_bytes(10, 12, 500, 3, C.byref(o), C.byref(out)) == want

@@ -190,3 +190,15 @@ def test_phase_timing_levels(n):
     for P in pops[1:]:
         for a, b in zip(pops[0], P):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dc,pc", [(1, 0), (2, 1), (3, 2), (0, 1)])
+def test_launch_shapes_change_nothing(n, orc, dc, pc):
+    """The launch-shape options (persistent CTAs per SM of the dominance
+    build, cooperative CTAs per SM of the peel) change no result: selections
+    of several shapes equal the oracle's."""
+    for m, N, p1, p2, kind in ((10, 3000, 3, 2, "early"), (5, 2000, 6, 0, "late"), (3, 4000, 40, 0, "dups")):
+        Z = orc.refdirs(m, p1, p2, 0.5)
+        with Run(n, m, m + 1, N, p1, p2=p2, seed=4, dom_ctas_per_sm=dc, peel_ctas_per_sm=pc) as r:
+            F = wl.objectives(kind, 2 * N, m, seed=dc + 3 * pc)
+            _compare(orc, r, F, Z, seed=4, gen=2)
