@@ -542,6 +542,7 @@ __global__ void __launch_bounds__(256) k_pick(RunView v)
         if (v.rho[j] == 0) {
             double bd = CUDART_INF;
             int bi = 0x7fffffff;
+#pragma unroll 4
             for (int e = lane; e < cnt; e += 32) {
                 const int i = v.bucket[off + e];
                 if (lex_less(v.dist[i], i, bd, bi)) {
@@ -645,7 +646,11 @@ cudaError_t launch_pick(const RunView& v, cudaStream_t s)
     k_pick<<<blocks, 256, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_pick_large<<<16, 512, 0, s>>>(v);
+    // one CTA per reference with a partial take, up to two per SM (how many
+    // there are is known on the device only: CTAs without one exit)
+    int lblocks = v.w < 2 * v.num_sms ? v.w : 2 * v.num_sms;
+    if (lblocks < 16) lblocks = 16;
+    k_pick_large<<<lblocks, 512, 0, s>>>(v);
     return cudaGetLastError();
 }
 
