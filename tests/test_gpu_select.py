@@ -202,3 +202,20 @@ def test_launch_shapes_change_nothing(n, orc, dc, pc):
         with Run(n, m, m + 1, N, p1, p2=p2, seed=4, dom_ctas_per_sm=dc, peel_ctas_per_sm=pc) as r:
             F = wl.objectives(kind, 2 * N, m, seed=dc + 3 * pc)
             _compare(orc, r, F, Z, seed=4, gen=2)
+
+
+@pytest.mark.parametrize("m", list(range(2, 11)))
+def test_dominance_entry_paths_every_m(n, orc, m):
+    """Every specialised dominance kernel (m = 2 ... 10): odd m takes the
+    scalar subtraction for its last objective in the live-column loop, m > 6
+    the early end after five objectives; early (many fronts), late and
+    simplex objective sets give entries with and without live rows and
+    columns, packed and unpacked row pairs.  Ranks and selections equal the
+    oracle's."""
+    N = 2500
+    p = wl.largest_p(m, N)
+    Z = orc.refdirs(m, p)
+    with Run(n, m, m + 1, N, p, seed=6) as r:
+        for s, kind in enumerate(("early", "late", "simplex")):
+            F = wl.objectives(kind, 2 * N, m, seed=40 + s)
+            _compare(orc, r, F, Z, seed=6, gen=s + 1)
