@@ -215,6 +215,28 @@ def ncu_traffic(kernel, workload):
     return None
 
 
+def ncu_issue_active(kernel):
+    """smsp__issue_active of `kernel` from the committed full-set capture
+    (profiles/issue.txt: kernel, workload of the capture, fraction, source
+    hash), or None when absent or taken on a different kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "issue.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) != 4 or line.startswith("#") or parts[0] != kernel:
+            continue
+        src = os.path.join(ROOT, "paper_2504_06067_gb300", "csrc", parts[3].split(":")[0])
+        try:
+            got = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        except OSError:
+            return None
+        if got == parts[3].split(":")[1]:
+            return {"value": float(parts[2]), "capture": parts[1], "source": "profiles/issue.txt"}
+    return None
+
+
 # ------------------------------------------------------------- our impl ----
 PHASE_NAMES = ["variation", "reset", "dominance", "peel", "niching", "gather", "total"]
 
@@ -421,6 +443,7 @@ def roofline_of(cfg, avg_ms, peel_rows_per_step, probe, peaks, peak_kind, domsta
                                    "row_dom_col": domstat[2] / tot, "col_dom_row": domstat[3] / tot,
                                    "both": domstat[4] / tot, "tiles_skipped": int(domstat[5])}
             roof["all_pairs_compare_rate"] = all_ops / sec / 1e12
+            roof["issue_active_ncu"] = ncu_issue_active("k_dominance")
             roof["dense_matrix_gbs"] = (n2 * n2 / 8 + n2 * cfg.m * 4) / sec / 1e9
         return roof
     bytes_read = peel_rows_per_step * 128 * 4.0  # row segments of 128 columns
