@@ -268,7 +268,7 @@ __device__ __forceinline__ void put_block(const RunView& v, size_t at, uint32_t 
     if (lane_id() == 0 && nzw) atomicOr(&nzw[byte >> 2], 1u << (8 * (byte & 3) + bit));
 }
 
-// Position of the (t+1)-th set bit of x (t < popc(x)): a binary search on
+// Position of the (t+1)-th set bit of x (31 when t >= popc(x)): a binary search on
 // the popcounts of halving windows.
 __device__ __forceinline__ int nth_set_bit(uint32_t x, int t)
 {
@@ -456,9 +456,10 @@ __device__ __forceinline__ void entry_row_dom_col(const RunView& v, const float*
     if (!live) return;
     const int nl = __popc(live);
     const uint32_t low = nl == 32 ? 0xffffffffu : (1u << nl) - 1u;
-    // lane t: shared-memory byte address of the t-th live column
-    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(colp) +
-                          (uint32_t)(lane < nl ? nth_set_bit(live, lane) : 0) * (uint32_t)(M4 * 4);
+    // lane t < nl: shared-memory byte address of the t-th live column (every
+    // lane searches, without a branch; lanes from nl on get a column of the
+    // block that is never read)
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(colp) + (uint32_t)nth_set_bit(live, lane) * (uint32_t)(M4 * 4);
     const uint32_t b0 = __ballot_sync(0xffffffffu, l0);
     const uint32_t b1 = __ballot_sync(0xffffffffu, l1);
     const int n0 = __popc(b0), nr = n0 + __popc(b1);
@@ -469,7 +470,9 @@ __device__ __forceinline__ void entry_row_dom_col(const RunView& v, const float*
         float fp[M];
         const bool first = lane < n0;
         if (two) {
-            const int src = lane < nr ? nth_set_bit(first ? b0 : b1, first ? lane : lane - n0) : 0;
+            // (lanes from nr on find no set bit and get row 31 of the second
+            // block, whose result is never read)
+            const int src = nth_set_bit(first ? b0 : b1, first ? lane : lane - n0);
             load_row<M, M4>(fp, srow + ((ri + (first ? 0 : 1)) * 32 + src) * M4);
         } else {
 #pragma unroll
