@@ -5,18 +5,22 @@
 // dominates j": a column j's dominators are NW words with j contiguous
 // across rows, which the front peel reads coalesced.
 //
-// Work: only unordered pairs are compared.  A CTA owns a 256 x 256 tile of
-// the upper block triangle; each warp takes two row blocks (lane = one row
-// of each, objectives in registers) against four column blocks jb >= ib,
-// the column points broadcast from shared memory to both rows.  Per
-// pair the m differences f_j - f_i and f_i - f_j run on the FMA pipe and
-// their sign bits are OR-ed (3-input LOP3): A = "no f_i > f_j" and
-// B = "no f_j > f_i"; "i dom j" = A & !B, "j dom i" = B & !A (identical
-// vectors: neither).  -0.0 is turned into +0.0 when the tile is staged.
-// Points are in bucket order of f_0 (k_sort.cu); when the row block's
-// largest f_0 is below the column block's smallest, only "i dom j" is
-// possible, strictness is implied by f_i0 < f_j0, and the test needs the
-// m - 1 differences of objectives 1..m-1 only.
+// Work: only unordered pairs are compared.  Persistent CTAs take 256 x 256
+// tiles of the upper block triangle from the tile plan; the tile's 32 x 32
+// block pairs are decided from per-block bounding boxes (no test, one
+// direction, or both), and the warps take the pairs to test from a shared
+// work list, lane = one row, objectives in registers, the column points
+// broadcast from shared memory.  Per pair the m differences f_j - f_i and
+// f_i - f_j run on the FMA pipe and their sign bits are OR-ed (3-input
+// LOP3): A = "no f_i > f_j" and B = "no f_j > f_i"; "i dom j" = A & !B,
+// "j dom i" = B & !A (identical vectors: neither).  -0.0 is turned into
+// +0.0 when the tile is staged.  Points are in sort-key order (k_sort.cu:
+// a dominator never has a larger key).  A block pair where only "row
+// dominates column" can hold tests only the live rows (no objective above
+// the column block's maximum) against the live columns (no objective below
+// the live rows' minimum), two objectives per sub.rn.f32x2, the live rows
+// of two row blocks packed onto one set of lanes when they fit
+// (entry_row_dom_col).
 // "j dom i" bits gathered over j are already column words Dom[jb][i];
 // "i dom j" bits gathered over j are row words and are transposed in-warp
 // (32 x 32 bit transpose by five shuffle stages) into Dom[ib][j].
